@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the VCT + SPH(2) step: particle-updates/s per SPH(2) step.
+
+Workload: the 2-D sigma-SPH solitary wave (H/d = 0.2) over a Gaussian bump
+(0.3 m high, 1 m wide) in a 10 m channel of depth 0.5 m, 42,480 fluid
+particles on a regular projected lattice (d0 = 1/90 m), mixed precision
+(FP32 compensated neighbour sums, FP64 solves and pressure iterate).  Inputs
+are the seeded synthetic scenario of paper_2607_28872_b300.scenarios.
+
+One step = one call of vct_step for one time step: map + cell sort,
+neighbours, Jbar smoothing, SPH(2) passes, predictor, pressure equation,
+BiCGSTAB, corrector.  The working set (~50 MB) fits in L2, so L2 is flushed
+(256 MB write) before every timed step, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain reference program of
+this project) on the host cores, on a bounded slice of the same workload.
+Multi-GPU: independent replicas (the step has no data-parallel split that
+avoids per-iteration halo exchange), one per rank, scaling "weak".
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s per SPH(2) step"
+UNIT = "particle-updates/s"
+WORKLOAD = ("2-D sigma-SPH solitary wave (H/d=0.2) over a 0.3 m Gaussian bump, 10 m x 0.5 m "
+            "channel, d0=1/90 m, mixed FP32/FP64")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(precision=1):
+    from paper_2607_28872_b300 import scenarios as S
+    return S.solitary_sigma(precision=precision)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per unit of each stage (compulsory traffic: every array
+# read or written once per pass; neighbour re-reads are not counted)
+# ---------------------------------------------------------------------------
+def krylov_bytes(iters, rows, nnz):
+    """BiCGSTAB launch: per unknown row and iteration, vectors 136 B (phase A
+    reads r, p, v, rh and writes p', v'; B reads r, v' and writes s, t; C reads
+    s, t, p', x, rh and writes x, r) plus the operator twice (pcnt 4 + diag 8 +
+    12 B per coefficient); set-up reads x, b and the operator once and writes
+    r, rh, p, v."""
+    nnz_row = nnz / max(rows, 1)
+    per_row_iter = 136 + 2 * (12 + 12 * nnz_row)
+    setup = 16 + 32 + 12 + 12 * nnz_row
+    return rows * (iters * per_row_iter + setup)
+
+
+def stage_bytes(stage, n, nf, dim, rows, nnz, nbr_row):
+    m = 3 if dim == 2 else 6
+    d = dim
+    if stage == "pass1":   # reads pos^, pos, vel, type, J, jbar, nbr list; writes L, gv, Ct, rho, lam, fs, nu
+        return nf * (8 * (3 * d + 3) + 4 + 4 * nbr_row + 8 * (2 * d * d + d * m + 3) + 4)
+    if stage == "pass2":   # reads L, Ct, gv, nu, pos^, vel, metric; writes acc, v*, coefficients
+        return nf * (8 * (2 * d * d + d * m + 1 + 2 * d + 4) + 4 * nbr_row + 8 * 2 * d
+                     + 12 * (nnz / max(rows, 1)) + 8 * 3 + 4)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2607_28872_b300 import vct
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sc = workload(args.precision)
+    n_fluid = sc.n_fluid
+    cpu_base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_base = cpu_baseline_sample(sc)
+
+    solver = vct.Solver(sc)
+    state = vct.DeviceState(sc)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        solver.vct_step(state, 1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    solver.vct_set_profiling(True)
+    total_ms = 0.0
+    iters = 0
+    launches = 0
+    last = None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = solver.vct_step(state, 1)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        iters += st.krylov_iters_total
+        launches += st.kernel_launches
+        last = st
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stages = solver.vct_stage_times()
+    solver.vct_set_profiling(False)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * n_fluid * args.steps / (total_ms / 1e3)
+
+    # e2e: the host-buffer entry point, copies in and out inside the timed region
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        s2 = vct.Solver(sc)
+        host = vct.HostState(sc, pin=True)
+        s2.vct_step_host(host, 1)
+        k = args.e2e_steps
+        t0 = time.perf_counter()
+        for _ in range(k):
+            s2.vct_step_host(host, 1)
+        dt = time.perf_counter() - t0
+        narr = 6 if sc.dim == 2 else 8
+        e2e = {"value": n_fluid * k / dt, "unit": UNIT,
+               "h2d_bytes_per_step": narr * 8 * sc.n + 4 * sc.n,
+               "d2h_bytes_per_step": narr * 8 * sc.n}
+        s2.close()
+
+    # roofline of the dominant stage
+    dom = max(stages.items(), key=lambda kv: kv[1][0])
+    name, (ms, cnt) = dom
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    rows, nnz = last.ppe_rows, last.ppe_nnz
+    if name == "krylov":
+        per_launch = krylov_bytes(iters / args.steps, rows, nnz)
+    else:
+        per_launch = stage_bytes(name, sc.n, n_fluid, sc.dim, rows, nnz, 20 if sc.dim == 2 else 56)
+    avg_ms = ms / max(cnt, 1)
+    achieved = per_launch / (avg_ms / 1e3) / 1e9 if per_launch else None
+    roof = {"kernel": {"krylov": "k_bicgstab"}.get(name, name), "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+            "peak_source": "measured" if peaks else "fallback",
+            "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": per_launch,
+            "note": "operator + vectors (~15 MB) are L2-resident within a step; L2 flushed between steps"}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == 1 else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_fluid": n_fluid, "n_particles": sc.n,
+                       "dt": sc.params["dt"], "krylov_rtol": sc.params["krylov_rtol"],
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "krylov_iters_per_step": iters / args.steps,
+            "stage_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in stages.items()},
+            "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_time(sc, nsteps):
+    from oracle import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    st = O.OracleState(sc)
+    t0 = time.perf_counter()
+    st, info = O.step(sc, st, nsteps=nsteps, rtol=sc.params["krylov_rtol"])
+    dt = time.perf_counter() - t0
+    return dt, cores, info
+
+
+def cpu_baseline_sample(sc, nsteps=1):
+    """The oracle as it stands, one step of the full workload on the host cores."""
+    dt, cores, info = _oracle_time(sc, nsteps)
+    return {"value": sc.n_fluid * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} step of the full {sc.n_fluid}-fluid-particle workload "
+                      f"({dt:.1f} s, BiCGSTAB rtol {sc.params['krylov_rtol']:g})"}
+
+
+def run_reference(args):
+    """The oracle (FP64 CPU reference) on the host cores, a bounded slice of the
+    workload per step so that --steps K --warmup W ends within a few minutes."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2607_28872_b300 import scenarios as S
+    budget_s = 150.0
+    full_step_s = 8.0          # measured order of one oracle step on the full channel
+    frac = min(1.0, max(0.08, budget_s / ((args.steps + args.warmup) * full_step_s)))
+    L = 10.0 * frac
+    sc = S.solitary_sigma(L=L, bump_x=0.5 * L, x0=0.2 * L, precision=args.precision)
+    from oracle import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    st = O.OracleState(sc)
+    if args.warmup:
+        st, _ = O.step(sc, st, nsteps=args.warmup, rtol=sc.params["krylov_rtol"])
+    t0 = time.perf_counter()
+    st, info = O.step(sc, st, nsteps=args.steps, rtol=sc.params["krylov_rtol"])
+    dt = time.perf_counter() - t0
+    value = sc.n_fluid * args.steps / dt
+    sample = (f"channel slice L={L:.2f} m ({sc.n_fluid} fluid particles) of the 10 m workload, "
+              f"{args.steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_fluid": sc.n_fluid, "sample_fraction": frac},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

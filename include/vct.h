@@ -1,0 +1,216 @@
+/*
+ * vct.h -- C ABI of the VCT + SPH(2) free-surface step on one B300 (sm_103a).
+ *
+ * The method: incompressible SPH with SPH(2) second derivatives, run in a
+ * vertically transformed ("projected") coordinate r^ = (x, y, alpha (z + beta))
+ * (Sec. 2.1, Eq. VCT) with the E, BF, BFE and sigma maps of Sec. 2.2.  One
+ * step is the projection scheme of Sec. 3.3 written with the VCT metric
+ * (Eqs. VCT_predictor, VCT_ppe / VCT_ppe_w, VCT_update).
+ *
+ * Conventions shared by every entry point
+ *  - All particle arrays are structure-of-arrays, one value per particle,
+ *    indexed by the caller's particle index i in [0, n).  That index is the
+ *    particle's id: neighbour lists are sorted by it and outputs are written
+ *    at it.  In 2-D the vertical axis is z; y and v are ignored (may be NULL).
+ *  - Particle type (int32): 0 fluid, 1 wall (on the wall surface), 2 virtual
+ *    (outside the wall; enters only the density and the free-surface test),
+ *    Sec. 3.5.
+ *  - Pointers are DEVICE pointers unless stated otherwise.  The caller owns
+ *    every buffer it passes; the context owns its scratch, allocated once in
+ *    vct_init up to `capacity` particles.  No call allocates device memory
+ *    after vct_init.
+ *  - Work is queued on the context's stream.  Calls that return a status
+ *    synchronise that stream once at their end to read the device status
+ *    word; nothing else blocks.
+ *  - Errors: every call returns a vct_status; no C++ exception crosses the
+ *    ABI.  Device-side problems (singular moment matrix, non-finite state,
+ *    Krylov not converged, neighbour capacity, spin-wait timeout) are sticky
+ *    in the context until the next call; vct_last_error() names the first
+ *    offending particle.  After an error the caller's state is left as it was
+ *    at the start of the failed call (vct_step writes back only on success).
+ *  - Units are the caller's (SI in this project's workloads).
+ */
+#ifndef VCT_H
+#define VCT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VCT_OK = 0,
+    VCT_ERR_ARG = 1,        /* invalid argument (NULL, size, dimension, capacity) */
+    VCT_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    VCT_ERR_CAPACITY = 3,   /* more neighbours than max_neighbours, or n > capacity */
+    VCT_ERR_SINGULAR = 4,   /* B_i or M_i not invertible (isolated particle) */
+    VCT_ERR_NONFINITE = 5,  /* NaN/Inf in the updated state */
+    VCT_ERR_NOCONV = 6,     /* pressure solve did not reach krylov_rtol in krylov_max_iter */
+    VCT_ERR_TIMEOUT = 7     /* a bounded device spin-wait gave up */
+} vct_status;
+
+/* Sec. 2.2: E (alpha = aspect, beta = 0), BF (alpha = 1, beta = -h),
+ * BFE (alpha = aspect, beta = -h), sigma (alpha = H_hat/(H - h), beta = -h,
+ * alpha clamped to [alpha_min, alpha_max] with zero derivatives outside). */
+typedef enum { VCT_MAP_E = 0, VCT_MAP_BF = 1, VCT_MAP_BFE = 2, VCT_MAP_SIGMA = 3 } vct_map_kind;
+
+/* FP64: every sum and solve in double.  MIXED: neighbour sums in FP32 with
+ * compensated (Kahan) accumulation, pair offsets r_ij formed in FP64 and
+ * rounded to FP32, the cancelling difference phi_ij - r_ij . <grad phi>_i
+ * formed in FP64; inversion of B_i, the SPH(2) solves with M_i and the
+ * pressure-equation iterate and residual in FP64. */
+typedef enum { VCT_FP64 = 0, VCT_MIXED = 1 } vct_precision;
+
+#define VCT_MAX_GAUSS 32
+
+/* Bottom elevation h(x,y) = h0 + slope_x x + slope_y y + cos_amp cos(2 pi x / cos_len)
+ * + sum_g amp_g exp(-((x-cx_g)^2 + (y-cy_g)^2) / (2 width_g^2)).
+ * Covers the bottoms of Sec. 4 (flat, linear, cosine, Gaussian bumps).
+ * amp/cx/cy/width are HOST arrays of n_gauss <= VCT_MAX_GAUSS entries,
+ * copied by vct_init. */
+typedef struct {
+    double h0, slope_x, slope_y, cos_amp, cos_len;
+    int32_t n_gauss;
+    int32_t reserved;
+    const double *amp, *cx, *cy, *width;
+} vct_bathymetry;
+
+typedef struct {
+    int32_t dim;            /* 2 (x, z) or 3 (x, y, z) */
+    int32_t reserved0;
+    double rho;             /* reference density */
+    double nu_k;            /* kinematic viscosity */
+    double g;               /* gravity magnitude, acting along -z */
+    double dt;              /* time step */
+    double d0;              /* projected particle spacing; V0 = d0^dim */
+    double l_over_d0;       /* smoothing length l = l_over_d0 d0 (1.2, Sec. 3.1) */
+    double re_over_l;       /* effective radius r_e = re_over_l l (2.0) */
+    double gamma_over_dt;   /* stabilisation gamma = gamma_over_dt dt (100, Sec. 3.3) */
+    double cv_over_dt;      /* volume smoothing C_V = cv_over_dt dt (100, Sec. 4.4.2) */
+    double cs;              /* Smagorinsky constant (0.2, Sec. 3.4) */
+    double ds;              /* reference spacing of the wall damping (0.01 m) */
+    double H, H_hat;        /* sigma map: still-water level and projected height */
+    double alpha_min, alpha_max; /* sigma map clamp */
+    double lam_fs_lo, lam_fs_hi; /* free-surface eigenvalue thresholds (0.2, 0.75) */
+    double krylov_rtol;     /* relative residual of the pressure solve */
+    int32_t krylov_max_iter;
+    int32_t smagorinsky;    /* 1: eddy viscosity on (Sec. 3.4) */
+    int32_t precision;      /* vct_precision */
+    int32_t volume_mode;    /* 0: Eq. VCT_ppe; 1: Eq. VCT_ppe_w0 (Jbar = J^0); 2: Eq. VCT_ppe_w */
+    double box_lo[3], box_hi[3]; /* projected-space box of the cell grid; particles
+                                    outside are clamped into the border cells */
+    int32_t max_neighbours; /* neighbour-list capacity per particle (0: 64 in 2-D, 160 in 3-D) */
+    int32_t reserved1;
+} vct_params;
+
+/* Particle state, caller order, DEVICE arrays of n entries (host arrays for
+ * vct_step_host).  jbar <= 0 means "set Jbar = J at the first step". */
+typedef struct {
+    int64_t n;
+    double *x, *y, *z;      /* physical position */
+    double *u, *v, *w;      /* physical velocity */
+    double *p;              /* pressure */
+    double *jbar;           /* smoothed Jacobian Jbar (Sec. 3.6) */
+    const int32_t *type;    /* 0 fluid, 1 wall, 2 virtual */
+} vct_state;
+
+typedef struct {
+    int64_t steps_done;
+    int64_t krylov_iters_total;
+    int32_t krylov_iters_max;
+    int32_t reserved;
+    double last_residual;   /* relative residual of the last pressure solve */
+    int64_t ppe_rows;       /* unknowns (fluid, not free surface) of the last step */
+    int64_t ppe_nnz;        /* off-diagonal coefficients of the last step's operator */
+    int64_t kernel_launches;/* kernels this call launched */
+} vct_stats;
+
+/* Stages timed by vct_stage_times, in step order. */
+typedef enum {
+    VCT_STAGE_LOAD = 0, VCT_STAGE_MAP, VCT_STAGE_SORT, VCT_STAGE_NEIGHBOURS,
+    VCT_STAGE_SMOOTHING, VCT_STAGE_PASS1, VCT_STAGE_PASS2, VCT_STAGE_RHS,
+    VCT_STAGE_KRYLOV, VCT_STAGE_CORRECTOR, VCT_STAGE_STORE, VCT_NSTAGES
+} vct_stage;
+
+/* Device buffers (caller order) that vct_step_probe fills for its single
+ * step; any pointer may be NULL. */
+typedef struct {
+    int32_t *fs;            /* free-surface flag (1: Dirichlet p = 0) */
+    double *rho_hat;        /* <rho^>_i, projected numerical density */
+    double *nu;             /* nu_K + nu_E */
+    double *lam_min;        /* smallest eigenvalue of B_i over all particle types */
+    double *vstar;          /* predictor velocity, dim x n component-major */
+    double *ppe_b;          /* right side of A p = b on unknown rows (0 elsewhere) */
+    const double *x_test;   /* optional input vector, n entries */
+    double *ppe_Ax;         /* A x_test on unknown rows (0 elsewhere) */
+    double *jbar_used;      /* Jbar after this step's volume smoothing */
+} vct_probe;
+
+typedef struct vct_ctx vct_ctx;
+
+/* Create a context: validates parameters, copies the bathymetry, allocates
+ * all scratch for up to `capacity` particles on the current CUDA device.
+ * stream: a cudaStream_t (NULL = legacy default stream).  (Sec. 2, Sec. 3.) */
+vct_status vct_init(vct_ctx **ctx, const vct_bathymetry *bathy, vct_map_kind kind,
+                    double aspect_ratio, const vct_params *params, int64_t capacity,
+                    void *stream);
+
+vct_status vct_set_stream(vct_ctx *ctx, void *stream);
+
+/* Neighbour sets S_i = { j != i : |r^_j - r^_i| < r_e } in projected space
+ * (Eq. SPH_neighbor_set), squared distance summed in coordinate order without
+ * FMA.  Writes CSR over caller indices: row_ptr (n+1 int64, device) and col
+ * (device, capacity col_cap) with each row sorted by ascending index; either
+ * may be NULL to get only *nnz (host).  VCT_ERR_CAPACITY if col_cap < nnz. */
+vct_status vct_build_neighbours(vct_ctx *ctx, const vct_state *state, int64_t *row_ptr,
+                                int32_t *col, int64_t col_cap, int64_t *nnz);
+
+/* SPH(2) derivatives of ncomp fields phi (ncomp x n, component-major, all
+ * particle types; wall values enter the sums) at the fluid particles:
+ *   grad_hat[(c*dim + K)*n + i] = <d phi_c / d x^_K>^(1)           (Eq. gra_1st)
+ *   d2_hat[(c*m + a)*n + i]     second projected derivatives, m = 3 in 2-D
+ *                               [xx, zz, xz], m = 6 in 3-D [xx, yy, zz, xy, yz, zx]
+ *                               (Eq. sec_SPH2, cross derivatives not doubled)
+ *   lap_phys[c*n + i]           c_trans . D^ phi, the physical Laplacian (Eq. lap_VCT)
+ * Non-fluid entries are 0.  Any output may be NULL.  Sums run over fluid and
+ * wall neighbours (virtual particles excluded), in the context's precision. */
+vct_status sph2_derivatives(vct_ctx *ctx, const vct_state *state, const double *phi,
+                            int32_t ncomp, double *grad_hat, double *d2_hat, double *lap_phys);
+
+/* Advance the state by nsteps steps of Sec. 3.3 with the VCT equations:
+ * map + cell sort, neighbours, Jbar smoothing (sigma, volume_mode 2),
+ * corrected gradients, free surface, eddy viscosity, SPH(2) predictor,
+ * pressure equation with wall Neumann extrapolation (Eq. PNC), BiCGSTAB,
+ * corrector and position update.  Device arrays, updated in place on success.
+ * out (host, may be NULL) receives solve statistics. */
+vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *out);
+
+/* Same as vct_step with HOST arrays: copies in, steps, copies back. */
+vct_status vct_step_host(vct_ctx *ctx, vct_state *host_state, int32_t nsteps, vct_stats *out);
+
+/* One step like vct_step that also writes the intermediate fields named in
+ * probe (device buffers, caller order). */
+vct_status vct_step_probe(vct_ctx *ctx, vct_state *state, const vct_probe *probe,
+                          vct_stats *out);
+
+/* Profiling: when on, every stage of every step (up to 512 steps per call) is
+ * bracketed by CUDA events on the context's stream; vct_stage_times adds the
+ * elapsed device milliseconds per stage and the number of bracketed launches
+ * (host arrays of VCT_NSTAGES).  Turning profiling on resets the totals.  Off
+ * by default; when off no event is recorded. */
+vct_status vct_set_profiling(vct_ctx *ctx, int32_t on);
+vct_status vct_stage_times(vct_ctx *ctx, double *ms, int64_t *launches);
+
+/* First failing particle of the last error (caller index, -1 if none). */
+vct_status vct_last_error(vct_ctx *ctx, int64_t *particle);
+
+const char *vct_strerror(vct_status status);
+
+void vct_destroy(vct_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VCT_H */

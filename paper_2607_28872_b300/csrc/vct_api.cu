@@ -1,0 +1,532 @@
+// C ABI of the VCT + SPH(2) library: context set-up, step orchestration,
+// neighbour export and the SPH(2) derivative entry point.  Every stage of the
+// path is one of the kernels in vct_kernels.cu; this file only allocates,
+// launches and reads the device status word.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "vct_internal.cuh"
+
+using namespace vct;
+
+struct vct_ctx {
+    DevParams P;
+    cudaStream_t st;
+    int64_t cap;
+    int device;
+    Part A, B;
+    bool cur_is_A;
+    Work W;
+    int coop_blocks;
+    // device mirror of a caller state for vct_step_host
+    vct_state mirror;
+    int64_t *row_int;          // CSR rows when the caller passes none
+    int32_t *host_status;      // pinned copy of status + stats
+    int64_t last_particle;
+    std::vector<void *> allocs;
+    // profiling
+    bool prof;
+    std::vector<cudaEvent_t> ev;      // 2 per stage per profiled step
+    std::vector<int> ev_stage;        // stage of each recorded pair
+    int ev_used;
+    double stage_ms[VCT_NSTAGES];
+    int64_t stage_n[VCT_NSTAGES];
+    int64_t launches;
+};
+
+namespace {
+
+constexpr int PROF_STEPS = 512;
+
+// Bracket a stage with events when profiling is on.
+struct StageTimer {
+    vct_ctx *c;
+    int stage;
+    int slot;
+    StageTimer(vct_ctx *c_, int s) : c(c_), stage(s), slot(-1)
+    {
+        if (c->prof && c->ev_used + 2 <= (int)c->ev.size()) {
+            slot = c->ev_used;
+            c->ev_used += 2;
+            c->ev_stage[slot / 2] = stage;
+            cudaEventRecord(c->ev[slot], c->st);
+        }
+    }
+    ~StageTimer()
+    {
+        if (slot >= 0) cudaEventRecord(c->ev[slot + 1], c->st);
+    }
+};
+
+void collect_times(vct_ctx *c)
+{
+    for (int k = 0; k + 1 < c->ev_used; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]) == cudaSuccess) {
+            c->stage_ms[c->ev_stage[k / 2]] += ms;
+            c->stage_n[c->ev_stage[k / 2]] += 1;
+        }
+    }
+    c->ev_used = 0;
+}
+
+vct_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? VCT_OK : VCT_ERR_CUDA; }
+
+template <typename T>
+T *dalloc(vct_ctx *c, int64_t count, cudaError_t &err)
+{
+    void *p = nullptr;
+    if (err != cudaSuccess) return nullptr;
+    size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    err = cudaMalloc(&p, bytes);
+    if (err == cudaSuccess) {
+        c->allocs.push_back(p);
+        cudaMemsetAsync(p, 0, bytes, c->st);
+    }
+    return (T *)p;
+}
+
+void alloc_part(vct_ctx *c, Part &p, cudaError_t &e)
+{
+    int64_t n = c->cap;
+    p.x = dalloc<double>(c, n, e); p.y = dalloc<double>(c, n, e); p.z = dalloc<double>(c, n, e);
+    p.u = dalloc<double>(c, n, e); p.v = dalloc<double>(c, n, e); p.w = dalloc<double>(c, n, e);
+    p.p = dalloc<double>(c, n, e); p.jbar = dalloc<double>(c, n, e);
+    p.type = dalloc<int32_t>(c, n, e); p.orig = dalloc<int32_t>(c, n, e);
+    p.xh = dalloc<double>(c, n, e); p.yh = dalloc<double>(c, n, e); p.zh = dalloc<double>(c, n, e);
+    p.J = dalloc<double>(c, n, e); p.sx = dalloc<double>(c, n, e); p.sy = dalloc<double>(c, n, e);
+    p.c0 = dalloc<double>(c, n, e); p.c3 = dalloc<double>(c, n, e);
+}
+
+Part &cur(vct_ctx *c) { return c->cur_is_A ? c->A : c->B; }
+Part &alt(vct_ctx *c) { return c->cur_is_A ? c->B : c->A; }
+
+vct_status check_state(vct_ctx *c, const vct_state *s)
+{
+    if (!c || !s) return VCT_ERR_ARG;
+    if (s->n <= 0 || s->n > c->cap) return s->n > c->cap ? VCT_ERR_CAPACITY : VCT_ERR_ARG;
+    if (!s->x || !s->z || !s->u || !s->w || !s->p || !s->jbar || !s->type) return VCT_ERR_ARG;
+    if (c->P.dim == 3 && (!s->y || !s->v)) return VCT_ERR_ARG;
+    return VCT_OK;
+}
+
+void reset_status(vct_ctx *c)
+{
+    c->launches = 0;
+    c->ev_used = 0;
+    cudaMemsetAsync(c->W.status, 0, sizeof(int32_t) * 4, c->st);
+    cudaMemsetAsync(c->W.kiters, 0, sizeof(int32_t) * 4, c->st);
+    cudaMemsetAsync(c->W.kresid, 0, sizeof(double), c->st);
+}
+
+// Reads the status word (synchronises the stream once).
+vct_status finish(vct_ctx *c, vct_stats *out, int nsteps)
+{
+    cudaError_t e = cudaMemcpyAsync(c->host_status, c->W.status, sizeof(int32_t) * 4,
+                                    cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->host_status + 4, c->W.kiters, sizeof(int32_t) * 4,
+                            cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->host_status + 8, c->W.kresid, sizeof(double),
+                            cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->host_status + 10, c->W.counts, 2 * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
+    int code = c->host_status[0];
+    c->last_particle = -1;
+    if (code != 0) {
+        int sorted = c->host_status[1];
+        if (sorted >= 0) {
+            int32_t o = -1;
+            cudaMemcpy(&o, cur(c).orig + sorted, sizeof(int32_t), cudaMemcpyDeviceToHost);
+            c->last_particle = o;
+        }
+    }
+    if (c->host_status[2] != 0 && code == 0) code = VCT_ERR_TIMEOUT;
+    if (out) {
+        out->steps_done = code == 0 ? nsteps : 0;
+        out->krylov_iters_total = c->host_status[4];
+        out->krylov_iters_max = c->host_status[5];
+        double r;
+        memcpy(&r, c->host_status + 8, sizeof(double));
+        out->last_residual = r;
+        int64_t cnt[2];
+        memcpy(cnt, c->host_status + 10, sizeof cnt);
+        out->ppe_rows = cnt[0];
+        out->ppe_nnz = cnt[1];
+        out->kernel_launches = c->launches;
+    }
+    if (c->prof) collect_times(c);
+    return (vct_status)code;
+}
+
+// Map, cell sort and neighbour lists of the current positions.
+void geometry(vct_ctx *c, int64_t n)
+{
+    { StageTimer t(c, VCT_STAGE_MAP); launch_map_key(c->P, cur(c), c->W, n, c->st); }
+    { StageTimer t(c, VCT_STAGE_SORT); launch_sort(c->P, cur(c), alt(c), c->W, n, c->st); }
+    c->cur_is_A = !c->cur_is_A;
+    { StageTimer t(c, VCT_STAGE_NEIGHBOURS); launch_neighbours(c->P, cur(c), c->W, n, c->st); }
+    c->launches += 1 + 6 + 1;   // map_key; scan x3, scatter, cell sort, reorder; neighbours
+}
+
+vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, vct_stats *out)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (nsteps < 0) return VCT_ERR_ARG;
+    const int64_t n = s->n;
+    reset_status(c);
+    { StageTimer t(c, VCT_STAGE_LOAD); launch_load(c->P, cur(c), *s, n, c->st); }
+    c->launches += 1;
+    for (int step = 0; step < nsteps; ++step) {
+        geometry(c, n);
+        if (c->P.kind == VCT_MAP_SIGMA && c->P.volume_mode == 2) {
+            StageTimer t(c, VCT_STAGE_SMOOTHING);
+            launch_smoothing(c->P, cur(c), c->W, n, c->st);
+            c->launches += 1;
+        }
+        cudaMemsetAsync(c->W.counts, 0, 2 * sizeof(int64_t), c->st);
+        { StageTimer t(c, VCT_STAGE_PASS1); launch_pass1(c->P, cur(c), c->W, n, c->st); }
+        { StageTimer t(c, VCT_STAGE_PASS2); launch_pass2(c->P, cur(c), c->W, n, 1, c->st); }
+        { StageTimer t(c, VCT_STAGE_RHS); launch_rhs(c->P, cur(c), c->W, n, c->st); }
+        int e;
+        {
+            StageTimer t(c, VCT_STAGE_KRYLOV);
+            e = launch_krylov(c->P, cur(c), c->W, n, step, c->coop_blocks, c->st);
+        }
+        if (e) return VCT_ERR_CUDA;
+        if (pr && step == nsteps - 1) {
+            launch_probe_out(c->P, cur(c), c->W, n, *pr, c->st);
+            c->launches += 1;
+            if (pr->x_test && pr->ppe_Ax) {
+                launch_probe_ax(c->P, cur(c), c->W, n, pr->x_test, pr->ppe_Ax, c->st);
+                c->launches += 2;
+            }
+        }
+        { StageTimer t(c, VCT_STAGE_CORRECTOR); launch_corrector(c->P, cur(c), c->W, n, c->st); }
+        c->launches += 5;   // pass1, pass2, rhs, krylov, corrector
+    }
+    { StageTimer t(c, VCT_STAGE_STORE); launch_store(c->P, cur(c), *s, n, c->W.status, c->st); }
+    c->launches += 1;
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, out, nsteps);
+}
+
+}  // namespace
+
+extern "C" {
+#define VCT_API __attribute__((visibility("default")))
+
+VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_kind kind,
+                    double aspect_ratio, const vct_params *prm, int64_t capacity, void *stream)
+{
+    if (!out || !bathy || !prm) return VCT_ERR_ARG;
+    *out = nullptr;
+    if (prm->dim != 2 && prm->dim != 3) return VCT_ERR_ARG;
+    if ((int)kind < 0 || (int)kind > 3) return VCT_ERR_ARG;
+    if (!(prm->d0 > 0) || !(prm->dt > 0) || !(prm->rho > 0) || capacity <= 0 ||
+        capacity > (int64_t)INT32_MAX / 4)
+        return VCT_ERR_ARG;
+    if (bathy->n_gauss < 0 || bathy->n_gauss > VCT_MAX_GAUSS) return VCT_ERR_ARG;
+    if (bathy->n_gauss > 0 && (!bathy->amp || !bathy->cx || !bathy->cy || !bathy->width))
+        return VCT_ERR_ARG;
+    if ((kind == VCT_MAP_E || kind == VCT_MAP_BFE) && !(aspect_ratio > 0)) return VCT_ERR_ARG;
+    if (kind == VCT_MAP_SIGMA && !(prm->H_hat > 0 && prm->alpha_min > 0 &&
+                                   prm->alpha_max >= prm->alpha_min))
+        return VCT_ERR_ARG;
+    if (prm->precision != VCT_FP64 && prm->precision != VCT_MIXED) return VCT_ERR_ARG;
+    if (prm->volume_mode < 0 || prm->volume_mode > 2) return VCT_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!(prm->box_hi[k] >= prm->box_lo[k])) return VCT_ERR_ARG;
+
+    vct_ctx *c = new (std::nothrow) vct_ctx();
+    if (!c) return VCT_ERR_ARG;
+    c->st = (cudaStream_t)stream;
+    c->cap = capacity;
+    cudaGetDevice(&c->device);
+    DevParams &P = c->P;
+    memset(&P, 0, sizeof P);
+    P.dim = prm->dim;
+    P.kind = (int)kind;
+    P.smag = prm->smagorinsky;
+    P.volume_mode = prm->volume_mode;
+    P.n_gauss = bathy->n_gauss;
+    P.max_nbr = prm->max_neighbours > 0 ? prm->max_neighbours : (prm->dim == 2 ? 64 : 160);
+    P.precision = prm->precision;
+    P.max_iter = prm->krylov_max_iter > 0 ? prm->krylov_max_iter : 1000;
+    P.aspect = aspect_ratio;
+    P.rho = prm->rho;
+    P.nu_k = prm->nu_k;
+    P.g = prm->g;
+    P.dt = prm->dt;
+    P.d0 = prm->d0;
+    // l, r_e and r_e^2 formed exactly as the parameters define them
+    P.l = prm->l_over_d0 * prm->d0;
+    P.inv_l = 1.0 / P.l;
+    P.re = prm->re_over_l * P.l;
+    P.re2 = P.re * P.re;
+    P.V0 = prm->dim == 2 ? prm->d0 * prm->d0 : prm->d0 * prm->d0 * prm->d0;
+    P.ad = prm->dim == 2 ? 10.0 / (7.0 * M_PI * P.l * P.l) : 1.0 / (M_PI * P.l * P.l * P.l);
+    P.gamma = prm->gamma_over_dt * prm->dt;
+    P.cv = prm->cv_over_dt * prm->dt;
+    P.cs = prm->cs;
+    P.ds = prm->ds;
+    P.H = prm->H;
+    P.H_hat = prm->H_hat;
+    P.amin = prm->alpha_min;
+    P.amax = prm->alpha_max;
+    P.lam_lo = prm->lam_fs_lo;
+    P.lam_hi = prm->lam_fs_hi;
+    P.rtol = prm->krylov_rtol;
+    P.cell_h = P.re;
+    P.inv_cell_h = 1.0 / P.cell_h;
+    int64_t ncell = 1;
+    for (int k = 0; k < 3; ++k) {
+        P.box_lo[k] = prm->box_lo[k];
+        int nk = (int)floor((prm->box_hi[k] - prm->box_lo[k]) * P.inv_cell_h) + 1;
+        if (prm->dim == 2 && k == 1) nk = 1;
+        P.nc[k] = nk;
+        ncell *= nk;
+    }
+    if (ncell > (int64_t)INT32_MAX / 2) { delete c; return VCT_ERR_CAPACITY; }
+    P.h0 = bathy->h0;
+    P.slope_x = bathy->slope_x;
+    P.slope_y = bathy->slope_y;
+    P.cos_amp = bathy->cos_amp;
+    P.cos_len = bathy->cos_len;
+    for (int g = 0; g < bathy->n_gauss; ++g) {
+        P.gamp[g] = bathy->amp[g];
+        P.gcx[g] = bathy->cx[g];
+        P.gcy[g] = bathy->cy[g];
+        P.gwid[g] = bathy->width[g];
+    }
+
+    cudaError_t e = cudaSuccess;
+    const int64_t n = capacity, d = prm->dim, m = d == 2 ? 3 : 6, K = P.max_nbr;
+    alloc_part(c, c->A, e);
+    alloc_part(c, c->B, e);
+    c->cur_is_A = true;
+    Work &W = c->W;
+    W.cap = n;
+    W.ncell = ncell;
+    W.key = dalloc<int32_t>(c, n, e);
+    W.cell_count = dalloc<int32_t>(c, ncell + 1, e);
+    W.cell_start = dalloc<int32_t>(c, ncell + 1, e);
+    W.cursor = dalloc<int32_t>(c, ncell, e);
+    W.perm = dalloc<int32_t>(c, n, e);
+    W.scan_tmp = dalloc<int32_t>(c, (ncell > n ? ncell : n) + 1024, e);
+    W.row_tmp = dalloc<int64_t>(c, n / 1024 + 1024, e);
+    W.nbr_cnt = dalloc<int32_t>(c, n, e);
+    W.nbr = dalloc<int32_t>(c, n * K, e);
+    W.L = dalloc<double>(c, n * d * d, e);
+    W.gv = dalloc<double>(c, n * d * d, e);
+    W.Ct = dalloc<double>(c, n * d * m, e);
+    W.rho_hat = dalloc<double>(c, n, e);
+    W.lam = dalloc<double>(c, n, e);
+    W.nu = dalloc<double>(c, n, e);
+    W.fs = dalloc<int32_t>(c, n, e);
+    W.vstar = dalloc<double>(c, n * d, e);
+    W.acc = dalloc<double>(c, n * d, e);
+    W.pcnt = dalloc<int32_t>(c, n, e);
+    W.pcol = dalloc<int32_t>(c, n * K, e);
+    W.pval = dalloc<double>(c, n * K, e);
+    W.diag = dalloc<double>(c, n, e);
+    W.bvec = dalloc<double>(c, n, e);
+    W.wallrhs = dalloc<double>(c, n, e);
+    W.jbar_tmp = dalloc<double>(c, n, e);
+    W.kx = dalloc<double>(c, n, e);
+    W.kr = dalloc<double>(c, n, e);
+    W.krh = dalloc<double>(c, n, e);
+    W.kp0 = dalloc<double>(c, n, e);
+    W.kp1 = dalloc<double>(c, n, e);
+    W.kv0 = dalloc<double>(c, n, e);
+    W.kv1 = dalloc<double>(c, n, e);
+    W.kt = dalloc<double>(c, n, e);
+    W.ks = dalloc<double>(c, n, e);
+    c->coop_blocks = krylov_coop_blocks(prm->dim);
+    if (c->coop_blocks <= 0) e = e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
+    W.partial = dalloc<double>(c, (int64_t)(c->coop_blocks > 0 ? c->coop_blocks : 1) * 4, e);
+    W.scal = dalloc<double>(c, 16, e);
+    W.kiters = dalloc<int32_t>(c, 4, e);
+    W.kresid = dalloc<double>(c, 1, e);
+    W.bar = dalloc<unsigned int>(c, 2, e);
+    W.status = dalloc<int32_t>(c, 4, e);
+    W.counts = dalloc<long long>(c, 2, e);
+    c->row_int = dalloc<int64_t>(c, n + 1, e);
+    c->mirror.x = dalloc<double>(c, n, e);
+    c->mirror.y = dalloc<double>(c, n, e);
+    c->mirror.z = dalloc<double>(c, n, e);
+    c->mirror.u = dalloc<double>(c, n, e);
+    c->mirror.v = dalloc<double>(c, n, e);
+    c->mirror.w = dalloc<double>(c, n, e);
+    c->mirror.p = dalloc<double>(c, n, e);
+    c->mirror.jbar = dalloc<double>(c, n, e);
+    c->mirror.type = dalloc<int32_t>(c, n, e);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->host_status, 64);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        vct_destroy(c);
+        return VCT_ERR_CUDA;
+    }
+    c->last_particle = -1;
+    *out = c;
+    return VCT_OK;
+}
+
+VCT_API vct_status vct_set_stream(vct_ctx *c, void *stream)
+{
+    if (!c) return VCT_ERR_ARG;
+    c->st = (cudaStream_t)stream;
+    return VCT_OK;
+}
+
+VCT_API vct_status vct_build_neighbours(vct_ctx *c, const vct_state *s, int64_t *row_ptr, int32_t *col,
+                                int64_t col_cap, int64_t *nnz)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    const int64_t n = s->n;
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    geometry(c, n);
+    int64_t *rows = row_ptr ? row_ptr : c->row_int;
+    launch_csr_export(c->P, cur(c), c->W, n, rows, nullptr, 0, c->st);
+    int64_t total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, rows + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
+    if (nnz) *nnz = total;
+    if (col) {
+        if (total > col_cap) return VCT_ERR_CAPACITY;
+        launch_csr_export(c->P, cur(c), c->W, n, rows, col, col_cap, c->st);
+    }
+    return finish(c, nullptr, 0);
+}
+
+VCT_API vct_status sph2_derivatives(vct_ctx *c, const vct_state *s, const double *phi, int32_t ncomp,
+                            double *grad_hat, double *d2_hat, double *lap_phys)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (!phi || ncomp <= 0) return VCT_ERR_ARG;
+    const int64_t n = s->n;
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    geometry(c, n);
+    launch_pass1(c->P, cur(c), c->W, n, c->st);
+    launch_sph2_field(c->P, cur(c), c->W, n, phi, ncomp, grad_hat, d2_hat, lap_phys, c->st);
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, nullptr, 0);
+}
+
+VCT_API vct_status vct_step(vct_ctx *c, vct_state *s, int32_t nsteps, vct_stats *out)
+{
+    return run_steps(c, s, nsteps, nullptr, out);
+}
+
+VCT_API vct_status vct_step_probe(vct_ctx *c, vct_state *s, const vct_probe *pr, vct_stats *out)
+{
+    if (!pr) return VCT_ERR_ARG;
+    return run_steps(c, s, 1, pr, out);
+}
+
+VCT_API vct_status vct_step_host(vct_ctx *c, vct_state *h, int32_t nsteps, vct_stats *out)
+{
+    if (!c || !h) return VCT_ERR_ARG;
+    if (h->n <= 0 || h->n > c->cap) return h->n > c->cap ? VCT_ERR_CAPACITY : VCT_ERR_ARG;
+    if (!h->x || !h->z || !h->u || !h->w || !h->p || !h->jbar || !h->type) return VCT_ERR_ARG;
+    const bool d3 = c->P.dim == 3;
+    if (d3 && (!h->y || !h->v)) return VCT_ERR_ARG;
+    const size_t bd = sizeof(double) * (size_t)h->n;
+    vct_state m = c->mirror;
+    m.n = h->n;
+    cudaError_t e = cudaSuccess;
+    double *src[8] = {h->x, h->y, h->z, h->u, h->v, h->w, h->p, h->jbar};
+    double *dst[8] = {m.x, m.y, m.z, m.u, m.v, m.w, m.p, m.jbar};
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+        if (!src[k]) continue;
+        e = cudaMemcpyAsync(dst[k], src[k], bd, cudaMemcpyHostToDevice, c->st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)m.type, h->type, sizeof(int32_t) * (size_t)h->n,
+                            cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
+    if (!d3) { m.y = nullptr; m.v = nullptr; }
+    vct_status v = run_steps(c, &m, nsteps, nullptr, out);
+    if (v != VCT_OK) return v;
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+        if (!src[k] || !dst[k] || (!d3 && (k == 1 || k == 4))) continue;
+        e = cudaMemcpyAsync(src[k], dst[k], bd, cudaMemcpyDeviceToHost, c->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    return cuda_ok(e);
+}
+
+VCT_API vct_status vct_set_profiling(vct_ctx *c, int32_t on)
+{
+    if (!c) return VCT_ERR_ARG;
+    if (on && c->ev.empty()) {
+        c->ev.resize(2 * VCT_NSTAGES * PROF_STEPS);
+        c->ev_stage.resize(VCT_NSTAGES * PROF_STEPS);
+        for (auto &e : c->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return VCT_ERR_CUDA;
+    }
+    c->prof = on != 0;
+    c->ev_used = 0;
+    for (int k = 0; k < VCT_NSTAGES; ++k) {
+        c->stage_ms[k] = 0.0;
+        c->stage_n[k] = 0;
+    }
+    return VCT_OK;
+}
+
+VCT_API vct_status vct_stage_times(vct_ctx *c, double *ms, int64_t *launches)
+{
+    if (!c || !ms) return VCT_ERR_ARG;
+    for (int k = 0; k < VCT_NSTAGES; ++k) {
+        ms[k] = c->stage_ms[k];
+        if (launches) launches[k] = c->stage_n[k];
+    }
+    return VCT_OK;
+}
+
+VCT_API vct_status vct_last_error(vct_ctx *c, int64_t *particle)
+{
+    if (!c || !particle) return VCT_ERR_ARG;
+    *particle = c->last_particle;
+    return VCT_OK;
+}
+
+VCT_API const char *vct_strerror(vct_status s)
+{
+    switch (s) {
+    case VCT_OK: return "ok";
+    case VCT_ERR_ARG: return "invalid argument";
+    case VCT_ERR_CUDA: return "CUDA runtime error";
+    case VCT_ERR_CAPACITY: return "capacity exceeded (particles or neighbours)";
+    case VCT_ERR_SINGULAR: return "singular correction or moment matrix";
+    case VCT_ERR_NONFINITE: return "non-finite state";
+    case VCT_ERR_NOCONV: return "pressure solve did not converge";
+    case VCT_ERR_TIMEOUT: return "device spin-wait timed out";
+    }
+    return "unknown status";
+}
+
+VCT_API void vct_destroy(vct_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    for (auto &e : c->ev) cudaEventDestroy(e);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->host_status) cudaFreeHost(c->host_status);
+    delete c;
+}
+
+}  // extern "C"

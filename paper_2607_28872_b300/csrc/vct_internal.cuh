@@ -1,0 +1,95 @@
+// Internal declarations of the VCT + SPH(2) CUDA library (sm_103a).
+//
+// Data layout in HBM: every per-particle quantity is a separate array in
+// cell-sorted order (structure of arrays); multi-component quantities are
+// component-major, q[k * cap + i], so one thread per particle reads and
+// writes coalesced.  Neighbour lists and pressure-equation coefficients are
+// ELL, slot-major, nbr[k * cap + i].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vct.h"
+
+namespace vct {
+
+constexpr int FLUID = 0, WALL = 1, VIRTUAL = 2;
+constexpr int MAXG = VCT_MAX_GAUSS;
+
+// Parameters broadcast to every kernel by value (kernel-parameter bank).
+struct DevParams {
+    int dim, kind, smag, volume_mode;
+    int n_gauss, max_nbr, precision, max_iter;
+    int nc[3];                // cells per axis (x, y, z); 2-D: y = 1
+    int pad1;
+    double aspect, rho, nu_k, g, dt, d0, l, inv_l, re, re2, V0, ad;
+    double gamma, cv, cs, ds, H, H_hat, amin, amax, lam_lo, lam_hi, rtol;
+    double box_lo[3], cell_h, inv_cell_h;
+    double h0, slope_x, slope_y, cos_amp, cos_len;
+    double gamp[MAXG], gcx[MAXG], gcy[MAXG], gwid[MAXG];
+};
+
+// One buffer set of the cell-sorted particle state.
+struct Part {
+    double *x, *y, *z;        // physical position
+    double *u, *v, *w;        // physical velocity
+    double *p, *jbar;
+    int32_t *type, *orig;     // orig = caller index
+    double *xh, *yh, *zh;     // projected position
+    double *J, *sx, *sy, *c0, *c3;  // metric: J = alpha, s = third column of the
+                                    // Jacobian, c_trans entries 0 and 3
+};
+
+// Scratch of one step.
+struct Work {
+    int64_t cap;
+    int32_t *key, *cell_count, *cell_start, *cursor, *perm, *scan_tmp;
+    int64_t ncell;
+    int32_t *nbr_cnt, *nbr;   // ELL neighbour lists, slot-major
+    double *L, *gv, *Ct;      // [d*d], [d*d], [d*m] per particle, component-major
+    double *rho_hat, *lam, *nu;
+    int32_t *fs;
+    double *vstar, *acc;      // [d] per particle
+    int32_t *pcnt, *pcol;     // pressure-equation coefficients (ELL)
+    double *pval, *diag, *bvec, *wallrhs;
+    double *jbar_tmp;
+    // Krylov
+    double *kx, *kr, *krh, *kp0, *kp1, *kv0, *kv1, *kt, *ks, *partial, *scal;
+    int32_t *kiters;          // per-step iteration counts (device)
+    double *kresid;           // per-step relative residuals (device)
+    unsigned int *bar;        // grid barrier: [0] count, [1] generation
+    int32_t *status;          // [0] code, [1] first particle (sorted index), [2] spin-timeouts
+    long long *counts;        // [0] unknown rows, [1] off-diagonal coefficients (last step)
+    // csr export
+    int64_t *row_tmp;
+};
+
+struct Ctx;
+
+// ---- launchers (vct_kernels.cu) ----
+void launch_load(const DevParams &P, Part cur, vct_state s, int64_t n, cudaStream_t st);
+void launch_store(const DevParams &P, Part cur, vct_state s, int64_t n, const int32_t *status,
+                  cudaStream_t st);
+void launch_map_key(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cudaStream_t st);
+void launch_neighbours(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+void launch_smoothing(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+void launch_pass1(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor,
+                  cudaStream_t st);
+void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot,
+                  int nblocks_coop, cudaStream_t st);
+void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
+                       int ncomp, double *grad, double *d2, double *lap, cudaStream_t st);
+void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,
+                       int32_t *col, int64_t col_cap, cudaStream_t st);
+void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct_probe &pr,
+                      cudaStream_t st);
+void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,
+                     double *out, cudaStream_t st);
+int krylov_coop_blocks(int dim);
+
+}  // namespace vct

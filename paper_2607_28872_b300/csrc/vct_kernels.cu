@@ -1,0 +1,1767 @@
+// CUDA kernels of the VCT + SPH(2) step for sm_103a.
+//
+// One thread per particle over the cell-sorted SoA.  Neighbour sums are
+// templated on the accumulation type R: double (the FP64 form) or float with
+// Kahan compensation (the mixed form); per-particle inversions of B_i and the
+// SPH(2) moment matrix M_i are always FP64, as are the pressure-equation
+// iterate and residual.  No tensor cores: every sum is a gather over about 20
+// (2-D) or 56 (3-D) neighbours.
+#include <cooperative_groups.h>
+
+#include "vct_internal.cuh"
+
+namespace vct {
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Acc {
+    R s;
+    __device__ __forceinline__ Acc() : s(R(0)) {}
+    __device__ __forceinline__ void add(R x) { s += x; }
+    __device__ __forceinline__ R val() const { return s; }
+};
+
+// Kahan (compensated) summation for the FP32 sums of the mixed form.
+template <>
+struct Acc<float> {
+    float s, c;
+    __device__ __forceinline__ Acc() : s(0.f), c(0.f) {}
+    __device__ __forceinline__ void add(float x)
+    {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float val() const { return s; }
+};
+
+__device__ __forceinline__ void set_error(int32_t *status, int code, int idx)
+{
+    if (atomicCAS(status, 0, code) == 0) status[1] = idx;
+}
+
+// Bottom elevation and derivatives h, h_x, h_y, h_xx, h_yy.
+__device__ void bathy(const DevParams &P, double x, double y, double h[5])
+{
+    double v = P.h0 + P.slope_x * x + P.slope_y * y;
+    double hx = P.slope_x, hy = P.slope_y, hxx = 0.0, hyy = 0.0;
+    if (P.cos_amp != 0.0) {
+        double k = 2.0 * 3.14159265358979323846 / P.cos_len;
+        double sn, cs;
+        sincos(k * x, &sn, &cs);
+        v += P.cos_amp * cs;
+        hx -= P.cos_amp * k * sn;
+        hxx -= P.cos_amp * k * k * cs;
+    }
+    for (int g = 0; g < P.n_gauss; ++g) {
+        double dx = x - P.gcx[g], dy = y - P.gcy[g], inv_s2 = 1.0 / (P.gwid[g] * P.gwid[g]);
+        double e = P.gamp[g] * exp(-0.5 * (dx * dx + dy * dy) * inv_s2);
+        v += e;
+        hx -= e * dx * inv_s2;
+        hy -= e * dy * inv_s2;
+        hxx += e * (dx * dx * inv_s2 - 1.0) * inv_s2;
+        hyy += e * (dy * dy * inv_s2 - 1.0) * inv_s2;
+    }
+    h[0] = v; h[1] = hx; h[2] = hy; h[3] = hxx; h[4] = hyy;
+}
+
+// Projected height and metric of Eqs. (VCT), (jacobi), (lap_VCT) for the map
+// kinds of Sec. 2.2.
+__device__ void map_metric(const DevParams &P, double x, double y, double z, double &zh,
+                           double &J, double &sx, double &sy, double &c0, double &c3)
+{
+    double a = 1.0, ax = 0, ay = 0, axx = 0, ayy = 0, b = 0, bx = 0, by = 0, bxx = 0, byy = 0;
+    if (P.kind == VCT_MAP_E) {
+        a = P.aspect;
+    } else {
+        double h[5];
+        bathy(P, x, y, h);
+        b = -h[0]; bx = -h[1]; by = -h[2]; bxx = -h[3]; byy = -h[4];
+        if (P.kind == VCT_MAP_BFE) {
+            a = P.aspect;
+        } else if (P.kind == VCT_MAP_SIGMA) {
+            double D = P.H - h[0];
+            if (D <= 0.0) {
+                a = P.amax;
+            } else {
+                double ai = P.H_hat / D;
+                if (ai < P.amin) a = P.amin;
+                else if (ai > P.amax) a = P.amax;
+                else {
+                    double iD = 1.0 / D;
+                    a = ai;
+                    ax = P.H_hat * h[1] * iD * iD;
+                    ay = P.H_hat * h[2] * iD * iD;
+                    axx = P.H_hat * (h[3] * iD * iD + 2.0 * h[1] * h[1] * iD * iD * iD);
+                    ayy = P.H_hat * (h[4] * iD * iD + 2.0 * h[2] * h[2] * iD * iD * iD);
+                }
+            }
+        }
+    }
+    double zeta = z + b;
+    zh = a * zeta;
+    J = a;
+    sx = ax * zeta + a * bx;
+    sy = ay * zeta + a * by;
+    c0 = (axx + ayy) * zeta + 2.0 * (ax * bx + ay * by) + a * (bxx + byy);
+    c3 = a * a + sx * sx + sy * sy;
+}
+
+// Cubic spline (Sec. 3.1) and its radial derivative.
+template <typename R>
+__device__ __forceinline__ void kern_wdw(R r, R inv_l, R ad, R &w, R &dw)
+{
+    R q = r * inv_l;
+    if (q < R(1)) {
+        w = ad * (R(1) - R(1.5) * q * q + R(0.75) * q * q * q);
+        dw = ad * (R(-3) * q + R(2.25) * q * q) * inv_l;
+    } else if (q < R(2)) {
+        R t = R(2) - q;
+        w = ad * R(0.25) * t * t * t;
+        dw = -ad * R(0.75) * t * t * inv_l;
+    } else {
+        w = R(0);
+        dw = R(0);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void load_hat(const Part &c, int i, double *x)
+{
+    x[0] = c.xh[i];
+    if (D == 3) x[1] = c.yh[i];
+    x[D - 1] = c.zh[i];
+}
+
+template <int D>
+__device__ __forceinline__ void load_phys(const Part &c, int i, double *x)
+{
+    x[0] = c.x[i];
+    if (D == 3) x[1] = c.y[i];
+    x[D - 1] = c.z[i];
+}
+
+template <int D>
+__device__ __forceinline__ void load_vel(const Part &c, int i, double *v)
+{
+    v[0] = c.u[i];
+    if (D == 3) v[1] = c.v[i];
+    v[D - 1] = c.w[i];
+}
+
+template <int D, typename R>
+__device__ __forceinline__ void qvec(const R *r, R *q)
+{
+    if (D == 2) {
+        q[0] = r[0] * r[0]; q[1] = r[1] * r[1]; q[2] = r[0] * r[1];
+    } else {
+        q[0] = r[0] * r[0]; q[1] = r[1] * r[1]; q[2] = r[2] * r[2];
+        q[3] = r[0] * r[1]; q[4] = r[1] * r[2]; q[5] = r[2] * r[0];
+    }
+}
+
+// Inverse of a D x D matrix (row-major) by the adjugate.  Returns false if singular.
+template <int D>
+__device__ bool inv_small(const double *B, double *L)
+{
+    if (D == 2) {
+        double det = B[0] * B[3] - B[1] * B[2];
+        double s = fabs(B[0]) + fabs(B[1]) + fabs(B[2]) + fabs(B[3]);
+        if (!(fabs(det) > 1e-14 * s * s)) return false;
+        double id = 1.0 / det;
+        L[0] = B[3] * id; L[1] = -B[1] * id; L[2] = -B[2] * id; L[3] = B[0] * id;
+        return true;
+    } else {
+        double c00 = B[4] * B[8] - B[5] * B[7], c01 = B[5] * B[6] - B[3] * B[8], c02 = B[3] * B[7] - B[4] * B[6];
+        double det = B[0] * c00 + B[1] * c01 + B[2] * c02;
+        double s = 0.0;
+        for (int k = 0; k < 9; ++k) s = fmax(s, fabs(B[k]));
+        if (!(fabs(det) > 1e-14 * s * s * s)) return false;
+        double id = 1.0 / det;
+        L[0] = c00 * id;
+        L[1] = (B[2] * B[7] - B[1] * B[8]) * id;
+        L[2] = (B[1] * B[5] - B[2] * B[4]) * id;
+        L[3] = c01 * id;
+        L[4] = (B[0] * B[8] - B[2] * B[6]) * id;
+        L[5] = (B[2] * B[3] - B[0] * B[5]) * id;
+        L[6] = c02 * id;
+        L[7] = (B[1] * B[6] - B[0] * B[7]) * id;
+        L[8] = (B[0] * B[4] - B[1] * B[3]) * id;
+        return true;
+    }
+}
+
+// Smallest eigenvalue of a symmetric D x D matrix (closed forms; trigonometric
+// form of the cubic's roots in 3-D).
+template <int D>
+__device__ double sym_lam_min(const double *S)
+{
+    if (D == 2) {
+        double m = 0.5 * (S[0] + S[3]), h = 0.5 * (S[0] - S[3]);
+        return m - sqrt(h * h + S[1] * S[1]);
+    } else {
+        double p1 = S[1] * S[1] + S[2] * S[2] + S[5] * S[5];
+        if (p1 == 0.0) return fmin(S[0], fmin(S[4], S[8]));
+        double q = (S[0] + S[4] + S[8]) / 3.0;
+        double a = S[0] - q, b = S[4] - q, c = S[8] - q;
+        double p2 = a * a + b * b + c * c + 2.0 * p1;
+        double p = sqrt(p2 / 6.0);
+        double ip = 1.0 / p;
+        double B0 = a * ip, B4 = b * ip, B8 = c * ip, B1 = S[1] * ip, B2 = S[2] * ip, B5 = S[5] * ip;
+        double det = B0 * (B4 * B8 - B5 * B5) - B1 * (B1 * B8 - B5 * B2) + B2 * (B1 * B5 - B4 * B2);
+        double r = fmin(1.0, fmax(-1.0, 0.5 * det));
+        double phi = acos(r) / 3.0;
+        return q + 2.0 * p * cos(phi + 2.0 * 3.14159265358979323846 / 3.0);
+    }
+}
+
+// Gaussian elimination with partial pivoting on an m x m system with nrhs
+// right-hand sides (columns of B, row-major m x nrhs).  FP64.
+template <int M, int NR>
+__device__ bool lu_solve(double *A, double *B)
+{
+    double amax = 0.0;
+#pragma unroll
+    for (int k = 0; k < M * M; ++k) amax = fmax(amax, fabs(A[k]));
+    if (!(amax > 0.0)) return false;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        int piv = k;
+        double pv = fabs(A[k * M + k]);
+#pragma unroll
+        for (int r = k + 1; r < M; ++r)
+            if (fabs(A[r * M + k]) > pv) { pv = fabs(A[r * M + k]); piv = r; }
+        if (!(pv > 1e-14 * amax)) return false;
+        if (piv != k) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double t = A[k * M + c];
+                A[k * M + c] = A[piv * M + c];
+                A[piv * M + c] = t;
+            }
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                double t = B[k * NR + c];
+                B[k * NR + c] = B[piv * NR + c];
+                B[piv * NR + c] = t;
+            }
+        }
+        double inv = 1.0 / A[k * M + k];
+#pragma unroll
+        for (int r = k + 1; r < M; ++r) {
+            double f = A[r * M + k] * inv;
+#pragma unroll
+            for (int c = k; c < M; ++c) A[r * M + c] -= f * A[k * M + c];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) B[r * NR + c] -= f * B[k * NR + c];
+        }
+    }
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            double s = B[k * NR + c];
+#pragma unroll
+            for (int j = k + 1; j < M; ++j) s -= A[k * M + j] * B[j * NR + c];
+            B[k * NR + c] = s / A[k * M + k];
+        }
+    }
+    return true;
+}
+
+// Coefficients of the SPH(2) output (cross terms doubled) in c_trans . D^:
+// 2-D [1, c3, c4/2], 3-D [1, 1, c3, 0, c5/2, c4/2]; c4 = 2 s_x, c5 = 2 s_y.
+template <int D>
+__device__ __forceinline__ void ctilde(double c3, double sx, double sy, double *ct)
+{
+    if (D == 2) {
+        ct[0] = 1.0; ct[1] = c3; ct[2] = sx;
+    } else {
+        ct[0] = 1.0; ct[1] = 1.0; ct[2] = c3; ct[3] = 0.0; ct[4] = sy; ct[5] = sx;
+    }
+}
+
+// Physical = Jacobian x projected gradient (Eq. grad_VCT), rows x, (y), z.
+template <int D>
+__device__ __forceinline__ void jac_apply(double J, double sx, double sy, const double *gh,
+                                          double *g)
+{
+    if (D == 2) {
+        g[0] = gh[0] + sx * gh[1];
+        g[1] = J * gh[1];
+    } else {
+        g[0] = gh[0] + sx * gh[2];
+        g[1] = gh[1] + sy * gh[2];
+        g[2] = J * gh[2];
+    }
+}
+
+__device__ __forceinline__ double vol_of(const DevParams &P, const Part &c, int j)
+{
+    // V_j = V0 J_j / Jbar_j (Sec. 3.6); V0 under Condition A.
+    return P.volume_mode == 0 ? P.V0 : P.V0 * c.J[j] / c.jbar[j];
+}
+
+// ---------------------------------------------------------------------------
+// Load / store between the caller's arrays and the sorted buffers
+// ---------------------------------------------------------------------------
+__global__ void k_load(DevParams P, Part c, vct_state s, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    c.x[i] = s.x[i];
+    c.y[i] = (P.dim == 3 && s.y) ? s.y[i] : 0.0;
+    c.z[i] = s.z[i];
+    c.u[i] = s.u[i];
+    c.v[i] = (P.dim == 3 && s.v) ? s.v[i] : 0.0;
+    c.w[i] = s.w[i];
+    c.p[i] = s.p[i];
+    c.jbar[i] = s.jbar[i];
+    c.type[i] = s.type[i];
+    c.orig[i] = i;
+}
+
+void launch_load(const DevParams &P, Part cur, vct_state s, int64_t n, cudaStream_t st)
+{
+    k_load<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, cur, s, (int)n);
+}
+
+__global__ void k_store_w(DevParams P, Part c, vct_state s, int n, const int32_t *status)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || status[0] != 0) return;
+    int o = c.orig[i];
+    s.x[o] = c.x[i];
+    if (P.dim == 3 && s.y) s.y[o] = c.y[i];
+    s.z[o] = c.z[i];
+    s.u[o] = c.u[i];
+    if (P.dim == 3 && s.v) s.v[o] = c.v[i];
+    s.w[o] = c.w[i];
+    s.p[o] = c.p[i];
+    s.jbar[o] = c.jbar[i];
+}
+
+// ---------------------------------------------------------------------------
+// a1: map + metric + cell key (current order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_coord(const DevParams &P, double xh, int axis)
+{
+    double f = floor((xh - P.box_lo[axis]) * P.inv_cell_h);
+    int c = f < 0.0 ? 0 : (f > (double)(P.nc[axis] - 1) ? P.nc[axis] - 1 : (int)f);
+    return c;
+}
+
+__global__ void k_map_key(DevParams P, Part c, Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double zh, J, sx, sy, c0, c3;
+    map_metric(P, c.x[i], P.dim == 3 ? c.y[i] : 0.0, c.z[i], zh, J, sx, sy, c0, c3);
+    c.xh[i] = c.x[i];
+    c.yh[i] = P.dim == 3 ? c.y[i] : 0.0;
+    c.zh[i] = zh;
+    c.J[i] = J;
+    c.sx[i] = sx;
+    c.sy[i] = sy;
+    c.c0[i] = c0;
+    c.c3[i] = c3;
+    if (!(c.jbar[i] > 0.0)) c.jbar[i] = J;   // Jbar^0 = J^0
+    int cx = cell_coord(P, c.xh[i], 0);
+    int cy = P.dim == 3 ? cell_coord(P, c.yh[i], 1) : 0;
+    int cz = cell_coord(P, zh, 2);
+    int key = (cz * P.nc[1] + cy) * P.nc[0] + cx;
+    W.key[i] = key;
+    atomicAdd(&W.cell_count[key], 1);
+}
+
+void launch_map_key(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    cudaMemsetAsync(W.cell_count, 0, sizeof(int32_t) * (W.ncell + 1), st);
+    k_map_key<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, cur, W, (int)n);
+}
+
+// ---------------------------------------------------------------------------
+// a2: stable counting sort by cell (ties by caller index) + reorder
+// ---------------------------------------------------------------------------
+// Exclusive scan of int counts, three kernels.  SCAN_B elements per block.
+constexpr int SCAN_T = 256, SCAN_V = 4, SCAN_B = SCAN_T * SCAN_V;
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *sh, T &total)
+{
+    // Hillis-Steele over SCAN_T thread totals in shared memory
+    int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int o = 1; o < SCAN_T; o <<= 1) {
+        T a = t >= o ? sh[t - o] : T(0);
+        __syncthreads();
+        sh[t] += a;
+        __syncthreads();
+    }
+    total = sh[SCAN_T - 1];
+    T excl = sh[t] - v;
+    __syncthreads();
+    return excl;
+}
+
+template <typename T>
+__global__ void k_scan_blocks(const int32_t *in, T *out, T *blk, int64_t m)
+{
+    __shared__ T sh[SCAN_T];
+    int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_V;
+    T loc[SCAN_V], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        loc[k] = base + k < m ? (T)in[base + k] : T(0);
+        s += loc[k];
+    }
+    T total;
+    T ex = block_exclusive_scan<T>(s, sh, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        if (base + k < m) out[base + k] = ex;
+        ex += loc[k];
+    }
+    if (threadIdx.x == 0) blk[blockIdx.x] = total;
+}
+
+template <typename T>
+__global__ void k_scan_tops(T *blk, int64_t nb, T *out_end, int64_t m)
+{
+    // one block: exclusive scan of nb block totals (nb <= SCAN_T * 64)
+    __shared__ T sh[SCAN_T];
+    int per = (int)((nb + SCAN_T - 1) / SCAN_T);
+    T loc = 0;
+    int64_t b0 = (int64_t)threadIdx.x * per;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) loc += blk[b0 + k];
+    T total;
+    T ex = block_exclusive_scan<T>(loc, sh, total);
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) {
+            T v = blk[b0 + k];
+            blk[b0 + k] = ex;
+            ex += v;
+        }
+    if (threadIdx.x == 0) out_end[m] = total;
+}
+
+template <typename T>
+__global__ void k_scan_add(T *out, const T *blk, int64_t m)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] += blk[i / SCAN_B];
+}
+
+// out[0..m] = exclusive scan of in[0..m-1], out[m] = total.
+template <typename T>
+static void exclusive_scan(const int32_t *in, T *out, T *tmp, int64_t m, cudaStream_t st)
+{
+    int64_t nb = (m + SCAN_B - 1) / SCAN_B;
+    if (nb == 0) nb = 1;
+    k_scan_blocks<T><<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, tmp, m);
+    k_scan_tops<T><<<1, SCAN_T, 0, st>>>(tmp, nb, out, m);
+    k_scan_add<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(out, tmp, m);
+}
+
+__global__ void k_scatter(Work W, const Part c, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int key = W.key[i];
+    int slot = W.cell_start[key] + atomicAdd(&W.cursor[key], 1);
+    W.perm[slot] = i;
+}
+
+// Within each cell, order particles by caller index (deterministic layout).
+__global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
+{
+    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ncell) return;
+    int a = W.cell_start[cell], b = W.cell_start[cell + 1];
+    for (int k = a + 1; k < b; ++k) {
+        int v = W.perm[k];
+        int key = c.orig[v];
+        int m = k - 1;
+        while (m >= a && c.orig[W.perm[m]] > key) {
+            W.perm[m + 1] = W.perm[m];
+            --m;
+        }
+        W.perm[m + 1] = v;
+    }
+}
+
+__global__ void k_reorder(const Part c, Part a, Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = W.perm[i];
+    a.x[i] = c.x[s]; a.y[i] = c.y[s]; a.z[i] = c.z[s];
+    a.u[i] = c.u[s]; a.v[i] = c.v[s]; a.w[i] = c.w[s];
+    a.p[i] = c.p[s]; a.jbar[i] = c.jbar[s];
+    a.type[i] = c.type[s]; a.orig[i] = c.orig[s];
+    a.xh[i] = c.xh[s]; a.yh[i] = c.yh[s]; a.zh[i] = c.zh[s];
+    a.J[i] = c.J[s]; a.sx[i] = c.sx[s]; a.sy[i] = c.sy[s]; a.c0[i] = c.c0[s]; a.c3[i] = c.c3[s];
+}
+
+void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cudaStream_t st)
+{
+    exclusive_scan<int32_t>(W.cell_count, W.cell_start, W.scan_tmp, W.ncell, st);
+    cudaMemsetAsync(W.cursor, 0, sizeof(int32_t) * W.ncell, st);
+    unsigned g = (unsigned)((n + 255) / 256);
+    k_scatter<<<g, 256, 0, st>>>(W, cur, (int)n);
+    k_cell_sort<<<(unsigned)((W.ncell + 127) / 128), 128, 0, st>>>(W, cur, W.ncell);
+    k_reorder<<<g, 256, 0, st>>>(cur, alt, W, (int)n);
+}
+
+// ---------------------------------------------------------------------------
+// a3: neighbour lists (FP64 predicate without FMA, cells in ascending key order)
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double xi[3];
+    load_hat<D>(c, i, xi);
+    int cx = cell_coord(P, xi[0], 0);
+    int cy = D == 3 ? cell_coord(P, xi[1], 1) : 0;
+    int cz = cell_coord(P, xi[D - 1], 2);
+    int cnt = 0, over = 0;
+    const int64_t cap = W.cap;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z2 = cz + dz;
+        if (z2 < 0 || z2 >= P.nc[2]) continue;
+        for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy) {
+            int y2 = cy + dy;
+            if (y2 < 0 || y2 >= P.nc[1]) continue;
+            int row = (z2 * P.nc[1] + y2) * P.nc[0];
+            int xa = cx > 0 ? cx - 1 : 0, xb = cx + 1 < P.nc[0] ? cx + 1 : P.nc[0] - 1;
+            int a = W.cell_start[row + xa], b = W.cell_start[row + xb + 1];
+            for (int j = a; j < b; ++j) {
+                if (j == i) continue;
+                double d2;
+                double dx = __dsub_rn(c.xh[j], xi[0]);
+                double dz2 = __dsub_rn(c.zh[j], xi[D - 1]);
+                if (D == 2) {
+                    d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dz2, dz2));
+                } else {
+                    double dy2 = __dsub_rn(c.yh[j], xi[1]);
+                    d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy2, dy2)),
+                                   __dmul_rn(dz2, dz2));
+                }
+                if (d2 < P.re2) {
+                    if (cnt < P.max_nbr) W.nbr[(int64_t)cnt * cap + i] = j;
+                    else over = 1;
+                    ++cnt;
+                }
+            }
+        }
+    }
+    if (over) {
+        set_error(W.status, VCT_ERR_CAPACITY, i);
+        cnt = P.max_nbr;
+    }
+    W.nbr_cnt[i] = cnt;
+    if (P.precision == VCT_FP64) {
+        // FP64 form: sum neighbours in ascending caller index, the order of the
+        // definition, so the only differences to a plain evaluation are roundings
+        for (int k = 1; k < cnt; ++k) {
+            int v = W.nbr[(int64_t)k * cap + i], key = c.orig[v], m = k - 1;
+            while (m >= 0 && c.orig[W.nbr[(int64_t)m * cap + i]] > key) {
+                W.nbr[(int64_t)(m + 1) * cap + i] = W.nbr[(int64_t)m * cap + i];
+                --m;
+            }
+            W.nbr[(int64_t)(m + 1) * cap + i] = v;
+        }
+    }
+}
+
+void launch_neighbours(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) k_neighbours<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    else k_neighbours<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+}
+
+// CSR export over caller indices, rows sorted by caller index.
+__global__ void k_csr_counts(const Part c, Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    W.scan_tmp[c.orig[i]] = W.nbr_cnt[i];
+}
+
+__global__ void k_csr_fill(const Part c, Work W, int n, const int64_t *row_ptr, int32_t *col,
+                           int64_t col_cap)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t base = row_ptr[c.orig[i]];
+    int cnt = W.nbr_cnt[i];
+    if (base + cnt > col_cap) return;
+    for (int k = 0; k < cnt; ++k) {
+        int v = c.orig[W.nbr[(int64_t)k * W.cap + i]];
+        int m = k - 1;
+        while (m >= 0 && col[base + m] > v) {
+            col[base + m + 1] = col[base + m];
+            --m;
+        }
+        col[base + m + 1] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a10: volume smoothing, simultaneous form of Eq. (VCT_bar_a): every fluid
+// pair is applied once from each end, from the values before the sweep.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double jb = c.jbar[i];
+    if (c.type[i] != FLUID) {
+        W.jbar_tmp[i] = jb;
+        return;
+    }
+    double xi[3];
+    load_hat<D>(c, i, xi);
+    double ri = c.J[i] / jb, sum = 0.0;
+    int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * W.cap + i];
+        if (c.type[j] != FLUID) continue;
+        double xj[3], rr2 = 0.0;
+        load_hat<D>(c, j, xj);
+        for (int K = 0; K < D; ++K) rr2 += (xj[K] - xi[K]) * (xj[K] - xi[K]);
+        double rr = sqrt(rr2);
+        sum += P.cv * (P.re - rr) / P.re * (c.J[j] / c.jbar[j] - ri);
+    }
+    W.jbar_tmp[i] = c.J[i] / (ri + 2.0 * sum);
+}
+
+void launch_smoothing(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) k_smoothing<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    else k_smoothing<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    cudaMemcpyAsync(cur.jbar, W.jbar_tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+}
+
+// ---------------------------------------------------------------------------
+// a4: pass 1 -- B_i and L_i (Eq. gra_1st), <grad^ v>, C~_i, rho^_i,
+// free-surface flag, Smagorinsky eddy viscosity (Sec. 3.4).
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_pass1(DevParams P, const Part c, Work W, int n)
+{
+    constexpr int M = D == 2 ? 3 : 6;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (c.type[i] != FLUID) return;
+    const int64_t cap = W.cap;
+    double xi[3], pi_[3], vi[3];
+    load_hat<D>(c, i, xi);
+    load_phys<D>(c, i, pi_);
+    load_vel<D>(c, i, vi);
+    Acc<R> B[D * D], Ball[D * D], nsum[D], Gv[D * D], Gq[D * M], rho;
+    double dwall2 = 1e300;
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        int tj = c.type[j];
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        rho.add((R)P.V0 * w);
+        if (rr2 == R(0)) continue;
+        R gw[D], fac = -dw / rr;
+#pragma unroll
+        for (int K = 0; K < D; ++K) gw[K] = fac * r[K];
+        const R V0 = (R)P.V0;
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            nsum[K].add(V0 * gw[K]);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) Ball[K * D + L2].add(V0 * gw[K] * r[L2]);
+        }
+        if (tj == VIRTUAL) continue;
+        R Vj = (R)vol_of(P, c, j);
+        R q[M];
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R vg = Vj * gw[K];
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) B[K * D + L2].add(vg * r[L2]);
+#pragma unroll
+            for (int a = 0; a < M; ++a) Gq[K * M + a].add(vg * q[a]);
+        }
+        double vj[3] = {0.0, 0.0, 0.0};
+        if (tj == FLUID) load_vel<D>(c, j, vj);
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            R vij = (R)(vj[cc] - vi[cc]);
+#pragma unroll
+            for (int K = 0; K < D; ++K) Gv[cc * D + K].add(Vj * vij * gw[K]);
+        }
+        if (tj == WALL) {
+            double pj[3], d2 = 0.0;
+            load_phys<D>(c, j, pj);
+#pragma unroll
+            for (int K = 0; K < D; ++K) d2 += (pj[K] - pi_[K]) * (pj[K] - pi_[K]);
+            dwall2 = fmin(dwall2, d2);
+        }
+    }
+    double rho_hat = P.rho * ((double)rho.val() + P.V0 * P.ad);   // + self term V0 w(0)
+    W.rho_hat[i] = rho_hat;
+    double Bd[D * D], L[D * D];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) Bd[k] = (double)B[k].val();
+    if (!inv_small<D>(Bd, L)) {
+        set_error(W.status, VCT_ERR_SINGULAR, i);
+        for (int k = 0; k < D * D; ++k) L[k] = 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) W.L[(int64_t)k * cap + i] = L[k];
+    double gv[D * D];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc)
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            double s = 0.0;
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * (double)Gv[cc * D + L2].val();
+            gv[cc * D + K] = s;
+            W.gv[(int64_t)(cc * D + K) * cap + i] = s;
+        }
+#pragma unroll
+    for (int K = 0; K < D; ++K)
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * (double)Gq[L2 * M + a].val();
+            W.Ct[(int64_t)(K * M + a) * cap + i] = s;
+        }
+    // free surface: eigenvalue rule on B over all particles, scan cone between thresholds
+    double Bs[D * D];
+#pragma unroll
+    for (int K = 0; K < D; ++K)
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2)
+            Bs[K * D + L2] = 0.5 * ((double)Ball[K * D + L2].val() + (double)Ball[L2 * D + K].val());
+    double lam = sym_lam_min<D>(Bs);
+    W.lam[i] = lam;
+    int fs;
+    if (lam <= P.lam_lo) fs = 1;
+    else if (lam > P.lam_hi) fs = 0;
+    else {
+        double Ba[D * D], La[D * D], nrm[D], nn = 0.0;
+#pragma unroll
+        for (int k = 0; k < D * D; ++k) Ba[k] = (double)Ball[k].val();
+        if (!inv_small<D>(Ba, La)) fs = 1;
+        else {
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                double s = 0.0;
+#pragma unroll
+                for (int L2 = 0; L2 < D; ++L2) s += La[K * D + L2] * (double)nsum[L2].val();
+                nrm[K] = -s;
+                nn += s * s;
+            }
+            nn = sqrt(nn);
+            if (!(nn > 0.0)) fs = 0;
+            else {
+                double T[D], h = P.l, c45 = sqrt(0.5), rlim = sqrt(2.0) * h;
+#pragma unroll
+                for (int K = 0; K < D; ++K) {
+                    nrm[K] /= nn;
+                    T[K] = xi[K] + h * nrm[K];
+                }
+                fs = 1;
+                for (int k = 0; k < cnt && fs; ++k) {
+                    int j = W.nbr[(int64_t)k * cap + i];
+                    double xj[3], rr2 = 0.0, tt2 = 0.0, nr = 0.0;
+                    load_hat<D>(c, j, xj);
+#pragma unroll
+                    for (int K = 0; K < D; ++K) {
+                        double rk = xj[K] - xi[K], tk = xj[K] - T[K];
+                        rr2 += rk * rk;
+                        tt2 += tk * tk;
+                        nr += nrm[K] * rk;
+                    }
+                    double rr = sqrt(rr2);
+                    if (rr == 0.0) continue;
+                    if (rr >= rlim) {
+                        if (sqrt(tt2) < h) fs = 0;
+                    } else if (nr > c45 * rr) {
+                        fs = 0;
+                    }
+                }
+            }
+        }
+    }
+    W.fs[i] = fs;
+    // Smagorinsky: nu_E = (C_s f_s r_e)^2 sqrt(2 S:S), S from G = J grad^ v
+    double nue = 0.0;
+    if (P.smag) {
+        double G[D * D];  // G[I*D + cc] = d v_cc / d x_I
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double gh[D], g[D];
+#pragma unroll
+            for (int K = 0; K < D; ++K) gh[K] = gv[cc * D + K];
+            jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gh, g);
+#pragma unroll
+            for (int I = 0; I < D; ++I) G[I * D + cc] = g[I];
+        }
+        double SS = 0.0;
+#pragma unroll
+        for (int I = 0; I < D; ++I)
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) {
+                double s = 0.5 * (G[I * D + cc] + G[cc * D + I]);
+                SS += s * s;
+            }
+        double fsd = 1.0;
+        if (dwall2 < 1e299) fsd = 1.0 - exp(-10.0 * P.d0 / P.ds * sqrt(dwall2) / P.re);
+        double cd = P.cs * fsd * P.re;
+        nue = cd * cd * sqrt(2.0 * SS);
+    }
+    W.nu[i] = P.nu_k + nue;
+}
+
+void launch_pass1(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        if (P.precision == VCT_MIXED) k_pass1<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_pass1<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    } else {
+        if (P.precision == VCT_MIXED) k_pass1<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_pass1<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5 + a6 + a7 (matrix part): SPH(2) moment matrix M_i (Eq. sec_SPH2), the
+// predictor (Eq. VCT_predictor) and the coefficients a_ij of the left side of
+// Eq. (VCT_ppe) written as sum_j a_ij (p_j - p_i):
+//   a_ij = V_j [ c0 (L grad w_ij)_z + 2 F_ij (w . q_ij) - 2 u . L grad w_ij ],
+//   w = M_i^-T c~,  u = sum_j V_j F_ij (w . q_ij) r_ij.
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W, int n,
+                                               int predictor)
+{
+    constexpr int M = D == 2 ? 3 : 6;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (c.type[i] != FLUID) {
+        if (predictor) W.pcnt[i] = -1;
+        return;
+    }
+    const int64_t cap = W.cap;
+    double xi[3], vi[3];
+    load_hat<D>(c, i, xi);
+    load_vel<D>(c, i, vi);
+    R L[D * D], Ct[D * M];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) L[k] = (R)W.L[(int64_t)k * cap + i];
+#pragma unroll
+    for (int k = 0; k < D * M; ++k) Ct[k] = (R)W.Ct[(int64_t)k * cap + i];
+    double gvd[D * D];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) gvd[k] = W.gv[(int64_t)k * cap + i];
+    const double nui = W.nu[i];
+    Acc<R> Mm[M * M], bv[M * D], Gnu[D], Q[M * D];
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        int tj = c.type[j];
+        if (tj == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+        double rd[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            rd[K] = xj[K] - xi[K];
+            r[K] = (R)rd[K];
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R gw[D], fac = -dw / rr, gt[D], rg = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) gw[K] = fac * r[K];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R s = R(0);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * gw[L2];
+            gt[K] = s;
+            rg += r[K] * s;
+        }
+        R Vj = (R)vol_of(P, c, j);
+        R F = rg / (rr2 * rr2), VF = Vj * F;
+        R q[M], pv[M];
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            R s = R(0);
+#pragma unroll
+            for (int K = 0; K < D; ++K) s += Ct[K * M + a] * r[K];
+            pv[a] = q[a] - s;
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            R vq = VF * q[a];
+#pragma unroll
+            for (int b = 0; b < M; ++b) Mm[a * M + b].add(vq * pv[b]);
+#pragma unroll
+            for (int K = 0; K < D; ++K) Q[a * D + K].add(vq * r[K]);
+        }
+        if (predictor) {
+            double vj[3] = {0.0, 0.0, 0.0};
+            if (tj == FLUID) load_vel<D>(c, j, vj);
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) {
+                // v_ij - r_ij . <grad v>_i cancels O(|grad v| r) down to O(|D v| r^2):
+                // formed in FP64, then summed in R
+                double rgv = 0.0;
+#pragma unroll
+                for (int K = 0; K < D; ++K) rgv += rd[K] * gvd[cc * D + K];
+                R e = (R)((vj[cc] - vi[cc]) - rgv);
+#pragma unroll
+                for (int a = 0; a < M; ++a) bv[a * D + cc].add(VF * q[a] * e);
+            }
+            double nuj = tj == FLUID ? W.nu[j] : P.nu_k;
+            R dn = (R)(nuj - nui);
+#pragma unroll
+            for (int K = 0; K < D; ++K) Gnu[K].add(Vj * dn * gw[K]);
+        }
+    }
+    double Md[M * M];
+#pragma unroll
+    for (int k = 0; k < M * M; ++k) Md[k] = (double)Mm[k].val();
+    double ct[M];
+    ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
+    double acc[D] = {};
+    if (predictor) {
+        double A[M * M], Bv[M * D];
+#pragma unroll
+        for (int k = 0; k < M * M; ++k) A[k] = Md[k];
+#pragma unroll
+        for (int k = 0; k < M * D; ++k) Bv[k] = (double)bv[k].val();
+        if (!lu_solve<M, D>(A, Bv)) set_error(W.status, VCT_ERR_SINGULAR, i);
+        // physical grad nu = J L sum V (nu_j - nu_i) grad w
+        double gnh[D], gn[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            double s = 0.0;
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + i] * (double)Gnu[L2].val();
+            gnh[K] = s;
+        }
+        jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gnh, gn);
+        double G[D * D];  // G[I*D + cc] = d v_cc / d x_I
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double gh[D], g[D];
+#pragma unroll
+            for (int K = 0; K < D; ++K) gh[K] = W.gv[(int64_t)(cc * D + K) * cap + i];
+            jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gh, g);
+#pragma unroll
+            for (int I = 0; I < D; ++I) G[I * D + cc] = g[I];
+        }
+        const double c0i = c.c0[i];
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double lap = c0i * W.gv[(int64_t)(cc * D + (D - 1)) * cap + i];
+#pragma unroll
+            for (int a = 0; a < M; ++a) lap += ct[a] * 2.0 * Bv[a * D + cc];
+            double term = 0.0;
+#pragma unroll
+            for (int J2 = 0; J2 < D; ++J2) term += (G[cc * D + J2] + G[J2 * D + cc]) * gn[J2];
+            double g = cc == D - 1 ? -P.g : 0.0;
+            acc[cc] = nui * lap + term + g;
+            W.acc[(int64_t)cc * cap + i] = acc[cc];
+            W.vstar[(int64_t)cc * cap + i] = vi[cc] + P.dt * acc[cc];
+        }
+    }
+    // pressure-equation row for unknowns (fluid, not free surface)
+    if (!predictor || W.fs[i]) {
+        if (predictor) W.pcnt[i] = -1;
+        return;
+    }
+    double wv[M];
+    {
+        // solve M^T w = c~
+        double A[M * M];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) A[a * M + b] = Md[b * M + a];
+#pragma unroll
+        for (int a = 0; a < M; ++a) wv[a] = ct[a];
+        if (!lu_solve<M, 1>(A, wv)) set_error(W.status, VCT_ERR_SINGULAR, i);
+    }
+    double u[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < M; ++a) s += wv[a] * (double)Q[a * D + K].val();
+        u[K] = s;
+    }
+    R wr[M], ur[D];
+#pragma unroll
+    for (int a = 0; a < M; ++a) wr[a] = (R)wv[a];
+#pragma unroll
+    for (int K = 0; K < D; ++K) ur[K] = (R)u[K];
+    const R c0r = (R)c.c0[i];
+    double diag = 0.0, wallrhs = 0.0;
+    double pi_[3];
+    load_phys<D>(c, i, pi_);
+    int pc = 0;
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        int tj = c.type[j];
+        if (tj == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R gw[D], fac = -dw / rr, gt[D], rg = R(0), ug = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) gw[K] = fac * r[K];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R s = R(0);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * gw[L2];
+            gt[K] = s;
+            rg += r[K] * s;
+            ug += ur[K] * s;
+        }
+        R F = rg / (rr2 * rr2), q[M], wq = R(0);
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int a = 0; a < M; ++a) wq += wr[a] * q[a];
+        R Vj = (R)vol_of(P, c, j);
+        double aij = (double)(Vj * (c0r * gt[D - 1] + R(2) * F * wq - R(2) * ug));
+        if (tj == FLUID) {
+            diag -= aij;
+            if (!W.fs[j]) {
+                W.pcol[(int64_t)pc * cap + i] = j;
+                W.pval[(int64_t)pc * cap + i] = aij;
+                ++pc;
+            }
+        } else {  // wall: p_ij = rho r_ij . f_i (Eq. PNC)
+            double pj[3], s = 0.0;
+            load_phys<D>(c, j, pj);
+#pragma unroll
+            for (int K = 0; K < D; ++K) s += (pj[K] - pi_[K]) * acc[K];
+            wallrhs += aij * P.rho * s;
+        }
+    }
+    W.pcnt[i] = pc;
+    W.diag[i] = diag;
+    W.wallrhs[i] = wallrhs;
+    atomicAdd((unsigned long long *)&W.counts[0], 1ull);
+    atomicAdd((unsigned long long *)&W.counts[1], (unsigned long long)pc);
+}
+
+void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor,
+                  cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        if (P.precision == VCT_MIXED) k_pass2<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, predictor);
+        else k_pass2<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, predictor);
+    } else {
+        if (P.precision == VCT_MIXED) k_pass2<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, predictor);
+        else k_pass2<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, predictor);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a7 (right side): b_i = rho/dt tr(J <grad^ (x) v*>) + gamma (rho Jbar/J - rho^)/dt^2
+//                       - (wall terms of Eq. PNC)
+// A wall neighbour carries v_wall + dt f_i, the intermediate velocity implied by
+// the acceleration Eq. (PNC) assumes.
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    if (c.type[i] != FLUID || W.fs[i]) {
+        W.bvec[i] = 0.0;
+        W.kx[i] = 0.0;
+        return;
+    }
+    double xi[3], vsi[D], acci[D];
+    load_hat<D>(c, i, xi);
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        vsi[cc] = W.vstar[(int64_t)cc * cap + i];
+        acci[cc] = W.acc[(int64_t)cc * cap + i];
+    }
+    Acc<R> X[D * D];
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        int tj = c.type[j];
+        if (tj == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R fac = -dw / rr, Vj = (R)vol_of(P, c, j);
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double vj = tj == FLUID ? W.vstar[(int64_t)cc * cap + j] : P.dt * acci[cc];
+            R e = Vj * (R)(vj - vsi[cc]) * fac;
+#pragma unroll
+            for (int K = 0; K < D; ++K) X[cc * D + K].add(e * r[K]);
+        }
+    }
+    double div = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        double gh[D], g[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            double s = 0.0;
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + i] * (double)X[cc * D + L2].val();
+            gh[K] = s;
+        }
+        jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gh, g);
+        div += g[cc];
+    }
+    double fac = P.volume_mode == 0 ? 1.0 : c.jbar[i] / c.J[i];
+    double rhs = P.rho / P.dt * div + P.gamma * (P.rho * fac - W.rho_hat[i]) / (P.dt * P.dt);
+    W.bvec[i] = rhs - W.wallrhs[i];
+    W.kx[i] = c.p[i];   // initial guess p^N
+}
+
+void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        if (P.precision == VCT_MIXED) k_rhs<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_rhs<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    } else {
+        if (P.precision == VCT_MIXED) k_rhs<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_rhs<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8: BiCGSTAB (van der Vorst 1992) in one cooperative persistent launch.
+// Three grid barriers per iteration: the new search direction p and the
+// intermediate s are formed on the fly inside the two products, so neither
+// needs its own barrier.  Dot products: per-block partials, every block sums
+// them in the same order (bitwise-identical scalars in all blocks).
+// ---------------------------------------------------------------------------
+constexpr int KT = 256;
+constexpr unsigned long long SPIN_LIMIT = 20000000ull;   // ~2 s with 64 ns naps
+
+__device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status)
+{
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > SPIN_LIMIT) {
+                    ok = 0;
+                    atomicExch(status + 2, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int32_t *)(status + 2)) ok = 0;
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+template <int NV>
+__device__ void block_partials(double (&v)[NV], double *partial)
+{
+    __shared__ double sh[NV][KT / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < KT / 32; ++w) s += sh[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+// Sum the per-block partials in a fixed order; every block gets the same bits.
+template <int NV>
+__device__ void grid_totals(const double *partial, unsigned nblocks, double (&out)[NV])
+{
+    __shared__ double tot[NV];
+    if (threadIdx.x < 32) {
+        int lane = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (unsigned b = lane; b < nblocks; b += 32) s += __ldcg(partial + (int64_t)b * 4 + k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) tot[k] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = tot[k];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(KT) k_bicgstab(Work W, int n, int maxit, double rtol,
+                                                 int32_t *iters_out, double *resid_out)
+{
+    const unsigned nb = gridDim.x;
+    const int64_t cap = W.cap;
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    double *x = W.kx, *r = W.kr, *rh = W.krh, *t = W.kt, *s = W.ks;
+    double *po = W.kp0, *pn = W.kp1, *vo = W.kv0, *vn = W.kv1;
+    // r = b - A x, rh = r, p = v = 0
+    double part[2] = {0.0, 0.0};
+    for (int i = t0; i < n; i += stride) {
+        int pc = W.pcnt[i];
+        double ri = 0.0;
+        if (pc >= 0) {
+            double xi = x[i], ax = W.diag[i] * xi;
+            for (int k = 0; k < pc; ++k)
+                ax += W.pval[(int64_t)k * cap + i] * x[W.pcol[(int64_t)k * cap + i]];
+            ri = W.bvec[i] - ax;
+            part[0] += ri * ri;
+            part[1] += W.bvec[i] * W.bvec[i];
+        }
+        r[i] = ri;
+        rh[i] = ri;
+        po[i] = 0.0;
+        vo[i] = 0.0;
+    }
+    block_partials<2>(part, W.partial);
+    if (!grid_barrier(W.bar, nb, W.status)) return;
+    double tot2[2];
+    grid_totals<2>(W.partial, nb, tot2);
+    double rn = sqrt(tot2[0]), bn = sqrt(tot2[1]);
+    double rho = tot2[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    int it = 0;
+    bool fail = false;
+    if (bn == 0.0) {
+        for (int i = t0; i < n; i += stride) x[i] = 0.0;
+        rn = 0.0;
+    }
+    while (bn > 0.0 && rn > rtol * bn) {
+        if (it >= maxit || rho == 0.0) { fail = true; break; }
+        ++it;
+        const double beta = (rho / rho_old) * (alpha / omega);
+        // phase A: p_new = r + beta (p - omega v); v_new = A p_new; partial (rh, v_new)
+        double pa[1] = {0.0};
+        for (int i = t0; i < n; i += stride) {
+            int pc = W.pcnt[i];
+            double pni = __ldcg(r + i) + beta * (__ldcg(po + i) - omega * __ldcg(vo + i));
+            double av = 0.0;
+            if (pc >= 0) {
+                av = W.diag[i] * pni;
+                for (int k = 0; k < pc; ++k) {
+                    int j = W.pcol[(int64_t)k * cap + i];
+                    double pj = __ldcg(r + j) + beta * (__ldcg(po + j) - omega * __ldcg(vo + j));
+                    av += W.pval[(int64_t)k * cap + i] * pj;
+                }
+                pa[0] += __ldcg(rh + i) * av;
+            } else {
+                pni = 0.0;
+            }
+            pn[i] = pni;
+            vn[i] = av;
+        }
+        block_partials<1>(pa, W.partial);
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        double tv[1];
+        grid_totals<1>(W.partial, nb, tv);
+        if (tv[0] == 0.0) { fail = true; break; }
+        alpha = rho / tv[0];
+        // phase B: s = r - alpha v_new; t = A s; partials (t,s), (t,t), (s,s)
+        double pb[3] = {0.0, 0.0, 0.0};
+        for (int i = t0; i < n; i += stride) {
+            int pc = W.pcnt[i];
+            double si = 0.0, ti = 0.0;
+            if (pc >= 0) {
+                si = __ldcg(r + i) - alpha * __ldcg(vn + i);
+                ti = W.diag[i] * si;
+                for (int k = 0; k < pc; ++k) {
+                    int j = W.pcol[(int64_t)k * cap + i];
+                    double sj = __ldcg(r + j) - alpha * __ldcg(vn + j);
+                    ti += W.pval[(int64_t)k * cap + i] * sj;
+                }
+                pb[0] += ti * si;
+                pb[1] += ti * ti;
+                pb[2] += si * si;
+            }
+            s[i] = si;
+            t[i] = ti;
+        }
+        block_partials<3>(pb, W.partial);
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        double tb[3];
+        grid_totals<3>(W.partial, nb, tb);
+        if (sqrt(tb[2]) <= rtol * bn) {
+            for (int i = t0; i < n; i += stride)
+                if (W.pcnt[i] >= 0) x[i] += alpha * pn[i];
+            rn = sqrt(tb[2]);
+            break;
+        }
+        if (tb[1] == 0.0) { fail = true; break; }
+        omega = tb[0] / tb[1];
+        // phase C: x += alpha p + omega s; r = s - omega t; partials (rh, r), (r, r)
+        double pcp[2] = {0.0, 0.0};
+        for (int i = t0; i < n; i += stride) {
+            if (W.pcnt[i] >= 0) {
+                double si = s[i];
+                x[i] += alpha * pn[i] + omega * si;
+                double ri = si - omega * t[i];
+                r[i] = ri;
+                pcp[0] += rh[i] * ri;
+                pcp[1] += ri * ri;
+            }
+        }
+        block_partials<2>(pcp, W.partial);
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        double tc[2];
+        grid_totals<2>(W.partial, nb, tc);
+        rho_old = rho;
+        rho = tc[0];
+        rn = sqrt(tc[1]);
+        double *tmp = po; po = pn; pn = tmp;
+        tmp = vo; vo = vn; vn = tmp;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (fail) set_error(W.status, VCT_ERR_NOCONV, -1);
+        iters_out[0] += it;
+        if (it > iters_out[1]) iters_out[1] = it;
+        iters_out[2] = it;
+        *resid_out = bn > 0.0 ? rn / bn : 0.0;
+    }
+}
+
+int krylov_coop_blocks(int dim)
+{
+    (void)dim;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bicgstab, KT, 0);
+    if (per > 4) per = 4;
+    return sms * per;
+}
+
+int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot,
+                  int nblocks_coop, cudaStream_t st)
+{
+    (void)cur;
+    (void)step_slot;
+    int nn = (int)n, maxit = P.max_iter;
+    double rtol = P.rtol;
+    int32_t *it_out = W.kiters;
+    double *res_out = W.kresid;
+    void *args[] = {(void *)&W, (void *)&nn, (void *)&maxit, (void *)&rtol, (void *)&it_out,
+                    (void *)&res_out};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_bicgstab, dim3(nblocks_coop),
+                                                dim3(KT), args, 0, st);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+// ---------------------------------------------------------------------------
+// a9: corrector and position update (Eqs. VCT_predictor, VCT_update)
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (c.type[i] != FLUID) return;
+    const int64_t cap = W.cap;
+    double xi[3], pi_[3], acci[D];
+    load_hat<D>(c, i, xi);
+    load_phys<D>(c, i, pi_);
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) acci[cc] = W.acc[(int64_t)cc * cap + i];
+    const double p_i = W.pcnt[i] >= 0 ? W.kx[i] : 0.0;
+    Acc<R> G[D];
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        int tj = c.type[j];
+        if (tj == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        double pij;
+        if (tj == FLUID) {
+            pij = (W.pcnt[j] >= 0 ? W.kx[j] : 0.0) - p_i;
+        } else {
+            double pj[3], s = 0.0;
+            load_phys<D>(c, j, pj);
+#pragma unroll
+            for (int K = 0; K < D; ++K) s += (pj[K] - pi_[K]) * acci[K];
+            pij = P.rho * s;
+        }
+        R e = (R)vol_of(P, c, j) * (R)pij * (-dw / rr);
+#pragma unroll
+        for (int K = 0; K < D; ++K) G[K].add(e * r[K]);
+    }
+    double gh[D], g[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double s = 0.0;
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + i] * (double)G[L2].val();
+        gh[K] = s;
+    }
+    jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gh, g);
+    double vn[D];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) vn[cc] = W.vstar[(int64_t)cc * cap + i] - P.dt / P.rho * g[cc];
+    c.p[i] = p_i;
+    c.u[i] = vn[0];
+    c.x[i] += P.dt * vn[0];
+    if (D == 3) {
+        c.v[i] = vn[1];
+        c.y[i] += P.dt * vn[1];
+    }
+    c.w[i] = vn[D - 1];
+    c.z[i] += P.dt * vn[D - 1];
+    bool finite = isfinite(c.x[i]) && isfinite(c.z[i]) && isfinite(p_i) && isfinite(vn[0]) &&
+                  isfinite(vn[D - 1]);
+    if (!finite) set_error(W.status, VCT_ERR_NONFINITE, i);
+}
+
+void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        if (P.precision == VCT_MIXED) k_corrector<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_corrector<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    } else {
+        if (P.precision == VCT_MIXED) k_corrector<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_corrector<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sph2_derivatives: corrected gradient + SPH(2) of caller fields
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_sph2_field(DevParams P, const Part c, Work W, int n,
+                                                    const double *phi, int ncomp,
+                                                    double *grad, double *d2, double *lap)
+{
+    constexpr int M = D == 2 ? 3 : 6;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int o = c.orig[i];
+    if (c.type[i] != FLUID) {
+        for (int cc = 0; cc < ncomp; ++cc) {
+            if (grad) for (int K = 0; K < D; ++K) grad[((int64_t)cc * D + K) * n + o] = 0.0;
+            if (d2) for (int a = 0; a < M; ++a) d2[((int64_t)cc * M + a) * n + o] = 0.0;
+            if (lap) lap[(int64_t)cc * n + o] = 0.0;
+        }
+        return;
+    }
+    const int64_t cap = W.cap;
+    double xi[3];
+    load_hat<D>(c, i, xi);
+    R L[D * D], Ct[D * M];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) L[k] = (R)W.L[(int64_t)k * cap + i];
+#pragma unroll
+    for (int k = 0; k < D * M; ++k) Ct[k] = (R)W.Ct[(int64_t)k * cap + i];
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    Acc<R> Mm[M * M];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R gw[D], fac = -dw / rr, rg = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) gw[K] = fac * r[K];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R s = R(0);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * gw[L2];
+            rg += r[K] * s;
+        }
+        R VF = (R)vol_of(P, c, j) * rg / (rr2 * rr2), q[M], pv[M];
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            R s = R(0);
+#pragma unroll
+            for (int K = 0; K < D; ++K) s += Ct[K * M + a] * r[K];
+            pv[a] = q[a] - s;
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) Mm[a * M + b].add(VF * q[a] * pv[b]);
+    }
+    double ct[M];
+    ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
+    for (int cc = 0; cc < ncomp; ++cc) {
+        const double *f = phi + (int64_t)cc * n;
+        const double fi = f[o];
+        Acc<R> G[D];
+        for (int k = 0; k < cnt; ++k) {
+            int j = W.nbr[(int64_t)k * cap + i];
+            if (c.type[j] == VIRTUAL) continue;
+            double xj[3];
+            load_hat<D>(c, j, xj);
+            R r[D], rr2 = R(0);
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                r[K] = (R)(xj[K] - xi[K]);
+                rr2 += r[K] * r[K];
+            }
+            if (rr2 == R(0)) continue;
+            R rr = sqrt(rr2), w, dw;
+            kern_wdw<R>(rr, inv_l, ad, w, dw);
+            R e = (R)vol_of(P, c, j) * (R)(f[c.orig[j]] - fi) * (-dw / rr);
+#pragma unroll
+            for (int K = 0; K < D; ++K) G[K].add(e * r[K]);
+        }
+        double g[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            double s = 0.0;
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + i] * (double)G[L2].val();
+            g[K] = s;
+        }
+        Acc<R> b[M];
+        for (int k = 0; k < cnt; ++k) {
+            int j = W.nbr[(int64_t)k * cap + i];
+            if (c.type[j] == VIRTUAL) continue;
+            double xj[3];
+            load_hat<D>(c, j, xj);
+            R r[D], rr2 = R(0);
+            double rgd = 0.0;
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                double rdk = xj[K] - xi[K];
+                r[K] = (R)rdk;
+                rr2 += r[K] * r[K];
+                rgd += rdk * g[K];
+            }
+            if (rr2 == R(0)) continue;
+            R rr = sqrt(rr2), w, dw;
+            kern_wdw<R>(rr, inv_l, ad, w, dw);
+            R gw[D], fac = -dw / rr, rg = R(0);
+#pragma unroll
+            for (int K = 0; K < D; ++K) gw[K] = fac * r[K];
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                R s = R(0);
+#pragma unroll
+                for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * gw[L2];
+                rg += r[K] * s;
+            }
+            R VF = (R)vol_of(P, c, j) * rg / (rr2 * rr2), q[M];
+            qvec<D, R>(r, q);
+            // phi_ij - r_ij . <grad phi>_i formed in FP64 (cancellation), summed in R
+            R e = VF * (R)((f[c.orig[j]] - fi) - rgd);
+#pragma unroll
+            for (int a = 0; a < M; ++a) b[a].add(e * q[a]);
+        }
+        double A[M * M], bb[M];
+#pragma unroll
+        for (int k = 0; k < M * M; ++k) A[k] = (double)Mm[k].val();
+#pragma unroll
+        for (int a = 0; a < M; ++a) bb[a] = (double)b[a].val();
+        if (!lu_solve<M, 1>(A, bb)) set_error(W.status, VCT_ERR_SINGULAR, i);
+#pragma unroll
+        for (int a = 0; a < M; ++a) bb[a] *= 2.0;   // D = 2 M^-1 b
+        if (grad)
+            for (int K = 0; K < D; ++K) grad[((int64_t)cc * D + K) * n + o] = g[K];
+        if (d2)
+            for (int a = 0; a < M; ++a) d2[((int64_t)cc * M + a) * n + o] = a < D ? bb[a] : 0.5 * bb[a];
+        if (lap) {
+            double s = c.c0[i] * g[D - 1];
+#pragma unroll
+            for (int a = 0; a < M; ++a) s += ct[a] * bb[a];
+            lap[(int64_t)cc * n + o] = s;
+        }
+    }
+}
+
+void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
+                       int ncomp, double *grad, double *d2, double *lap, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        if (P.precision == VCT_MIXED)
+            k_sph2_field<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, ncomp, grad, d2, lap);
+        else k_sph2_field<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, ncomp, grad, d2, lap);
+    } else {
+        if (P.precision == VCT_MIXED)
+            k_sph2_field<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, ncomp, grad, d2, lap);
+        else k_sph2_field<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, ncomp, grad, d2, lap);
+    }
+}
+
+void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,
+                       int32_t *col, int64_t col_cap, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    k_csr_counts<<<g, 128, 0, st>>>(cur, W, (int)n);
+    exclusive_scan<int64_t>(W.scan_tmp, row_ptr, W.row_tmp, n, st);
+    if (col) k_csr_fill<<<g, 128, 0, st>>>(cur, W, (int)n, row_ptr, col, col_cap);
+}
+
+// ---------------------------------------------------------------------------
+// Probe outputs (caller order)
+// ---------------------------------------------------------------------------
+__global__ void k_probe_out(DevParams P, const Part c, Work W, int n, vct_probe pr)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = c.orig[i];
+    bool fl = c.type[i] == FLUID;
+    if (pr.fs) pr.fs[o] = fl ? W.fs[i] : 0;
+    if (pr.rho_hat) pr.rho_hat[o] = fl ? W.rho_hat[i] : 0.0;
+    if (pr.nu) pr.nu[o] = fl ? W.nu[i] : 0.0;
+    if (pr.lam_min) pr.lam_min[o] = fl ? W.lam[i] : 0.0;
+    if (pr.vstar)
+        for (int cc = 0; cc < P.dim; ++cc)
+            pr.vstar[(int64_t)cc * n + o] = fl ? W.vstar[(int64_t)cc * W.cap + i] : 0.0;
+    if (pr.ppe_b) pr.ppe_b[o] = W.bvec[i];
+    if (pr.jbar_used) pr.jbar_used[o] = c.jbar[i];
+}
+
+void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct_probe &pr,
+                      cudaStream_t st)
+{
+    k_probe_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, cur, W, (int)n, pr);
+}
+
+__global__ void k_gather_masked(const Part c, Work W, int n, const double *xin, double *xs)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    xs[i] = W.pcnt[i] >= 0 ? xin[c.orig[i]] : 0.0;
+}
+
+__global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int pc = W.pcnt[i];
+    double y = 0.0;
+    if (pc >= 0) {
+        y = W.diag[i] * xs[i];
+        for (int k = 0; k < pc; ++k) y += W.pval[(int64_t)k * W.cap + i] * xs[W.pcol[(int64_t)k * W.cap + i]];
+    }
+    out[c.orig[i]] = y;
+}
+
+void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,
+                     double *out, cudaStream_t st)
+{
+    (void)P;
+    unsigned g = (unsigned)((n + 255) / 256);
+    k_gather_masked<<<g, 256, 0, st>>>(cur, W, (int)n, x_test, W.kt);
+    k_spmv_out<<<g, 256, 0, st>>>(cur, W, (int)n, W.kt, out);
+}
+
+void launch_store(const DevParams &P, Part cur, vct_state s, int64_t n, const int32_t *status,
+                  cudaStream_t st)
+{
+    k_store_w<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, cur, s, (int)n, status);
+}
+
+}  // namespace vct

@@ -1,0 +1,304 @@
+"""Thin Python binding of the C ABI in include/vct.h (argument marshalling only).
+
+Every stage of the step runs in the CUDA library libvct.so; PyTorch provides
+device memory and streams.  The binding raises if the library is missing:
+there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvct.so")
+
+VCT_OK, VCT_ERR_ARG, VCT_ERR_CUDA, VCT_ERR_CAPACITY = 0, 1, 2, 3
+VCT_ERR_SINGULAR, VCT_ERR_NONFINITE, VCT_ERR_NOCONV, VCT_ERR_TIMEOUT = 4, 5, 6, 7
+MAP = {"E": 0, "BF": 1, "BFE": 2, "SIGMA": 3}
+VCT_MAX_GAUSS = 32
+
+EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives", "vct_step",
+           "vct_step_host", "vct_step_probe", "vct_set_profiling", "vct_stage_times",
+           "vct_last_error", "vct_strerror", "vct_destroy")
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class vct_bathymetry(C.Structure):
+    _fields_ = [("h0", C.c_double), ("slope_x", C.c_double), ("slope_y", C.c_double),
+                ("cos_amp", C.c_double), ("cos_len", C.c_double), ("n_gauss", C.c_int32),
+                ("reserved", C.c_int32), ("amp", _dp), ("cx", _dp), ("cy", _dp), ("width", _dp)]
+
+
+class vct_params(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("reserved0", C.c_int32)] + [
+        (k, C.c_double) for k in ("rho", "nu_k", "g", "dt", "d0", "l_over_d0", "re_over_l",
+                                  "gamma_over_dt", "cv_over_dt", "cs", "ds", "H", "H_hat",
+                                  "alpha_min", "alpha_max", "lam_fs_lo", "lam_fs_hi",
+                                  "krylov_rtol")] + [
+        ("krylov_max_iter", C.c_int32), ("smagorinsky", C.c_int32), ("precision", C.c_int32),
+        ("volume_mode", C.c_int32), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+        ("max_neighbours", C.c_int32), ("reserved1", C.c_int32)]
+
+
+class vct_state(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, C.c_void_p) for k in
+                                     ("x", "y", "z", "u", "v", "w", "p", "jbar", "type")]
+
+
+class vct_stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int64), ("krylov_iters_total", C.c_int64),
+                ("krylov_iters_max", C.c_int32), ("reserved", C.c_int32),
+                ("last_residual", C.c_double), ("ppe_rows", C.c_int64), ("ppe_nnz", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
+STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "rhs", "krylov",
+          "corrector", "store")
+
+
+class vct_probe(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("fs", "rho_hat", "nu", "lam_min", "vstar", "ppe_b",
+                                          "x_test", "ppe_Ax", "jbar_used")]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libvct.so (built by paper_2607_28872_b300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "`python -m paper_2607_28872_b300.build`; there is no CPU fallback")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.vct_init.argtypes = [C.POINTER(vp), C.POINTER(vct_bathymetry), C.c_int, C.c_double,
+                           C.POINTER(vct_params), C.c_int64, vp]
+    L.vct_set_stream.argtypes = [vp, vp]
+    L.vct_build_neighbours.argtypes = [vp, C.POINTER(vct_state), vp, vp, C.c_int64,
+                                       C.POINTER(C.c_int64)]
+    L.sph2_derivatives.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp, vp]
+    L.vct_step.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
+    L.vct_step_host.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
+    L.vct_step_probe.argtypes = [vp, C.POINTER(vct_state), C.POINTER(vct_probe),
+                                 C.POINTER(vct_stats)]
+    L.vct_set_profiling.argtypes = [vp, C.c_int32]
+    L.vct_stage_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.vct_last_error.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.vct_strerror.argtypes = [C.c_int]
+    L.vct_strerror.restype = C.c_char_p
+    L.vct_destroy.argtypes = [vp]
+    L.vct_destroy.restype = None
+    for name in ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives",
+                 "vct_step", "vct_step_host", "vct_step_probe", "vct_set_profiling",
+                 "vct_stage_times", "vct_last_error"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def vct_strerror(status):
+    return load_library().vct_strerror(int(status)).decode()
+
+
+class VCTError(RuntimeError):
+    def __init__(self, status, where, particle=-1):
+        self.status = status
+        self.particle = particle
+        super().__init__(f"{where}: {vct_strerror(status)} (status {status}, particle {particle})")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def make_bathymetry(b):
+    """vct_bathymetry from a scenarios.Bathymetry; returns (struct, keep-alive)."""
+    ng = len(b.amp)
+    if ng > VCT_MAX_GAUSS:
+        raise ValueError("too many Gaussian bumps")
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1) if ng else np.zeros(1))
+            for a in (b.amp, b.cx, b.cy, b.width)]
+    s = vct_bathymetry(b.h0, b.slope_x, b.slope_y, b.cos_amp, b.cos_len, ng, 0,
+                       *[a.ctypes.data_as(_dp) for a in arrs])
+    return s, arrs
+
+
+def make_params(sc, **over):
+    p = dict(sc.params)
+    p.update(over)
+    P = vct_params()
+    P.dim = sc.dim
+    for k in ("rho", "nu_k", "g", "dt", "d0", "l_over_d0", "re_over_l", "gamma_over_dt",
+              "cv_over_dt", "cs", "ds", "H", "H_hat", "alpha_min", "alpha_max", "lam_fs_lo",
+              "lam_fs_hi", "krylov_rtol"):
+        setattr(P, k, float(p[k]))
+    P.krylov_max_iter = int(p["krylov_max_iter"])
+    P.smagorinsky = int(p["smagorinsky"])
+    P.precision = int(p["precision"])
+    P.volume_mode = int(p["volume_mode"])
+    for k in range(3):
+        P.box_lo[k] = float(sc.box_lo[k])
+        P.box_hi[k] = float(sc.box_hi[k])
+    P.max_neighbours = int(p.get("max_neighbours", 0))
+    return P
+
+
+class DeviceState:
+    """Caller-owned particle state as torch CUDA tensors (caller order)."""
+
+    FIELDS = ("x", "y", "z", "u", "v", "w", "p", "jbar")
+
+    def __init__(self, sc, device="cuda"):
+        import torch
+        self.n = sc.n
+        self.dim = sc.dim
+        for k in self.FIELDS:
+            setattr(self, k, torch.tensor(np.asarray(getattr(sc, k), dtype=np.float64),
+                                          device=device))
+        self.type = torch.tensor(np.asarray(sc.type, dtype=np.int32), device=device)
+
+    def struct(self):
+        return vct_state(self.n, *[_ptr(getattr(self, k)) for k in self.FIELDS], _ptr(self.type))
+
+    def numpy(self):
+        out = {k: getattr(self, k).cpu().numpy() for k in self.FIELDS}
+        out["type"] = self.type.cpu().numpy()
+        return out
+
+
+class HostState:
+    """Host (pinned) copy of a particle state for vct_step_host."""
+
+    FIELDS = DeviceState.FIELDS
+
+    def __init__(self, sc, pin=True):
+        import torch
+        self.n = sc.n
+        for k in self.FIELDS:
+            t = torch.tensor(np.asarray(getattr(sc, k), dtype=np.float64))
+            setattr(self, k, t.pin_memory() if pin else t)
+        t = torch.tensor(np.asarray(sc.type, dtype=np.int32))
+        self.type = t.pin_memory() if pin else t
+
+    def struct(self):
+        return vct_state(self.n, *[_ptr(getattr(self, k)) for k in self.FIELDS], _ptr(self.type))
+
+
+class Solver:
+    """A vct_ctx for one scenario's map, bathymetry and parameters."""
+
+    def __init__(self, sc, capacity=None, stream=None, **over):
+        import torch
+        self.lib = load_library()
+        self.sc = sc
+        self.dim = sc.dim
+        self.bathy, self._keep = make_bathymetry(sc.bathy)
+        self.params = make_params(sc, **over)
+        self.capacity = int(capacity or sc.n)
+        self.ctx = C.c_void_p()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        rc = self.lib.vct_init(C.byref(self.ctx), C.byref(self.bathy), MAP[sc.map_kind],
+                               float(sc.aspect), C.byref(self.params), self.capacity,
+                               C.c_void_p(stream.cuda_stream))
+        if rc != VCT_OK:
+            raise VCTError(rc, "vct_init")
+
+    def _check(self, rc, where):
+        if rc != VCT_OK:
+            part = C.c_int64(-1)
+            self.lib.vct_last_error(self.ctx, C.byref(part))
+            raise VCTError(rc, where, part.value)
+
+    def close(self):
+        if self.ctx:
+            self.lib.vct_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- entry points -----------------------------------------------------
+    def vct_build_neighbours(self, state):
+        import torch
+        s = state.struct()
+        nnz = C.c_int64(0)
+        row = torch.zeros(state.n + 1, dtype=torch.int64, device="cuda")
+        self._check(self.lib.vct_build_neighbours(self.ctx, C.byref(s), _ptr(row), None, 0,
+                                                  C.byref(nnz)), "vct_build_neighbours")
+        col = torch.zeros(max(nnz.value, 1), dtype=torch.int32, device="cuda")
+        self._check(self.lib.vct_build_neighbours(self.ctx, C.byref(s), _ptr(row), _ptr(col),
+                                                  col.numel(), C.byref(nnz)),
+                    "vct_build_neighbours")
+        return row, col[:nnz.value]
+
+    def sph2_derivatives(self, state, phi):
+        """phi: (ncomp, n) float64 CUDA tensor -> grad_hat (ncomp, d, n),
+        d2_hat (ncomp, m, n), lap_phys (ncomp, n)."""
+        import torch
+        phi = phi.contiguous()
+        nc = phi.shape[0]
+        m = 3 if self.dim == 2 else 6
+        g = torch.zeros((nc, self.dim, state.n), dtype=torch.float64, device="cuda")
+        d2 = torch.zeros((nc, m, state.n), dtype=torch.float64, device="cuda")
+        lap = torch.zeros((nc, state.n), dtype=torch.float64, device="cuda")
+        s = state.struct()
+        self._check(self.lib.sph2_derivatives(self.ctx, C.byref(s), _ptr(phi), nc, _ptr(g),
+                                              _ptr(d2), _ptr(lap)), "sph2_derivatives")
+        return g, d2, lap
+
+    def vct_step(self, state, nsteps=1):
+        s = state.struct()
+        st = vct_stats()
+        self._check(self.lib.vct_step(self.ctx, C.byref(s), int(nsteps), C.byref(st)), "vct_step")
+        return st
+
+    def vct_step_host(self, hstate, nsteps=1):
+        s = hstate.struct()
+        st = vct_stats()
+        self._check(self.lib.vct_step_host(self.ctx, C.byref(s), int(nsteps), C.byref(st)),
+                    "vct_step_host")
+        return st
+
+    def vct_set_profiling(self, on=True):
+        self._check(self.lib.vct_set_profiling(self.ctx, 1 if on else 0), "vct_set_profiling")
+
+    def vct_stage_times(self):
+        """{stage: (device ms, bracketed launches)} accumulated while profiling."""
+        ms = (C.c_double * len(STAGES))()
+        cnt = (C.c_int64 * len(STAGES))()
+        self._check(self.lib.vct_stage_times(self.ctx, ms, cnt), "vct_stage_times")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(STAGES)}
+
+    def vct_step_probe(self, state, x_test=None):
+        import torch
+        n, d = state.n, self.dim
+        out = dict(fs=torch.zeros(n, dtype=torch.int32, device="cuda"),
+                   rho_hat=torch.zeros(n, dtype=torch.float64, device="cuda"),
+                   nu=torch.zeros(n, dtype=torch.float64, device="cuda"),
+                   lam_min=torch.zeros(n, dtype=torch.float64, device="cuda"),
+                   vstar=torch.zeros((d, n), dtype=torch.float64, device="cuda"),
+                   ppe_b=torch.zeros(n, dtype=torch.float64, device="cuda"),
+                   jbar_used=torch.zeros(n, dtype=torch.float64, device="cuda"))
+        if x_test is not None:
+            out["ppe_Ax"] = torch.zeros(n, dtype=torch.float64, device="cuda")
+            x_test = x_test.contiguous()
+        pr = vct_probe(_ptr(out["fs"]), _ptr(out["rho_hat"]), _ptr(out["nu"]),
+                       _ptr(out["lam_min"]), _ptr(out["vstar"]), _ptr(out["ppe_b"]),
+                       _ptr(x_test), _ptr(out.get("ppe_Ax")), _ptr(out["jbar_used"]))
+        s = state.struct()
+        st = vct_stats()
+        self._check(self.lib.vct_step_probe(self.ctx, C.byref(s), C.byref(pr), C.byref(st)),
+                    "vct_step_probe")
+        return out, st
