@@ -336,7 +336,8 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.acc = dalloc<double>(c, n * d, e);
     W.pcnt = dalloc<int32_t>(c, n, e);
     W.pcol = dalloc<int32_t>(c, n * K, e);
-    W.pval = dalloc<double>(c, n * K, e);
+    W.pval = dalloc<double>(c, prm->precision == VCT_MIXED ? 1 : n * K, e);
+    W.pvalf = dalloc<float>(c, prm->precision == VCT_MIXED ? n * K : 1, e);
     W.diag = dalloc<double>(c, n, e);
     W.bvec = dalloc<double>(c, n, e);
     W.wallrhs = dalloc<double>(c, n, e);
@@ -350,9 +351,11 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.kv1 = dalloc<double>(c, n, e);
     W.kt = dalloc<double>(c, n, e);
     W.ks = dalloc<double>(c, n, e);
-    c->coop_blocks = krylov_coop_blocks(prm->dim);
+    W.kd = dalloc<double>(c, n, e);
+    W.kf = dalloc<double>(c, n, e);
+    c->coop_blocks = krylov_coop_blocks(prm->precision, prm->dim);
     if (c->coop_blocks <= 0) e = e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
-    W.partial = dalloc<double>(c, (int64_t)(c->coop_blocks > 0 ? c->coop_blocks : 1) * 4, e);
+    W.partial = dalloc<double>(c, (int64_t)8 * 4096, e);   // k-major, 4096 blocks max
     W.scal = dalloc<double>(c, 16, e);
     W.kiters = dalloc<int32_t>(c, 4, e);
     W.kresid = dalloc<double>(c, 1, e);

@@ -53,9 +53,12 @@ struct Work {
     double *vstar, *acc;      // [d] per particle
     int32_t *pcnt, *pcol;     // pressure-equation coefficients (ELL)
     double *pval, *diag, *bvec, *wallrhs;
+    float *pvalf;             // FP32 coefficients of the mixed form
     double *jbar_tmp;
     // Krylov
-    double *kx, *kr, *krh, *kp0, *kp1, *kv0, *kv1, *kt, *ks, *partial, *scal;
+    double *kx, *kf;          // FP64 iterate and residual
+    double *kr, *krh, *kp0, *kp1, *kv0, *kv1, *kt, *ks, *kd;   // inner vectors (FP64 or FP32)
+    double *partial, *scal;
     int32_t *kiters;          // per-step iteration counts (device)
     double *kresid;           // per-step relative residuals (device)
     unsigned int *bar;        // grid barrier: [0] count, [1] generation
@@ -90,6 +93,6 @@ void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct
                       cudaStream_t st);
 void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,
                      double *out, cudaStream_t st);
-int krylov_coop_blocks(int dim);
+int krylov_coop_blocks(int precision, int dim);
 
 }  // namespace vct

@@ -1078,7 +1078,8 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
             diag -= aij;
             if (!W.fs[j]) {
                 W.pcol[(int64_t)pc * cap + i] = j;
-                W.pval[(int64_t)pc * cap + i] = aij;
+                if (P.precision == VCT_MIXED) W.pvalf[(int64_t)pc * cap + i] = (float)aij;
+                else W.pval[(int64_t)pc * cap + i] = aij;
                 ++pc;
             }
         } else {  // wall: p_ij = rho r_ij . f_i (Eq. PNC)
@@ -1193,23 +1194,37 @@ void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st
 }
 
 // ---------------------------------------------------------------------------
-// a8: BiCGSTAB (van der Vorst 1992) in one cooperative persistent launch.
-// Three grid barriers per iteration: the new search direction p and the
-// intermediate s are formed on the fly inside the two products, so neither
-// needs its own barrier.  Dot products: per-block partials, every block sums
-// them in the same order (bitwise-identical scalars in all blocks).
+// a8: pressure solve.  FP64 iterative refinement on the true residual
+// f = b - A x around an inner BiCGSTAB (van der Vorst 1992) in precision T:
+// T = double for the FP64 form (one pass to krylov_rtol), T = float with
+// FP32-stored coefficients for the mixed form (each pass to 1e-4, then a new
+// FP64 residual).  Everything runs in one cooperative persistent launch.
+// Two grid barriers per inner iteration: the recurrences are rearranged so that
+// (rh, r_new) = (rh, s) - w (rh, t) and |r_new|^2 = (s,s) - 2w (t,s) + w^2 (t,t)
+// come out of the second reduction, the x/r update of iteration k is applied at
+// the start of iteration k+1, and the new search direction and s are formed on
+// the fly inside the two operator products.  Dot products: per-block partials
+// summed in the same order by every block (identical scalars everywhere,
+// bit-reproducible runs).
 // ---------------------------------------------------------------------------
 constexpr int KT = 256;
-constexpr unsigned long long SPIN_LIMIT = 20000000ull;   // ~2 s with 64 ns naps
+constexpr unsigned long long SPIN_LIMIT = 40000000ull;   // bounded: ~1-2 s at most
 
+__device__ __forceinline__ unsigned ld_volatile(const unsigned int *p)
+{
+    return *(const volatile unsigned int *)p;
+}
+
+// Sense-reversal grid barrier for a cooperative launch (all blocks resident).
+// Spins are bounded: on timeout the block records status[2] and every block
+// leaves at its next barrier, so the kernel always ends.
 __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status)
 {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int *vgen = bar + 1;
-        unsigned gen = *vgen;
+        unsigned gen = ld_volatile(bar + 1);
         __threadfence();
         unsigned arrived = atomicAdd(bar, 1u);
         if (arrived == nblocks - 1) {
@@ -1218,13 +1233,13 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *statu
             atomicAdd(bar + 1, 1u);
         } else {
             unsigned long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > SPIN_LIMIT) {
+            while (ld_volatile(bar + 1) == gen) {
+                if (++spins > 2048) __nanosleep(20);
+                if (spins > SPIN_LIMIT) {
                     ok = 0;
                     atomicExch(status + 2, 1);
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
@@ -1235,8 +1250,11 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *statu
     return ok_sh != 0;
 }
 
+// Per-block partial sums, stored k-major: partial[k * PSTRIDE + block].
+constexpr int PSTRIDE = 4096;
+
 template <int NV>
-__device__ void block_partials(double (&v)[NV], double *partial)
+__device__ void block_partials(const double (&v)[NV], double *partial)
 {
     __shared__ double sh[NV][KT / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1244,32 +1262,44 @@ __device__ void block_partials(double (&v)[NV], double *partial)
     for (int k = 0; k < NV; ++k) {
         double x = v[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) sh[k][wid] = x;
     }
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
         for (int w = 0; w < KT / 32; ++w) s += sh[threadIdx.x][w];
-        partial[(int64_t)blockIdx.x * 4 + threadIdx.x] = s;
+        partial[(int64_t)threadIdx.x * PSTRIDE + blockIdx.x] = s;
     }
 }
 
-// Sum the per-block partials in a fixed order; every block gets the same bits.
+// Sum the per-block partials: every thread of the block loads a strided
+// subset (independent, coalesced loads), then a fixed-order tree.  The order
+// does not depend on the block, so every block gets the same bits.
 template <int NV>
 __device__ void grid_totals(const double *partial, unsigned nblocks, double (&out)[NV])
 {
+    __shared__ double red[NV][KT / 32];
     __shared__ double tot[NV];
-    if (threadIdx.x < 32) {
-        int lane = threadIdx.x;
+    double acc[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (unsigned b = lane; b < nblocks; b += 32) s += __ldcg(partial + (int64_t)b * 4 + k);
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < nblocks; b += KT)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) tot[k] = s;
-        }
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partial + (int64_t)k * PSTRIDE + b);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < KT / 32; ++w) s += red[threadIdx.x][w];
+        tot[threadIdx.x] = s;
     }
     __syncthreads();
 #pragma unroll
@@ -1277,147 +1307,232 @@ __device__ void grid_totals(const double *partial, unsigned nblocks, double (&ou
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(KT) k_bicgstab(Work W, int n, int maxit, double rtol,
-                                                 int32_t *iters_out, double *resid_out)
+template <typename CT>
+__device__ __forceinline__ CT coef(const Work &W, int64_t k);
+template <>
+__device__ __forceinline__ double coef<double>(const Work &W, int64_t k) { return W.pval[k]; }
+template <>
+__device__ __forceinline__ float coef<float>(const Work &W, int64_t k) { return W.pvalf[k]; }
+
+// Sum over the G lanes of a row group (G consecutive lanes of a warp).  The
+// shuffle names only the group's lanes: the groups of one warp work on
+// different rows and may leave the row loop at different times, while the
+// lanes of one group always share the row, its coefficient count and the trip
+// count, so they reach every shuffle together.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v)
+{
+    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "G: power of two <= 32");
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, G);
+    return v;
+}
+
+// G lanes per row: lane g of the group takes coefficients g, g+G, ...; the
+// row's scalar work is repeated by every lane of the group (same addresses,
+// broadcast loads) and only lane 0 writes.
+template <typename T, typename CT, int G>
+__global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double rtol,
+                                               double inner_floor, int32_t *iters_out,
+                                               double *resid_out)
 {
     const unsigned nb = gridDim.x;
     const int64_t cap = W.cap;
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    double *x = W.kx, *r = W.kr, *rh = W.krh, *t = W.kt, *s = W.ks;
-    double *po = W.kp0, *pn = W.kp1, *vo = W.kv0, *vn = W.kv1;
-    // r = b - A x, rh = r, p = v = 0
-    double part[2] = {0.0, 0.0};
-    for (int i = t0; i < n; i += stride) {
-        int pc = W.pcnt[i];
-        double ri = 0.0;
-        if (pc >= 0) {
-            double xi = x[i], ax = W.diag[i] * xi;
-            for (int k = 0; k < pc; ++k)
-                ax += W.pval[(int64_t)k * cap + i] * x[W.pcol[(int64_t)k * cap + i]];
-            ri = W.bvec[i] - ax;
-            part[0] += ri * ri;
-            part[1] += W.bvec[i] * W.bvec[i];
-        }
-        r[i] = ri;
-        rh[i] = ri;
-        po[i] = 0.0;
-        vo[i] = 0.0;
-    }
-    block_partials<2>(part, W.partial);
-    if (!grid_barrier(W.bar, nb, W.status)) return;
-    double tot2[2];
-    grid_totals<2>(W.partial, nb, tot2);
-    double rn = sqrt(tot2[0]), bn = sqrt(tot2[1]);
-    double rho = tot2[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
-    int it = 0;
+    const int lg = threadIdx.x & (G - 1);
+    const bool lead = lg == 0;
+    const int ngroups = (gridDim.x * blockDim.x) / G;
+    const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    double *x = W.kx, *f = W.kf;
+    T *r = (T *)W.kr, *rh = (T *)W.krh, *s = (T *)W.ks, *t = (T *)W.kt, *dl = (T *)W.kd;
+    T *pold = (T *)W.kp0, *pnew = (T *)W.kp1, *vold = (T *)W.kv0, *vnew = (T *)W.kv1;
+    int total_it = 0;
     bool fail = false;
-    if (bn == 0.0) {
-        for (int i = t0; i < n; i += stride) x[i] = 0.0;
-        rn = 0.0;
-    }
-    while (bn > 0.0 && rn > rtol * bn) {
-        if (it >= maxit || rho == 0.0) { fail = true; break; }
-        ++it;
-        const double beta = (rho / rho_old) * (alpha / omega);
-        // phase A: p_new = r + beta (p - omega v); v_new = A p_new; partial (rh, v_new)
-        double pa[1] = {0.0};
-        for (int i = t0; i < n; i += stride) {
+    double bn = 0.0, rn = 0.0;
+    for (int outer = 0;; ++outer) {
+        // true residual in FP64: f = b - A x
+        double part[2] = {0.0, 0.0};
+        for (int i = g0; i < n; i += ngroups) {
             int pc = W.pcnt[i];
-            double pni = __ldcg(r + i) + beta * (__ldcg(po + i) - omega * __ldcg(vo + i));
-            double av = 0.0;
-            if (pc >= 0) {
-                av = W.diag[i] * pni;
-                for (int k = 0; k < pc; ++k) {
-                    int j = W.pcol[(int64_t)k * cap + i];
-                    double pj = __ldcg(r + j) + beta * (__ldcg(po + j) - omega * __ldcg(vo + j));
-                    av += W.pval[(int64_t)k * cap + i] * pj;
-                }
-                pa[0] += __ldcg(rh + i) * av;
-            } else {
-                pni = 0.0;
+            if (pc < 0) continue;
+            double ax = 0.0;
+            for (int k = lg; k < pc; k += G) {
+                int64_t q = (int64_t)k * cap + i;
+                ax += (double)coef<CT>(W, q) * __ldcg(x + W.pcol[q]);
             }
-            pn[i] = pni;
-            vn[i] = av;
-        }
-        block_partials<1>(pa, W.partial);
-        if (!grid_barrier(W.bar, nb, W.status)) return;
-        double tv[1];
-        grid_totals<1>(W.partial, nb, tv);
-        if (tv[0] == 0.0) { fail = true; break; }
-        alpha = rho / tv[0];
-        // phase B: s = r - alpha v_new; t = A s; partials (t,s), (t,t), (s,s)
-        double pb[3] = {0.0, 0.0, 0.0};
-        for (int i = t0; i < n; i += stride) {
-            int pc = W.pcnt[i];
-            double si = 0.0, ti = 0.0;
-            if (pc >= 0) {
-                si = __ldcg(r + i) - alpha * __ldcg(vn + i);
-                ti = W.diag[i] * si;
-                for (int k = 0; k < pc; ++k) {
-                    int j = W.pcol[(int64_t)k * cap + i];
-                    double sj = __ldcg(r + j) - alpha * __ldcg(vn + j);
-                    ti += W.pval[(int64_t)k * cap + i] * sj;
-                }
-                pb[0] += ti * si;
-                pb[1] += ti * ti;
-                pb[2] += si * si;
+            ax = group_sum<G>(ax);
+            if (lead) {
+                double bi = W.bvec[i], fi = bi - (ax + W.diag[i] * x[i]);
+                f[i] = fi;
+                part[0] += fi * fi;
+                part[1] += bi * bi;
             }
-            s[i] = si;
-            t[i] = ti;
         }
-        block_partials<3>(pb, W.partial);
+        block_partials<2>(part, W.partial);
         if (!grid_barrier(W.bar, nb, W.status)) return;
-        double tb[3];
-        grid_totals<3>(W.partial, nb, tb);
-        if (sqrt(tb[2]) <= rtol * bn) {
-            for (int i = t0; i < n; i += stride)
-                if (W.pcnt[i] >= 0) x[i] += alpha * pn[i];
-            rn = sqrt(tb[2]);
+        double tot[2];
+        grid_totals<2>(W.partial, nb, tot);
+        rn = sqrt(tot[0]);
+        bn = sqrt(tot[1]);
+        if (bn == 0.0) {
+            for (int i = g0; i < n; i += ngroups)
+                if (lead) x[i] = 0.0;
+            rn = 0.0;
             break;
         }
-        if (tb[1] == 0.0) { fail = true; break; }
-        omega = tb[0] / tb[1];
-        // phase C: x += alpha p + omega s; r = s - omega t; partials (rh, r), (r, r)
-        double pcp[2] = {0.0, 0.0};
-        for (int i = t0; i < n; i += stride) {
-            if (W.pcnt[i] >= 0) {
-                double si = s[i];
-                x[i] += alpha * pn[i] + omega * si;
-                double ri = si - omega * t[i];
-                r[i] = ri;
-                pcp[0] += rh[i] * ri;
-                pcp[1] += ri * ri;
-            }
+        if (rn <= rtol * bn) break;
+        if (total_it >= maxit || outer >= 64) {
+            fail = true;
+            break;
         }
-        block_partials<2>(pcp, W.partial);
+        // inner solve A d = f in precision T, to |r| <= tol_in |f|
+        const double fn = rn, tol_in = fmax(rtol * bn / rn, inner_floor);
+        double rho = fn * fn, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        double pend_a = 0.0, pend_w = 0.0;   // update of the last completed iteration
+        bool first = true, have_pend = false;
+        for (;;) {
+            if (total_it >= maxit) break;
+            ++total_it;
+            const double beta = first ? 0.0 : (rho / rho_old) * (alpha / omega);
+            const T tb = (T)beta, tw = (T)omega, ta = (T)alpha;
+            // phase A: apply the pending update, p_new = r + beta (p - w v), v_new = A p_new
+            double pa[1] = {0.0};
+            for (int i = g0; i < n; i += ngroups) {
+                int pc = W.pcnt[i];
+                if (pc < 0) continue;
+                T ri, pn;
+                if (first) {
+                    ri = (T)f[i];
+                    pn = ri;
+                } else {
+                    T si = s[i];
+                    ri = si - tw * t[i];
+                    pn = ri + tb * (pold[i] - tw * vold[i]);
+                }
+                T acc = T(0);
+                for (int k = lg; k < pc; k += G) {
+                    int64_t q = (int64_t)k * cap + i;
+                    int j = W.pcol[q];
+                    T pj;
+                    if (first) pj = (T)__ldcg(f + j);
+                    else
+                        pj = (__ldcg(s + j) - tw * __ldcg(t + j)) +
+                             tb * (__ldcg(pold + j) - tw * __ldcg(vold + j));
+                    acc += (T)coef<CT>(W, q) * pj;
+                }
+                acc = group_sum<G>(acc);
+                if (lead) {
+                    acc += (T)W.diag[i] * pn;
+                    if (first) {
+                        rh[i] = ri;
+                        dl[i] = T(0);
+                    } else {
+                        dl[i] += ta * pold[i] + tw * s[i];
+                    }
+                    r[i] = ri;
+                    pnew[i] = pn;
+                    vnew[i] = acc;
+                    pa[0] += (double)rh[i] * (double)acc;
+                }
+            }
+            block_partials<1>(pa, W.partial);
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            double tv[1];
+            grid_totals<1>(W.partial, nb, tv);
+            first = false;
+            have_pend = false;
+            if (tv[0] == 0.0) {
+                fail = true;
+                break;
+            }
+            alpha = rho / tv[0];
+            const T ta2 = (T)alpha;
+            // phase B: s = r - alpha v_new, t = A s; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
+            double pb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int i = g0; i < n; i += ngroups) {
+                int pc = W.pcnt[i];
+                if (pc < 0) continue;
+                T acc = T(0);
+                for (int k = lg; k < pc; k += G) {
+                    int64_t q = (int64_t)k * cap + i;
+                    int j = W.pcol[q];
+                    acc += (T)coef<CT>(W, q) * (__ldcg(r + j) - ta2 * __ldcg(vnew + j));
+                }
+                acc = group_sum<G>(acc);
+                if (lead) {
+                    T si = r[i] - ta2 * vnew[i];
+                    acc += (T)W.diag[i] * si;
+                    s[i] = si;
+                    t[i] = acc;
+                    double sd = (double)si, td = (double)acc, hd = (double)rh[i];
+                    pb[0] += td * sd;
+                    pb[1] += td * td;
+                    pb[2] += sd * sd;
+                    pb[3] += hd * sd;
+                    pb[4] += hd * td;
+                }
+            }
+            block_partials<5>(pb, W.partial);
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            double tq[5];
+            grid_totals<5>(W.partial, nb, tq);
+            T *tp = pold; pold = pnew; pnew = tp;
+            tp = vold; vold = vnew; vnew = tp;
+            have_pend = true;
+            pend_a = alpha;
+            if (sqrt(tq[2]) <= tol_in * fn) {   // s already small: x += alpha p
+                pend_w = 0.0;
+                break;
+            }
+            if (tq[1] == 0.0) {
+                pend_w = 0.0;
+                fail = true;
+                break;
+            }
+            omega = tq[0] / tq[1];
+            pend_w = omega;
+            rho_old = rho;
+            rho = tq[3] - omega * tq[4];
+            double rr = tq[2] - 2.0 * omega * tq[0] + omega * omega * tq[1];
+            if (sqrt(fmax(rr, 0.0)) <= tol_in * fn || rho == 0.0) break;
+        }
+        // apply the last update and x += d (FP64)
+        const T fa = (T)pend_a, fw = (T)pend_w;
+        for (int i = g0; i < n; i += ngroups) {
+            if (!lead || W.pcnt[i] < 0) continue;
+            T d = dl[i];
+            if (have_pend) d += fa * pold[i] + fw * s[i];
+            x[i] += (double)d;
+        }
         if (!grid_barrier(W.bar, nb, W.status)) return;
-        double tc[2];
-        grid_totals<2>(W.partial, nb, tc);
-        rho_old = rho;
-        rho = tc[0];
-        rn = sqrt(tc[1]);
-        double *tmp = po; po = pn; pn = tmp;
-        tmp = vo; vo = vn; vn = tmp;
+        if (fail) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (fail) set_error(W.status, VCT_ERR_NOCONV, -1);
-        iters_out[0] += it;
-        if (it > iters_out[1]) iters_out[1] = it;
-        iters_out[2] = it;
+        iters_out[0] += total_it;
+        if (total_it > iters_out[1]) iters_out[1] = total_it;
+        iters_out[2] = total_it;
         *resid_out = bn > 0.0 ? rn / bn : 0.0;
     }
 }
 
-int krylov_coop_blocks(int dim)
+static const void *krylov_fn(int precision, int dim)
 {
-    (void)dim;
+    if (precision == VCT_MIXED)
+        return dim == 2 ? (const void *)k_krylov<float, float, 8> : (const void *)k_krylov<float, float, 16>;
+    return dim == 2 ? (const void *)k_krylov<double, double, 8> : (const void *)k_krylov<double, double, 16>;
+}
+
+int krylov_coop_blocks(int precision, int dim)
+{
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bicgstab, KT, 0);
-    if (per > 4) per = 4;
-    return sms * per;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, krylov_fn(precision, dim), KT, 0);
+    if (per > 2) per = 2;   // fewer arrivals per grid barrier
+    int nb = sms * per;
+    return nb < PSTRIDE ? nb : PSTRIDE;
 }
 
 int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot,
@@ -1426,12 +1541,17 @@ int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot
     (void)cur;
     (void)step_slot;
     int nn = (int)n, maxit = P.max_iter;
-    double rtol = P.rtol;
+    double rtol = P.rtol, floor_ = P.precision == VCT_MIXED ? 1e-4 : 0.0;
     int32_t *it_out = W.kiters;
     double *res_out = W.kresid;
-    void *args[] = {(void *)&W, (void *)&nn, (void *)&maxit, (void *)&rtol, (void *)&it_out,
-                    (void *)&res_out};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_bicgstab, dim3(nblocks_coop),
+    // a grid no larger than the rows need: fewer arrivals per barrier
+    const int G = P.dim == 2 ? 8 : 16;
+    int64_t want = (n * G + KT - 1) / KT;
+    int nblk = (int)(want < nblocks_coop ? want : nblocks_coop);
+    if (nblk < 1) nblk = 1;
+    void *args[] = {(void *)&W, (void *)&nn, (void *)&maxit, (void *)&rtol, (void *)&floor_,
+                    (void *)&it_out, (void *)&res_out};
+    cudaError_t e = cudaLaunchCooperativeKernel(krylov_fn(P.precision, P.dim), dim3(nblk),
                                                 dim3(KT), args, 0, st);
     return e == cudaSuccess ? 0 : (int)e;
 }
@@ -1736,7 +1856,8 @@ __global__ void k_gather_masked(const Part c, Work W, int n, const double *xin, 
     xs[i] = W.pcnt[i] >= 0 ? xin[c.orig[i]] : 0.0;
 }
 
-__global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double *out)
+__global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double *out,
+                           int mixed)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1744,7 +1865,11 @@ __global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double
     double y = 0.0;
     if (pc >= 0) {
         y = W.diag[i] * xs[i];
-        for (int k = 0; k < pc; ++k) y += W.pval[(int64_t)k * W.cap + i] * xs[W.pcol[(int64_t)k * W.cap + i]];
+        for (int k = 0; k < pc; ++k) {
+            int64_t q = (int64_t)k * W.cap + i;
+            double a = mixed ? (double)W.pvalf[q] : W.pval[q];
+            y += a * xs[W.pcol[q]];
+        }
     }
     out[c.orig[i]] = y;
 }
@@ -1752,10 +1877,9 @@ __global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double
 void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,
                      double *out, cudaStream_t st)
 {
-    (void)P;
     unsigned g = (unsigned)((n + 255) / 256);
     k_gather_masked<<<g, 256, 0, st>>>(cur, W, (int)n, x_test, W.kt);
-    k_spmv_out<<<g, 256, 0, st>>>(cur, W, (int)n, W.kt, out);
+    k_spmv_out<<<g, 256, 0, st>>>(cur, W, (int)n, W.kt, out, P.precision == VCT_MIXED);
 }
 
 void launch_store(const DevParams &P, Part cur, vct_state s, int64_t n, const int32_t *status,
