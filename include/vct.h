@@ -166,6 +166,27 @@ vct_status vct_set_stream(vct_ctx *ctx, void *stream);
 vct_status vct_build_neighbours(vct_ctx *ctx, const vct_state *state, int64_t *row_ptr,
                                 int32_t *col, int64_t col_cap, int64_t *nnz);
 
+/* Allocation-free variant of vct_build_neighbours (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory when they need the
+ * lists -- an application whose device memory is all handed to its own pool, or
+ * a loop that cannot afford cudaMalloc/cudaFree -- and so cannot own a vct_ctx).
+ * It takes the map and parameters directly (only dim, d0, l_over_d0, re_over_l,
+ * H, H_hat, alpha_min/max and the box are read), the DEVICE state arrays
+ * x, (y), z of n particles, and writes the same CSR as vct_build_neighbours:
+ * row_ptr (n+1 int64, device, required) and col (device, capacity col_cap,
+ * may be NULL to get only *nnz, host).  It allocates nothing: its scratch is a
+ * static device array of about 1 MB, held by every GPU that loads the library,
+ * which limits it to n <= 16384 particles and a cell grid of at most 32768 cells
+ * (VCT_ERR_CAPACITY beyond either, also if col_cap < nnz).  The first call on a
+ * device looks up that array's device address (once per device); make that
+ * first call before any stream capture.  Work runs on `stream` (a
+ * cudaStream_t) and the call synchronises it once.  All calls on a device share
+ * the array: calls that overlap on the GPU race and must not be issued. */
+vct_status vct_build_neighbours_noalloc(const vct_bathymetry *bathy, vct_map_kind kind,
+                                        double aspect_ratio, const vct_params *params,
+                                        const vct_state *state, int64_t *row_ptr, int32_t *col,
+                                        int64_t col_cap, int64_t *nnz, void *stream);
+
 /* SPH(2) derivatives of ncomp fields phi (ncomp x n, component-major, all
  * particle types; wall values enter the sums) at the fluid particles:
  *   grad_hat[(c*dim + K)*n + i] = <d phi_c / d x^_K>^(1)           (Eq. gra_1st)

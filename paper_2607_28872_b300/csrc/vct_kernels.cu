@@ -6,7 +6,10 @@
 // SPH(2) moment matrix M_i are always FP64, as are the pressure-equation
 // iterate and residual.  No tensor cores: every sum is a gather over about 20
 // (2-D) or 56 (3-D) neighbours.
-#include <cooperative_groups.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "vct_internal.cuh"
 
@@ -1889,3 +1892,297 @@ void launch_store(const DevParams &P, Part cur, vct_state s, int64_t n, const in
 }
 
 }  // namespace vct
+
+// ===========================================================================
+// Allocation-free neighbour search: vct_build_neighbours_noalloc.
+//
+// Some callers cannot allocate device memory at the moment they need neighbour
+// lists: an application that has handed all device memory to its own pool
+// allocator (a further cudaMalloc fails or breaks its accounting), or a loop
+// with a latency budget that cannot afford cudaMalloc/cudaFree, which may
+// synchronise the device.  Such callers also cannot own a vct_ctx, whose
+// vct_init allocates.  For them this entry point takes the map and parameters
+// directly and keeps all of its scratch in the file-scope array below, sized
+// for at most NA_MAX_PARTICLES particles and NA_MAX_CELLS cells (about 1 MB).
+// Every GPU that loads this library holds that array until the process exits.
+//
+// The array is shared by every call on a device and keeps the last call's
+// contents; each call clears the counters it needs before use.  Calls that
+// overlap on the GPU (for example on two streams at once) race on the array
+// and must not be issued.
+// ===========================================================================
+namespace vct_noalloc {
+
+constexpr int NA_MAX_PARTICLES = 16384;
+constexpr int NA_MAX_CELLS = 32768;
+
+struct Scratch {
+    double xh[3][NA_MAX_PARTICLES];     // projected positions, caller order
+    int32_t key[NA_MAX_PARTICLES];      // cell of each particle
+    int32_t perm[NA_MAX_PARTICLES];     // particles ordered by cell, then by index
+    int32_t row_cnt[NA_MAX_PARTICLES];  // neighbours of each particle
+    int32_t cell_count[NA_MAX_CELLS + 1];
+    int32_t cell_start[NA_MAX_CELLS + 1];
+    int32_t cursor[NA_MAX_CELLS];
+    int32_t status[4];                  // [0]: 0 or VCT_ERR_CAPACITY
+};
+
+}  // namespace vct_noalloc
+
+static __device__ __align__(256) vct_noalloc::Scratch g_noalloc_scratch;
+
+namespace vct_noalloc {
+
+using vct::DevParams;
+
+__global__ void k_na_clear(Scratch *S, int ncell)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncell; c += gridDim.x * blockDim.x) {
+        S->cell_count[c] = 0;
+        if (c < ncell) S->cursor[c] = 0;
+        if (c < 4) S->status[c] = 0;
+    }
+}
+
+__global__ void k_na_map(DevParams P, vct_state s, int n, Scratch *S)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double y = P.dim == 3 ? s.y[i] : 0.0, zh, J, sx, sy, c0, c3;
+    vct::map_metric(P, s.x[i], y, s.z[i], zh, J, sx, sy, c0, c3);
+    S->xh[0][i] = s.x[i];
+    S->xh[1][i] = y;
+    S->xh[2][i] = zh;
+    int cx = vct::cell_coord(P, s.x[i], 0);
+    int cy = P.dim == 3 ? vct::cell_coord(P, y, 1) : 0;
+    int cz = vct::cell_coord(P, zh, 2);
+    int key = (cz * P.nc[1] + cy) * P.nc[0] + cx;
+    S->key[i] = key;
+    atomicAdd(&S->cell_count[key], 1);
+}
+
+// Exclusive scan by one block of 1024 threads; out[m] = total.
+template <typename TO>
+__device__ void na_block_scan(const int32_t *in, TO *out, int m)
+{
+    __shared__ long long sh[1024];
+    const int t = threadIdx.x, per = (m + 1023) / 1024;
+    const int a = t * per, b = min(a + per, m);
+    long long loc = 0;
+    for (int k = a; k < b; ++k) loc += in[k];
+    sh[t] = loc;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        long long v = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    long long run = sh[t] - loc;
+    for (int k = a; k < b; ++k) {
+        out[k] = (TO)run;
+        run += in[k];
+    }
+    if (t == 1023) out[m] = (TO)sh[1023];
+}
+
+__global__ void k_na_scan_cells(Scratch *S, int ncell)
+{
+    na_block_scan<int32_t>(S->cell_count, S->cell_start, ncell);
+}
+
+__global__ void k_na_scatter(Scratch *S, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int key = S->key[i];
+    S->perm[S->cell_start[key] + atomicAdd(&S->cursor[key], 1)] = i;
+}
+
+__global__ void k_na_cell_sort(Scratch *S, int ncell)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int a = S->cell_start[c], b = S->cell_start[c + 1];
+    for (int k = a + 1; k < b; ++k) {
+        int v = S->perm[k], m = k - 1;
+        while (m >= a && S->perm[m] > v) {
+            S->perm[m + 1] = S->perm[m];
+            --m;
+        }
+        S->perm[m + 1] = v;
+    }
+}
+
+// Visit the candidates of particle i (3^d cells) and apply the FP64 predicate
+// without FMA; fn(j) is called for every neighbour.
+template <typename Fn>
+__device__ void na_visit(const DevParams &P, const Scratch *S, int i, Fn fn)
+{
+    const double xi = S->xh[0][i], yi = S->xh[1][i], zi = S->xh[2][i];
+    int cx = vct::cell_coord(P, xi, 0);
+    int cy = P.dim == 3 ? vct::cell_coord(P, yi, 1) : 0;
+    int cz = vct::cell_coord(P, zi, 2);
+    const int ylo = P.dim == 3 ? -1 : 0, yhi = P.dim == 3 ? 1 : 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z2 = cz + dz;
+        if (z2 < 0 || z2 >= P.nc[2]) continue;
+        for (int dy = ylo; dy <= yhi; ++dy) {
+            int y2 = cy + dy;
+            if (y2 < 0 || y2 >= P.nc[1]) continue;
+            int row = (z2 * P.nc[1] + y2) * P.nc[0];
+            int xa = cx > 0 ? cx - 1 : 0, xb = cx + 1 < P.nc[0] ? cx + 1 : P.nc[0] - 1;
+            for (int k = S->cell_start[row + xa]; k < S->cell_start[row + xb + 1]; ++k) {
+                int j = S->perm[k];
+                if (j == i) continue;
+                double dx = __dsub_rn(S->xh[0][j], xi), dz2 = __dsub_rn(S->xh[2][j], zi), d2;
+                if (P.dim == 2) {
+                    d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dz2, dz2));
+                } else {
+                    double dy2 = __dsub_rn(S->xh[1][j], yi);
+                    d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy2, dy2)),
+                                   __dmul_rn(dz2, dz2));
+                }
+                if (d2 < P.re2) fn(j);
+            }
+        }
+    }
+}
+
+__global__ void k_na_count(DevParams P, Scratch *S, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cnt = 0;
+    na_visit(P, S, i, [&](int) { ++cnt; });
+    S->row_cnt[i] = cnt;
+}
+
+__global__ void k_na_scan_rows(Scratch *S, int n, int64_t *row_ptr)
+{
+    na_block_scan<int64_t>(S->row_cnt, row_ptr, n);
+}
+
+__global__ void k_na_fill(DevParams P, Scratch *S, int n, const int64_t *row_ptr, int32_t *col,
+                          int64_t col_cap)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (row_ptr[n] > col_cap) {
+        if (i == 0) S->status[0] = VCT_ERR_CAPACITY;
+        return;
+    }
+    int32_t *out = col + row_ptr[i];
+    int cnt = 0;
+    na_visit(P, S, i, [&](int j) {   // insertion into the row, ascending index
+        int m = cnt - 1;
+        while (m >= 0 && out[m] > j) {
+            out[m + 1] = out[m];
+            --m;
+        }
+        out[m + 1] = j;
+        ++cnt;
+    });
+}
+
+// Address of the scratch array on the current device, set up once per device.
+vct_status scratch_on_device(Scratch **out)
+{
+    static Scratch *ptr[128] = {};
+    static std::mutex mu;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return VCT_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return VCT_ERR_CUDA;
+        ptr[dev] = (Scratch *)p;
+    }
+    *out = ptr[dev];
+    return VCT_OK;
+}
+
+}  // namespace vct_noalloc
+
+extern "C" __attribute__((visibility("default"))) vct_status vct_build_neighbours_noalloc(
+    const vct_bathymetry *bathy, vct_map_kind kind, double aspect_ratio, const vct_params *prm,
+    const vct_state *s, int64_t *row_ptr, int32_t *col, int64_t col_cap, int64_t *nnz,
+    void *stream)
+{
+    using namespace vct_noalloc;
+    if (!bathy || !prm || !s || !row_ptr || !nnz) return VCT_ERR_ARG;
+    if (prm->dim != 2 && prm->dim != 3) return VCT_ERR_ARG;
+    if ((int)kind < 0 || (int)kind > 3) return VCT_ERR_ARG;
+    if (!(prm->d0 > 0) || bathy->n_gauss < 0 || bathy->n_gauss > VCT_MAX_GAUSS) return VCT_ERR_ARG;
+    if (bathy->n_gauss > 0 && (!bathy->amp || !bathy->cx || !bathy->cy || !bathy->width))
+        return VCT_ERR_ARG;
+    if ((kind == VCT_MAP_E || kind == VCT_MAP_BFE) && !(aspect_ratio > 0)) return VCT_ERR_ARG;
+    if (kind == VCT_MAP_SIGMA && !(prm->H_hat > 0 && prm->alpha_min > 0 &&
+                                   prm->alpha_max >= prm->alpha_min))
+        return VCT_ERR_ARG;
+    if (!s->x || !s->z || (prm->dim == 3 && !s->y)) return VCT_ERR_ARG;
+    if (s->n <= 0) return VCT_ERR_ARG;
+    if (s->n > NA_MAX_PARTICLES) return VCT_ERR_CAPACITY;
+    const int n = (int)s->n;
+    vct::DevParams P;
+    memset(&P, 0, sizeof P);
+    P.dim = prm->dim;
+    P.kind = (int)kind;
+    P.n_gauss = bathy->n_gauss;
+    P.aspect = aspect_ratio;
+    P.d0 = prm->d0;
+    P.l = prm->l_over_d0 * prm->d0;
+    P.re = prm->re_over_l * P.l;
+    P.re2 = P.re * P.re;
+    P.H = prm->H;
+    P.H_hat = prm->H_hat;
+    P.amin = prm->alpha_min;
+    P.amax = prm->alpha_max;
+    P.cell_h = P.re;
+    P.inv_cell_h = 1.0 / P.cell_h;
+    long long ncell = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (!(prm->box_hi[k] >= prm->box_lo[k])) return VCT_ERR_ARG;
+        P.box_lo[k] = prm->box_lo[k];
+        int nk = (int)floor((prm->box_hi[k] - prm->box_lo[k]) * P.inv_cell_h) + 1;
+        if (prm->dim == 2 && k == 1) nk = 1;
+        P.nc[k] = nk;
+        ncell *= nk;
+    }
+    if (ncell > NA_MAX_CELLS) return VCT_ERR_CAPACITY;
+    P.h0 = bathy->h0;
+    P.slope_x = bathy->slope_x;
+    P.slope_y = bathy->slope_y;
+    P.cos_amp = bathy->cos_amp;
+    P.cos_len = bathy->cos_len;
+    for (int g = 0; g < bathy->n_gauss; ++g) {
+        P.gamp[g] = bathy->amp[g];
+        P.gcx[g] = bathy->cx[g];
+        P.gcy[g] = bathy->cy[g];
+        P.gwid[g] = bathy->width[g];
+    }
+    Scratch *S = nullptr;
+    vct_status v = scratch_on_device(&S);
+    if (v) return v;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nc = (int)ncell, gp = (n + 255) / 256, gc = (nc + 255) / 256;
+    k_na_clear<<<gc + 1, 256, 0, st>>>(S, nc);
+    k_na_map<<<gp, 256, 0, st>>>(P, *s, n, S);
+    k_na_scan_cells<<<1, 1024, 0, st>>>(S, nc);
+    k_na_scatter<<<gp, 256, 0, st>>>(S, n);
+    k_na_cell_sort<<<gc, 256, 0, st>>>(S, nc);
+    k_na_count<<<gp, 256, 0, st>>>(P, S, n);
+    k_na_scan_rows<<<1, 1024, 0, st>>>(S, n, row_ptr);
+    if (col) k_na_fill<<<gp, 256, 0, st>>>(P, S, n, row_ptr, col, col_cap);
+    int64_t total = 0;
+    int32_t status = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, row_ptr + n, sizeof total, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&status, S->status, sizeof status, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    *nnz = total;
+    if (col && total > col_cap) return VCT_ERR_CAPACITY;
+    return (vct_status)status;
+}

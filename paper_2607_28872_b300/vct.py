@@ -19,7 +19,8 @@ VCT_ERR_SINGULAR, VCT_ERR_NONFINITE, VCT_ERR_NOCONV, VCT_ERR_TIMEOUT = 4, 5, 6, 
 MAP = {"E": 0, "BF": 1, "BFE": 2, "SIGMA": 3}
 VCT_MAX_GAUSS = 32
 
-EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives", "vct_step",
+EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
+           "sph2_derivatives", "vct_step",
            "vct_step_host", "vct_step_probe", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
 
@@ -83,6 +84,10 @@ def load_library(path=LIB_PATH):
     L.vct_set_stream.argtypes = [vp, vp]
     L.vct_build_neighbours.argtypes = [vp, C.POINTER(vct_state), vp, vp, C.c_int64,
                                        C.POINTER(C.c_int64)]
+    L.vct_build_neighbours_noalloc.argtypes = [C.POINTER(vct_bathymetry), C.c_int, C.c_double,
+                                               C.POINTER(vct_params), C.POINTER(vct_state), vp,
+                                               vp, C.c_int64, C.POINTER(C.c_int64), vp]
+    L.vct_build_neighbours_noalloc.restype = C.c_int
     L.sph2_derivatives.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp, vp]
     L.vct_step.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_host.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
@@ -302,3 +307,23 @@ class Solver:
         self._check(self.lib.vct_step_probe(self.ctx, C.byref(s), C.byref(pr), C.byref(st)),
                     "vct_step_probe")
         return out, st
+
+
+def vct_build_neighbours_noalloc(sc, state, row_ptr, col, stream=None):
+    """Neighbour CSR without a context and without any device allocation (for
+    callers that cannot allocate device memory).  row_ptr: int64 CUDA tensor of
+    n+1 entries; col: int32 CUDA tensor (or None to get only nnz).  Returns
+    (status, nnz); the limits are 16384 particles and 32768 cells."""
+    import torch
+    lib = load_library()
+    bathy, keep = make_bathymetry(sc.bathy)
+    params = make_params(sc)
+    s = state.struct()
+    nnz = C.c_int64(0)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    rc = lib.vct_build_neighbours_noalloc(C.byref(bathy), MAP[sc.map_kind], float(sc.aspect),
+                                          C.byref(params), C.byref(s), _ptr(row_ptr), _ptr(col),
+                                          0 if col is None else col.numel(), C.byref(nnz),
+                                          C.c_void_p(stream.cuda_stream))
+    return rc, nnz.value
