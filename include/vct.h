@@ -101,7 +101,8 @@ typedef struct {
     double box_lo[3], box_hi[3]; /* projected-space box of the cell grid; particles
                                     outside are clamped into the border cells */
     int32_t max_neighbours; /* neighbour-list capacity per particle (0: 64 in 2-D, 160 in 3-D) */
-    int32_t reserved1;
+    int32_t preconditioner; /* pressure solve: 0 plain BiCGSTAB; 1 BiCGSTAB preconditioned by an
+                               aggregation multigrid V-cycle on the cell grid */
 } vct_params;
 
 /* Particle state, caller order, DEVICE arrays of n entries (host arrays for

@@ -21,6 +21,9 @@ struct vct_ctx {
     bool cur_is_A;
     Work W;
     int coop_blocks;
+    int coop_blocks_mg;
+    int precond;
+    MG mg;
     // device mirror of a caller state for vct_step_host
     vct_state mirror;
     int64_t *row_int;          // CSR rows when the caller passes none
@@ -199,7 +202,13 @@ vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, 
         int e;
         {
             StageTimer t(c, VCT_STAGE_KRYLOV);
-            e = launch_krylov(c->P, cur(c), c->W, n, step, c->coop_blocks, c->st);
+            if (c->precond) {
+                launch_mg_setup(c->P, c->W, c->mg, n, c->st);
+                e = launch_krylov_mg(c->P, c->W, c->mg, n, c->coop_blocks_mg, c->st);
+                c->launches += 2 + (c->mg.L - 1);
+            } else {
+                e = launch_krylov(c->P, cur(c), c->W, n, step, c->coop_blocks, c->st);
+            }
         }
         if (e) return VCT_ERR_CUDA;
         if (pr && step == nsteps - 1) {
@@ -315,6 +324,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     c->cur_is_A = true;
     Work &W = c->W;
     W.cap = n;
+    W.max_nbr = (int32_t)K;
     W.ncell = ncell;
     W.key = dalloc<int32_t>(c, n, e);
     W.cell_count = dalloc<int32_t>(c, ncell + 1, e);
@@ -354,6 +364,48 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.kd = dalloc<double>(c, n, e);
     W.kf = dalloc<double>(c, n, e);
     c->coop_blocks = krylov_coop_blocks(prm->precision, prm->dim);
+    c->precond = prm->preconditioner == 1;
+    c->coop_blocks_mg = krylov_mg_coop_blocks(prm->precision, prm->dim);
+    {   // multigrid hierarchy over the cell grid
+        MG &M = c->mg;
+        memset(&M, 0, sizeof M);
+        M.S = prm->dim == 2 ? 9 : 27;
+        M.omega = 0.7f;
+        M.kappa = 1.0f;
+        M.coarse_sweeps = 24;
+        M.dims[1][0] = P.nc[0];
+        M.dims[1][1] = P.nc[1];
+        M.dims[1][2] = P.nc[2];
+        M.n[1] = (int)ncell;
+        int l = 1;
+        while (M.n[l] > 4 && l < MG_MAXL) {
+            int nx = (M.dims[l][0] + 1) / 2, ny = prm->dim == 3 ? (M.dims[l][1] + 1) / 2 : 1;
+            int nz = (M.dims[l][2] + 1) / 2;
+            if ((long long)nx * ny * nz == M.n[l]) break;
+            M.dims[l + 1][0] = nx;
+            M.dims[l + 1][1] = ny;
+            M.dims[l + 1][2] = nz;
+            M.n[l + 1] = nx * ny * nz;
+            ++l;
+        }
+        M.L = l;
+        M.first_local = M.L;
+        for (int q = 1; q <= M.L; ++q)
+            if (M.n[q] <= 2048) { M.first_local = q; break; }
+        long long pos = 0;
+        for (int q = 1; q <= M.L; ++q) {
+            M.offA[q] = pos;
+            pos += (long long)M.S * M.n[q];
+            M.offv[q] = pos;
+            pos += 4LL * M.n[q];
+        }
+        W.mg_pool = dalloc<float>(c, pos, e);
+        W.mg_dsc = dalloc<float>(c, n, e);
+        W.cellid = dalloc<int32_t>(c, n, e);
+        W.kr0 = dalloc<double>(c, n, e);
+        W.kq0 = dalloc<double>(c, n, e);
+        W.kq1 = dalloc<double>(c, n, e);
+    }
     if (c->coop_blocks <= 0) e = e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
     W.partial = dalloc<double>(c, (int64_t)8 * 4096, e);   // k-major, 4096 blocks max
     W.scal = dalloc<double>(c, 16, e);

@@ -44,6 +44,7 @@ struct Part {
 // Scratch of one step.
 struct Work {
     int64_t cap;
+    int32_t max_nbr;          // ELL slots per particle
     int32_t *key, *cell_count, *cell_start, *cursor, *perm, *scan_tmp;
     int64_t ncell;
     int32_t *nbr_cnt, *nbr;   // ELL neighbour lists, slot-major
@@ -66,6 +67,29 @@ struct Work {
     long long *counts;        // [0] unknown rows, [1] off-diagonal coefficients (last step)
     // csr export
     int64_t *row_tmp;
+    // multigrid preconditioner
+    int32_t *cellid;          // level-1 node (cell) of each sorted particle
+    float *mg_dsc;            // 1 / diag of each unknown row (0 elsewhere)
+    float *mg_pool;           // coarse operators and vectors of all levels
+    double *kr0;              // fine residual of the V-cycle (FP32 or FP64 slots)
+    double *kq0, *kq1;        // preconditioned directions p^, s^
+};
+
+// Coarse levels of the aggregation multigrid: level 1 = the cell grid, level
+// l+1 = 2 x 2 (x 2) blocks of level l.  Each level stores, in mg_pool, its
+// stencil operator A[o * n + I] (S = 3^dim entries per node) at offA and four
+// vectors at offv: dinv, b, z, zu (each n floats).
+constexpr int MG_MAXL = 24;
+struct MG {
+    int L;               // coarsest level index (levels 1..L)
+    int first_local;     // first level processed by block 0 alone
+    int S;               // stencil size, 9 (2-D) or 27 (3-D)
+    int coarse_sweeps;   // Jacobi sweeps on the coarsest level
+    float omega, kappa;  // Jacobi damping and coarse-correction scale
+    int n[MG_MAXL + 1];
+    int dims[MG_MAXL + 1][3];
+    long long offA[MG_MAXL + 1];
+    long long offv[MG_MAXL + 1];
 };
 
 struct Ctx;
@@ -84,6 +108,10 @@ void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor
 void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot,
                   int nblocks_coop, cudaStream_t st);
+void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st);
+int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
+                     cudaStream_t st);
+int krylov_mg_coop_blocks(int precision, int dim);
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
                        int ncomp, double *grad, double *d2, double *lap, cudaStream_t st);

@@ -509,6 +509,7 @@ __global__ void k_reorder(const Part c, Part a, Work W, int n)
     a.type[i] = c.type[s]; a.orig[i] = c.orig[s];
     a.xh[i] = c.xh[s]; a.yh[i] = c.yh[s]; a.zh[i] = c.zh[s];
     a.J[i] = c.J[s]; a.sx[i] = c.sx[s]; a.sy[i] = c.sy[s]; a.c0[i] = c.c0[s]; a.c3[i] = c.c3[s];
+    W.cellid[i] = W.key[s];
 }
 
 void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cudaStream_t st)
@@ -1213,13 +1214,25 @@ void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st
 constexpr int KT = 256;
 constexpr unsigned long long SPIN_LIMIT = 40000000ull;   // bounded: ~1-2 s at most
 
-__device__ __forceinline__ unsigned ld_volatile(const unsigned int *p)
+__device__ __forceinline__ unsigned ld_acquire(const unsigned int *p)
 {
-    return *(const volatile unsigned int *)p;
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Sense-reversal grid barrier for a cooperative launch (all blocks resident).
-// Spins are bounded: on timeout the block records status[2] and every block
+__device__ __forceinline__ unsigned atom_add_release(unsigned int *p, unsigned v)
+{
+    unsigned o;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(o) : "l"(p), "r"(v) : "memory");
+    return o;
+}
+
+// Grid barrier for a cooperative launch (all blocks resident), one atomic per
+// block: block 0 adds 2^31 - (nblocks - 1), every other block adds 1, so the
+// word's top bit flips exactly when the last block arrives; each block waits
+// for the top bit to differ from the value it saw.  The word needs no reset.
+// Spins are bounded: on timeout the block records status[2], and every block
 // leaves at its next barrier, so the kernel always ends.
 __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status)
 {
@@ -1227,25 +1240,16 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *statu
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned gen = ld_volatile(bar + 1);
-        __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (ld_volatile(bar + 1) == gen) {
-                if (++spins > 2048) __nanosleep(20);
-                if (spins > SPIN_LIMIT) {
-                    ok = 0;
-                    atomicExch(status + 2, 1);
-                    break;
-                }
+        unsigned inc = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
+        unsigned old = atom_add_release(bar, inc);
+        unsigned long long spins = 0;
+        while (((ld_acquire(bar) ^ old) & 0x80000000u) == 0u) {
+            if (++spins > SPIN_LIMIT) {
+                ok = 0;
+                atomicExch(status + 2, 1);
+                break;
             }
         }
-        __threadfence();
         if (*(volatile int32_t *)(status + 2)) ok = 0;
         ok_sh = ok;
     }
@@ -1333,16 +1337,47 @@ __device__ __forceinline__ T group_sum(T v)
     return v;
 }
 
-// G lanes per row: lane g of the group takes coefficients g, g+G, ...; the
-// row's scalar work is repeated by every lane of the group (same addresses,
-// broadcast loads) and only lane 0 writes.
-template <typename T, typename CT, int G>
+// Dot of row i with a gathered vector: lane lg of the row's group takes slots
+// lg, lg+G, ...  The first NS slots' columns and coefficients are loaded before
+// the row's count is known (ELL slots below max_nbr are always allocated), so a
+// row costs one round trip for its operator and one for the gathers.
+template <typename T, typename CT, int G, int NS, typename GetX>
+__device__ __forceinline__ T row_dot(const Work &W, int i, int pc, int lg, GetX getx)
+{
+    const int64_t cap = W.cap;
+    int jj[NS];
+    CT aa[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int kk = lg + s * G;
+        jj[s] = 0;
+        aa[s] = CT(0);
+        if (kk < W.max_nbr) {
+            const int64_t q = (int64_t)kk * cap + i;
+            jj[s] = W.pcol[q];
+            aa[s] = coef<CT>(W, q);
+        }
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (lg + s * G < pc) acc += (T)aa[s] * getx(jj[s]);
+    for (int kk = lg + NS * G; kk < pc; kk += G) {
+        const int64_t q = (int64_t)kk * cap + i;
+        acc += (T)coef<CT>(W, q) * getx(W.pcol[q]);
+    }
+    return acc;
+}
+
+// G lanes per row; the row's scalar work is repeated by every lane of the group
+// (same addresses, broadcast loads) and only lane 0 writes.  Dot-product
+// partials are accumulated per thread in T and summed per block in FP64.
+template <typename T, typename CT, int G, int NS>
 __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double rtol,
                                                double inner_floor, int32_t *iters_out,
                                                double *resid_out)
 {
     const unsigned nb = gridDim.x;
-    const int64_t cap = W.cap;
     const int lg = threadIdx.x & (G - 1);
     const bool lead = lg == 0;
     const int ngroups = (gridDim.x * blockDim.x) / G;
@@ -1357,13 +1392,9 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
         // true residual in FP64: f = b - A x
         double part[2] = {0.0, 0.0};
         for (int i = g0; i < n; i += ngroups) {
-            int pc = W.pcnt[i];
+            const int pc = W.pcnt[i];
             if (pc < 0) continue;
-            double ax = 0.0;
-            for (int k = lg; k < pc; k += G) {
-                int64_t q = (int64_t)k * cap + i;
-                ax += (double)coef<CT>(W, q) * __ldcg(x + W.pcol[q]);
-            }
+            double ax = row_dot<double, CT, G, NS>(W, i, pc, lg, [&](int j) { return __ldcg(x + j); });
             ax = group_sum<G>(ax);
             if (lead) {
                 double bi = W.bvec[i], fi = bi - (ax + W.diag[i] * x[i]);
@@ -1400,46 +1431,43 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
             const double beta = first ? 0.0 : (rho / rho_old) * (alpha / omega);
             const T tb = (T)beta, tw = (T)omega, ta = (T)alpha;
             // phase A: apply the pending update, p_new = r + beta (p - w v), v_new = A p_new
-            double pa[1] = {0.0};
+            T pa = T(0);
             for (int i = g0; i < n; i += ngroups) {
-                int pc = W.pcnt[i];
+                const int pc = W.pcnt[i];
                 if (pc < 0) continue;
-                T ri, pn;
-                if (first) {
-                    ri = (T)f[i];
-                    pn = ri;
-                } else {
-                    T si = s[i];
-                    ri = si - tw * t[i];
-                    pn = ri + tb * (pold[i] - tw * vold[i]);
-                }
-                T acc = T(0);
-                for (int k = lg; k < pc; k += G) {
-                    int64_t q = (int64_t)k * cap + i;
-                    int j = W.pcol[q];
-                    T pj;
-                    if (first) pj = (T)__ldcg(f + j);
-                    else
-                        pj = (__ldcg(s + j) - tw * __ldcg(t + j)) +
-                             tb * (__ldcg(pold + j) - tw * __ldcg(vold + j));
-                    acc += (T)coef<CT>(W, q) * pj;
-                }
+                T acc;
+                if (first)
+                    acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) { return (T)__ldcg(f + j); });
+                else
+                    acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) {
+                        return (__ldcg(s + j) - tw * __ldcg(t + j)) +
+                               tb * (__ldcg(pold + j) - tw * __ldcg(vold + j));
+                    });
                 acc = group_sum<G>(acc);
                 if (lead) {
-                    acc += (T)W.diag[i] * pn;
+                    T ri, pn;
                     if (first) {
+                        ri = (T)f[i];
+                        pn = ri;
                         rh[i] = ri;
                         dl[i] = T(0);
                     } else {
-                        dl[i] += ta * pold[i] + tw * s[i];
+                        const T si = s[i], po = pold[i];
+                        ri = si - tw * t[i];
+                        pn = ri + tb * (po - tw * vold[i]);
+                        dl[i] += ta * po + tw * si;
                     }
+                    acc += (T)W.diag[i] * pn;
                     r[i] = ri;
                     pnew[i] = pn;
                     vnew[i] = acc;
-                    pa[0] += (double)rh[i] * (double)acc;
+                    pa += rh[i] * acc;
                 }
             }
-            block_partials<1>(pa, W.partial);
+            {
+                double pd[1] = {(double)pa};
+                block_partials<1>(pd, W.partial);
+            }
             if (!grid_barrier(W.bar, nb, W.status)) return;
             double tv[1];
             grid_totals<1>(W.partial, nb, tv);
@@ -1452,31 +1480,30 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
             alpha = rho / tv[0];
             const T ta2 = (T)alpha;
             // phase B: s = r - alpha v_new, t = A s; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
-            double pb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
             for (int i = g0; i < n; i += ngroups) {
-                int pc = W.pcnt[i];
+                const int pc = W.pcnt[i];
                 if (pc < 0) continue;
-                T acc = T(0);
-                for (int k = lg; k < pc; k += G) {
-                    int64_t q = (int64_t)k * cap + i;
-                    int j = W.pcol[q];
-                    acc += (T)coef<CT>(W, q) * (__ldcg(r + j) - ta2 * __ldcg(vnew + j));
-                }
+                T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) {
+                    return __ldcg(r + j) - ta2 * __ldcg(vnew + j);
+                });
                 acc = group_sum<G>(acc);
                 if (lead) {
-                    T si = r[i] - ta2 * vnew[i];
+                    const T si = r[i] - ta2 * vnew[i], hi = rh[i];
                     acc += (T)W.diag[i] * si;
                     s[i] = si;
                     t[i] = acc;
-                    double sd = (double)si, td = (double)acc, hd = (double)rh[i];
-                    pb[0] += td * sd;
-                    pb[1] += td * td;
-                    pb[2] += sd * sd;
-                    pb[3] += hd * sd;
-                    pb[4] += hd * td;
+                    pb0 += acc * si;
+                    pb1 += acc * acc;
+                    pb2 += si * si;
+                    pb3 += hi * si;
+                    pb4 += hi * acc;
                 }
             }
-            block_partials<5>(pb, W.partial);
+            {
+                double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
+                block_partials<5>(pd, W.partial);
+            }
             if (!grid_barrier(W.bar, nb, W.status)) return;
             double tq[5];
             grid_totals<5>(W.partial, nb, tq);
@@ -1520,11 +1547,14 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
     }
 }
 
+// 2-D: 4 lanes per row (~20 coefficients, 5 slots each); 3-D: 8 lanes (~56, 7 slots).
 static const void *krylov_fn(int precision, int dim)
 {
     if (precision == VCT_MIXED)
-        return dim == 2 ? (const void *)k_krylov<float, float, 8> : (const void *)k_krylov<float, float, 16>;
-    return dim == 2 ? (const void *)k_krylov<double, double, 8> : (const void *)k_krylov<double, double, 16>;
+        return dim == 2 ? (const void *)k_krylov<float, float, 4, 5>
+                        : (const void *)k_krylov<float, float, 8, 7>;
+    return dim == 2 ? (const void *)k_krylov<double, double, 4, 5>
+                    : (const void *)k_krylov<double, double, 8, 7>;
 }
 
 int krylov_coop_blocks(int precision, int dim)
@@ -1533,7 +1563,7 @@ int krylov_coop_blocks(int precision, int dim)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, krylov_fn(precision, dim), KT, 0);
-    if (per > 2) per = 2;   // fewer arrivals per grid barrier
+    if (per > 4) per = 4;
     int nb = sms * per;
     return nb < PSTRIDE ? nb : PSTRIDE;
 }
@@ -1548,13 +1578,554 @@ int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot
     int32_t *it_out = W.kiters;
     double *res_out = W.kresid;
     // a grid no larger than the rows need: fewer arrivals per barrier
-    const int G = P.dim == 2 ? 8 : 16;
+    const int G = P.dim == 2 ? 4 : 8;
     int64_t want = (n * G + KT - 1) / KT;
     int nblk = (int)(want < nblocks_coop ? want : nblocks_coop);
     if (nblk < 1) nblk = 1;
     void *args[] = {(void *)&W, (void *)&nn, (void *)&maxit, (void *)&rtol, (void *)&floor_,
                     (void *)&it_out, (void *)&res_out};
+    cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);   // fresh barrier word
     cudaError_t e = cudaLaunchCooperativeKernel(krylov_fn(P.precision, P.dim), dim3(nblk),
+                                                dim3(KT), args, 0, st);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+// ---------------------------------------------------------------------------
+// a8 preconditioner: aggregation multigrid on the cell grid.
+// Level 1 nodes are the neighbour-search cells (their particles are contiguous
+// after the sort); the prolongation is piecewise constant, so the Galerkin
+// operator of level 1 sums the pressure-equation coefficients between cells,
+// giving a 3^d-point stencil; level l+1 aggregates 2 x 2 (x 2) nodes of level
+// l the same way.  The V(1,1) cycle uses damped Jacobi; every neighbour value a
+// phase needs is formed on the fly, so each level costs one grid barrier going
+// down and one coming up.  Levels with at most 2048 nodes run inside block 0.
+// All sums run in a fixed order (no floating-point atomics).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mg_coords(const MG &M, int l, int I, int &cx, int &cy, int &cz)
+{
+    const int nx = M.dims[l][0], ny = M.dims[l][1];
+    cx = I % nx;
+    int tq = I / nx;
+    cy = tq % ny;
+    cz = tq / ny;
+}
+
+template <int D>
+__device__ __forceinline__ int stencil_index(int dx, int dy, int dz)
+{
+    return D == 2 ? (dz + 1) * 3 + (dx + 1) : ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
+}
+
+template <int D>
+__global__ void k_mg_level1(Work W, MG M, int mixed)
+{
+    constexpr int S = D == 2 ? 9 : 27;
+    const int N = M.n[1];
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= N) return;
+    float acc[S];
+#pragma unroll
+    for (int o = 0; o < S; ++o) acc[o] = 0.f;
+    int cx, cy, cz;
+    mg_coords(M, 1, I, cx, cy, cz);
+    const int a = W.cell_start[I], b = W.cell_start[I + 1];
+    const int64_t cap = W.cap;
+    int rows = 0;
+    double center = 0.0;
+    for (int i = a; i < b; ++i) {
+        const int pc = W.pcnt[i];
+        if (pc < 0) continue;
+        ++rows;
+        center += W.diag[i];
+        for (int k = 0; k < pc; ++k) {
+            const int64_t q = (int64_t)k * cap + i;
+            const int j = W.pcol[q];
+            const float av = mixed ? W.pvalf[q] : (float)W.pval[q];
+            int jx, jy, jz;
+            mg_coords(M, 1, W.cellid[j], jx, jy, jz);
+            acc[stencil_index<D>(jx - cx, jy - cy, jz - cz)] += av;
+        }
+    }
+    const int cidx = stencil_index<D>(0, 0, 0);
+    acc[cidx] += (float)center;
+    float *A = M.offA[1] + W.mg_pool;
+    float *v = M.offv[1] + W.mg_pool;
+#pragma unroll
+    for (int o = 0; o < S; ++o) A[(int64_t)o * N + I] = acc[o];
+    v[I] = (rows > 0 && acc[cidx] != 0.f) ? 1.f / acc[cidx] : 0.f;   // dinv
+}
+
+template <int D>
+__global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from level l
+{
+    constexpr int S = D == 2 ? 9 : 27;
+    const int Nc = M.n[l + 1], Nf = M.n[l];
+    const int Ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Ic >= Nc) return;
+    float acc[S];
+#pragma unroll
+    for (int o = 0; o < S; ++o) acc[o] = 0.f;
+    int px, py, pz;
+    mg_coords(M, l + 1, Ic, px, py, pz);
+    const float *Af = W.mg_pool + M.offA[l];
+    const float *vf = W.mg_pool + M.offv[l];
+    const int fx = M.dims[l][0], fy = M.dims[l][1], fz = M.dims[l][2];
+    bool any = false;
+    for (int c = 0; c < (D == 2 ? 4 : 8); ++c) {
+        const int ax = px * 2 + (c & 1);
+        const int ay = D == 3 ? py * 2 + ((c >> 1) & 1) : 0;
+        const int az = pz * 2 + (D == 2 ? ((c >> 1) & 1) : ((c >> 2) & 1));
+        if (ax >= fx || ay >= fy || az >= fz) continue;
+        const int If = (az * fy + ay) * fx + ax;
+        if (vf[If] == 0.f) continue;          // inactive node
+        any = true;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const float aval = Af[(int64_t)stencil_index<D>(dx, dy, dz) * Nf + If];
+                    if (aval == 0.f) continue;
+                    const int jx = ax + dx, jy = ay + dy, jz = az + dz;
+                    acc[stencil_index<D>((jx >> 1) - px, D == 3 ? (jy >> 1) - py : 0, (jz >> 1) - pz)] += aval;
+                }
+    }
+    float *Ac = W.mg_pool + M.offA[l + 1];
+    float *vc = W.mg_pool + M.offv[l + 1];
+#pragma unroll
+    for (int o = 0; o < S; ++o) Ac[(int64_t)o * Nc + Ic] = acc[o];
+    const float cc = acc[stencil_index<D>(0, 0, 0)];
+    vc[Ic] = (any && cc != 0.f) ? 1.f / cc : 0.f;
+}
+
+__global__ void k_mg_dsc(Work W, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    W.mg_dsc[i] = (W.pcnt[i] >= 0 && W.diag[i] != 0.0) ? (float)(1.0 / W.diag[i]) : 0.f;
+}
+
+void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st)
+{
+    k_mg_dsc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
+    const unsigned g1 = (unsigned)((M.n[1] + 127) / 128);
+    const int mixed = P.precision == VCT_MIXED;
+    if (P.dim == 2) k_mg_level1<2><<<g1, 128, 0, st>>>(W, M, mixed);
+    else k_mg_level1<3><<<g1, 128, 0, st>>>(W, M, mixed);
+    for (int l = 1; l < M.L; ++l) {
+        const unsigned g = (unsigned)((M.n[l + 1] + 127) / 128);
+        if (P.dim == 2) k_mg_coarsen<2><<<g, 128, 0, st>>>(W, M, l);
+        else k_mg_coarsen<3><<<g, 128, 0, st>>>(W, M, l);
+    }
+}
+
+// One coarse down phase: nodes of level l+1 (start, stride) sum the residuals of
+// their children at level l and take one damped Jacobi step from zero.
+template <int D>
+__device__ void mg_down(const Work &W, const MG &M, int l, int start, int stride)
+{
+    const int Nc = M.n[l + 1], Nf = M.n[l];
+    const float *Af = W.mg_pool + M.offA[l];
+    const float *vf = W.mg_pool + M.offv[l];
+    const float *bf = vf + Nf, *zf = vf + 2 * Nf;
+    float *vc = W.mg_pool + M.offv[l + 1];
+    const int fx = M.dims[l][0], fy = M.dims[l][1], fz = M.dims[l][2];
+    for (int Ic = start; Ic < Nc; Ic += stride) {
+        int px, py, pz;
+        mg_coords(M, l + 1, Ic, px, py, pz);
+        float bsum = 0.f;
+        for (int c = 0; c < (D == 2 ? 4 : 8); ++c) {
+            const int ax = px * 2 + (c & 1);
+            const int ay = D == 3 ? py * 2 + ((c >> 1) & 1) : 0;
+            const int az = pz * 2 + (D == 2 ? ((c >> 1) & 1) : ((c >> 2) & 1));
+            if (ax >= fx || ay >= fy || az >= fz) continue;
+            const int If = (az * fy + ay) * fx + ax;
+            if (__ldcg(vf + If) == 0.f) continue;
+            float res = __ldcg(bf + If);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int jx = ax + dx, jy = ay + dy, jz = az + dz;
+                        if (jx < 0 || jy < 0 || jz < 0 || jx >= fx || jy >= fy || jz >= fz) continue;
+                        const float aval = Af[(int64_t)stencil_index<D>(dx, dy, dz) * Nf + If];
+                        res -= aval * __ldcg(zf + (jz * fy + jy) * fx + jx);
+                    }
+            bsum += res;
+        }
+        const float dinv = vc[Ic];
+        vc[Nc + Ic] = bsum;                  // b
+        vc[2 * Nc + Ic] = M.omega * bsum * dinv;   // z
+    }
+}
+
+// One coarse up phase: nodes of level l add kappa x the coarser correction and
+// take one damped Jacobi step; the result goes to zu.
+template <int D>
+__device__ void mg_up(const Work &W, const MG &M, int l, int start, int stride)
+{
+    const int N = M.n[l], Nc = M.n[l + 1];
+    const float *A = W.mg_pool + M.offA[l];
+    float *v = W.mg_pool + M.offv[l];
+    const float *b = v + N, *z = v + 2 * N;
+    float *zu = v + 3 * N;
+    const float *zuc = W.mg_pool + M.offv[l + 1] + 3 * Nc;
+    const int nx = M.dims[l][0], ny = M.dims[l][1], nz = M.dims[l][2];
+    const int cxn = M.dims[l + 1][0], cyn = M.dims[l + 1][1];
+    const float kap = M.kappa, om = M.omega;
+    for (int I = start; I < N; I += stride) {
+        const float dinv = v[I];
+        if (dinv == 0.f) {
+            zu[I] = 0.f;
+            continue;
+        }
+        int cx, cy, cz;
+        mg_coords(M, l, I, cx, cy, cz);
+        float res = __ldcg(b + I), zi = 0.f;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int jx = cx + dx, jy = cy + dy, jz = cz + dz;
+                    if (jx < 0 || jy < 0 || jz < 0 || jx >= nx || jy >= ny || jz >= nz) continue;
+                    const int J = (jz * ny + jy) * nx + jx;
+                    const int Jc = ((jz >> 1) * cyn + (D == 3 ? (jy >> 1) : 0)) * cxn + (jx >> 1);
+                    const float zj = __ldcg(z + J) + kap * __ldcg(zuc + Jc);
+                    if (dx == 0 && dy == 0 && dz == 0) zi = zj;
+                    res -= A[(int64_t)stencil_index<D>(dx, dy, dz) * N + I] * zj;
+                }
+        zu[I] = zi + om * dinv * res;
+    }
+}
+
+// Coarsest level: Jacobi sweeps by the calling block alone; the result is zu.
+__device__ void mg_coarsest(const Work &W, const MG &M, int D)
+{
+    const int l = M.L, N = M.n[l];
+    const float *A = W.mg_pool + M.offA[l];
+    float *v = W.mg_pool + M.offv[l];
+    const float *b = v + N;
+    float *z = v + 2 * N, *zu = v + 3 * N;
+    const int nx = M.dims[l][0], ny = M.dims[l][1], nz = M.dims[l][2];
+    for (int sw = 0; sw < M.coarse_sweeps; ++sw) {
+        const float *src = (sw & 1) ? zu : z;
+        float *dst = (sw & 1) ? z : zu;
+        for (int I = threadIdx.x; I < N; I += blockDim.x) {
+            const float dinv = v[I];
+            if (dinv == 0.f) {
+                dst[I] = 0.f;
+                continue;
+            }
+            int cx, cy, cz;
+            mg_coords(M, l, I, cx, cy, cz);
+            float res = __ldcg(b + I);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int jx = cx + dx, jy = cy + dy, jz = cz + dz;
+                        if (jx < 0 || jy < 0 || jz < 0 || jx >= nx || jy >= ny || jz >= nz) continue;
+                        const int o = D == 2 ? (dz + 1) * 3 + (dx + 1) : ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
+                        res -= A[(int64_t)o * N + I] * __ldcg(src + (jz * ny + jy) * nx + jx);
+                    }
+            dst[I] = __ldcg(src + I) + M.omega * dinv * res;
+        }
+        __syncthreads();
+    }
+    if (M.coarse_sweeps & 1) return;   // result already in zu
+    for (int I = threadIdx.x; I < N; I += blockDim.x) zu[I] = __ldcg(z + I);
+    __syncthreads();
+}
+
+// z_out = M^-1 v for the fine vector given on the fly by in(j).  own(i) runs once
+// for every unknown row in the first phase (lane 0 of the row's group), before
+// any phase writes z_out.  Returns false if a grid barrier timed out.
+template <typename T, typename CT, int G, int NS, int D, typename In, typename Own>
+__device__ bool vcycle(const Work &W, const MG &M, int n, In in, Own own, T *zout, int lg, bool lead,
+                       int g0, int ngroups, int gtid, int gthreads)
+{
+    const unsigned nb = gridDim.x;
+    const float om = M.omega, kap = M.kappa;
+    T *r0 = (T *)W.kr0;
+    // D0: fine residual of one Jacobi step from zero, r0 = v - A (om D^-1 v)
+    for (int i = g0; i < n; i += ngroups) {
+        const int pc = W.pcnt[i];
+        if (pc < 0) continue;
+        T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) {
+            return (T)om * in(j) * (T)__ldcg(W.mg_dsc + j);
+        });
+        acc = group_sum<G>(acc);
+        if (lead) {
+            own(i);
+            const T vi = in(i);
+            r0[i] = vi - acc - (T)om * vi;
+        }
+    }
+    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    // D1: restriction to the cells, one Jacobi step from zero on level 1
+    {
+        const int N1 = M.n[1];
+        float *v1 = W.mg_pool + M.offv[1];
+        for (int I = gtid; I < N1; I += gthreads) {
+            float bs = 0.f;
+            const int a = W.cell_start[I], b = W.cell_start[I + 1];
+            for (int i = a; i < b; ++i)
+                if (W.pcnt[i] >= 0) bs += (float)__ldcg(r0 + i);
+            v1[N1 + I] = bs;
+            v1[2 * N1 + I] = om * bs * v1[I];
+        }
+    }
+    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    for (int l = 1; l + 1 <= M.first_local && l < M.L; ++l) {
+        mg_down<D>(W, M, l, gtid, gthreads);
+        if (!grid_barrier(W.bar, nb, W.status)) return false;
+    }
+    if (blockIdx.x == 0) {
+        const int l0 = M.first_local < 1 ? 1 : M.first_local;
+        for (int l = l0; l < M.L; ++l) {
+            mg_down<D>(W, M, l, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+        mg_coarsest(W, M, D);
+        for (int l = M.L - 1; l >= l0; --l) {
+            mg_up<D>(W, M, l, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+    }
+    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    for (int l = (M.first_local < 1 ? 1 : M.first_local) - 1; l >= 1; --l) {
+        mg_up<D>(W, M, l, gtid, gthreads);
+        if (!grid_barrier(W.bar, nb, W.status)) return false;
+    }
+    // U0: prolongation from the cells + one damped Jacobi step on the fine level
+    const float *zu1 = W.mg_pool + M.offv[1] + 3 * M.n[1];
+    for (int i = g0; i < n; i += ngroups) {
+        const int pc = W.pcnt[i];
+        if (pc < 0) continue;
+        auto zb = [&](int j) -> T {
+            return (T)om * in(j) * (T)__ldcg(W.mg_dsc + j) + (T)kap * (T)__ldcg(zu1 + W.cellid[j]);
+        };
+        T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, zb);
+        acc = group_sum<G>(acc);
+        if (lead) {
+            const T zi = zb(i);
+            const T res = in(i) - acc - (T)W.diag[i] * zi;
+            zout[i] = zi + (T)om * res * (T)W.mg_dsc[i];
+        }
+    }
+    return grid_barrier(W.bar, nb, W.status);
+}
+
+// Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
+template <typename T, typename CT, int G, int NS, int D>
+__global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit, double rtol,
+                                                  double inner_floor, int32_t *iters_out,
+                                                  double *resid_out)
+{
+    const unsigned nb = gridDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const bool lead = lg == 0;
+    const int ngroups = (gridDim.x * blockDim.x) / G;
+    const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    double *x = W.kx, *f = W.kf;
+    T *r = (T *)W.kr, *rh = (T *)W.krh, *s = (T *)W.ks, *t = (T *)W.kt, *dl = (T *)W.kd;
+    T *pold = (T *)W.kp0, *pnew = (T *)W.kp1, *vold = (T *)W.kv0, *vnew = (T *)W.kv1;
+    T *ph = (T *)W.kq0, *sh = (T *)W.kq1;   // p^ = M^-1 p, s^ = M^-1 s
+    int total_it = 0;
+    bool fail = false;
+    double bn = 0.0, rn = 0.0;
+    for (int outer = 0;; ++outer) {
+        double part[2] = {0.0, 0.0};
+        for (int i = g0; i < n; i += ngroups) {
+            const int pc = W.pcnt[i];
+            if (pc < 0) continue;
+            double ax = row_dot<double, CT, G, NS>(W, i, pc, lg, [&](int j) { return __ldcg(x + j); });
+            ax = group_sum<G>(ax);
+            if (lead) {
+                double bi = W.bvec[i], fi = bi - (ax + W.diag[i] * x[i]);
+                f[i] = fi;
+                part[0] += fi * fi;
+                part[1] += bi * bi;
+            }
+        }
+        block_partials<2>(part, W.partial);
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        double tot[2];
+        grid_totals<2>(W.partial, nb, tot);
+        rn = sqrt(tot[0]);
+        bn = sqrt(tot[1]);
+        if (bn == 0.0) {
+            for (int i = g0; i < n; i += ngroups)
+                if (lead) x[i] = 0.0;
+            rn = 0.0;
+            break;
+        }
+        if (rn <= rtol * bn) break;
+        if (total_it >= maxit || outer >= 64) {
+            fail = true;
+            break;
+        }
+        const double fn = rn, tol_in = fmax(rtol * bn / rn, inner_floor);
+        double rho = fn * fn, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        bool first = true, have_pend = false;
+        double pend_a = 0.0, pend_w = 0.0;
+        for (;;) {
+            if (total_it >= maxit) break;
+            ++total_it;
+            const double beta = first ? 0.0 : (rho / rho_old) * (alpha / omega);
+            const T tb = (T)beta, tw = (T)omega, ta = (T)pend_a, twp = (T)pend_w;
+            const bool fst = first, hp = have_pend;
+            // p_new = r + beta (p - w v) with r = s - w t; p^ = M^-1 p_new
+            bool ok;
+            if (fst) {
+                ok = vcycle<T, CT, G, NS, D>(W, M, n,
+                    [&](int j) -> T { return (T)__ldcg(f + j); },
+                    [&](int i) { const T ri = (T)f[i]; r[i] = ri; rh[i] = ri; pnew[i] = ri; dl[i] = T(0); },
+                    ph, lg, lead, g0, ngroups, gtid, gthreads);
+            } else {
+                ok = vcycle<T, CT, G, NS, D>(W, M, n,
+                    [&](int j) -> T {
+                        return (__ldcg(s + j) - tw * __ldcg(t + j)) + tb * (__ldcg(pold + j) - tw * __ldcg(vold + j));
+                    },
+                    [&](int i) {
+                        const T ri = s[i] - tw * t[i];
+                        r[i] = ri;
+                        pnew[i] = ri + tb * (pold[i] - tw * vold[i]);
+                        if (hp) dl[i] += ta * ph[i] + twp * sh[i];
+                    },
+                    ph, lg, lead, g0, ngroups, gtid, gthreads);
+            }
+            if (!ok) return;
+            first = false;
+            have_pend = false;
+            // v = A p^, partial (rh, v)
+            T pa = T(0);
+            for (int i = g0; i < n; i += ngroups) {
+                const int pc = W.pcnt[i];
+                if (pc < 0) continue;
+                T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) { return __ldcg(ph + j); });
+                acc = group_sum<G>(acc);
+                if (lead) {
+                    acc += (T)W.diag[i] * ph[i];
+                    vnew[i] = acc;
+                    pa += rh[i] * acc;
+                }
+            }
+            {
+                double pd[1] = {(double)pa};
+                block_partials<1>(pd, W.partial);
+            }
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            double tv[1];
+            grid_totals<1>(W.partial, nb, tv);
+            if (tv[0] == 0.0) {
+                fail = true;
+                break;
+            }
+            alpha = rho / tv[0];
+            const T ta2 = (T)alpha;
+            // s = r - alpha v; s^ = M^-1 s
+            if (!vcycle<T, CT, G, NS, D>(W, M, n,
+                    [&](int j) -> T { return __ldcg(r + j) - ta2 * __ldcg(vnew + j); },
+                    [&](int i) { s[i] = r[i] - ta2 * vnew[i]; },
+                    sh, lg, lead, g0, ngroups, gtid, gthreads))
+                return;
+            // t = A s^; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
+            T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
+            for (int i = g0; i < n; i += ngroups) {
+                const int pc = W.pcnt[i];
+                if (pc < 0) continue;
+                T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) { return __ldcg(sh + j); });
+                acc = group_sum<G>(acc);
+                if (lead) {
+                    const T si = s[i], hi = rh[i];
+                    acc += (T)W.diag[i] * sh[i];
+                    t[i] = acc;
+                    pb0 += acc * si;
+                    pb1 += acc * acc;
+                    pb2 += si * si;
+                    pb3 += hi * si;
+                    pb4 += hi * acc;
+                }
+            }
+            {
+                double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
+                block_partials<5>(pd, W.partial);
+            }
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            double tq[5];
+            grid_totals<5>(W.partial, nb, tq);
+            T *tp = pold; pold = pnew; pnew = tp;
+            tp = vold; vold = vnew; vnew = tp;
+            have_pend = true;
+            pend_a = alpha;
+            if (sqrt(tq[2]) <= tol_in * fn) {
+                pend_w = 0.0;
+                break;
+            }
+            if (tq[1] == 0.0) {
+                pend_w = 0.0;
+                fail = true;
+                break;
+            }
+            omega = tq[0] / tq[1];
+            pend_w = omega;
+            rho_old = rho;
+            rho = tq[3] - omega * tq[4];
+            const double rr = tq[2] - 2.0 * omega * tq[0] + omega * omega * tq[1];
+            if (sqrt(fmax(rr, 0.0)) <= tol_in * fn || rho == 0.0) break;
+        }
+        const T fa = (T)pend_a, fw = (T)pend_w;
+        for (int i = g0; i < n; i += ngroups) {
+            if (!lead || W.pcnt[i] < 0) continue;
+            T d = dl[i];
+            if (have_pend) d += fa * ph[i] + fw * sh[i];
+            x[i] += (double)d;
+        }
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (fail) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (fail) set_error(W.status, VCT_ERR_NOCONV, -1);
+        iters_out[0] += total_it;
+        if (total_it > iters_out[1]) iters_out[1] = total_it;
+        iters_out[2] = total_it;
+        *resid_out = bn > 0.0 ? rn / bn : 0.0;
+    }
+}
+
+static const void *krylov_mg_fn(int precision, int dim)
+{
+    if (precision == VCT_MIXED)
+        return dim == 2 ? (const void *)k_krylov_mg<float, float, 4, 5, 2>
+                        : (const void *)k_krylov_mg<float, float, 8, 7, 3>;
+    return dim == 2 ? (const void *)k_krylov_mg<double, double, 4, 5, 2>
+                    : (const void *)k_krylov_mg<double, double, 8, 7, 3>;
+}
+
+int krylov_mg_coop_blocks(int precision, int dim)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, krylov_mg_fn(precision, dim), KT, 0);
+    if (per > 4) per = 4;
+    int nb = sms * per;
+    return nb < PSTRIDE ? nb : PSTRIDE;
+}
+
+int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
+                     cudaStream_t st)
+{
+    int nn = (int)n, maxit = P.max_iter;
+    double rtol = P.rtol, floor_ = P.precision == VCT_MIXED ? 1e-4 : 0.0;
+    int32_t *it_out = W.kiters;
+    double *res_out = W.kresid;
+    const int G = P.dim == 2 ? 4 : 8;
+    int64_t want = (n * G + KT - 1) / KT;
+    int nblk = (int)(want < nblocks_coop ? want : nblocks_coop);
+    if (nblk < 1) nblk = 1;
+    MG Mc = M;
+    void *args[] = {(void *)&W, (void *)&Mc, (void *)&nn, (void *)&maxit, (void *)&rtol,
+                    (void *)&floor_, (void *)&it_out, (void *)&res_out};
+    cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);
+    cudaError_t e = cudaLaunchCooperativeKernel(krylov_mg_fn(P.precision, P.dim), dim3(nblk),
                                                 dim3(KT), args, 0, st);
     return e == cudaSuccess ? 0 : (int)e;
 }

@@ -42,7 +42,7 @@ class vct_params(C.Structure):
                                   "krylov_rtol")] + [
         ("krylov_max_iter", C.c_int32), ("smagorinsky", C.c_int32), ("precision", C.c_int32),
         ("volume_mode", C.c_int32), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
-        ("max_neighbours", C.c_int32), ("reserved1", C.c_int32)]
+        ("max_neighbours", C.c_int32), ("preconditioner", C.c_int32)]
 
 
 class vct_state(C.Structure):
@@ -152,6 +152,7 @@ def make_params(sc, **over):
         P.box_lo[k] = float(sc.box_lo[k])
         P.box_hi[k] = float(sc.box_hi[k])
     P.max_neighbours = int(p.get("max_neighbours", 0))
+    P.preconditioner = int(p.get("preconditioner", 1))
     return P
 
 
