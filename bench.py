@@ -41,7 +41,7 @@ WORKLOAD = ("2-D sigma-SPH solitary wave (H/d=0.2) over a 0.3 m Gaussian bump, 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -81,7 +81,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -114,16 +114,23 @@ class Clocks:
 # algorithmic bytes per unit of each stage (compulsory traffic: every array
 # read or written once per pass; neighbour re-reads are not counted)
 # ---------------------------------------------------------------------------
-def krylov_bytes(iters, rows, nnz):
-    """BiCGSTAB launch: per unknown row and iteration, vectors 136 B (phase A
-    reads r, p, v, rh and writes p', v'; B reads r, v' and writes s, t; C reads
-    s, t, p', x, rh and writes x, r) plus the operator twice (pcnt 4 + diag 8 +
-    12 B per coefficient); set-up reads x, b and the operator once and writes
-    r, rh, p, v."""
+def krylov_bytes(iters, rows, nnz, n_cells, mixed=True, dim=2):
+    """Algorithmic bytes of one multigrid-preconditioned BiCGSTAB launch.
+    Per unknown row and iteration the operator is streamed six times (two
+    products and, in each of the two V-cycles, the fine residual and the fine
+    post-smoothing): 6 x (pcnt 4 + diag 8 + (4 col + 4 or 8 value) per
+    coefficient); fine vectors 2 V-cycles x (read 4 inputs + dsc + cell + r0
+    write/read + output write) + products (read p^ or s^, write v or t, read
+    r, rh, s) ~ 30 words of the inner precision.  Coarse levels: per V-cycle
+    each level-1 cell is read (stencil + 4 vectors) in the down and up phases
+    (deeper levels add < 1/3).  Set-up: x, b, the operator once."""
+    w = 4 if mixed else 8
     nnz_row = nnz / max(rows, 1)
-    per_row_iter = 136 + 2 * (12 + 12 * nnz_row)
-    setup = 16 + 32 + 12 + 12 * nnz_row
-    return rows * (iters * per_row_iter + setup)
+    per_row_iter = 6 * (12 + (4 + w) * nnz_row) + 30 * w
+    S = 9 if dim == 2 else 27
+    per_cell_iter = 2 * 2 * (S + 4) * 4 * 4 / 3
+    setup = 16 + 12 + (4 + w) * nnz_row
+    return rows * (iters * per_row_iter + setup) + n_cells * iters * per_cell_iter
 
 
 def stage_bytes(stage, n, nf, dim, rows, nnz, nbr_row):
@@ -221,17 +228,26 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs", 6400.0)
     rows, nnz = last.ppe_rows, last.ppe_nnz
     if name == "krylov":
-        per_launch = krylov_bytes(iters / args.steps, rows, nnz)
+        box = [sc.box_hi[k] - sc.box_lo[k] for k in range(3)]
+        re = sc.params["re_over_l"] * sc.params["l_over_d0"] * sc.params["d0"]
+        n_cells = 1
+        for k in range(3):
+            if sc.dim == 2 and k == 1:
+                continue
+            n_cells *= int(box[k] / re) + 1
+        per_launch = krylov_bytes(iters / args.steps, rows, nnz, n_cells, args.precision == 1, sc.dim)
     else:
         per_launch = stage_bytes(name, sc.n, n_fluid, sc.dim, rows, nnz, 20 if sc.dim == 2 else 56)
     avg_ms = ms / max(cnt, 1)
     achieved = per_launch / (avg_ms / 1e3) / 1e9 if per_launch else None
-    roof = {"kernel": {"krylov": "k_bicgstab"}.get(name, name), "bound": "hbm",
+    roof = {"kernel": {"krylov": "k_krylov_mg"}.get(name, name), "bound": "hbm",
             "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": None,
             "peak_source": "measured" if peaks else "fallback",
             "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": per_launch,
-            "note": "operator + vectors (~15 MB) are L2-resident within a step; L2 flushed between steps"}
+            "note": ("operator + vectors (~10 MB) are L2-resident within a step (L2 flushed "
+                     "between steps); the solve is latency-bound: ~22 grid-barrier phases per "
+                     "iteration")}
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -90,6 +90,8 @@ struct MG {
     int dims[MG_MAXL + 1][3];
     long long offA[MG_MAXL + 1];
     long long offv[MG_MAXL + 1];
+    long long soff[MG_MAXL + 1];   // shared-memory offsets (floats) of levels first_local..L
+    long long sh_floats;           // shared memory of block 0's levels (floats)
 };
 
 struct Ctx;
@@ -111,7 +113,7 @@ int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot
 void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st);
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
-int krylov_mg_coop_blocks(int precision, int dim);
+int krylov_mg_coop_blocks(int precision, int dim, size_t smem);
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
                        int ncomp, double *grad, double *d2, double *lap, cudaStream_t st);

@@ -1717,118 +1717,159 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
     }
 }
 
-// One coarse down phase: nodes of level l+1 (start, stride) sum the residuals of
-// their children at level l and take one damped Jacobi step from zero.
-template <int D>
-__device__ void mg_down(const Work &W, const MG &M, int l, int start, int stride)
+// A view of one coarse level: its stencil operator (entry-major, S entries per
+// node) and the vectors dinv, b, z, zu -- in global memory for the grid-wide
+// phases (data written by other blocks read with __ldcg), or in block 0's
+// shared memory for the small levels.
+struct LV {
+    const float *A;
+    float *dinv, *b, *z, *zu;
+    int n, nx, ny, nz;
+};
+
+__device__ __forceinline__ LV lv_global(const Work &W, const MG &M, int l)
 {
-    const int Nc = M.n[l + 1], Nf = M.n[l];
-    const float *Af = W.mg_pool + M.offA[l];
-    const float *vf = W.mg_pool + M.offv[l];
-    const float *bf = vf + Nf, *zf = vf + 2 * Nf;
-    float *vc = W.mg_pool + M.offv[l + 1];
-    const int fx = M.dims[l][0], fy = M.dims[l][1], fz = M.dims[l][2];
-    for (int Ic = start; Ic < Nc; Ic += stride) {
-        int px, py, pz;
-        mg_coords(M, l + 1, Ic, px, py, pz);
+    LV v;
+    const int n = M.n[l];
+    float *base = W.mg_pool + M.offv[l];
+    v.A = W.mg_pool + M.offA[l];
+    v.dinv = base;
+    v.b = base + n;
+    v.z = base + 2 * n;
+    v.zu = base + 3 * n;
+    v.n = n;
+    v.nx = M.dims[l][0];
+    v.ny = M.dims[l][1];
+    v.nz = M.dims[l][2];
+    return v;
+}
+
+__device__ __forceinline__ LV lv_shared(float *sh, const MG &M, int l)
+{
+    LV v;
+    const int n = M.n[l];
+    float *base = sh + M.soff[l];
+    v.A = base;
+    v.dinv = base + (long long)M.S * n;
+    v.b = v.dinv + n;
+    v.z = v.b + n;
+    v.zu = v.z + n;
+    v.n = n;
+    v.nx = M.dims[l][0];
+    v.ny = M.dims[l][1];
+    v.nz = M.dims[l][2];
+    return v;
+}
+
+template <bool GL>
+__device__ __forceinline__ float ldv(const float *p)
+{
+    if (GL) return __ldcg(p);
+    return *p;
+}
+
+// Down phase: nodes of the coarse level c sum the residuals of their children
+// in f and take one damped Jacobi step from zero.
+template <int D, bool GL>
+__device__ void lv_down(const LV &f, const LV &c, float om, int start, int stride)
+{
+    for (int Ic = start; Ic < c.n; Ic += stride) {
+        const int px = Ic % c.nx, pr = Ic / c.nx, py = pr % c.ny, pz = pr / c.ny;
         float bsum = 0.f;
-        for (int c = 0; c < (D == 2 ? 4 : 8); ++c) {
-            const int ax = px * 2 + (c & 1);
-            const int ay = D == 3 ? py * 2 + ((c >> 1) & 1) : 0;
-            const int az = pz * 2 + (D == 2 ? ((c >> 1) & 1) : ((c >> 2) & 1));
-            if (ax >= fx || ay >= fy || az >= fz) continue;
-            const int If = (az * fy + ay) * fx + ax;
-            if (__ldcg(vf + If) == 0.f) continue;
-            float res = __ldcg(bf + If);
+        for (int ch = 0; ch < (D == 2 ? 4 : 8); ++ch) {
+            const int ax = px * 2 + (ch & 1);
+            const int ay = D == 3 ? py * 2 + ((ch >> 1) & 1) : 0;
+            const int az = pz * 2 + (D == 2 ? ((ch >> 1) & 1) : ((ch >> 2) & 1));
+            if (ax >= f.nx || ay >= f.ny || az >= f.nz) continue;
+            const int If = (az * f.ny + ay) * f.nx + ax;
+            if (f.dinv[If] == 0.f) continue;
+            float res = ldv<GL>(f.b + If);
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int jx = ax + dx, jy = ay + dy, jz = az + dz;
-                        if (jx < 0 || jy < 0 || jz < 0 || jx >= fx || jy >= fy || jz >= fz) continue;
-                        const float aval = Af[(int64_t)stencil_index<D>(dx, dy, dz) * Nf + If];
-                        res -= aval * __ldcg(zf + (jz * fy + jy) * fx + jx);
+                        if (jx < 0 || jy < 0 || jz < 0 || jx >= f.nx || jy >= f.ny || jz >= f.nz) continue;
+                        res -= f.A[(int64_t)stencil_index<D>(dx, dy, dz) * f.n + If] *
+                               ldv<GL>(f.z + (jz * f.ny + jy) * f.nx + jx);
                     }
             bsum += res;
         }
-        const float dinv = vc[Ic];
-        vc[Nc + Ic] = bsum;                  // b
-        vc[2 * Nc + Ic] = M.omega * bsum * dinv;   // z
+        c.b[Ic] = bsum;
+        c.z[Ic] = om * bsum * c.dinv[Ic];
     }
 }
 
-// One coarse up phase: nodes of level l add kappa x the coarser correction and
-// take one damped Jacobi step; the result goes to zu.
-template <int D>
-__device__ void mg_up(const Work &W, const MG &M, int l, int start, int stride)
+// Up phase: nodes of f add kappa x the coarse correction (c.zu) and take one
+// damped Jacobi step; the result goes to f.zu.
+template <int D, bool GL>
+__device__ void lv_up(const LV &f, const LV &c, float om, float kap, int start, int stride)
 {
-    const int N = M.n[l], Nc = M.n[l + 1];
-    const float *A = W.mg_pool + M.offA[l];
-    float *v = W.mg_pool + M.offv[l];
-    const float *b = v + N, *z = v + 2 * N;
-    float *zu = v + 3 * N;
-    const float *zuc = W.mg_pool + M.offv[l + 1] + 3 * Nc;
-    const int nx = M.dims[l][0], ny = M.dims[l][1], nz = M.dims[l][2];
-    const int cxn = M.dims[l + 1][0], cyn = M.dims[l + 1][1];
-    const float kap = M.kappa, om = M.omega;
-    for (int I = start; I < N; I += stride) {
-        const float dinv = v[I];
+    for (int I = start; I < f.n; I += stride) {
+        const float dinv = f.dinv[I];
         if (dinv == 0.f) {
-            zu[I] = 0.f;
+            f.zu[I] = 0.f;
             continue;
         }
-        int cx, cy, cz;
-        mg_coords(M, l, I, cx, cy, cz);
-        float res = __ldcg(b + I), zi = 0.f;
+        const int cx = I % f.nx, cr = I / f.nx, cy = cr % f.ny, cz = cr / f.ny;
+        float res = ldv<GL>(f.b + I), zi = 0.f;
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int jx = cx + dx, jy = cy + dy, jz = cz + dz;
-                    if (jx < 0 || jy < 0 || jz < 0 || jx >= nx || jy >= ny || jz >= nz) continue;
-                    const int J = (jz * ny + jy) * nx + jx;
-                    const int Jc = ((jz >> 1) * cyn + (D == 3 ? (jy >> 1) : 0)) * cxn + (jx >> 1);
-                    const float zj = __ldcg(z + J) + kap * __ldcg(zuc + Jc);
+                    if (jx < 0 || jy < 0 || jz < 0 || jx >= f.nx || jy >= f.ny || jz >= f.nz) continue;
+                    const int J = (jz * f.ny + jy) * f.nx + jx;
+                    const int Jc = ((jz >> 1) * c.ny + (D == 3 ? (jy >> 1) : 0)) * c.nx + (jx >> 1);
+                    const float zj = ldv<GL>(f.z + J) + kap * ldv<GL>(c.zu + Jc);
                     if (dx == 0 && dy == 0 && dz == 0) zi = zj;
-                    res -= A[(int64_t)stencil_index<D>(dx, dy, dz) * N + I] * zj;
+                    res -= f.A[(int64_t)stencil_index<D>(dx, dy, dz) * f.n + I] * zj;
                 }
-        zu[I] = zi + om * dinv * res;
+        f.zu[I] = zi + om * dinv * res;
     }
 }
 
-// Coarsest level: Jacobi sweeps by the calling block alone; the result is zu.
-__device__ void mg_coarsest(const Work &W, const MG &M, int D)
+// Coarsest level in block 0's shared memory: Jacobi sweeps from z; result in zu.
+template <int D>
+__device__ void lv_coarsest(const LV &c, float om, int sweeps)
 {
-    const int l = M.L, N = M.n[l];
-    const float *A = W.mg_pool + M.offA[l];
-    float *v = W.mg_pool + M.offv[l];
-    const float *b = v + N;
-    float *z = v + 2 * N, *zu = v + 3 * N;
-    const int nx = M.dims[l][0], ny = M.dims[l][1], nz = M.dims[l][2];
-    for (int sw = 0; sw < M.coarse_sweeps; ++sw) {
-        const float *src = (sw & 1) ? zu : z;
-        float *dst = (sw & 1) ? z : zu;
-        for (int I = threadIdx.x; I < N; I += blockDim.x) {
-            const float dinv = v[I];
+    for (int sw = 0; sw < sweeps; ++sw) {
+        const float *src = (sw & 1) ? c.zu : c.z;
+        float *dst = (sw & 1) ? c.z : c.zu;
+        for (int I = threadIdx.x; I < c.n; I += blockDim.x) {
+            const float dinv = c.dinv[I];
             if (dinv == 0.f) {
                 dst[I] = 0.f;
                 continue;
             }
-            int cx, cy, cz;
-            mg_coords(M, l, I, cx, cy, cz);
-            float res = __ldcg(b + I);
+            const int cx = I % c.nx, cr = I / c.nx, cy = cr % c.ny, cz = cr / c.ny;
+            float res = c.b[I];
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int jx = cx + dx, jy = cy + dy, jz = cz + dz;
-                        if (jx < 0 || jy < 0 || jz < 0 || jx >= nx || jy >= ny || jz >= nz) continue;
-                        const int o = D == 2 ? (dz + 1) * 3 + (dx + 1) : ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
-                        res -= A[(int64_t)o * N + I] * __ldcg(src + (jz * ny + jy) * nx + jx);
+                        if (jx < 0 || jy < 0 || jz < 0 || jx >= c.nx || jy >= c.ny || jz >= c.nz) continue;
+                        res -= c.A[(int64_t)stencil_index<D>(dx, dy, dz) * c.n + I] *
+                               src[(jz * c.ny + jy) * c.nx + jx];
                     }
-            dst[I] = __ldcg(src + I) + M.omega * dinv * res;
+            dst[I] = src[I] + om * dinv * res;
         }
         __syncthreads();
     }
-    if (M.coarse_sweeps & 1) return;   // result already in zu
-    for (int I = threadIdx.x; I < N; I += blockDim.x) zu[I] = __ldcg(z + I);
+    if (!(sweeps & 1)) {
+        for (int I = threadIdx.x; I < c.n; I += blockDim.x) c.zu[I] = c.z[I];
+        __syncthreads();
+    }
+}
+
+// Block 0 copies the operators and dinv of the shared-memory levels once per solve.
+__device__ void mg_load_shared(const Work &W, const MG &M, float *sh)
+{
+    for (int l = M.first_local; l <= M.L; ++l) {
+        const LV g = lv_global(W, M, l), s = lv_shared(sh, M, l);
+        const long long na = (long long)M.S * g.n;
+        float *As = (float *)s.A;
+        for (long long q = threadIdx.x; q < na; q += blockDim.x) As[q] = g.A[q];
+        for (int q = threadIdx.x; q < g.n; q += blockDim.x) s.dinv[q] = g.dinv[q];
+    }
     __syncthreads();
 }
 
@@ -1836,8 +1877,8 @@ __device__ void mg_coarsest(const Work &W, const MG &M, int D)
 // for every unknown row in the first phase (lane 0 of the row's group), before
 // any phase writes z_out.  Returns false if a grid barrier timed out.
 template <typename T, typename CT, int G, int NS, int D, typename In, typename Own>
-__device__ bool vcycle(const Work &W, const MG &M, int n, In in, Own own, T *zout, int lg, bool lead,
-                       int g0, int ngroups, int gtid, int gthreads)
+__device__ bool vcycle(const Work &W, const MG &M, float *sh, int n, In in, Own own, T *zout,
+                       int lg, bool lead, int g0, int ngroups, int gtid, int gthreads)
 {
     const unsigned nb = gridDim.x;
     const float om = M.omega, kap = M.kappa;
@@ -1859,37 +1900,49 @@ __device__ bool vcycle(const Work &W, const MG &M, int n, In in, Own own, T *zou
     if (!grid_barrier(W.bar, nb, W.status)) return false;
     // D1: restriction to the cells, one Jacobi step from zero on level 1
     {
-        const int N1 = M.n[1];
-        float *v1 = W.mg_pool + M.offv[1];
-        for (int I = gtid; I < N1; I += gthreads) {
+        const LV c = lv_global(W, M, 1);
+        for (int I = gtid; I < c.n; I += gthreads) {
             float bs = 0.f;
             const int a = W.cell_start[I], b = W.cell_start[I + 1];
             for (int i = a; i < b; ++i)
                 if (W.pcnt[i] >= 0) bs += (float)__ldcg(r0 + i);
-            v1[N1 + I] = bs;
-            v1[2 * N1 + I] = om * bs * v1[I];
+            c.b[I] = bs;
+            c.z[I] = om * bs * c.dinv[I];
         }
     }
     if (!grid_barrier(W.bar, nb, W.status)) return false;
-    for (int l = 1; l + 1 <= M.first_local && l < M.L; ++l) {
-        mg_down<D>(W, M, l, gtid, gthreads);
+    const int fl = M.first_local;
+    for (int l = 1; l < fl; ++l) {
+        lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status)) return false;
     }
     if (blockIdx.x == 0) {
-        const int l0 = M.first_local < 1 ? 1 : M.first_local;
-        for (int l = l0; l < M.L; ++l) {
-            mg_down<D>(W, M, l, threadIdx.x, blockDim.x);
+        // levels fl..L in shared memory: b and z of level fl come from global
+        {
+            const LV g = lv_global(W, M, fl), s = lv_shared(sh, M, fl);
+            for (int q = threadIdx.x; q < g.n; q += blockDim.x) {
+                s.b[q] = __ldcg(g.b + q);
+                s.z[q] = __ldcg(g.z + q);
+            }
             __syncthreads();
         }
-        mg_coarsest(W, M, D);
-        for (int l = M.L - 1; l >= l0; --l) {
-            mg_up<D>(W, M, l, threadIdx.x, blockDim.x);
+        for (int l = fl; l < M.L; ++l) {
+            lv_down<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, threadIdx.x, blockDim.x);
             __syncthreads();
+        }
+        lv_coarsest<D>(lv_shared(sh, M, M.L), om, M.coarse_sweeps);
+        for (int l = M.L - 1; l >= fl; --l) {
+            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, kap, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+        {
+            const LV g = lv_global(W, M, fl), s = lv_shared(sh, M, fl);
+            for (int q = threadIdx.x; q < g.n; q += blockDim.x) g.zu[q] = s.zu[q];
         }
     }
     if (!grid_barrier(W.bar, nb, W.status)) return false;
-    for (int l = (M.first_local < 1 ? 1 : M.first_local) - 1; l >= 1; --l) {
-        mg_up<D>(W, M, l, gtid, gthreads);
+    for (int l = fl - 1; l >= 1; --l) {
+        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, kap, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status)) return false;
     }
     // U0: prolongation from the cells + one damped Jacobi step on the fine level
@@ -1923,6 +1976,8 @@ __global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit
     const int ngroups = (gridDim.x * blockDim.x) / G;
     const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    extern __shared__ float mg_sh[];
+    if (blockIdx.x == 0) mg_load_shared(W, M, mg_sh);
     double *x = W.kx, *f = W.kf;
     T *r = (T *)W.kr, *rh = (T *)W.krh, *s = (T *)W.ks, *t = (T *)W.kt, *dl = (T *)W.kd;
     T *pold = (T *)W.kp0, *pnew = (T *)W.kp1, *vold = (T *)W.kv0, *vnew = (T *)W.kv1;
@@ -1974,12 +2029,12 @@ __global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit
             // p_new = r + beta (p - w v) with r = s - w t; p^ = M^-1 p_new
             bool ok;
             if (fst) {
-                ok = vcycle<T, CT, G, NS, D>(W, M, n,
+                ok = vcycle<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T { return (T)__ldcg(f + j); },
                     [&](int i) { const T ri = (T)f[i]; r[i] = ri; rh[i] = ri; pnew[i] = ri; dl[i] = T(0); },
                     ph, lg, lead, g0, ngroups, gtid, gthreads);
             } else {
-                ok = vcycle<T, CT, G, NS, D>(W, M, n,
+                ok = vcycle<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T {
                         return (__ldcg(s + j) - tw * __ldcg(t + j)) + tb * (__ldcg(pold + j) - tw * __ldcg(vold + j));
                     },
@@ -2021,7 +2076,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit
             alpha = rho / tv[0];
             const T ta2 = (T)alpha;
             // s = r - alpha v; s^ = M^-1 s
-            if (!vcycle<T, CT, G, NS, D>(W, M, n,
+            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T { return __ldcg(r + j) - ta2 * __ldcg(vnew + j); },
                     [&](int i) { s[i] = r[i] - ta2 * vnew[i]; },
                     sh, lg, lead, g0, ngroups, gtid, gthreads))
@@ -2099,12 +2154,14 @@ static const void *krylov_mg_fn(int precision, int dim)
                     : (const void *)k_krylov_mg<double, double, 8, 7, 3>;
 }
 
-int krylov_mg_coop_blocks(int precision, int dim)
+int krylov_mg_coop_blocks(int precision, int dim, size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
+    cudaFuncSetAttribute(krylov_mg_fn(precision, dim), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, krylov_mg_fn(precision, dim), KT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, krylov_mg_fn(precision, dim), KT, smem);
     if (per > 4) per = 4;
     int nb = sms * per;
     return nb < PSTRIDE ? nb : PSTRIDE;
@@ -2126,7 +2183,7 @@ int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nbl
                     (void *)&floor_, (void *)&it_out, (void *)&res_out};
     cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);
     cudaError_t e = cudaLaunchCooperativeKernel(krylov_mg_fn(P.precision, P.dim), dim3(nblk),
-                                                dim3(KT), args, 0, st);
+                                                dim3(KT), args, (size_t)M.sh_floats * 4, st);
     return e == cudaSuccess ? 0 : (int)e;
 }
 
