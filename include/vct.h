@@ -204,6 +204,18 @@ vct_status vct_build_neighbours_noalloc(const vct_bathymetry *bathy, vct_map_kin
 vct_status sph2_derivatives(vct_ctx *ctx, const vct_state *state, const double *phi,
                             int32_t ncomp, double *grad_hat, double *d2_hat, double *lap_phys);
 
+/* Adjoint of sph2_derivatives with respect to the fields (same state, same
+ * layouts): given the adjoints of the outputs grad_hat_bar (ncomp x dim x n),
+ * d2_hat_bar (ncomp x m x n), lap_phys_bar (ncomp x n) -- any may be NULL for
+ * zero -- writes phi_bar (ncomp x n) = J^T (output adjoints), J the Jacobian of
+ * the linear map phi -> (grad_hat, d2_hat, lap_phys) at the current positions.
+ * Transpose of the SPH(2) operator (Eq. sec_SPH2) including the adjoint of the
+ * per-particle solve with M_i^T; computed as a gather over the symmetric
+ * neighbour relation, deterministic.  Virtual particles get 0. */
+vct_status sph2_derivatives_backward(vct_ctx *ctx, const vct_state *state, int32_t ncomp,
+                                     const double *grad_hat_bar, const double *d2_hat_bar,
+                                     const double *lap_phys_bar, double *phi_bar);
+
 /* Advance the state by nsteps steps of Sec. 3.3 with the VCT equations:
  * map + cell sort, neighbours, Jbar smoothing (sigma, volume_mode 2),
  * corrected gradients, free surface, eddy viscosity, SPH(2) predictor,

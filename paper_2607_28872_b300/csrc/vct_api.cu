@@ -353,6 +353,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.bvec = dalloc<double>(c, n, e);
     W.wallrhs = dalloc<double>(c, n, e);
     W.jbar_tmp = dalloc<double>(c, n, e);
+    W.adj = dalloc<double>(c, n * (m + d), e);
     W.kx = dalloc<double>(c, n, e);
     W.kr = dalloc<double>(c, n, e);
     W.krh = dalloc<double>(c, n, e);
@@ -495,6 +496,24 @@ VCT_API vct_status sph2_derivatives(vct_ctx *c, const vct_state *s, const double
     geometry(c, n);
     launch_pass1(c->P, cur(c), c->W, n, c->st);
     launch_sph2_field(c->P, cur(c), c->W, n, phi, ncomp, grad_hat, d2_hat, lap_phys, c->st);
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, nullptr, 0);
+}
+
+VCT_API vct_status sph2_derivatives_backward(vct_ctx *c, const vct_state *s, int32_t ncomp,
+                                             const double *grad_hat_bar, const double *d2_hat_bar,
+                                             const double *lap_phys_bar, double *phi_bar)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (!phi_bar || ncomp <= 0) return VCT_ERR_ARG;
+    const int64_t n = s->n;
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    geometry(c, n);
+    launch_pass1(c->P, cur(c), c->W, n, c->st);
+    launch_sph2_adjoint(c->P, cur(c), c->W, n, ncomp, grad_hat_bar, d2_hat_bar, lap_phys_bar,
+                        phi_bar, c->st);
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
     return finish(c, nullptr, 0);
 }

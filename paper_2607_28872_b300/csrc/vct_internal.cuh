@@ -73,6 +73,7 @@ struct Work {
     float *mg_pool;           // coarse operators and vectors of all levels
     double *kr0;              // fine residual of the V-cycle (FP32 or FP64 slots)
     double *kq0, *kq1;        // preconditioned directions p^, s^
+    double *adj;              // adjoint scratch: [m + dim] per particle
 };
 
 // Coarse levels of the aggregation multigrid: level 1 = the cell grid, level
@@ -119,6 +120,9 @@ void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const do
                        int ncomp, double *grad, double *d2, double *lap, cudaStream_t st);
 void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,
                        int32_t *col, int64_t col_cap, cudaStream_t st);
+void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
+                         const double *gbar, const double *d2bar, const double *lapbar,
+                         double *phibar, cudaStream_t st);
 void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct_probe &pr,
                       cudaStream_t st);
 void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,

@@ -2445,6 +2445,229 @@ void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const do
     }
 }
 
+// ---------------------------------------------------------------------------
+// a12 (operator part): adjoint of sph2_derivatives with respect to the field.
+// For fluid particle i the outputs are linear in phi_ij = phi_j - phi_i:
+//   g_i = L_i sum_j V_j phi_ij grad w_ij,
+//   D_i = 2 M_i^-1 sum_j V_j F_ij q_ij (phi_ij - r_ij . g_i)      (Eq. sec_SPH2)
+//   d2_i = H D_i (cross entries halved),  lap_i = c0 g_i,z + c~ . D_i (Eq. lap_VCT)
+// Given the output adjoints, pass 1 forms per particle
+//   Dbar = H d2bar + c~ lapbar,  bbar = 2 M_i^-T Dbar   (adjoint of the small solve)
+//   gbar' = gbar + c0 lapbar e_z - sum_j V_j F_ij (bbar . q_ij) r_ij,
+// and each pair (i, j) carries w_ij = V_j [F_ij (bbar_i . q_ij) + (L_i grad w_ij) . gbar'_i];
+// pass 2 gathers phibar_j = sum_{i : j in S_i} w_ij - sum_{k in S_j} w_jk over the
+// symmetric neighbour relation (the transpose scatter written as a gather).
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_sph2_adj1(DevParams P, const Part c, Work W, int n,
+                                                   const double *gbar, const double *d2bar,
+                                                   const double *lapbar, int comp)
+{
+    constexpr int M = D == 2 ? 3 : 6;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    if (c.type[i] != FLUID) {
+        for (int a = 0; a < M + D; ++a) W.adj[(int64_t)a * cap + i] = 0.0;
+        return;
+    }
+    const int o = c.orig[i];
+    double xi[3];
+    load_hat<D>(c, i, xi);
+    R L[D * D], Ct[D * M];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) L[k] = (R)W.L[(int64_t)k * cap + i];
+#pragma unroll
+    for (int k = 0; k < D * M; ++k) Ct[k] = (R)W.Ct[(int64_t)k * cap + i];
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    Acc<R> Mm[M * M];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R gw[D], fac = -dw / rr, rg = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) gw[K] = fac * r[K];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R s = R(0);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * gw[L2];
+            rg += r[K] * s;
+        }
+        R VF = (R)vol_of(P, c, j) * rg / (rr2 * rr2), q[M], pv[M];
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            R s = R(0);
+#pragma unroll
+            for (int K = 0; K < D; ++K) s += Ct[K * M + a] * r[K];
+            pv[a] = q[a] - s;
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) Mm[a * M + b].add(VF * q[a] * pv[b]);
+    }
+    double ct[M];
+    ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
+    const double lb = lapbar ? lapbar[(int64_t)comp * n + o] : 0.0;
+    double Dbar[M], gb[D];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        const double d2b = d2bar ? d2bar[((int64_t)comp * M + a) * n + o] : 0.0;
+        Dbar[a] = (a < D ? d2b : 0.5 * d2b) + ct[a] * lb;
+    }
+#pragma unroll
+    for (int K = 0; K < D; ++K) gb[K] = gbar ? gbar[((int64_t)comp * D + K) * n + o] : 0.0;
+    gb[D - 1] += c.c0[i] * lb;
+    // bbar = 2 M^-T Dbar
+    double A[M * M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) A[a * M + b] = (double)Mm[b * M + a].val();
+    if (!lu_solve<M, 1>(A, Dbar)) set_error(W.status, VCT_ERR_SINGULAR, i);
+    R bb[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) bb[a] = (R)(2.0 * Dbar[a]);
+    // gbar' = gbar - sum_j V F (bbar . q) r
+    Acc<R> u[D];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R fac = -dw / rr, rg = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R s = R(0);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * fac * r[L2];
+            rg += r[K] * s;
+        }
+        R VF = (R)vol_of(P, c, j) * rg / (rr2 * rr2), q[M], bq = R(0);
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int a = 0; a < M; ++a) bq += bb[a] * q[a];
+#pragma unroll
+        for (int K = 0; K < D; ++K) u[K].add(VF * bq * r[K]);
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) W.adj[(int64_t)a * cap + i] = (double)bb[a];
+#pragma unroll
+    for (int K = 0; K < D; ++K) W.adj[(int64_t)(M + K) * cap + i] = gb[K] - (double)u[K].val();
+}
+
+// Pair weight w_ij seen from particle i (the owner of the outputs) for neighbour j.
+template <int D, typename R>
+__device__ __forceinline__ R adj_pair(const DevParams &P, const Part &c, const Work &W, int i, int j,
+                                      const double *xi, const double *xj)
+{
+    constexpr int M = D == 2 ? 3 : 6;
+    const int64_t cap = W.cap;
+    R r[D], rr2 = R(0);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        r[K] = (R)(xj[K] - xi[K]);
+        rr2 += r[K] * r[K];
+    }
+    if (rr2 == R(0)) return R(0);
+    R rr = sqrt(rr2), w, dw;
+    kern_wdw<R>(rr, (R)P.inv_l, (R)P.ad, w, dw);
+    R fac = -dw / rr, gt[D], rg = R(0);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        R s = R(0);
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) s += (R)W.L[(int64_t)(K * D + L2) * cap + i] * fac * r[L2];
+        gt[K] = s;
+        rg += r[K] * s;
+    }
+    R F = rg / (rr2 * rr2), q[M], bq = R(0), gg = R(0);
+    qvec<D, R>(r, q);
+#pragma unroll
+    for (int a = 0; a < M; ++a) bq += (R)W.adj[(int64_t)a * cap + i] * q[a];
+#pragma unroll
+    for (int K = 0; K < D; ++K) gg += gt[K] * (R)W.adj[(int64_t)(M + K) * cap + i];
+    return (R)vol_of(P, c, j) * (F * bq + gg);
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_sph2_adj2(DevParams P, const Part c, Work W, int n,
+                                                   double *phibar, int comp)
+{
+    int jdx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jdx >= n) return;
+    const int o = c.orig[jdx];
+    const int tj = c.type[jdx];
+    if (tj == VIRTUAL) {
+        phibar[(int64_t)comp * n + o] = 0.0;
+        return;
+    }
+    const int64_t cap = W.cap;
+    double xj[3];
+    load_hat<D>(c, jdx, xj);
+    Acc<R> acc;
+    const int cnt = W.nbr_cnt[jdx];
+    for (int k = 0; k < cnt; ++k) {
+        const int i = W.nbr[(int64_t)k * cap + jdx];
+        const int ti = c.type[i];
+        if (ti == VIRTUAL) continue;
+        double xi[3];
+        load_hat<D>(c, i, xi);
+        if (ti == FLUID) acc.add(adj_pair<D, R>(P, c, W, i, jdx, xi, xj));        // incoming w_ij
+        if (tj == FLUID) acc.add(-adj_pair<D, R>(P, c, W, jdx, i, xj, xi));       // outgoing w_ji
+    }
+    phibar[(int64_t)comp * n + o] = (double)acc.val();
+}
+
+void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
+                         const double *gbar, const double *d2bar, const double *lapbar,
+                         double *phibar, cudaStream_t st)
+{
+    unsigned g = (unsigned)((n + 127) / 128);
+    for (int comp = 0; comp < ncomp; ++comp) {
+        if (P.dim == 2) {
+            if (P.precision == VCT_MIXED) {
+                k_sph2_adj1<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, gbar, d2bar, lapbar, comp);
+                k_sph2_adj2<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, phibar, comp);
+            } else {
+                k_sph2_adj1<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, gbar, d2bar, lapbar, comp);
+                k_sph2_adj2<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, phibar, comp);
+            }
+        } else {
+            if (P.precision == VCT_MIXED) {
+                k_sph2_adj1<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, gbar, d2bar, lapbar, comp);
+                k_sph2_adj2<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, phibar, comp);
+            } else {
+                k_sph2_adj1<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, gbar, d2bar, lapbar, comp);
+                k_sph2_adj2<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, phibar, comp);
+            }
+        }
+    }
+}
+
 void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,
                        int32_t *col, int64_t col_cap, cudaStream_t st)
 {

@@ -20,7 +20,7 @@ MAP = {"E": 0, "BF": 1, "BFE": 2, "SIGMA": 3}
 VCT_MAX_GAUSS = 32
 
 EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
-           "sph2_derivatives", "vct_step",
+           "sph2_derivatives", "sph2_derivatives_backward", "vct_step",
            "vct_step_host", "vct_step_probe", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
 
@@ -89,6 +89,7 @@ def load_library(path=LIB_PATH):
                                                vp, C.c_int64, C.POINTER(C.c_int64), vp]
     L.vct_build_neighbours_noalloc.restype = C.c_int
     L.sph2_derivatives.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp, vp]
+    L.sph2_derivatives_backward.argtypes = [vp, C.POINTER(vct_state), C.c_int32, vp, vp, vp, vp]
     L.vct_step.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_host.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_probe.argtypes = [vp, C.POINTER(vct_state), C.POINTER(vct_probe),
@@ -101,6 +102,7 @@ def load_library(path=LIB_PATH):
     L.vct_destroy.argtypes = [vp]
     L.vct_destroy.restype = None
     for name in ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives",
+                 "sph2_derivatives_backward",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
@@ -264,6 +266,20 @@ class Solver:
                                               _ptr(d2), _ptr(lap)), "sph2_derivatives")
         return g, d2, lap
 
+    def sph2_derivatives_backward(self, state, grad_bar=None, d2_bar=None, lap_bar=None):
+        """Adjoint of sph2_derivatives w.r.t. phi: returns phi_bar (ncomp, n)."""
+        import torch
+        ref = next(t for t in (grad_bar, d2_bar, lap_bar) if t is not None)
+        nc = ref.shape[0]
+        phib = torch.zeros((nc, state.n), dtype=torch.float64, device="cuda")
+        c = lambda t: None if t is None else t.contiguous()
+        grad_bar, d2_bar, lap_bar = c(grad_bar), c(d2_bar), c(lap_bar)
+        s = state.struct()
+        self._check(self.lib.sph2_derivatives_backward(self.ctx, C.byref(s), nc, _ptr(grad_bar),
+                                                       _ptr(d2_bar), _ptr(lap_bar), _ptr(phib)),
+                    "sph2_derivatives_backward")
+        return phib
+
     def vct_step(self, state, nsteps=1):
         s = state.struct()
         st = vct_stats()
@@ -328,3 +344,24 @@ def vct_build_neighbours_noalloc(sc, state, row_ptr, col, stream=None):
                                           0 if col is None else col.numel(), C.byref(nnz),
                                           C.c_void_p(stream.cuda_stream))
     return rc, nnz.value
+
+
+def sph2_function():
+    """torch.autograd.Function over sph2_derivatives: forward and backward both
+    run in the CUDA library (backward = sph2_derivatives_backward)."""
+    import torch
+
+    class SPH2Derivatives(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi, solver, state):
+            g, d2, lap = solver.sph2_derivatives(state, phi.detach())
+            ctx.solver = solver
+            ctx.state = state
+            return g, d2, lap
+
+        @staticmethod
+        def backward(ctx, gbar, d2bar, lapbar):
+            phib = ctx.solver.sph2_derivatives_backward(ctx.state, gbar, d2bar, lapbar)
+            return phib, None, None
+
+    return SPH2Derivatives
