@@ -216,6 +216,20 @@ vct_status sph2_derivatives_backward(vct_ctx *ctx, const vct_state *state, int32
                                      const double *grad_hat_bar, const double *d2_hat_bar,
                                      const double *lap_phys_bar, double *phi_bar);
 
+/* Derivative through the map with respect to the bathymetry parameters
+ * theta = [h0, slope_x, slope_y, cos_amp, cos_len, amp[G], cx[G], cy[G], width[G]]
+ * (G = n_gauss; 5 + 4G entries): given per-particle adjoints (DEVICE arrays of n,
+ * caller order, any may be NULL for zero) of the projected height z^ =
+ * alpha (z + beta), J = alpha, the Jacobian column s_x, s_y and the c_trans
+ * entries c0 and c3 (Sec. 2, Eqs. VCT, jacobi, lap_VCT), writes theta_bar (HOST,
+ * 5 + 4G doubles) = sum_i sum_q mbar_q,i dm_q,i / dtheta at the state's
+ * physical positions.  Exact derivatives (forward-mode dual arithmetic, one
+ * parameter per pass), summed over particles in a fixed order.  The sigma
+ * clamp is respected: where alpha is clamped its derivatives are zero. */
+vct_status vct_map_backward(vct_ctx *ctx, const vct_state *state, const double *zh_bar,
+                            const double *J_bar, const double *sx_bar, const double *sy_bar,
+                            const double *c0_bar, const double *c3_bar, double *theta_bar);
+
 /* Advance the state by nsteps steps of Sec. 3.3 with the VCT equations:
  * map + cell sort, neighbours, Jbar smoothing (sigma, volume_mode 2),
  * corrected gradients, free surface, eddy viscosity, SPH(2) predictor,

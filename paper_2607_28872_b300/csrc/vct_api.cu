@@ -28,6 +28,7 @@ struct vct_ctx {
     // device mirror of a caller state for vct_step_host
     vct_state mirror;
     int64_t *row_int;          // CSR rows when the caller passes none
+    double *theta_out;         // bathymetry-parameter adjoint (5 + 4 VCT_MAX_GAUSS)
     int32_t *host_status;      // pinned copy of status + stats
     int64_t last_particle;
     std::vector<void *> allocs;
@@ -434,6 +435,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.status = dalloc<int32_t>(c, 4, e);
     W.counts = dalloc<long long>(c, 2, e);
     c->row_int = dalloc<int64_t>(c, n + 1, e);
+    c->theta_out = dalloc<double>(c, 5 + 4 * VCT_MAX_GAUSS, e);
     c->mirror.x = dalloc<double>(c, n, e);
     c->mirror.y = dalloc<double>(c, n, e);
     c->mirror.z = dalloc<double>(c, n, e);
@@ -516,6 +518,29 @@ VCT_API vct_status sph2_derivatives_backward(vct_ctx *c, const vct_state *s, int
                         phi_bar, c->st);
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
     return finish(c, nullptr, 0);
+}
+
+VCT_API vct_status vct_map_backward(vct_ctx *c, const vct_state *s, const double *zh_bar,
+                                    const double *J_bar, const double *sx_bar,
+                                    const double *sy_bar, const double *c0_bar,
+                                    const double *c3_bar, double *theta_bar)
+{
+    if (!c || !s || !theta_bar) return VCT_ERR_ARG;
+    if (s->n <= 0 || s->n > c->cap) return s->n > c->cap ? VCT_ERR_CAPACITY : VCT_ERR_ARG;
+    if (!s->x || !s->z || (c->P.dim == 3 && !s->y)) return VCT_ERR_ARG;
+    const int nparam = 5 + 4 * c->P.n_gauss;
+    // device table of the six adjoint pointers lives in the context's scratch
+    const double *tab[6] = {zh_bar, J_bar, sx_bar, sy_bar, c0_bar, c3_bar};
+    cudaError_t e = cudaMemcpyAsync(c->W.scal, tab, sizeof tab, cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
+    double *out = c->theta_out;   // 5 + 4 * VCT_MAX_GAUSS doubles
+    if (launch_map_adjoint(c->P, *s, s->n, (const double *const *)c->W.scal, c->W.adj,
+                           c->cap * (c->P.dim == 2 ? 5 : 9), out, c->st))
+        return VCT_ERR_CAPACITY;
+    e = cudaMemcpyAsync(theta_bar, out, sizeof(double) * nparam, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return VCT_OK;
 }
 
 VCT_API vct_status vct_step(vct_ctx *c, vct_state *s, int32_t nsteps, vct_stats *out)

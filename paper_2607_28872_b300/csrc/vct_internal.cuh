@@ -120,6 +120,8 @@ void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const do
                        int ncomp, double *grad, double *d2, double *lap, cudaStream_t st);
 void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,
                        int32_t *col, int64_t col_cap, cudaStream_t st);
+int launch_map_adjoint(const DevParams &P, vct_state s, int64_t n, const double *const *mbar_dev,
+                       double *partial, int64_t partial_cap, double *out, cudaStream_t st);
 void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
                          const double *gbar, const double *d2bar, const double *lapbar,
                          double *phibar, cudaStream_t st);

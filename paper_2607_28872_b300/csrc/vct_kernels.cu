@@ -2668,6 +2668,176 @@ void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int nc
     }
 }
 
+// ---------------------------------------------------------------------------
+// a12 (map part): derivative of the per-particle metric with respect to the
+// bathymetry parameters theta = [h0, slope_x, slope_y, cos_amp, cos_len,
+// amp_g, cx_g, cy_g, width_g (g < n_gauss)].  Exact forward-mode derivatives
+// with dual numbers, one parameter seeded per pass, contracted with the
+// caller's adjoints of (z^, J, s_x, s_y, c0, c3) and summed over particles
+// (per-block partials, then a fixed-order sum).
+// ---------------------------------------------------------------------------
+struct Dual {
+    double v, d;
+    __device__ Dual() : v(0.0), d(0.0) {}
+    __device__ Dual(double a, double b = 0.0) : v(a), d(b) {}
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b)
+{
+    return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+__device__ __forceinline__ Dual dexp(Dual a) { double e = exp(a.v); return Dual(e, e * a.d); }
+__device__ __forceinline__ Dual dsin(Dual a) { return Dual(sin(a.v), cos(a.v) * a.d); }
+__device__ __forceinline__ Dual dcos(Dual a) { return Dual(cos(a.v), -sin(a.v) * a.d); }
+
+// parameter k of theta as a dual (derivative 1 if k == seed)
+__device__ __forceinline__ Dual theta(const DevParams &P, int k, int seed)
+{
+    const int G = P.n_gauss;
+    double v;
+    if (k == 0) v = P.h0;
+    else if (k == 1) v = P.slope_x;
+    else if (k == 2) v = P.slope_y;
+    else if (k == 3) v = P.cos_amp;
+    else if (k == 4) v = P.cos_len;
+    else {
+        int q = k - 5, g = q % G, w = q / G;
+        v = w == 0 ? P.gamp[g] : w == 1 ? P.gcx[g] : w == 2 ? P.gcy[g] : P.gwid[g];
+    }
+    return Dual(v, k == seed ? 1.0 : 0.0);
+}
+
+__device__ void bathy_dual(const DevParams &P, double x, double y, int seed, Dual h[5])
+{
+    Dual X(x), Y(y);
+    Dual sx = theta(P, 1, seed), sy = theta(P, 2, seed);
+    h[0] = theta(P, 0, seed) + sx * X + sy * Y;
+    h[1] = sx;
+    h[2] = sy;
+    h[3] = Dual(0.0);
+    h[4] = Dual(0.0);
+    Dual ca = theta(P, 3, seed);
+    if (P.cos_amp != 0.0 || seed == 3) {
+        Dual k = Dual(2.0 * 3.14159265358979323846) / theta(P, 4, seed);
+        Dual kx = k * X, s = dsin(kx), c = dcos(kx);
+        h[0] = h[0] + ca * c;
+        h[1] = h[1] - ca * k * s;
+        h[3] = h[3] - ca * k * k * c;
+    }
+    for (int g = 0; g < P.n_gauss; ++g) {
+        Dual A = theta(P, 5 + g, seed), cx = theta(P, 5 + P.n_gauss + g, seed);
+        Dual cy = theta(P, 5 + 2 * P.n_gauss + g, seed), wd = theta(P, 5 + 3 * P.n_gauss + g, seed);
+        Dual dx = X - cx, dy = Y - cy, is2 = Dual(1.0) / (wd * wd);
+        Dual e = A * dexp(Dual(-0.5) * (dx * dx + dy * dy) * is2);
+        h[0] = h[0] + e;
+        h[1] = h[1] - e * dx * is2;
+        h[2] = h[2] - e * dy * is2;
+        h[3] = h[3] + e * (dx * dx * is2 - Dual(1.0)) * is2;
+        h[4] = h[4] + e * (dy * dy * is2 - Dual(1.0)) * is2;
+    }
+}
+
+// Same metric as map_metric, in dual arithmetic: out = {z^, J, s_x, s_y, c0, c3}.
+__device__ void metric_dual(const DevParams &P, double x, double y, double z, int seed, Dual out[6])
+{
+    Dual a(1.0), ax, ay, axx, ayy, b, bx, by, bxx, byy;
+    if (P.kind == VCT_MAP_E) {
+        a = Dual(P.aspect);
+    } else {
+        Dual h[5];
+        bathy_dual(P, x, y, seed, h);
+        b = -h[0]; bx = -h[1]; by = -h[2]; bxx = -h[3]; byy = -h[4];
+        if (P.kind == VCT_MAP_BFE) {
+            a = Dual(P.aspect);
+        } else if (P.kind == VCT_MAP_SIGMA) {
+            Dual D = Dual(P.H) - h[0];
+            if (D.v <= 0.0) {
+                a = Dual(P.amax);
+            } else {
+                double ai = P.H_hat / D.v;
+                if (ai < P.amin) a = Dual(P.amin);
+                else if (ai > P.amax) a = Dual(P.amax);
+                else {
+                    Dual Hh(P.H_hat), iD = Dual(1.0) / D;
+                    a = Hh * iD;
+                    ax = Hh * h[1] * iD * iD;
+                    ay = Hh * h[2] * iD * iD;
+                    axx = Hh * (h[3] * iD * iD + Dual(2.0) * h[1] * h[1] * iD * iD * iD);
+                    ayy = Hh * (h[4] * iD * iD + Dual(2.0) * h[2] * h[2] * iD * iD * iD);
+                }
+            }
+        }
+    }
+    Dual zeta = Dual(z) + b;
+    Dual sx = ax * zeta + a * bx, sy = ay * zeta + a * by;
+    out[0] = a * zeta;
+    out[1] = a;
+    out[2] = sx;
+    out[3] = sy;
+    out[4] = (axx + ayy) * zeta + Dual(2.0) * (ax * bx + ay * by) + a * (bxx + byy);
+    out[5] = a * a + sx * sx + sy * sy;
+}
+
+constexpr int MAPT = 128;
+
+// partial[k * nblk + block] = sum over the block's particles of sum_q mbar_q dm_q/dtheta_k
+__global__ void __launch_bounds__(MAPT) k_map_adjoint(DevParams P, vct_state s, int n, int nparam,
+                                                      const double *const *mbar, double *partial)
+{
+    __shared__ double red[MAPT / 32];
+    const int i = blockIdx.x * MAPT + threadIdx.x;
+    double bar[6] = {0, 0, 0, 0, 0, 0};
+    double x = 0, y = 0, z = 0;
+    const bool act = i < n;
+    if (act) {
+        x = s.x[i];
+        y = P.dim == 3 && s.y ? s.y[i] : 0.0;
+        z = s.z[i];
+        for (int q = 0; q < 6; ++q) bar[q] = mbar[q] ? mbar[q][i] : 0.0;
+    }
+    for (int k = 0; k < nparam; ++k) {
+        double c = 0.0;
+        if (act) {
+            Dual out[6];
+            metric_dual(P, x, y, z, k, out);
+            for (int q = 0; q < 6; ++q) c += bar[q] * out[q].d;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < MAPT / 32; ++w) t += red[w];
+            partial[(int64_t)k * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_map_adjoint_sum(const double *partial, int nblk, int nparam, double *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nparam) return;
+    double t = 0.0;
+    for (int b = 0; b < nblk; ++b) t += partial[(int64_t)k * nblk + b];
+    out[k] = t;
+}
+
+int launch_map_adjoint(const DevParams &P, vct_state s, int64_t n, const double *const *mbar_dev,
+                       double *partial, int64_t partial_cap, double *out, cudaStream_t st)
+{
+    const int nparam = 5 + 4 * P.n_gauss;
+    const int nblk = (int)((n + MAPT - 1) / MAPT);
+    if ((int64_t)nblk * nparam > partial_cap) return 1;
+    k_map_adjoint<<<nblk, MAPT, 0, st>>>(P, s, (int)n, nparam, mbar_dev, partial);
+    k_map_adjoint_sum<<<(nparam + 127) / 128, 128, 0, st>>>(partial, nblk, nparam, out);
+    return 0;
+}
+
 void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,
                        int32_t *col, int64_t col_cap, cudaStream_t st)
 {

@@ -20,7 +20,7 @@ MAP = {"E": 0, "BF": 1, "BFE": 2, "SIGMA": 3}
 VCT_MAX_GAUSS = 32
 
 EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
-           "sph2_derivatives", "sph2_derivatives_backward", "vct_step",
+           "sph2_derivatives", "sph2_derivatives_backward", "vct_map_backward", "vct_step",
            "vct_step_host", "vct_step_probe", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
 
@@ -90,6 +90,8 @@ def load_library(path=LIB_PATH):
     L.vct_build_neighbours_noalloc.restype = C.c_int
     L.sph2_derivatives.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp, vp]
     L.sph2_derivatives_backward.argtypes = [vp, C.POINTER(vct_state), C.c_int32, vp, vp, vp, vp]
+    L.vct_map_backward.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp, vp, vp, vp,
+                                   C.POINTER(C.c_double)]
     L.vct_step.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_host.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_probe.argtypes = [vp, C.POINTER(vct_state), C.POINTER(vct_probe),
@@ -102,7 +104,7 @@ def load_library(path=LIB_PATH):
     L.vct_destroy.argtypes = [vp]
     L.vct_destroy.restype = None
     for name in ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives",
-                 "sph2_derivatives_backward",
+                 "sph2_derivatives_backward", "vct_map_backward",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
@@ -279,6 +281,19 @@ class Solver:
                                                        _ptr(d2_bar), _ptr(lap_bar), _ptr(phib)),
                     "sph2_derivatives_backward")
         return phib
+
+    def vct_map_backward(self, state, zh_bar=None, J_bar=None, sx_bar=None, sy_bar=None,
+                         c0_bar=None, c3_bar=None):
+        """theta_bar (numpy, 5 + 4 n_gauss): adjoint of the per-particle metric
+        (z^, J, s_x, s_y, c0, c3) pulled back to the bathymetry parameters."""
+        ng = len(self.sc.bathy.amp)
+        out = (C.c_double * (5 + 4 * ng))()
+        s = state.struct()
+        c = lambda t: None if t is None else _ptr(t.contiguous())
+        self._check(self.lib.vct_map_backward(self.ctx, C.byref(s), c(zh_bar), c(J_bar), c(sx_bar),
+                                              c(sy_bar), c(c0_bar), c(c3_bar), out),
+                    "vct_map_backward")
+        return np.array(out[:])
 
     def vct_step(self, state, nsteps=1):
         s = state.struct()

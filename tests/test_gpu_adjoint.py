@@ -97,3 +97,51 @@ def test_autograd_matches_central_differences():
         e[0, k] = h
         fd = (float(loss(phi0 + e)) - float(loss(phi0 - e))) / (2 * h)
         assert abs(fd - grad[k]) <= 1e-6 * (abs(fd) + 1.0)
+
+
+def _theta_vector(b):
+    return np.array([b.h0, b.slope_x, b.slope_y, b.cos_amp, b.cos_len] + list(b.amp) + list(b.cx)
+                    + list(b.cy) + list(b.width), dtype=np.float64)
+
+
+def _set_theta(b, th):
+    G = len(b.amp)
+    b.h0, b.slope_x, b.slope_y, b.cos_amp, b.cos_len = (float(v) for v in th[:5])
+    b.amp = list(th[5:5 + G])
+    b.cx = list(th[5 + G:5 + 2 * G])
+    b.cy = list(th[5 + 2 * G:5 + 3 * G])
+    b.width = list(th[5 + 3 * G:5 + 4 * G])
+
+
+@pytest.mark.parametrize("kind,dim", [("SIGMA", 2), ("BF", 2), ("BFE", 3), ("SIGMA", 3)])
+def test_map_backward_matches_oracle_differences(kind, dim):
+    """theta_bar from the GPU against central differences of the oracle's metric
+    (z^, J, s_x, s_y, c0, c3) for every bathymetry parameter."""
+    import copy
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    bathy = S.Bathymetry(h0=0.01, slope_x=0.03, slope_y=-0.02, cos_amp=0.004, cos_len=0.17,
+                         amp=[0.02, -0.015], cx=[0.05, 0.09], cy=[0.02, 0.03], width=[0.03, 0.04])
+    sc = S.small_tank(dim=dim, kind=kind, L=0.12, W=0.05, H=0.06, d0=0.01, seed=6, bathy=bathy,
+                      aspect=2.0, alpha_min=0.5, alpha_max=4.0)
+    rng = np.random.default_rng(7)
+    n = sc.n
+    bars = [rng.normal(size=n) for _ in range(6)]
+    s = V.Solver(sc)
+    got = s.vct_map_backward(V.DeviceState(sc), *[torch.tensor(b, device="cuda") for b in bars])
+    th0 = _theta_vector(sc.bathy)
+
+    def objective(th):
+        sc2 = copy.deepcopy(sc)
+        _set_theta(sc2.bathy, th)
+        zh, met = O.map_metric(sc2, sc.x, sc.y, sc.z)
+        q = [zh, met[:, 0], met[:, 1], met[:, 2], met[:, 3], met[:, 4]]
+        return sum(float(np.dot(bars[k], q[k])) for k in range(6))
+
+    for k in range(th0.size):
+        h = 1e-6 * max(1.0, abs(th0[k]))
+        tp, tm = th0.copy(), th0.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (objective(tp) - objective(tm)) / (2 * h)
+        assert abs(fd - got[k]) <= 1e-5 * (abs(fd) + abs(got[k]) + 1e-3), (k, fd, got[k])
