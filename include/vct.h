@@ -238,6 +238,17 @@ vct_status vct_map_backward(vct_ctx *ctx, const vct_state *state, const double *
  * out (host, may be NULL) receives solve statistics. */
 vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *out);
 
+/* Ensemble: advance n_scen independent scenarios (one context and one device
+ * state each, uneven particle counts allowed) by nsteps steps in one call.
+ * All scenarios' kernels are queued back to back on the FIRST context's stream
+ * (so the cooperative pressure solves never overlap), with no host
+ * synchronisation until the end, where each scenario's status is read once.
+ * out (host, may be NULL) receives n_scen stats.  Each scenario's result is
+ * bit-identical to vct_step on its own.  Returns the first failing status;
+ * scenarios that failed keep their state, the others are written back. */
+vct_status vct_batch_step(vct_ctx *const *ctxs, vct_state *const *states, int32_t n_scen,
+                          int32_t nsteps, vct_stats *out);
+
 /* Same as vct_step with HOST arrays: copies in, steps, copies back. */
 vct_status vct_step_host(vct_ctx *ctx, vct_state *host_state, int32_t nsteps, vct_stats *out);
 

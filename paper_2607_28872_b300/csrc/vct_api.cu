@@ -181,16 +181,10 @@ void geometry(vct_ctx *c, int64_t n)
     c->launches += 1 + 6 + 1;   // map_key; scan x3, scatter, cell sort, reorder; neighbours
 }
 
-vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, vct_stats *out)
+// Queue one time step of the current state on the context's stream.
+vct_status queue_step(vct_ctx *c, int64_t n, int step, int nsteps, const vct_probe *pr)
 {
-    vct_status v = check_state(c, s);
-    if (v) return v;
-    if (nsteps < 0) return VCT_ERR_ARG;
-    const int64_t n = s->n;
-    reset_status(c);
-    { StageTimer t(c, VCT_STAGE_LOAD); launch_load(c->P, cur(c), *s, n, c->st); }
-    c->launches += 1;
-    for (int step = 0; step < nsteps; ++step) {
+    {
         geometry(c, n);
         if (c->P.kind == VCT_MAP_SIGMA && c->P.volume_mode == 2) {
             StageTimer t(c, VCT_STAGE_SMOOTHING);
@@ -223,6 +217,22 @@ vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, 
         }
         { StageTimer t(c, VCT_STAGE_CORRECTOR); launch_corrector(c->P, cur(c), c->W, n, c->st); }
         c->launches += 5;   // pass1, pass2, rhs, krylov, corrector
+    }
+    return VCT_OK;
+}
+
+vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, vct_stats *out)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (nsteps < 0) return VCT_ERR_ARG;
+    const int64_t n = s->n;
+    reset_status(c);
+    { StageTimer t(c, VCT_STAGE_LOAD); launch_load(c->P, cur(c), *s, n, c->st); }
+    c->launches += 1;
+    for (int step = 0; step < nsteps; ++step) {
+        v = queue_step(c, n, step, nsteps, pr);
+        if (v) return v;
     }
     { StageTimer t(c, VCT_STAGE_STORE); launch_store(c->P, cur(c), *s, n, c->W.status, c->st); }
     c->launches += 1;
@@ -546,6 +556,43 @@ VCT_API vct_status vct_map_backward(vct_ctx *c, const vct_state *s, const double
 VCT_API vct_status vct_step(vct_ctx *c, vct_state *s, int32_t nsteps, vct_stats *out)
 {
     return run_steps(c, s, nsteps, nullptr, out);
+}
+
+VCT_API vct_status vct_batch_step(vct_ctx *const *ctxs, vct_state *const *states, int32_t n_scen,
+                                  int32_t nsteps, vct_stats *out)
+{
+    if (!ctxs || !states || n_scen <= 0 || nsteps < 0) return VCT_ERR_ARG;
+    for (int k = 0; k < n_scen; ++k) {
+        vct_status v = check_state(ctxs[k], states[k]);
+        if (v) return v;
+        for (int q = 0; q < k; ++q)
+            if (ctxs[q] == ctxs[k]) return VCT_ERR_ARG;   // one context per scenario
+    }
+    // every scenario's work goes to the first context's stream, in order
+    cudaStream_t st = ctxs[0]->st;
+    std::vector<cudaStream_t> saved(n_scen);
+    for (int k = 0; k < n_scen; ++k) {
+        saved[k] = ctxs[k]->st;
+        ctxs[k]->st = st;
+        reset_status(ctxs[k]);
+        launch_load(ctxs[k]->P, cur(ctxs[k]), *states[k], states[k]->n, st);
+        ctxs[k]->launches += 1;
+    }
+    vct_status first = VCT_OK;
+    for (int step = 0; step < nsteps && !first; ++step)
+        for (int k = 0; k < n_scen && !first; ++k)
+            first = queue_step(ctxs[k], states[k]->n, step, nsteps, nullptr);
+    for (int k = 0; k < n_scen; ++k) {
+        launch_store(ctxs[k]->P, cur(ctxs[k]), *states[k], states[k]->n, ctxs[k]->W.status, st);
+        ctxs[k]->launches += 1;
+    }
+    if (!first && cudaGetLastError() != cudaSuccess) first = VCT_ERR_CUDA;
+    for (int k = 0; k < n_scen; ++k) {
+        vct_status v = finish(ctxs[k], out ? out + k : nullptr, nsteps);
+        if (!first) first = v;
+        ctxs[k]->st = saved[k];
+    }
+    return first;
 }
 
 VCT_API vct_status vct_step_probe(vct_ctx *c, vct_state *s, const vct_probe *pr, vct_stats *out)

@@ -2157,8 +2157,12 @@ static const void *krylov_mg_fn(int precision, int dim)
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
-    cudaFuncSetAttribute(krylov_mg_fn(precision, dim), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    // the limit is per kernel, shared by every context: only ever raise it
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, krylov_mg_fn(precision, dim)) == cudaSuccess &&
+        fa.maxDynamicSharedSizeBytes < (int)smem)
+        cudaFuncSetAttribute(krylov_mg_fn(precision, dim), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, krylov_mg_fn(precision, dim), KT, smem);

@@ -21,6 +21,7 @@ VCT_MAX_GAUSS = 32
 
 EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
            "sph2_derivatives", "sph2_derivatives_backward", "vct_map_backward", "vct_step",
+           "vct_batch_step",
            "vct_step_host", "vct_step_probe", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
 
@@ -94,6 +95,9 @@ def load_library(path=LIB_PATH):
                                    C.POINTER(C.c_double)]
     L.vct_step.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_host.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
+    L.vct_batch_step.argtypes = [C.POINTER(vp), C.POINTER(C.POINTER(vct_state)), C.c_int32,
+                                 C.c_int32, C.POINTER(vct_stats)]
+    L.vct_batch_step.restype = C.c_int
     L.vct_step_probe.argtypes = [vp, C.POINTER(vct_state), C.POINTER(vct_probe),
                                  C.POINTER(vct_stats)]
     L.vct_set_profiling.argtypes = [vp, C.c_int32]
@@ -380,3 +384,19 @@ def sph2_function():
             return phib, None, None
 
     return SPH2Derivatives
+
+
+def vct_batch_step(solvers, states, nsteps=1):
+    """Advance several scenarios (one Solver and one DeviceState each) in one
+    call; returns the list of per-scenario vct_stats."""
+    lib = load_library()
+    n = len(solvers)
+    ctxs = (C.c_void_p * n)(*[s.ctx.value for s in solvers])
+    structs = [st.struct() for st in states]
+    # vct_state* const* : an array of pointers to the structs
+    arr = (C.POINTER(vct_state) * n)(*[C.pointer(x) for x in structs])
+    stats = (vct_stats * n)()
+    rc = lib.vct_batch_step(ctxs, arr, n, int(nsteps), stats)
+    if rc != VCT_OK:
+        raise VCTError(rc, "vct_batch_step")
+    return list(stats)
