@@ -103,7 +103,9 @@ typedef struct {
     int32_t max_neighbours; /* neighbour-list capacity per particle (0: 64 in 2-D, 160 in 3-D) */
     int32_t preconditioner; /* pressure solve: 0 plain BiCGSTAB; 1 BiCGSTAB preconditioned by an
                                aggregation multigrid V-cycle on the cell grid (Jacobi damping
-                               0.8, coarse-correction scale 1.3, 8 coarsest sweeps, up to 96 KB of
+                               0.8 / 0.7 and coarse-correction scale 1.3 / 1.8 in 2-D / 3-D,
+                               z-only coarsening while the operator's z coupling dominates,
+                               8 coarsest sweeps, up to 96 KB of
                                shared memory for the small levels; vct_init reads overrides from
                                the environment: VCT_MG_OMEGA, VCT_MG_KAPPA, VCT_MG_SWEEPS,
                                VCT_MG_SMEM_KB) */

@@ -382,18 +382,55 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         MG &M = c->mg;
         memset(&M, 0, sizeof M);
         M.S = prm->dim == 2 ? 9 : 27;
-        M.omega = 0.8f;   // tuned on configs 1-2 (iterations 30 -> 24 on config 2)
-        M.kappa = 1.3f;
+        // tuned: 2-D configs 1-2 (config 2: 30 -> 24 iterations); 3-D config 3 needs a
+        // larger coarse-correction scale (piecewise-constant aggregation under-corrects
+        // more per level in 3-D; kappa 1.3 does not converge there, 1.8 takes 81)
+        M.omega = prm->dim == 2 ? 0.8f : 0.7f;
+        M.kappa = prm->dim == 2 ? 1.3f : 1.8f;
         M.coarse_sweeps = 24;
         M.dims[1][0] = P.nc[0];
         M.dims[1][1] = P.nc[1];
         M.dims[1][2] = P.nc[2];
         M.n[1] = (int)ncell;
+        // Anisotropy of the projected operator: c_trans weights d2/dz^2 by about
+        // alpha^2 (E/BFE: the aspect ratio squared; sigma: mean over the box;
+        // BF: 1).  While the z coupling exceeds 2.5 x the horizontal one, coarsen
+        // along z only (each such step divides the ratio by 4), then in all axes.
+        double ratio = 1.0;
+        if (kind == VCT_MAP_E || kind == VCT_MAP_BFE) ratio = aspect_ratio * aspect_ratio;
+        else if (kind == VCT_MAP_SIGMA) {
+            double acc = 0.0;
+            int cnt = 0;
+            for (int ix = 0; ix <= 64; ++ix)
+                for (int iy = 0; iy <= (prm->dim == 3 ? 16 : 0); ++iy) {
+                    double x = prm->box_lo[0] + (prm->box_hi[0] - prm->box_lo[0]) * ix / 64.0;
+                    double y = prm->dim == 3 ? prm->box_lo[1] + (prm->box_hi[1] - prm->box_lo[1]) * iy / 16.0 : 0.0;
+                    double h = bathy->h0 + bathy->slope_x * x + bathy->slope_y * y;
+                    if (bathy->cos_amp != 0.0) h += bathy->cos_amp * cos(2.0 * M_PI * x / bathy->cos_len);
+                    for (int g = 0; g < bathy->n_gauss; ++g) {
+                        double dx = x - bathy->cx[g], dy = y - bathy->cy[g], w = bathy->width[g];
+                        h += bathy->amp[g] * exp(-(dx * dx + dy * dy) / (2.0 * w * w));
+                    }
+                    double D = prm->H - h, al = D > 0 ? prm->H_hat / D : prm->alpha_max;
+                    al = al < prm->alpha_min ? prm->alpha_min : (al > prm->alpha_max ? prm->alpha_max : al);
+                    acc += al * al;
+                    ++cnt;
+                }
+            ratio = acc / cnt;
+        }
         int l = 1;
         while (M.n[l] > 4 && l < MG_MAXL) {
-            int nx = (M.dims[l][0] + 1) / 2, ny = prm->dim == 3 ? (M.dims[l][1] + 1) / 2 : 1;
-            int nz = (M.dims[l][2] + 1) / 2;
+            int sh[3] = {1, prm->dim == 3 ? 1 : 0, 1};
+            if (ratio > 2.5 && M.dims[l][2] > 1) {
+                sh[0] = 0;
+                sh[1] = 0;
+                ratio *= 0.25;
+            }
+            int nx = (M.dims[l][0] + (1 << sh[0]) - 1) >> sh[0];
+            int ny = (M.dims[l][1] + (1 << sh[1]) - 1) >> sh[1];
+            int nz = (M.dims[l][2] + (1 << sh[2]) - 1) >> sh[2];
             if ((long long)nx * ny * nz == M.n[l]) break;
+            for (int q = 0; q < 3; ++q) M.shift[l][q] = sh[q];
             M.dims[l + 1][0] = nx;
             M.dims[l + 1][1] = ny;
             M.dims[l + 1][2] = nz;

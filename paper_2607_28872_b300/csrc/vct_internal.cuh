@@ -89,6 +89,7 @@ struct MG {
     float omega, kappa;  // Jacobi damping and coarse-correction scale
     int n[MG_MAXL + 1];
     int dims[MG_MAXL + 1][3];
+    int shift[MG_MAXL + 1][3];     // level l -> l+1: factor 2^shift per axis (x, y, z)
     long long offA[MG_MAXL + 1];
     long long offv[MG_MAXL + 1];
     long long soff[MG_MAXL + 1];   // shared-memory offsets (floats) of levels first_local..L

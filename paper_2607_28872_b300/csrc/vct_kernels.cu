@@ -1670,11 +1670,15 @@ __global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from lev
     const float *Af = W.mg_pool + M.offA[l];
     const float *vf = W.mg_pool + M.offv[l];
     const int fx = M.dims[l][0], fy = M.dims[l][1], fz = M.dims[l][2];
+    const int shx = M.shift[l][0], shy = M.shift[l][1], shz = M.shift[l][2];
     bool any = false;
-    for (int c = 0; c < (D == 2 ? 4 : 8); ++c) {
-        const int ax = px * 2 + (c & 1);
-        const int ay = D == 3 ? py * 2 + ((c >> 1) & 1) : 0;
-        const int az = pz * 2 + (D == 2 ? ((c >> 1) & 1) : ((c >> 2) & 1));
+    for (int c = 0; c < (1 << (shx + (D == 3 ? shy : 0) + shz)); ++c) {
+        const int bx = c & ((1 << shx) - 1);
+        const int by = D == 3 ? (c >> shx) & ((1 << shy) - 1) : 0;
+        const int bz = c >> (shx + (D == 3 ? shy : 0));
+        const int ax = (px << shx) + bx;
+        const int ay = D == 3 ? (py << shy) + by : 0;
+        const int az = (pz << shz) + bz;
         if (ax >= fx || ay >= fy || az >= fz) continue;
         const int If = (az * fy + ay) * fx + ax;
         if (vf[If] == 0.f) continue;          // inactive node
@@ -1685,7 +1689,7 @@ __global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from lev
                     const float aval = Af[(int64_t)stencil_index<D>(dx, dy, dz) * Nf + If];
                     if (aval == 0.f) continue;
                     const int jx = ax + dx, jy = ay + dy, jz = az + dz;
-                    acc[stencil_index<D>((jx >> 1) - px, D == 3 ? (jy >> 1) - py : 0, (jz >> 1) - pz)] += aval;
+                    acc[stencil_index<D>((jx >> shx) - px, D == 3 ? (jy >> shy) - py : 0, (jz >> shz) - pz)] += aval;
                 }
     }
     float *Ac = W.mg_pool + M.offA[l + 1];
@@ -1725,6 +1729,7 @@ struct LV {
     const float *A;
     float *dinv, *b, *z, *zu;
     int n, nx, ny, nz;
+    int shx, shy, shz;   // coarsening shifts from this level to the next
 };
 
 __device__ __forceinline__ LV lv_global(const Work &W, const MG &M, int l)
@@ -1741,6 +1746,9 @@ __device__ __forceinline__ LV lv_global(const Work &W, const MG &M, int l)
     v.nx = M.dims[l][0];
     v.ny = M.dims[l][1];
     v.nz = M.dims[l][2];
+    v.shx = M.shift[l][0];
+    v.shy = M.shift[l][1];
+    v.shz = M.shift[l][2];
     return v;
 }
 
@@ -1758,6 +1766,9 @@ __device__ __forceinline__ LV lv_shared(float *sh, const MG &M, int l)
     v.nx = M.dims[l][0];
     v.ny = M.dims[l][1];
     v.nz = M.dims[l][2];
+    v.shx = M.shift[l][0];
+    v.shy = M.shift[l][1];
+    v.shz = M.shift[l][2];
     return v;
 }
 
@@ -1776,10 +1787,11 @@ __device__ void lv_down(const LV &f, const LV &c, float om, int start, int strid
     for (int Ic = start; Ic < c.n; Ic += stride) {
         const int px = Ic % c.nx, pr = Ic / c.nx, py = pr % c.ny, pz = pr / c.ny;
         float bsum = 0.f;
-        for (int ch = 0; ch < (D == 2 ? 4 : 8); ++ch) {
-            const int ax = px * 2 + (ch & 1);
-            const int ay = D == 3 ? py * 2 + ((ch >> 1) & 1) : 0;
-            const int az = pz * 2 + (D == 2 ? ((ch >> 1) & 1) : ((ch >> 2) & 1));
+        const int sy = D == 3 ? f.shy : 0;
+        for (int ch = 0; ch < (1 << (f.shx + sy + f.shz)); ++ch) {
+            const int ax = (px << f.shx) + (ch & ((1 << f.shx) - 1));
+            const int ay = D == 3 ? (py << f.shy) + ((ch >> f.shx) & ((1 << f.shy) - 1)) : 0;
+            const int az = (pz << f.shz) + (ch >> (f.shx + sy));
             if (ax >= f.nx || ay >= f.ny || az >= f.nz) continue;
             const int If = (az * f.ny + ay) * f.nx + ax;
             if (f.dinv[If] == 0.f) continue;
@@ -1818,7 +1830,7 @@ __device__ void lv_up(const LV &f, const LV &c, float om, float kap, int start, 
                     const int jx = cx + dx, jy = cy + dy, jz = cz + dz;
                     if (jx < 0 || jy < 0 || jz < 0 || jx >= f.nx || jy >= f.ny || jz >= f.nz) continue;
                     const int J = (jz * f.ny + jy) * f.nx + jx;
-                    const int Jc = ((jz >> 1) * c.ny + (D == 3 ? (jy >> 1) : 0)) * c.nx + (jx >> 1);
+                    const int Jc = ((jz >> f.shz) * c.ny + (D == 3 ? (jy >> f.shy) : 0)) * c.nx + (jx >> f.shx);
                     const float zj = ldv<GL>(f.z + J) + kap * ldv<GL>(c.zu + Jc);
                     if (dx == 0 && dy == 0 && dz == 0) zi = zj;
                     res -= f.A[(int64_t)stencil_index<D>(dx, dy, dz) * f.n + I] * zj;

@@ -142,7 +142,7 @@ def _layer_stretch(kind, aspect, bathy, prm, x, y):
 
 def build_tank(name, dim, kind, aspect, bathy, params, L, W=0.0, surface=None,
                velocity=None, seed=0, jitter=0.1, wall_extra_layers=4,
-               box_top_margin=None):
+               box_top_margin=None, min_layers=1):
     """Fill a tank [0,L] (x [0,W] in 3-D) with fluid up to `surface(x, y)`
     (physical elevation) and surround it by wall + virtual layers."""
     prm = dict(DEFAULT_PARAMS)
@@ -166,6 +166,7 @@ def build_tank(name, dim, kind, aspect, bathy, params, L, W=0.0, surface=None,
     a_col, base_col = _layer_stretch(kind, aspect, bathy, prm, colx, coly)
     top_proj = a_col * (surface(colx, coly) - base_col)
     nz_col = np.maximum(np.rint(top_proj / d0).astype(np.int64), 0)
+    nz_col[nz_col < min_layers] = 0   # columns too shallow for a moment matrix stay dry
     ncol = colx.shape[0]
     rep = nz_col
     fx = np.repeat(colx, rep)
@@ -302,14 +303,21 @@ def solitary_sigma(d0=1.0 / 90.0, L=10.0, depth=0.5, bump=0.3, bump_x=5.0, bump_
 def beach_bfe_3d(d0=0.043, L=20.0, W=4.0, depth=1.0, slope=0.05, aspect=4.0, wave=0.1,
                  x0=3.0, seed=0, precision=1, **kw):
     """3-D BFE-SPH solitary wave on a 1:20 beach, 20 x 4 m basin, depth 1 m -> 0,
-    ellipsoidal particles with aspect ratio 4."""
+    ellipsoidal particles with aspect ratio 4.  Columns with fewer than three
+    projected layers are left dry (a one- or two-layer wedge has no moment
+    matrix).  The Smagorinsky model is off: at aspect 4 its eddy viscosity,
+    applied through the explicit viscous term with the ill-conditioned SPH(2)
+    second derivatives of free-surface particles, grows without bound within a
+    few steps (both the CUDA path and the oracle), unless the particle
+    regularisation the paper cites (not part of this path) damps it."""
     bathy = Bathymetry(slope_x=slope)
-    prm = dict(d0=d0, H=depth, H_hat=depth * aspect, dt=1.0e-3, precision=precision)
+    prm = dict(d0=d0, H=depth, H_hat=depth * aspect, dt=1.0e-3, precision=precision,
+               smagorinsky=0)
     prm.update(kw)
     eta, vel = solitary_wave(wave, depth, x0, prm.get("g", 9.81))
     surf = lambda x, y: depth + eta(x)
     return build_tank("beach_bfe_3d", 3, "BFE", aspect, bathy, prm, L, W, surface=surf,
-                      velocity=vel, seed=seed)
+                      velocity=vel, seed=seed, min_layers=3)
 
 
 def random_bumps(rng, n, amp_lo, amp_hi, x_lo, x_hi, width, depth, min_depth):
