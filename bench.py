@@ -41,14 +41,14 @@ WORKLOAD = ("2-D sigma-SPH solitary wave (H/d=0.2) over a 0.3 m Gaussian bump, 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="host-buffer steps timed for e2e (default: min(steps, 20))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--workload", default="config2", choices=["config2", "config1", "config3",
-                                                               "ensemble"])
+    ap.add_argument("--workload", default="sigma_solitary", choices=sorted(WORKLOADS))
     ap.add_argument("--ensemble-size", type=int, default=64)
     return ap.parse_args()
 
@@ -61,19 +61,23 @@ def dist_env():
 
 
 WORKLOADS = {
-    "config1": "2-D BF still water over a 1:10 slope, 1 m x 0.2 m, d0=0.01 m, jitter 0.1 d0",
-    "config2": WORKLOAD,
-    "config3": "3-D BFE solitary wave on a 1:20 beach, 20 x 4 m, depth 1 m, aspect 4, d0=0.043 m",
+    "sigma_solitary": WORKLOAD,
+    "still_water_bf": "2-D BF still water over a 1:10 slope, 1 m x 0.2 m, d0=0.01 m, jitter 0.1 d0",
+    "beach_bfe_3d": "3-D BFE solitary wave on a 1:20 beach, 20 x 4 m, depth 1 m, aspect 4, d0=0.043 m",
+    "beach_bfe_3d_slice": ("3-D BFE solitary wave, 8 x 1.6 m slice of the 1:20 beach (depth 1 -> 0.6 m), "
+                           "aspect 4, d0=0.043 m (profiling size)"),
     "ensemble": "sigma-SPH ensemble, particle counts log-uniform 5e3-2e5 (seed 2), 4 bumps each",
 }
 
 
-def workload(precision=1, name="config2"):
+def workload(precision=1, name="sigma_solitary"):
     from paper_2607_28872_b300 import scenarios as S
-    if name == "config1":
+    if name == "still_water_bf":
         return S.still_water_bf(precision=precision)
-    if name == "config3":
+    if name == "beach_bfe_3d":
         return S.beach_bfe_3d(precision=precision)
+    if name == "beach_bfe_3d_slice":
+        return S.beach_bfe_3d(L=8.0, W=1.6, precision=precision)
     return S.solitary_sigma(precision=precision)
 
 
@@ -245,11 +249,12 @@ def run_ours(args):
 
     # e2e: the host-buffer entry point, copies in and out inside the timed region
     e2e = None
-    if rank == 0 and args.e2e_steps > 0:
+    e2e_steps = min(args.steps, 20) if args.e2e_steps is None else args.e2e_steps
+    if rank == 0 and e2e_steps > 0:
         s2 = vct.Solver(sc)
         host = vct.HostState(sc, pin=True)
         s2.vct_step_host(host, 1)
-        k = args.e2e_steps
+        k = e2e_steps
         t0 = time.perf_counter()
         for _ in range(k):
             s2.vct_step_host(host, 1)

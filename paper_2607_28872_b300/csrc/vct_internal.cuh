@@ -42,6 +42,23 @@ struct Part {
 };
 
 // Scratch of one step.
+// Slot kk of row i in the pressure-equation ELL arrays.  Slots are kept in
+// blocks of EG consecutive slots per row (EG = 4 in 2-D, 8 in 3-D: the width of
+// the solver's row groups), blocks of all rows one after the other, so the EG
+// lanes of a row group read one contiguous EG x 4-byte segment per block and a
+// warp's load covers one 128-byte line.  Storage: roundup(max_nbr, EG) x cap.
+template <int EG>
+__host__ __device__ __forceinline__ int64_t ell_at(int kk, int64_t i, int64_t cap)
+{
+    return ((int64_t)(kk / EG) * cap + i) * EG + (kk % EG);
+}
+__host__ __device__ __forceinline__ int64_t ell_at_dim(int dim, int kk, int64_t i, int64_t cap)
+{
+    return dim == 2 ? ell_at<4>(kk, i, cap) : ell_at<8>(kk, i, cap);
+}
+template <int D>
+__host__ __device__ constexpr int ell_group() { return D == 2 ? 4 : 8; }
+
 struct Work {
     int64_t cap;
     int32_t max_nbr;          // ELL slots per particle
@@ -52,7 +69,7 @@ struct Work {
     double *rho_hat, *lam, *nu;
     int32_t *fs;
     double *vstar, *acc;      // [d] per particle
-    int32_t *pcnt, *pcol;     // pressure-equation coefficients (ELL)
+    int32_t *pcnt, *pcol;     // pressure-equation coefficients (ELL, slot-blocked: ell_at)
     double *pval, *diag, *bvec, *wallrhs;
     float *pvalf;             // FP32 coefficients of the mixed form
     double *jbar_tmp;
@@ -73,6 +90,7 @@ struct Work {
     float *mg_pool;           // coarse operators and vectors of all levels
     double *kr0;              // fine residual of the V-cycle (FP32 or FP64 slots)
     double *kq0, *kq1;        // preconditioned directions p^, s^
+    double *kz0, *kzb;        // V-cycle: first Jacobi step and prolonged correction
     double *adj;              // adjoint scratch: [m + dim] per particle
 };
 
@@ -94,6 +112,11 @@ struct MG {
     long long offv[MG_MAXL + 1];
     long long soff[MG_MAXL + 1];   // shared-memory offsets (floats) of levels first_local..L
     long long sh_floats;           // shared memory of block 0's levels (floats)
+    int fly;                       // 1: V-cycle inputs formed on the fly (small systems)
+    int staged;                    // large-system form: rows staged by cp.async
+    int gather_l1;                 // large-system form: fine gathers through L1
+    long long stage_off;           // byte offset of the row-staging area (large systems)
+    long long smem_bytes;          // dynamic shared memory of the solver launch
 };
 
 struct Ctx;
@@ -115,7 +138,9 @@ int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot
 void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st);
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
-int krylov_mg_coop_blocks(int precision, int dim, size_t smem);
+bool krylov_mg_fly_default(long long rows);
+int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly);
+size_t krylov_mg_stage_bytes(int precision, int dim, bool staged);
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
                        int ncomp, double *grad, double *d2, double *lap, cudaStream_t st);

@@ -1081,9 +1081,10 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
         if (tj == FLUID) {
             diag -= aij;
             if (!W.fs[j]) {
-                W.pcol[(int64_t)pc * cap + i] = j;
-                if (P.precision == VCT_MIXED) W.pvalf[(int64_t)pc * cap + i] = (float)aij;
-                else W.pval[(int64_t)pc * cap + i] = aij;
+                const int64_t q = ell_at<ell_group<D>()>(pc, i, cap);
+                W.pcol[q] = j;
+                if (P.precision == VCT_MIXED) W.pvalf[q] = (float)aij;
+                else W.pval[q] = aij;
                 ++pc;
             }
         } else {  // wall: p_ij = rho r_ij . f_i (Eq. PNC)
@@ -1353,7 +1354,7 @@ __device__ __forceinline__ T row_dot(const Work &W, int i, int pc, int lg, GetX 
         jj[s] = 0;
         aa[s] = CT(0);
         if (kk < W.max_nbr) {
-            const int64_t q = (int64_t)kk * cap + i;
+            const int64_t q = ell_at<G>(kk, i, cap);
             jj[s] = W.pcol[q];
             aa[s] = coef<CT>(W, q);
         }
@@ -1363,9 +1364,40 @@ __device__ __forceinline__ T row_dot(const Work &W, int i, int pc, int lg, GetX 
     for (int s = 0; s < NS; ++s)
         if (lg + s * G < pc) acc += (T)aa[s] * getx(jj[s]);
     for (int kk = lg + NS * G; kk < pc; kk += G) {
-        const int64_t q = (int64_t)kk * cap + i;
+        const int64_t q = ell_at<G>(kk, i, cap);
         acc += (T)coef<CT>(W, q) * getx(W.pcol[q]);
     }
+    return acc;
+}
+
+// As row_dot, with the row's count loaded in the same round trip as its operator.
+template <typename T, typename CT, int G, int NS, typename GetX>
+__device__ __forceinline__ T row_dot_pc(const Work &W, int i, int lg, int &pc_out, GetX getx)
+{
+    const int64_t cap = W.cap;
+    const int pc = W.pcnt[i];
+    int jj[NS];
+    CT aa[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int kk = lg + s * G;
+        jj[s] = 0;
+        aa[s] = CT(0);
+        if (kk < W.max_nbr) {
+            const int64_t q = ell_at<G>(kk, i, cap);
+            jj[s] = W.pcol[q];
+            aa[s] = coef<CT>(W, q);
+        }
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (lg + s * G < pc) acc += (T)aa[s] * getx(jj[s]);
+    for (int kk = lg + NS * G; kk < pc; kk += G) {
+        const int64_t q = ell_at<G>(kk, i, cap);
+        acc += (T)coef<CT>(W, q) * getx(W.pcol[q]);
+    }
+    pc_out = pc;
     return acc;
 }
 
@@ -1638,7 +1670,7 @@ __global__ void k_mg_level1(Work W, MG M, int mixed)
         ++rows;
         center += W.diag[i];
         for (int k = 0; k < pc; ++k) {
-            const int64_t q = (int64_t)k * cap + i;
+            const int64_t q = ell_at<ell_group<D>()>(k, i, cap);
             const int j = W.pcol[q];
             const float av = mixed ? W.pvalf[q] : (float)W.pval[q];
             int jx, jy, jz;
@@ -1885,11 +1917,422 @@ __device__ void mg_load_shared(const Work &W, const MG &M, float *sh)
     __syncthreads();
 }
 
+// Software-pipelined row products (large systems).  Every lane stages the next
+// row's count, columns and coefficients (its own slots lg, lg+G, ... below NS*G)
+// in shared memory with cp.async while it gathers for the current row (ROW_STAGES
+// rows in flight per group), so a row costs about one round trip (the gathers)
+// instead of three (count, operator, gathers).  Each thread reads back only
+// what it copied itself, so cp.async.wait_group alone orders the copies before
+// the reads.  The staging area is slot-major over the block's threads.
+template <int B>
+__device__ __forceinline__ void cp_async(void *sdst, const void *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename CT>
+__device__ __forceinline__ const CT *coef_ptr(const Work &W);
+template <>
+__device__ __forceinline__ const double *coef_ptr<double>(const Work &W) { return W.pval; }
+template <>
+__device__ __forceinline__ const float *coef_ptr<float>(const Work &W) { return W.pvalf; }
+
+#ifndef VCT_ROW_STAGES
+#define VCT_ROW_STAGES 2
+#endif
+constexpr int ROW_STAGES = VCT_ROW_STAGES;
+
+template <typename CT, int NS>
+struct RowStage {
+    int32_t *pc;   // [ROW_STAGES][KT]
+    int32_t *jj;   // [ROW_STAGES][NS][KT]
+    CT *aa;        // [ROW_STAGES][NS][KT]
+};
+
+template <typename CT, int NS>
+__host__ __device__ constexpr size_t row_stage_bytes()
+{
+    return (size_t)ROW_STAGES * KT * (sizeof(int32_t) * (1 + NS) + sizeof(CT) * NS);
+}
+
+// Fine-vector gathers: through L1 (valid after the grid barrier's acquire) or L2 only.
+template <typename T>
+__device__ __forceinline__ T ldx(const T *p, int j, bool l1)
+{
+    return l1 ? p[j] : __ldcg(p + j);
+}
+
+template <typename CT, int NS>
+__device__ __forceinline__ RowStage<CT, NS> row_stage(unsigned char *base, bool staged)
+{
+    RowStage<CT, NS> S;
+    if (!staged) {
+        S.aa = nullptr;
+        S.jj = S.pc = nullptr;
+        return S;
+    }
+    S.aa = (CT *)base;                                   // 8-byte aligned first
+    S.jj = (int32_t *)(base + sizeof(CT) * ROW_STAGES * NS * KT);
+    S.pc = S.jj + ROW_STAGES * NS * KT;
+    return S;
+}
+
+template <typename CT, int G, int NS>
+__device__ __forceinline__ void stage_row(const Work &W, const RowStage<CT, NS> &S, int b, int i, int lg)
+{
+    const int t = threadIdx.x;
+    const int64_t cap = W.cap;
+    const CT *cv = coef_ptr<CT>(W);
+    cp_async<4>(S.pc + b * KT + t, W.pcnt + i);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int kk = lg + s * G;
+        if (kk < W.max_nbr) {
+            const int64_t q = ell_at<G>(kk, i, cap);
+            cp_async<4>(S.jj + (b * NS + s) * KT + t, W.pcol + q);
+            cp_async<(int)sizeof(CT)>(S.aa + (b * NS + s) * KT + t, cv + q);
+        }
+    }
+}
+
+// Row operands the epilogue needs besides the product (loaded with the gathers).
+template <typename A>
+struct Own4 {
+    A v[4];
+};
+
+// body(i, sum, o) runs for every unknown row i (pcnt >= 0) with the group's sum
+// of a_ik x_k over the stored coefficients (the diagonal is not included) and
+// o = own(i), whose loads are issued before the gathers so that both share one
+// round trip.
+template <typename T, typename CT, int G, int NS, typename GetX, typename OwnF, typename Body>
+__device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT, NS> &S, int n, int g0,
+                                               int ngroups, int lg, GetX getx, OwnF own, Body body)
+{
+    const int t = threadIdx.x;
+    const int64_t cap = W.cap;
+    if (S.pc == nullptr) {   // staging off: count and operator, then the gathers
+        for (int i = g0; i < n; i += ngroups) {
+            int pc;
+            const auto o = own(i);
+            T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, getx);
+            if (pc < 0) continue;
+            acc = group_sum<G>(acc);
+            body(i, acc, o);
+        }
+        return;
+    }
+    int b = 0;   // stage of row i
+#pragma unroll
+    for (int r = 0; r < ROW_STAGES - 1; ++r) {
+        if (g0 + r * ngroups < n) stage_row<CT, G, NS>(W, S, r, g0 + r * ngroups, lg);
+        cp_async_commit();
+    }
+    for (int i = g0; i < n; i += ngroups) {
+        const int ia = i + (ROW_STAGES - 1) * ngroups;
+        if (ia < n) stage_row<CT, G, NS>(W, S, (b + ROW_STAGES - 1) % ROW_STAGES, ia, lg);
+        cp_async_commit();
+        cp_async_wait<ROW_STAGES - 1>();
+        const int pc = S.pc[b * KT + t];
+        const auto o = own(i);
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (lg + s * G < pc)
+                acc += (T)S.aa[(b * NS + s) * KT + t] * getx(S.jj[(b * NS + s) * KT + t]);
+        for (int kk = lg + NS * G; kk < pc; kk += G) {
+            const int64_t q = ell_at<G>(kk, i, cap);
+            acc += (T)coef<CT>(W, q) * getx(W.pcol[q]);
+        }
+        b = b + 1 == ROW_STAGES ? 0 : b + 1;
+        if (pc < 0) continue;
+        acc = group_sum<G>(acc);
+        body(i, acc, o);
+    }
+    cp_async_wait<0>();
+}
+
+// z_out = M^-1 v.  On entry v and z0 = omega D^-1 v (the first Jacobi step from
+// zero) are in memory for every unknown row and visible grid-wide; each fine
+// product then gathers one value per neighbour.  Returns false if a grid
+// barrier timed out.
+template <typename T, typename CT, int G, int NS, int D>
+__device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT, NS> &S, int n,
+                       const T *v, const T *z0, T *zb, T *zout, int lg, bool lead, int g0, int ngroups,
+                       int gtid, int gthreads)
+{
+    const unsigned nb = gridDim.x;
+    const float om = M.omega, kap = M.kappa;
+    const bool l1 = M.gather_l1 != 0;
+    T *r0 = (T *)W.kr0;
+    // D0: fine residual r0 = v - A z0
+    rows_pipelined<T, CT, G, NS>(
+        W, S, n, g0, ngroups, lg, [&](int j) { return ldx(z0, j, l1); },
+        [&](int i) { return Own4<T>{{__ldcg(v + i), __ldcg(z0 + i), (T)W.diag[i], T(0)}}; },
+        [&](int i, T acc, const Own4<T> &o) {
+            if (lead) r0[i] = o.v[0] - acc - o.v[2] * o.v[1];
+        });
+    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    // D1: restriction to the cells, one Jacobi step from zero on level 1
+    {
+        const LV c = lv_global(W, M, 1);
+        for (int I = gtid; I < c.n; I += gthreads) {
+            float bs = 0.f;
+            const int a = W.cell_start[I], b = W.cell_start[I + 1];
+            for (int i = a; i < b; ++i)
+                if (W.pcnt[i] >= 0) bs += (float)__ldcg(r0 + i);
+            c.b[I] = bs;
+            c.z[I] = om * bs * c.dinv[I];
+        }
+    }
+    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    const int fl = M.first_local;
+    for (int l = 1; l < fl; ++l) {
+        lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, gtid, gthreads);
+        if (!grid_barrier(W.bar, nb, W.status)) return false;
+    }
+    if (blockIdx.x == 0) {
+        {
+            const LV g = lv_global(W, M, fl), s = lv_shared(sh, M, fl);
+            for (int q = threadIdx.x; q < g.n; q += blockDim.x) {
+                s.b[q] = __ldcg(g.b + q);
+                s.z[q] = __ldcg(g.z + q);
+            }
+            __syncthreads();
+        }
+        for (int l = fl; l < M.L; ++l) {
+            lv_down<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+        lv_coarsest<D>(lv_shared(sh, M, M.L), om, M.coarse_sweeps);
+        for (int l = M.L - 1; l >= fl; --l) {
+            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, kap, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+        {
+            const LV g = lv_global(W, M, fl), s = lv_shared(sh, M, fl);
+            for (int q = threadIdx.x; q < g.n; q += blockDim.x) g.zu[q] = s.zu[q];
+        }
+    }
+    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    for (int l = fl - 1; l >= 1; --l) {
+        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, kap, gtid, gthreads);
+        if (!grid_barrier(W.bar, nb, W.status)) return false;
+    }
+    // P0: prolongation from the cells, zb = z0 + kappa zu_1(cell)
+    {
+        const float *zu1 = W.mg_pool + M.offv[1] + 3 * M.n[1];
+        for (int i = gtid; i < n; i += gthreads)
+            if (W.pcnt[i] >= 0) zb[i] = __ldcg(z0 + i) + (T)kap * (T)__ldcg(zu1 + W.cellid[i]);
+    }
+    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    // U0: one damped Jacobi step on the fine level
+    rows_pipelined<T, CT, G, NS>(
+        W, S, n, g0, ngroups, lg, [&](int j) { return ldx(zb, j, l1); },
+        [&](int i) { return Own4<T>{{__ldcg(zb + i), __ldcg(v + i), (T)W.diag[i], (T)W.mg_dsc[i]}}; },
+        [&](int i, T acc, const Own4<T> &o) {
+            if (lead) {
+                const T res = o.v[1] - acc - o.v[2] * o.v[0];
+                zout[i] = o.v[0] + (T)om * res * o.v[3];
+            }
+        });
+    return grid_barrier(W.bar, nb, W.status);
+}
+
+// Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
+template <typename T, typename CT, int G, int NS, int D>
+__global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int maxit, double rtol,
+                                                  double inner_floor, int32_t *iters_out,
+                                                  double *resid_out)
+{
+    const unsigned nb = gridDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const bool lead = lg == 0;
+    const int ngroups = (gridDim.x * blockDim.x) / G;
+    const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    extern __shared__ __align__(16) float mg_sh[];
+    if (blockIdx.x == 0) mg_load_shared(W, M, mg_sh);
+    const RowStage<CT, NS> S = row_stage<CT, NS>((unsigned char *)mg_sh + M.stage_off, M.staged != 0);
+    const bool l1 = M.gather_l1 != 0;
+    const float om = M.omega;
+    double *x = W.kx, *f = W.kf;
+    T *r = (T *)W.kr, *rh = (T *)W.krh, *s = (T *)W.ks, *t = (T *)W.kt, *dl = (T *)W.kd;
+    T *pold = (T *)W.kp0, *pnew = (T *)W.kp1, *vold = (T *)W.kv0, *vnew = (T *)W.kv1;
+    T *ph = (T *)W.kq0, *sh = (T *)W.kq1;   // p^ = M^-1 p, s^ = M^-1 s
+    T *z0 = (T *)W.kz0, *zb = (T *)W.kzb;
+    int total_it = 0;
+    bool fail = false;
+    double bn = 0.0, rn = 0.0;
+    for (int outer = 0;; ++outer) {
+        double part[2] = {0.0, 0.0};
+        rows_pipelined<double, CT, G, NS>(
+            W, S, n, g0, ngroups, lg, [&](int j) { return ldx(x, j, l1); },
+            [&](int i) { return Own4<double>{{W.bvec[i], W.diag[i], __ldcg(x + i), 0.0}}; },
+            [&](int i, double ax, const Own4<double> &o) {
+                if (lead) {
+                    const double bi = o.v[0], fi = bi - (ax + o.v[1] * o.v[2]);
+                    f[i] = fi;
+                    part[0] += fi * fi;
+                    part[1] += bi * bi;
+                }
+            });
+        block_partials<2>(part, W.partial);
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        double tot[2];
+        grid_totals<2>(W.partial, nb, tot);
+        rn = sqrt(tot[0]);
+        bn = sqrt(tot[1]);
+        if (bn == 0.0) {
+            for (int i = g0; i < n; i += ngroups)
+                if (lead) x[i] = 0.0;
+            rn = 0.0;
+            break;
+        }
+        if (rn <= rtol * bn) break;
+        if (total_it >= maxit || outer >= 64) {
+            fail = true;
+            break;
+        }
+        const double fn = rn, tol_in = fmax(rtol * bn / rn, inner_floor);
+        double rho = fn * fn, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        bool first = true, have_pend = false;
+        double pend_a = 0.0, pend_w = 0.0;
+        for (;;) {
+            if (total_it >= maxit) break;
+            ++total_it;
+            const double beta = first ? 0.0 : (rho / rho_old) * (alpha / omega);
+            const T tb = (T)beta, tw = (T)omega, ta = (T)pend_a, twp = (T)pend_w;
+            // E1 (own rows): apply the pending update, r = s - w t, p_new = r + beta (p - w v)
+            for (int i = gtid; i < n; i += gthreads) {
+                if (W.pcnt[i] < 0) continue;
+                T ri, pn;
+                if (first) {
+                    ri = (T)__ldcg(f + i);
+                    rh[i] = ri;
+                    dl[i] = T(0);
+                    pn = ri;
+                } else {
+                    ri = __ldcg(s + i) - tw * __ldcg(t + i);
+                    pn = ri + tb * (pold[i] - tw * __ldcg(vold + i));
+                    if (have_pend) dl[i] += ta * __ldcg(ph + i) + twp * __ldcg(sh + i);
+                }
+                r[i] = ri;
+                pnew[i] = pn;
+                z0[i] = (T)om * pn * (T)W.mg_dsc[i];
+            }
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, pnew, z0, zb, ph, lg, lead, g0, ngroups, gtid, gthreads))
+                return;
+            first = false;
+            have_pend = false;
+            // v = A p^, partial (rh, v)
+            T pa = T(0);
+            rows_pipelined<T, CT, G, NS>(
+                W, S, n, g0, ngroups, lg, [&](int j) { return ldx(ph, j, l1); },
+                [&](int i) { return Own4<T>{{(T)W.diag[i], __ldcg(ph + i), __ldcg(rh + i), T(0)}}; },
+                [&](int i, T acc, const Own4<T> &o) {
+                    if (lead) {
+                        acc += o.v[0] * o.v[1];
+                        vnew[i] = acc;
+                        pa += o.v[2] * acc;
+                    }
+                });
+            {
+                double pd[1] = {(double)pa};
+                block_partials<1>(pd, W.partial);
+            }
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            double tv[1];
+            grid_totals<1>(W.partial, nb, tv);
+            if (tv[0] == 0.0) {
+                fail = true;
+                break;
+            }
+            alpha = rho / tv[0];
+            const T ta2 = (T)alpha;
+            // E2 (own rows): s = r - alpha v
+            for (int i = gtid; i < n; i += gthreads) {
+                if (W.pcnt[i] < 0) continue;
+                const T si = r[i] - ta2 * __ldcg(vnew + i);
+                s[i] = si;
+                z0[i] = (T)om * si * (T)W.mg_dsc[i];
+            }
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, s, z0, zb, sh, lg, lead, g0, ngroups, gtid, gthreads))
+                return;
+            // t = A s^; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
+            T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
+            rows_pipelined<T, CT, G, NS>(
+                W, S, n, g0, ngroups, lg, [&](int j) { return ldx(sh, j, l1); },
+                [&](int i) { return Own4<T>{{__ldcg(s + i), __ldcg(rh + i), (T)W.diag[i], __ldcg(sh + i)}}; },
+                [&](int i, T acc, const Own4<T> &o) {
+                    if (lead) {
+                        const T si = o.v[0], hi = o.v[1];
+                        acc += o.v[2] * o.v[3];
+                        t[i] = acc;
+                        pb0 += acc * si;
+                        pb1 += acc * acc;
+                        pb2 += si * si;
+                        pb3 += hi * si;
+                        pb4 += hi * acc;
+                    }
+                });
+            {
+                double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
+                block_partials<5>(pd, W.partial);
+            }
+            if (!grid_barrier(W.bar, nb, W.status)) return;
+            double tq[5];
+            grid_totals<5>(W.partial, nb, tq);
+            T *tp = pold; pold = pnew; pnew = tp;
+            tp = vold; vold = vnew; vnew = tp;
+            have_pend = true;
+            pend_a = alpha;
+            if (sqrt(tq[2]) <= tol_in * fn) {
+                pend_w = 0.0;
+                break;
+            }
+            if (tq[1] == 0.0) {
+                pend_w = 0.0;
+                fail = true;
+                break;
+            }
+            omega = tq[0] / tq[1];
+            pend_w = omega;
+            rho_old = rho;
+            rho = tq[3] - omega * tq[4];
+            const double rr = tq[2] - 2.0 * omega * tq[0] + omega * omega * tq[1];
+            if (sqrt(fmax(rr, 0.0)) <= tol_in * fn || rho == 0.0) break;
+        }
+        const T fa = (T)pend_a, fw = (T)pend_w;
+        for (int i = gtid; i < n; i += gthreads) {
+            if (W.pcnt[i] < 0) continue;
+            T d = dl[i];
+            if (have_pend) d += fa * __ldcg(ph + i) + fw * __ldcg(sh + i);
+            x[i] += (double)d;
+        }
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (fail) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (fail) set_error(W.status, VCT_ERR_NOCONV, -1);
+        iters_out[0] += total_it;
+        if (total_it > iters_out[1]) iters_out[1] = total_it;
+        iters_out[2] = total_it;
+        *resid_out = bn > 0.0 ? rn / bn : 0.0;
+    }
+}
+
 // z_out = M^-1 v for the fine vector given on the fly by in(j).  own(i) runs once
 // for every unknown row in the first phase (lane 0 of the row's group), before
 // any phase writes z_out.  Returns false if a grid barrier timed out.
 template <typename T, typename CT, int G, int NS, int D, typename In, typename Own>
-__device__ bool vcycle(const Work &W, const MG &M, float *sh, int n, In in, Own own, T *zout,
+__device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, Own own, T *zout,
                        int lg, bool lead, int g0, int ngroups, int gtid, int gthreads)
 {
     const unsigned nb = gridDim.x;
@@ -1978,7 +2421,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, int n, In in, Own 
 
 // Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
 template <typename T, typename CT, int G, int NS, int D>
-__global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit, double rtol,
+__global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int maxit, double rtol,
                                                   double inner_floor, int32_t *iters_out,
                                                   double *resid_out)
 {
@@ -2041,12 +2484,12 @@ __global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit
             // p_new = r + beta (p - w v) with r = s - w t; p^ = M^-1 p_new
             bool ok;
             if (fst) {
-                ok = vcycle<T, CT, G, NS, D>(W, M, mg_sh, n,
+                ok = vcycle_fly<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T { return (T)__ldcg(f + j); },
                     [&](int i) { const T ri = (T)f[i]; r[i] = ri; rh[i] = ri; pnew[i] = ri; dl[i] = T(0); },
                     ph, lg, lead, g0, ngroups, gtid, gthreads);
             } else {
-                ok = vcycle<T, CT, G, NS, D>(W, M, mg_sh, n,
+                ok = vcycle_fly<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T {
                         return (__ldcg(s + j) - tw * __ldcg(t + j)) + tb * (__ldcg(pold + j) - tw * __ldcg(vold + j));
                     },
@@ -2088,7 +2531,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit
             alpha = rho / tv[0];
             const T ta2 = (T)alpha;
             // s = r - alpha v; s^ = M^-1 s
-            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, n,
+            if (!vcycle_fly<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T { return __ldcg(r + j) - ta2 * __ldcg(vnew + j); },
                     [&](int i) { s[i] = r[i] - ta2 * vnew[i]; },
                     sh, lg, lead, g0, ngroups, gtid, gthreads))
@@ -2157,8 +2600,20 @@ __global__ void __launch_bounds__(KT) k_krylov_mg(Work W, MG M, int n, int maxit
     }
 }
 
-static const void *krylov_mg_fn(int precision, int dim)
+// Small systems (up to FLY_MAX_ROWS unknowns) form the V-cycle inputs on the fly
+// inside the products (fewer grid barriers); large systems keep them as
+// vectors, so each fine product gathers one value per neighbour.
+constexpr long long FLY_MAX_ROWS = 200000;
+
+static const void *krylov_mg_fn(int precision, int dim, bool fly)
 {
+    if (fly) {
+        if (precision == VCT_MIXED)
+            return dim == 2 ? (const void *)k_krylov_mg_fly<float, float, 4, 5, 2>
+                            : (const void *)k_krylov_mg_fly<float, float, 8, 7, 3>;
+        return dim == 2 ? (const void *)k_krylov_mg_fly<double, double, 4, 5, 2>
+                        : (const void *)k_krylov_mg_fly<double, double, 8, 7, 3>;
+    }
     if (precision == VCT_MIXED)
         return dim == 2 ? (const void *)k_krylov_mg<float, float, 4, 5, 2>
                         : (const void *)k_krylov_mg<float, float, 8, 7, 3>;
@@ -2166,18 +2621,26 @@ static const void *krylov_mg_fn(int precision, int dim)
                     : (const void *)k_krylov_mg<double, double, 8, 7, 3>;
 }
 
-int krylov_mg_coop_blocks(int precision, int dim, size_t smem)
+bool krylov_mg_fly_default(long long rows) { return rows <= FLY_MAX_ROWS; }
+
+size_t krylov_mg_stage_bytes(int precision, int dim, bool staged)
+{
+    if (!staged) return 0;
+    if (precision == VCT_MIXED) return dim == 2 ? row_stage_bytes<float, 5>() : row_stage_bytes<float, 7>();
+    return dim == 2 ? row_stage_bytes<double, 5>() : row_stage_bytes<double, 7>();
+}
+
+int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly)
 {
     int dev = 0, sms = 0, per = 0;
-    // the limit is per kernel, shared by every context: only ever raise it
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, krylov_mg_fn(precision, dim)) == cudaSuccess &&
-        fa.maxDynamicSharedSizeBytes < (int)smem)
-        cudaFuncSetAttribute(krylov_mg_fn(precision, dim), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, krylov_mg_fn(precision, dim), KT, smem);
+    const void *fn = krylov_mg_fn(precision, dim, fly);
+    // the limit is per kernel, shared by every context: only ever raise it
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.maxDynamicSharedSizeBytes < (int)smem)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, KT, smem);
     if (per > 4) per = 4;
     int nb = sms * per;
     return nb < PSTRIDE ? nb : PSTRIDE;
@@ -2198,8 +2661,8 @@ int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nbl
     void *args[] = {(void *)&W, (void *)&Mc, (void *)&nn, (void *)&maxit, (void *)&rtol,
                     (void *)&floor_, (void *)&it_out, (void *)&res_out};
     cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);
-    cudaError_t e = cudaLaunchCooperativeKernel(krylov_mg_fn(P.precision, P.dim), dim3(nblk),
-                                                dim3(KT), args, (size_t)M.sh_floats * 4, st);
+    cudaError_t e = cudaLaunchCooperativeKernel(krylov_mg_fn(P.precision, P.dim, M.fly != 0),
+                                                dim3(nblk), dim3(KT), args, (size_t)M.smem_bytes, st);
     return e == cudaSuccess ? 0 : (int)e;
 }
 
@@ -2897,7 +3360,7 @@ __global__ void k_gather_masked(const Part c, Work W, int n, const double *xin, 
 }
 
 __global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double *out,
-                           int mixed)
+                           int mixed, int dim)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -2906,7 +3369,7 @@ __global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double
     if (pc >= 0) {
         y = W.diag[i] * xs[i];
         for (int k = 0; k < pc; ++k) {
-            int64_t q = (int64_t)k * W.cap + i;
+            int64_t q = ell_at_dim(dim, k, i, W.cap);
             double a = mixed ? (double)W.pvalf[q] : W.pval[q];
             y += a * xs[W.pcol[q]];
         }
@@ -2919,7 +3382,7 @@ void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const doub
 {
     unsigned g = (unsigned)((n + 255) / 256);
     k_gather_masked<<<g, 256, 0, st>>>(cur, W, (int)n, x_test, W.kt);
-    k_spmv_out<<<g, 256, 0, st>>>(cur, W, (int)n, W.kt, out, P.precision == VCT_MIXED);
+    k_spmv_out<<<g, 256, 0, st>>>(cur, W, (int)n, W.kt, out, P.precision == VCT_MIXED, P.dim);
 }
 
 void launch_store(const DevParams &P, Part cur, vct_state s, int64_t n, const int32_t *status,

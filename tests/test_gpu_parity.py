@@ -53,8 +53,8 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("name,make", SMALL + [("config1", S.still_water_bf)],
-                         ids=[s[0] for s in SMALL] + ["config1"])
+@pytest.mark.parametrize("name,make", SMALL + [("still_water_bf", S.still_water_bf)],
+                         ids=[s[0] for s in SMALL] + ["still_water_bf"])
 def test_neighbours_bit_exact(vct, name, make):
     sc = make()
     solver = vct.Solver(sc)
@@ -67,7 +67,7 @@ def test_neighbours_bit_exact(vct, name, make):
     assert np.array_equal(col.cpu().numpy(), ocol)
 
 
-def test_neighbours_bit_exact_config2(vct):
+def test_neighbours_bit_exact_sigma_solitary(vct):
     sc = S.solitary_sigma()
     solver = vct.Solver(sc)
     row, col = solver.vct_build_neighbours(vct.DeviceState(sc))
@@ -172,21 +172,54 @@ def _probe_compare(vct, sc, precision, tol, band):
     return stats, tied.sum()
 
 
-@pytest.mark.parametrize("name,make", SMALL + [("config1", S.still_water_bf)],
-                         ids=[s[0] for s in SMALL] + ["config1"])
+@pytest.mark.parametrize("name,make", SMALL + [("still_water_bf", S.still_water_bf)],
+                         ids=[s[0] for s in SMALL] + ["still_water_bf"])
 def test_step_parity_fp64(vct, name, make):
     _probe_compare(vct, make(), 0, 1e-12, 1e-9)
 
 
-@pytest.mark.parametrize("name,make", SMALL + [("config1", S.still_water_bf)],
-                         ids=[s[0] for s in SMALL] + ["config1"])
+@pytest.mark.parametrize("name,make", SMALL + [("still_water_bf", S.still_water_bf)],
+                         ids=[s[0] for s in SMALL] + ["still_water_bf"])
 def test_step_parity_mixed(vct, name, make):
     _probe_compare(vct, make(), 1, 1e-5, 1e-5)
 
 
-def test_step_parity_config2_mixed(vct):
-    """Full-size config 2 (sigma solitary wave, ~42.5k fluid), mixed form."""
+def test_step_parity_sigma_solitary_mixed(vct):
+    """Full-size sigma solitary wave over a Gaussian bump (~42.5k fluid), mixed form."""
     _probe_compare(vct, S.solitary_sigma(), 1, 1e-5, 1e-5)
+
+
+# The multigrid solver has two forms: V-cycle inputs formed on the fly (systems up
+# to 200k unknowns) and kept as vectors with cp.async-staged rows (larger ones).
+# VCT_MG_FORM forces the large-system form on the small cases.
+@pytest.mark.parametrize("precision,tol,band", [(0, 1e-12, 1e-9), (1, 1e-5, 1e-5)],
+                         ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name,make", [SMALL[1], SMALL[3], ("still_water_bf", S.still_water_bf)],
+                         ids=[SMALL[1][0], SMALL[3][0], "still_water_bf"])
+def test_step_parity_explicit_form(vct, monkeypatch, name, make, precision, tol, band):
+    monkeypatch.setenv("VCT_MG_FORM", "explicit")
+    _probe_compare(vct, make(), precision, tol, band)
+
+
+def test_step_parity_sigma_solitary_explicit_form(vct, monkeypatch):
+    monkeypatch.setenv("VCT_MG_FORM", "explicit")
+    _probe_compare(vct, S.solitary_sigma(), 1, 1e-5, 1e-5)
+
+
+def test_forms_agree_over_steps(vct, monkeypatch):
+    """Both solver forms run the same iteration; after 20 mixed steps of the still-water tank
+    their states agree to the solver tolerance."""
+    out = {}
+    for form in ("fly", "explicit"):
+        monkeypatch.setenv("VCT_MG_FORM", form)
+        sc = S.still_water_bf(precision=1)
+        s = vct.Solver(sc)
+        st = vct.DeviceState(sc)
+        s.vct_step(st, 20)
+        out[form] = st.numpy()
+    f = S.still_water_bf().type == S.FLUID
+    assert rel(out["fly"]["p"][f], out["explicit"]["p"][f]) < 1e-5
+    assert rel(out["fly"]["w"][f], out["explicit"]["w"][f]) < 1e-4
 
 
 def test_multi_step_fp64_matches_oracle(vct):
@@ -261,7 +294,7 @@ def test_poisoned_input_nonfinite(vct):
     assert e.value.status in (vct.VCT_ERR_NONFINITE, vct.VCT_ERR_NOCONV)
 
 
-def test_multi_step_3d_trajectory_matches_oracle():
+def test_multi_step_3d_trajectory_matches_oracle(monkeypatch):
     """Ten steps of a 1 m x 0.3 m slice of the 3-D BFE beach (aspect 4, ~36k
     particles): the GPU (FP64 and mixed) follows the oracle's maximum speed step
     by step (the configuration develops the slow growth of the method without
@@ -275,7 +308,8 @@ def test_multi_step_3d_trajectory_matches_oracle():
         assert info["rc"] == 0
         ref.append(np.sqrt(st.u ** 2 + st.v ** 2 + st.w ** 2)[f].max())
     from paper_2607_28872_b300 import vct as V
-    for prec in (0, 1):
+    for prec, form in ((0, "fly"), (1, "fly"), (1, "explicit")):
+        monkeypatch.setenv("VCT_MG_FORM", form)
         sc = sc0.copy()
         sc.params["precision"] = prec
         s = V.Solver(sc)
@@ -284,4 +318,4 @@ def test_multi_step_3d_trajectory_matches_oracle():
             s.vct_step(dst, 1)
             g = dst.numpy()
             vmax = np.sqrt(g["u"] ** 2 + g["v"] ** 2 + g["w"] ** 2)[f].max()
-            assert abs(vmax - ref[k]) <= 2e-3 * ref[k], (prec, k, vmax, ref[k])
+            assert abs(vmax - ref[k]) <= 2e-3 * ref[k], (prec, form, k, vmax, ref[k])

@@ -345,8 +345,8 @@ def test_still_water_exactly_at_rest(kind, aspect):
     assert np.allclose(st.p[f], sc.p[f], atol=1e-8 * sc.p.max())
 
 
-def test_still_water_config1_bounded():
-    """Config 1 as specified (jitter 0.1 d0, gamma = 100 dt): the density
+def test_still_water_jittered_bounded():
+    """The jittered still-water tank as specified (jitter 0.1 d0, gamma = 100 dt): the density
     relaxation of the stabilised PPE moves particles, but 20 steps stay
     bounded and the pressure stays near hydrostatic."""
     sc = S.still_water_bf()
