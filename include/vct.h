@@ -105,10 +105,22 @@ typedef struct {
                                aggregation multigrid V-cycle on the cell grid (Jacobi damping
                                0.8 / 0.7 and coarse-correction scale 1.3 / 1.8 in 2-D / 3-D,
                                z-only coarsening while the operator's z coupling dominates,
-                               8 coarsest sweeps, up to 96 KB of
-                               shared memory for the small levels; vct_init reads overrides from
-                               the environment: VCT_MG_OMEGA, VCT_MG_KAPPA, VCT_MG_SWEEPS,
-                               VCT_MG_SMEM_KB) */
+                               8 coarsest sweeps, small levels in block 0's shared memory:
+                               96 KB up to 200k particles, 16 KB above, where the solver
+                               also stages operator rows with cp.async and gathers through
+                               L1).  vct_init reads overrides from the environment:
+                               VCT_MG_OMEGA, VCT_MG_KAPPA, VCT_MG_SWEEPS, VCT_MG_SMEM_KB,
+                               VCT_MG_FORM (fly | explicit), VCT_MG_STAGE, VCT_GATHER_L1 */
+    /* Particle regularisation after the position update (Sec. 4.1 applies all
+     * three; 0 switches each off).  It acts in projected space with the
+     * step's neighbour lists, in FP64 in both precisions:
+     *   ds_overlap  dynamic stabilization: pairs closer than (1 - ds_overlap) d0
+     *               are pushed back to that distance within the step (0.4)
+     *   xsph_eps    XSPH velocity smoothing of free-surface particles (5e-3)
+     *   ops_shift   optimized particle shifting, dr^ = -A l |v^| dt grad^C,
+     *               tangential only at the free surface (0.2)
+     * ds_overlap outside [0, 1) or a negative value is VCT_ERR_ARG. */
+    double ops_shift, ds_overlap, xsph_eps;
 } vct_params;
 
 /* Particle state, caller order, DEVICE arrays of n entries (host arrays for
@@ -137,7 +149,7 @@ typedef struct {
 typedef enum {
     VCT_STAGE_LOAD = 0, VCT_STAGE_MAP, VCT_STAGE_SORT, VCT_STAGE_NEIGHBOURS,
     VCT_STAGE_SMOOTHING, VCT_STAGE_PASS1, VCT_STAGE_PASS2, VCT_STAGE_RHS,
-    VCT_STAGE_KRYLOV, VCT_STAGE_CORRECTOR, VCT_STAGE_STORE, VCT_NSTAGES
+    VCT_STAGE_KRYLOV, VCT_STAGE_CORRECTOR, VCT_STAGE_REGULARISE, VCT_STAGE_STORE, VCT_NSTAGES
 } vct_stage;
 
 /* Device buffers (caller order) that vct_step_probe fills for its single

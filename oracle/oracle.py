@@ -30,7 +30,8 @@ class OrcParams(C.Structure):
                                   "alpha_min", "alpha_max", "lam_fs_lo", "lam_fs_hi",
                                   "ppe_rtol")] + [
         (k, C.c_int) for k in ("ppe_max_iter", "smagorinsky", "volume_mode", "neighbour_mode",
-                               "smoothing_mode", "pad_")]
+                               "smoothing_mode", "pad_")] + [
+        (k, C.c_double) for k in ("ops_shift", "ds_overlap", "xsph_eps")]
 
 
 class OrcState(C.Structure):
@@ -66,6 +67,8 @@ def lib():
                                            C.POINTER(OrcState), C.c_int]
         L.orc_step.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy), C.POINTER(OrcState),
                                C.c_int, C.POINTER(OrcProbe), C.POINTER(C.c_int)]
+        L.orc_regularise.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
+                                     C.POINTER(OrcState), C.POINTER(C.c_int32)]
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
@@ -121,6 +124,8 @@ def make_params(sc, neighbour_mode=1, smoothing_mode=1, rtol=1e-13, max_iter=200
     P.volume_mode = int(p["volume_mode"])
     P.neighbour_mode = int(neighbour_mode)
     P.smoothing_mode = int(smoothing_mode)
+    for k in ("ops_shift", "ds_overlap", "xsph_eps"):
+        setattr(P, k, float(p.get(k, 0.0)))
     return P
 
 
@@ -240,6 +245,18 @@ def volume_smoothing(sc, state, mode):
     P = make_params(sc)
     S = state.struct()
     return lib().orc_volume_smoothing(C.byref(P), C.byref(B), C.byref(S), mode)
+
+
+def regularise(sc, state, fs=None, **over):
+    """Particle regularisation alone (dynamic stabilization, XSPH, shifting)
+    on `state` in place, neighbour sets at its positions; fs: free-surface flags."""
+    keep = _Keep()
+    B = make_bathy(sc.bathy, keep)
+    P = make_params(sc, **over)
+    S = state.struct()
+    f = None if fs is None else np.ascontiguousarray(fs, dtype=np.int32)
+    return lib().orc_regularise(C.byref(P), C.byref(B), C.byref(S),
+                                None if f is None else f.ctypes.data_as(C.POINTER(C.c_int32)))
 
 
 def step(sc, state=None, nsteps=1, probe=False, x_test=None, **over):

@@ -24,6 +24,9 @@
  *   walls        no-slip v = 0, pressure Neumann extrapolation Sec. 3.5, Eq. (PNC)
  *   corrector    v = v* - dt/rho J grad^ p; r += dt v          Eqs. (VCT_predictor), (VCT_update)
  *   smoothing    Jbar exchange between neighbours              Sec. 3.6, Eq. (VCT_bar_a)
+ *   regularise   dynamic stabilization, XSPH on free-surface particles and
+ *                optimized particle shifting after the update  Sec. 4.1 (parameters;
+ *                the formulas are restated from the cited methods, see stage_regularise)
  *
  * Readings of points the paper leaves open (each is also listed in the
  * design notes): r_e = 2 l; grad w_ij = -(w'(r)/r) r_ij (gradient w.r.t. r_i,
@@ -68,6 +71,7 @@ typedef struct {
     double rho, nu_k, g, dt, d0, l_over_d0, re_over_l, gamma_over_dt, cv_over_dt, cs, ds;
     double H, H_hat, alpha_min, alpha_max, lam_fs_lo, lam_fs_hi, ppe_rtol;
     int ppe_max_iter, smagorinsky, volume_mode, neighbour_mode, smoothing_mode, pad_;
+    double ops_shift, ds_overlap, xsph_eps;   /* particle regularisation, 0 = off */
 } orc_params;
 
 typedef struct {
@@ -1098,6 +1102,186 @@ int orc_volume_smoothing(const orc_params *P, const orc_bathy *b, orc_state *S, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Particle regularisation after the position update.  Sec. 4.1 stabilises   */
+/* every simulation with optimized particle shifting (shift parameter 0.2),  */
+/* dynamic stabilization (allowed overlap 40 % of the particle diameter) and */
+/* XSPH on free-surface particles (velocity smoothing 5e-3); it gives the    */
+/* parameters only.  Restated here from the cited methods, in projected      */
+/* space (where particles are isotropic with spacing d0), with the step's    */
+/* neighbour sets and the positions after the update:                        */
+/*  DS   (Tsuruta et al.): every pair with |r^_ij| < d_DS = (1 - overlap) d0  */
+/*       is pushed apart so that, moving with the corrected velocities for    */
+/*       one step, it would be d_DS apart: du^_i = -sum mu_ij (d_DS - |r^_ij|) */
+/*       / dt e_ij, e_ij = r^_ij/|r^_ij| (towards j), mu = 1/2 for a fluid j  */
+/*       (equal masses, momentum kept), 1 for a wall or virtual j (fixed);    */
+/*       the velocity gains J^-1 du^ and the position dt J^-1 du^.            */
+/*  XSPH (Monaghan): free-surface particles take                              */
+/*       u_i + eps sum_{j fluid} V0 (u_j - u_i) w(|r^_ij|), the DS-corrected   */
+/*       velocities on both sides.                                            */
+/*  OPS  (Fickian shifting of Lind et al. with the free-surface treatment of  */
+/*       Khayyer et al.): dr^_i = -A l |v^_i| dt grad^C_i, grad^C_i =          */
+/*       sum_{all j} V0 grad w_ij, v^ = J v the projected velocity after XSPH; */
+/*       on free-surface particles only the part tangential to the surface is */
+/*       kept, with the normal of Marrone et al., n = -L grad^C / |L grad^C|,  */
+/*       L = B^-1, B = sum_{all j} V0 (r^_j - r^_i) (x) grad w_ij (no shift if */
+/*       B is singular).                                                      */
+/* The projected displacement dr^ goes back to physical space through the     */
+/* Jacobian at the new position: dx = dx^, dy = dy^, dz = (dz^ - s_x dx^ -    */
+/* s_y dy^)/alpha.  Every particle's correction uses the same inputs (no      */
+/* in-place updates), so the result does not depend on the particle order.  */
+/* ------------------------------------------------------------------------ */
+static void to_phys(int d, const double *met, const double *dh, double *dp)
+{
+    dp[0] = dh[0];
+    if (d == 2) {
+        dp[1] = (dh[1] - met[1] * dh[0]) / met[0];
+    } else {
+        dp[1] = dh[1];
+        dp[2] = (dh[2] - met[1] * dh[0] - met[2] * dh[1]) / met[0];
+    }
+}
+
+static void stage_regularise(const orc_params *P, const orc_bathy *b, orc_state *S, const work_t *W)
+{
+    int n = S->n, d = P->dim;
+    double l = W->l, V0 = W->V0, dt = P->dt;
+    double *xh = malloc(sizeof(double) * (size_t)n * d + 8);
+    double *met = malloc(sizeof(double) * (size_t)n * 7 + 8);
+    double *ud = malloc(sizeof(double) * (size_t)n * 3 + 8);   /* DS-corrected velocity */
+    double *dh = calloc((size_t)n * 3 + 1, 8);                 /* projected displacement */
+    double *un = malloc(sizeof(double) * (size_t)n * 3 + 8);   /* final velocity */
+    for (int i = 0; i < n; ++i) {
+        double y = d == 3 ? S->y[i] : 0.0, zh;
+        metric_at(P, b, S->x[i], y, S->z[i], &zh, met + 7 * i);
+        xh[d * i] = S->x[i];
+        if (d == 3) xh[3 * i + 1] = S->y[i];
+        xh[d * i + d - 1] = zh;
+        for (int c = 0; c < d; ++c) ud[3 * i + c] = vel(S, d, i, c);
+    }
+    /* dynamic stabilization */
+    double dds = (1.0 - P->ds_overlap) * P->d0;
+    if (P->ds_overlap > 0.0) {
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            if (S->type[i] != ORC_FLUID) continue;
+            double du[3] = {0.0, 0.0, 0.0};
+            for (int64_t k = W->row_ptr[i]; k < W->row_ptr[i + 1]; ++k) {
+                int j = W->col[k];
+                double r[3], r2 = 0.0;
+                for (int K = 0; K < d; ++K) {
+                    r[K] = xh[d * j + K] - xh[d * i + K];
+                    r2 += r[K] * r[K];
+                }
+                double rr = sqrt(r2);
+                if (!(rr < dds) || rr == 0.0) continue;
+                double mu = S->type[j] == ORC_FLUID ? 0.5 : 1.0;
+                double f = mu * (dds - rr) / (dt * rr);
+                for (int K = 0; K < d; ++K) du[K] -= f * r[K];
+            }
+            double dv[3];
+            to_phys(d, met + 7 * i, du, dv);
+            for (int c = 0; c < d; ++c) {
+                ud[3 * i + c] += dv[c];
+                dh[3 * i + c] = dt * du[c];
+            }
+        }
+    }
+    /* XSPH on free-surface particles, then optimized particle shifting */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        for (int c = 0; c < d; ++c) un[3 * i + c] = ud[3 * i + c];
+        if (S->type[i] != ORC_FLUID) continue;
+        double gc[3] = {0.0, 0.0, 0.0}, xs[3] = {0.0, 0.0, 0.0}, B[9] = {0.0};
+        for (int64_t k = W->row_ptr[i]; k < W->row_ptr[i + 1]; ++k) {
+            int j = W->col[k];
+            double r[3], r2 = 0.0;
+            for (int K = 0; K < d; ++K) {
+                r[K] = xh[d * i + K] - xh[d * j + K];   /* r^_i - r^_j */
+                r2 += r[K] * r[K];
+            }
+            double rr = sqrt(r2);
+            if (rr == 0.0) continue;
+            if (P->xsph_eps > 0.0 && W->fs[i] && S->type[j] == ORC_FLUID) {
+                double wv = kern_w(rr, l, d);
+                for (int c = 0; c < d; ++c) xs[c] += V0 * (ud[3 * j + c] - ud[3 * i + c]) * wv;
+            }
+            if (P->ops_shift > 0.0) {
+                double dwr = kern_dw(rr, l, d) / rr;
+                for (int K = 0; K < d; ++K) gc[K] += V0 * dwr * r[K];
+                for (int a = 0; a < d; ++a)
+                    for (int c = 0; c < d; ++c) B[a * d + c] -= V0 * dwr * r[a] * r[c];
+            }
+        }
+        if (P->xsph_eps > 0.0 && W->fs[i])
+            for (int c = 0; c < d; ++c) un[3 * i + c] = ud[3 * i + c] + P->xsph_eps * xs[c];
+        if (P->ops_shift > 0.0) {
+            const double *m = met + 7 * i;
+            double vh[3];
+            vh[0] = un[3 * i];
+            if (d == 2) {
+                vh[1] = m[1] * un[3 * i] + m[0] * un[3 * i + 1];
+            } else {
+                vh[1] = un[3 * i + 1];
+                vh[2] = m[1] * un[3 * i] + m[2] * un[3 * i + 1] + m[0] * un[3 * i + 2];
+            }
+            double sp = 0.0;
+            for (int K = 0; K < d; ++K) sp += vh[K] * vh[K];
+            double D = P->ops_shift * l * sqrt(sp) * dt, s[3];
+            for (int K = 0; K < d; ++K) s[K] = -D * gc[K];
+            if (W->fs[i]) {
+                double Li[9], nv[3], nn = 0.0, sn = 0.0;
+                int bad = invert_dxd(d, B, Li);
+                for (int a = 0; a < d && !bad; ++a) {
+                    nv[a] = 0.0;
+                    for (int c = 0; c < d; ++c) nv[a] -= Li[a * d + c] * gc[c];
+                    nn += nv[a] * nv[a];
+                }
+                if (bad || !(nn > 0.0)) {
+                    for (int K = 0; K < d; ++K) s[K] = 0.0;
+                } else {
+                    nn = sqrt(nn);
+                    for (int K = 0; K < d; ++K) {
+                        nv[K] /= nn;
+                        sn += s[K] * nv[K];
+                    }
+                    for (int K = 0; K < d; ++K) s[K] -= sn * nv[K];
+                }
+            }
+            for (int K = 0; K < d; ++K) dh[3 * i + K] += s[K];
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        if (S->type[i] != ORC_FLUID) continue;
+        double dp[3];
+        to_phys(d, met + 7 * i, dh + 3 * i, dp);
+        S->x[i] += dp[0];
+        if (d == 2) {
+            S->z[i] += dp[1];
+            S->u[i] = un[3 * i]; S->w[i] = un[3 * i + 1];
+        } else {
+            S->y[i] += dp[1];
+            S->z[i] += dp[2];
+            S->u[i] = un[3 * i]; S->v[i] = un[3 * i + 1]; S->w[i] = un[3 * i + 2];
+        }
+    }
+    free(xh); free(met); free(ud); free(dh); free(un);
+}
+
+/* Public: regularisation alone on a state, with neighbour sets taken at the
+ * given positions (for its pins). */
+int orc_regularise(const orc_params *P, const orc_bathy *b, orc_state *S, const int32_t *fs)
+{
+    work_t W;
+    memset(&W, 0, sizeof W);
+    stage_geometry(P, b, S, &W);
+    W.fs = (int32_t *)calloc((size_t)S->n + 1, 4);
+    for (int i = 0; i < S->n; ++i) W.fs[i] = fs ? fs[i] : 0;
+    stage_regularise(P, b, S, &W);
+    work_free(&W);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Public: nsteps of the projection scheme (Sec. 3.3 with the VCT equations). */
 /* ------------------------------------------------------------------------ */
 int orc_step(const orc_params *P, const orc_bathy *b, orc_state *S, int nsteps, orc_probe *pr,
@@ -1221,6 +1405,8 @@ int orc_step(const orc_params *P, const orc_bathy *b, orc_state *S, int nsteps, 
                     S->z[i] += P->dt * S->w[i];
                 }
             }
+            if (P->ops_shift > 0.0 || P->ds_overlap > 0.0 || P->xsph_eps > 0.0)
+                stage_regularise(P, b, S, &W);
             for (int i = 0; i < n; ++i)
                 if (S->type[i] == ORC_FLUID && !(isfinite(S->x[i]) && isfinite(S->z[i]) && isfinite(S->p[i])))
                     rc = ORC_ERR_NONFINITE;

@@ -217,6 +217,10 @@ vct_status queue_step(vct_ctx *c, int64_t n, int step, int nsteps, const vct_pro
         }
         { StageTimer t(c, VCT_STAGE_CORRECTOR); launch_corrector(c->P, cur(c), c->W, n, c->st); }
         c->launches += 5;   // pass1, pass2, rhs, krylov, corrector
+        if (regularise_on(c->P)) {
+            StageTimer t(c, VCT_STAGE_REGULARISE);
+            c->launches += launch_regularise(c->P, cur(c), c->W, n, c->st);
+        }
     }
     return VCT_OK;
 }
@@ -256,6 +260,9 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         capacity > (int64_t)INT32_MAX / 4)
         return VCT_ERR_ARG;
     if (bathy->n_gauss < 0 || bathy->n_gauss > VCT_MAX_GAUSS) return VCT_ERR_ARG;
+    if (!(prm->ops_shift >= 0.0) || !(prm->ds_overlap >= 0.0 && prm->ds_overlap < 1.0) ||
+        !(prm->xsph_eps >= 0.0))
+        return VCT_ERR_ARG;
     if (bathy->n_gauss > 0 && (!bathy->amp || !bathy->cx || !bathy->cy || !bathy->width))
         return VCT_ERR_ARG;
     if ((kind == VCT_MAP_E || kind == VCT_MAP_BFE) && !(aspect_ratio > 0)) return VCT_ERR_ARG;
@@ -306,6 +313,9 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     P.lam_lo = prm->lam_fs_lo;
     P.lam_hi = prm->lam_fs_hi;
     P.rtol = prm->krylov_rtol;
+    P.ops_shift = prm->ops_shift;
+    P.ds_overlap = prm->ds_overlap;
+    P.xsph_eps = prm->xsph_eps;
     P.cell_h = P.re;
     P.inv_cell_h = 1.0 / P.cell_h;
     int64_t ncell = 1;
@@ -366,6 +376,12 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.wallrhs = dalloc<double>(c, n, e);
     W.jbar_tmp = dalloc<double>(c, n, e);
     W.adj = dalloc<double>(c, n * (m + d), e);
+    if (prm->ops_shift > 0.0 || prm->ds_overlap > 0.0 || prm->xsph_eps > 0.0) {
+        W.rxh = dalloc<double>(c, n * d, e);
+        W.rmet = dalloc<double>(c, n * 3, e);
+        W.rud = dalloc<double>(c, n * d, e);
+        W.rdh = dalloc<double>(c, n * d, e);
+    }
     W.kx = dalloc<double>(c, n, e);
     W.kr = dalloc<double>(c, n, e);
     W.krh = dalloc<double>(c, n, e);

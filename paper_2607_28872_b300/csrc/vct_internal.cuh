@@ -24,6 +24,7 @@ struct DevParams {
     int nc[3];                // cells per axis (x, y, z); 2-D: y = 1
     int pad1;
     double aspect, rho, nu_k, g, dt, d0, l, inv_l, re, re2, V0, ad;
+    double ops_shift, ds_overlap, xsph_eps;   // particle regularisation (0: off)
     double gamma, cv, cs, ds, H, H_hat, amin, amax, lam_lo, lam_hi, rtol;
     double box_lo[3], cell_h, inv_cell_h;
     double h0, slope_x, slope_y, cos_amp, cos_len;
@@ -41,7 +42,6 @@ struct Part {
                                     // Jacobian, c_trans entries 0 and 3
 };
 
-// Scratch of one step.
 // Slot kk of row i in the pressure-equation ELL arrays.  Slots are kept in
 // blocks of EG consecutive slots per row (EG = 4 in 2-D, 8 in 3-D: the width of
 // the solver's row groups), blocks of all rows one after the other, so the EG
@@ -59,6 +59,7 @@ __host__ __device__ __forceinline__ int64_t ell_at_dim(int dim, int kk, int64_t 
 template <int D>
 __host__ __device__ constexpr int ell_group() { return D == 2 ? 4 : 8; }
 
+// Scratch of one step.
 struct Work {
     int64_t cap;
     int32_t max_nbr;          // ELL slots per particle
@@ -92,6 +93,9 @@ struct Work {
     double *kq0, *kq1;        // preconditioned directions p^, s^
     double *kz0, *kzb;        // V-cycle: first Jacobi step and prolonged correction
     double *adj;              // adjoint scratch: [m + dim] per particle
+    double *rxh, *rmet;       // regularisation: projected position [d] and J, s_x, s_y
+    double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
+                              //   projected displacement [d]
 };
 
 // Coarse levels of the aggregation multigrid: level 1 = the cell grid, level
@@ -142,6 +146,8 @@ bool krylov_mg_fly_default(long long rows);
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly);
 size_t krylov_mg_stage_bytes(int precision, int dim, bool staged);
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+bool regularise_on(const DevParams &P);
+int launch_regularise(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 void launch_sph2_field(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
                        int ncomp, double *grad, double *d2, double *lap, cudaStream_t st);
 void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,

@@ -2753,6 +2753,281 @@ void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
+// Particle regularisation after the position update.  Sec. 4.1 stabilises its
+// simulations with optimized particle shifting (shift parameter A), dynamic
+// stabilization (allowed overlap of the particle diameter) and XSPH on
+// free-surface particles (velocity smoothing eps), and gives only those
+// parameters.  The methods, restated from their published forms, act in
+// projected space with the step's neighbour lists and the updated positions:
+//  * dynamic stabilization: a pair closer than d_DS = (1 - overlap) d0 is
+//    pushed apart so that it would be d_DS apart after one step with the
+//    corrected velocities, du^_i = -sum mu (d_DS - r)/dt e_ij (mu = 1/2 against
+//    a fluid particle, 1 against a wall or virtual one); the velocity gains
+//    J^-1 du^ and the position dt J^-1 du^;
+//  * XSPH: a free-surface particle takes u_i + eps sum_{j fluid} V0 (u_j - u_i) w_ij;
+//  * shifting: dr^_i = -A l |v^_i| dt grad^C_i, grad^C_i = sum_j V0 grad w_ij
+//    over all neighbours, v^ = J v; a free-surface particle keeps only the part
+//    tangential to the surface, whose normal is -L grad^C normalised with
+//    L = B^-1, B = sum_j V0 (r^_j - r^_i) (x) grad w_ij (none if B is singular).
+// Projected displacements return through the Jacobian at the new position
+// (dz = (dz^ - s_x dx^ - s_y dy^)/alpha).  All sums are FP64 in list order; a
+// particle's correction reads only copies made before the kernel writes, so
+// the result does not depend on the thread order.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void reg_to_phys(double J, double sx, double sy, const double *dh, double *dp)
+{
+    dp[0] = dh[0];
+    if (D == 2) {
+        dp[1] = (dh[1] - sx * dh[0]) / J;
+    } else {
+        dp[1] = dh[1];
+        dp[2] = (dh[2] - sx * dh[0] - sy * dh[1]) / J;
+    }
+}
+
+// In-place inverse of a D x D matrix by Gaussian elimination with partial
+// pivoting; false when a pivot falls below 1e-14 of the largest entry.
+template <int D>
+__device__ bool reg_invert(double (&A)[D * D], double (&X)[D * D])
+{
+    double amax = 0.0;
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) amax = fmax(amax, fabs(A[q]));
+    if (!(amax > 0.0)) return false;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) X[r * D + c] = r == c ? 1.0 : 0.0;
+    for (int k = 0; k < D; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < D; ++r)
+            if (fabs(A[r * D + k]) > fabs(A[piv * D + k])) piv = r;
+        if (!(fabs(A[piv * D + k]) > 1e-14 * amax)) return false;
+        if (piv != k)
+            for (int c = 0; c < D; ++c) {
+                double t = A[k * D + c]; A[k * D + c] = A[piv * D + c]; A[piv * D + c] = t;
+                t = X[k * D + c]; X[k * D + c] = X[piv * D + c]; X[piv * D + c] = t;
+            }
+        for (int r = k + 1; r < D; ++r) {
+            const double f = A[r * D + k] / A[k * D + k];
+            for (int c = k; c < D; ++c) A[r * D + c] -= f * A[k * D + c];
+            for (int c = 0; c < D; ++c) X[r * D + c] -= f * X[k * D + c];
+        }
+    }
+    for (int k = D - 1; k >= 0; --k)
+        for (int c = 0; c < D; ++c) {
+            double s = X[k * D + c];
+            for (int j = k + 1; j < D; ++j) s -= A[k * D + j] * X[j * D + c];
+            X[k * D + c] = s / A[k * D + k];
+        }
+    return true;
+}
+
+// Projected positions and metric at the updated positions; velocity copies.
+template <int D>
+__global__ void __launch_bounds__(128) k_reg_geom(DevParams P, Part c, Work W, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    double zh, J, sx, sy, c0, c3;
+    const double y = D == 3 ? c.y[i] : 0.0;
+    map_metric(P, c.x[i], y, c.z[i], zh, J, sx, sy, c0, c3);
+    W.rxh[i] = c.x[i];
+    if (D == 3) W.rxh[cap + i] = y;
+    W.rxh[(D - 1) * cap + i] = zh;
+    W.rmet[i] = J;
+    W.rmet[cap + i] = sx;
+    W.rmet[2 * cap + i] = sy;
+    W.rud[i] = c.u[i];
+    if (D == 3) W.rud[cap + i] = c.v[i];
+    W.rud[(D - 1) * cap + i] = c.w[i];
+#pragma unroll
+    for (int K = 0; K < D; ++K) W.rdh[K * cap + i] = 0.0;
+}
+
+template <int D>
+__device__ __forceinline__ void reg_load(const Work &W, int i, double *x)
+{
+#pragma unroll
+    for (int K = 0; K < D; ++K) x[K] = W.rxh[K * W.cap + i];
+}
+
+// Dynamic stabilization: corrected velocity copy and projected displacement.
+template <int D>
+__global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || c.type[i] != FLUID) return;
+    const int64_t cap = W.cap;
+    const double dds = (1.0 - P.ds_overlap) * P.d0;
+    double xi[D], du[D];
+    reg_load<D>(W, i, xi);
+#pragma unroll
+    for (int K = 0; K < D; ++K) du[K] = 0.0;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        const int j = W.nbr[(int64_t)k * cap + i];
+        double xj[D], r[D], r2 = 0.0;
+        reg_load<D>(W, j, xj);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xj[K] - xi[K];
+            r2 += r[K] * r[K];
+        }
+        const double rr = sqrt(r2);
+        if (!(rr < dds) || rr == 0.0) continue;
+        const double f = (c.type[j] == FLUID ? 0.5 : 1.0) * (dds - rr) / (P.dt * rr);
+#pragma unroll
+        for (int K = 0; K < D; ++K) du[K] -= f * r[K];
+    }
+    double dv[D];
+    reg_to_phys<D>(W.rmet[i], W.rmet[cap + i], W.rmet[2 * cap + i], du, dv);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        W.rud[K * cap + i] += dv[K];
+        W.rdh[K * cap + i] = P.dt * du[K];
+    }
+}
+
+// XSPH on free-surface particles, shifting, and the final write of the state.
+template <int D>
+__global__ void __launch_bounds__(128) k_reg_apply(DevParams P, Part c, Work W, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || c.type[i] != FLUID) return;
+    const int64_t cap = W.cap;
+    const double inv_l = P.inv_l, ad = P.ad, V0 = P.V0;
+    const bool fsi = W.fs[i] != 0;
+    const bool do_x = P.xsph_eps > 0.0 && fsi, do_s = P.ops_shift > 0.0;
+    double xi[D], ui[D], gc[D], xs[D], B[D * D];
+    reg_load<D>(W, i, xi);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        ui[K] = W.rud[K * cap + i];
+        gc[K] = 0.0;
+        xs[K] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) B[q] = 0.0;
+    const int cnt = (do_x || do_s) ? W.nbr_cnt[i] : 0;
+    for (int k = 0; k < cnt; ++k) {
+        const int j = W.nbr[(int64_t)k * cap + i];
+        double xj[D], r[D], r2 = 0.0;
+        reg_load<D>(W, j, xj);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xi[K] - xj[K];
+            r2 += r[K] * r[K];
+        }
+        const double rr = sqrt(r2);
+        if (rr == 0.0) continue;
+        double w, dw;
+        kern_wdw<double>(rr, inv_l, ad, w, dw);
+        if (do_x && c.type[j] == FLUID) {
+#pragma unroll
+            for (int K = 0; K < D; ++K) xs[K] += V0 * (W.rud[K * cap + j] - ui[K]) * w;
+        }
+        if (do_s) {
+            const double dwr = dw / rr;
+#pragma unroll
+            for (int K = 0; K < D; ++K) gc[K] += V0 * dwr * r[K];
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) B[a * D + b] -= V0 * dwr * r[a] * r[b];
+        }
+    }
+    double un[D], dh[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        un[K] = do_x ? ui[K] + P.xsph_eps * xs[K] : ui[K];
+        dh[K] = W.rdh[K * cap + i];
+    }
+    if (do_s) {
+        const double J = W.rmet[i], sx = W.rmet[cap + i], sy = W.rmet[2 * cap + i];
+        double vh[D];
+        vh[0] = un[0];
+        if (D == 2) {
+            vh[1] = sx * un[0] + J * un[1];
+        } else {
+            vh[1] = un[1];
+            vh[2] = sx * un[0] + sy * un[1] + J * un[2];
+        }
+        double sp = 0.0;
+#pragma unroll
+        for (int K = 0; K < D; ++K) sp += vh[K] * vh[K];
+        const double Df = P.ops_shift * P.l * sqrt(sp) * P.dt;
+        double s[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) s[K] = -Df * gc[K];
+        if (fsi) {
+            double Li[D * D], nv[D], nn = 0.0;
+            const bool ok = reg_invert<D>(B, Li);
+            if (ok) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    nv[a] = 0.0;
+#pragma unroll
+                    for (int b = 0; b < D; ++b) nv[a] -= Li[a * D + b] * gc[b];
+                    nn += nv[a] * nv[a];
+                }
+            }
+            if (!ok || !(nn > 0.0)) {
+#pragma unroll
+                for (int K = 0; K < D; ++K) s[K] = 0.0;
+            } else {
+                nn = sqrt(nn);
+                double sn = 0.0;
+#pragma unroll
+                for (int K = 0; K < D; ++K) {
+                    nv[K] /= nn;
+                    sn += s[K] * nv[K];
+                }
+#pragma unroll
+                for (int K = 0; K < D; ++K) s[K] -= sn * nv[K];
+            }
+        }
+#pragma unroll
+        for (int K = 0; K < D; ++K) dh[K] += s[K];
+    }
+    double dp[D];
+    reg_to_phys<D>(W.rmet[i], W.rmet[cap + i], W.rmet[2 * cap + i], dh, dp);
+    c.x[i] += dp[0];
+    c.u[i] = un[0];
+    if (D == 3) {
+        c.y[i] += dp[1];
+        c.v[i] = un[1];
+    }
+    c.z[i] += dp[D - 1];
+    c.w[i] = un[D - 1];
+    if (!(isfinite(c.x[i]) && isfinite(c.z[i]) && isfinite(un[0]) && isfinite(un[D - 1])))
+        set_error(W.status, VCT_ERR_NONFINITE, i);
+}
+
+bool regularise_on(const DevParams &P)
+{
+    return P.ops_shift > 0.0 || P.ds_overlap > 0.0 || P.xsph_eps > 0.0;
+}
+
+int launch_regularise(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    if (!regularise_on(P)) return 0;
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        k_reg_geom<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.ds_overlap > 0.0) k_reg_ds<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_reg_apply<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    } else {
+        k_reg_geom<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.ds_overlap > 0.0) k_reg_ds<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_reg_apply<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    }
+    return P.ds_overlap > 0.0 ? 3 : 2;
+}
+
+// ---------------------------------------------------------------------------
 // sph2_derivatives: corrected gradient + SPH(2) of caller fields
 // ---------------------------------------------------------------------------
 template <int D, typename R>

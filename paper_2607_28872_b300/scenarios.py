@@ -55,7 +55,15 @@ DEFAULT_PARAMS = dict(
     smagorinsky=1,
     precision=0,         # 0 = FP64, 1 = mixed FP32 sums / FP64 solve
     volume_mode=2,       # 0 = Condition A, 1 = Condition B, 2 = Condition C
+    ops_shift=0.0,       # particle regularisation, off unless a workload sets it
+    ds_overlap=0.0,
+    xsph_eps=0.0,
 )
+
+# Sec. 4.1: every simulation of the paper runs with optimized particle shifting
+# (shift parameter 0.2), dynamic stabilization (40 % allowed overlap) and XSPH on
+# free-surface particles (5e-3).  The wave workloads use them.
+REGULARISATION = dict(ops_shift=0.2, ds_overlap=0.4, xsph_eps=5.0e-3)
 
 
 @dataclass
@@ -293,6 +301,7 @@ def solitary_sigma(d0=1.0 / 90.0, L=10.0, depth=0.5, bump=0.3, bump_x=5.0, bump_
     bathy = Bathymetry(amp=[bump], cx=[bump_x], cy=[0.0], width=[bump_s])
     prm = dict(d0=d0, H=depth, H_hat=depth, dt=1.0e-3, precision=precision,
                alpha_min=1.0, alpha_max=4.0)
+    prm.update(REGULARISATION)
     prm.update(kw)
     eta, vel = solitary_wave(wave * depth, depth, x0, prm.get("g", 9.81))
     surf = lambda x, y: depth + eta(x)
@@ -301,23 +310,26 @@ def solitary_sigma(d0=1.0 / 90.0, L=10.0, depth=0.5, bump=0.3, bump_x=5.0, bump_
 
 
 def beach_bfe_3d(d0=0.043, L=20.0, W=4.0, depth=1.0, slope=0.05, aspect=4.0, wave=0.1,
-                 x0=3.0, seed=0, precision=1, **kw):
+                 x0=3.0, seed=0, precision=1, jitter=0.0, **kw):
     """3-D BFE-SPH solitary wave on a 1:20 beach, 20 x 4 m basin, depth 1 m -> 0,
-    ellipsoidal particles with aspect ratio 4.  Columns with fewer than three
-    projected layers are left dry (a one- or two-layer wedge has no moment
-    matrix).  The Smagorinsky model is off: at aspect 4 its eddy viscosity,
-    applied through the explicit viscous term with the ill-conditioned SPH(2)
-    second derivatives of free-surface particles, grows without bound within a
-    few steps (both the CUDA path and the oracle), unless the particle
-    regularisation the paper cites (not part of this path) damps it."""
+    ellipsoidal particles with aspect ratio 4, on a regular projected lattice
+    (a random jitter's density errors drive the stabilisation term of the
+    pressure equation hard at this aspect ratio).  Columns with fewer than
+    three projected layers are left dry (a one- or two-layer wedge has no
+    moment matrix).  Particle regularisation is on (Sec. 4.1).  The
+    Smagorinsky model is off: at aspect 4 its eddy viscosity, applied through
+    the explicit viscous term with the ill-conditioned SPH(2) second
+    derivatives of free-surface particles, grows without bound within a few
+    steps (both the CUDA path and the oracle)."""
     bathy = Bathymetry(slope_x=slope)
     prm = dict(d0=d0, H=depth, H_hat=depth * aspect, dt=1.0e-3, precision=precision,
                smagorinsky=0)
+    prm.update(REGULARISATION)
     prm.update(kw)
     eta, vel = solitary_wave(wave, depth, x0, prm.get("g", 9.81))
     surf = lambda x, y: depth + eta(x)
     return build_tank("beach_bfe_3d", 3, "BFE", aspect, bathy, prm, L, W, surface=surf,
-                      velocity=vel, seed=seed, min_layers=3)
+                      velocity=vel, seed=seed, min_layers=3, jitter=jitter)
 
 
 def random_bumps(rng, n, amp_lo, amp_hi, x_lo, x_hi, width, depth, min_depth):
@@ -358,6 +370,7 @@ def ensemble(n_scen=64, seed=2, precision=1, **kw):
         d0 = math.sqrt(5.0 / ns)
         bathy = random_bumps(rng, 4, 0.02, 0.2, 1.0, 9.0, 0.25, 0.5, 0.2)
         prm = dict(d0=d0, H=0.5, H_hat=0.5, dt=1.0e-3, precision=precision)
+        prm.update(REGULARISATION)
         prm.update(kw)
         eta, vel = solitary_wave(0.05, 0.5, 2.0, 9.81)
         out.append(build_tank(f"ensemble_{s}", 2, "SIGMA", 1.0, bathy, prm, 10.0,

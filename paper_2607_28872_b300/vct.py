@@ -43,7 +43,8 @@ class vct_params(C.Structure):
                                   "krylov_rtol")] + [
         ("krylov_max_iter", C.c_int32), ("smagorinsky", C.c_int32), ("precision", C.c_int32),
         ("volume_mode", C.c_int32), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
-        ("max_neighbours", C.c_int32), ("preconditioner", C.c_int32)]
+        ("max_neighbours", C.c_int32), ("preconditioner", C.c_int32),
+        ("ops_shift", C.c_double), ("ds_overlap", C.c_double), ("xsph_eps", C.c_double)]
 
 
 class vct_state(C.Structure):
@@ -59,7 +60,7 @@ class vct_stats(C.Structure):
 
 
 STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "rhs", "krylov",
-          "corrector", "store")
+          "corrector", "regularise", "store")
 
 
 class vct_probe(C.Structure):
@@ -161,6 +162,8 @@ def make_params(sc, **over):
         P.box_hi[k] = float(sc.box_hi[k])
     P.max_neighbours = int(p.get("max_neighbours", 0))
     P.preconditioner = int(p.get("preconditioner", 1))
+    for k in ("ops_shift", "ds_overlap", "xsph_eps"):
+        setattr(P, k, float(p.get(k, 0.0)))
     return P
 
 

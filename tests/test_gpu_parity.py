@@ -189,6 +189,29 @@ def test_step_parity_sigma_solitary_mixed(vct):
     _probe_compare(vct, S.solitary_sigma(), 1, 1e-5, 1e-5)
 
 
+# Particle regularisation on (dynamic stabilization, XSPH, shifting; Sec. 4.1):
+# a jitter of 0.35 d0 puts pairs inside the stabilization distance 0.6 d0.
+REG = [
+    ("sigma2d_reg", lambda: S.small_tank(dim=2, kind="SIGMA", L=0.41, H=0.1, d0=0.01, seed=6,
+                                         with_wave=True, jitter=0.35, **S.REGULARISATION)),
+    ("bfe3d_reg", lambda: S.small_tank(dim=3, kind="BFE", L=0.17, W=0.09, H=0.06, d0=0.01,
+                                       seed=7, aspect=2.0, jitter=0.35, **S.REGULARISATION)),
+]
+
+
+@pytest.mark.parametrize("precision,tol,band", [(0, 1e-12, 1e-9), (1, 1e-5, 1e-5)],
+                         ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name,make", REG, ids=[r[0] for r in REG])
+def test_step_parity_regularised(vct, name, make, precision, tol, band):
+    from scipy.spatial import cKDTree
+    sc = make()
+    xh, _ = O.projected(sc)
+    pts = np.asarray(xh).T if np.asarray(xh).shape[0] == sc.dim else np.asarray(xh)
+    dmin, _ = cKDTree(pts).query(pts, k=2)
+    assert dmin[:, 1].min() < 0.6 * sc.params["d0"]       # stabilization is exercised
+    _probe_compare(vct, sc, precision, tol, band)
+
+
 # The multigrid solver has two forms: V-cycle inputs formed on the fly (systems up
 # to 200k unknowns) and kept as vectors with cp.async-staged rows (larger ones).
 # VCT_MG_FORM forces the large-system form on the small cases.
