@@ -70,6 +70,18 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes (read + write) of the dominant kernel, k_krylov_mg, from one ncu capture of
+# its current version in the mixed form (summaries under profiles/).  The 2-D wave is
+# L2-resident: bytes per launch.  The 3-D beach was captured on its 8 x 1.6 m slice and
+# its traffic grows with rows x iterations: bytes per fluid particle per iteration.
+NCU_TRAFFIC = {
+    "sigma_solitary": ("per_launch", 9.73e6, "profiles/k_krylov_mg_fly_sigma_solitary_42k.md"),
+    "beach_bfe_3d": ("per_unit", 4366.0, "profiles/k_krylov_mg_staged_beach_bfe_3d_540k.md"),
+    "beach_bfe_3d_slice": ("per_unit", 4366.0,
+                           "profiles/k_krylov_mg_staged_beach_bfe_3d_540k.md"),
+}
+
+
 def workload(precision=1, name="sigma_solitary"):
     from paper_2607_28872_b300 import scenarios as S
     if name == "still_water_bf":
@@ -90,22 +102,30 @@ def run_ensemble(args):
     nf = sum(sc.n_fluid for sc in scs)
     solvers = [vct.Solver(sc) for sc in scs]
     states = [vct.DeviceState(sc) for sc in scs]
-    vct.vct_batch_step(solvers, states, max(args.warmup, 1))
+    # every scenario is a wave with the 2-D wave's stable horizon: time at most 100 steps
+    steps, warmup = min(args.steps, 100), max(args.warmup, 3)
+    vct.vct_batch_step(solvers, states, warmup)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
     e0.record()
-    stats = vct.vct_batch_step(solvers, states, args.steps)
+    stats = vct.vct_batch_step(solvers, states, steps)
     e1.record()
     e1.synchronize()
+    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    print(json.dumps({"metric": METRIC, "value": nf * args.steps / (ms / 1e3), "unit": UNIT,
-                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": ms / args.steps, "higher_is_better": True,
+    print(json.dumps({"metric": METRIC, "value": nf * steps / (ms / 1e3), "unit": UNIT,
+                      "n_gpus": 1, "steps": steps, "warmup": warmup,
+                      "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+                      "data": "synthetic",
                       "config": {"workload": WORKLOADS["ensemble"], "scenarios": len(scs),
-                                 "n_fluid_total": nf},
-                      "krylov_iters_per_step": sum(s.krylov_iters_total for s in stats) / args.steps,
-                      "dtype": "f32+f64" if args.precision == 1 else "f64"}), flush=True)
+                                 "n_fluid_total": nf, "l2": "not flushed (~3 GB working set)"},
+                      "krylov_iters_per_step": sum(s.krylov_iters_total for s in stats) / steps,
+                      "gpu_launches": int(sum(s.kernel_launches for s in stats)),
+                      "dtype": "f32+f64" if args.precision == 1 else "f64", "clocks": clk}),
+          flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -287,9 +307,15 @@ def run_ours(args):
         per_launch = stage_bytes(name, sc.n, n_fluid, sc.dim, rows, nnz, 20 if sc.dim == 2 else 56)
     avg_ms = ms / max(cnt, 1)
     achieved = per_launch / (avg_ms / 1e3) / 1e9 if per_launch else None
+    traffic, traffic_src = None, None
+    tr = NCU_TRAFFIC.get(args.workload)
+    if tr and name == "krylov" and args.precision == 1:
+        kind, val, traffic_src = tr
+        traffic = val if kind == "per_launch" else val * n_fluid * (iters / max(cnt, 1))
     roof = {"kernel": {"krylov": "k_krylov_mg"}.get(name, name), "bound": "hbm",
             "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+            "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+            "traffic_source": traffic_src,
             "peak_source": "measured" if peaks else "fallback",
             "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": per_launch,
             "note": ("multigrid-preconditioned BiCGSTAB, ~22 grid-barrier phases per iteration; "

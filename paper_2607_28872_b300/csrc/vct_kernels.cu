@@ -46,6 +46,14 @@ __device__ __forceinline__ void set_error(int32_t *status, int code, int idx)
     if (atomicCAS(status, 0, code) == 0) status[1] = idx;
 }
 
+// A step kernel does nothing once an earlier kernel of the same call has
+// recorded an error: the state is then invalid, the call returns the error
+// and writes nothing back, and later steps queued in the call become no-ops.
+__device__ __forceinline__ bool step_failed(const int32_t *status)
+{
+    return *(const volatile int32_t *)status != 0;
+}
+
 // Bottom elevation and derivatives h, h_x, h_y, h_xx, h_yy.
 __device__ void bathy(const DevParams &P, double x, double y, double h[5])
 {
@@ -359,6 +367,7 @@ __device__ __forceinline__ int cell_coord(const DevParams &P, double xh, int axi
 
 __global__ void k_map_key(DevParams P, Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double zh, J, sx, sy, c0, c3;
@@ -473,6 +482,7 @@ static void exclusive_scan(const int32_t *in, T *out, T *tmp, int64_t m, cudaStr
 
 __global__ void k_scatter(Work W, const Part c, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int key = W.key[i];
@@ -483,6 +493,7 @@ __global__ void k_scatter(Work W, const Part c, int n)
 // Within each cell, order particles by caller index (deterministic layout).
 __global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
 {
+    if (step_failed(W.status)) return;
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= ncell) return;
     int a = W.cell_start[cell], b = W.cell_start[cell + 1];
@@ -500,6 +511,7 @@ __global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
 
 __global__ void k_reorder(const Part c, Part a, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int s = W.perm[i];
@@ -528,6 +540,7 @@ void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cuda
 template <int D>
 __global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double xi[3];
@@ -626,6 +639,7 @@ __global__ void k_csr_fill(const Part c, Work W, int n, const int64_t *row_ptr, 
 template <int D>
 __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double jb = c.jbar[i];
@@ -664,6 +678,7 @@ void launch_smoothing(const DevParams &P, Part cur, Work W, int64_t n, cudaStrea
 template <int D, typename R>
 __global__ void __launch_bounds__(128) k_pass1(DevParams P, const Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     constexpr int M = D == 2 ? 3 : 6;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -872,6 +887,7 @@ template <int D, typename R>
 __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W, int n,
                                                int predictor)
 {
+    if (step_failed(W.status)) return;
     constexpr int M = D == 2 ? 3 : 6;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1124,6 +1140,7 @@ void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor
 template <int D, typename R>
 __global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t cap = W.cap;
@@ -1409,6 +1426,7 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
                                                double inner_floor, int32_t *iters_out,
                                                double *resid_out)
 {
+    if (step_failed(W.status)) return;
     const unsigned nb = gridDim.x;
     const int lg = threadIdx.x & (G - 1);
     const bool lead = lg == 0;
@@ -1651,6 +1669,7 @@ __device__ __forceinline__ int stencil_index(int dx, int dy, int dz)
 template <int D>
 __global__ void k_mg_level1(Work W, MG M, int mixed)
 {
+    if (step_failed(W.status)) return;
     constexpr int S = D == 2 ? 9 : 27;
     const int N = M.n[1];
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1690,6 +1709,7 @@ __global__ void k_mg_level1(Work W, MG M, int mixed)
 template <int D>
 __global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from level l
 {
+    if (step_failed(W.status)) return;
     constexpr int S = D == 2 ? 9 : 27;
     const int Nc = M.n[l + 1], Nf = M.n[l];
     const int Ic = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1734,6 +1754,7 @@ __global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from lev
 
 __global__ void k_mg_dsc(Work W, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     W.mg_dsc[i] = (W.pcnt[i] >= 0 && W.diag[i] != 0.0) ? (float)(1.0 / W.diag[i]) : 0.f;
@@ -2149,6 +2170,7 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
                                                   double inner_floor, int32_t *iters_out,
                                                   double *resid_out)
 {
+    if (step_failed(W.status)) return;
     const unsigned nb = gridDim.x;
     const int lg = threadIdx.x & (G - 1);
     const bool lead = lg == 0;
@@ -2425,6 +2447,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
                                                   double inner_floor, int32_t *iters_out,
                                                   double *resid_out)
 {
+    if (step_failed(W.status)) return;
     const unsigned nb = gridDim.x;
     const int lg = threadIdx.x & (G - 1);
     const bool lead = lg == 0;
@@ -2672,6 +2695,7 @@ int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nbl
 template <int D, typename R>
 __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (c.type[i] != FLUID) return;
@@ -2828,6 +2852,7 @@ __device__ bool reg_invert(double (&A)[D * D], double (&X)[D * D])
 template <int D>
 __global__ void __launch_bounds__(128) k_reg_geom(DevParams P, Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t cap = W.cap;
@@ -2858,6 +2883,7 @@ __device__ __forceinline__ void reg_load(const Work &W, int i, double *x)
 template <int D>
 __global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || c.type[i] != FLUID) return;
     const int64_t cap = W.cap;
@@ -2895,6 +2921,7 @@ __global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int
 template <int D>
 __global__ void __launch_bounds__(128) k_reg_apply(DevParams P, Part c, Work W, int n)
 {
+    if (step_failed(W.status)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || c.type[i] != FLUID) return;
     const int64_t cap = W.cap;

@@ -360,9 +360,10 @@ def ensemble_sizes(n_scen=64, lo=5e3, hi=2e5, seed=2):
     return [int(round(math.exp(v))) for v in rng.uniform(math.log(lo), math.log(hi), n_scen)]
 
 
-def ensemble(n_scen=64, seed=2, precision=1, **kw):
+def ensemble(n_scen=64, seed=2, precision=1, jitter=0.0, **kw):
     """64 2-D sigma scenarios, particle counts log-uniform 5e3..2e5 (seed 2),
-    d0 = sqrt(5 / N_s) on a 10 m x 0.5 m projected channel, 4 random bumps each."""
+    d0 = sqrt(5 / N_s) on a 10 m x 0.5 m projected channel, 4 random bumps each,
+    regular projected lattice and particle regularisation as the solitary wave."""
     sizes = ensemble_sizes(n_scen, seed=seed)
     rng = np.random.default_rng(seed + 1000)
     out = []
@@ -374,7 +375,8 @@ def ensemble(n_scen=64, seed=2, precision=1, **kw):
         prm.update(kw)
         eta, vel = solitary_wave(0.05, 0.5, 2.0, 9.81)
         out.append(build_tank(f"ensemble_{s}", 2, "SIGMA", 1.0, bathy, prm, 10.0,
-                              surface=lambda x, y: 0.5 + eta(x), velocity=vel, seed=seed + s))
+                              surface=lambda x, y: 0.5 + eta(x), velocity=vel, seed=seed + s,
+                              jitter=jitter))
     return out
 
 
