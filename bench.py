@@ -67,6 +67,8 @@ WORKLOADS = {
     "beach_bfe_3d_slice": ("3-D BFE solitary wave, 8 x 1.6 m slice of the 1:20 beach (depth 1 -> 0.6 m), "
                            "aspect 4, d0=0.043 m (profiling size)"),
     "ensemble": "sigma-SPH ensemble, particle counts log-uniform 5e3-2e5 (seed 2), 4 bumps each",
+    "adjoint": ("2-D sigma channel 10 m, flat 0.5 m + 16 random Gaussian bumps (seed 1), d0=0.01 m, "
+                "adjoint of the SPH(2) derivative operator"),
 }
 
 
@@ -91,6 +93,49 @@ def workload(precision=1, name="sigma_solitary"):
     if name == "beach_bfe_3d_slice":
         return S.beach_bfe_3d(L=8.0, W=1.6, precision=precision)
     return S.solitary_sigma(precision=precision)
+
+
+def run_adjoint(args):
+    """Adjoint/forward time of the SPH(2) derivative operator on the 2-D adjoint
+    workload (sigma channel, flat 0.5 m + 16 random bumps, ~53k fluid): the
+    forward call (neighbours, corrected gradient, moment solves, derivatives of
+    three fields) against its adjoint (sph2_derivatives_backward, all three
+    outputs carrying adjoints).  Not the headline line."""
+    import torch
+    from paper_2607_28872_b300 import scenarios as S
+    from paper_2607_28872_b300 import vct
+    sc = S.adjoint_sigma(precision=args.precision)
+    solver = vct.Solver(sc)
+    state = vct.DeviceState(sc)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    phi = torch.randn((3, sc.n), dtype=torch.float64, device="cuda", generator=g)
+    gb, db, lb = solver.sph2_derivatives(state, phi)
+    gb, db, lb = torch.randn_like(gb), torch.randn_like(db), torch.randn_like(lb)
+
+    def timed(fn, k):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k = min(args.steps, 50)
+    fwd = timed(lambda: solver.sph2_derivatives(state, phi), k)
+    bwd = timed(lambda: solver.sph2_derivatives_backward(state, gb, db, lb), k)
+    print(json.dumps({"metric": "adjoint/forward time, SPH(2) derivative operator",
+                      "value": bwd / fwd, "unit": "x", "higher_is_better": False,
+                      "forward_ms": fwd, "backward_ms": bwd, "calls": k, "n_gpus": 1,
+                      "data": "synthetic",
+                      "dtype": "f32+f64" if args.precision == 1 else "f64",
+                      "config": {"workload": WORKLOADS["adjoint"], "n_fluid": sc.n_fluid,
+                                 "fields": 3},
+                      "scope": "operator adjoint only; the checkpointed full-step adjoint is "
+                               "not built"}), flush=True)
 
 
 def run_ensemble(args):
@@ -411,6 +456,8 @@ def main():
         run_reference(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -248,8 +248,10 @@ vct_status vct_map_backward(vct_ctx *ctx, const vct_state *state, const double *
  * map + cell sort, neighbours, Jbar smoothing (sigma, volume_mode 2),
  * corrected gradients, free surface, eddy viscosity, SPH(2) predictor,
  * pressure equation with wall Neumann extrapolation (Eq. PNC), BiCGSTAB,
- * corrector and position update.  Device arrays, updated in place on success.
- * out (host, may be NULL) receives solve statistics. */
+ * corrector and position update, then the particle regularisation of
+ * vct_params when on.  Device arrays, updated in place on success; on an
+ * error the state is left as it was and the steps after the failing one do
+ * no work.  out (host, may be NULL) receives solve statistics. */
 vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *out);
 
 /* Ensemble: advance n_scen independent scenarios (one context and one device
