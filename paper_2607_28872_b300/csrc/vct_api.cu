@@ -496,6 +496,8 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         if (getenv("VCT_MG_OMEGA")) M.omega = (float)atof(getenv("VCT_MG_OMEGA"));
         if (getenv("VCT_MG_KAPPA")) M.kappa = (float)atof(getenv("VCT_MG_KAPPA"));
         if (getenv("VCT_MG_SWEEPS")) M.coarse_sweeps = atoi(getenv("VCT_MG_SWEEPS"));
+        M.presmooth = 1;
+        if (getenv("VCT_MG_PRESMOOTH")) M.presmooth = atoi(getenv("VCT_MG_PRESMOOTH"));
         long long pos = 0;
         for (int q = 1; q <= M.L; ++q) {
             M.offA[q] = pos;

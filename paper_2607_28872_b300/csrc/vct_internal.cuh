@@ -108,6 +108,7 @@ struct MG {
     int first_local;     // first level processed by block 0 alone
     int S;               // stencil size, 9 (2-D) or 27 (3-D)
     int coarse_sweeps;   // Jacobi sweeps on the coarsest level
+    int presmooth;       // 1: V(1,1); 0: V(0,1), no fine pre-smoothing (on-the-fly form)
     float omega, kappa;  // Jacobi damping and coarse-correction scale
     int n[MG_MAXL + 1];
     int dims[MG_MAXL + 1][3];

@@ -2351,8 +2351,9 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
 }
 
 // z_out = M^-1 v for the fine vector given on the fly by in(j).  own(i) runs once
-// for every unknown row in the first phase (lane 0 of the row's group), before
-// any phase writes z_out.  Returns false if a grid barrier timed out.
+// for every unknown row in the first phase (lane 0 of the row's group, or the
+// cell's thread without pre-smoothing), before any phase writes z_out; it must
+// not write what in(j) reads.  Returns false if a grid barrier timed out.
 template <typename T, typename CT, int G, int NS, int D, typename In, typename Own>
 __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, Own own, T *zout,
                        int lg, bool lead, int g0, int ngroups, int gtid, int gthreads)
@@ -2360,13 +2361,15 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
     const unsigned nb = gridDim.x;
     const float om = M.omega, kap = M.kappa;
     T *r0 = (T *)W.kr0;
-    // D0: fine residual of one Jacobi step from zero, r0 = v - A (om D^-1 v)
+    const bool pre = M.presmooth != 0;
+    // D0 (V(1,1) only): fine residual of one Jacobi step from zero, r0 = v - A (om D^-1 v)
+    if (pre) {
     for (int i = g0; i < n; i += ngroups) {
-        const int pc = W.pcnt[i];
-        if (pc < 0) continue;
-        T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) {
+        int pc;
+        T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, [&](int j) {
             return (T)om * in(j) * (T)__ldcg(W.mg_dsc + j);
         });
+        if (pc < 0) continue;
         acc = group_sum<G>(acc);
         if (lead) {
             own(i);
@@ -2375,14 +2378,23 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
         }
     }
     if (!grid_barrier(W.bar, nb, W.status)) return false;
-    // D1: restriction to the cells, one Jacobi step from zero on level 1
+    }
+    // D1: restriction to the cells (of r0, or of v itself without pre-smoothing,
+    // where own(i) runs here instead), one Jacobi step from zero on level 1
     {
         const LV c = lv_global(W, M, 1);
         for (int I = gtid; I < c.n; I += gthreads) {
             float bs = 0.f;
             const int a = W.cell_start[I], b = W.cell_start[I + 1];
-            for (int i = a; i < b; ++i)
-                if (W.pcnt[i] >= 0) bs += (float)__ldcg(r0 + i);
+            for (int i = a; i < b; ++i) {
+                if (W.pcnt[i] < 0) continue;
+                if (pre) {
+                    bs += (float)__ldcg(r0 + i);
+                } else {
+                    own(i);
+                    bs += (float)in(i);
+                }
+            }
             c.b[I] = bs;
             c.z[I] = om * bs * c.dinv[I];
         }
@@ -2424,13 +2436,14 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
     }
     // U0: prolongation from the cells + one damped Jacobi step on the fine level
     const float *zu1 = W.mg_pool + M.offv[1] + 3 * M.n[1];
+    auto zb = [&](int j) -> T {
+        const T zc = (T)kap * (T)__ldcg(zu1 + W.cellid[j]);
+        return pre ? (T)om * in(j) * (T)__ldcg(W.mg_dsc + j) + zc : zc;
+    };
     for (int i = g0; i < n; i += ngroups) {
-        const int pc = W.pcnt[i];
+        int pc;
+        T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, zb);
         if (pc < 0) continue;
-        auto zb = [&](int j) -> T {
-            return (T)om * in(j) * (T)__ldcg(W.mg_dsc + j) + (T)kap * (T)__ldcg(zu1 + W.cellid[j]);
-        };
-        T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, zb);
         acc = group_sum<G>(acc);
         if (lead) {
             const T zi = zb(i);
@@ -2466,9 +2479,9 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
     for (int outer = 0;; ++outer) {
         double part[2] = {0.0, 0.0};
         for (int i = g0; i < n; i += ngroups) {
-            const int pc = W.pcnt[i];
+            int pc;
+            double ax = row_dot_pc<double, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(x + j); });
             if (pc < 0) continue;
-            double ax = row_dot<double, CT, G, NS>(W, i, pc, lg, [&](int j) { return __ldcg(x + j); });
             ax = group_sum<G>(ax);
             if (lead) {
                 double bi = W.bvec[i], fi = bi - (ax + W.diag[i] * x[i]);
@@ -2530,9 +2543,9 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
             // v = A p^, partial (rh, v)
             T pa = T(0);
             for (int i = g0; i < n; i += ngroups) {
-                const int pc = W.pcnt[i];
+                int pc;
+                T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(ph + j); });
                 if (pc < 0) continue;
-                T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) { return __ldcg(ph + j); });
                 acc = group_sum<G>(acc);
                 if (lead) {
                     acc += (T)W.diag[i] * ph[i];
@@ -2562,9 +2575,9 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
             // t = A s^; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
             T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
             for (int i = g0; i < n; i += ngroups) {
-                const int pc = W.pcnt[i];
+                int pc;
+                T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(sh + j); });
                 if (pc < 0) continue;
-                T acc = row_dot<T, CT, G, NS>(W, i, pc, lg, [&](int j) { return __ldcg(sh + j); });
                 acc = group_sum<G>(acc);
                 if (lead) {
                     const T si = s[i], hi = rh[i];
