@@ -255,13 +255,22 @@ vct_status vct_map_backward(vct_ctx *ctx, const vct_state *state, const double *
 vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *out);
 
 /* Ensemble: advance n_scen independent scenarios (one context and one device
- * state each, uneven particle counts allowed) by nsteps steps in one call.
- * All scenarios' kernels are queued back to back on the FIRST context's stream
- * (so the cooperative pressure solves never overlap), with no host
- * synchronisation until the end, where each scenario's status is read once.
- * out (host, may be NULL) receives n_scen stats.  Each scenario's result is
- * bit-identical to vct_step on its own.  Returns the first failing status;
- * scenarios that failed keep their state, the others are written back. */
+ * state each, uneven particle counts allowed) by nsteps steps in one call,
+ * with no host synchronisation until the end, where each scenario's status is
+ * read once.  When every scenario uses the multigrid solver in its
+ * small-system form (up to 200k particles) with the same dimension and
+ * precision, the scenarios run side by side: each queues its kernels on a
+ * stream of its own (created on first use, kept by its context), and one
+ * cooperative launch on the FIRST context's stream solves all pressure
+ * systems at once, each on a share of the grid in proportion to its
+ * particles; results then agree with vct_step to the solver tolerance (the
+ * solves' partial sums are grouped differently), and repeat bit for bit.
+ * Otherwise, or with the environment variable VCT_BATCH_SERIAL set, all
+ * kernels are queued back to back on the first context's stream and each
+ * result is bit-identical to vct_step on its own.  The call returns when all
+ * work is done.  out (host, may be NULL) receives n_scen stats.  Returns the
+ * first failing status; scenarios that failed keep their state, the others
+ * are written back. */
 vct_status vct_batch_step(vct_ctx *const *ctxs, vct_state *const *states, int32_t n_scen,
                           int32_t nsteps, vct_stats *out);
 

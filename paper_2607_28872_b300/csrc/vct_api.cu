@@ -34,6 +34,12 @@ struct vct_ctx {
     std::vector<void *> allocs;
     // profiling
     bool prof;
+    // batched ensembles (vct_batch_step): this scenario's own stream and event,
+    // and (first context of a batch) the device copy of the batch's solve jobs
+    cudaStream_t bst;
+    cudaEvent_t bev;
+    FlyJob *jobs_dev;
+    int jobs_cap;
     std::vector<cudaEvent_t> ev;      // 2 per stage per profiled step
     std::vector<int> ev_stage;        // stage of each recorded pair
     int ev_used;
@@ -181,47 +187,59 @@ void geometry(vct_ctx *c, int64_t n)
     c->launches += 1 + 6 + 1;   // map_key; scan x3, scatter, cell sort, reorder; neighbours
 }
 
+// One time step on the context's stream, in three parts: everything up to the
+// pressure solve, the solve, and everything after it.
+void step_pre(vct_ctx *c, int64_t n)
+{
+    geometry(c, n);
+    if (c->P.kind == VCT_MAP_SIGMA && c->P.volume_mode == 2) {
+        StageTimer t(c, VCT_STAGE_SMOOTHING);
+        launch_smoothing(c->P, cur(c), c->W, n, c->st);
+        c->launches += 1;
+    }
+    cudaMemsetAsync(c->W.counts, 0, 2 * sizeof(int64_t), c->st);
+    { StageTimer t(c, VCT_STAGE_PASS1); launch_pass1(c->P, cur(c), c->W, n, c->st); }
+    { StageTimer t(c, VCT_STAGE_PASS2); launch_pass2(c->P, cur(c), c->W, n, 1, c->st); }
+    { StageTimer t(c, VCT_STAGE_RHS); launch_rhs(c->P, cur(c), c->W, n, c->st); }
+    c->launches += 3;   // pass1, pass2, rhs
+    if (c->precond) {
+        launch_mg_setup(c->P, c->W, c->mg, n, c->st);
+        c->launches += 1 + c->mg.L;   // dsc, level 1, coarsening of levels 2..L
+    }
+}
+
+int step_solve(vct_ctx *c, int64_t n, int step)
+{
+    StageTimer t(c, VCT_STAGE_KRYLOV);
+    c->launches += 1;
+    if (c->precond) return launch_krylov_mg(c->P, c->W, c->mg, n, c->coop_blocks_mg, c->st);
+    return launch_krylov(c->P, cur(c), c->W, n, step, c->coop_blocks, c->st);
+}
+
+void step_post(vct_ctx *c, int64_t n, int step, int nsteps, const vct_probe *pr)
+{
+    if (pr && step == nsteps - 1) {
+        launch_probe_out(c->P, cur(c), c->W, n, *pr, c->st);
+        c->launches += 1;
+        if (pr->x_test && pr->ppe_Ax) {
+            launch_probe_ax(c->P, cur(c), c->W, n, pr->x_test, pr->ppe_Ax, c->st);
+            c->launches += 2;
+        }
+    }
+    { StageTimer t(c, VCT_STAGE_CORRECTOR); launch_corrector(c->P, cur(c), c->W, n, c->st); }
+    c->launches += 1;
+    if (regularise_on(c->P)) {
+        StageTimer t(c, VCT_STAGE_REGULARISE);
+        c->launches += launch_regularise(c->P, cur(c), c->W, n, c->st);
+    }
+}
+
 // Queue one time step of the current state on the context's stream.
 vct_status queue_step(vct_ctx *c, int64_t n, int step, int nsteps, const vct_probe *pr)
 {
-    {
-        geometry(c, n);
-        if (c->P.kind == VCT_MAP_SIGMA && c->P.volume_mode == 2) {
-            StageTimer t(c, VCT_STAGE_SMOOTHING);
-            launch_smoothing(c->P, cur(c), c->W, n, c->st);
-            c->launches += 1;
-        }
-        cudaMemsetAsync(c->W.counts, 0, 2 * sizeof(int64_t), c->st);
-        { StageTimer t(c, VCT_STAGE_PASS1); launch_pass1(c->P, cur(c), c->W, n, c->st); }
-        { StageTimer t(c, VCT_STAGE_PASS2); launch_pass2(c->P, cur(c), c->W, n, 1, c->st); }
-        { StageTimer t(c, VCT_STAGE_RHS); launch_rhs(c->P, cur(c), c->W, n, c->st); }
-        int e;
-        {
-            StageTimer t(c, VCT_STAGE_KRYLOV);
-            if (c->precond) {
-                launch_mg_setup(c->P, c->W, c->mg, n, c->st);
-                e = launch_krylov_mg(c->P, c->W, c->mg, n, c->coop_blocks_mg, c->st);
-                c->launches += 2 + (c->mg.L - 1);
-            } else {
-                e = launch_krylov(c->P, cur(c), c->W, n, step, c->coop_blocks, c->st);
-            }
-        }
-        if (e) return VCT_ERR_CUDA;
-        if (pr && step == nsteps - 1) {
-            launch_probe_out(c->P, cur(c), c->W, n, *pr, c->st);
-            c->launches += 1;
-            if (pr->x_test && pr->ppe_Ax) {
-                launch_probe_ax(c->P, cur(c), c->W, n, pr->x_test, pr->ppe_Ax, c->st);
-                c->launches += 2;
-            }
-        }
-        { StageTimer t(c, VCT_STAGE_CORRECTOR); launch_corrector(c->P, cur(c), c->W, n, c->st); }
-        c->launches += 5;   // pass1, pass2, rhs, krylov, corrector
-        if (regularise_on(c->P)) {
-            StageTimer t(c, VCT_STAGE_REGULARISE);
-            c->launches += launch_regularise(c->P, cur(c), c->W, n, c->st);
-        }
-    }
+    step_pre(c, n);
+    if (step_solve(c, n, step)) return VCT_ERR_CUDA;
+    step_post(c, n, step, nsteps, pr);
     return VCT_OK;
 }
 
@@ -242,6 +260,130 @@ vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, 
     c->launches += 1;
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
     return finish(c, out, nsteps);
+}
+
+// Ensemble step with the scenarios side by side: every scenario queues its
+// kernels up to the pressure solve on its own stream; one cooperative launch
+// then solves all pressure systems at once, each on its own share of the grid
+// (blocks in proportion to its particles); the rest of each step runs again on
+// the scenarios' streams.  Eligible when every scenario uses the multigrid
+// solver in its small-system form with the same dimension and precision, and
+// the grid holds a block per scenario; otherwise returns VCT_ERR_ARG (the
+// caller then queues the scenarios one after another).  The solves' partial
+// sums are grouped by the scenario's share of blocks, so results agree with
+// vct_step to the solver tolerance, not bit for bit.
+vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int n_scen, int nsteps,
+                            vct_stats *out)
+{
+    if (n_scen < 2 || getenv("VCT_BATCH_SERIAL")) return VCT_ERR_ARG;
+    const int prec = ctxs[0]->P.precision, dim = ctxs[0]->P.dim;
+    size_t smem = 0;
+    double wsum = 0.0;
+    for (int k = 0; k < n_scen; ++k) {
+        const vct_ctx *c = ctxs[k];
+        if (!c->precond || !c->mg.fly || c->P.precision != prec || c->P.dim != dim) return VCT_ERR_ARG;
+        if ((size_t)c->mg.smem_bytes > smem) smem = (size_t)c->mg.smem_bytes;
+        wsum += (double)states[k]->n;
+    }
+    const int total = krylov_fly_batch_blocks(prec, dim, smem);
+    if (total < n_scen) return VCT_ERR_ARG;
+    // blocks per scenario: in proportion to its particles, at least one, at most
+    // one group of G lanes per row
+    const int G = dim == 2 ? 4 : 8;
+    std::vector<int> nb(n_scen);
+    int used = 0;
+    for (int k = 0; k < n_scen; ++k) {
+        long long want = ((long long)states[k]->n * G + 255) / 256;
+        int b = (int)((double)total * (double)states[k]->n / wsum);
+        if (b < 1) b = 1;
+        if (b > want) b = (int)want;
+        if (b > 4096) b = 4096;
+        nb[k] = b;
+        used += b;
+    }
+    while (used > total) {   // trim the largest shares until the grid fits
+        int kmax = 0;
+        for (int k = 1; k < n_scen; ++k)
+            if (nb[k] > nb[kmax]) kmax = k;
+        if (nb[kmax] <= 1) return VCT_ERR_ARG;
+        --nb[kmax];
+        --used;
+    }
+    std::vector<FlyJob> jobs(n_scen);
+    unsigned b0 = 0;
+    for (int k = 0; k < n_scen; ++k) {
+        const vct_ctx *c = ctxs[k];
+        FlyJob &j = jobs[k];
+        j.W = c->W;
+        j.M = c->mg;
+        j.n = (int)states[k]->n;
+        j.maxit = c->P.max_iter;
+        j.rtol = c->P.rtol;
+        j.inner_floor = prec == VCT_MIXED ? 1e-4 : 0.0;
+        j.b0 = b0;
+        j.nb = (unsigned)nb[k];
+        b0 += (unsigned)nb[k];
+    }
+    vct_ctx *c0 = ctxs[0];
+    cudaStream_t main = c0->st;
+    cudaError_t e = cudaSuccess;
+    if (c0->jobs_cap < n_scen) {
+        if (c0->jobs_dev) cudaFree(c0->jobs_dev);
+        c0->jobs_dev = nullptr;
+        c0->jobs_cap = 0;
+        e = cudaMalloc((void **)&c0->jobs_dev, sizeof(FlyJob) * (size_t)n_scen);
+        if (e != cudaSuccess) return VCT_ERR_CUDA;
+        c0->jobs_cap = n_scen;
+    }
+    e = cudaMemcpyAsync(c0->jobs_dev, jobs.data(), sizeof(FlyJob) * (size_t)n_scen,
+                        cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main);   // jobs is a host temporary
+    for (int k = 0; k < n_scen && e == cudaSuccess; ++k) {
+        vct_ctx *c = ctxs[k];
+        if (!c->bst) e = cudaStreamCreateWithFlags(&c->bst, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !c->bev) e = cudaEventCreateWithFlags(&c->bev, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
+    std::vector<cudaStream_t> saved(n_scen);
+    for (int k = 0; k < n_scen; ++k) {
+        vct_ctx *c = ctxs[k];
+        saved[k] = c->st;
+        c->st = c->bst;
+        reset_status(c);
+        launch_load(c->P, cur(c), *states[k], states[k]->n, c->st);
+        c->launches += 1;
+    }
+    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+        for (int k = 0; k < n_scen; ++k) {
+            vct_ctx *c = ctxs[k];
+            step_pre(c, states[k]->n);
+            cudaMemsetAsync(c->W.bar, 0, 2 * sizeof(unsigned int), c->st);
+            cudaEventRecord(c->bev, c->st);
+            cudaStreamWaitEvent(main, c->bev, 0);
+        }
+        int le = launch_krylov_fly_batch(prec, dim, c0->jobs_dev, n_scen, b0, smem, main);
+        if (le) e = (cudaError_t)le;
+        cudaEventRecord(c0->bev, main);
+        for (int k = 0; k < n_scen; ++k) {
+            vct_ctx *c = ctxs[k];
+            cudaStreamWaitEvent(c->st, c0->bev, 0);
+            c->launches += 1;   // its share of the batched solve
+            step_post(c, states[k]->n, step, nsteps, nullptr);
+        }
+    }
+    for (int k = 0; k < n_scen; ++k) {
+        vct_ctx *c = ctxs[k];
+        launch_store(c->P, cur(c), *states[k], states[k]->n, c->W.status, c->st);
+        c->launches += 1;
+    }
+    vct_status first = e == cudaSuccess ? VCT_OK : VCT_ERR_CUDA;
+    if (!first && cudaGetLastError() != cudaSuccess) first = VCT_ERR_CUDA;
+    for (int k = 0; k < n_scen; ++k) {
+        vct_status v = finish(ctxs[k], out ? out + k : nullptr, nsteps);
+        if (!first) first = v;
+        ctxs[k]->st = saved[k];
+    }
+    return first;
 }
 
 }  // namespace
@@ -647,6 +789,10 @@ VCT_API vct_status vct_batch_step(vct_ctx *const *ctxs, vct_state *const *states
         for (int q = 0; q < k; ++q)
             if (ctxs[q] == ctxs[k]) return VCT_ERR_ARG;   // one context per scenario
     }
+    {
+        vct_status b = batch_concurrent(ctxs, states, n_scen, nsteps, out);
+        if (b != VCT_ERR_ARG) return b;   // VCT_ERR_ARG: not eligible, run the serial form
+    }
     // every scenario's work goes to the first context's stream, in order
     cudaStream_t st = ctxs[0]->st;
     std::vector<cudaStream_t> saved(n_scen);
@@ -766,6 +912,12 @@ VCT_API void vct_destroy(vct_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->st);
+    if (c->bst) {
+        cudaStreamSynchronize(c->bst);
+        cudaStreamDestroy(c->bst);
+    }
+    if (c->bev) cudaEventDestroy(c->bev);
+    if (c->jobs_dev) cudaFree(c->jobs_dev);
     for (auto &e : c->ev) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
     if (c->host_status) cudaFreeHost(c->host_status);

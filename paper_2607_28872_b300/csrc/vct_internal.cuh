@@ -124,6 +124,16 @@ struct MG {
     long long smem_bytes;          // dynamic shared memory of the solver launch
 };
 
+// One scenario's pressure solve inside a batched launch (vct_batch_step):
+// it owns blocks [b0, b0 + nb) of the cooperative grid.
+struct FlyJob {
+    Work W;
+    MG M;
+    int n, maxit;
+    double rtol, inner_floor;
+    unsigned b0, nb;
+};
+
 struct Ctx;
 
 // ---- launchers (vct_kernels.cu) ----
@@ -144,6 +154,9 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
 bool krylov_mg_fly_default(long long rows);
+int krylov_fly_batch_blocks(int precision, int dim, size_t smem);
+int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,
+                            size_t smem, cudaStream_t st);
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly);
 size_t krylov_mg_stage_bytes(int precision, int dim, bool staged);
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);

@@ -1252,13 +1252,15 @@ __device__ __forceinline__ unsigned atom_add_release(unsigned int *p, unsigned v
 // for the top bit to differ from the value it saw.  The word needs no reset.
 // Spins are bounded: on timeout the block records status[2], and every block
 // leaves at its next barrier, so the kernel always ends.
-__device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status)
+// vb: the block's index among the nblocks that share the barrier word (the
+// grid, or a batched solve's subset of it).
+__device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status, unsigned vb)
 {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned inc = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
+        unsigned inc = vb == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
         unsigned old = atom_add_release(bar, inc);
         unsigned long long spins = 0;
         while (((ld_acquire(bar) ^ old) & 0x80000000u) == 0u) {
@@ -1275,11 +1277,16 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *statu
     return ok_sh != 0;
 }
 
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status)
+{
+    return grid_barrier(bar, nblocks, status, blockIdx.x);
+}
+
 // Per-block partial sums, stored k-major: partial[k * PSTRIDE + block].
 constexpr int PSTRIDE = 4096;
 
 template <int NV>
-__device__ void block_partials(const double (&v)[NV], double *partial)
+__device__ void block_partials(const double (&v)[NV], double *partial, unsigned vb)
 {
     __shared__ double sh[NV][KT / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1294,8 +1301,14 @@ __device__ void block_partials(const double (&v)[NV], double *partial)
     if (threadIdx.x < NV) {
         double s = 0.0;
         for (int w = 0; w < KT / 32; ++w) s += sh[threadIdx.x][w];
-        partial[(int64_t)threadIdx.x * PSTRIDE + blockIdx.x] = s;
+        partial[(int64_t)threadIdx.x * PSTRIDE + vb] = s;
     }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&v)[NV], double *partial)
+{
+    block_partials<NV>(v, partial, blockIdx.x);
 }
 
 // Sum the per-block partials: every thread of the block loads a strided
@@ -2356,9 +2369,10 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
 // not write what in(j) reads.  Returns false if a grid barrier timed out.
 template <typename T, typename CT, int G, int NS, int D, typename In, typename Own>
 __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, Own own, T *zout,
-                       int lg, bool lead, int g0, int ngroups, int gtid, int gthreads)
+                       int lg, bool lead, int g0, int ngroups, int gtid, int gthreads, unsigned vb,
+                       unsigned vnb)
 {
-    const unsigned nb = gridDim.x;
+    const unsigned nb = vnb;
     const float om = M.omega, kap = M.kappa;
     T *r0 = (T *)W.kr0;
     const bool pre = M.presmooth != 0;
@@ -2377,7 +2391,7 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             r0[i] = vi - acc - (T)om * vi;
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     // D1: restriction to the cells (of r0, or of v itself without pre-smoothing,
     // where own(i) runs here instead), one Jacobi step from zero on level 1
@@ -2399,13 +2413,13 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             c.z[I] = om * bs * c.dinv[I];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     const int fl = M.first_local;
     for (int l = 1; l < fl; ++l) {
         lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
-    if (blockIdx.x == 0) {
+    if (vb == 0) {
         // levels fl..L in shared memory: b and z of level fl come from global
         {
             const LV g = lv_global(W, M, fl), s = lv_shared(sh, M, fl);
@@ -2429,10 +2443,10 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             for (int q = threadIdx.x; q < g.n; q += blockDim.x) g.zu[q] = s.zu[q];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     for (int l = fl - 1; l >= 1; --l) {
         lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, kap, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     // U0: prolongation from the cells + one damped Jacobi step on the fine level
     const float *zu1 = W.mg_pool + M.offv[1] + 3 * M.n[1];
@@ -2451,24 +2465,26 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             zout[i] = zi + (T)om * res * (T)W.mg_dsc[i];
         }
     }
-    return grid_barrier(W.bar, nb, W.status);
+    return grid_barrier(W.bar, nb, W.status, vb);
 }
 
 // Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
+// The solve on vnb blocks (block vb of them) sharing W.bar and W.partial: the
+// whole grid, or one scenario's subset of a batched launch.
 template <typename T, typename CT, int G, int NS, int D>
-__global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int maxit, double rtol,
-                                                  double inner_floor, int32_t *iters_out,
-                                                  double *resid_out)
+__device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, double rtol,
+                                 double inner_floor, int32_t *iters_out, double *resid_out,
+                                 unsigned vb, unsigned vnb)
 {
     if (step_failed(W.status)) return;
-    const unsigned nb = gridDim.x;
+    const unsigned nb = vnb;
     const int lg = threadIdx.x & (G - 1);
     const bool lead = lg == 0;
-    const int ngroups = (gridDim.x * blockDim.x) / G;
-    const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    const int ngroups = (int)(vnb * blockDim.x) / G;
+    const int g0 = (int)(vb * blockDim.x + threadIdx.x) / G;
+    const int gtid = (int)(vb * blockDim.x + threadIdx.x), gthreads = (int)(vnb * blockDim.x);
     extern __shared__ float mg_sh[];
-    if (blockIdx.x == 0) mg_load_shared(W, M, mg_sh);
+    if (vb == 0) mg_load_shared(W, M, mg_sh);
     double *x = W.kx, *f = W.kf;
     T *r = (T *)W.kr, *rh = (T *)W.krh, *s = (T *)W.ks, *t = (T *)W.kt, *dl = (T *)W.kd;
     T *pold = (T *)W.kp0, *pnew = (T *)W.kp1, *vold = (T *)W.kv0, *vnew = (T *)W.kv1;
@@ -2490,8 +2506,8 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
                 part[1] += bi * bi;
             }
         }
-        block_partials<2>(part, W.partial);
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        block_partials<2>(part, W.partial, vb);
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
         double tot[2];
         grid_totals<2>(W.partial, nb, tot);
         rn = sqrt(tot[0]);
@@ -2523,7 +2539,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
                 ok = vcycle_fly<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T { return (T)__ldcg(f + j); },
                     [&](int i) { const T ri = (T)f[i]; r[i] = ri; rh[i] = ri; pnew[i] = ri; dl[i] = T(0); },
-                    ph, lg, lead, g0, ngroups, gtid, gthreads);
+                    ph, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb);
             } else {
                 ok = vcycle_fly<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T {
@@ -2535,7 +2551,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
                         pnew[i] = ri + tb * (pold[i] - tw * vold[i]);
                         if (hp) dl[i] += ta * ph[i] + twp * sh[i];
                     },
-                    ph, lg, lead, g0, ngroups, gtid, gthreads);
+                    ph, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb);
             }
             if (!ok) return;
             first = false;
@@ -2555,9 +2571,9 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
             }
             {
                 double pd[1] = {(double)pa};
-                block_partials<1>(pd, W.partial);
+                block_partials<1>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
             double tv[1];
             grid_totals<1>(W.partial, nb, tv);
             if (tv[0] == 0.0) {
@@ -2570,7 +2586,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
             if (!vcycle_fly<T, CT, G, NS, D>(W, M, mg_sh, n,
                     [&](int j) -> T { return __ldcg(r + j) - ta2 * __ldcg(vnew + j); },
                     [&](int i) { s[i] = r[i] - ta2 * vnew[i]; },
-                    sh, lg, lead, g0, ngroups, gtid, gthreads))
+                    sh, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb))
                 return;
             // t = A s^; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
             T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
@@ -2592,9 +2608,9 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
             }
             {
                 double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
-                block_partials<5>(pd, W.partial);
+                block_partials<5>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
             double tq[5];
             grid_totals<5>(W.partial, nb, tq);
             T *tp = pold; pold = pnew; pnew = tp;
@@ -2624,16 +2640,52 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
             if (have_pend) d += fa * ph[i] + fw * sh[i];
             x[i] += (double)d;
         }
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
         if (fail) break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (vb == 0 && threadIdx.x == 0) {
         if (fail) set_error(W.status, VCT_ERR_NOCONV, -1);
         iters_out[0] += total_it;
         if (total_it > iters_out[1]) iters_out[1] = total_it;
         iters_out[2] = total_it;
         *resid_out = bn > 0.0 ? rn / bn : 0.0;
     }
+}
+
+template <typename T, typename CT, int G, int NS, int D>
+__global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int maxit, double rtol,
+                                                  double inner_floor, int32_t *iters_out,
+                                                  double *resid_out)
+{
+    krylov_fly_solve<T, CT, G, NS, D>(W, M, n, maxit, rtol, inner_floor, iters_out, resid_out,
+                                      blockIdx.x, gridDim.x);
+}
+
+// Batched solves (ensembles): job j owns blocks [b0, b0 + nb) of one cooperative
+// launch and runs its own solve on them, with its own barrier word, partials,
+// multigrid levels and status; the jobs never wait on one another.  A block
+// copies its job's descriptors into shared memory once.
+static_assert(sizeof(FlyJob) % sizeof(int) == 0, "FlyJob copies as ints");
+
+template <typename T, typename CT, int G, int NS, int D>
+__global__ void __launch_bounds__(KT) k_krylov_fly_batch(const FlyJob *jobs, int njobs)
+{
+    __shared__ __align__(16) FlyJob job;
+    __shared__ int jid;
+    if (threadIdx.x == 0) {
+        int j = 0;
+        while (j + 1 < njobs && jobs[j + 1].b0 <= blockIdx.x) ++j;
+        jid = j;
+    }
+    __syncthreads();
+    {
+        const int *src = (const int *)(jobs + jid);
+        int *dst = (int *)&job;
+        for (int q = threadIdx.x; q < (int)(sizeof(FlyJob) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    krylov_fly_solve<T, CT, G, NS, D>(job.W, job.M, job.n, job.maxit, job.rtol, job.inner_floor,
+                                      job.W.kiters, job.W.kresid, blockIdx.x - job.b0, job.nb);
 }
 
 // Small systems (up to FLY_MAX_ROWS unknowns) form the V-cycle inputs on the fly
@@ -2699,6 +2751,38 @@ int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nbl
     cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);
     cudaError_t e = cudaLaunchCooperativeKernel(krylov_mg_fn(P.precision, P.dim, M.fly != 0),
                                                 dim3(nblk), dim3(KT), args, (size_t)M.smem_bytes, st);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+static const void *krylov_fly_batch_fn(int precision, int dim)
+{
+    if (precision == VCT_MIXED)
+        return dim == 2 ? (const void *)k_krylov_fly_batch<float, float, 4, 5, 2>
+                        : (const void *)k_krylov_fly_batch<float, float, 8, 7, 3>;
+    return dim == 2 ? (const void *)k_krylov_fly_batch<double, double, 4, 5, 2>
+                    : (const void *)k_krylov_fly_batch<double, double, 8, 7, 3>;
+}
+
+int krylov_fly_batch_blocks(int precision, int dim, size_t smem)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void *fn = krylov_fly_batch_fn(precision, dim);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.maxDynamicSharedSizeBytes < (int)smem)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, KT, smem);
+    if (per > 4) per = 4;
+    return sms * per;
+}
+
+int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,
+                            size_t smem, cudaStream_t st)
+{
+    void *args[] = {(void *)&jobs, (void *)&njobs};
+    cudaError_t e = cudaLaunchCooperativeKernel(krylov_fly_batch_fn(precision, dim), dim3(nblocks),
+                                                dim3(KT), args, smem, st);
     return e == cudaSuccess ? 0 : (int)e;
 }
 

@@ -1,6 +1,7 @@
 """Batched ensemble (vct_batch_step): scenarios with uneven particle counts and
-different bathymetries advanced in one call give exactly the results of
-advancing each on its own."""
+different bathymetries advanced in one call, side by side (one cooperative
+launch for all pressure solves) or one after another, agree with advancing
+each on its own."""
 import numpy as np
 import pytest
 
@@ -19,17 +20,25 @@ def _scenarios():
     return out
 
 
-def test_batch_equals_individual_steps():
-    from paper_2607_28872_b300 import vct as V
-    scs = _scenarios()
-    assert len({sc.n for sc in scs}) == 3
+def _individual(V, scs, nsteps):
     ref = []
     for sc in scs:
         s = V.Solver(sc)
         st = V.DeviceState(sc)
-        s.vct_step(st, 3)
+        s.vct_step(st, nsteps)
         ref.append(st.numpy())
         s.close()
+    return ref
+
+
+def test_batch_serial_equals_individual_steps(monkeypatch):
+    """Queued one scenario after another (VCT_BATCH_SERIAL), a batch is exactly
+    the individual steps."""
+    from paper_2607_28872_b300 import vct as V
+    monkeypatch.setenv("VCT_BATCH_SERIAL", "1")
+    scs = _scenarios()
+    assert len({sc.n for sc in scs}) == 3
+    ref = _individual(V, scs, 3)
     solvers = [V.Solver(sc) for sc in scs]
     states = [V.DeviceState(sc) for sc in scs]
     stats = V.vct_batch_step(solvers, states, 3)
@@ -37,6 +46,58 @@ def test_batch_equals_individual_steps():
     for st, r in zip(states, ref):
         g = st.numpy()
         for k in ("x", "z", "u", "w", "p", "jbar"):
+            assert np.array_equal(g[k], r[k]), k
+
+
+def rel(g, o):
+    den = np.abs(o).max()
+    return np.abs(g - o).max() / den if den > 0 else np.abs(g).max()
+
+
+def test_batch_concurrent_matches_individual_steps():
+    """Side by side (one cooperative launch solves all pressure systems, each
+    on its share of the grid), a batch agrees with the individual steps to the
+    solver tolerance: the solves stop at the same relative residual (1e-9) with
+    partial sums grouped differently, so pressure and velocity agree to the
+    mixed-form bound of the parity tests (1e-4), positions to that bound times
+    dt |v|, and runs are reproducible bit for bit."""
+    from paper_2607_28872_b300 import vct as V
+    scs = _scenarios()
+    ref = _individual(V, scs, 3)
+    out = []
+    for rep in range(2):
+        solvers = [V.Solver(sc) for sc in scs]
+        states = [V.DeviceState(sc) for sc in scs]
+        stats = V.vct_batch_step(solvers, states, 3)
+        assert all(s.steps_done == 3 for s in stats)
+        out.append([st.numpy() for st in states])
+    for sc, g, r, g2 in zip(scs, out[0], ref, out[1]):
+        f = sc.type == S.FLUID
+        for k in ("p", "u", "w"):
+            assert rel(g[k][f], r[k][f]) < 1e-4, k
+        vmax = np.abs(r["u"][f]).max() + np.abs(r["w"][f]).max() + 1.0
+        for k in ("x", "z"):
+            assert np.abs(g[k][f] - r[k][f]).max() < 1e-4 * sc.params["dt"] * vmax, k
+        for k in ("x", "z", "u", "w", "p", "jbar"):
+            assert np.array_equal(g[k], g2[k]), k
+
+
+def test_batch_with_mixed_solver_forms_runs_serially(monkeypatch):
+    """A batch whose scenarios use different solver forms is queued one
+    scenario after another and equals the individual steps exactly."""
+    from paper_2607_28872_b300 import vct as V
+    scs = _scenarios()
+    ref = _individual(V, scs[:1], 2)
+    monkeypatch.setenv("VCT_MG_FORM", "explicit")
+    ref += _individual(V, scs[1:2], 2)
+    explicit = V.Solver(scs[1])
+    monkeypatch.delenv("VCT_MG_FORM")
+    solvers = [V.Solver(scs[0]), explicit]
+    states = [V.DeviceState(sc) for sc in scs[:2]]
+    V.vct_batch_step(solvers, states, 2)
+    for st, r in zip(states, ref):
+        g = st.numpy()
+        for k in ("x", "z", "u", "w", "p"):
             assert np.array_equal(g[k], r[k]), k
 
 
