@@ -187,6 +187,29 @@ void geometry(vct_ctx *c, int64_t n)
     c->launches += 1 + 6 + 1;   // map_key; scan x3, scatter, cell sort, reorder; neighbours
 }
 
+// Which levels block 0 keeps in shared memory (the smallest ones, within
+// budget_b bytes and at most 4096 nodes each), their offsets, and where the
+// row-staging area of `stage` bytes starts.
+void mg_split_shared(MG &M, long long budget_b, long long stage)
+{
+    const long long budget = budget_b / 4;
+    long long tail = 0;
+    M.first_local = M.L;
+    for (int q = M.L; q >= 1; --q) {
+        tail += (long long)(M.S + 4) * M.n[q];
+        if (tail > budget || M.n[q] > 4096) break;
+        M.first_local = q;
+    }
+    long long so = 0;
+    for (int q = M.first_local; q <= M.L; ++q) {
+        M.soff[q] = so;
+        so += (long long)(M.S + 4) * M.n[q];
+    }
+    M.sh_floats = so;
+    M.stage_off = (so * 4 + 15) / 16 * 16;
+    M.smem_bytes = M.stage_off + stage;
+}
+
 // One time step on the context's stream, in three parts: everything up to the
 // pressure solve, the solve, and everything after it.
 void step_pre(vct_ctx *c, int64_t n)
@@ -267,9 +290,12 @@ vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, 
 // then solves all pressure systems at once, each on its own share of the grid
 // (blocks in proportion to its particles); the rest of each step runs again on
 // the scenarios' streams.  Eligible when every scenario uses the multigrid
-// solver in its small-system form with the same dimension and precision, and
-// the grid holds a block per scenario; otherwise returns VCT_ERR_ARG (the
-// caller then queues the scenarios one after another).  The solves' partial
+// solver in the same form with the same dimension and precision, and the grid
+// holds a block per scenario; otherwise returns VCT_ERR_ARG (the caller then
+// queues the scenarios one after another).  To the solver the batch is one
+// system: above the small-system size in total every scenario's solve runs in
+// the large-system form (vectors, staged rows, L1 gathers, 16 KB of shared
+// levels; VCT_BATCH_FORM=fly|explicit overrides).  The solves' partial
 // sums are grouped by the scenario's share of blocks, so results agree with
 // vct_step to the solver tolerance, not bit for bit.
 vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int n_scen, int nsteps,
@@ -277,15 +303,37 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
 {
     if (n_scen < 2 || getenv("VCT_BATCH_SERIAL")) return VCT_ERR_ARG;
     const int prec = ctxs[0]->P.precision, dim = ctxs[0]->P.dim;
-    size_t smem = 0;
     double wsum = 0.0;
     for (int k = 0; k < n_scen; ++k) {
         const vct_ctx *c = ctxs[k];
-        if (!c->precond || !c->mg.fly || c->P.precision != prec || c->P.dim != dim) return VCT_ERR_ARG;
-        if ((size_t)c->mg.smem_bytes > smem) smem = (size_t)c->mg.smem_bytes;
+        if (!c->precond || c->mg.fly != ctxs[0]->mg.fly || c->P.precision != prec || c->P.dim != dim)
+            return VCT_ERR_ARG;
         wsum += (double)states[k]->n;
     }
-    const int total = krylov_fly_batch_blocks(prec, dim, smem);
+    bool expl = !ctxs[0]->mg.fly || !krylov_mg_fly_default((long long)wsum);
+    if (const char *bf = getenv("VCT_BATCH_FORM")) {
+        if (!strcmp(bf, "fly") && ctxs[0]->mg.fly) expl = false;
+        if (!strcmp(bf, "explicit")) expl = true;
+    }
+    // each job's multigrid descriptor: the context's, its shared levels re-split
+    // for the large-system form when the batch uses that form
+    std::vector<MG> mgs(n_scen);
+    size_t smem = 0;
+    const long long stage = expl ? (long long)krylov_batch_stage_bytes(prec, dim) : 0;
+    for (int k = 0; k < n_scen; ++k) {
+        mgs[k] = ctxs[k]->mg;
+        if (expl && ctxs[k]->mg.fly) {
+            MG &M = mgs[k];
+            M.fly = 0;
+            M.staged = 1;
+            M.gather_l1 = 1;
+            long long budget_b = 16 * 1024;
+            if (budget_b > 110 * 1024 - stage) budget_b = 110 * 1024 - stage;
+            mg_split_shared(M, budget_b, stage);
+        }
+        if ((size_t)mgs[k].smem_bytes > smem) smem = (size_t)mgs[k].smem_bytes;
+    }
+    const int total = krylov_fly_batch_blocks(prec, dim, smem, expl);
     if (total < n_scen) return VCT_ERR_ARG;
     // blocks per scenario: in proportion to its particles, at least one, at most
     // one group of G lanes per row
@@ -315,7 +363,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         const vct_ctx *c = ctxs[k];
         FlyJob &j = jobs[k];
         j.W = c->W;
-        j.M = c->mg;
+        j.M = mgs[k];
         j.n = (int)states[k]->n;
         j.maxit = c->P.max_iter;
         j.rtol = c->P.rtol;
@@ -361,7 +409,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             cudaEventRecord(c->bev, c->st);
             cudaStreamWaitEvent(main, c->bev, 0);
         }
-        int le = launch_krylov_fly_batch(prec, dim, c0->jobs_dev, n_scen, b0, smem, main);
+        int le = launch_krylov_fly_batch(prec, dim, c0->jobs_dev, n_scen, b0, smem, expl, main);
         if (le) e = (cudaError_t)le;
         cudaEventRecord(c0->bev, main);
         for (int k = 0; k < n_scen; ++k) {
@@ -618,22 +666,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         long long budget_b = M.fly ? 96 * 1024 : 16 * 1024;
         if (budget_b > 110 * 1024 - stage) budget_b = 110 * 1024 - stage;
         if (getenv("VCT_MG_SMEM_KB")) budget_b = (long long)atoi(getenv("VCT_MG_SMEM_KB")) * 1024;
-        const long long budget = budget_b / 4;
-        long long tail = 0;
-        M.first_local = M.L;
-        for (int q = M.L; q >= 1; --q) {
-            tail += (long long)(M.S + 4) * M.n[q];
-            if (tail > budget || M.n[q] > 4096) break;
-            M.first_local = q;
-        }
-        long long so = 0;
-        for (int q = M.first_local; q <= M.L; ++q) {
-            M.soff[q] = so;
-            so += (long long)(M.S + 4) * M.n[q];
-        }
-        M.sh_floats = so;
-        M.stage_off = (so * 4 + 15) / 16 * 16;
-        M.smem_bytes = M.stage_off + stage;
+        mg_split_shared(M, budget_b, stage);
         M.coarse_sweeps = 8;
         if (getenv("VCT_MG_OMEGA")) M.omega = (float)atof(getenv("VCT_MG_OMEGA"));
         if (getenv("VCT_MG_KAPPA")) M.kappa = (float)atof(getenv("VCT_MG_KAPPA"));

@@ -154,9 +154,10 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
 bool krylov_mg_fly_default(long long rows);
-int krylov_fly_batch_blocks(int precision, int dim, size_t smem);
+int krylov_fly_batch_blocks(int precision, int dim, size_t smem, bool expl);
+size_t krylov_batch_stage_bytes(int precision, int dim);
 int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,
-                            size_t smem, cudaStream_t st);
+                            size_t smem, bool expl, cudaStream_t st);
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly);
 size_t krylov_mg_stage_bytes(int precision, int dim, bool staged);
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);

@@ -2097,9 +2097,9 @@ __device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT,
 template <typename T, typename CT, int G, int NS, int D>
 __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT, NS> &S, int n,
                        const T *v, const T *z0, T *zb, T *zout, int lg, bool lead, int g0, int ngroups,
-                       int gtid, int gthreads)
+                       int gtid, int gthreads, unsigned vb, unsigned vnb)
 {
-    const unsigned nb = gridDim.x;
+    const unsigned nb = vnb;
     const float om = M.omega, kap = M.kappa;
     const bool l1 = M.gather_l1 != 0;
     T *r0 = (T *)W.kr0;
@@ -2110,7 +2110,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
         [&](int i, T acc, const Own4<T> &o) {
             if (lead) r0[i] = o.v[0] - acc - o.v[2] * o.v[1];
         });
-    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     // D1: restriction to the cells, one Jacobi step from zero on level 1
     {
         const LV c = lv_global(W, M, 1);
@@ -2123,13 +2123,13 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
             c.z[I] = om * bs * c.dinv[I];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     const int fl = M.first_local;
     for (int l = 1; l < fl; ++l) {
         lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
-    if (blockIdx.x == 0) {
+    if (vb == 0) {
         {
             const LV g = lv_global(W, M, fl), s = lv_shared(sh, M, fl);
             for (int q = threadIdx.x; q < g.n; q += blockDim.x) {
@@ -2152,10 +2152,10 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
             for (int q = threadIdx.x; q < g.n; q += blockDim.x) g.zu[q] = s.zu[q];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     for (int l = fl - 1; l >= 1; --l) {
         lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, kap, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     // P0: prolongation from the cells, zb = z0 + kappa zu_1(cell)
     {
@@ -2163,7 +2163,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
         for (int i = gtid; i < n; i += gthreads)
             if (W.pcnt[i] >= 0) zb[i] = __ldcg(z0 + i) + (T)kap * (T)__ldcg(zu1 + W.cellid[i]);
     }
-    if (!grid_barrier(W.bar, nb, W.status)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     // U0: one damped Jacobi step on the fine level
     rows_pipelined<T, CT, G, NS>(
         W, S, n, g0, ngroups, lg, [&](int j) { return ldx(zb, j, l1); },
@@ -2174,24 +2174,26 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
                 zout[i] = o.v[0] + (T)om * res * o.v[3];
             }
         });
-    return grid_barrier(W.bar, nb, W.status);
+    return grid_barrier(W.bar, nb, W.status, vb);
 }
 
 // Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
+// The large-system solve on vnb blocks (block vb of them): the whole grid, or
+// one scenario's subset of a batched launch.
 template <typename T, typename CT, int G, int NS, int D>
-__global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int maxit, double rtol,
-                                                  double inner_floor, int32_t *iters_out,
-                                                  double *resid_out)
+__device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int maxit, double rtol,
+                                      double inner_floor, int32_t *iters_out, double *resid_out,
+                                      unsigned vb, unsigned vnb)
 {
     if (step_failed(W.status)) return;
-    const unsigned nb = gridDim.x;
+    const unsigned nb = vnb;
     const int lg = threadIdx.x & (G - 1);
     const bool lead = lg == 0;
-    const int ngroups = (gridDim.x * blockDim.x) / G;
-    const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+    const int ngroups = (int)(vnb * blockDim.x) / G;
+    const int g0 = (int)(vb * blockDim.x + threadIdx.x) / G;
+    const int gtid = (int)(vb * blockDim.x + threadIdx.x), gthreads = (int)(vnb * blockDim.x);
     extern __shared__ __align__(16) float mg_sh[];
-    if (blockIdx.x == 0) mg_load_shared(W, M, mg_sh);
+    if (vb == 0) mg_load_shared(W, M, mg_sh);
     const RowStage<CT, NS> S = row_stage<CT, NS>((unsigned char *)mg_sh + M.stage_off, M.staged != 0);
     const bool l1 = M.gather_l1 != 0;
     const float om = M.omega;
@@ -2216,8 +2218,8 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
                     part[1] += bi * bi;
                 }
             });
-        block_partials<2>(part, W.partial);
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        block_partials<2>(part, W.partial, vb);
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
         double tot[2];
         grid_totals<2>(W.partial, nb, tot);
         rn = sqrt(tot[0]);
@@ -2260,8 +2262,8 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
                 pnew[i] = pn;
                 z0[i] = (T)om * pn * (T)W.mg_dsc[i];
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
-            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, pnew, z0, zb, ph, lg, lead, g0, ngroups, gtid, gthreads))
+            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, pnew, z0, zb, ph, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb))
                 return;
             first = false;
             have_pend = false;
@@ -2279,9 +2281,9 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
                 });
             {
                 double pd[1] = {(double)pa};
-                block_partials<1>(pd, W.partial);
+                block_partials<1>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
             double tv[1];
             grid_totals<1>(W.partial, nb, tv);
             if (tv[0] == 0.0) {
@@ -2297,8 +2299,8 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
                 s[i] = si;
                 z0[i] = (T)om * si * (T)W.mg_dsc[i];
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
-            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, s, z0, zb, sh, lg, lead, g0, ngroups, gtid, gthreads))
+            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, s, z0, zb, sh, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb))
                 return;
             // t = A s^; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
             T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
@@ -2319,9 +2321,9 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
                 });
             {
                 double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
-                block_partials<5>(pd, W.partial);
+                block_partials<5>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
             double tq[5];
             grid_totals<5>(W.partial, nb, tq);
             T *tp = pold; pold = pnew; pnew = tp;
@@ -2351,16 +2353,25 @@ __global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int ma
             if (have_pend) d += fa * __ldcg(ph + i) + fw * __ldcg(sh + i);
             x[i] += (double)d;
         }
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
         if (fail) break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (vb == 0 && threadIdx.x == 0) {
         if (fail) set_error(W.status, VCT_ERR_NOCONV, -1);
         iters_out[0] += total_it;
         if (total_it > iters_out[1]) iters_out[1] = total_it;
         iters_out[2] = total_it;
         *resid_out = bn > 0.0 ? rn / bn : 0.0;
     }
+}
+
+template <typename T, typename CT, int G, int NS, int D>
+__global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int maxit, double rtol,
+                                                  double inner_floor, int32_t *iters_out,
+                                                  double *resid_out)
+{
+    krylov_explicit_solve<T, CT, G, NS, D>(W, M, n, maxit, rtol, inner_floor, iters_out, resid_out,
+                                           blockIdx.x, gridDim.x);
 }
 
 // z_out = M^-1 v for the fine vector given on the fly by in(j).  own(i) runs once
@@ -2667,8 +2678,8 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
 // copies its job's descriptors into shared memory once.
 static_assert(sizeof(FlyJob) % sizeof(int) == 0, "FlyJob copies as ints");
 
-template <typename T, typename CT, int G, int NS, int D>
-__global__ void __launch_bounds__(KT) k_krylov_fly_batch(const FlyJob *jobs, int njobs)
+template <typename T, typename CT, int G, int NS, int D, bool EXPL>
+__global__ void __launch_bounds__(KT, 2) k_krylov_fly_batch(const FlyJob *jobs, int njobs)
 {
     __shared__ __align__(16) FlyJob job;
     __shared__ int jid;
@@ -2684,8 +2695,13 @@ __global__ void __launch_bounds__(KT) k_krylov_fly_batch(const FlyJob *jobs, int
         for (int q = threadIdx.x; q < (int)(sizeof(FlyJob) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
     }
     __syncthreads();
-    krylov_fly_solve<T, CT, G, NS, D>(job.W, job.M, job.n, job.maxit, job.rtol, job.inner_floor,
-                                      job.W.kiters, job.W.kresid, blockIdx.x - job.b0, job.nb);
+    if (EXPL)
+        krylov_explicit_solve<T, CT, G, NS, D>(job.W, job.M, job.n, job.maxit, job.rtol,
+                                               job.inner_floor, job.W.kiters, job.W.kresid,
+                                               blockIdx.x - job.b0, job.nb);
+    else
+        krylov_fly_solve<T, CT, G, NS, D>(job.W, job.M, job.n, job.maxit, job.rtol, job.inner_floor,
+                                          job.W.kiters, job.W.kresid, blockIdx.x - job.b0, job.nb);
 }
 
 // Small systems (up to FLY_MAX_ROWS unknowns) form the V-cycle inputs on the fly
@@ -2754,21 +2770,32 @@ int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nbl
     return e == cudaSuccess ? 0 : (int)e;
 }
 
-static const void *krylov_fly_batch_fn(int precision, int dim)
+template <bool EXPL>
+static const void *krylov_batch_fn_form(int precision, int dim)
 {
     if (precision == VCT_MIXED)
-        return dim == 2 ? (const void *)k_krylov_fly_batch<float, float, 4, 5, 2>
-                        : (const void *)k_krylov_fly_batch<float, float, 8, 7, 3>;
-    return dim == 2 ? (const void *)k_krylov_fly_batch<double, double, 4, 5, 2>
-                    : (const void *)k_krylov_fly_batch<double, double, 8, 7, 3>;
+        return dim == 2 ? (const void *)k_krylov_fly_batch<float, float, 4, 5, 2, EXPL>
+                        : (const void *)k_krylov_fly_batch<float, float, 8, 7, 3, EXPL>;
+    return dim == 2 ? (const void *)k_krylov_fly_batch<double, double, 4, 5, 2, EXPL>
+                    : (const void *)k_krylov_fly_batch<double, double, 8, 7, 3, EXPL>;
 }
 
-int krylov_fly_batch_blocks(int precision, int dim, size_t smem)
+static const void *krylov_fly_batch_fn(int precision, int dim, bool expl)
+{
+    return expl ? krylov_batch_fn_form<true>(precision, dim) : krylov_batch_fn_form<false>(precision, dim);
+}
+
+size_t krylov_batch_stage_bytes(int precision, int dim)
+{
+    return krylov_mg_stage_bytes(precision, dim, true);
+}
+
+int krylov_fly_batch_blocks(int precision, int dim, size_t smem, bool expl)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void *fn = krylov_fly_batch_fn(precision, dim);
+    const void *fn = krylov_fly_batch_fn(precision, dim, expl);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.maxDynamicSharedSizeBytes < (int)smem)
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2778,10 +2805,10 @@ int krylov_fly_batch_blocks(int precision, int dim, size_t smem)
 }
 
 int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,
-                            size_t smem, cudaStream_t st)
+                            size_t smem, bool expl, cudaStream_t st)
 {
     void *args[] = {(void *)&jobs, (void *)&njobs};
-    cudaError_t e = cudaLaunchCooperativeKernel(krylov_fly_batch_fn(precision, dim), dim3(nblocks),
+    cudaError_t e = cudaLaunchCooperativeKernel(krylov_fly_batch_fn(precision, dim, expl), dim3(nblocks),
                                                 dim3(KT), args, smem, st);
     return e == cudaSuccess ? 0 : (int)e;
 }

@@ -54,14 +54,18 @@ def rel(g, o):
     return np.abs(g - o).max() / den if den > 0 else np.abs(g).max()
 
 
-def test_batch_concurrent_matches_individual_steps():
+@pytest.mark.parametrize("form", ["fly", "explicit"])
+def test_batch_concurrent_matches_individual_steps(monkeypatch, form):
     """Side by side (one cooperative launch solves all pressure systems, each
     on its share of the grid), a batch agrees with the individual steps to the
     solver tolerance: the solves stop at the same relative residual (1e-9) with
     partial sums grouped differently, so pressure and velocity agree to the
     mixed-form bound of the parity tests (1e-4), positions to that bound times
-    dt |v|, and runs are reproducible bit for bit."""
+    dt |v|, and runs are reproducible bit for bit.  Both solver forms of the
+    batch are covered (a batch above 200k particles in total uses the
+    large-system one; VCT_BATCH_FORM forces either)."""
     from paper_2607_28872_b300 import vct as V
+    monkeypatch.setenv("VCT_BATCH_FORM", form)
     scs = _scenarios()
     ref = _individual(V, scs, 3)
     out = []
