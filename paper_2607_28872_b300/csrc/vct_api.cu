@@ -573,6 +573,12 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         W.rdh = dalloc<double>(c, n * d, e);
     }
     W.kx = dalloc<double>(c, n, e);
+    W.p_last = dalloc<double>(c, n, e);
+    W.p_prev = dalloc<double>(c, n, e);
+    if (e == cudaSuccess) {   // NaN: no history yet
+        cudaMemset(W.p_last, 0xFF, sizeof(double) * (size_t)n);
+        cudaMemset(W.p_prev, 0xFF, sizeof(double) * (size_t)n);
+    }
     W.kr = dalloc<double>(c, n, e);
     W.krh = dalloc<double>(c, n, e);
     W.kp0 = dalloc<double>(c, n, e);

@@ -96,6 +96,8 @@ struct Work {
     double *rxh, *rmet;       // regularisation: projected position [d] and J, s_x, s_y
     double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
                               //   projected displacement [d]
+    double *p_last, *p_prev;  // caller order: pressure after the last step and before
+                              // it (NaN until set), for the solve's initial guess
 };
 
 // Coarse levels of the aggregation multigrid: level 1 = the cell grid, level

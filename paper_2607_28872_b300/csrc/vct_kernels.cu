@@ -1200,7 +1200,11 @@ __global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, 
     double fac = P.volume_mode == 0 ? 1.0 : c.jbar[i] / c.J[i];
     double rhs = P.rho / P.dt * div + P.gamma * (P.rho * fac - W.rho_hat[i]) / (P.dt * P.dt);
     W.bvec[i] = rhs - W.wallrhs[i];
-    W.kx[i] = c.p[i];   // initial guess p^N
+    // initial guess: p^N, or 2 p^N - p^(N-1) when this particle's pressure is
+    // exactly what this context's previous step left (the caller continued it)
+    const int o = c.orig[i];
+    const double pn = c.p[i];
+    W.kx[i] = pn == W.p_last[o] ? 2.0 * pn - W.p_prev[o] : pn;
 }
 
 void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -2874,6 +2878,11 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
     double vn[D];
 #pragma unroll
     for (int cc = 0; cc < D; ++cc) vn[cc] = W.vstar[(int64_t)cc * cap + i] - P.dt / P.rho * g[cc];
+    {
+        const int o = c.orig[i];
+        W.p_prev[o] = c.p[i];
+        W.p_last[o] = p_i;
+    }
     c.p[i] = p_i;
     c.u[i] = vn[0];
     c.x[i] += P.dt * vn[0];
