@@ -506,6 +506,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     P.ops_shift = prm->ops_shift;
     P.ds_overlap = prm->ds_overlap;
     P.xsph_eps = prm->xsph_eps;
+    P.pguess = getenv("VCT_PGUESS") ? atoi(getenv("VCT_PGUESS")) : 2;   // 0: none, 1: linear
     P.cell_h = P.re;
     P.inv_cell_h = 1.0 / P.cell_h;
     int64_t ncell = 1;
@@ -575,9 +576,11 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.kx = dalloc<double>(c, n, e);
     W.p_last = dalloc<double>(c, n, e);
     W.p_prev = dalloc<double>(c, n, e);
+    W.p_prev2 = dalloc<double>(c, n, e);
     if (e == cudaSuccess) {   // NaN: no history yet
         cudaMemset(W.p_last, 0xFF, sizeof(double) * (size_t)n);
         cudaMemset(W.p_prev, 0xFF, sizeof(double) * (size_t)n);
+        cudaMemset(W.p_prev2, 0xFF, sizeof(double) * (size_t)n);
     }
     W.kr = dalloc<double>(c, n, e);
     W.krh = dalloc<double>(c, n, e);

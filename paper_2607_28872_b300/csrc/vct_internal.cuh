@@ -25,6 +25,8 @@ struct DevParams {
     int pad1;
     double aspect, rho, nu_k, g, dt, d0, l, inv_l, re, re2, V0, ad;
     double ops_shift, ds_overlap, xsph_eps;   // particle regularisation (0: off)
+    int pguess;               // order of the pressure extrapolation of the initial guess
+    int pad2;
     double gamma, cv, cs, ds, H, H_hat, amin, amax, lam_lo, lam_hi, rtol;
     double box_lo[3], cell_h, inv_cell_h;
     double h0, slope_x, slope_y, cos_amp, cos_len;
@@ -97,7 +99,8 @@ struct Work {
     double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
                               //   projected displacement [d]
     double *p_last, *p_prev;  // caller order: pressure after the last step and before
-                              // it (NaN until set), for the solve's initial guess
+    double *p_prev2;          // it, and before that (NaN until set), for the solve's
+                              // initial guess
 };
 
 // Coarse levels of the aggregation multigrid: level 1 = the cell grid, level

@@ -1200,11 +1200,18 @@ __global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, 
     double fac = P.volume_mode == 0 ? 1.0 : c.jbar[i] / c.J[i];
     double rhs = P.rho / P.dt * div + P.gamma * (P.rho * fac - W.rho_hat[i]) / (P.dt * P.dt);
     W.bvec[i] = rhs - W.wallrhs[i];
-    // initial guess: p^N, or 2 p^N - p^(N-1) when this particle's pressure is
-    // exactly what this context's previous step left (the caller continued it)
+    // initial guess: p^N, or its extrapolation from the previous steps when this
+    // particle's pressure is exactly what this context's previous step left (the
+    // caller continued it): 2 p^N - p^(N-1), or 3 p^N - 3 p^(N-1) + p^(N-2)
     const int o = c.orig[i];
     const double pn = c.p[i];
-    W.kx[i] = pn == W.p_last[o] ? 2.0 * pn - W.p_prev[o] : pn;
+    double x0 = pn;
+    if (pn == W.p_last[o]) {
+        const double p1 = W.p_prev[o], p2 = W.p_prev2[o];
+        x0 = (P.pguess >= 2 && isfinite(p2)) ? 3.0 * pn - 3.0 * p1 + p2 : 2.0 * pn - p1;
+    }
+    if (P.pguess == 0) x0 = pn;
+    W.kx[i] = x0;
 }
 
 void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -2880,6 +2887,7 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
     for (int cc = 0; cc < D; ++cc) vn[cc] = W.vstar[(int64_t)cc * cap + i] - P.dt / P.rho * g[cc];
     {
         const int o = c.orig[i];
+        W.p_prev2[o] = W.p_prev[o];
         W.p_prev[o] = c.p[i];
         W.p_last[o] = p_i;
     }
