@@ -636,7 +636,8 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         }
         int l = 1;
         while (M.n[l] > 4 && l < MG_MAXL) {
-            int sh[3] = {1, prm->dim == 3 ? 1 : 0, 1};
+            const int agg = getenv("VCT_MG_SHIFT") ? atoi(getenv("VCT_MG_SHIFT")) : 1;
+            int sh[3] = {agg, prm->dim == 3 ? agg : 0, agg};
             if (ratio > 2.5 && M.dims[l][2] > 1) {
                 sh[0] = 0;
                 sh[1] = 0;

@@ -342,3 +342,33 @@ def test_multi_step_3d_trajectory_matches_oracle(monkeypatch):
             g = dst.numpy()
             vmax = np.sqrt(g["u"] ** 2 + g["v"] ** 2 + g["w"] ** 2)[f].max()
             assert abs(vmax - ref[k]) <= 2e-3 * ref[k], (prec, form, k, vmax, ref[k])
+
+
+def test_initial_guess_history(vct, monkeypatch):
+    """The solve starts from the pressure extrapolated over the context's last
+    steps only when the caller continues the run.  Over 8 steps (in calls of
+    one step) the extrapolated and the plain starts agree to the solver
+    tolerance; a state the context did not produce (here a fresh copy of the
+    scenario) is stepped exactly as by a fresh context."""
+    sc = S.solitary_sigma(L=2.0, bump_x=1.0, x0=0.4, precision=1)
+    f = sc.type == S.FLUID
+    out = {}
+    for g in ("0", "2"):
+        monkeypatch.setenv("VCT_PGUESS", g)
+        s = vct.Solver(sc)
+        st = vct.DeviceState(sc)
+        for _ in range(8):
+            s.vct_step(st, 1)
+        out[g] = st.numpy()
+        if g == "2":
+            used = s
+    assert rel(out["2"]["p"][f], out["0"]["p"][f]) < 1e-4
+    assert rel(out["2"]["u"][f], out["0"]["u"][f]) < 1e-4
+    fresh_state = vct.DeviceState(sc)
+    used.vct_step(fresh_state, 1)
+    s2 = vct.Solver(sc)
+    ref = vct.DeviceState(sc)
+    s2.vct_step(ref, 1)
+    a, b = fresh_state.numpy(), ref.numpy()
+    for k in ("x", "z", "u", "w", "p"):
+        assert np.array_equal(a[k], b[k]), k
