@@ -38,6 +38,7 @@ struct vct_ctx {
     // and (first context of a batch) the device copy of the batch's solve jobs
     cudaStream_t bst;
     cudaEvent_t bev;
+    bool rows_list;            // a batch runs this scenario's solve in the large-system form
     FlyJob *jobs_dev;
     int jobs_cap;
     std::vector<cudaEvent_t> ev;      // 2 per stage per profiled step
@@ -226,7 +227,7 @@ void step_pre(vct_ctx *c, int64_t n)
     { StageTimer t(c, VCT_STAGE_RHS); launch_rhs(c->P, cur(c), c->W, n, c->st); }
     c->launches += 3;   // pass1, pass2, rhs
     if (c->precond) {
-        launch_mg_setup(c->P, c->W, c->mg, n, c->st);
+        launch_mg_setup(c->P, c->W, c->mg, n, c->st, !c->mg.fly || c->rows_list);
         c->launches += 1 + c->mg.L;   // dsc, level 1, coarsening of levels 2..L
     }
 }
@@ -397,6 +398,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         vct_ctx *c = ctxs[k];
         saved[k] = c->st;
         c->st = c->bst;
+        c->rows_list = expl;
         reset_status(c);
         launch_load(c->P, cur(c), *states[k], states[k]->n, c->st);
         c->launches += 1;
@@ -430,6 +432,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         vct_status v = finish(ctxs[k], out ? out + k : nullptr, nsteps);
         if (!first) first = v;
         ctxs[k]->st = saved[k];
+        ctxs[k]->rows_list = false;
     }
     return first;
 }
@@ -574,6 +577,9 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         W.rdh = dalloc<double>(c, n * d, e);
     }
     W.kx = dalloc<double>(c, n, e);
+    W.urow_flag = dalloc<int32_t>(c, n, e);
+    W.urow_pos = dalloc<int32_t>(c, n + 1, e);
+    W.urow = dalloc<int32_t>(c, n, e);
     W.p_last = dalloc<double>(c, n, e);
     W.p_prev = dalloc<double>(c, n, e);
     W.p_prev2 = dalloc<double>(c, n, e);

@@ -98,6 +98,8 @@ struct Work {
     double *rxh, *rmet;       // regularisation: projected position [d] and J, s_x, s_y
     double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
                               //   projected displacement [d]
+    int32_t *urow_flag, *urow_pos, *urow;   // unknown rows (pcnt >= 0) in ascending order,
+                                            // urow_pos[n] = their number (large-system solve)
     double *p_last, *p_prev;  // caller order: pressure after the last step and before
     double *p_prev2;          // it, and before that (NaN until set), for the solve's
                               // initial guess
@@ -155,7 +157,8 @@ void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor
 void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot,
                   int nblocks_coop, cudaStream_t st);
-void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st);
+void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st,
+                     bool rows_list);
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
 bool krylov_mg_fly_default(long long rows);

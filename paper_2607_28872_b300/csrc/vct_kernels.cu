@@ -1784,8 +1784,30 @@ __global__ void k_mg_dsc(Work W, int n)
     W.mg_dsc[i] = (W.pcnt[i] >= 0 && W.diag[i] != 0.0) ? (float)(1.0 / W.diag[i]) : 0.f;
 }
 
-void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st)
+// The large-system solve iterates over the unknown rows only (walls, virtual
+// and free-surface particles have no row): their ascending list, by a scan.
+__global__ void k_urow_flags(Work W, int n)
 {
+    if (step_failed(W.status)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) W.urow_flag[i] = W.pcnt[i] >= 0 ? 1 : 0;
+}
+
+__global__ void k_urow_scatter(Work W, int n)
+{
+    if (step_failed(W.status)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && W.urow_flag[i]) W.urow[W.urow_pos[i]] = i;
+}
+
+void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st,
+                     bool rows_list)
+{
+    if (rows_list) {
+        k_urow_flags<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
+        exclusive_scan<int32_t>(W.urow_flag, W.urow_pos, W.scan_tmp, n, st);
+        k_urow_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
+    }
     k_mg_dsc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
     const unsigned g1 = (unsigned)((M.n[1] + 127) / 128);
     const int mixed = P.precision == VCT_MIXED;
@@ -2054,14 +2076,18 @@ struct Own4 {
 // of a_ik x_k over the stored coefficients (the diagonal is not included) and
 // o = own(i), whose loads are issued before the gathers so that both share one
 // round trip.
+// Rows are rows[0..nr) (the unknown rows in ascending order); each row's index
+// is loaded one row ahead of its staging, so the list adds no round trip.
 template <typename T, typename CT, int G, int NS, typename GetX, typename OwnF, typename Body>
-__device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT, NS> &S, int n, int g0,
+__device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT, NS> &S,
+                                               const int32_t *rows, int nr, int g0,
                                                int ngroups, int lg, GetX getx, OwnF own, Body body)
 {
     const int t = threadIdx.x;
     const int64_t cap = W.cap;
     if (S.pc == nullptr) {   // staging off: count and operator, then the gathers
-        for (int i = g0; i < n; i += ngroups) {
+        for (int q = g0; q < nr; q += ngroups) {
+            const int i = __ldg(rows + q);
             int pc;
             const auto o = own(i);
             T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, getx);
@@ -2071,16 +2097,17 @@ __device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT,
         }
         return;
     }
-    int b = 0;   // stage of row i
-#pragma unroll
-    for (int r = 0; r < ROW_STAGES - 1; ++r) {
-        if (g0 + r * ngroups < n) stage_row<CT, G, NS>(W, S, r, g0 + r * ngroups, lg);
+    static_assert(ROW_STAGES == 2, "the row-index prefetch below assumes two stages");
+    int b = 0;   // stage of the current row
+    int icur = g0 < nr ? __ldg(rows + g0) : 0;
+    if (g0 < nr) stage_row<CT, G, NS>(W, S, 0, icur, lg);
+    cp_async_commit();
+    int inext = g0 + ngroups < nr ? __ldg(rows + g0 + ngroups) : 0;
+    for (int q = g0; q < nr; q += ngroups) {
+        const int i = icur;
+        if (q + ngroups < nr) stage_row<CT, G, NS>(W, S, b ^ 1, inext, lg);
         cp_async_commit();
-    }
-    for (int i = g0; i < n; i += ngroups) {
-        const int ia = i + (ROW_STAGES - 1) * ngroups;
-        if (ia < n) stage_row<CT, G, NS>(W, S, (b + ROW_STAGES - 1) % ROW_STAGES, ia, lg);
-        cp_async_commit();
+        const int iafter = q + 2 * ngroups < nr ? __ldg(rows + q + 2 * ngroups) : 0;
         cp_async_wait<ROW_STAGES - 1>();
         const int pc = S.pc[b * KT + t];
         const auto o = own(i);
@@ -2093,7 +2120,9 @@ __device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT,
             const int64_t q = ell_at<G>(kk, i, cap);
             acc += (T)coef<CT>(W, q) * getx(W.pcol[q]);
         }
-        b = b + 1 == ROW_STAGES ? 0 : b + 1;
+        b ^= 1;
+        icur = inext;
+        inext = iafter;
         if (pc < 0) continue;
         acc = group_sum<G>(acc);
         body(i, acc, o);
@@ -2113,10 +2142,11 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
     const unsigned nb = vnb;
     const float om = M.omega, kap = M.kappa;
     const bool l1 = M.gather_l1 != 0;
+    const int32_t *urow = W.urow;
+    const int nu = W.urow_pos[n];
     T *r0 = (T *)W.kr0;
     // D0: fine residual r0 = v - A z0
-    rows_pipelined<T, CT, G, NS>(
-        W, S, n, g0, ngroups, lg, [&](int j) { return ldx(z0, j, l1); },
+    rows_pipelined<T, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(z0, j, l1); },
         [&](int i) { return Own4<T>{{__ldcg(v + i), __ldcg(z0 + i), (T)W.diag[i], T(0)}}; },
         [&](int i, T acc, const Own4<T> &o) {
             if (lead) r0[i] = o.v[0] - acc - o.v[2] * o.v[1];
@@ -2171,13 +2201,14 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
     // P0: prolongation from the cells, zb = z0 + kappa zu_1(cell)
     {
         const float *zu1 = W.mg_pool + M.offv[1] + 3 * M.n[1];
-        for (int i = gtid; i < n; i += gthreads)
-            if (W.pcnt[i] >= 0) zb[i] = __ldcg(z0 + i) + (T)kap * (T)__ldcg(zu1 + W.cellid[i]);
+        for (int q = gtid; q < nu; q += gthreads) {
+            const int i = __ldg(urow + q);
+            zb[i] = __ldcg(z0 + i) + (T)kap * (T)__ldcg(zu1 + W.cellid[i]);
+        }
     }
     if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     // U0: one damped Jacobi step on the fine level
-    rows_pipelined<T, CT, G, NS>(
-        W, S, n, g0, ngroups, lg, [&](int j) { return ldx(zb, j, l1); },
+    rows_pipelined<T, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(zb, j, l1); },
         [&](int i) { return Own4<T>{{__ldcg(zb + i), __ldcg(v + i), (T)W.diag[i], (T)W.mg_dsc[i]}}; },
         [&](int i, T acc, const Own4<T> &o) {
             if (lead) {
@@ -2206,6 +2237,8 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
     extern __shared__ __align__(16) float mg_sh[];
     if (vb == 0) mg_load_shared(W, M, mg_sh);
     const RowStage<CT, NS> S = row_stage<CT, NS>((unsigned char *)mg_sh + M.stage_off, M.staged != 0);
+    const int32_t *urow = W.urow;
+    const int nu = W.urow_pos[n];
     const bool l1 = M.gather_l1 != 0;
     const float om = M.omega;
     double *x = W.kx, *f = W.kf;
@@ -2218,8 +2251,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
     double bn = 0.0, rn = 0.0;
     for (int outer = 0;; ++outer) {
         double part[2] = {0.0, 0.0};
-        rows_pipelined<double, CT, G, NS>(
-            W, S, n, g0, ngroups, lg, [&](int j) { return ldx(x, j, l1); },
+        rows_pipelined<double, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(x, j, l1); },
             [&](int i) { return Own4<double>{{W.bvec[i], W.diag[i], __ldcg(x + i), 0.0}}; },
             [&](int i, double ax, const Own4<double> &o) {
                 if (lead) {
@@ -2256,8 +2288,8 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
             const double beta = first ? 0.0 : (rho / rho_old) * (alpha / omega);
             const T tb = (T)beta, tw = (T)omega, ta = (T)pend_a, twp = (T)pend_w;
             // E1 (own rows): apply the pending update, r = s - w t, p_new = r + beta (p - w v)
-            for (int i = gtid; i < n; i += gthreads) {
-                if (W.pcnt[i] < 0) continue;
+            for (int q = gtid; q < nu; q += gthreads) {
+                const int i = __ldg(urow + q);
                 T ri, pn;
                 if (first) {
                     ri = (T)__ldcg(f + i);
@@ -2280,8 +2312,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
             have_pend = false;
             // v = A p^, partial (rh, v)
             T pa = T(0);
-            rows_pipelined<T, CT, G, NS>(
-                W, S, n, g0, ngroups, lg, [&](int j) { return ldx(ph, j, l1); },
+            rows_pipelined<T, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(ph, j, l1); },
                 [&](int i) { return Own4<T>{{(T)W.diag[i], __ldcg(ph + i), __ldcg(rh + i), T(0)}}; },
                 [&](int i, T acc, const Own4<T> &o) {
                     if (lead) {
@@ -2304,8 +2335,8 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
             alpha = rho / tv[0];
             const T ta2 = (T)alpha;
             // E2 (own rows): s = r - alpha v
-            for (int i = gtid; i < n; i += gthreads) {
-                if (W.pcnt[i] < 0) continue;
+            for (int q = gtid; q < nu; q += gthreads) {
+                const int i = __ldg(urow + q);
                 const T si = r[i] - ta2 * __ldcg(vnew + i);
                 s[i] = si;
                 z0[i] = (T)om * si * (T)W.mg_dsc[i];
@@ -2315,8 +2346,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 return;
             // t = A s^; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
             T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
-            rows_pipelined<T, CT, G, NS>(
-                W, S, n, g0, ngroups, lg, [&](int j) { return ldx(sh, j, l1); },
+            rows_pipelined<T, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(sh, j, l1); },
                 [&](int i) { return Own4<T>{{__ldcg(s + i), __ldcg(rh + i), (T)W.diag[i], __ldcg(sh + i)}}; },
                 [&](int i, T acc, const Own4<T> &o) {
                     if (lead) {
@@ -2358,8 +2388,8 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
             if (sqrt(fmax(rr, 0.0)) <= tol_in * fn || rho == 0.0) break;
         }
         const T fa = (T)pend_a, fw = (T)pend_w;
-        for (int i = gtid; i < n; i += gthreads) {
-            if (W.pcnt[i] < 0) continue;
+        for (int q = gtid; q < nu; q += gthreads) {
+            const int i = __ldg(urow + q);
             T d = dl[i];
             if (have_pend) d += fa * __ldcg(ph + i) + fw * __ldcg(sh + i);
             x[i] += (double)d;
