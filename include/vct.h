@@ -106,7 +106,7 @@ typedef struct {
                                0.8 / 0.7 and coarse-correction scale 1.3 / 1.8 in 2-D / 3-D,
                                z-only coarsening while the operator's z coupling dominates,
                                8 coarsest sweeps, small levels in block 0's shared memory:
-                               96 KB up to 200k particles, 16 KB above, where the solver
+                               96 KB up to 75k particles in 2-D / 30k in 3-D, 16 KB above, where the solver
                                also stages operator rows with cp.async and gathers through
                                L1).  vct_init reads overrides from the environment:
                                VCT_MG_OMEGA, VCT_MG_KAPPA, VCT_MG_SWEEPS, VCT_MG_SMEM_KB,
@@ -257,11 +257,12 @@ vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *o
 /* Ensemble: advance n_scen independent scenarios (one context and one device
  * state each, uneven particle counts allowed) by nsteps steps in one call,
  * with no host synchronisation until the end, where each scenario's status is
- * read once.  When every scenario uses the multigrid solver in its
- * small-system form (up to 200k particles) with the same dimension and
- * precision, the scenarios run side by side: each queues its kernels on a
- * stream of its own (created on first use, kept by its context), and one
- * cooperative launch on the FIRST context's stream solves all pressure
+ * read once.  When every scenario uses the multigrid solver with the same
+ * dimension and precision, the scenarios run side by side (to the solver the
+ * batch counts as one system: above 75k particles in total in 2-D, 30k in 3-D,
+ * or with any large scenario, every solve uses the large-system form): each
+ * queues its kernels on a stream of its own (created on first use, kept by
+ * its context), and one cooperative launch on the FIRST context's stream solves all pressure
  * systems at once, each on a share of the grid in proportion to its
  * particles; results then agree with vct_step to the solver tolerance (the
  * solves' partial sums are grouped differently), and repeat bit for bit.

@@ -291,12 +291,13 @@ vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, 
 // then solves all pressure systems at once, each on its own share of the grid
 // (blocks in proportion to its particles); the rest of each step runs again on
 // the scenarios' streams.  Eligible when every scenario uses the multigrid
-// solver in the same form with the same dimension and precision, and the grid
-// holds a block per scenario; otherwise returns VCT_ERR_ARG (the caller then
-// queues the scenarios one after another).  To the solver the batch is one
-// system: above the small-system size in total every scenario's solve runs in
-// the large-system form (vectors, staged rows, L1 gathers, 16 KB of shared
-// levels; VCT_BATCH_FORM=fly|explicit overrides).  The solves' partial
+// solver with the same dimension and precision, and the grid holds a block per
+// scenario; otherwise returns VCT_ERR_ARG (the caller then queues the
+// scenarios one after another).  To the solver the batch is one system: when
+// it exceeds the small-system size in total, or any scenario is a large system,
+// every scenario's solve runs in the large-system form (vectors, staged rows,
+// L1 gathers, 16 KB of shared levels; VCT_BATCH_FORM=fly|explicit overrides
+// where it can).  The solves' partial
 // sums are grouped by the scenario's share of blocks, so results agree with
 // vct_step to the solver tolerance, not bit for bit.
 vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int n_scen, int nsteps,
@@ -305,15 +306,16 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
     if (n_scen < 2 || getenv("VCT_BATCH_SERIAL")) return VCT_ERR_ARG;
     const int prec = ctxs[0]->P.precision, dim = ctxs[0]->P.dim;
     double wsum = 0.0;
+    bool any_expl = false;
     for (int k = 0; k < n_scen; ++k) {
         const vct_ctx *c = ctxs[k];
-        if (!c->precond || c->mg.fly != ctxs[0]->mg.fly || c->P.precision != prec || c->P.dim != dim)
-            return VCT_ERR_ARG;
+        if (!c->precond || c->P.precision != prec || c->P.dim != dim) return VCT_ERR_ARG;
+        any_expl |= !c->mg.fly;
         wsum += (double)states[k]->n;
     }
-    bool expl = !ctxs[0]->mg.fly || !krylov_mg_fly_default((long long)wsum);
+    bool expl = any_expl || !krylov_mg_fly_default((long long)wsum, dim);
     if (const char *bf = getenv("VCT_BATCH_FORM")) {
-        if (!strcmp(bf, "fly") && ctxs[0]->mg.fly) expl = false;
+        if (!strcmp(bf, "fly") && !any_expl) expl = false;
         if (!strcmp(bf, "explicit")) expl = true;
     }
     // each job's multigrid descriptor: the context's, its shared levels re-split
@@ -666,7 +668,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         // shared memory (every block), and the levels give way so that two solver
         // blocks still fit on an SM (<= 110 KB each).
         // VCT_MG_FORM=fly|explicit overrides the size rule (tests cover both forms)
-        M.fly = krylov_mg_fly_default(n) ? 1 : 0;
+        M.fly = krylov_mg_fly_default(n, prm->dim) ? 1 : 0;
         if (const char *fm = getenv("VCT_MG_FORM")) {
             if (!strcmp(fm, "fly")) M.fly = 1;
             if (!strcmp(fm, "explicit")) M.fly = 0;

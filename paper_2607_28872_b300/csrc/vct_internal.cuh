@@ -161,7 +161,7 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
                      bool rows_list);
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
-bool krylov_mg_fly_default(long long rows);
+bool krylov_mg_fly_default(long long rows, int dim);
 int krylov_fly_batch_blocks(int precision, int dim, size_t smem, bool expl);
 size_t krylov_batch_stage_bytes(int precision, int dim);
 int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,

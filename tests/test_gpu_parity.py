@@ -213,7 +213,7 @@ def test_step_parity_regularised(vct, name, make, precision, tol, band):
 
 
 # The multigrid solver has two forms: V-cycle inputs formed on the fly (systems up
-# to 200k unknowns) and kept as vectors with cp.async-staged rows (larger ones).
+# to 75k particles in 2-D, 30k in 3-D) and kept as vectors with cp.async-staged rows (larger ones).
 # VCT_MG_FORM forces the large-system form on the small cases.
 @pytest.mark.parametrize("precision,tol,band", [(0, 1e-12, 1e-9), (1, 1e-5, 1e-5)],
                          ids=["fp64", "mixed"])
