@@ -148,7 +148,7 @@ typedef struct {
 /* Stages timed by vct_stage_times, in step order. */
 typedef enum {
     VCT_STAGE_LOAD = 0, VCT_STAGE_MAP, VCT_STAGE_SORT, VCT_STAGE_NEIGHBOURS,
-    VCT_STAGE_SMOOTHING, VCT_STAGE_PASS1, VCT_STAGE_PASS2, VCT_STAGE_RHS,
+    VCT_STAGE_SMOOTHING, VCT_STAGE_PASS1, VCT_STAGE_PASS2, VCT_STAGE_RHS, VCT_STAGE_PRECOND,
     VCT_STAGE_KRYLOV, VCT_STAGE_CORRECTOR, VCT_STAGE_REGULARISE, VCT_STAGE_STORE, VCT_NSTAGES
 } vct_stage;
 

@@ -227,8 +227,10 @@ void step_pre(vct_ctx *c, int64_t n)
     { StageTimer t(c, VCT_STAGE_RHS); launch_rhs(c->P, cur(c), c->W, n, c->st); }
     c->launches += 3;   // pass1, pass2, rhs
     if (c->precond) {
-        launch_mg_setup(c->P, c->W, c->mg, n, c->st, !c->mg.fly || c->rows_list);
-        c->launches += 1 + c->mg.L;   // dsc, level 1, coarsening of levels 2..L
+        StageTimer t(c, VCT_STAGE_PRECOND);
+        const bool rows = !c->mg.fly || c->rows_list;
+        launch_mg_setup(c->P, c->W, c->mg, n, c->st, rows);
+        c->launches += mg_setup_launches(c->mg) + (rows ? 5 : 0);   // + row list: flags, scan x3, scatter
     }
 }
 
@@ -707,6 +709,10 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         W.kz0 = dalloc<double>(c, n, e);
         W.kzb = dalloc<double>(c, n, e);
         c->coop_blocks_mg = krylov_mg_coop_blocks(prm->precision, prm->dim, (size_t)M.smem_bytes, M.fly != 0);
+        if (getenv("VCT_SOLVE_BLOCKS")) {   // cap on the solve's grid (tuning)
+            const int cap_b = atoi(getenv("VCT_SOLVE_BLOCKS"));
+            if (cap_b > 0 && cap_b < c->coop_blocks_mg) c->coop_blocks_mg = cap_b;
+        }
     }
     if (c->coop_blocks <= 0) e = e == cudaSuccess ? cudaErrorInvalidConfiguration : e;
     W.partial = dalloc<double>(c, (int64_t)8 * 4096, e);   // k-major, 4096 blocks max

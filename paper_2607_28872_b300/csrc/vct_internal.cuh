@@ -159,6 +159,7 @@ int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot
                   int nblocks_coop, cudaStream_t st);
 void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st,
                      bool rows_list);
+int mg_setup_launches(const MG &M);
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
 bool krylov_mg_fly_default(long long rows, int dim);

@@ -1690,13 +1690,25 @@ __device__ __forceinline__ int stencil_index(int dx, int dy, int dz)
     return D == 2 ? (dz + 1) * 3 + (dx + 1) : ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
 }
 
+// Add v to the stencil entry o, keeping the S accumulators in registers (a
+// dynamically indexed array would live in local memory).
+template <int S>
+__device__ __forceinline__ void stencil_add(float (&acc)[S], int o, float v)
+{
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[s] += s == o ? v : 0.f;
+}
+
+// One warp per cell: the lanes take the slots of the cell's rows in turn and
+// the 3^d sums are reduced across the warp in a fixed order.
 template <int D>
 __global__ void k_mg_level1(Work W, MG M, int mixed)
 {
     if (step_failed(W.status)) return;
     constexpr int S = D == 2 ? 9 : 27;
     const int N = M.n[1];
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int I = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (I >= N) return;
     float acc[S];
 #pragma unroll
@@ -1712,15 +1724,20 @@ __global__ void k_mg_level1(Work W, MG M, int mixed)
         if (pc < 0) continue;
         ++rows;
         center += W.diag[i];
-        for (int k = 0; k < pc; ++k) {
+        for (int k = lane; k < pc; k += 32) {
             const int64_t q = ell_at<ell_group<D>()>(k, i, cap);
             const int j = W.pcol[q];
             const float av = mixed ? W.pvalf[q] : (float)W.pval[q];
             int jx, jy, jz;
             mg_coords(M, 1, W.cellid[j], jx, jy, jz);
-            acc[stencil_index<D>(jx - cx, jy - cy, jz - cz)] += av;
+            stencil_add<S>(acc, stencil_index<D>(jx - cx, jy - cy, jz - cz), av);
         }
     }
+#pragma unroll
+    for (int o = 0; o < S; ++o)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[o] += __shfl_xor_sync(0xffffffffu, acc[o], off);
+    if (lane != 0) return;
     const int cidx = stencil_index<D>(0, 0, 0);
     acc[cidx] += (float)center;
     float *A = M.offA[1] + W.mg_pool;
@@ -1730,14 +1747,12 @@ __global__ void k_mg_level1(Work W, MG M, int mixed)
     v[I] = (rows > 0 && acc[cidx] != 0.f) ? 1.f / acc[cidx] : 0.f;   // dinv
 }
 
+// Node Ic of level l+1 from level l: sums of the children's stencils.
 template <int D>
-__global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from level l
+__device__ void coarsen_node(const Work &W, const MG &M, int l, int Ic)
 {
-    if (step_failed(W.status)) return;
     constexpr int S = D == 2 ? 9 : 27;
     const int Nc = M.n[l + 1], Nf = M.n[l];
-    const int Ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (Ic >= Nc) return;
     float acc[S];
 #pragma unroll
     for (int o = 0; o < S; ++o) acc[o] = 0.f;
@@ -1765,7 +1780,8 @@ __global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from lev
                     const float aval = Af[(int64_t)stencil_index<D>(dx, dy, dz) * Nf + If];
                     if (aval == 0.f) continue;
                     const int jx = ax + dx, jy = ay + dy, jz = az + dz;
-                    acc[stencil_index<D>((jx >> shx) - px, D == 3 ? (jy >> shy) - py : 0, (jz >> shz) - pz)] += aval;
+                    stencil_add<S>(acc, stencil_index<D>((jx >> shx) - px, D == 3 ? (jy >> shy) - py : 0,
+                                                         (jz >> shz) - pz), aval);
                 }
     }
     float *Ac = W.mg_pool + M.offA[l + 1];
@@ -1774,6 +1790,26 @@ __global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from lev
     for (int o = 0; o < S; ++o) Ac[(int64_t)o * Nc + Ic] = acc[o];
     const float cc = acc[stencil_index<D>(0, 0, 0)];
     vc[Ic] = (any && cc != 0.f) ? 1.f / cc : 0.f;
+}
+
+template <int D>
+__global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from level l
+{
+    if (step_failed(W.status)) return;
+    const int Ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Ic < M.n[l + 1]) coarsen_node<D>(W, M, l, Ic);
+}
+
+// Levels l0+1 .. L (small) built by one block, level after level.
+template <int D>
+__global__ void k_mg_coarsen_small(Work W, MG M, int l0)
+{
+    if (step_failed(W.status)) return;
+    for (int l = l0; l < M.L; ++l) {
+        for (int Ic = threadIdx.x; Ic < M.n[l + 1]; Ic += blockDim.x) coarsen_node<D>(W, M, l, Ic);
+        __threadfence_block();
+        __syncthreads();
+    }
 }
 
 __global__ void k_mg_dsc(Work W, int n)
@@ -1800,6 +1836,8 @@ __global__ void k_urow_scatter(Work W, int n)
     if (i < n && W.urow_flag[i]) W.urow[W.urow_pos[i]] = i;
 }
 
+constexpr int SMALL_LEVEL = 4096;   // coarse levels up to this size are built by one block
+
 void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st,
                      bool rows_list)
 {
@@ -1809,15 +1847,27 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
         k_urow_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
     }
     k_mg_dsc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
-    const unsigned g1 = (unsigned)((M.n[1] + 127) / 128);
+    const unsigned g1 = (unsigned)(((int64_t)M.n[1] * 32 + 255) / 256);   // a warp per cell
     const int mixed = P.precision == VCT_MIXED;
-    if (P.dim == 2) k_mg_level1<2><<<g1, 128, 0, st>>>(W, M, mixed);
-    else k_mg_level1<3><<<g1, 128, 0, st>>>(W, M, mixed);
-    for (int l = 1; l < M.L; ++l) {
+    if (P.dim == 2) k_mg_level1<2><<<g1, 256, 0, st>>>(W, M, mixed);
+    else k_mg_level1<3><<<g1, 256, 0, st>>>(W, M, mixed);
+    int l = 1;
+    for (; l < M.L && M.n[l + 1] > SMALL_LEVEL; ++l) {
         const unsigned g = (unsigned)((M.n[l + 1] + 127) / 128);
         if (P.dim == 2) k_mg_coarsen<2><<<g, 128, 0, st>>>(W, M, l);
         else k_mg_coarsen<3><<<g, 128, 0, st>>>(W, M, l);
     }
+    if (l < M.L) {
+        if (P.dim == 2) k_mg_coarsen_small<2><<<1, 256, 0, st>>>(W, M, l);
+        else k_mg_coarsen_small<3><<<1, 256, 0, st>>>(W, M, l);
+    }
+}
+
+int mg_setup_launches(const MG &M)
+{
+    int l = 1, n = 2;   // dsc, level 1
+    for (; l < M.L && M.n[l + 1] > SMALL_LEVEL; ++l) ++n;
+    return n + (l < M.L ? 1 : 0);
 }
 
 // A view of one coarse level: its stencil operator (entry-major, S entries per

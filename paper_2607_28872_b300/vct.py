@@ -59,7 +59,8 @@ class vct_stats(C.Structure):
                 ("kernel_launches", C.c_int64)]
 
 
-STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "rhs", "krylov",
+STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "rhs", "precond",
+          "krylov",
           "corrector", "regularise", "store")
 
 
