@@ -113,7 +113,8 @@ typedef struct {
                                VCT_MG_FORM (fly | explicit), VCT_MG_STAGE, VCT_GATHER_L1 */
     /* Particle regularisation after the position update (Sec. 4.1 applies all
      * three; 0 switches each off).  It acts in projected space with the
-     * step's neighbour lists, in FP64 in both precisions:
+     * step's neighbour lists; pair sums in FP64 (FP64 form) or compensated
+     * FP32 on FP64 differences (mixed form), corrections applied in FP64:
      *   ds_overlap  dynamic stabilization: pairs closer than (1 - ds_overlap) d0
      *               are pushed back to that distance within the step (0.4)
      *   xsph_eps    XSPH velocity smoothing of free-surface particles (5e-3)

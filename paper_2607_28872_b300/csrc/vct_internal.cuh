@@ -98,6 +98,7 @@ struct Work {
     double *rxh, *rmet;       // regularisation: projected position [d] and J, s_x, s_y
     double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
                               //   projected displacement [d]
+    double *jratio;           // J / Jbar per particle (sorted order), for the smoothing
     int32_t *urow_flag, *urow_pos, *urow;   // unknown rows (pcnt >= 0) in ascending order,
                                             // urow_pos[n] = their number (large-system solve)
     double *p_last, *p_prev;  // caller order: pressure after the last step and before

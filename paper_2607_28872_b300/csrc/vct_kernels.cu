@@ -522,6 +522,7 @@ __global__ void k_reorder(const Part c, Part a, Work W, int n)
     a.xh[i] = c.xh[s]; a.yh[i] = c.yh[s]; a.zh[i] = c.zh[s];
     a.J[i] = c.J[s]; a.sx[i] = c.sx[s]; a.sy[i] = c.sy[s]; a.c0[i] = c.c0[s]; a.c3[i] = c.c3[s];
     W.cellid[i] = W.key[s];
+    W.jratio[i] = c.J[s] / c.jbar[s];   // J / Jbar, used by every pair of the smoothing
 }
 
 void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cudaStream_t st)
@@ -636,7 +637,7 @@ __global__ void k_csr_fill(const Part c, Work W, int n, const int64_t *row_ptr, 
 // a10: volume smoothing, simultaneous form of Eq. (VCT_bar_a): every fluid
 // pair is applied once from each end, from the values before the sweep.
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, typename R>
 __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
 {
     if (step_failed(W.status)) return;
@@ -649,7 +650,7 @@ __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
     }
     double xi[3];
     load_hat<D>(c, i, xi);
-    double ri = c.J[i] / jb, sum = 0.0;
+    double ri = W.jratio[i], sum = 0.0;
     int cnt = W.nbr_cnt[i];
     for (int k = 0; k < cnt; ++k) {
         int j = W.nbr[(int64_t)k * W.cap + i];
@@ -657,8 +658,8 @@ __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
         double xj[3], rr2 = 0.0;
         load_hat<D>(c, j, xj);
         for (int K = 0; K < D; ++K) rr2 += (xj[K] - xi[K]) * (xj[K] - xi[K]);
-        double rr = sqrt(rr2);
-        sum += P.cv * (P.re - rr) / P.re * (c.J[j] / c.jbar[j] - ri);
+        double rr = (double)sqrt((R)rr2);
+        sum += P.cv * (P.re - rr) / P.re * (W.jratio[j] - ri);
     }
     W.jbar_tmp[i] = c.J[i] / (ri + 2.0 * sum);
 }
@@ -666,8 +667,14 @@ __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
 void launch_smoothing(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
 {
     unsigned g = (unsigned)((n + 127) / 128);
-    if (P.dim == 2) k_smoothing<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
-    else k_smoothing<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    const bool mixed = P.precision == VCT_MIXED;
+    if (P.dim == 2) {
+        if (mixed) k_smoothing<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_smoothing<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    } else {
+        if (mixed) k_smoothing<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_smoothing<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    }
     cudaMemcpyAsync(cur.jbar, W.jbar_tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
 }
 
@@ -3020,9 +3027,11 @@ void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStrea
 //    tangential to the surface, whose normal is -L grad^C normalised with
 //    L = B^-1, B = sum_j V0 (r^_j - r^_i) (x) grad w_ij (none if B is singular).
 // Projected displacements return through the Jacobian at the new position
-// (dz = (dz^ - s_x dx^ - s_y dy^)/alpha).  All sums are FP64 in list order; a
-// particle's correction reads only copies made before the kernel writes, so
-// the result does not depend on the thread order.
+// (dz = (dz^ - s_x dx^ - s_y dy^)/alpha).  Pair sums run in list order, in FP64
+// (FP64 form) or compensated FP32 on FP64 differences (mixed form); the
+// corrections themselves are FP64.  A particle's correction reads only copies
+// made before the kernel writes, so the result does not depend on the thread
+// order.
 // ---------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ void reg_to_phys(double J, double sx, double sy, const double *dh, double *dp)
@@ -3106,7 +3115,9 @@ __device__ __forceinline__ void reg_load(const Work &W, int i, double *x)
 }
 
 // Dynamic stabilization: corrected velocity copy and projected displacement.
-template <int D>
+// R: precision of the pair terms (FP64 form: double; mixed form: float, the
+// differences formed in FP64 first).
+template <int D, typename R>
 __global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int n)
 {
     if (step_failed(W.status)) return;
@@ -3114,84 +3125,92 @@ __global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int
     if (i >= n || c.type[i] != FLUID) return;
     const int64_t cap = W.cap;
     const double dds = (1.0 - P.ds_overlap) * P.d0;
-    double xi[D], du[D];
+    const R ddsr = (R)dds, dtr = (R)P.dt;
+    double xi[D];
+    R du[D];
     reg_load<D>(W, i, xi);
 #pragma unroll
-    for (int K = 0; K < D; ++K) du[K] = 0.0;
+    for (int K = 0; K < D; ++K) du[K] = R(0);
     const int cnt = W.nbr_cnt[i];
     for (int k = 0; k < cnt; ++k) {
         const int j = W.nbr[(int64_t)k * cap + i];
-        double xj[D], r[D], r2 = 0.0;
+        double xj[D];
+        R r[D], r2 = R(0);
         reg_load<D>(W, j, xj);
 #pragma unroll
         for (int K = 0; K < D; ++K) {
-            r[K] = xj[K] - xi[K];
+            r[K] = (R)(xj[K] - xi[K]);
             r2 += r[K] * r[K];
         }
-        const double rr = sqrt(r2);
-        if (!(rr < dds) || rr == 0.0) continue;
-        const double f = (c.type[j] == FLUID ? 0.5 : 1.0) * (dds - rr) / (P.dt * rr);
+        const R rr = sqrt(r2);
+        if (!(rr < ddsr) || rr == R(0)) continue;
+        const R f = (c.type[j] == FLUID ? R(0.5) : R(1)) * (ddsr - rr) / (dtr * rr);
 #pragma unroll
         for (int K = 0; K < D; ++K) du[K] -= f * r[K];
     }
-    double dv[D];
-    reg_to_phys<D>(W.rmet[i], W.rmet[cap + i], W.rmet[2 * cap + i], du, dv);
+    double dud[D], dv[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) dud[K] = (double)du[K];
+    reg_to_phys<D>(W.rmet[i], W.rmet[cap + i], W.rmet[2 * cap + i], dud, dv);
 #pragma unroll
     for (int K = 0; K < D; ++K) {
         W.rud[K * cap + i] += dv[K];
-        W.rdh[K * cap + i] = P.dt * du[K];
+        W.rdh[K * cap + i] = P.dt * dud[K];
     }
 }
 
 // XSPH on free-surface particles, shifting, and the final write of the state.
-template <int D>
+template <int D, typename R>
 __global__ void __launch_bounds__(128) k_reg_apply(DevParams P, Part c, Work W, int n)
 {
     if (step_failed(W.status)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || c.type[i] != FLUID) return;
     const int64_t cap = W.cap;
-    const double inv_l = P.inv_l, ad = P.ad, V0 = P.V0;
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad, V0 = (R)P.V0;
     const bool fsi = W.fs[i] != 0;
     const bool do_x = P.xsph_eps > 0.0 && fsi, do_s = P.ops_shift > 0.0;
     double xi[D], ui[D], gc[D], xs[D], B[D * D];
+    Acc<R> gca[D], xsa[D], Ba[D * D];
     reg_load<D>(W, i, xi);
 #pragma unroll
-    for (int K = 0; K < D; ++K) {
-        ui[K] = W.rud[K * cap + i];
-        gc[K] = 0.0;
-        xs[K] = 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < D * D; ++q) B[q] = 0.0;
+    for (int K = 0; K < D; ++K) ui[K] = W.rud[K * cap + i];
     const int cnt = (do_x || do_s) ? W.nbr_cnt[i] : 0;
     for (int k = 0; k < cnt; ++k) {
         const int j = W.nbr[(int64_t)k * cap + i];
-        double xj[D], r[D], r2 = 0.0;
+        double xj[D];
+        R r[D], r2 = R(0);
         reg_load<D>(W, j, xj);
 #pragma unroll
         for (int K = 0; K < D; ++K) {
-            r[K] = xi[K] - xj[K];
+            r[K] = (R)(xi[K] - xj[K]);
             r2 += r[K] * r[K];
         }
-        const double rr = sqrt(r2);
-        if (rr == 0.0) continue;
-        double w, dw;
-        kern_wdw<double>(rr, inv_l, ad, w, dw);
+        const R rr = sqrt(r2);
+        if (rr == R(0)) continue;
+        R w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
         if (do_x && c.type[j] == FLUID) {
 #pragma unroll
-            for (int K = 0; K < D; ++K) xs[K] += V0 * (W.rud[K * cap + j] - ui[K]) * w;
+            for (int K = 0; K < D; ++K) xsa[K].add(V0 * (R)(W.rud[K * cap + j] - ui[K]) * w);
         }
         if (do_s) {
-            const double dwr = dw / rr;
+            const R dwr = dw / rr;
 #pragma unroll
-            for (int K = 0; K < D; ++K) gc[K] += V0 * dwr * r[K];
+            for (int K = 0; K < D; ++K) gca[K].add(V0 * dwr * r[K]);
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int b = 0; b < D; ++b) B[a * D + b] -= V0 * dwr * r[a] * r[b];
+                for (int b = 0; b < D; ++b) Ba[a * D + b].add(-(V0 * dwr * r[a] * r[b]));
         }
     }
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        gc[K] = (double)gca[K].val();
+        xs[K] = (double)xsa[K].val();
+    }
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) B[q] = (double)Ba[q].val();
     double un[D], dh[D];
 #pragma unroll
     for (int K = 0; K < D; ++K) {
@@ -3268,14 +3287,23 @@ int launch_regularise(const DevParams &P, Part cur, Work W, int64_t n, cudaStrea
 {
     if (!regularise_on(P)) return 0;
     const unsigned g = (unsigned)((n + 127) / 128);
+    const bool mixed = P.precision == VCT_MIXED;
     if (P.dim == 2) {
         k_reg_geom<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
-        if (P.ds_overlap > 0.0) k_reg_ds<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
-        k_reg_apply<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.ds_overlap > 0.0) {
+            if (mixed) k_reg_ds<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            else k_reg_ds<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        }
+        if (mixed) k_reg_apply<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_reg_apply<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
     } else {
         k_reg_geom<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
-        if (P.ds_overlap > 0.0) k_reg_ds<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
-        k_reg_apply<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.ds_overlap > 0.0) {
+            if (mixed) k_reg_ds<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            else k_reg_ds<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        }
+        if (mixed) k_reg_apply<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_reg_apply<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
     }
     return P.ds_overlap > 0.0 ? 3 : 2;
 }
