@@ -110,7 +110,11 @@ typedef struct {
                                also stages operator rows with cp.async and gathers through
                                L1).  vct_init reads overrides from the environment:
                                VCT_MG_OMEGA, VCT_MG_KAPPA, VCT_MG_SWEEPS, VCT_MG_SMEM_KB,
-                               VCT_MG_FORM (fly | explicit), VCT_MG_STAGE, VCT_GATHER_L1 */
+                               VCT_MG_FORM (fly | explicit), VCT_MG_STAGE, VCT_GATHER_L1,
+                               VCT_MG_PRESMOOTH (0: V(0,1)), VCT_MG_SHIFT (aggregation
+                               2^s per axis), VCT_SOLVE_BLOCKS (grid cap), VCT_PGUESS
+                               (initial guess: 0 p^N, 1 linear, 2 quadratic extrapolation
+                               of the context's last pressures, the default) */
     /* Particle regularisation after the position update (Sec. 4.1 applies all
      * three; 0 switches each off).  It acts in projected space with the
      * step's neighbour lists; pair sums in FP64 (FP64 form) or compensated
