@@ -143,7 +143,8 @@ typedef struct {
     int64_t steps_done;
     int64_t krylov_iters_total;
     int32_t krylov_iters_max;
-    int32_t reserved;
+    int32_t graph_steps;    /* steps of this call replayed from a captured CUDA graph
+                               (vct_batch_step side by side; 0 otherwise) */
     double last_residual;   /* relative residual of the last pressure solve */
     int64_t ppe_rows;       /* unknowns (fluid, not free surface) of the last step */
     int64_t ppe_nnz;        /* off-diagonal coefficients of the last step's operator */
@@ -267,10 +268,20 @@ vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *o
  * batch counts as one system: above 75k particles in total in 2-D, 30k in 3-D,
  * or with any large scenario, every solve uses the large-system form): each
  * queues its kernels on a stream of its own (created on first use, kept by
- * its context), and one cooperative launch on the FIRST context's stream solves all pressure
- * systems at once, each on a share of the grid in proportion to its
- * particles; results then agree with vct_step to the solver tolerance (the
- * solves' partial sums are grouped differently), and repeat bit for bit.
+ * its context), and one cooperative launch on a stream the FIRST context
+ * keeps for it solves all pressure systems at once, each on a share of the
+ * grid in proportion to its particles; results then agree with vct_step to
+ * the solver tolerance (the solves' partial sums are grouped differently),
+ * and repeat bit for bit.  In this form, steps run in pairs from a CUDA graph:
+ * the first call for a batch captures two steps (every scenario's kernels, the
+ * batched solve and the events between the streams) and instantiates them
+ * once; that call's and later calls' pairs (same contexts, particle counts
+ * and buffer parity) are one graph launch each, an odd last step runs from
+ * direct launches.  A changed batch is captured anew (the first context keeps
+ * one graph).  Not with stage profiling on, nor with the environment variable
+ * VCT_BATCH_NOGRAPH set; if a capture fails, the first context uses direct
+ * launches from then on.  Graph and direct launches give identical results;
+ * stats.graph_steps counts the replayed steps.
  * Otherwise, or with the environment variable VCT_BATCH_SERIAL set, all
  * kernels are queued back to back on the first context's stream and each
  * result is bit-identical to vct_step on its own.  The call returns when all

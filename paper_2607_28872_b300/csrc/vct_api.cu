@@ -41,6 +41,15 @@ struct vct_ctx {
     bool rows_list;            // a batch runs this scenario's solve in the large-system form
     FlyJob *jobs_dev;
     int jobs_cap;
+    // (first context of a batch) two side-by-side batch steps captured as a CUDA
+    // graph, the batch it was captured for, and each scenario's launches in it
+    cudaGraphExec_t bgraph;
+    std::vector<long long> bgraph_key;
+    std::vector<int64_t> bgraph_launches;
+    bool bgraph_off;           // a capture failed: direct launches from then on
+    cudaStream_t gst;          // the batched solve's stream
+    long long serial;          // unique per context, never reused
+    int graph_steps;           // steps of the current call replayed from the graph
     std::vector<cudaEvent_t> ev;      // 2 per stage per profiled step
     std::vector<int> ev_stage;        // stage of each recorded pair
     int ev_used;
@@ -137,6 +146,8 @@ void reset_status(vct_ctx *c)
 // Reads the status word (synchronises the stream once).
 vct_status finish(vct_ctx *c, vct_stats *out, int nsteps)
 {
+    const int graph_steps = c->graph_steps;
+    c->graph_steps = 0;
     cudaError_t e = cudaMemcpyAsync(c->host_status, c->W.status, sizeof(int32_t) * 4,
                                     cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess)
@@ -173,6 +184,7 @@ vct_status finish(vct_ctx *c, vct_stats *out, int nsteps)
         out->ppe_rows = cnt[0];
         out->ppe_nnz = cnt[1];
         out->kernel_launches = c->launches;
+        out->graph_steps = graph_steps;
     }
     if (c->prof) collect_times(c);
     return (vct_status)code;
@@ -378,7 +390,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         b0 += (unsigned)nb[k];
     }
     vct_ctx *c0 = ctxs[0];
-    cudaStream_t main = c0->st;
+    cudaStream_t main = c0->st;   // the caller's: job table upload
     cudaError_t e = cudaSuccess;
     if (c0->jobs_cap < n_scen) {
         if (c0->jobs_dev) cudaFree(c0->jobs_dev);
@@ -396,18 +408,26 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         if (!c->bst) e = cudaStreamCreateWithFlags(&c->bst, cudaStreamNonBlocking);
         if (e == cudaSuccess && !c->bev) e = cudaEventCreateWithFlags(&c->bev, cudaEventDisableTiming);
     }
+    // the batched solve runs on a stream of the first context's own (a graph
+    // cannot be captured on the legacy default stream a caller may pass)
+    if (e == cudaSuccess && !c0->gst) e = cudaStreamCreateWithFlags(&c0->gst, cudaStreamNonBlocking);
     if (e != cudaSuccess) return VCT_ERR_CUDA;
+    main = c0->gst;
     std::vector<cudaStream_t> saved(n_scen);
+    bool prof = false;
     for (int k = 0; k < n_scen; ++k) {
         vct_ctx *c = ctxs[k];
         saved[k] = c->st;
         c->st = c->bst;
         c->rows_list = expl;
+        prof |= c->prof;
         reset_status(c);
         launch_load(c->P, cur(c), *states[k], states[k]->n, c->st);
         c->launches += 1;
     }
-    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+    // one step: each scenario's kernels up to the solve on its stream, the
+    // batched solve on the first context's stream, the rest on the scenarios'
+    auto one_step = [&](int step) -> cudaError_t {
         for (int k = 0; k < n_scen; ++k) {
             vct_ctx *c = ctxs[k];
             step_pre(c, states[k]->n);
@@ -416,7 +436,6 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             cudaStreamWaitEvent(main, c->bev, 0);
         }
         int le = launch_krylov_fly_batch(prec, dim, c0->jobs_dev, n_scen, b0, smem, expl, main);
-        if (le) e = (cudaError_t)le;
         cudaEventRecord(c0->bev, main);
         for (int k = 0; k < n_scen; ++k) {
             vct_ctx *c = ctxs[k];
@@ -424,7 +443,83 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             c->launches += 1;   // its share of the batched solve
             step_post(c, states[k]->n, step, nsteps, nullptr);
         }
+        return le ? (cudaError_t)le : cudaSuccess;
+    };
+    // Steps in pairs from a CUDA graph: the state buffers alternate every step,
+    // so after two steps every pointer is back where it started and one captured
+    // pair serves all pairs of this and later calls with the same batch.  The
+    // capture forks from the first context's stream to each scenario's stream
+    // and joins back; a replay is one graph launch on the first context's
+    // stream.  Not with stage profiling (its events are per step), nor with
+    // VCT_BATCH_NOGRAPH set; if a capture fails, direct launches from then on.
+    int step0 = 0;
+    if (nsteps >= 2 && !prof && !c0->bgraph_off && !getenv("VCT_BATCH_NOGRAPH")) {
+        std::vector<long long> key = {n_scen, expl ? 1 : 0, (long long)smem, (long long)b0,
+                                      (long long)(intptr_t)c0->jobs_dev};
+        for (int k = 0; k < n_scen; ++k) {
+            key.push_back(ctxs[k]->serial);
+            key.push_back(states[k]->n);
+            key.push_back(ctxs[k]->cur_is_A ? 1 : 0);
+        }
+        if (!c0->bgraph || key != c0->bgraph_key) {
+            if (c0->bgraph) cudaGraphExecDestroy(c0->bgraph);
+            c0->bgraph = nullptr;
+            c0->bgraph_key.clear();
+            std::vector<int64_t> l0(n_scen);
+            std::vector<char> cur0(n_scen);
+            for (int k = 0; k < n_scen; ++k) {
+                l0[k] = ctxs[k]->launches;
+                cur0[k] = ctxs[k]->cur_is_A;
+            }
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed);
+            cudaError_t se = cudaSuccess;
+            if (ce == cudaSuccess) {
+                cudaEventRecord(c0->bev, main);
+                for (int k = 0; k < n_scen; ++k) cudaStreamWaitEvent(ctxs[k]->st, c0->bev, 0);
+                for (int q = 0; q < 2 && se == cudaSuccess; ++q) se = one_step(q);
+                for (int k = 0; k < n_scen; ++k) {
+                    cudaEventRecord(ctxs[k]->bev, ctxs[k]->st);
+                    cudaStreamWaitEvent(main, ctxs[k]->bev, 0);
+                }
+                ce = cudaStreamEndCapture(main, &g);
+            }
+            if (ce == cudaSuccess && se == cudaSuccess && g)
+                ce = cudaGraphInstantiate(&c0->bgraph, g, 0);
+            else if (ce == cudaSuccess)
+                ce = se;
+            if (g) cudaGraphDestroy(g);
+            c0->bgraph_launches.assign(n_scen, 0);
+            for (int k = 0; k < n_scen; ++k) {
+                c0->bgraph_launches[k] = ctxs[k]->launches - l0[k];
+                ctxs[k]->launches = l0[k];   // nothing ran yet
+                ctxs[k]->cur_is_A = cur0[k] != 0;
+            }
+            if (ce != cudaSuccess) {
+                cudaGetLastError();   // the failed capture launched nothing
+                c0->bgraph = nullptr;
+                c0->bgraph_off = true;
+            } else {
+                c0->bgraph_key = key;
+            }
+        }
+        if (c0->bgraph) {
+            for (int k = 0; k < n_scen; ++k) {   // the loads before the first replay
+                cudaEventRecord(ctxs[k]->bev, ctxs[k]->st);
+                cudaStreamWaitEvent(main, ctxs[k]->bev, 0);
+            }
+            const int pairs = nsteps / 2;
+            for (int q = 0; q < pairs && e == cudaSuccess; ++q) e = cudaGraphLaunch(c0->bgraph, main);
+            cudaEventRecord(c0->bev, main);   // and the scenarios' work after the last
+            for (int k = 0; k < n_scen; ++k) {
+                cudaStreamWaitEvent(ctxs[k]->st, c0->bev, 0);
+                ctxs[k]->launches += (int64_t)pairs * c0->bgraph_launches[k];
+                ctxs[k]->graph_steps = 2 * pairs;
+            }
+            step0 = 2 * pairs;
+        }
     }
+    for (int step = step0; step < nsteps && e == cudaSuccess; ++step) e = one_step(step);
     for (int k = 0; k < n_scen; ++k) {
         vct_ctx *c = ctxs[k];
         launch_store(c->P, cur(c), *states[k], states[k]->n, c->W.status, c->st);
@@ -471,8 +566,10 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     for (int k = 0; k < 3; ++k)
         if (!(prm->box_hi[k] >= prm->box_lo[k])) return VCT_ERR_ARG;
 
+    static long long serials = 0;
     vct_ctx *c = new (std::nothrow) vct_ctx();
     if (!c) return VCT_ERR_ARG;
+    c->serial = __atomic_add_fetch(&serials, 1, __ATOMIC_RELAXED);
     c->st = (cudaStream_t)stream;
     c->cap = capacity;
     cudaGetDevice(&c->device);
@@ -976,6 +1073,11 @@ VCT_API void vct_destroy(vct_ctx *c)
     }
     if (c->bev) cudaEventDestroy(c->bev);
     if (c->jobs_dev) cudaFree(c->jobs_dev);
+    if (c->bgraph) cudaGraphExecDestroy(c->bgraph);
+    if (c->gst) {
+        cudaStreamSynchronize(c->gst);
+        cudaStreamDestroy(c->gst);
+    }
     for (auto &e : c->ev) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
     if (c->host_status) cudaFreeHost(c->host_status);

@@ -54,7 +54,7 @@ class vct_state(C.Structure):
 
 class vct_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("krylov_iters_total", C.c_int64),
-                ("krylov_iters_max", C.c_int32), ("reserved", C.c_int32),
+                ("krylov_iters_max", C.c_int32), ("graph_steps", C.c_int32),
                 ("last_residual", C.c_double), ("ppe_rows", C.c_int64), ("ppe_nnz", C.c_int64),
                 ("kernel_launches", C.c_int64)]
 

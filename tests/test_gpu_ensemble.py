@@ -124,3 +124,43 @@ def test_batch_rejects_shared_context():
     with pytest.raises(V.VCTError) as e:
         V.vct_batch_step([s, s], [a, b], 1)
     assert e.value.status == V.VCT_ERR_ARG
+
+
+@pytest.mark.parametrize("form", ["fly", "explicit"])
+def test_batch_graph_replay_equals_direct_launches(monkeypatch, form):
+    """Side-by-side steps replayed from the captured CUDA graph give exactly the
+    results of the same steps launched directly, over a call of 4 steps (two
+    replays of one capture), one of 3 (a replay of the same graph and a direct
+    step, which leaves the state buffers in the other parity) and one of 2 (a
+    capture for that parity)."""
+    from paper_2607_28872_b300 import vct as V
+    monkeypatch.setenv("VCT_BATCH_FORM", form)
+    scs = _scenarios()
+
+    def run(graph):
+        if graph:
+            monkeypatch.delenv("VCT_BATCH_NOGRAPH", raising=False)
+        else:
+            monkeypatch.setenv("VCT_BATCH_NOGRAPH", "1")
+        solvers = [V.Solver(sc) for sc in scs]
+        states = [V.DeviceState(sc) for sc in scs]
+        out, replayed, launches = [], [], []
+        for n in (4, 3, 2):
+            stats = V.vct_batch_step(solvers, states, n)
+            assert all(s.steps_done == n for s in stats)
+            replayed.append([s.graph_steps for s in stats])
+            launches.append([s.kernel_launches for s in stats])
+            out.append([st.numpy() for st in states])
+        for s in solvers:
+            s.close()
+        return out, replayed, launches
+
+    g, g_replayed, g_launches = run(True)
+    d, d_replayed, d_launches = run(False)
+    assert g_replayed == [[4] * 3, [2] * 3, [2] * 3]
+    assert d_replayed == [[0] * 3] * 3
+    assert g_launches == d_launches
+    for call_g, call_d in zip(g, d):
+        for a, b in zip(call_g, call_d):
+            for k in ("x", "z", "u", "w", "p", "jbar"):
+                assert np.array_equal(a[k], b[k]), k
