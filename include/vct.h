@@ -303,7 +303,9 @@ vct_status vct_step_probe(vct_ctx *ctx, vct_state *state, const vct_probe *probe
  * bracketed by CUDA events on the context's stream; vct_stage_times adds the
  * elapsed device milliseconds per stage and the number of bracketed launches
  * (host arrays of VCT_NSTAGES).  Turning profiling on resets the totals.  Off
- * by default; when off no event is recorded. */
+ * by default; when off no event is recorded.  In vct_batch_step side by side,
+ * the first context's VCT_STAGE_KRYLOV times the one batched solve of all
+ * scenarios (on its own stream), and no step is replayed from the graph. */
 vct_status vct_set_profiling(vct_ctx *ctx, int32_t on);
 vct_status vct_stage_times(vct_ctx *ctx, double *ms, int64_t *launches);
 

@@ -67,18 +67,20 @@ struct StageTimer {
     vct_ctx *c;
     int stage;
     int slot;
-    StageTimer(vct_ctx *c_, int s) : c(c_), stage(s), slot(-1)
+    cudaStream_t st;
+    StageTimer(vct_ctx *c_, int s, cudaStream_t on = nullptr) : c(c_), stage(s), slot(-1),
+        st(on ? on : c_->st)
     {
         if (c->prof && c->ev_used + 2 <= (int)c->ev.size()) {
             slot = c->ev_used;
             c->ev_used += 2;
             c->ev_stage[slot / 2] = stage;
-            cudaEventRecord(c->ev[slot], c->st);
+            cudaEventRecord(c->ev[slot], st);
         }
     }
     ~StageTimer()
     {
-        if (slot >= 0) cudaEventRecord(c->ev[slot + 1], c->st);
+        if (slot >= 0) cudaEventRecord(c->ev[slot + 1], st);
     }
 };
 
@@ -435,7 +437,11 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             cudaEventRecord(c->bev, c->st);
             cudaStreamWaitEvent(main, c->bev, 0);
         }
-        int le = launch_krylov_fly_batch(prec, dim, c0->jobs_dev, n_scen, b0, smem, expl, main);
+        int le;
+        {   // with profiling on, the first context's krylov stage times the batched solve
+            StageTimer t(c0, VCT_STAGE_KRYLOV, main);
+            le = launch_krylov_fly_batch(prec, dim, c0->jobs_dev, n_scen, b0, smem, expl, main);
+        }
         cudaEventRecord(c0->bev, main);
         for (int k = 0; k < n_scen; ++k) {
             vct_ctx *c = ctxs[k];
@@ -706,11 +712,14 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         MG &M = c->mg;
         memset(&M, 0, sizeof M);
         M.S = prm->dim == 2 ? 9 : 27;
-        // tuned: 2-D configs 1-2 (config 2: 30 -> 24 iterations); 3-D config 3 needs a
-        // larger coarse-correction scale (piecewise-constant aggregation under-corrects
-        // more per level in 3-D; kappa 1.3 does not converge there, 1.8 takes 81)
-        M.omega = prm->dim == 2 ? 0.8f : 0.7f;
-        M.kappa = prm->dim == 2 ? 1.3f : 1.8f;
+        // tuned: 2-D wave (42k particles, 100 steps, kappa 1.3), iterations per step
+        // by omega: 0.7 17.4, 0.75 16.5, 0.8 15.8, 0.85 15.2, 0.9 15.0 (kappa 1.1-1.4
+        // within 1.5 of these; 0.85 keeps a margin to divergence); 3-D BFE
+        // beach (aspect 4, 2.1M particles), iterations per step by kappa at omega 0.7:
+        // 1.8: 77, 1.5: 47, 1.4: 40, 1.3: 33, 1.2: 31 (540k slice: 1.0 36, 1.1 32,
+        // 1.2 32); omega 0.8 does not converge there, 0.75 is within 1 iteration
+        M.omega = prm->dim == 2 ? 0.85f : 0.7f;
+        M.kappa = prm->dim == 2 ? 1.3f : 1.2f;
         M.coarse_sweeps = 24;
         M.dims[1][0] = P.nc[0];
         M.dims[1][1] = P.nc[1];
