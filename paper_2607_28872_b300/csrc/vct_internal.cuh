@@ -99,6 +99,8 @@ struct Work {
     double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
                               //   projected displacement [d]
     double *jratio;           // J / Jbar per particle (sorted order), for the smoothing
+    float4 *hatf;             // projected position rounded to FP32 (sorted order; y = 0
+                              // in 2-D), the neighbour search's first test
     int32_t *urow_flag, *urow_pos, *urow;   // unknown rows (pcnt >= 0) in ascending order,
                                             // urow_pos[n] = their number (large-system solve)
     double *p_last, *p_prev;  // caller order: pressure after the last step and before

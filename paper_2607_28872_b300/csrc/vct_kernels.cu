@@ -509,7 +509,7 @@ __global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
     }
 }
 
-__global__ void k_reorder(const Part c, Part a, Work W, int n)
+__global__ void k_reorder(const Part c, Part a, Work W, int n, int dim)
 {
     if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -523,6 +523,7 @@ __global__ void k_reorder(const Part c, Part a, Work W, int n)
     a.J[i] = c.J[s]; a.sx[i] = c.sx[s]; a.sy[i] = c.sy[s]; a.c0[i] = c.c0[s]; a.c3[i] = c.c3[s];
     W.cellid[i] = W.key[s];
     W.jratio[i] = c.J[s] / c.jbar[s];   // J / Jbar, used by every pair of the smoothing
+    W.hatf[i] = make_float4((float)c.xh[s], dim == 3 ? (float)c.yh[s] : 0.f, (float)c.zh[s], 0.f);
 }
 
 void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cudaStream_t st)
@@ -532,12 +533,40 @@ void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cuda
     unsigned g = (unsigned)((n + 255) / 256);
     k_scatter<<<g, 256, 0, st>>>(W, cur, (int)n);
     k_cell_sort<<<(unsigned)((W.ncell + 127) / 128), 128, 0, st>>>(W, cur, W.ncell);
-    k_reorder<<<g, 256, 0, st>>>(cur, alt, W, (int)n);
+    k_reorder<<<g, 256, 0, st>>>(cur, alt, W, (int)n, P.dim);
 }
 
 // ---------------------------------------------------------------------------
 // a3: neighbour lists (FP64 predicate without FMA, cells in ascending key order)
+//
+// The predicate |r_ij|^2 < r_e^2 is defined in FP64 (the projected positions'
+// differences and squares rounded to nearest, no fused multiply-add).  FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU, so each
+// candidate is first tested in FP32 on the positions rounded to FP32; where
+// that value is farther from r_e^2 than its error bound, it decides, and only
+// the candidates within the bound are tested in FP64.  The lists are the FP64
+// predicate's exactly.
+//
+// Error bound (u = 2^-24, the unit roundoff of FP32).  With x~ = fl32(x),
+// |x~ - x| <= u|x|; the FP32 difference d~ = fl32(x~_j - x~_i) satisfies
+// |d~ - d| <= u(|x_i| + |x_j|) + u|d~| (1 + 2u), so, with |x_j| <= |x_i| + |d|,
+// |d~ - d| <= e = 2u(|x_i| + |d~|)(1 + 4u).  Over the D coordinates, |sum d~^2 - sum d^2| <=
+// sum (2|d~| e + e^2), and summing the squares in FP32 adds at most
+// (D + 1)u sum d~^2 <= 4u s~ with s~ the FP32 sum.  The test uses twice that
+// bound, which also covers the FP32 roundings of the bound itself and the FP64
+// predicate's own roundings (relative 2^-51 at most), against r_e^2 rounded down
+// (inside) or up (outside); rounding to nearest is monotone, so fl(s~ + b) <
+// re2_dn implies s~ + b < re2_dn in exact arithmetic, and likewise outside.
+// Non-finite values fail both tests and go to the FP64 predicate.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float nbr_bound(float ad, float xa)
+{
+    // one coordinate's share: 2|d~| e + e^2 with e = 2u(|x_i| + |d~|)(1 + 1e-4)
+    const float u = 5.9604645e-8f;   // 2^-24
+    const float e = 2.0002f * u * (xa + ad);
+    return 2.f * ad * e + e * e;
+}
+
 template <int D>
 __global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
 {
@@ -546,6 +575,10 @@ __global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
     if (i >= n) return;
     double xi[3];
     load_hat<D>(c, i, xi);
+    const float4 fi = W.hatf[i];
+    const float axi = fabsf(fi.x) * 1.0001f, ayi = fabsf(fi.y) * 1.0001f, azi = fabsf(fi.z) * 1.0001f;
+    const float re2_dn = __double2float_rd(P.re2), re2_up = __double2float_ru(P.re2);
+    const float u4 = 4.0004f * 5.9604645e-8f;
     int cx = cell_coord(P, xi[0], 0);
     int cy = D == 3 ? cell_coord(P, xi[1], 1) : 0;
     int cz = cell_coord(P, xi[D - 1], 2);
@@ -562,17 +595,36 @@ __global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
             int a = W.cell_start[row + xa], b = W.cell_start[row + xb + 1];
             for (int j = a; j < b; ++j) {
                 if (j == i) continue;
-                double d2;
-                double dx = __dsub_rn(c.xh[j], xi[0]);
-                double dz2 = __dsub_rn(c.zh[j], xi[D - 1]);
-                if (D == 2) {
-                    d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dz2, dz2));
-                } else {
-                    double dy2 = __dsub_rn(c.yh[j], xi[1]);
-                    d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy2, dy2)),
-                                   __dmul_rn(dz2, dz2));
+                const float4 fj = W.hatf[j];
+                const float fx = __fsub_rn(fj.x, fi.x), fz = __fsub_rn(fj.z, fi.z);
+                const float ax = fabsf(fx), az = fabsf(fz);
+                float s2 = __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fz, fz));
+                float bnd = nbr_bound(ax, axi) + nbr_bound(az, azi);
+                if (D == 3) {
+                    const float fy = __fsub_rn(fj.y, fi.y), ay = fabsf(fy);
+                    s2 = __fadd_rn(s2, __fmul_rn(fy, fy));
+                    bnd += nbr_bound(ay, ayi);
                 }
-                if (d2 < P.re2) {
+                bnd = 2.f * (bnd + u4 * s2);
+                bool in;
+                if (s2 + bnd < re2_dn) {
+                    in = true;
+                } else if (s2 - bnd > re2_up) {
+                    in = false;
+                } else {   // within the bound (or not finite): the FP64 predicate
+                    double d2;
+                    double dx = __dsub_rn(c.xh[j], xi[0]);
+                    double dz2 = __dsub_rn(c.zh[j], xi[D - 1]);
+                    if (D == 2) {
+                        d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dz2, dz2));
+                    } else {
+                        double dy2 = __dsub_rn(c.yh[j], xi[1]);
+                        d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy2, dy2)),
+                                       __dmul_rn(dz2, dz2));
+                    }
+                    in = d2 < P.re2;
+                }
+                if (in) {
                     if (cnt < P.max_nbr) W.nbr[(int64_t)cnt * cap + i] = j;
                     else over = 1;
                     ++cnt;

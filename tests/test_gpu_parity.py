@@ -67,6 +67,50 @@ def test_neighbours_bit_exact(vct, name, make):
     assert np.array_equal(col.cpu().numpy(), ocol)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_neighbours_bit_exact_at_the_radius(vct, dim):
+    """Particle pairs at r_e (1 + delta), delta from -1e-2 to 1e-2 down to 1e-8
+    and 0, along x, along a diagonal and (3-D) along a space diagonal, near the
+    origin and 5.5 m from it: the search's FP32 first test decides outside its
+    error bound, the FP64 predicate within it, and the lists are the oracle's
+    FP64 predicate's exactly."""
+    d0 = 0.01
+    params = dict(S.DEFAULT_PARAMS)
+    params.update(d0=d0, H=1.0, H_hat=1.0, dt=1e-3)
+    sc0 = S.Scenario(name="radius", dim=dim, map_kind="E", aspect=1.0, bathy=S.Bathymetry(),
+                     params=params, x=np.zeros(1), y=np.zeros(1), z=np.zeros(1), u=np.zeros(1),
+                     v=np.zeros(1), w=np.zeros(1), p=np.zeros(1), jbar=np.ones(1),
+                     type=np.zeros(1, np.int32), box_lo=(-0.1, -0.1, -0.1), box_hi=(10.0, 0.6, 0.6))
+    _, re, _ = O.radii(sc0)
+    deltas = [-1e-2, -1e-3, -3e-4, -1e-4, -3e-5, -1e-5, -1e-6, -1e-8, 0.0,
+              1e-8, 1e-6, 1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 1e-2]
+    dirs = [(1.0, 0.0, 0.0), (np.cos(0.7), 0.0, np.sin(0.7))]
+    if dim == 3:
+        dirs.append(tuple(np.array([1.0, 0.6, 0.8]) / np.linalg.norm([1.0, 0.6, 0.8])))
+    pts = []
+    for x0 in (0.05, 5.5):
+        for q, e in enumerate(dirs):
+            for k, dl in enumerate(deltas):
+                a = np.array([x0 + 5 * re * k, 0.2 if dim == 3 else 0.0, 0.1 + 0.15 * q])
+                pts += [a, a + re * (1.0 + dl) * np.array(e)]
+    P = np.array(pts)
+    n = len(P)
+    sc = S.Scenario(name="radius", dim=dim, map_kind="E", aspect=1.0, bathy=S.Bathymetry(),
+                    params=params, x=P[:, 0].copy(), y=P[:, 1].copy() if dim == 3 else np.zeros(n),
+                    z=P[:, 2].copy(), u=np.zeros(n), v=np.zeros(n), w=np.zeros(n), p=np.zeros(n),
+                    jbar=np.ones(n), type=np.zeros(n, np.int32), box_lo=sc0.box_lo, box_hi=sc0.box_hi)
+    solver = vct.Solver(sc)
+    row, col = solver.vct_build_neighbours(vct.DeviceState(sc))
+    xh, _ = O.projected(sc)
+    _, re, re2 = O.radii(sc)
+    orow, ocol = O.neighbours(dim, xh, re, re2, mode=0)
+    assert np.array_equal(row.cpu().numpy(), orow)
+    assert np.array_equal(col.cpu().numpy(), ocol)
+    # the cases exist on both sides of the radius
+    pair = np.diff(orow)[0::2]
+    assert pair.min() == 0 and pair.max() == 1
+
+
 def test_neighbours_bit_exact_sigma_solitary(vct):
     sc = S.solitary_sigma()
     solver = vct.Solver(sc)
