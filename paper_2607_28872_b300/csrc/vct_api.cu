@@ -678,6 +678,13 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.jbar_tmp = dalloc<double>(c, n, e);
     W.jratio = dalloc<double>(c, n, e);
     W.hatf = dalloc<float4>(c, n, e);
+    W.hatlo = dalloc<float4>(c, n, e);
+    W.velhi = dalloc<float4>(c, n, e);
+    W.vello = dalloc<float4>(c, n, e);
+    W.vshi = dalloc<float4>(c, n, e);
+    W.vslo = dalloc<float4>(c, n, e);
+    W.vol = dalloc<double>(c, n, e);
+    W.volf = dalloc<float>(c, n, e);
     W.adj = dalloc<double>(c, n * (m + d), e);
     if (prm->ops_shift > 0.0 || prm->ds_overlap > 0.0 || prm->xsph_eps > 0.0) {
         W.rxh = dalloc<double>(c, n * d, e);

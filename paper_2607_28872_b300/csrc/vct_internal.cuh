@@ -100,7 +100,12 @@ struct Work {
                               //   projected displacement [d]
     double *jratio;           // J / Jbar per particle (sorted order), for the smoothing
     float4 *hatf;             // projected position rounded to FP32 (sorted order; y = 0
-                              // in 2-D), the neighbour search's first test
+                              // in 2-D), the neighbour search's first test, and the
+    float4 *hatlo;            // rest, fl32(x - hatf): hi + lo pairs for the mixed form's
+    float4 *velhi, *vello;    // pair differences, like the velocity's and
+    float4 *vshi, *vslo;      // the intermediate velocity v*'s
+    double *vol;              // V_i = V0 J_i / Jbar_i (Sec. 3.6; V0 under Condition A), once
+    float *volf;              // per step, and rounded to FP32
     int32_t *urow_flag, *urow_pos, *urow;   // unknown rows (pcnt >= 0) in ascending order,
                                             // urow_pos[n] = their number (large-system solve)
     double *p_last, *p_prev;  // caller order: pressure after the last step and before

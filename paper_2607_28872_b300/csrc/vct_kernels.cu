@@ -163,6 +163,49 @@ __device__ __forceinline__ void load_vel(const Part &c, int i, double *v)
     v[D - 1] = c.w[i];
 }
 
+// Mixed-form pair differences without FP64 arithmetic (which this GPU runs at
+// a small fraction of its FP32 rate).  A sorted particle's projected position
+// (and velocity, and v*) is kept as two FP32 numbers, hi = fl32(x) and
+// lo = fl32(x - hi), so x = hi + lo up to u|lo| <= u^2|x| (u = 2^-24).  Then
+// (hi_j - hi_i) + (lo_j - lo_i) is x_j - x_i to within u|x_j - x_i| plus a few
+// u^2|x|: hi_j - hi_i is exact when hi_i and hi_j are within a factor two of
+// each other (Sterbenz) and otherwise rounded relative to the difference
+// itself.  That is as accurate as rounding the FP64 difference to FP32.
+__device__ __forceinline__ float4 f4_hilo_split(double x, double y, double z, float4 &lo)
+{
+    const float hx = (float)x, hy = (float)y, hz = (float)z;
+    lo = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.f);
+    return make_float4(hx, hy, hz, 0.f);
+}
+
+template <int D>
+__device__ __forceinline__ void hilo_diff(const float4 &hj, const float4 &lj, const float4 &hi,
+                                          const float4 &li, float *d)
+{
+    d[0] = __fsub_rn(hj.x, hi.x) + __fsub_rn(lj.x, li.x);
+    if (D == 3) d[1] = __fsub_rn(hj.y, hi.y) + __fsub_rn(lj.y, li.y);
+    d[D - 1] = __fsub_rn(hj.z, hi.z) + __fsub_rn(lj.z, li.z);
+}
+
+// r_ij in the arithmetic of R: FP64 differences rounded to R (FP64 form), or
+// the hi/lo FP32 differences (mixed form).
+template <int D, typename R>
+__device__ __forceinline__ void pair_r(const Part &c, const Work &W, int j, const double *xi,
+                                       const float4 &hi, const float4 &li, R *r)
+{
+    if constexpr (sizeof(R) == sizeof(float)) {
+        float d[D];
+        hilo_diff<D>(W.hatf[j], W.hatlo[j], hi, li, d);
+#pragma unroll
+        for (int K = 0; K < D; ++K) r[K] = d[K];
+    } else {
+        double xj[3];
+        load_hat<D>(c, j, xj);
+#pragma unroll
+        for (int K = 0; K < D; ++K) r[K] = (R)(xj[K] - xi[K]);
+    }
+}
+
 template <int D, typename R>
 __device__ __forceinline__ void qvec(const R *r, R *q)
 {
@@ -314,6 +357,14 @@ __device__ __forceinline__ double vol_of(const DevParams &P, const Part &c, int 
 {
     // V_j = V0 J_j / Jbar_j (Sec. 3.6); V0 under Condition A.
     return P.volume_mode == 0 ? P.V0 : P.V0 * c.J[j] / c.jbar[j];
+}
+
+// vol_of(P, c, j) rounded to R, as formed once per step (W.vol, W.volf).
+template <typename R>
+__device__ __forceinline__ R vol_at(const Work &W, int j)
+{
+    if constexpr (sizeof(R) == sizeof(float)) return W.volf[j];
+    else return (R)W.vol[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -509,7 +560,7 @@ __global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
     }
 }
 
-__global__ void k_reorder(const Part c, Part a, Work W, int n, int dim)
+__global__ void k_reorder(const Part c, Part a, Work W, int n, DevParams P)
 {
     if (step_failed(W.status)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -523,7 +574,15 @@ __global__ void k_reorder(const Part c, Part a, Work W, int n, int dim)
     a.J[i] = c.J[s]; a.sx[i] = c.sx[s]; a.sy[i] = c.sy[s]; a.c0[i] = c.c0[s]; a.c3[i] = c.c3[s];
     W.cellid[i] = W.key[s];
     W.jratio[i] = c.J[s] / c.jbar[s];   // J / Jbar, used by every pair of the smoothing
-    W.hatf[i] = make_float4((float)c.xh[s], dim == 3 ? (float)c.yh[s] : 0.f, (float)c.zh[s], 0.f);
+    const bool d3 = P.dim == 3;
+    float4 lo;
+    W.hatf[i] = f4_hilo_split(c.xh[s], d3 ? c.yh[s] : 0.0, c.zh[s], lo);
+    W.hatlo[i] = lo;
+    W.velhi[i] = f4_hilo_split(c.u[s], d3 ? c.v[s] : 0.0, c.w[s], lo);
+    W.vello[i] = lo;
+    const double V = P.volume_mode == 0 ? P.V0 : P.V0 * c.J[s] / c.jbar[s];   // vol_of
+    W.vol[i] = V;
+    W.volf[i] = (float)V;
 }
 
 void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cudaStream_t st)
@@ -533,7 +592,7 @@ void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cuda
     unsigned g = (unsigned)((n + 255) / 256);
     k_scatter<<<g, 256, 0, st>>>(W, cur, (int)n);
     k_cell_sort<<<(unsigned)((W.ncell + 127) / 128), 128, 0, st>>>(W, cur, W.ncell);
-    k_reorder<<<g, 256, 0, st>>>(cur, alt, W, (int)n, P.dim);
+    k_reorder<<<g, 256, 0, st>>>(cur, alt, W, (int)n, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -713,7 +772,11 @@ __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
         double rr = (double)sqrt((R)rr2);
         sum += P.cv * (P.re - rr) / P.re * (W.jratio[j] - ri);
     }
-    W.jbar_tmp[i] = c.J[i] / (ri + 2.0 * sum);
+    const double jb_new = c.J[i] / (ri + 2.0 * sum);
+    W.jbar_tmp[i] = jb_new;
+    const double V = P.V0 * c.J[i] / jb_new;   // vol_of with the smoothed Jbar
+    W.vol[i] = V;
+    W.volf[i] = (float)V;
 }
 
 void launch_smoothing(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -745,8 +808,10 @@ __global__ void __launch_bounds__(128) k_pass1(DevParams P, const Part c, Work W
     const int64_t cap = W.cap;
     double xi[3], pi_[3], vi[3];
     load_hat<D>(c, i, xi);
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
     load_phys<D>(c, i, pi_);
     load_vel<D>(c, i, vi);
+    const float4 vhi = W.velhi[i], vlo = W.vello[i];
     Acc<R> B[D * D], Ball[D * D], nsum[D], Gv[D * D], Gq[D * M], rho;
     double dwall2 = 1e300;
     const R inv_l = (R)P.inv_l, ad = (R)P.ad;
@@ -754,14 +819,10 @@ __global__ void __launch_bounds__(128) k_pass1(DevParams P, const Part c, Work W
     for (int k = 0; k < cnt; ++k) {
         int j = W.nbr[(int64_t)k * cap + i];
         int tj = c.type[j];
-        double xj[3];
-        load_hat<D>(c, j, xj);
         R r[D], rr2 = R(0);
+        pair_r<D, R>(c, W, j, xi, hfi, lfi, r);
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            r[K] = (R)(xj[K] - xi[K]);
-            rr2 += r[K] * r[K];
-        }
+        for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
         R rr = sqrt(rr2), w, dw;
         kern_wdw<R>(rr, inv_l, ad, w, dw);
         rho.add((R)P.V0 * w);
@@ -777,7 +838,7 @@ __global__ void __launch_bounds__(128) k_pass1(DevParams P, const Part c, Work W
             for (int L2 = 0; L2 < D; ++L2) Ball[K * D + L2].add(V0 * gw[K] * r[L2]);
         }
         if (tj == VIRTUAL) continue;
-        R Vj = (R)vol_of(P, c, j);
+        R Vj = vol_at<R>(W, j);
         R q[M];
         qvec<D, R>(r, q);
 #pragma unroll
@@ -788,13 +849,25 @@ __global__ void __launch_bounds__(128) k_pass1(DevParams P, const Part c, Work W
 #pragma unroll
             for (int a = 0; a < M; ++a) Gq[K * M + a].add(vg * q[a]);
         }
-        double vj[3] = {0.0, 0.0, 0.0};
-        if (tj == FLUID) load_vel<D>(c, j, vj);
+        R vij[D];
+        if constexpr (sizeof(R) == sizeof(float)) {   // mixed: hi/lo differences
+            if (tj == FLUID) {
+                hilo_diff<D>(W.velhi[j], W.vello[j], vhi, vlo, vij);
+            } else {
+                vij[0] = -(vhi.x + vlo.x);
+                if (D == 3) vij[1] = -(vhi.y + vlo.y);
+                vij[D - 1] = -(vhi.z + vlo.z);
+            }
+        } else {
+            double vj[3] = {0.0, 0.0, 0.0};
+            if (tj == FLUID) load_vel<D>(c, j, vj);
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) vij[cc] = (R)(vj[cc] - vi[cc]);
+        }
 #pragma unroll
         for (int cc = 0; cc < D; ++cc) {
-            R vij = (R)(vj[cc] - vi[cc]);
 #pragma unroll
-            for (int K = 0; K < D; ++K) Gv[cc * D + K].add(Vj * vij * gw[K]);
+            for (int K = 0; K < D; ++K) Gv[cc * D + K].add(Vj * vij[cc] * gw[K]);
         }
         if (tj == WALL) {
             double pj[3], d2 = 0.0;
@@ -957,6 +1030,7 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
     const int64_t cap = W.cap;
     double xi[3], vi[3];
     load_hat<D>(c, i, xi);
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
     load_vel<D>(c, i, vi);
     R L[D * D], Ct[D * M];
 #pragma unroll
@@ -967,6 +1041,11 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
 #pragma unroll
     for (int k = 0; k < D * D; ++k) gvd[k] = W.gv[(int64_t)k * cap + i];
     const double nui = W.nu[i];
+    constexpr bool MIXED = sizeof(R) == sizeof(float);
+    float gvf[D * D];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) gvf[k] = (float)gvd[k];
+    const float4 vhi = W.velhi[i], vlo = W.vello[i];
     Acc<R> Mm[M * M], bv[M * D], Gnu[D], Q[M * D];
     const R inv_l = (R)P.inv_l, ad = (R)P.ad;
     const int cnt = W.nbr_cnt[i];
@@ -974,16 +1053,21 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
         int j = W.nbr[(int64_t)k * cap + i];
         int tj = c.type[j];
         if (tj == VIRTUAL) continue;
-        double xj[3];
-        load_hat<D>(c, j, xj);
         R r[D], rr2 = R(0);
         double rd[D];
+        if constexpr (MIXED) {
+            pair_r<D, R>(c, W, j, xi, hfi, lfi, r);
+        } else {
+            double xj[3];
+            load_hat<D>(c, j, xj);
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            rd[K] = xj[K] - xi[K];
-            r[K] = (R)rd[K];
-            rr2 += r[K] * r[K];
+            for (int K = 0; K < D; ++K) {
+                rd[K] = xj[K] - xi[K];
+                r[K] = (R)rd[K];
+            }
         }
+#pragma unroll
+        for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
         if (rr2 == R(0)) continue;
         R rr = sqrt(rr2), w, dw;
         kern_wdw<R>(rr, inv_l, ad, w, dw);
@@ -998,7 +1082,7 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
             gt[K] = s;
             rg += r[K] * s;
         }
-        R Vj = (R)vol_of(P, c, j);
+        R Vj = vol_at<R>(W, j);
         R F = rg / (rr2 * rr2), VF = Vj * F;
         R q[M], pv[M];
         qvec<D, R>(r, q);
@@ -1018,23 +1102,50 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
             for (int K = 0; K < D; ++K) Q[a * D + K].add(vq * r[K]);
         }
         if (predictor) {
-            double vj[3] = {0.0, 0.0, 0.0};
-            if (tj == FLUID) load_vel<D>(c, j, vj);
+            // v_ij - r_ij . <grad v>_i cancels O(|grad v| r) down to O(|D v| r^2).
+            // FP64 form: formed in FP64.  Mixed form: v_ij from the hi/lo velocities
+            // (relative error ~u, as the FP64 difference rounded), r . <grad v> in
+            // FP32; the remainder then carries ~5u |v_ij|, a relative error of
+            // ~5u |v_ij| / |e| in e, which only enters the viscous term.
+            if constexpr (MIXED) {
+                float vij[D];
+                if (tj == FLUID) {
+                    hilo_diff<D>(W.velhi[j], W.vello[j], vhi, vlo, vij);
+                } else {
+                    vij[0] = -(vhi.x + vlo.x);
+                    if (D == 3) vij[1] = -(vhi.y + vlo.y);
+                    vij[D - 1] = -(vhi.z + vlo.z);
+                }
 #pragma unroll
-            for (int cc = 0; cc < D; ++cc) {
-                // v_ij - r_ij . <grad v>_i cancels O(|grad v| r) down to O(|D v| r^2):
-                // formed in FP64, then summed in R
-                double rgv = 0.0;
+                for (int cc = 0; cc < D; ++cc) {
+                    float rgv = 0.f;
 #pragma unroll
-                for (int K = 0; K < D; ++K) rgv += rd[K] * gvd[cc * D + K];
-                R e = (R)((vj[cc] - vi[cc]) - rgv);
+                    for (int K = 0; K < D; ++K) rgv += r[K] * gvf[cc * D + K];
+                    const R e = vij[cc] - rgv;
 #pragma unroll
-                for (int a = 0; a < M; ++a) bv[a * D + cc].add(VF * q[a] * e);
+                    for (int a = 0; a < M; ++a) bv[a * D + cc].add(VF * q[a] * e);
+                }
+            } else {
+                double vj[3] = {0.0, 0.0, 0.0};
+                if (tj == FLUID) load_vel<D>(c, j, vj);
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) {
+                    double rgv = 0.0;
+#pragma unroll
+                    for (int K = 0; K < D; ++K) rgv += rd[K] * gvd[cc * D + K];
+                    R e = (R)((vj[cc] - vi[cc]) - rgv);
+#pragma unroll
+                    for (int a = 0; a < M; ++a) bv[a * D + cc].add(VF * q[a] * e);
+                }
             }
-            double nuj = tj == FLUID ? W.nu[j] : P.nu_k;
-            R dn = (R)(nuj - nui);
+            // without the Smagorinsky model nu is nu_K everywhere and every
+            // difference is zero (adding zeros leaves the compensated sums as they are)
+            if (P.smag) {
+                double nuj = tj == FLUID ? W.nu[j] : P.nu_k;
+                R dn = (R)(nuj - nui);
 #pragma unroll
-            for (int K = 0; K < D; ++K) Gnu[K].add(Vj * dn * gw[K]);
+                for (int K = 0; K < D; ++K) Gnu[K].add(Vj * dn * gw[K]);
+            }
         }
     }
     double Md[M * M];
@@ -1084,6 +1195,14 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
             W.acc[(int64_t)cc * cap + i] = acc[cc];
             W.vstar[(int64_t)cc * cap + i] = vi[cc] + P.dt * acc[cc];
         }
+        {
+            double vs[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) vs[cc] = W.vstar[(int64_t)cc * cap + i];
+            float4 lo;
+            W.vshi[i] = f4_hilo_split(vs[0], D == 3 ? vs[1] : 0.0, vs[D - 1], lo);
+            W.vslo[i] = lo;
+        }
     }
     // pressure-equation row for unknowns (fluid, not free surface)
     if (!predictor || W.fs[i]) {
@@ -1124,14 +1243,10 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
         int j = W.nbr[(int64_t)k * cap + i];
         int tj = c.type[j];
         if (tj == VIRTUAL) continue;
-        double xj[3];
-        load_hat<D>(c, j, xj);
         R r[D], rr2 = R(0);
+        pair_r<D, R>(c, W, j, xi, hfi, lfi, r);
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            r[K] = (R)(xj[K] - xi[K]);
-            rr2 += r[K] * r[K];
-        }
+        for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
         if (rr2 == R(0)) continue;
         R rr = sqrt(rr2), w, dw;
         kern_wdw<R>(rr, inv_l, ad, w, dw);
@@ -1151,7 +1266,7 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
         qvec<D, R>(r, q);
 #pragma unroll
         for (int a = 0; a < M; ++a) wq += wr[a] * q[a];
-        R Vj = (R)vol_of(P, c, j);
+        R Vj = vol_at<R>(W, j);
         double aij = (double)(Vj * (c0r * gt[D - 1] + R(2) * F * wq - R(2) * ug));
         if (tj == FLUID) {
             diag -= aij;
@@ -1210,11 +1325,16 @@ __global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, 
     }
     double xi[3], vsi[D], acci[D];
     load_hat<D>(c, i, xi);
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
 #pragma unroll
     for (int cc = 0; cc < D; ++cc) {
         vsi[cc] = W.vstar[(int64_t)cc * cap + i];
         acci[cc] = W.acc[(int64_t)cc * cap + i];
     }
+    R wall_dv[D];   // a wall neighbour's v_j - v*_i, the same for every wall neighbour
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) wall_dv[cc] = (R)(P.dt * acci[cc] - vsi[cc]);
+    const float4 vshi_i = W.vshi[i], vslo_i = W.vslo[i];
     Acc<R> X[D * D];
     const R inv_l = (R)P.inv_l, ad = (R)P.ad;
     const int cnt = W.nbr_cnt[i];
@@ -1222,22 +1342,27 @@ __global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, 
         int j = W.nbr[(int64_t)k * cap + i];
         int tj = c.type[j];
         if (tj == VIRTUAL) continue;
-        double xj[3];
-        load_hat<D>(c, j, xj);
         R r[D], rr2 = R(0);
+        pair_r<D, R>(c, W, j, xi, hfi, lfi, r);
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            r[K] = (R)(xj[K] - xi[K]);
-            rr2 += r[K] * r[K];
-        }
+        for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
         if (rr2 == R(0)) continue;
         R rr = sqrt(rr2), w, dw;
         kern_wdw<R>(rr, inv_l, ad, w, dw);
-        R fac = -dw / rr, Vj = (R)vol_of(P, c, j);
+        R fac = -dw / rr, Vj = vol_at<R>(W, j);
+        R dv[D];
+        if (tj != FLUID) {
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) dv[cc] = wall_dv[cc];
+        } else if constexpr (sizeof(R) == sizeof(float)) {   // mixed: hi/lo differences
+            hilo_diff<D>(W.vshi[j], W.vslo[j], vshi_i, vslo_i, dv);
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) dv[cc] = (R)(W.vstar[(int64_t)cc * cap + j] - vsi[cc]);
+        }
 #pragma unroll
         for (int cc = 0; cc < D; ++cc) {
-            double vj = tj == FLUID ? W.vstar[(int64_t)cc * cap + j] : P.dt * acci[cc];
-            R e = Vj * (R)(vj - vsi[cc]) * fac;
+            R e = Vj * dv[cc] * fac;
 #pragma unroll
             for (int K = 0; K < D; ++K) X[cc * D + K].add(e * r[K]);
         }
@@ -2981,6 +3106,7 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
     const int64_t cap = W.cap;
     double xi[3], pi_[3], acci[D];
     load_hat<D>(c, i, xi);
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
     load_phys<D>(c, i, pi_);
 #pragma unroll
     for (int cc = 0; cc < D; ++cc) acci[cc] = W.acc[(int64_t)cc * cap + i];
@@ -2992,14 +3118,10 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
         int j = W.nbr[(int64_t)k * cap + i];
         int tj = c.type[j];
         if (tj == VIRTUAL) continue;
-        double xj[3];
-        load_hat<D>(c, j, xj);
         R r[D], rr2 = R(0);
+        pair_r<D, R>(c, W, j, xi, hfi, lfi, r);
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            r[K] = (R)(xj[K] - xi[K]);
-            rr2 += r[K] * r[K];
-        }
+        for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
         if (rr2 == R(0)) continue;
         R rr = sqrt(rr2), w, dw;
         kern_wdw<R>(rr, inv_l, ad, w, dw);
@@ -3013,7 +3135,7 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
             for (int K = 0; K < D; ++K) s += (pj[K] - pi_[K]) * acci[K];
             pij = P.rho * s;
         }
-        R e = (R)vol_of(P, c, j) * (R)pij * (-dw / rr);
+        R e = vol_at<R>(W, j) * (R)pij * (-dw / rr);
 #pragma unroll
         for (int K = 0; K < D; ++K) G[K].add(e * r[K]);
     }
