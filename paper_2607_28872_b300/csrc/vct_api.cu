@@ -386,7 +386,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         j.n = (int)states[k]->n;
         j.maxit = c->P.max_iter;
         j.rtol = c->P.rtol;
-        j.inner_floor = prec == VCT_MIXED ? 1e-4 : 0.0;
+        j.inner_floor = c->P.inner_floor;
         j.b0 = b0;
         j.nb = (unsigned)nb[k];
         b0 += (unsigned)nb[k];
@@ -617,6 +617,8 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     P.ds_overlap = prm->ds_overlap;
     P.xsph_eps = prm->xsph_eps;
     P.pguess = getenv("VCT_PGUESS") ? atoi(getenv("VCT_PGUESS")) : 2;   // 0: none, 1: linear
+    P.inner_floor = prm->precision == VCT_MIXED ? 1e-4 : 0.0;
+    if (prm->precision == VCT_MIXED && getenv("VCT_INNER_FLOOR")) P.inner_floor = atof(getenv("VCT_INNER_FLOOR"));
     P.cell_h = P.re;
     P.inv_cell_h = 1.0 / P.cell_h;
     int64_t ncell = 1;

@@ -28,6 +28,7 @@ struct DevParams {
     int pguess;               // order of the pressure extrapolation of the initial guess
     int pad2;
     double gamma, cv, cs, ds, H, H_hat, amin, amax, lam_lo, lam_hi, rtol;
+    double inner_floor;       // mixed form: each FP32 BiCGSTAB pass stops at this relative residual
     double box_lo[3], cell_h, inv_cell_h;
     double h0, slope_x, slope_y, cos_amp, cos_len;
     double gamp[MAXG], gcx[MAXG], gcy[MAXG], gwid[MAXG];

@@ -1832,7 +1832,7 @@ int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot
     (void)cur;
     (void)step_slot;
     int nn = (int)n, maxit = P.max_iter;
-    double rtol = P.rtol, floor_ = P.precision == VCT_MIXED ? 1e-4 : 0.0;
+    double rtol = P.rtol, floor_ = P.inner_floor;
     int32_t *it_out = W.kiters;
     double *res_out = W.kresid;
     // a grid no larger than the rows need: fewer arrivals per barrier
@@ -3034,7 +3034,7 @@ int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nbl
                      cudaStream_t st)
 {
     int nn = (int)n, maxit = P.max_iter;
-    double rtol = P.rtol, floor_ = P.precision == VCT_MIXED ? 1e-4 : 0.0;
+    double rtol = P.rtol, floor_ = P.inner_floor;
     int32_t *it_out = W.kiters;
     double *res_out = W.kresid;
     const int G = P.dim == 2 ? 4 : 8;
