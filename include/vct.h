@@ -56,10 +56,14 @@ typedef enum {
 typedef enum { VCT_MAP_E = 0, VCT_MAP_BF = 1, VCT_MAP_BFE = 2, VCT_MAP_SIGMA = 3 } vct_map_kind;
 
 /* FP64: every sum and solve in double.  MIXED: neighbour sums in FP32 with
- * compensated (Kahan) accumulation, pair offsets r_ij formed in FP64 and
- * rounded to FP32, the cancelling difference phi_ij - r_ij . <grad phi>_i
- * formed in FP64; inversion of B_i, the SPH(2) solves with M_i and the
- * pressure-equation iterate and residual in FP64. */
+ * compensated (Kahan) accumulation; in the step's passes 1 and 2, right side
+ * and corrector, the pair offsets r_ij and velocity differences v_ij (v*_ij)
+ * come from each particle's value kept as two FP32 numbers (hi + lo), as
+ * accurate as the FP64 difference rounded to FP32, and the remainder
+ * v_ij - r_ij . <grad v>_i is formed in FP32 from them (sph2_derivatives and the
+ * regularisation form their differences in FP64 and round them); inversion of
+ * B_i, the SPH(2) solves with M_i and the pressure-equation iterate and
+ * residual in FP64. */
 typedef enum { VCT_FP64 = 0, VCT_MIXED = 1 } vct_precision;
 
 #define VCT_MAX_GAUSS 32
@@ -103,7 +107,7 @@ typedef struct {
     int32_t max_neighbours; /* neighbour-list capacity per particle (0: 64 in 2-D, 160 in 3-D) */
     int32_t preconditioner; /* pressure solve: 0 plain BiCGSTAB; 1 BiCGSTAB preconditioned by an
                                aggregation multigrid V-cycle on the cell grid (Jacobi damping
-                               0.8 / 0.7 and coarse-correction scale 1.3 / 1.8 in 2-D / 3-D,
+                               0.85 / 0.7 and coarse-correction scale 1.3 / 1.2 in 2-D / 3-D,
                                z-only coarsening while the operator's z coupling dominates,
                                8 coarsest sweeps, small levels in block 0's shared memory:
                                96 KB up to 75k particles in 2-D / 30k in 3-D, 16 KB above, where the solver
@@ -114,7 +118,10 @@ typedef struct {
                                VCT_MG_PRESMOOTH (0: V(0,1)), VCT_MG_SHIFT (aggregation
                                2^s per axis), VCT_SOLVE_BLOCKS (grid cap), VCT_PGUESS
                                (initial guess: 0 p^N, 1 linear, 2 quadratic extrapolation
-                               of the context's last pressures, the default) */
+                               of the context's last pressures, the default),
+                               VCT_INNER_FLOOR (mixed form: relative residual at which
+                               each FP32 BiCGSTAB pass hands back to the FP64 residual,
+                               1e-4) */
     /* Particle regularisation after the position update (Sec. 4.1 applies all
      * three; 0 switches each off).  It acts in projected space with the
      * step's neighbour lists; pair sums in FP64 (FP64 form) or compensated
