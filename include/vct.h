@@ -57,11 +57,12 @@ typedef enum { VCT_MAP_E = 0, VCT_MAP_BF = 1, VCT_MAP_BFE = 2, VCT_MAP_SIGMA = 3
 
 /* FP64: every sum and solve in double.  MIXED: neighbour sums in FP32 with
  * compensated (Kahan) accumulation; in the step's passes 1 and 2, right side
- * and corrector, the pair offsets r_ij and velocity differences v_ij (v*_ij)
+ * corrector, J-bar smoothing and regularisation, the pair offsets r_ij and
+ * velocity differences v_ij (v*_ij)
  * come from each particle's value kept as two FP32 numbers (hi + lo), as
  * accurate as the FP64 difference rounded to FP32, and the remainder
- * v_ij - r_ij . <grad v>_i is formed in FP32 from them (sph2_derivatives and the
- * regularisation form their differences in FP64 and round them); inversion of
+ * v_ij - r_ij . <grad v>_i is formed in FP32 from them (sph2_derivatives forms
+ * its differences in FP64 and rounds them); inversion of
  * B_i, the SPH(2) solves with M_i and the pressure-equation iterate and
  * residual in FP64. */
 typedef enum { VCT_FP64 = 0, VCT_MIXED = 1 } vct_precision;
@@ -125,7 +126,8 @@ typedef struct {
     /* Particle regularisation after the position update (Sec. 4.1 applies all
      * three; 0 switches each off).  It acts in projected space with the
      * step's neighbour lists; pair sums in FP64 (FP64 form) or compensated
-     * FP32 on FP64 differences (mixed form), corrections applied in FP64:
+     * FP32 on the hi/lo FP32 position differences (mixed form), corrections
+     * applied in FP64:
      *   ds_overlap  dynamic stabilization: pairs closer than (1 - ds_overlap) d0
      *               are pushed back to that distance within the step (0.4)
      *   xsph_eps    XSPH velocity smoothing of free-surface particles (5e-3)

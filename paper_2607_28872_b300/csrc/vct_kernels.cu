@@ -763,14 +763,27 @@ __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
     load_hat<D>(c, i, xi);
     double ri = W.jratio[i], sum = 0.0;
     int cnt = W.nbr_cnt[i];
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
+    const float cvf = (float)P.cv, ref = (float)P.re, inv_re = (float)(1.0 / P.re);
     for (int k = 0; k < cnt; ++k) {
         int j = W.nbr[(int64_t)k * W.cap + i];
         if (c.type[j] != FLUID) continue;
-        double xj[3], rr2 = 0.0;
-        load_hat<D>(c, j, xj);
-        for (int K = 0; K < D; ++K) rr2 += (xj[K] - xi[K]) * (xj[K] - xi[K]);
-        double rr = (double)sqrt((R)rr2);
-        sum += P.cv * (P.re - rr) / P.re * (W.jratio[j] - ri);
+        if constexpr (sizeof(R) == sizeof(float)) {
+            // mixed: distance and weight in FP32 from the hi/lo positions; the
+            // J/Jbar difference (small against J/Jbar itself) and the sum in FP64
+            float d[D], rr2 = 0.f;
+            hilo_diff<D>(W.hatf[j], W.hatlo[j], hfi, lfi, d);
+#pragma unroll
+            for (int K = 0; K < D; ++K) rr2 += d[K] * d[K];
+            const float wgt = cvf * (ref - sqrtf(rr2)) * inv_re;
+            sum += (double)wgt * (W.jratio[j] - ri);
+        } else {
+            double xj[3], rr2 = 0.0;
+            load_hat<D>(c, j, xj);
+            for (int K = 0; K < D; ++K) rr2 += (xj[K] - xi[K]) * (xj[K] - xi[K]);
+            double rr = sqrt(rr2);
+            sum += P.cv * (P.re - rr) / P.re * (W.jratio[j] - ri);
+        }
     }
     const double jb_new = c.J[i] / (ri + 2.0 * sum);
     W.jbar_tmp[i] = jb_new;
@@ -3271,6 +3284,12 @@ __global__ void __launch_bounds__(128) k_reg_geom(DevParams P, Part c, Work W, i
     W.rxh[i] = c.x[i];
     if (D == 3) W.rxh[cap + i] = y;
     W.rxh[(D - 1) * cap + i] = zh;
+    {   // hi/lo FP32 copy for the mixed form's pair differences (the step's copy
+        // is no longer needed: the next step's reorder writes it again)
+        float4 lo;
+        W.hatf[i] = f4_hilo_split(c.x[i], y, zh, lo);
+        W.hatlo[i] = lo;
+    }
     W.rmet[i] = J;
     W.rmet[cap + i] = sx;
     W.rmet[2 * cap + i] = sy;
@@ -3303,19 +3322,23 @@ __global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int
     double xi[D];
     R du[D];
     reg_load<D>(W, i, xi);
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
 #pragma unroll
     for (int K = 0; K < D; ++K) du[K] = R(0);
     const int cnt = W.nbr_cnt[i];
     for (int k = 0; k < cnt; ++k) {
         const int j = W.nbr[(int64_t)k * cap + i];
-        double xj[D];
         R r[D], r2 = R(0);
-        reg_load<D>(W, j, xj);
+        if constexpr (sizeof(R) == sizeof(float)) {   // mixed: hi/lo differences
+            hilo_diff<D>(W.hatf[j], W.hatlo[j], hfi, lfi, r);
+        } else {
+            double xj[D];
+            reg_load<D>(W, j, xj);
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            r[K] = (R)(xj[K] - xi[K]);
-            r2 += r[K] * r[K];
+            for (int K = 0; K < D; ++K) r[K] = (R)(xj[K] - xi[K]);
         }
+#pragma unroll
+        for (int K = 0; K < D; ++K) r2 += r[K] * r[K];
         const R rr = sqrt(r2);
         if (!(rr < ddsr) || rr == R(0)) continue;
         const R f = (c.type[j] == FLUID ? R(0.5) : R(1)) * (ddsr - rr) / (dtr * rr);
@@ -3350,16 +3373,20 @@ __global__ void __launch_bounds__(128) k_reg_apply(DevParams P, Part c, Work W, 
 #pragma unroll
     for (int K = 0; K < D; ++K) ui[K] = W.rud[K * cap + i];
     const int cnt = (do_x || do_s) ? W.nbr_cnt[i] : 0;
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
     for (int k = 0; k < cnt; ++k) {
         const int j = W.nbr[(int64_t)k * cap + i];
-        double xj[D];
         R r[D], r2 = R(0);
-        reg_load<D>(W, j, xj);
+        if constexpr (sizeof(R) == sizeof(float)) {   // mixed: hi/lo differences, r = x_i - x_j
+            hilo_diff<D>(hfi, lfi, W.hatf[j], W.hatlo[j], r);
+        } else {
+            double xj[D];
+            reg_load<D>(W, j, xj);
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            r[K] = (R)(xi[K] - xj[K]);
-            r2 += r[K] * r[K];
+            for (int K = 0; K < D; ++K) r[K] = (R)(xi[K] - xj[K]);
         }
+#pragma unroll
+        for (int K = 0; K < D; ++K) r2 += r[K] * r[K];
         const R rr = sqrt(r2);
         if (rr == R(0)) continue;
         R w, dw;
