@@ -2033,7 +2033,15 @@ __global__ void k_urow_scatter(Work W, int n)
     if (i < n && W.urow_flag[i]) W.urow[W.urow_pos[i]] = i;
 }
 
-constexpr int SMALL_LEVEL = 4096;   // coarse levels up to this size are built by one block
+// coarse levels up to this size are built by one block (2-D wave, set-up per step
+// by the threshold: 4096 nodes 88 us, 2048 57, 1100 57, 512 55, 256 61; VCT_MG_SMALL
+// overrides)
+constexpr int SMALL_LEVEL = 1024;
+static int small_level()
+{
+    static const int v = getenv("VCT_MG_SMALL") ? atoi(getenv("VCT_MG_SMALL")) : SMALL_LEVEL;
+    return v;
+}
 
 void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st,
                      bool rows_list)
@@ -2049,7 +2057,7 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
     if (P.dim == 2) k_mg_level1<2><<<g1, 256, 0, st>>>(W, M, mixed);
     else k_mg_level1<3><<<g1, 256, 0, st>>>(W, M, mixed);
     int l = 1;
-    for (; l < M.L && M.n[l + 1] > SMALL_LEVEL; ++l) {
+    for (; l < M.L && M.n[l + 1] > small_level(); ++l) {
         const unsigned g = (unsigned)((M.n[l + 1] + 127) / 128);
         if (P.dim == 2) k_mg_coarsen<2><<<g, 128, 0, st>>>(W, M, l);
         else k_mg_coarsen<3><<<g, 128, 0, st>>>(W, M, l);
@@ -2063,7 +2071,7 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
 int mg_setup_launches(const MG &M)
 {
     int l = 1, n = 2;   // dsc, level 1
-    for (; l < M.L && M.n[l + 1] > SMALL_LEVEL; ++l) ++n;
+    for (; l < M.L && M.n[l + 1] > small_level(); ++l) ++n;
     return n + (l < M.L ? 1 : 0);
 }
 
