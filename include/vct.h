@@ -269,6 +269,24 @@ vct_status vct_map_backward(vct_ctx *ctx, const vct_state *state, const double *
  * no work.  out (host, may be NULL) receives solve statistics. */
 vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *out);
 
+/* Adjoint of the pressure solve of the context's last step (Sec. 3.3, Eqs.
+ * VCT_ppe and PNC give the system A p = b on the unknown rows, the fluid
+ * particles off the free surface).  For p = A^-1 b and a gradient p_bar of a
+ * loss with respect to p, writes b_bar = A^-T p_bar, the gradient with respect
+ * to b; the gradient with respect to A's coefficients is then -b_bar p^T on A's
+ * pattern.  The operator is the one the forward solve used (FP32 coefficients
+ * in the mixed form); the transposed system is solved in FP64 by BiCGSTAB with
+ * a Jacobi right preconditioner to the context's krylov_rtol (relative to
+ * |p_bar|, at most krylov_max_iter iterations; VCT_ERR_NOCONV otherwise).
+ * p_bar, b_bar: device arrays of n doubles in caller order, n the particle
+ * count of that step; entries of rows that are not unknowns are ignored in
+ * p_bar and written as 0 in b_bar.  Returns VCT_ERR_ARG if the context holds
+ * no pressure system (no step yet, or a call since then that sorted the
+ * particles again: vct_build_neighbours, sph2_derivatives).  Overwrites the
+ * context's neighbour lists and solver vectors, which the next step rebuilds.
+ * out (host, may be NULL) receives the iteration count and residual. */
+vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct_stats *out);
+
 /* Ensemble: advance n_scen independent scenarios (one context and one device
  * state each, uneven particle counts allowed) by nsteps steps in one call,
  * with no host synchronisation until the end, where each scenario's status is

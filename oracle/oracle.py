@@ -290,3 +290,29 @@ def step(sc, state=None, nsteps=1, probe=False, x_test=None, **over):
         info["n_iter"] = pr.n_iter
         info["resid"] = pr.resid
     return st, info
+
+
+def ppe_system(sc, **over):
+    """The pressure equation of one step from the scenario's state (Sec. 3.3,
+    Eqs. VCT_ppe and PNC) as a dense matrix on its unknown rows (fluid particles
+    off the free surface), assembled column by column from the oracle's own
+    operator application (the probe's A x for unit vectors x), with the step's
+    right side b and solution p.  Returns (rows, A, b, p); rows are caller
+    indices.  One oracle step per unknown: small cases only."""
+    st, info = step(sc, probe=True, **over)
+    fs = info["fs"]
+    rows = np.flatnonzero((sc.type == 0) & (fs == 0))
+    m = rows.size
+    A = np.zeros((m, m))
+    for k, col in enumerate(rows):
+        e = np.zeros(sc.n)
+        e[col] = 1.0
+        _, ik = step(sc, probe=True, x_test=e, **over)
+        A[:, k] = ik["ppe_Ax"][rows]
+    return rows, A, info["ppe_b"][rows].copy(), st.p[rows].copy()
+
+
+def ppe_adjoint(A, p_bar):
+    """b_bar = A^-T p_bar: the adjoint of p = A^-1 b with respect to b (the
+    transpose solve; numpy's dense LU)."""
+    return np.linalg.solve(A.T, p_bar)

@@ -50,6 +50,7 @@ struct vct_ctx {
     cudaStream_t gst;          // the batched solve's stream
     long long serial;          // unique per context, never reused
     int graph_steps;           // steps of the current call replayed from the graph
+    int64_t ppe_n;             // particles of the last pressure system still held (0: none)
     std::vector<cudaEvent_t> ev;      // 2 per stage per profiled step
     std::vector<int> ev_stage;        // stage of each recorded pair
     int ev_used;
@@ -195,6 +196,7 @@ vct_status finish(vct_ctx *c, vct_stats *out, int nsteps)
 // Map, cell sort and neighbour lists of the current positions.
 void geometry(vct_ctx *c, int64_t n)
 {
+    c->ppe_n = 0;   // a new cell order: the held pressure system no longer matches it
     { StageTimer t(c, VCT_STAGE_MAP); launch_map_key(c->P, cur(c), c->W, n, c->st); }
     { StageTimer t(c, VCT_STAGE_SORT); launch_sort(c->P, cur(c), alt(c), c->W, n, c->st); }
     c->cur_is_A = !c->cur_is_A;
@@ -252,6 +254,7 @@ int step_solve(vct_ctx *c, int64_t n, int step)
 {
     StageTimer t(c, VCT_STAGE_KRYLOV);
     c->launches += 1;
+    c->ppe_n = n;
     if (c->precond) return launch_krylov_mg(c->P, c->W, c->mg, n, c->coop_blocks_mg, c->st);
     return launch_krylov(c->P, cur(c), c->W, n, step, c->coop_blocks, c->st);
 }
@@ -447,6 +450,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             vct_ctx *c = ctxs[k];
             cudaStreamWaitEvent(c->st, c0->bev, 0);
             c->launches += 1;   // its share of the batched solve
+            c->ppe_n = states[k]->n;
             step_post(c, states[k]->n, step, nsteps, nullptr);
         }
         return le ? (cudaError_t)le : cudaSuccess;
@@ -992,6 +996,18 @@ VCT_API vct_status vct_batch_step(vct_ctx *const *ctxs, vct_state *const *states
         ctxs[k]->st = saved[k];
     }
     return first;
+}
+
+VCT_API vct_status vct_ppe_adjoint(vct_ctx *c, const double *p_bar, double *b_bar, vct_stats *out)
+{
+    if (!c || !p_bar || !b_bar) return VCT_ERR_ARG;
+    if (c->ppe_n <= 0) return VCT_ERR_ARG;   // no pressure system held
+    const int64_t n = c->ppe_n;
+    reset_status(c);
+    const int e = launch_ppe_adjoint(c->P, cur(c), c->W, n, p_bar, b_bar, c->st);
+    c->launches += 4;   // gather, transposed slots, solve, scatter
+    if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, out, 1);
 }
 
 VCT_API vct_status vct_step_probe(vct_ctx *c, vct_state *s, const vct_probe *pr, vct_stats *out)

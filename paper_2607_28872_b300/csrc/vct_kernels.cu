@@ -4156,6 +4156,221 @@ void launch_store(const DevParams &P, Part cur, vct_state s, int64_t n, const in
     k_store_w<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, cur, s, (int)n, status);
 }
 
+
+// ---------------------------------------------------------------------------
+// a12 (part): adjoint of the pressure solve.  The step solves A p = b on the
+// unknown rows (fluid particles off the free surface; Eqs. VCT_ppe, PNC).  For
+// p = A^-1 b, a loss gradient p_bar gives b_bar = A^-T p_bar, and the
+// coefficients' adjoint is A_bar = -b_bar p^T on A's pattern.
+//
+// A's pattern is symmetric: row i holds the unknown neighbours of i, and the
+// neighbour relation is symmetric in projected space.  So row j of A^T has the
+// columns of row j of A, and its coefficient in column i is row i's
+// coefficient in column j; k_adj_tslot finds that slot of row i once per call
+// (in the neighbour-list scratch, which the next step rebuilds).  The solve is
+// BiCGSTAB (van der Vorst 1992) in FP64 with a Jacobi (diagonal) right
+// preconditioner, one thread per row, in one cooperative launch; the operator
+// is the one the forward solve used (FP32 coefficients in the mixed form).
+// ---------------------------------------------------------------------------
+__global__ void k_adj_gather(const Part c, Work W, int n, const double *p_bar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    W.bvec[i] = W.pcnt[i] >= 0 ? p_bar[c.orig[i]] : 0.0;
+    W.kx[i] = 0.0;
+}
+
+template <int D>
+__global__ void k_adj_tslot(Work W, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int pc = W.pcnt[j];
+    const int64_t cap = W.cap;
+    for (int k = 0; k < pc; ++k) {
+        const int i = W.pcol[ell_at<ell_group<D>()>(k, j, cap)];
+        const int pi = W.pcnt[i];
+        int t = -1;
+        for (int q = 0; q < pi && t < 0; ++q)
+            if (W.pcol[ell_at<ell_group<D>()>(q, i, cap)] == j) t = q;
+        // only a truncated neighbour list (capacity error) breaks the symmetry
+        if (t < 0) set_error(W.status, VCT_ERR_CAPACITY, j);
+        W.nbr[(int64_t)k * cap + j] = t;
+    }
+}
+
+// (A^T x)_j for an unknown row j
+template <int D, typename CT>
+__device__ __forceinline__ double adj_row(const Work &W, int j, const double *x)
+{
+    const int64_t cap = W.cap;
+    const int pc = W.pcnt[j];
+    double s = W.diag[j] * __ldcg(x + j);
+    for (int k = 0; k < pc; ++k) {
+        const int i = W.pcol[ell_at<ell_group<D>()>(k, j, cap)];
+        const int t = W.nbr[(int64_t)k * cap + j];
+        if (t >= 0) s += (double)coef<CT>(W, ell_at<ell_group<D>()>(t, i, cap)) * __ldcg(x + i);
+    }
+    return s;
+}
+
+// Jacobi preconditioner: 1 / diag (1 where a row has no coupling at all)
+__device__ __forceinline__ double adj_dinv(const Work &W, int i)
+{
+    const double d = W.diag[i];
+    return d != 0.0 ? 1.0 / d : 1.0;
+}
+
+template <int D, typename CT>
+__global__ void __launch_bounds__(KT) k_adj_bicgstab(Work W, int n, int maxit, double rtol,
+                                                      int32_t *iters_out, double *resid_out)
+{
+    if (step_failed(W.status)) return;
+    const unsigned nb = gridDim.x;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gth = gridDim.x * blockDim.x;
+    const double *g = W.bvec;
+    double *x = W.kx, *r = W.kf, *rh = (double *)W.kr, *p = (double *)W.kp0, *ph = (double *)W.kp1;
+    double *v = (double *)W.kv0, *s = (double *)W.ks, *sh = (double *)W.kv1, *t = (double *)W.kt;
+    // r = g (x = 0), rh = r, p = r, ph = D^-1 p; |g|^2
+    double part[1] = {0.0};
+    for (int i = gtid; i < n; i += gth) {
+        if (W.pcnt[i] < 0) continue;
+        const double gi = g[i];
+        r[i] = gi;
+        rh[i] = gi;
+        p[i] = gi;
+        ph[i] = gi * adj_dinv(W, i);
+        part[0] += gi * gi;
+    }
+    block_partials<1>(part, W.partial);
+    if (!grid_barrier(W.bar, nb, W.status)) return;
+    double tot[1];
+    grid_totals<1>(W.partial, nb, tot);
+    const double bn = sqrt(tot[0]);
+    double rho = tot[0], rn = bn;
+    int it = 0;
+    bool fail = false;
+    while (bn > 0.0 && rn > rtol * bn) {
+        if (it >= maxit) {
+            fail = true;
+            break;
+        }
+        ++it;
+        // v = A^T ph; (rh, v)
+        double pv[1] = {0.0};
+        for (int i = gtid; i < n; i += gth) {
+            if (W.pcnt[i] < 0) continue;
+            const double vi = adj_row<D, CT>(W, i, ph);
+            v[i] = vi;
+            pv[0] += rh[i] * vi;
+        }
+        block_partials<1>(pv, W.partial);
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        grid_totals<1>(W.partial, nb, tot);
+        if (tot[0] == 0.0) {
+            fail = true;
+            break;
+        }
+        const double alpha = rho / tot[0];
+        // s = r - alpha v, sh = D^-1 s
+        for (int i = gtid; i < n; i += gth) {
+            if (W.pcnt[i] < 0) continue;
+            const double si = r[i] - alpha * v[i];
+            s[i] = si;
+            sh[i] = si * adj_dinv(W, i);
+        }
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        // t = A^T sh; (t, s), (t, t), (s, s), (rh, s), (rh, t)
+        double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i = gtid; i < n; i += gth) {
+            if (W.pcnt[i] < 0) continue;
+            const double ti = adj_row<D, CT>(W, i, sh), si = s[i], hi = rh[i];
+            t[i] = ti;
+            q[0] += ti * si;
+            q[1] += ti * ti;
+            q[2] += si * si;
+            q[3] += hi * si;
+            q[4] += hi * ti;
+        }
+        block_partials<5>(q, W.partial);
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        double tq[5];
+        grid_totals<5>(W.partial, nb, tq);
+        const double omega = tq[1] > 0.0 ? tq[0] / tq[1] : 0.0;
+        const double rho_new = tq[3] - omega * tq[4];
+        rn = sqrt(fmax(tq[2] - 2.0 * omega * tq[0] + omega * omega * tq[1], 0.0));
+        if (omega == 0.0 || rho_new == 0.0) {   // the update below still applies alpha
+            fail = rn > rtol * bn;
+        }
+        const double beta = (rho_new / rho) * (alpha / (omega != 0.0 ? omega : 1.0));
+        // x += alpha ph + omega sh; r = s - omega t; p = r + beta (p - omega v); ph = D^-1 p
+        for (int i = gtid; i < n; i += gth) {
+            if (W.pcnt[i] < 0) continue;
+            x[i] += alpha * ph[i] + omega * sh[i];
+            const double ri = s[i] - omega * t[i];
+            r[i] = ri;
+            const double pi = ri + beta * (p[i] - omega * v[i]);
+            p[i] = pi;
+            ph[i] = pi * adj_dinv(W, i);
+        }
+        rho = rho_new;
+        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (omega == 0.0 || rho_new == 0.0) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (fail) set_error(W.status, VCT_ERR_NOCONV, -1);
+        iters_out[0] += it;
+        if (it > iters_out[1]) iters_out[1] = it;
+        iters_out[2] = it;
+        *resid_out = bn > 0.0 ? rn / bn : 0.0;
+    }
+}
+
+__global__ void k_adj_scatter(const Part c, Work W, int n, double *b_bar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    b_bar[c.orig[i]] = W.pcnt[i] >= 0 ? W.kx[i] : 0.0;
+}
+
+static const void *adj_fn(int precision, int dim)
+{
+    if (precision == VCT_MIXED)
+        return dim == 2 ? (const void *)k_adj_bicgstab<2, float> : (const void *)k_adj_bicgstab<3, float>;
+    return dim == 2 ? (const void *)k_adj_bicgstab<2, double> : (const void *)k_adj_bicgstab<3, double>;
+}
+
+int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, int64_t n, const double *p_bar,
+                       double *b_bar, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 255) / 256);
+    k_adj_gather<<<g, 256, 0, st>>>(cur, W, (int)n, p_bar);
+    if (P.dim == 2) k_adj_tslot<2><<<g, 256, 0, st>>>(W, (int)n);
+    else k_adj_tslot<3><<<g, 256, 0, st>>>(W, (int)n);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void *fn = adj_fn(P.precision, P.dim);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, KT, 0);
+    if (per > 2) per = 2;
+    int64_t want = (n + KT - 1) / KT;
+    int nblk = sms * per;
+    if (nblk > PSTRIDE) nblk = PSTRIDE;
+    if (want < nblk) nblk = (int)want;
+    if (nblk < 1) nblk = 1;
+    int nn = (int)n, maxit = P.max_iter;
+    double rtol = P.rtol;
+    int32_t *it_out = W.kiters;
+    double *res_out = W.kresid;
+    void *args[] = {(void *)&W, (void *)&nn, (void *)&maxit, (void *)&rtol, (void *)&it_out,
+                    (void *)&res_out};
+    cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblk), dim3(KT), args, 0, st);
+    if (e != cudaSuccess) return (int)e;
+    k_adj_scatter<<<g, 256, 0, st>>>(cur, W, (int)n, b_bar);
+    return 0;
+}
+
 }  // namespace vct
 
 // ===========================================================================

@@ -22,7 +22,7 @@ VCT_MAX_GAUSS = 32
 EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
            "sph2_derivatives", "sph2_derivatives_backward", "vct_map_backward", "vct_step",
            "vct_batch_step",
-           "vct_step_host", "vct_step_probe", "vct_set_profiling", "vct_stage_times",
+           "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
 
 _dp = C.POINTER(C.c_double)
@@ -102,6 +102,7 @@ def load_library(path=LIB_PATH):
     L.vct_batch_step.restype = C.c_int
     L.vct_step_probe.argtypes = [vp, C.POINTER(vct_state), C.POINTER(vct_probe),
                                  C.POINTER(vct_stats)]
+    L.vct_ppe_adjoint.argtypes = [vp, vp, vp, C.POINTER(vct_stats)]
     L.vct_set_profiling.argtypes = [vp, C.c_int32]
     L.vct_stage_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.vct_last_error.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -111,7 +112,7 @@ def load_library(path=LIB_PATH):
     L.vct_destroy.restype = None
     for name in ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives",
                  "sph2_derivatives_backward", "vct_map_backward",
-                 "vct_step", "vct_step_host", "vct_step_probe", "vct_set_profiling",
+                 "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -302,6 +303,18 @@ class Solver:
                                               c(sy_bar), c(c0_bar), c(c3_bar), out),
                     "vct_map_backward")
         return np.array(out[:])
+
+    def vct_ppe_adjoint(self, p_bar):
+        """b_bar = A^-T p_bar for the pressure system of the last step (caller
+        order, float64 CUDA tensors of the state's length); returns (b_bar, stats)."""
+        import torch
+        p_bar = p_bar.to(device="cuda", dtype=torch.float64).contiguous()
+        b_bar = torch.zeros_like(p_bar)
+        st = vct_stats()
+        self._check(self.lib.vct_ppe_adjoint(self.ctx, C.c_void_p(p_bar.data_ptr()),
+                                             C.c_void_p(b_bar.data_ptr()), C.byref(st)),
+                    "vct_ppe_adjoint")
+        return b_bar, st
 
     def vct_step(self, state, nsteps=1):
         s = state.struct()
