@@ -127,6 +127,20 @@ def run_adjoint(args):
     k = min(args.steps, 50)
     fwd = timed(lambda: solver.sph2_derivatives(state, phi), k)
     bwd = timed(lambda: solver.sph2_derivatives_backward(state, gb, db, lb), k)
+    # the pressure solve and its adjoint (transpose solve) on one step of the workload
+    solver.vct_set_profiling(True)
+    solver.vct_step(state, 1)
+    fwd_solve_ms = solver.vct_stage_times()["krylov"][0]
+    solver.vct_set_profiling(False)
+    pb = torch.randn(sc.n, dtype=torch.float64, device="cuda", generator=g)
+    solver.vct_ppe_adjoint(pb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, ast = solver.vct_ppe_adjoint(pb)
+    e1.record()
+    e1.synchronize()
+    ppe_adj_ms = e0.elapsed_time(e1)
     print(json.dumps({"metric": "adjoint/forward time, SPH(2) derivative operator",
                       "value": bwd / fwd, "unit": "x", "higher_is_better": False,
                       "forward_ms": fwd, "backward_ms": bwd, "calls": k, "n_gpus": 1,
@@ -134,8 +148,11 @@ def run_adjoint(args):
                       "dtype": "f32+f64" if args.precision == 1 else "f64",
                       "config": {"workload": WORKLOADS["adjoint"], "n_fluid": sc.n_fluid,
                                  "fields": 3},
-                      "scope": "operator adjoint only; the checkpointed full-step adjoint is "
-                               "not built"}), flush=True)
+                      "ppe_solve": {"forward_ms": fwd_solve_ms, "adjoint_ms": ppe_adj_ms,
+                                    "ratio": ppe_adj_ms / fwd_solve_ms,
+                                    "adjoint_iters": int(ast.krylov_iters_total)},
+                      "scope": "operator adjoint and pressure-solve adjoint; the checkpointed "
+                               "full-step adjoint is not built"}), flush=True)
 
 
 def run_ensemble(args):

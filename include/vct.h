@@ -275,9 +275,14 @@ vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *o
  * loss with respect to p, writes b_bar = A^-T p_bar, the gradient with respect
  * to b; the gradient with respect to A's coefficients is then -b_bar p^T on A's
  * pattern.  The operator is the one the forward solve used (FP32 coefficients
- * in the mixed form); the transposed system is solved in FP64 by BiCGSTAB with
- * a Jacobi right preconditioner to the context's krylov_rtol (relative to
- * |p_bar|, at most krylov_max_iter iterations; VCT_ERR_NOCONV otherwise).
+ * in the mixed form).  The transposed system is solved like the forward one:
+ * BiCGSTAB in the form's precision inside FP64 refinement, right-preconditioned
+ * by the forward solve's multigrid V-cycle without coarse over-correction (A is
+ * close to symmetric, so its hierarchy serves A^T; small-system solver form at
+ * any size), or by Jacobi in FP64 when the context has no multigrid or the
+ * multigrid solve does not converge (then the call solves again that way); to
+ * the context's krylov_rtol relative to |p_bar|, at most krylov_max_iter
+ * iterations per attempt (VCT_ERR_NOCONV otherwise).
  * p_bar, b_bar: device arrays of n doubles in caller order, n the particle
  * count of that step; entries of rows that are not unknowns are ignored in
  * p_bar and written as 0 in b_bar.  Returns VCT_ERR_ARG if the context holds

@@ -1004,10 +1004,21 @@ VCT_API vct_status vct_ppe_adjoint(vct_ctx *c, const double *p_bar, double *b_ba
     if (c->ppe_n <= 0) return VCT_ERR_ARG;   // no pressure system held
     const int64_t n = c->ppe_n;
     reset_status(c);
-    const int e = launch_ppe_adjoint(c->P, cur(c), c->W, n, p_bar, b_bar, c->st);
+    int e = launch_ppe_adjoint(c->P, cur(c), c->W, c->precond ? &c->mg : nullptr, n, p_bar,
+                               b_bar, c->st);
     c->launches += 4;   // gather, transposed slots, solve, scatter
     if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
-    return finish(c, out, 1);
+    vct_status v = finish(c, out, 1);
+    if (v == VCT_ERR_NOCONV && c->precond) {
+        // the forward hierarchy did not carry the transposed system: solve it
+        // again with the Jacobi-preconditioned BiCGSTAB
+        reset_status(c);
+        e = launch_ppe_adjoint(c->P, cur(c), c->W, nullptr, n, p_bar, b_bar, c->st);
+        c->launches += 4;
+        if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+        v = finish(c, out, 1);
+    }
+    return v;
 }
 
 VCT_API vct_status vct_step_probe(vct_ctx *c, vct_state *s, const vct_probe *pr, vct_stats *out)

@@ -175,8 +175,9 @@ bool krylov_mg_fly_default(long long rows, int dim);
 int krylov_fly_batch_blocks(int precision, int dim, size_t smem, bool expl);
 size_t krylov_batch_stage_bytes(int precision, int dim);
 // adjoint of the last step's pressure solve: b_bar = A^-T p_bar (caller order)
-int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, int64_t n, const double *p_bar,
-                       double *b_bar, cudaStream_t st);
+// (M: the context's multigrid hierarchy, or null for Jacobi preconditioning)
+int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_t n,
+                       const double *p_bar, double *b_bar, cudaStream_t st);
 int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,
                             size_t smem, bool expl, cudaStream_t st);
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly);
