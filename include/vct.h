@@ -110,7 +110,7 @@ typedef struct {
                                aggregation multigrid V-cycle on the cell grid (Jacobi damping
                                0.85 / 0.7 and coarse-correction scale 1.3 / 1.2 in 2-D / 3-D,
                                z-only coarsening while the operator's z coupling dominates,
-                               8 coarsest sweeps, small levels in block 0's shared memory:
+                               no sweeps on the coarsest level (<= 4 nodes), small levels in block 0's shared memory:
                                96 KB up to 75k particles in 2-D / 30k in 3-D, 16 KB above, where the solver
                                also stages operator rows with cp.async and gathers through
                                L1).  vct_init reads overrides from the environment:
