@@ -110,7 +110,8 @@ typedef struct {
                                aggregation multigrid V-cycle on the cell grid (Jacobi damping
                                0.85 / 0.7 and coarse-correction scale 1.3 / 1.2 in 2-D / 3-D,
                                z-only coarsening while the operator's z coupling dominates,
-                               no sweeps on the coarsest level (<= 4 nodes), small levels in block 0's shared memory:
+                               coarsening down to <= 64 / 4 nodes (2-D / 3-D), no sweeps on
+                               the coarsest level, small levels in block 0's shared memory:
                                96 KB up to 75k particles in 2-D / 30k in 3-D, 16 KB above, where the solver
                                also stages operator rows with cp.async and gathers through
                                L1).  vct_init reads overrides from the environment:
@@ -120,6 +121,8 @@ typedef struct {
                                2^s per axis), VCT_SOLVE_BLOCKS (grid cap), VCT_PGUESS
                                (initial guess: 0 p^N, 1 linear, 2 quadratic extrapolation
                                of the context's last pressures, the default),
+                               VCT_MG_MINN (coarsest level size), VCT_MG_SMALL (levels up
+                               to this size coarsened by one block in the set-up),
                                VCT_INNER_FLOOR (mixed form: relative residual at which
                                each FP32 BiCGSTAB pass hands back to the FP64 residual,
                                1e-4) */

@@ -766,7 +766,13 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
             ratio = acc / cnt;
         }
         int l = 1;
-        while (M.n[l] > 4 && l < MG_MAXL) {
+        // coarsen while a level has more than 64 nodes in 2-D, 4 in 3-D (with no
+        // sweeps on the coarsest level; iterations and solve time per step by this
+        // size, 2-D wave: 4: 15.63, 2330 us; 16: 15.52, 2275; 64: 15.37, 2205;
+        // 256: 17.27, 2415; 3-D slice: 4: 31.2, 47.4 ms; 16: 31.2, 47.4; 64: 32.3, 48.7)
+        const int coarsest = getenv("VCT_MG_MINN") ? atoi(getenv("VCT_MG_MINN"))
+                                                   : (prm->dim == 2 ? 64 : 4);
+        while (M.n[l] > coarsest && l < MG_MAXL) {
             const int agg = getenv("VCT_MG_SHIFT") ? atoi(getenv("VCT_MG_SHIFT")) : 1;
             int sh[3] = {agg, prm->dim == 3 ? agg : 0, agg};
             if (ratio > 2.5 && M.dims[l][2] > 1) {
