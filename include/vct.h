@@ -121,7 +121,8 @@ typedef struct {
                                2^s per axis), VCT_SOLVE_BLOCKS (grid cap), VCT_PGUESS
                                (initial guess: 0 p^N, 1 linear, 2 quadratic extrapolation
                                of the context's last pressures, the default),
-                               VCT_MG_MINN (coarsest level size), VCT_MG_SMALL (levels up
+                               VCT_MG_MINN (coarsest level size), VCT_MG_KAPPA_C (scale
+                               between coarse levels, = kappa), VCT_MG_SMALL (levels up
                                to this size coarsened by one block in the set-up),
                                VCT_INNER_FLOOR (mixed form: relative residual at which
                                each FP32 BiCGSTAB pass hands back to the FP64 residual,

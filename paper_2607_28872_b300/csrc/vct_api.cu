@@ -820,6 +820,8 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         M.coarse_sweeps = 0;
         if (getenv("VCT_MG_OMEGA")) M.omega = (float)atof(getenv("VCT_MG_OMEGA"));
         if (getenv("VCT_MG_KAPPA")) M.kappa = (float)atof(getenv("VCT_MG_KAPPA"));
+        M.kappa_c = M.kappa;
+        if (getenv("VCT_MG_KAPPA_C")) M.kappa_c = (float)atof(getenv("VCT_MG_KAPPA_C"));
         if (getenv("VCT_MG_SWEEPS")) M.coarse_sweeps = atoi(getenv("VCT_MG_SWEEPS"));
         M.presmooth = 1;
         if (getenv("VCT_MG_PRESMOOTH")) M.presmooth = atoi(getenv("VCT_MG_PRESMOOTH"));

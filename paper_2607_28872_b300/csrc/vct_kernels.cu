@@ -2466,7 +2466,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
         }
         lv_coarsest<D>(lv_shared(sh, M, M.L), om, M.coarse_sweeps);
         for (int l = M.L - 1; l >= fl; --l) {
-            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, kap, threadIdx.x, blockDim.x);
+            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, M.kappa_c, threadIdx.x, blockDim.x);
             __syncthreads();
         }
         {
@@ -2476,7 +2476,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
     }
     if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     for (int l = fl - 1; l >= 1; --l) {
-        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, kap, gtid, gthreads);
+        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, M.kappa_c, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     // P0: prolongation from the cells, zb = z0 + kappa zu_1(cell)
@@ -2768,7 +2768,7 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
         }
         lv_coarsest<D>(lv_shared(sh, M, M.L), om, M.coarse_sweeps);
         for (int l = M.L - 1; l >= fl; --l) {
-            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, kap, threadIdx.x, blockDim.x);
+            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, M.kappa_c, threadIdx.x, blockDim.x);
             __syncthreads();
         }
         {
@@ -2778,7 +2778,7 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
     }
     if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     for (int l = fl - 1; l >= 1; --l) {
-        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, kap, gtid, gthreads);
+        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, M.kappa_c, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     // U0: prolongation from the cells + one damped Jacobi step on the fine level
@@ -4420,6 +4420,7 @@ int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_
         // (the forward solve 24); the hierarchy itself does not depend on kappa.
         MG Mc = *M;
         Mc.kappa = 1.0f;
+        Mc.kappa_c = 1.0f;
         void *args[] = {(void *)&W, (void *)&Mc, (void *)&nn, (void *)&maxit, (void *)&rtol,
                         (void *)&floor_, (void *)&it_out, (void *)&res_out};
         cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);
