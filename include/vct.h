@@ -108,7 +108,7 @@ typedef struct {
     int32_t max_neighbours; /* neighbour-list capacity per particle (0: 64 in 2-D, 160 in 3-D) */
     int32_t preconditioner; /* pressure solve: 0 plain BiCGSTAB; 1 BiCGSTAB preconditioned by an
                                aggregation multigrid V-cycle on the cell grid (Jacobi damping
-                               0.85 / 0.7 and coarse-correction scale 1.3 / 1.2 in 2-D / 3-D,
+                               0.9 / 0.7 and coarse-correction scale 1.3 / 1.2 in 2-D / 3-D,
                                z-only coarsening while the operator's z coupling dominates,
                                coarsening down to <= 64 / 4 nodes (2-D / 3-D), no sweeps on
                                the coarsest level, small levels in block 0's shared memory:

@@ -728,11 +728,13 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         M.S = prm->dim == 2 ? 9 : 27;
         // tuned: 2-D wave (42k particles, 100 steps, kappa 1.3), iterations per step
         // by omega: 0.7 17.4, 0.75 16.5, 0.8 15.8, 0.85 15.2, 0.9 15.0 (kappa 1.1-1.4
-        // within 1.5 of these; 0.85 keeps a margin to divergence); 3-D BFE
+        // within 1.5 of these); with the hierarchy down to 64 nodes: 0.8 15.6,
+        // 0.85 15.2, 0.9 14.9, and 0.9 converges on every 2-D case and ensemble
+        // scenario tested (in 3-D, 0.8 already diverges); 3-D BFE
         // beach (aspect 4, 2.1M particles), iterations per step by kappa at omega 0.7:
         // 1.8: 77, 1.5: 47, 1.4: 40, 1.3: 33, 1.2: 31 (540k slice: 1.0 36, 1.1 32,
         // 1.2 32); omega 0.8 does not converge there, 0.75 is within 1 iteration
-        M.omega = prm->dim == 2 ? 0.85f : 0.7f;
+        M.omega = prm->dim == 2 ? 0.9f : 0.7f;
         M.kappa = prm->dim == 2 ? 1.3f : 1.2f;
         M.coarse_sweeps = 24;
         M.dims[1][0] = P.nc[0];
