@@ -156,8 +156,7 @@ typedef struct {
     int64_t steps_done;
     int64_t krylov_iters_total;
     int32_t krylov_iters_max;
-    int32_t graph_steps;    /* steps of this call replayed from a captured CUDA graph
-                               (vct_batch_step side by side; 0 otherwise) */
+    int32_t graph_steps;    /* steps of this call replayed from a captured CUDA graph */
     double last_residual;   /* relative residual of the last pressure solve */
     int64_t ppe_rows;       /* unknowns (fluid, not free surface) of the last step */
     int64_t ppe_nnz;        /* off-diagonal coefficients of the last step's operator */
@@ -270,7 +269,14 @@ vct_status vct_map_backward(vct_ctx *ctx, const vct_state *state, const double *
  * corrector and position update, then the particle regularisation of
  * vct_params when on.  Device arrays, updated in place on success; on an
  * error the state is left as it was and the steps after the failing one do
- * no work.  out (host, may be NULL) receives solve statistics. */
+ * no work.  out (host, may be NULL) receives solve statistics.  The steps
+ * are replayed from CUDA graphs, one step each, captured on the first call for
+ * each particle count and sorted-buffer parity and kept by the context; they
+ * run on a stream the context creates for them, ordered after the load and
+ * before the write-back on the context's stream, with results identical to
+ * direct launches.  Not with stage profiling on, nor with the environment
+ * variable VCT_STEP_NOGRAPH set; if a capture fails, the context launches
+ * directly from then on; stats.graph_steps counts the replayed steps. */
 vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *out);
 
 /* Adjoint of the pressure solve of the context's last step (Sec. 3.3, Eqs.

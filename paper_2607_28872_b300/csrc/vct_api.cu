@@ -51,6 +51,14 @@ struct vct_ctx {
     long long serial;          // unique per context, never reused
     int graph_steps;           // steps of the current call replayed from the graph
     int64_t ppe_n;             // particles of the last pressure system still held (0: none)
+    // vct_step: one step captured as a CUDA graph per state-buffer parity (the
+    // sorted buffers alternate every step), replayed on a stream of its own
+    cudaStream_t sst;
+    cudaEvent_t sev0, sev1;
+    cudaGraphExec_t sgraph[2];
+    int64_t sgraph_n[2];
+    int64_t sgraph_launches[2];
+    bool sgraph_off;           // a capture failed: direct launches from then on
     std::vector<cudaEvent_t> ev;      // 2 per stage per profiled step
     std::vector<int> ev_stage;        // stage of each recorded pair
     int ev_used;
@@ -286,6 +294,48 @@ vct_status queue_step(vct_ctx *c, int64_t n, int step, int nsteps, const vct_pro
     return VCT_OK;
 }
 
+// Capture one step from buffer parity par (0: A current) on the context's step
+// stream; on failure the context launches directly from then on.
+void capture_step(vct_ctx *c, int64_t n, int par)
+{
+    cudaError_t ce = cudaSuccess;
+    if (!c->sst) ce = cudaStreamCreateWithFlags(&c->sst, cudaStreamNonBlocking);
+    if (ce == cudaSuccess && !c->sev0) ce = cudaEventCreateWithFlags(&c->sev0, cudaEventDisableTiming);
+    if (ce == cudaSuccess && !c->sev1) ce = cudaEventCreateWithFlags(&c->sev1, cudaEventDisableTiming);
+    if (c->sgraph[par]) cudaGraphExecDestroy(c->sgraph[par]);
+    c->sgraph[par] = nullptr;
+    if (ce != cudaSuccess) {
+        c->sgraph_off = true;
+        return;
+    }
+    const cudaStream_t saved = c->st;
+    const bool cur0 = c->cur_is_A;
+    const int64_t l0 = c->launches, pn0 = c->ppe_n;
+    c->st = c->sst;
+    c->cur_is_A = par == 0;   // the parity this graph starts from
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamBeginCapture(c->sst, cudaStreamCaptureModeRelaxed);
+    if (ce == cudaSuccess) {
+        const vct_status qs = queue_step(c, n, 0, 1, nullptr);
+        ce = cudaStreamEndCapture(c->sst, &g);
+        if (ce == cudaSuccess && qs != VCT_OK) ce = cudaErrorUnknown;
+    }
+    if (ce == cudaSuccess && g) ce = cudaGraphInstantiate(&c->sgraph[par], g, 0);
+    if (g) cudaGraphDestroy(g);
+    c->sgraph_launches[par] = c->launches - l0;
+    c->launches = l0;   // nothing ran yet
+    c->cur_is_A = cur0;
+    c->ppe_n = pn0;
+    c->st = saved;
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        c->sgraph[par] = nullptr;
+        c->sgraph_off = true;
+    } else {
+        c->sgraph_n[par] = n;
+    }
+}
+
 vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, vct_stats *out)
 {
     vct_status v = check_state(c, s);
@@ -295,7 +345,35 @@ vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, 
     reset_status(c);
     { StageTimer t(c, VCT_STAGE_LOAD); launch_load(c->P, cur(c), *s, n, c->st); }
     c->launches += 1;
-    for (int step = 0; step < nsteps; ++step) {
+    // Steps from the captured graphs (not with a probe or stage profiling, nor
+    // with VCT_STEP_NOGRAPH set): every step's work is the same but for the
+    // buffer parity, so one graph per parity serves all steps of this and
+    // later calls with the same particle count.  They run on the context's step
+    // stream, after the load and before the store on the context's stream.
+    const bool graphs = !pr && !c->prof && !c->sgraph_off && nsteps > 0 && !getenv("VCT_STEP_NOGRAPH");
+    int step0 = 0;
+    if (graphs) {
+        for (int par = 0; par < 2 && !c->sgraph_off; ++par)
+            if (!c->sgraph[par] || c->sgraph_n[par] != n) capture_step(c, n, par);
+    }
+    if (graphs && !c->sgraph_off) {
+        cudaEventRecord(c->sev0, c->st);
+        cudaStreamWaitEvent(c->sst, c->sev0, 0);
+        cudaError_t e = cudaSuccess;
+        for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+            const int par = c->cur_is_A ? 0 : 1;
+            e = cudaGraphLaunch(c->sgraph[par], c->sst);
+            c->cur_is_A = !c->cur_is_A;
+            c->launches += c->sgraph_launches[par];
+        }
+        c->ppe_n = n;
+        cudaEventRecord(c->sev1, c->sst);
+        cudaStreamWaitEvent(c->st, c->sev1, 0);
+        if (e != cudaSuccess) return VCT_ERR_CUDA;
+        step0 = nsteps;
+        c->graph_steps = nsteps;
+    }
+    for (int step = step0; step < nsteps; ++step) {
         v = queue_step(c, n, step, nsteps, pr);
         if (v) return v;
     }
@@ -1133,6 +1211,14 @@ VCT_API void vct_destroy(vct_ctx *c)
     if (c->bev) cudaEventDestroy(c->bev);
     if (c->jobs_dev) cudaFree(c->jobs_dev);
     if (c->bgraph) cudaGraphExecDestroy(c->bgraph);
+    for (int par = 0; par < 2; ++par)
+        if (c->sgraph[par]) cudaGraphExecDestroy(c->sgraph[par]);
+    if (c->sst) {
+        cudaStreamSynchronize(c->sst);
+        cudaStreamDestroy(c->sst);
+    }
+    if (c->sev0) cudaEventDestroy(c->sev0);
+    if (c->sev1) cudaEventDestroy(c->sev1);
     if (c->gst) {
         cudaStreamSynchronize(c->gst);
         cudaStreamDestroy(c->gst);

@@ -328,6 +328,34 @@ def test_run_to_run_bit_identical(vct):
         assert np.array_equal(outs[0][k], outs[1][k]), k
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_graph_steps_equal_direct_steps(vct, monkeypatch, precision):
+    """vct_step replays its steps from captured CUDA graphs (one per buffer
+    parity); the results are those of the same steps launched directly, bit for
+    bit, over calls of 3 steps and then 2 (the second call starts from the other
+    parity), and the stats count the replayed steps and the same launches."""
+    sc = S.small_tank(dim=2, kind="SIGMA", L=0.3, H=0.1, d0=0.01, seed=8, with_wave=True,
+                      precision=precision)
+
+    def run(graph):
+        if graph:
+            monkeypatch.delenv("VCT_STEP_NOGRAPH", raising=False)
+        else:
+            monkeypatch.setenv("VCT_STEP_NOGRAPH", "1")
+        s = vct.Solver(sc)
+        st = vct.DeviceState(sc)
+        a = s.vct_step(st, 3)
+        b = s.vct_step(st, 2)
+        return st.numpy(), (a.graph_steps, b.graph_steps), (a.kernel_launches, b.kernel_launches)
+
+    g, g_steps, g_launches = run(True)
+    d, d_steps, d_launches = run(False)
+    assert g_steps == (3, 2) and d_steps == (0, 0)
+    assert g_launches == d_launches
+    for k in ("x", "z", "u", "w", "p", "jbar"):
+        assert np.array_equal(g[k], d[k]), k
+
+
 def test_errors_are_reported(vct):
     sc = S.small_tank(dim=2, kind="BF", L=0.2, H=0.08, d0=0.01, seed=1)
     s = vct.Solver(sc, max_neighbours=8)
