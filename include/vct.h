@@ -108,7 +108,8 @@ typedef struct {
     int32_t max_neighbours; /* neighbour-list capacity per particle (0: 64 in 2-D, 160 in 3-D) */
     int32_t preconditioner; /* pressure solve: 0 plain BiCGSTAB; 1 BiCGSTAB preconditioned by an
                                aggregation multigrid V-cycle on the cell grid (Jacobi damping
-                               0.9 / 0.7 and coarse-correction scale 1.3 / 1.2 in 2-D / 3-D,
+                               0.85 / 0.7 on the particles and 1.0 / 0.8 on the coarse
+                               levels, coarse-correction scale 1.3 / 1.2 in 2-D / 3-D,
                                z-only coarsening while the operator's z coupling dominates,
                                coarsening down to <= 64 / 4 nodes (2-D / 3-D), no sweeps on
                                the coarsest level, small levels in block 0's shared memory:
@@ -121,7 +122,8 @@ typedef struct {
                                2^s per axis), VCT_SOLVE_BLOCKS (grid cap), VCT_PGUESS
                                (initial guess: 0 p^N, 1 linear, 2 quadratic extrapolation
                                of the context's last pressures, the default),
-                               VCT_MG_MINN (coarsest level size), VCT_MG_KAPPA_C (scale
+                               VCT_MG_MINN (coarsest level size), VCT_MG_OMEGA_C (coarse
+                               levels' damping), VCT_MG_KAPPA_C (scale
                                between coarse levels, = kappa), VCT_MG_SMALL (levels up
                                to this size coarsened by one block in the set-up),
                                VCT_INNER_FLOOR (mixed form: relative residual at which

@@ -807,12 +807,12 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         // tuned: 2-D wave (42k particles, 100 steps, kappa 1.3), iterations per step
         // by omega: 0.7 17.4, 0.75 16.5, 0.8 15.8, 0.85 15.2, 0.9 15.0 (kappa 1.1-1.4
         // within 1.5 of these); with the hierarchy down to 64 nodes: 0.8 15.6,
-        // 0.85 15.2, 0.9 14.9, and 0.9 converges on every 2-D case and ensemble
-        // scenario tested (in 3-D, 0.8 already diverges); 3-D BFE
+        // 0.85 15.2, 0.9 14.9 (in 3-D, 0.8 already diverges); with the coarse levels'
+        // own damping (below) 0.85 is as fast as 0.9; 3-D BFE
         // beach (aspect 4, 2.1M particles), iterations per step by kappa at omega 0.7:
         // 1.8: 77, 1.5: 47, 1.4: 40, 1.3: 33, 1.2: 31 (540k slice: 1.0 36, 1.1 32,
         // 1.2 32); omega 0.8 does not converge there, 0.75 is within 1 iteration
-        M.omega = prm->dim == 2 ? 0.9f : 0.7f;
+        M.omega = prm->dim == 2 ? 0.85f : 0.7f;
         M.kappa = prm->dim == 2 ? 1.3f : 1.2f;
         M.coarse_sweeps = 24;
         M.dims[1][0] = P.nc[0];
@@ -901,6 +901,14 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         if (getenv("VCT_MG_OMEGA")) M.omega = (float)atof(getenv("VCT_MG_OMEGA"));
         if (getenv("VCT_MG_KAPPA")) M.kappa = (float)atof(getenv("VCT_MG_KAPPA"));
         M.kappa_c = M.kappa;
+        // damping on the coarse levels (measured, iterations / solve time per step):
+        // 2-D wave 0.7 16.35 / 2.28 ms, 0.8 15.35 / 2.15, 0.9 (= fine) 14.89 / 2.08,
+        // 1.0 14.60 / 2.05, 1.1 14.32 / 2.01, and with the fine damping 0.85 and
+        // 1.0 here 14.35 / 2.01 (the default: no over-relaxation anywhere); 3-D
+        // slice 0.6 32.3 / 48.6 ms, 0.7 (= fine) 31.2 / 46.9, 0.8 30.1 / 45.3,
+        // 0.85 30.5 / 46.2, 0.9 30.5 / 45.9
+        M.omega_c = prm->dim == 2 ? 1.0f : 0.8f;
+        if (getenv("VCT_MG_OMEGA_C")) M.omega_c = (float)atof(getenv("VCT_MG_OMEGA_C"));
         if (getenv("VCT_MG_KAPPA_C")) M.kappa_c = (float)atof(getenv("VCT_MG_KAPPA_C"));
         if (getenv("VCT_MG_SWEEPS")) M.coarse_sweeps = atoi(getenv("VCT_MG_SWEEPS"));
         M.presmooth = 1;

@@ -127,7 +127,7 @@ struct MG {
     int presmooth;       // 1: V(1,1); 0: V(0,1), no fine pre-smoothing (on-the-fly form)
     float omega, kappa;  // Jacobi damping and coarse-correction scale (cells to particles)
     float kappa_c;       // coarse-correction scale between the coarse levels
-    int pad_k;
+    float omega_c;       // Jacobi damping on the coarse levels (cells and coarser)
     int n[MG_MAXL + 1];
     int dims[MG_MAXL + 1][3];
     int shift[MG_MAXL + 1][3];     // level l -> l+1: factor 2^shift per axis (x, y, z)

@@ -2442,13 +2442,13 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
             for (int i = a; i < b; ++i)
                 if (W.pcnt[i] >= 0) bs += (float)__ldcg(r0 + i);
             c.b[I] = bs;
-            c.z[I] = om * bs * c.dinv[I];
+            c.z[I] = M.omega_c * bs * c.dinv[I];
         }
     }
     if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     const int fl = M.first_local;
     for (int l = 1; l < fl; ++l) {
-        lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, gtid, gthreads);
+        lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     if (vb == 0) {
@@ -2461,12 +2461,12 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
             __syncthreads();
         }
         for (int l = fl; l < M.L; ++l) {
-            lv_down<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, threadIdx.x, blockDim.x);
+            lv_down<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), M.omega_c, threadIdx.x, blockDim.x);
             __syncthreads();
         }
-        lv_coarsest<D>(lv_shared(sh, M, M.L), om, M.coarse_sweeps);
+        lv_coarsest<D>(lv_shared(sh, M, M.L), M.omega_c, M.coarse_sweeps);
         for (int l = M.L - 1; l >= fl; --l) {
-            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, M.kappa_c, threadIdx.x, blockDim.x);
+            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), M.omega_c, M.kappa_c, threadIdx.x, blockDim.x);
             __syncthreads();
         }
         {
@@ -2476,7 +2476,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
     }
     if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     for (int l = fl - 1; l >= 1; --l) {
-        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, M.kappa_c, gtid, gthreads);
+        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, M.kappa_c, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     // P0: prolongation from the cells, zb = z0 + kappa zu_1(cell)
@@ -2743,13 +2743,13 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
                 }
             }
             c.b[I] = bs;
-            c.z[I] = om * bs * c.dinv[I];
+            c.z[I] = M.omega_c * bs * c.dinv[I];
         }
     }
     if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     const int fl = M.first_local;
     for (int l = 1; l < fl; ++l) {
-        lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, gtid, gthreads);
+        lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     if (vb == 0) {
@@ -2763,12 +2763,12 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             __syncthreads();
         }
         for (int l = fl; l < M.L; ++l) {
-            lv_down<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, threadIdx.x, blockDim.x);
+            lv_down<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), M.omega_c, threadIdx.x, blockDim.x);
             __syncthreads();
         }
-        lv_coarsest<D>(lv_shared(sh, M, M.L), om, M.coarse_sweeps);
+        lv_coarsest<D>(lv_shared(sh, M, M.L), M.omega_c, M.coarse_sweeps);
         for (int l = M.L - 1; l >= fl; --l) {
-            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), om, M.kappa_c, threadIdx.x, blockDim.x);
+            lv_up<D, false>(lv_shared(sh, M, l), lv_shared(sh, M, l + 1), M.omega_c, M.kappa_c, threadIdx.x, blockDim.x);
             __syncthreads();
         }
         {
@@ -2778,7 +2778,7 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
     }
     if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     for (int l = fl - 1; l >= 1; --l) {
-        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), om, M.kappa_c, gtid, gthreads);
+        lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, M.kappa_c, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
     }
     // U0: prolongation from the cells + one damped Jacobi step on the fine level

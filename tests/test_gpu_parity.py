@@ -379,6 +379,35 @@ def test_errors_are_reported(vct):
     assert e.value.status == vct.VCT_ERR_CAPACITY
 
 
+def test_degenerate_inputs(vct):
+    """An empty state is an argument error; a state without fluid particles
+    steps (nothing moves, no pressure unknowns, no iterations); a batch of one
+    scenario is vct_step of that scenario bit for bit."""
+    sc = S.small_tank(dim=2, kind="BF", L=0.2, H=0.08, d0=0.01, seed=1)
+    s = vct.Solver(sc)
+    empty = vct.DeviceState(sc)
+    empty.n = 0
+    with pytest.raises(vct.VCTError) as e:
+        s.vct_step(empty, 1)
+    assert e.value.status == vct.VCT_ERR_ARG
+    walls = sc.copy()
+    walls.type[:] = S.WALL
+    s2 = vct.Solver(walls)
+    st = vct.DeviceState(walls)
+    stats = s2.vct_step(st, 2)
+    assert stats.steps_done == 2 and stats.ppe_rows == 0 and stats.krylov_iters_total == 0
+    g = st.numpy()
+    for k in ("x", "z", "u", "w"):
+        assert np.array_equal(g[k], getattr(walls, k)), k
+    one = vct.DeviceState(sc)
+    vct.vct_batch_step([vct.Solver(sc)], [one], 3)
+    ref = vct.DeviceState(sc)
+    vct.Solver(sc).vct_step(ref, 3)
+    a, b = one.numpy(), ref.numpy()
+    for k in ("x", "z", "u", "w", "p", "jbar"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_poisoned_input_nonfinite(vct):
     sc = S.small_tank(dim=2, kind="BF", L=0.2, H=0.08, d0=0.01, seed=1)
     sc.u[3] = np.nan
