@@ -850,12 +850,13 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         // sweeps on the coarsest level; iterations and solve time per step by this
         // size, 2-D wave: 4: 15.63, 2330 us; 16: 15.52, 2275; 64: 15.37, 2205;
         // 256: 17.27, 2415; 3-D slice: 4: 31.2, 47.4 ms; 16: 31.2, 47.4; 64: 32.3, 48.7)
+        const double zratio = getenv("VCT_MG_ZRATIO") ? atof(getenv("VCT_MG_ZRATIO")) : 2.5;
         const int coarsest = getenv("VCT_MG_MINN") ? atoi(getenv("VCT_MG_MINN"))
                                                    : (prm->dim == 2 ? 64 : 4);
         while (M.n[l] > coarsest && l < MG_MAXL) {
             const int agg = getenv("VCT_MG_SHIFT") ? atoi(getenv("VCT_MG_SHIFT")) : 1;
             int sh[3] = {agg, prm->dim == 3 ? agg : 0, agg};
-            if (ratio > 2.5 && M.dims[l][2] > 1) {
+            if (ratio > zratio && M.dims[l][2] > 1) {
                 sh[0] = 0;
                 sh[1] = 0;
                 ratio *= 0.25;
