@@ -77,7 +77,7 @@ WORKLOADS = {
 # L2-resident: bytes per launch.  The 3-D beach was captured on its 8 x 1.6 m slice and
 # its traffic grows with rows x iterations: bytes per fluid particle per iteration.
 NCU_TRAFFIC = {
-    "sigma_solitary": ("per_launch", 10.02e6, "profiles/k_krylov_mg_fly_sigma_solitary_42k.md"),
+    "sigma_solitary": ("per_launch", 10.11e6, "profiles/k_krylov_mg_fly_sigma_solitary_42k.md"),
     "beach_bfe_3d": ("per_unit", 3520.0, "profiles/k_krylov_mg_staged_beach_bfe_3d_540k.md"),
     "beach_bfe_3d_slice": ("per_unit", 3520.0,
                            "profiles/k_krylov_mg_staged_beach_bfe_3d_540k.md"),
