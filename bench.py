@@ -60,6 +60,24 @@ def dist_env():
     return rank, world, local
 
 
+def job_ms(local_ms, world, device="cuda"):
+    """The job's time: the slowest rank's (max over ranks), returned on every
+    rank; one replica per GPU, so this reduction is the only exchange."""
+    if world <= 1:
+        return local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, steps, ms):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank * steps / (ms / 1e3)
+
+
 WORKLOADS = {
     "sigma_solitary": WORKLOAD,
     "still_water_bf": "2-D BF still water over a 1:10 slope, 1 m x 0.2 m, d0=0.01 m, jitter 0.1 d0",
@@ -377,13 +395,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     stages = solver.vct_stage_times()
     solver.vct_set_profiling(False)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        total_ms = float(t.item())
+    total_ms = job_ms(total_ms, world)
     ms_step = total_ms / args.steps
-    value = world * n_fluid * args.steps / (total_ms / 1e3)
+    value = job_throughput(n_fluid, world, args.steps, total_ms)
 
     # e2e: the host-buffer entry point, copies in and out inside the timed region
     e2e = None
