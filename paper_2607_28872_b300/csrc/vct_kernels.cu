@@ -326,6 +326,105 @@ __device__ bool lu_solve(double *A, double *B)
     return true;
 }
 
+// The same elimination kept as factors, for one matrix with two systems
+// (M x = B and M^T w = c).  lu_factor runs lu_solve's elimination on A alone:
+// at step k rows k and piv[k] are swapped in the columns not yet eliminated and
+// the multipliers are stored below the diagonal where they were formed, so
+// lu_apply (swap, then subtract, step by step) repeats lu_solve's operations on
+// B exactly.  For M^T: M = P_0 E_0^-1 ... P_(m-1) E_(m-1)^-1 U with E_k the
+// step-k row operations, so M^-T c = P_0 E_0^T ... P_(m-1) E_(m-1)^T U^-T c.
+template <int M>
+__device__ bool lu_factor(double *A, int *piv)
+{
+    double amax = 0.0;
+#pragma unroll
+    for (int k = 0; k < M * M; ++k) amax = fmax(amax, fabs(A[k]));
+    bool ok = amax > 0.0;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        int p = k;
+        double pv = fabs(A[k * M + k]);
+#pragma unroll
+        for (int r = k + 1; r < M; ++r)
+            if (fabs(A[r * M + k]) > pv) { pv = fabs(A[r * M + k]); p = r; }
+        if (!(pv > 1e-14 * amax)) ok = false;
+        piv[k] = p;
+        if (p != k) {
+#pragma unroll
+            for (int c = k; c < M; ++c) {
+                double t = A[k * M + c];
+                A[k * M + c] = A[p * M + c];
+                A[p * M + c] = t;
+            }
+        }
+        double inv = 1.0 / A[k * M + k];
+#pragma unroll
+        for (int r = k + 1; r < M; ++r) {
+            double f = A[r * M + k] * inv;
+            A[r * M + k] = f;
+#pragma unroll
+            for (int c = k + 1; c < M; ++c) A[r * M + c] -= f * A[k * M + c];
+        }
+    }
+    return ok;
+}
+
+template <int M, int NR>
+__device__ void lu_apply(const double *A, const int *piv, double *B)
+{
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const int p = piv[k];
+        if (p != k) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                double t = B[k * NR + c];
+                B[k * NR + c] = B[p * NR + c];
+                B[p * NR + c] = t;
+            }
+        }
+#pragma unroll
+        for (int r = k + 1; r < M; ++r)
+#pragma unroll
+            for (int c = 0; c < NR; ++c) B[r * NR + c] -= A[r * M + k] * B[k * NR + c];
+    }
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            double s = B[k * NR + c];
+#pragma unroll
+            for (int j = k + 1; j < M; ++j) s -= A[k * M + j] * B[j * NR + c];
+            B[k * NR + c] = s / A[k * M + k];
+        }
+    }
+}
+
+template <int M>
+__device__ void lu_apply_t(const double *A, const int *piv, double *w)
+{
+#pragma unroll
+    for (int k = 0; k < M; ++k) {   // U^T y = c
+        double s = w[k];
+#pragma unroll
+        for (int j = 0; j < k; ++j) s -= A[j * M + k] * w[j];
+        w[k] = s / A[k * M + k];
+    }
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {   // E_k^T, then P_k
+        double s = w[k];
+#pragma unroll
+        for (int r = k + 1; r < M; ++r) s -= A[r * M + k] * w[r];
+        w[k] = s;
+        const int p = piv[k];
+        if (p != k) {
+            const double t = w[k];
+            w[k] = w[p];
+            w[p] = t;
+        }
+    }
+}
+
 // Coefficients of the SPH(2) output (cross terms doubled) in c_trans . D^:
 // 2-D [1, c3, c4/2], 3-D [1, 1, c3, 0, c5/2, c4/2]; c4 = 2 s_x, c5 = 2 s_y.
 template <int D>
@@ -1167,13 +1266,14 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
     double ct[M];
     ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
     double acc[D] = {};
+    int piv[M];
     if (predictor) {
-        double A[M * M], Bv[M * D];
-#pragma unroll
-        for (int k = 0; k < M * M; ++k) A[k] = Md[k];
+        double Bv[M * D];
 #pragma unroll
         for (int k = 0; k < M * D; ++k) Bv[k] = (double)bv[k].val();
-        if (!lu_solve<M, D>(A, Bv)) set_error(W.status, VCT_ERR_SINGULAR, i);
+        // M is factored once: D^v = 2 M^-1 b here, M^-T c~ for the pressure row below
+        if (!lu_factor<M>(Md, piv)) set_error(W.status, VCT_ERR_SINGULAR, i);
+        lu_apply<M, D>(Md, piv, Bv);
         // physical grad nu = J L sum V (nu_j - nu_i) grad w
         double gnh[D], gn[D];
 #pragma unroll
@@ -1223,17 +1323,9 @@ __global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W
         return;
     }
     double wv[M];
-    {
-        // solve M^T w = c~
-        double A[M * M];
 #pragma unroll
-        for (int a = 0; a < M; ++a)
-#pragma unroll
-            for (int b = 0; b < M; ++b) A[a * M + b] = Md[b * M + a];
-#pragma unroll
-        for (int a = 0; a < M; ++a) wv[a] = ct[a];
-        if (!lu_solve<M, 1>(A, wv)) set_error(W.status, VCT_ERR_SINGULAR, i);
-    }
+    for (int a = 0; a < M; ++a) wv[a] = ct[a];
+    lu_apply_t<M>(Md, piv, wv);   // M^T w = c~ from the factors of M
     double u[D];
 #pragma unroll
     for (int K = 0; K < D; ++K) {
