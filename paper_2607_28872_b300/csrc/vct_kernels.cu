@@ -905,12 +905,20 @@ void launch_smoothing(const DevParams &P, Part cur, Work W, int64_t n, cudaStrea
     cudaMemcpyAsync(cur.jbar, W.jbar_tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
 }
 
+// Blocks of 128 per SM the passes are compiled for (the register budget):
+// measured, 3 instead of 1 (<= 168 registers, more spills): pass 1 3-D slice
+// 1.76 -> 1.42 ms, 2-D wave 57 -> 61 us; pass 2 3-D 3.50 -> 3.57 ms, 2-D 81 -> 79 us.
+template <int D>
+constexpr int pass1_min_blocks() { return D == 3 ? 3 : 1; }
+template <int D>
+constexpr int pass2_min_blocks() { return D == 2 ? 3 : 1; }
+
 // ---------------------------------------------------------------------------
 // a4: pass 1 -- B_i and L_i (Eq. gra_1st), <grad^ v>, C~_i, rho^_i,
 // free-surface flag, Smagorinsky eddy viscosity (Sec. 3.4).
 // ---------------------------------------------------------------------------
 template <int D, typename R>
-__global__ void __launch_bounds__(128) k_pass1(DevParams P, const Part c, Work W, int n)
+__global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams P, const Part c, Work W, int n)
 {
     if (step_failed(W.status)) return;
     constexpr int M = D == 2 ? 3 : 6;
@@ -1128,7 +1136,7 @@ void launch_pass1(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t 
 //   w = M_i^-T c~,  u = sum_j V_j F_ij (w . q_ij) r_ij.
 // ---------------------------------------------------------------------------
 template <int D, typename R>
-__global__ void __launch_bounds__(128) k_pass2(DevParams P, const Part c, Work W, int n,
+__global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams P, const Part c, Work W, int n,
                                                int predictor)
 {
     if (step_failed(W.status)) return;
