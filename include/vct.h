@@ -250,6 +250,20 @@ vct_status sph2_derivatives_backward(vct_ctx *ctx, const vct_state *state, int32
                                      const double *grad_hat_bar, const double *d2_hat_bar,
                                      const double *lap_phys_bar, double *phi_bar);
 
+/* Derivative of the corrected gradient of sph2_derivatives (grad_hat =
+ * L_i sum_j V_j (phi_j - phi_i) grad w_ij, Eq. gra_1st) with respect to the
+ * projected particle positions, through the kernel's first and second
+ * derivatives, for the current state with its neighbour sets and particle
+ * volumes held fixed: given grad_hat_bar (ncomp x dim x n, caller order) and
+ * the fields phi (ncomp x n), writes xh_bar (dim x n, caller order) = the
+ * gradient of sum grad_hat_bar . grad_hat with respect to r^ (x, [y], z^).
+ * ncomp 1..3.  FP64; a gather over the symmetric neighbour relation,
+ * deterministic; virtual particles get 0.  Overwrites the context's pass-1
+ * scratch (rebuilt by the next step). */
+vct_status sph2_gradient_backward_positions(vct_ctx *ctx, const vct_state *state,
+                                            const double *phi, int32_t ncomp,
+                                            const double *grad_hat_bar, double *xh_bar);
+
 /* Derivative through the map with respect to the bathymetry parameters
  * theta = [h0, slope_x, slope_y, cos_amp, cos_len, amp[G], cx[G], cy[G], width[G]]
  * (G = n_gauss; 5 + 4G entries): given per-particle adjoints (DEVICE arrays of n,

@@ -1029,6 +1029,23 @@ VCT_API vct_status sph2_derivatives_backward(vct_ctx *c, const vct_state *s, int
     return finish(c, nullptr, 0);
 }
 
+VCT_API vct_status sph2_gradient_backward_positions(vct_ctx *c, const vct_state *s,
+                                                    const double *phi, int32_t ncomp,
+                                                    const double *grad_hat_bar, double *xh_bar)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (!phi || !grad_hat_bar || !xh_bar || ncomp <= 0 || ncomp > 3) return VCT_ERR_ARG;
+    const int64_t n = s->n;
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    geometry(c, n);
+    launch_gradpos(c->P, cur(c), c->W, n, ncomp, phi, grad_hat_bar, xh_bar, c->st);
+    c->launches += 3;
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, nullptr, 0);
+}
+
 VCT_API vct_status vct_map_backward(vct_ctx *c, const vct_state *s, const double *zh_bar,
                                     const double *J_bar, const double *sx_bar,
                                     const double *sy_bar, const double *c0_bar,

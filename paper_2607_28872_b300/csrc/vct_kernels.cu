@@ -4550,6 +4550,218 @@ int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_
     return 0;
 }
 
+
+// ---------------------------------------------------------------------------
+// a12 (part): derivative of the corrected gradient <grad^ phi>_i = L_i g_i,
+// g_i = sum_j V_j (phi_j - phi_i) grad w_ij, L_i = B_i^-1, B_i = sum_j V_j
+// grad w_ij (x) r_ij (Eq. gra_1st; fluid and wall neighbours), with respect to
+// the projected positions, through w' and w'' of the kernel; neighbour sets and
+// volumes held fixed.  With grad w_ij = f(rho) r_ij, f = -w'/rho, rho = |r_ij|,
+// r_ij = r_j - r_i, its Jacobian is H = f I + (f'/rho) r r^T, f' = (w' - w''
+// rho) / rho^2.  For the loss sum_i Gbar_i . G_i: gbar_i = L_i^T Gbar_i,
+// Bbar_i = -L_i^T (sum_c Gbar_i,c g_i,c^T) L_i^T (the inverse's adjoint), and
+// pair (i, j) adds rbar_ij = V_j [H (sum_c dphi_c gbar_i,c + Bbar_i r) +
+// Bbar_i^T f r] to r_j and subtracts it from r_i.  k_gradpos_a forms gbar_i
+// and Bbar_i per fluid particle (into the pass-1 scratch W.Ct and W.gv);
+// k_gradpos_b gathers every particle's sum over its pairs from both ends (the
+// neighbour relation is symmetric), deterministic.  FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double kern_w2(double r, double inv_l, double ad)
+{
+    const double q = r * inv_l;
+    if (q < 1.0) return ad * (-3.0 + 4.5 * q) * inv_l * inv_l;
+    if (q < 2.0) return ad * 1.5 * (2.0 - q) * inv_l * inv_l;
+    return 0.0;
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_gradpos_a(DevParams P, const Part c, Work W, int n,
+                                                   int ncomp, const double *phi,
+                                                   const double *grad_bar)
+{
+    if (step_failed(W.status)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || c.type[i] != FLUID) return;
+    const int64_t cap = W.cap;
+    double xi[3];
+    load_hat<D>(c, i, xi);
+    const int oi = c.orig[i];
+    double B[D * D], g[3][D];
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) B[q] = 0.0;
+    for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+        for (int K = 0; K < D; ++K) g[cc][K] = 0.0;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        const int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3], r[D], rr2 = 0.0;
+        load_hat<D>(c, j, xj);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xj[K] - xi[K];
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == 0.0) continue;
+        const double rr = sqrt(rr2);
+        double w, dw;
+        kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+        const double f = -dw / rr, V = W.vol[j];
+#pragma unroll
+        for (int K = 0; K < D; ++K)
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) B[K * D + L2] += V * f * r[K] * r[L2];
+        const int oj = c.orig[j];
+        for (int cc = 0; cc < ncomp; ++cc) {
+            const double dphi = phi[(int64_t)cc * n + oj] - phi[(int64_t)cc * n + oi];
+#pragma unroll
+            for (int K = 0; K < D; ++K) g[cc][K] += V * dphi * f * r[K];
+        }
+    }
+    double L[D * D];
+    if (!inv_small<D>(B, L)) {
+        set_error(W.status, VCT_ERR_SINGULAR, i);
+        return;
+    }
+    double Lbar[D * D];
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) Lbar[q] = 0.0;
+    for (int cc = 0; cc < ncomp; ++cc) {
+        double Gb[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) Gb[K] = grad_bar[((int64_t)cc * D + K) * n + oi];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {   // gbar = L^T Gbar
+            double s = 0.0;
+#pragma unroll
+            for (int M2 = 0; M2 < D; ++M2) s += L[M2 * D + K] * Gb[M2];
+            W.Ct[((int64_t)cc * D + K) * cap + i] = s;
+        }
+#pragma unroll
+        for (int K = 0; K < D; ++K)
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) Lbar[K * D + L2] += Gb[K] * g[cc][L2];
+    }
+    // Bbar = -L^T Lbar L^T
+    double T[D * D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < D; ++m) s += L[m * D + a] * Lbar[m * D + b];
+            T[a * D + b] = s;
+        }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < D; ++m) s += T[a * D + m] * L[b * D + m];
+            W.gv[(int64_t)(a * D + b) * cap + i] = -s;
+        }
+}
+
+// rbar of pair (i, j) at r = r_j - r_i, from i's gbar and Bbar
+template <int D>
+__device__ __forceinline__ void gradpos_pair(const Work &W, int i, int ncomp, const double *dphi,
+                                             const double *r, double rr, double f, double fp,
+                                             double V, double *rb)
+{
+    const int64_t cap = W.cap;
+    double v[D], Bt[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double s = 0.0, t = 0.0;
+        for (int cc = 0; cc < ncomp; ++cc) s += dphi[cc] * W.Ct[((int64_t)cc * D + K) * cap + i];
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) {
+            s += W.gv[(int64_t)(K * D + L2) * cap + i] * r[L2];        // Bbar r
+            t += W.gv[(int64_t)(L2 * D + K) * cap + i] * f * r[L2];    // Bbar^T f r
+        }
+        v[K] = s;
+        Bt[K] = t;
+    }
+    double rv = 0.0;
+#pragma unroll
+    for (int K = 0; K < D; ++K) rv += r[K] * v[K];
+#pragma unroll
+    for (int K = 0; K < D; ++K) rb[K] = V * (f * v[K] + fp / rr * r[K] * rv + Bt[K]);
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_gradpos_b(DevParams P, const Part c, Work W, int n,
+                                                   int ncomp, const double *phi, double *xh_bar)
+{
+    if (step_failed(W.status)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t cap = W.cap;
+    const int tk = c.type[k], ok = c.orig[k];
+    double out[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) out[K] = 0.0;
+    if (tk != VIRTUAL) {
+        double xk[3];
+        load_hat<D>(c, k, xk);
+        const int cnt = W.nbr_cnt[k];
+        for (int q = 0; q < cnt; ++q) {
+            const int m = W.nbr[(int64_t)q * cap + k];
+            const int tm = c.type[m];
+            if (tm == VIRTUAL) continue;
+            if (tk != FLUID && tm != FLUID) continue;
+            double xm[3], r[D], rn[D], rr2 = 0.0;
+            load_hat<D>(c, m, xm);
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                r[K] = xm[K] - xk[K];   // r_km
+                rn[K] = -r[K];          // r_mk
+                rr2 += r[K] * r[K];
+            }
+            if (rr2 == 0.0) continue;
+            const double rr = sqrt(rr2);
+            double w, dw;
+            kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+            const double w2 = kern_w2(rr, P.inv_l, P.ad);
+            const double f = -dw / rr, fp = (dw - w2 * rr) / (rr * rr);
+            const int om = c.orig[m];
+            double dphi[3], rb[D];
+            if (tk == FLUID) {   // pair (k, m): rbar_km leaves r_k
+                for (int cc = 0; cc < ncomp; ++cc)
+                    dphi[cc] = phi[(int64_t)cc * n + om] - phi[(int64_t)cc * n + ok];
+                gradpos_pair<D>(W, k, ncomp, dphi, r, rr, f, fp, W.vol[m], rb);
+#pragma unroll
+                for (int K = 0; K < D; ++K) out[K] -= rb[K];
+            }
+            if (tm == FLUID) {   // pair (m, k): rbar_mk arrives at r_k
+                for (int cc = 0; cc < ncomp; ++cc)
+                    dphi[cc] = phi[(int64_t)cc * n + ok] - phi[(int64_t)cc * n + om];
+                gradpos_pair<D>(W, m, ncomp, dphi, rn, rr, f, fp, W.vol[k], rb);
+#pragma unroll
+                for (int K = 0; K < D; ++K) out[K] += rb[K];
+            }
+        }
+    }
+#pragma unroll
+    for (int K = 0; K < D; ++K) xh_bar[(int64_t)K * n + ok] = out[K];
+}
+
+void launch_gradpos(const DevParams &P, Part cur, Work W, int64_t n, int ncomp, const double *phi,
+                    const double *grad_bar, double *xh_bar, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        k_gradpos_a<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, ncomp, phi, grad_bar);
+        k_gradpos_b<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, ncomp, phi, xh_bar);
+    } else {
+        k_gradpos_a<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, ncomp, phi, grad_bar);
+        k_gradpos_b<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, ncomp, phi, xh_bar);
+    }
+}
+
 }  // namespace vct
 
 // ===========================================================================

@@ -20,7 +20,8 @@ MAP = {"E": 0, "BF": 1, "BFE": 2, "SIGMA": 3}
 VCT_MAX_GAUSS = 32
 
 EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
-           "sph2_derivatives", "sph2_derivatives_backward", "vct_map_backward", "vct_step",
+           "sph2_derivatives", "sph2_derivatives_backward", "sph2_gradient_backward_positions",
+           "vct_map_backward", "vct_step",
            "vct_batch_step",
            "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
@@ -103,6 +104,7 @@ def load_library(path=LIB_PATH):
     L.vct_step_probe.argtypes = [vp, C.POINTER(vct_state), C.POINTER(vct_probe),
                                  C.POINTER(vct_stats)]
     L.vct_ppe_adjoint.argtypes = [vp, vp, vp, C.POINTER(vct_stats)]
+    L.sph2_gradient_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp]
     L.vct_set_profiling.argtypes = [vp, C.c_int32]
     L.vct_stage_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.vct_last_error.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -111,7 +113,7 @@ def load_library(path=LIB_PATH):
     L.vct_destroy.argtypes = [vp]
     L.vct_destroy.restype = None
     for name in ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives",
-                 "sph2_derivatives_backward", "vct_map_backward",
+                 "sph2_derivatives_backward", "sph2_gradient_backward_positions", "vct_map_backward",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
@@ -303,6 +305,20 @@ class Solver:
                                               c(sy_bar), c(c0_bar), c(c3_bar), out),
                     "vct_map_backward")
         return np.array(out[:])
+
+    def sph2_gradient_backward_positions(self, state, phi, grad_bar):
+        """Gradient of sum grad_bar . grad_hat (sph2_derivatives' corrected
+        gradient) with respect to the projected positions, (dim, n) float64."""
+        import torch
+        phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").reshape(-1, state.n).contiguous()
+        grad_bar = torch.as_tensor(grad_bar, dtype=torch.float64, device="cuda").contiguous()
+        out = torch.zeros((self.dim, state.n), dtype=torch.float64, device="cuda")
+        s = state.struct()
+        self._check(self.lib.sph2_gradient_backward_positions(
+            self.ctx, C.byref(s), C.c_void_p(phi.data_ptr()), int(phi.shape[0]),
+            C.c_void_p(grad_bar.data_ptr()), C.c_void_p(out.data_ptr())),
+            "sph2_gradient_backward_positions")
+        return out
 
     def vct_ppe_adjoint(self, p_bar):
         """b_bar = A^-T p_bar for the pressure system of the last step (caller
