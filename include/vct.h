@@ -264,6 +264,20 @@ vct_status sph2_gradient_backward_positions(vct_ctx *ctx, const vct_state *state
                                             const double *phi, int32_t ncomp,
                                             const double *grad_hat_bar, double *xh_bar);
 
+/* Derivative of the SPH(2) second derivatives of sph2_derivatives (d2_hat, from
+ * D = 2 M_i^-1 b_i, Eq. sec_SPH2, cross terms halved) with respect to the
+ * projected particle positions, through the kernel's first and second
+ * derivatives, the corrected gradient, C_i, F_ij, q_ij and p_ij, for the current
+ * state with its neighbour sets and particle volumes held fixed: given one field
+ * phi (n, caller order) and d2_hat_bar (m x n, caller order; m = 3 / 6), writes
+ * xh_bar (dim x n, caller order) = the gradient of sum d2_hat_bar . d2_hat with
+ * respect to r^.  FP64; deterministic; virtual particles get 0.  Keeps its
+ * per-particle factors (2 d^2 + 2 d m + 2 d + 2 m doubles) in the context's
+ * pressure-coefficient storage: VCT_ERR_CAPACITY if max_neighbours leaves too
+ * few slots there; the next step rebuilds that storage. */
+vct_status sph2_d2_backward_positions(vct_ctx *ctx, const vct_state *state, const double *phi,
+                                      const double *d2_hat_bar, double *xh_bar);
+
 /* Derivative through the map with respect to the bathymetry parameters
  * theta = [h0, slope_x, slope_y, cos_amp, cos_len, amp[G], cx[G], cy[G], width[G]]
  * (G = n_gauss; 5 + 4G entries): given per-particle adjoints (DEVICE arrays of n,

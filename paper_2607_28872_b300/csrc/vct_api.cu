@@ -1046,6 +1046,27 @@ VCT_API vct_status sph2_gradient_backward_positions(vct_ctx *c, const vct_state 
     return finish(c, nullptr, 0);
 }
 
+VCT_API vct_status sph2_d2_backward_positions(vct_ctx *c, const vct_state *s, const double *phi,
+                                              const double *d2_hat_bar, double *xh_bar)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (!phi || !d2_hat_bar || !xh_bar) return VCT_ERR_ARG;
+    // the per-particle factors and adjoints live in the pressure coefficients'
+    // storage: 30 (2-D) / 72 (3-D) doubles per particle must fit in its slots
+    const int64_t eg = c->P.dim == 2 ? 4 : 8, need = c->P.dim == 2 ? 30 : 72;
+    const int64_t kb = ((int64_t)c->W.max_nbr + eg - 1) / eg * eg;
+    if ((c->P.precision == VCT_MIXED ? kb / 2 : kb) < need) return VCT_ERR_CAPACITY;
+    const int64_t n = s->n;
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    geometry(c, n);
+    launch_d2pos(c->P, cur(c), c->W, n, phi, d2_hat_bar, xh_bar, c->st);
+    c->launches += 3;
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, nullptr, 0);
+}
+
 VCT_API vct_status vct_map_backward(vct_ctx *c, const vct_state *s, const double *zh_bar,
                                     const double *J_bar, const double *sx_bar,
                                     const double *sy_bar, const double *c0_bar,

@@ -176,6 +176,9 @@ int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nbl
 bool krylov_mg_fly_default(long long rows, int dim);
 int krylov_fly_batch_blocks(int precision, int dim, size_t smem, bool expl);
 size_t krylov_batch_stage_bytes(int precision, int dim);
+// derivative of the SPH(2) second derivatives with respect to the projected positions
+void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
+                  const double *d2_bar, double *xh_bar, cudaStream_t st);
 // derivative of the corrected gradient with respect to the projected positions
 void launch_gradpos(const DevParams &P, Part cur, Work W, int64_t n, int ncomp, const double *phi,
                     const double *grad_bar, double *xh_bar, cudaStream_t st);

@@ -4762,6 +4762,370 @@ void launch_gradpos(const DevParams &P, Part cur, Work W, int64_t n, int ncomp, 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// a12 (part): derivative of the SPH(2) second derivatives (Eq. sec_SPH2,
+// D = 2 M_i^-1 b_i, cross terms halved in the output) with respect to the
+// projected positions, neighbour sets and volumes held fixed.  Per fluid
+// particle i, with gt = L_i grad w, F = r.gt / rho^4, q = q(r), p = q - C_i^T r
+// (C_i = L_i sum V grad w q^T), e = phi_ij - r.g_i (g_i the corrected
+// gradient): M_i = sum V F q p^T, b_i = sum V F q e.  Reverse: xbar = 2 Dbar,
+// bbar = M^-T xbar, Mbar = -bbar x^T; per pair Fbar = V (q.bbar)(e - x.p),
+// qbar = V F (e - x.p) bbar + pbar, pbar = -V F (q.bbar) x, ebar = V F (q.bbar),
+// which feed gbar = -sum ebar r, Cbar = -sum r pbar^T and Lbar (through gt),
+// then Lbar += gbar g_raw^T + Cbar Gq^T, Bbar = -L^T Lbar L^T, and every term's
+// dependence on r (through rho, grad w, q, p, e) gives the pair's rbar.
+// k_d2pos_a forms and stores i's factors and adjoints (L, C, g, x, bbar,
+// L^T gbar, L^T Cbar, Bbar: 2d^2 + 2dm + 2d + 2m doubles, in the scratch of the
+// pressure-equation coefficients, which the next step rebuilds); k_d2pos_b
+// gathers each particle's sum over its pairs from both ends.  FP64, one field.
+// ---------------------------------------------------------------------------
+template <int D>
+struct D2Slots {
+    static constexpr int M = D == 2 ? 3 : 6;
+    static constexpr int L = 0, C = L + D * D, G = C + D * M, X = G + D, BB = X + M, GR = BB + M,
+                         GQ = GR + D, BBAR = GQ + D * M, N = BBAR + D * D;
+};
+
+template <int D>
+__device__ __forceinline__ void qvec_d(const double *r, double *q)
+{
+    if (D == 2) {
+        q[0] = r[0] * r[0]; q[1] = r[1] * r[1]; q[2] = r[0] * r[1];
+    } else {
+        q[0] = r[0] * r[0]; q[1] = r[1] * r[1]; q[2] = r[2] * r[2];
+        q[3] = r[0] * r[1]; q[4] = r[1] * r[2]; q[5] = r[2] * r[0];
+    }
+}
+
+// (dq/dr)^T qb
+template <int D>
+__device__ __forceinline__ void qjac_t(const double *r, const double *qb, double *out)
+{
+    if (D == 2) {
+        out[0] = 2.0 * r[0] * qb[0] + r[1] * qb[2];
+        out[1] = 2.0 * r[1] * qb[1] + r[0] * qb[2];
+    } else {
+        out[0] = 2.0 * r[0] * qb[0] + r[1] * qb[3] + r[2] * qb[5];
+        out[1] = 2.0 * r[1] * qb[1] + r[0] * qb[3] + r[2] * qb[4];
+        out[2] = 2.0 * r[2] * qb[2] + r[1] * qb[4] + r[0] * qb[5];
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_d2pos_a(DevParams P, const Part c, Work W, int n,
+                                                 const double *phi, const double *d2_bar,
+                                                 double *scr)
+{
+    constexpr int M = D2Slots<D>::M;
+    using SL = D2Slots<D>;
+    if (step_failed(W.status)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || c.type[i] != FLUID) return;
+    const int64_t cap = W.cap;
+    double xi[3];
+    load_hat<D>(c, i, xi);
+    const int oi = c.orig[i];
+    const double phii = phi[oi];
+    double B[D * D], Gq[D * M], graw[D];
+    for (int q = 0; q < D * D; ++q) B[q] = 0.0;
+    for (int q = 0; q < D * M; ++q) Gq[q] = 0.0;
+    for (int K = 0; K < D; ++K) graw[K] = 0.0;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {   // B, Gq, g_raw
+        const int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3], r[D], rr2 = 0.0, q[M];
+        load_hat<D>(c, j, xj);
+        for (int K = 0; K < D; ++K) { r[K] = xj[K] - xi[K]; rr2 += r[K] * r[K]; }
+        if (rr2 == 0.0) continue;
+        const double rr = sqrt(rr2);
+        double w, dw;
+        kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+        const double f = -dw / rr, V = W.vol[j], dphi = phi[c.orig[j]] - phii;
+        qvec_d<D>(r, q);
+        for (int K = 0; K < D; ++K) {
+            const double gk = f * r[K];
+            for (int L2 = 0; L2 < D; ++L2) B[K * D + L2] += V * gk * r[L2];
+            for (int a = 0; a < M; ++a) Gq[K * M + a] += V * gk * q[a];
+            graw[K] += V * dphi * gk;
+        }
+    }
+    double L[D * D];
+    if (!inv_small<D>(B, L)) {
+        set_error(W.status, VCT_ERR_SINGULAR, i);
+        return;
+    }
+    double C[D * M], g[D];
+    for (int K = 0; K < D; ++K) {
+        g[K] = 0.0;
+        for (int L2 = 0; L2 < D; ++L2) g[K] += L[K * D + L2] * graw[L2];
+        for (int a = 0; a < M; ++a) {
+            double s2 = 0.0;
+            for (int L2 = 0; L2 < D; ++L2) s2 += L[K * D + L2] * Gq[L2 * M + a];
+            C[K * M + a] = s2;
+        }
+    }
+    double Mm[M * M], b[M];
+    for (int q = 0; q < M * M; ++q) Mm[q] = 0.0;
+    for (int a = 0; a < M; ++a) b[a] = 0.0;
+    for (int k = 0; k < cnt; ++k) {   // M, b
+        const int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3], r[D], rr2 = 0.0, q[M], pv[M], gt[D];
+        load_hat<D>(c, j, xj);
+        for (int K = 0; K < D; ++K) { r[K] = xj[K] - xi[K]; rr2 += r[K] * r[K]; }
+        if (rr2 == 0.0) continue;
+        const double rr = sqrt(rr2);
+        double w, dw;
+        kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+        const double f = -dw / rr, V = W.vol[j], dphi = phi[c.orig[j]] - phii;
+        double rg = 0.0, rgg = 0.0;
+        for (int K = 0; K < D; ++K) {
+            double s2 = 0.0;
+            for (int L2 = 0; L2 < D; ++L2) s2 += L[K * D + L2] * f * r[L2];
+            gt[K] = s2;
+            rg += r[K] * s2;
+            rgg += r[K] * g[K];
+        }
+        const double F = rg / (rr2 * rr2), e = dphi - rgg;
+        qvec_d<D>(r, q);
+        for (int a = 0; a < M; ++a) {
+            double s2 = 0.0;
+            for (int K = 0; K < D; ++K) s2 += C[K * M + a] * r[K];
+            pv[a] = q[a] - s2;
+        }
+        for (int a = 0; a < M; ++a) {
+            for (int bq = 0; bq < M; ++bq) Mm[a * M + bq] += V * F * q[a] * pv[bq];
+            b[a] += V * F * q[a] * e;
+        }
+    }
+    int piv[M];
+    if (!lu_factor<M>(Mm, piv)) {
+        set_error(W.status, VCT_ERR_SINGULAR, i);
+        return;
+    }
+    double x[M], bb[M];
+    for (int a = 0; a < M; ++a) x[a] = b[a];
+    lu_apply<M, 1>(Mm, piv, x);
+    for (int a = 0; a < M; ++a) {   // xbar = 2 Dbar, the output's cross terms halved
+        const double db = d2_bar[(int64_t)a * n + oi];
+        bb[a] = 2.0 * (a < D ? db : 0.5 * db);
+    }
+    lu_apply_t<M>(Mm, piv, bb);
+    double gb[D], Cb[D * M], Lb[D * D];
+    for (int K = 0; K < D; ++K) gb[K] = 0.0;
+    for (int q = 0; q < D * M; ++q) Cb[q] = 0.0;
+    for (int q = 0; q < D * D; ++q) Lb[q] = 0.0;
+    for (int k = 0; k < cnt; ++k) {   // per-i sums of the pair adjoints
+        const int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3], r[D], rr2 = 0.0, q[M], pv[M], gw[D];
+        load_hat<D>(c, j, xj);
+        for (int K = 0; K < D; ++K) { r[K] = xj[K] - xi[K]; rr2 += r[K] * r[K]; }
+        if (rr2 == 0.0) continue;
+        const double rr = sqrt(rr2);
+        double w, dw;
+        kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+        const double f = -dw / rr, V = W.vol[j], dphi = phi[c.orig[j]] - phii;
+        double rg = 0.0, rgg = 0.0;
+        for (int K = 0; K < D; ++K) gw[K] = f * r[K];
+        for (int K = 0; K < D; ++K) {
+            double s2 = 0.0;
+            for (int L2 = 0; L2 < D; ++L2) s2 += L[K * D + L2] * gw[L2];
+            rg += r[K] * s2;
+            rgg += r[K] * g[K];
+        }
+        const double F = rg / (rr2 * rr2), e = dphi - rgg;
+        qvec_d<D>(r, q);
+        double qbd = 0.0, xp = 0.0;
+        for (int a = 0; a < M; ++a) {
+            double s2 = 0.0;
+            for (int K = 0; K < D; ++K) s2 += C[K * M + a] * r[K];
+            pv[a] = q[a] - s2;
+            qbd += q[a] * bb[a];
+        }
+        for (int a = 0; a < M; ++a) xp += x[a] * pv[a];
+        const double Fb = V * qbd * (e - xp), eb = V * F * qbd;
+        for (int K = 0; K < D; ++K) gb[K] -= eb * r[K];
+        for (int K = 0; K < D; ++K)
+            for (int a = 0; a < M; ++a) Cb[K * M + a] += r[K] * V * F * qbd * x[a];   // -r pbar^T
+        const double rgb = Fb / (rr2 * rr2);
+        for (int K = 0; K < D; ++K)
+            for (int L2 = 0; L2 < D; ++L2) Lb[K * D + L2] += rgb * r[K] * gw[L2];
+    }
+    for (int K = 0; K < D; ++K)
+        for (int L2 = 0; L2 < D; ++L2) {
+            double s2 = gb[K] * graw[L2];
+            for (int a = 0; a < M; ++a) s2 += Cb[K * M + a] * Gq[L2 * M + a];
+            Lb[K * D + L2] += s2;
+        }
+    double gr[D], Gqb[D * M], T[D * D];
+    for (int K = 0; K < D; ++K) {
+        double s2 = 0.0;
+        for (int L2 = 0; L2 < D; ++L2) s2 += L[L2 * D + K] * gb[L2];
+        gr[K] = s2;
+        for (int a = 0; a < M; ++a) {
+            double s3 = 0.0;
+            for (int L2 = 0; L2 < D; ++L2) s3 += L[L2 * D + K] * Cb[L2 * M + a];
+            Gqb[K * M + a] = s3;
+        }
+    }
+    for (int a = 0; a < D; ++a)
+        for (int bq = 0; bq < D; ++bq) {
+            double s2 = 0.0;
+            for (int m2 = 0; m2 < D; ++m2) s2 += L[m2 * D + a] * Lb[m2 * D + bq];
+            T[a * D + bq] = s2;
+        }
+    auto st = [&](int slot, double v) { scr[(int64_t)slot * cap + i] = v; };
+    for (int q = 0; q < D * D; ++q) st(SL::L + q, L[q]);
+    for (int q = 0; q < D * M; ++q) st(SL::C + q, C[q]);
+    for (int K = 0; K < D; ++K) st(SL::G + K, g[K]);
+    for (int a = 0; a < M; ++a) st(SL::X + a, x[a]);
+    for (int a = 0; a < M; ++a) st(SL::BB + a, bb[a]);
+    for (int K = 0; K < D; ++K) st(SL::GR + K, gr[K]);
+    for (int q = 0; q < D * M; ++q) st(SL::GQ + q, Gqb[q]);
+    for (int a = 0; a < D; ++a)
+        for (int bq = 0; bq < D; ++bq) {
+            double s2 = 0.0;
+            for (int m2 = 0; m2 < D; ++m2) s2 += T[a * D + m2] * L[bq * D + m2];
+            st(SL::BBAR + a * D + bq, -s2);
+        }
+}
+
+// rbar of pair (i, j) at r = r_j - r_i from i's stored factors and adjoints
+template <int D>
+__device__ void d2pos_pair(const DevParams &P, const double *scr, int64_t cap, int i, double dphi,
+                           const double *r, double V, double *rb)
+{
+    constexpr int M = D2Slots<D>::M;
+    using SL = D2Slots<D>;
+    auto ld = [&](int slot) { return scr[(int64_t)slot * cap + i]; };
+    double rr2 = 0.0;
+    for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
+    const double rr = sqrt(rr2);
+    double w, dw;
+    kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+    const double w2 = kern_w2(rr, P.inv_l, P.ad);
+    const double f = -dw / rr, fp = (dw - w2 * rr) / rr2;
+    double gw[D], gt[D], q[M], pv[M], rg = 0.0, rgg = 0.0;
+    for (int K = 0; K < D; ++K) gw[K] = f * r[K];
+    for (int K = 0; K < D; ++K) {
+        double s2 = 0.0;
+        for (int L2 = 0; L2 < D; ++L2) s2 += ld(SL::L + K * D + L2) * gw[L2];
+        gt[K] = s2;
+        rg += r[K] * s2;
+        rgg += r[K] * ld(SL::G + K);
+    }
+    const double F = rg / (rr2 * rr2), e = dphi - rgg;
+    qvec_d<D>(r, q);
+    double qbd = 0.0, xp = 0.0;
+    for (int a = 0; a < M; ++a) {
+        double s2 = 0.0;
+        for (int K = 0; K < D; ++K) s2 += ld(SL::C + K * M + a) * r[K];
+        pv[a] = q[a] - s2;
+        qbd += q[a] * ld(SL::BB + a);
+    }
+    for (int a = 0; a < M; ++a) xp += ld(SL::X + a) * pv[a];
+    const double Fb = V * qbd * (e - xp), eb = V * F * qbd;
+    double qb[M], pb[M];
+    for (int a = 0; a < M; ++a) {
+        pb[a] = -V * F * qbd * ld(SL::X + a);
+        qb[a] = V * F * (e - xp) * ld(SL::BB + a) + pb[a];
+    }
+    for (int K = 0; K < D; ++K) {   // from e, p, F (rho and r.gt)
+        double s2 = 0.0;
+        for (int a = 0; a < M; ++a) s2 += ld(SL::C + K * M + a) * pb[a];
+        rb[K] = -eb * ld(SL::G + K) - s2 + (-4.0 * rg / (rr2 * rr2 * rr) * Fb) * r[K] / rr +
+                Fb / (rr2 * rr2) * gt[K];
+    }
+    // grad w's adjoint: L^T (rgbar r) + V dphi L^T gbar + V (L^T Cbar) q + V Bbar r
+    const double rgb = Fb / (rr2 * rr2);
+    double gwb[D];
+    for (int K = 0; K < D; ++K) {
+        double s2 = 0.0;
+        for (int L2 = 0; L2 < D; ++L2)
+            s2 += ld(SL::L + L2 * D + K) * rgb * r[L2] + V * ld(SL::BBAR + K * D + L2) * r[L2];
+        s2 += V * dphi * ld(SL::GR + K);
+        for (int a = 0; a < M; ++a) s2 += V * ld(SL::GQ + K * M + a) * q[a];
+        gwb[K] = s2;
+    }
+    double rgw = 0.0;
+    for (int K = 0; K < D; ++K) rgw += r[K] * gwb[K];
+    for (int K = 0; K < D; ++K) rb[K] += f * gwb[K] + fp / rr * r[K] * rgw;   // H gwbar
+    for (int a = 0; a < M; ++a) {   // q's adjoint, with V (L^T Cbar)^T grad w
+        double s2 = 0.0;
+        for (int K = 0; K < D; ++K) s2 += ld(SL::GQ + K * M + a) * gw[K];
+        qb[a] += V * s2;
+    }
+    double qj[D];
+    qjac_t<D>(r, qb, qj);
+    for (int K = 0; K < D; ++K) {
+        double s2 = 0.0;
+        for (int L2 = 0; L2 < D; ++L2) s2 += ld(SL::BBAR + L2 * D + K) * gw[L2];
+        rb[K] += qj[K] + V * s2;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_d2pos_b(DevParams P, const Part c, Work W, int n,
+                                                 const double *phi, const double *scr,
+                                                 double *xh_bar)
+{
+    if (step_failed(W.status)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t cap = W.cap;
+    const int tk = c.type[k], ok = c.orig[k];
+    double out[D];
+    for (int K = 0; K < D; ++K) out[K] = 0.0;
+    if (tk != VIRTUAL) {
+        double xk[3];
+        load_hat<D>(c, k, xk);
+        const int cnt = W.nbr_cnt[k];
+        for (int q = 0; q < cnt; ++q) {
+            const int m = W.nbr[(int64_t)q * cap + k];
+            const int tm = c.type[m];
+            if (tm == VIRTUAL || (tk != FLUID && tm != FLUID)) continue;
+            double xm[3], r[D], rn[D], rr2 = 0.0;
+            load_hat<D>(c, m, xm);
+            for (int K = 0; K < D; ++K) {
+                r[K] = xm[K] - xk[K];
+                rn[K] = -r[K];
+                rr2 += r[K] * r[K];
+            }
+            if (rr2 == 0.0) continue;
+            const double dphi = phi[c.orig[m]] - phi[ok];
+            double rb[D];
+            if (tk == FLUID) {   // pair (k, m)
+                d2pos_pair<D>(P, scr, cap, k, dphi, r, W.vol[m], rb);
+                for (int K = 0; K < D; ++K) out[K] -= rb[K];
+            }
+            if (tm == FLUID) {   // pair (m, k)
+                d2pos_pair<D>(P, scr, cap, m, -dphi, rn, W.vol[k], rb);
+                for (int K = 0; K < D; ++K) out[K] += rb[K];
+            }
+        }
+    }
+    for (int K = 0; K < D; ++K) xh_bar[(int64_t)K * n + ok] = out[K];
+}
+
+void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
+                  const double *d2_bar, double *xh_bar, cudaStream_t st)
+{
+    // scratch: the pressure-equation coefficients' storage (>= 32 doubles per
+    // particle in 2-D, 80 in 3-D in either form; the next step rebuilds it)
+    double *scr = P.precision == VCT_MIXED ? (double *)W.pvalf : W.pval;
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        k_d2pos_a<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, d2_bar, scr);
+        k_d2pos_b<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+    } else {
+        k_d2pos_a<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, d2_bar, scr);
+        k_d2pos_b<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+    }
+}
+
 }  // namespace vct
 
 // ===========================================================================

@@ -21,6 +21,7 @@ VCT_MAX_GAUSS = 32
 
 EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
            "sph2_derivatives", "sph2_derivatives_backward", "sph2_gradient_backward_positions",
+           "sph2_d2_backward_positions",
            "vct_map_backward", "vct_step",
            "vct_batch_step",
            "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling", "vct_stage_times",
@@ -105,6 +106,7 @@ def load_library(path=LIB_PATH):
                                  C.POINTER(vct_stats)]
     L.vct_ppe_adjoint.argtypes = [vp, vp, vp, C.POINTER(vct_stats)]
     L.sph2_gradient_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp]
+    L.sph2_d2_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp]
     L.vct_set_profiling.argtypes = [vp, C.c_int32]
     L.vct_stage_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.vct_last_error.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -113,7 +115,8 @@ def load_library(path=LIB_PATH):
     L.vct_destroy.argtypes = [vp]
     L.vct_destroy.restype = None
     for name in ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives",
-                 "sph2_derivatives_backward", "sph2_gradient_backward_positions", "vct_map_backward",
+                 "sph2_derivatives_backward", "sph2_gradient_backward_positions",
+                 "sph2_d2_backward_positions", "vct_map_backward",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
@@ -318,6 +321,19 @@ class Solver:
             self.ctx, C.byref(s), C.c_void_p(phi.data_ptr()), int(phi.shape[0]),
             C.c_void_p(grad_bar.data_ptr()), C.c_void_p(out.data_ptr())),
             "sph2_gradient_backward_positions")
+        return out
+
+    def sph2_d2_backward_positions(self, state, phi, d2_bar):
+        """Gradient of sum d2_bar . d2_hat (sph2_derivatives' second derivatives
+        of one field) with respect to the projected positions, (dim, n) float64."""
+        import torch
+        phi = torch.as_tensor(phi, dtype=torch.float64, device="cuda").reshape(state.n).contiguous()
+        d2_bar = torch.as_tensor(d2_bar, dtype=torch.float64, device="cuda").contiguous()
+        out = torch.zeros((self.dim, state.n), dtype=torch.float64, device="cuda")
+        s = state.struct()
+        self._check(self.lib.sph2_d2_backward_positions(
+            self.ctx, C.byref(s), C.c_void_p(phi.data_ptr()), C.c_void_p(d2_bar.data_ptr()),
+            C.c_void_p(out.data_ptr())), "sph2_d2_backward_positions")
         return out
 
     def vct_ppe_adjoint(self, p_bar):

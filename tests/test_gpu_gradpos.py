@@ -1,6 +1,7 @@
-"""Derivative of the corrected gradient with respect to the projected particle
-positions (sph2_gradient_backward_positions): against central differences of
-the oracle's gradient (Eq. gra_1st) in each projected coordinate of fluid and
+"""Derivatives of the corrected gradient (sph2_gradient_backward_positions) and
+of the SPH(2) second derivatives (sph2_d2_backward_positions) with respect to
+the projected particle positions: against central differences of
+the oracle's outputs (Eqs. gra_1st, sec_SPH2) in each projected coordinate of fluid and
 wall particles, with the neighbour sets unchanged by the step, in 2-D (E map,
 aspect 1) and 3-D (E map, aspect 2: a projected step dz^ is a physical step
 dz^ / 2); and, at the 2-D wave's size, the invariance of the loss under a
@@ -78,3 +79,52 @@ def test_position_gradient_translation_invariance(vct):
     assert np.abs(xb).max() > 0.0
     for K in range(sc.dim):
         assert abs(xb[K].sum()) <= 1e-10 * np.abs(xb[K]).sum()
+
+
+@pytest.mark.parametrize("name,make,aspect", CASES, ids=[c[0] for c in CASES])
+def test_second_derivative_position_gradient_matches_oracle_differences(vct, name, make, aspect):
+    import torch
+    sc = make()
+    d, n = sc.dim, sc.n
+    m = 3 if d == 2 else 6
+    rng = np.random.default_rng(23)
+    phi = rng.normal(size=n)
+    dbar = rng.normal(size=(m, n))
+    solver = vct.Solver(sc)
+    xb = solver.sph2_d2_backward_positions(vct.DeviceState(sc), torch.tensor(phi),
+                                           torch.tensor(dbar)).cpu().numpy()
+    assert np.all(xb[:, sc.type == S.VIRTUAL] == 0.0)
+    l, re, re2 = O.radii(sc)
+    xh0, _ = O.projected(sc)
+    row0, col0 = O.neighbours(d, xh0, re, re2, mode=0)
+    eps = 1e-7 * sc.params["d0"]
+    names = ("x", "y", "z") if d == 3 else ("x", "z")
+    picks = list(np.flatnonzero(sc.type == S.FLUID)[::19][:5]) + \
+        list(np.flatnonzero(sc.type == S.WALL)[::13][:3])
+    scale = np.abs(xb).max()
+    for p in picks:
+        for K, nm in enumerate(names):
+            step = eps / aspect if nm == "z" else eps
+            vals = []
+            for sgn in (1.0, -1.0):
+                s2 = sc.copy()
+                getattr(s2, nm)[p] += sgn * step
+                xh, _ = O.projected(s2)
+                row, col = O.neighbours(d, xh, re, re2, mode=0)
+                assert np.array_equal(row, row0) and np.array_equal(col, col0)
+                _, d2, _ = O.sph2_derivatives(s2, phi[None, :])
+                vals.append(np.sum(dbar * d2[0]))
+            fd = (vals[0] - vals[1]) / (2 * eps)
+            assert abs(fd - xb[K, p]) <= 1e-6 * scale, (p, nm, fd, xb[K, p])
+    for K in range(d):   # rigid translation leaves the outputs unchanged
+        assert abs(xb[K].sum()) <= 1e-10 * np.abs(xb[K]).sum()
+
+
+def test_second_derivative_position_gradient_needs_scratch(vct):
+    import torch
+    sc = CASES[0][1]()
+    solver = vct.Solver(sc, max_neighbours=24)
+    with pytest.raises(vct.VCTError) as e:
+        solver.sph2_d2_backward_positions(vct.DeviceState(sc), torch.zeros(sc.n),
+                                          torch.zeros((3, sc.n)))
+    assert e.value.status == vct.VCT_ERR_CAPACITY
