@@ -197,6 +197,15 @@ vct_status vct_init(vct_ctx **ctx, const vct_bathymetry *bathy, vct_map_kind kin
 
 vct_status vct_set_stream(vct_ctx *ctx, void *stream);
 
+/* Forget the pressures of the context's previous steps (the history the
+ * pressure solve's initial guess extrapolates, used when a call continues the
+ * previous call's state): the next step starts its solve from the state's own
+ * pressure, as a fresh context would.  A run that is replayed from a snapshot
+ * (checkpointing for a reverse sweep) calls it at each snapshot, on the
+ * forward run and on the replay, so that both compute the same bits.  Queued
+ * on the context's stream; allocates nothing. */
+vct_status vct_reset_history(vct_ctx *ctx);
+
 /* Neighbour sets S_i = { j != i : |r^_j - r^_i| < r_e } in projected space
  * (Eq. SPH_neighbor_set), squared distance summed in coordinate order without
  * FMA.  Writes CSR over caller indices: row_ptr (n+1 int64, device) and col

@@ -972,6 +972,16 @@ VCT_API vct_status vct_set_stream(vct_ctx *c, void *stream)
     return VCT_OK;
 }
 
+VCT_API vct_status vct_reset_history(vct_ctx *c)
+{
+    if (!c) return VCT_ERR_ARG;
+    const size_t bytes = sizeof(double) * (size_t)c->cap;
+    cudaError_t e = cudaMemsetAsync(c->W.p_last, 0xFF, bytes, c->st);   // NaN: no history
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->W.p_prev, 0xFF, bytes, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->W.p_prev2, 0xFF, bytes, c->st);
+    return e == cudaSuccess ? VCT_OK : VCT_ERR_CUDA;
+}
+
 VCT_API vct_status vct_build_neighbours(vct_ctx *c, const vct_state *s, int64_t *row_ptr, int32_t *col,
                                 int64_t col_cap, int64_t *nnz)
 {

@@ -19,7 +19,8 @@ VCT_ERR_SINGULAR, VCT_ERR_NONFINITE, VCT_ERR_NOCONV, VCT_ERR_TIMEOUT = 4, 5, 6, 
 MAP = {"E": 0, "BF": 1, "BFE": 2, "SIGMA": 3}
 VCT_MAX_GAUSS = 32
 
-EXPORTS = ("vct_init", "vct_set_stream", "vct_build_neighbours", "vct_build_neighbours_noalloc",
+EXPORTS = ("vct_init", "vct_set_stream", "vct_reset_history", "vct_build_neighbours",
+           "vct_build_neighbours_noalloc",
            "sph2_derivatives", "sph2_derivatives_backward", "sph2_gradient_backward_positions",
            "sph2_d2_backward_positions",
            "vct_map_backward", "vct_step",
@@ -87,6 +88,7 @@ def load_library(path=LIB_PATH):
     L.vct_init.argtypes = [C.POINTER(vp), C.POINTER(vct_bathymetry), C.c_int, C.c_double,
                            C.POINTER(vct_params), C.c_int64, vp]
     L.vct_set_stream.argtypes = [vp, vp]
+    L.vct_reset_history.argtypes = [vp]
     L.vct_build_neighbours.argtypes = [vp, C.POINTER(vct_state), vp, vp, C.c_int64,
                                        C.POINTER(C.c_int64)]
     L.vct_build_neighbours_noalloc.argtypes = [C.POINTER(vct_bathymetry), C.c_int, C.c_double,
@@ -114,7 +116,8 @@ def load_library(path=LIB_PATH):
     L.vct_strerror.restype = C.c_char_p
     L.vct_destroy.argtypes = [vp]
     L.vct_destroy.restype = None
-    for name in ("vct_init", "vct_set_stream", "vct_build_neighbours", "sph2_derivatives",
+    for name in ("vct_init", "vct_set_stream", "vct_reset_history", "vct_build_neighbours",
+                 "sph2_derivatives",
                  "sph2_derivatives_backward", "sph2_gradient_backward_positions",
                  "sph2_d2_backward_positions", "vct_map_backward",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
@@ -336,6 +339,9 @@ class Solver:
             C.c_void_p(out.data_ptr())), "sph2_d2_backward_positions")
         return out
 
+    def vct_reset_history(self):
+        self._check(self.lib.vct_reset_history(self.ctx), "vct_reset_history")
+
     def vct_ppe_adjoint(self, p_bar):
         """b_bar = A^-T p_bar for the pressure system of the last step (caller
         order, float64 CUDA tensors of the state's length); returns (b_bar, stats)."""
@@ -449,3 +455,49 @@ def vct_batch_step(solvers, states, nsteps=1):
     if rc != VCT_OK:
         raise VCTError(rc, "vct_batch_step")
     return list(stats)
+
+
+class Checkpointer:
+    """Checkpointed forward run for a reverse sweep over steps (the adjoint
+    workload keeps a checkpoint every 20 steps): a copy of the state every
+    `every` steps, and the states of one segment recomputed from its checkpoint
+    on demand.  The context's pressure history is reset at every checkpoint,
+    on the forward run and on the replays alike, so a replay reproduces the
+    forward run's states bit for bit."""
+
+    def __init__(self, solver, every=20):
+        self.solver = solver
+        self.every = int(every)
+        self.snapshots, self.lengths = [], []
+
+    @staticmethod
+    def _copy(state):
+        import copy
+        out = copy.copy(state)
+        for k in DeviceState.FIELDS + ("type",):
+            setattr(out, k, getattr(state, k).clone())
+        return out
+
+    def run(self, state, nsteps):
+        """Advance `state` by nsteps, keeping a checkpoint at every segment start."""
+        self.snapshots, self.lengths = [], []
+        done = 0
+        while done < nsteps:
+            k = min(self.every, nsteps - done)
+            self.snapshots.append(self._copy(state))
+            self.lengths.append(k)
+            self.solver.vct_reset_history()
+            self.solver.vct_step(state, k)
+            done += k
+        return state
+
+    def replay(self, seg):
+        """The states after each step of segment `seg`, recomputed from its
+        checkpoint (a list of DeviceState copies; the checkpoint is kept)."""
+        state = self._copy(self.snapshots[seg])
+        self.solver.vct_reset_history()
+        out = []
+        for _ in range(self.lengths[seg]):
+            self.solver.vct_step(state, 1)
+            out.append(self._copy(state))
+        return out
