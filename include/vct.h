@@ -287,6 +287,21 @@ vct_status sph2_gradient_backward_positions(vct_ctx *ctx, const vct_state *state
 vct_status sph2_d2_backward_positions(vct_ctx *ctx, const vct_state *state, const double *phi,
                                       const double *d2_hat_bar, double *xh_bar);
 
+/* Derivative of the pressure operator's linear part (Eqs. VCT_ppe, lap_VCT:
+ * (A x)_i = c0_i <dx/dz^>_i + c~_i . D_i on the unknown rows, D the SPH(2)
+ * second derivatives of x; x = 0 on free-surface particles, wall neighbours in
+ * the right side) with respect to the projected positions of the current
+ * state: given x and pbar (n, caller order; entries off the unknown rows are
+ * ignored), writes xh_bar (dim x n) = the gradient of pbar . (A x) with respect
+ * to r^, through the same chain as sph2_d2_backward_positions, with neighbour
+ * sets, free-surface flags, volumes and the metric terms c0, c~ held fixed
+ * (exact for maps with a constant metric).  With vct_ppe_adjoint's b_bar as
+ * pbar and the solution p as x it is the pressure solve's position term
+ * -b_bar^T (dA/dr^) p with the sign reversed.  FP64; the same scratch rule and
+ * VCT_ERR_CAPACITY as sph2_d2_backward_positions. */
+vct_status vct_ppe_backward_positions(vct_ctx *ctx, const vct_state *state, const double *x,
+                                      const double *p_bar, double *xh_bar);
+
 /* Derivative through the map with respect to the bathymetry parameters
  * theta = [h0, slope_x, slope_y, cos_amp, cos_len, amp[G], cx[G], cy[G], width[G]]
  * (G = n_gauss; 5 + 4G entries): given per-particle adjoints (DEVICE arrays of n,

@@ -1071,8 +1071,28 @@ VCT_API vct_status sph2_d2_backward_positions(vct_ctx *c, const vct_state *s, co
     reset_status(c);
     launch_load(c->P, cur(c), *s, n, c->st);
     geometry(c, n);
-    launch_d2pos(c->P, cur(c), c->W, n, phi, d2_hat_bar, xh_bar, c->st);
+    launch_d2pos(c->P, cur(c), c->W, n, false, phi, d2_hat_bar, xh_bar, c->st);
     c->launches += 3;
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, nullptr, 0);
+}
+
+VCT_API vct_status vct_ppe_backward_positions(vct_ctx *c, const vct_state *s, const double *x,
+                                              const double *p_bar, double *xh_bar)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (!x || !p_bar || !xh_bar) return VCT_ERR_ARG;
+    const int64_t eg = c->P.dim == 2 ? 4 : 8, need = c->P.dim == 2 ? 30 : 72;
+    const int64_t kb = ((int64_t)c->W.max_nbr + eg - 1) / eg * eg;
+    if ((c->P.precision == VCT_MIXED ? kb / 2 : kb) < need) return VCT_ERR_CAPACITY;
+    const int64_t n = s->n;
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    geometry(c, n);
+    launch_pass1(c->P, cur(c), c->W, n, c->st);   // free-surface flags: the unknown rows
+    launch_d2pos(c->P, cur(c), c->W, n, true, x, p_bar, xh_bar, c->st);
+    c->launches += 4;
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
     return finish(c, nullptr, 0);
 }

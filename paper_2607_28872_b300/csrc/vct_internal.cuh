@@ -177,8 +177,9 @@ bool krylov_mg_fly_default(long long rows, int dim);
 int krylov_fly_batch_blocks(int precision, int dim, size_t smem, bool expl);
 size_t krylov_batch_stage_bytes(int precision, int dim);
 // derivative of the SPH(2) second derivatives with respect to the projected positions
-void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
-                  const double *d2_bar, double *xh_bar, cudaStream_t st);
+// (ppe: the pressure operator's linear part with phi = x and wbar = pbar)
+void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, bool ppe, const double *phi,
+                  const double *wbar, double *xh_bar, cudaStream_t st);
 // derivative of the corrected gradient with respect to the projected positions
 void launch_gradpos(const DevParams &P, Part cur, Work W, int64_t n, int ncomp, const double *phi,
                     const double *grad_bar, double *xh_bar, cudaStream_t st);

@@ -4812,9 +4812,24 @@ __device__ __forceinline__ void qjac_t(const double *r, const double *qb, double
     }
 }
 
+// PPE = false: a field phi, the loss sum d2_bar . d2_hat.  PPE = true: the
+// pressure operator's linear part (A x)_i = c0_i <dx/dz^>_i + c~_i . D_i (Eqs.
+// VCT_ppe, lap_VCT) on the unknown rows, with pair differences x_j - x_i for
+// fluid neighbours (x = 0 off the unknowns) and none for walls (their term is
+// the right side's), the loss sum_i pbar_i (A x)_i; phi = x, wbar = pbar.
 template <int D>
+__device__ __forceinline__ double d2pos_dphi(const Part &c, const Work &W, bool ppe,
+                                             const double *phi, int i, int j)
+{
+    if (!ppe) return phi[c.orig[j]] - phi[c.orig[i]];
+    if (c.type[j] != FLUID) return 0.0;
+    const double xj = W.fs[j] ? 0.0 : phi[c.orig[j]];
+    return xj - phi[c.orig[i]];
+}
+
+template <int D, bool PPE>
 __global__ void __launch_bounds__(128) k_d2pos_a(DevParams P, const Part c, Work W, int n,
-                                                 const double *phi, const double *d2_bar,
+                                                 const double *phi, const double *wbar,
                                                  double *scr)
 {
     constexpr int M = D2Slots<D>::M;
@@ -4826,7 +4841,6 @@ __global__ void __launch_bounds__(128) k_d2pos_a(DevParams P, const Part c, Work
     double xi[3];
     load_hat<D>(c, i, xi);
     const int oi = c.orig[i];
-    const double phii = phi[oi];
     double B[D * D], Gq[D * M], graw[D];
     for (int q = 0; q < D * D; ++q) B[q] = 0.0;
     for (int q = 0; q < D * M; ++q) Gq[q] = 0.0;
@@ -4842,7 +4856,7 @@ __global__ void __launch_bounds__(128) k_d2pos_a(DevParams P, const Part c, Work
         const double rr = sqrt(rr2);
         double w, dw;
         kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
-        const double f = -dw / rr, V = W.vol[j], dphi = phi[c.orig[j]] - phii;
+        const double f = -dw / rr, V = W.vol[j], dphi = d2pos_dphi<D>(c, W, PPE, phi, i, j);
         qvec_d<D>(r, q);
         for (int K = 0; K < D; ++K) {
             const double gk = f * r[K];
@@ -4879,7 +4893,7 @@ __global__ void __launch_bounds__(128) k_d2pos_a(DevParams P, const Part c, Work
         const double rr = sqrt(rr2);
         double w, dw;
         kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
-        const double f = -dw / rr, V = W.vol[j], dphi = phi[c.orig[j]] - phii;
+        const double f = -dw / rr, V = W.vol[j], dphi = d2pos_dphi<D>(c, W, PPE, phi, i, j);
         double rg = 0.0, rgg = 0.0;
         for (int K = 0; K < D; ++K) {
             double s2 = 0.0;
@@ -4908,13 +4922,23 @@ __global__ void __launch_bounds__(128) k_d2pos_a(DevParams P, const Part c, Work
     double x[M], bb[M];
     for (int a = 0; a < M; ++a) x[a] = b[a];
     lu_apply<M, 1>(Mm, piv, x);
-    for (int a = 0; a < M; ++a) {   // xbar = 2 Dbar, the output's cross terms halved
-        const double db = d2_bar[(int64_t)a * n + oi];
-        bb[a] = 2.0 * (a < D ? db : 0.5 * db);
+    double gdir[D];   // the loss's own weight on the corrected gradient
+    for (int K = 0; K < D; ++K) gdir[K] = 0.0;
+    if (PPE) {   // xbar = 2 pbar c~ on D; pbar c0 on the gradient's z^ component
+        const double pb = W.fs[i] ? 0.0 : wbar[oi];
+        double ct[M];
+        ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
+        for (int a = 0; a < M; ++a) bb[a] = 2.0 * pb * ct[a];
+        gdir[D - 1] = pb * c.c0[i];
+    } else {
+        for (int a = 0; a < M; ++a) {   // xbar = 2 Dbar, the output's cross terms halved
+            const double db = wbar[(int64_t)a * n + oi];
+            bb[a] = 2.0 * (a < D ? db : 0.5 * db);
+        }
     }
     lu_apply_t<M>(Mm, piv, bb);
     double gb[D], Cb[D * M], Lb[D * D];
-    for (int K = 0; K < D; ++K) gb[K] = 0.0;
+    for (int K = 0; K < D; ++K) gb[K] = gdir[K];
     for (int q = 0; q < D * M; ++q) Cb[q] = 0.0;
     for (int q = 0; q < D * D; ++q) Lb[q] = 0.0;
     for (int k = 0; k < cnt; ++k) {   // per-i sums of the pair adjoints
@@ -4927,7 +4951,7 @@ __global__ void __launch_bounds__(128) k_d2pos_a(DevParams P, const Part c, Work
         const double rr = sqrt(rr2);
         double w, dw;
         kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
-        const double f = -dw / rr, V = W.vol[j], dphi = phi[c.orig[j]] - phii;
+        const double f = -dw / rr, V = W.vol[j], dphi = d2pos_dphi<D>(c, W, PPE, phi, i, j);
         double rg = 0.0, rgg = 0.0;
         for (int K = 0; K < D; ++K) gw[K] = f * r[K];
         for (int K = 0; K < D; ++K) {
@@ -5067,7 +5091,7 @@ __device__ void d2pos_pair(const DevParams &P, const double *scr, int64_t cap, i
     }
 }
 
-template <int D>
+template <int D, bool PPE>
 __global__ void __launch_bounds__(128) k_d2pos_b(DevParams P, const Part c, Work W, int n,
                                                  const double *phi, const double *scr,
                                                  double *xh_bar)
@@ -5095,14 +5119,13 @@ __global__ void __launch_bounds__(128) k_d2pos_b(DevParams P, const Part c, Work
                 rr2 += r[K] * r[K];
             }
             if (rr2 == 0.0) continue;
-            const double dphi = phi[c.orig[m]] - phi[ok];
             double rb[D];
             if (tk == FLUID) {   // pair (k, m)
-                d2pos_pair<D>(P, scr, cap, k, dphi, r, W.vol[m], rb);
+                d2pos_pair<D>(P, scr, cap, k, d2pos_dphi<D>(c, W, PPE, phi, k, m), r, W.vol[m], rb);
                 for (int K = 0; K < D; ++K) out[K] -= rb[K];
             }
             if (tm == FLUID) {   // pair (m, k)
-                d2pos_pair<D>(P, scr, cap, m, -dphi, rn, W.vol[k], rb);
+                d2pos_pair<D>(P, scr, cap, m, d2pos_dphi<D>(c, W, PPE, phi, m, k), rn, W.vol[k], rb);
                 for (int K = 0; K < D; ++K) out[K] += rb[K];
             }
         }
@@ -5110,19 +5133,29 @@ __global__ void __launch_bounds__(128) k_d2pos_b(DevParams P, const Part c, Work
     for (int K = 0; K < D; ++K) xh_bar[(int64_t)K * n + ok] = out[K];
 }
 
-void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, const double *phi,
-                  const double *d2_bar, double *xh_bar, cudaStream_t st)
+void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, bool ppe, const double *phi,
+                  const double *wbar, double *xh_bar, cudaStream_t st)
 {
     // scratch: the pressure-equation coefficients' storage (>= 32 doubles per
     // particle in 2-D, 80 in 3-D in either form; the next step rebuilds it)
     double *scr = P.precision == VCT_MIXED ? (double *)W.pvalf : W.pval;
     const unsigned g = (unsigned)((n + 127) / 128);
     if (P.dim == 2) {
-        k_d2pos_a<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, d2_bar, scr);
-        k_d2pos_b<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+        if (ppe) {
+            k_d2pos_a<2, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, wbar, scr);
+            k_d2pos_b<2, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+        } else {
+            k_d2pos_a<2, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, wbar, scr);
+            k_d2pos_b<2, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+        }
     } else {
-        k_d2pos_a<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, d2_bar, scr);
-        k_d2pos_b<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+        if (ppe) {
+            k_d2pos_a<3, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, wbar, scr);
+            k_d2pos_b<3, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+        } else {
+            k_d2pos_a<3, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, wbar, scr);
+            k_d2pos_b<3, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, phi, scr, xh_bar);
+        }
     }
 }
 

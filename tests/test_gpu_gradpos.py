@@ -128,3 +128,45 @@ def test_second_derivative_position_gradient_needs_scratch(vct):
         solver.sph2_d2_backward_positions(vct.DeviceState(sc), torch.zeros(sc.n),
                                           torch.zeros((3, sc.n)))
     assert e.value.status == vct.VCT_ERR_CAPACITY
+
+
+@pytest.mark.parametrize("name,make,aspect", CASES, ids=[c[0] for c in CASES])
+def test_pressure_operator_position_gradient_matches_oracle_differences(vct, name, make, aspect):
+    """pbar . (A x) with the oracle's operator (its probe of A x_test), x zero
+    off the unknown rows, free-surface flags and neighbour sets checked
+    unchanged by each step (maps with a constant metric: E)."""
+    import torch
+    sc = make()
+    d, n = sc.dim, sc.n
+    _, info0 = O.step(sc, probe=True, rtol=1e-13)
+    fs0 = info0["fs"]
+    unknown = (sc.type == S.FLUID) & (fs0 == 0)
+    rng = np.random.default_rng(24)
+    x = np.where(unknown, rng.normal(size=n), 0.0)
+    pbar = rng.normal(size=n)
+    solver = vct.Solver(sc)
+    xb = solver.vct_ppe_backward_positions(vct.DeviceState(sc), torch.tensor(x),
+                                           torch.tensor(pbar)).cpu().numpy()
+    assert np.all(xb[:, sc.type == S.VIRTUAL] == 0.0)
+    l, re, re2 = O.radii(sc)
+    xh0, _ = O.projected(sc)
+    row0, col0 = O.neighbours(d, xh0, re, re2, mode=0)
+    eps = 1e-7 * sc.params["d0"]
+    names = ("x", "y", "z") if d == 3 else ("x", "z")
+    picks = list(np.flatnonzero(unknown)[::19][:5]) + list(np.flatnonzero(sc.type == S.WALL)[::13][:3])
+    scale = np.abs(xb).max()
+    for p in picks:
+        for K, nm in enumerate(names):
+            step = eps / aspect if nm == "z" else eps
+            vals = []
+            for sgn in (1.0, -1.0):
+                s2 = sc.copy()
+                getattr(s2, nm)[p] += sgn * step
+                xh, _ = O.projected(s2)
+                row, col = O.neighbours(d, xh, re, re2, mode=0)
+                assert np.array_equal(row, row0) and np.array_equal(col, col0)
+                _, info = O.step(s2, probe=True, x_test=x, rtol=1e-13)
+                assert np.array_equal(info["fs"], fs0)
+                vals.append(np.sum(pbar[unknown] * info["ppe_Ax"][unknown]))
+            fd = (vals[0] - vals[1]) / (2 * eps)
+            assert abs(fd - xb[K, p]) <= 1e-6 * scale, (p, nm, fd, xb[K, p])
