@@ -122,6 +122,8 @@ def run_adjoint(args):
     import torch
     from paper_2607_28872_b300 import scenarios as S
     from paper_2607_28872_b300 import vct
+    if dist_env()[0] != 0:   # one line per job: rank 0's (replicas only)
+        return
     sc = S.adjoint_sigma(precision=args.precision)
     solver = vct.Solver(sc)
     state = vct.DeviceState(sc)
@@ -178,6 +180,8 @@ def run_ensemble(args):
     import torch
     from paper_2607_28872_b300 import scenarios as S
     from paper_2607_28872_b300 import vct
+    if dist_env()[0] != 0:   # one line per job: rank 0's (replicas only)
+        return
     scs = S.ensemble(n_scen=args.ensemble_size, precision=args.precision)
     nf = sum(sc.n_fluid for sc in scs)
     solvers = [vct.Solver(sc) for sc in scs]

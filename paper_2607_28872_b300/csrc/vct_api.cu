@@ -1056,17 +1056,24 @@ VCT_API vct_status sph2_gradient_backward_positions(vct_ctx *c, const vct_state 
     return finish(c, nullptr, 0);
 }
 
+// The second-derivative position adjoints keep per-particle factors and
+// adjoints (30 doubles in 2-D, 72 in 3-D) in the pressure coefficients' storage,
+// roundup(max_neighbours, 4 / 8) slots per particle of doubles (FP64 form) or
+// floats (mixed form).
+static bool d2pos_scratch_fits(const vct_ctx *c)
+{
+    const int64_t eg = c->P.dim == 2 ? 4 : 8, need = c->P.dim == 2 ? 30 : 72;
+    const int64_t kb = ((int64_t)c->W.max_nbr + eg - 1) / eg * eg;
+    return (c->P.precision == VCT_MIXED ? kb / 2 : kb) >= need;
+}
+
 VCT_API vct_status sph2_d2_backward_positions(vct_ctx *c, const vct_state *s, const double *phi,
                                               const double *d2_hat_bar, double *xh_bar)
 {
     vct_status v = check_state(c, s);
     if (v) return v;
     if (!phi || !d2_hat_bar || !xh_bar) return VCT_ERR_ARG;
-    // the per-particle factors and adjoints live in the pressure coefficients'
-    // storage: 30 (2-D) / 72 (3-D) doubles per particle must fit in its slots
-    const int64_t eg = c->P.dim == 2 ? 4 : 8, need = c->P.dim == 2 ? 30 : 72;
-    const int64_t kb = ((int64_t)c->W.max_nbr + eg - 1) / eg * eg;
-    if ((c->P.precision == VCT_MIXED ? kb / 2 : kb) < need) return VCT_ERR_CAPACITY;
+    if (!d2pos_scratch_fits(c)) return VCT_ERR_CAPACITY;
     const int64_t n = s->n;
     reset_status(c);
     launch_load(c->P, cur(c), *s, n, c->st);
@@ -1083,9 +1090,7 @@ VCT_API vct_status vct_ppe_backward_positions(vct_ctx *c, const vct_state *s, co
     vct_status v = check_state(c, s);
     if (v) return v;
     if (!x || !p_bar || !xh_bar) return VCT_ERR_ARG;
-    const int64_t eg = c->P.dim == 2 ? 4 : 8, need = c->P.dim == 2 ? 30 : 72;
-    const int64_t kb = ((int64_t)c->W.max_nbr + eg - 1) / eg * eg;
-    if ((c->P.precision == VCT_MIXED ? kb / 2 : kb) < need) return VCT_ERR_CAPACITY;
+    if (!d2pos_scratch_fits(c)) return VCT_ERR_CAPACITY;
     const int64_t n = s->n;
     reset_status(c);
     launch_load(c->P, cur(c), *s, n, c->st);
