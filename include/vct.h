@@ -302,6 +302,15 @@ vct_status sph2_d2_backward_positions(vct_ctx *ctx, const vct_state *state, cons
 vct_status vct_ppe_backward_positions(vct_ctx *ctx, const vct_state *state, const double *x,
                                       const double *p_bar, double *xh_bar);
 
+/* Derivative of the density estimate rho^_i = rho sum_j V0 w_ij (self term
+ * included; every neighbour type; the <rho^> of the pressure equation's
+ * stabilisation term) with respect to the projected positions of the current
+ * state, neighbour sets fixed: given rho_bar (n, caller order; used on fluid
+ * particles), writes xh_bar (dim x n, caller order) = the gradient of
+ * sum_i rho_bar_i rho^_i with respect to r^.  FP64; deterministic. */
+vct_status vct_rho_backward_positions(vct_ctx *ctx, const vct_state *state, const double *rho_bar,
+                                      double *xh_bar);
+
 /* Derivative through the map with respect to the bathymetry parameters
  * theta = [h0, slope_x, slope_y, cos_amp, cos_len, amp[G], cx[G], cy[G], width[G]]
  * (G = n_gauss; 5 + 4G entries): given per-particle adjoints (DEVICE arrays of n,

@@ -1102,6 +1102,22 @@ VCT_API vct_status vct_ppe_backward_positions(vct_ctx *c, const vct_state *s, co
     return finish(c, nullptr, 0);
 }
 
+VCT_API vct_status vct_rho_backward_positions(vct_ctx *c, const vct_state *s,
+                                              const double *rho_bar, double *xh_bar)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (!rho_bar || !xh_bar) return VCT_ERR_ARG;
+    const int64_t n = s->n;
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    geometry(c, n);
+    launch_rhopos(c->P, cur(c), c->W, n, rho_bar, xh_bar, c->st);
+    c->launches += 1;
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return finish(c, nullptr, 0);
+}
+
 VCT_API vct_status vct_map_backward(vct_ctx *c, const vct_state *s, const double *zh_bar,
                                     const double *J_bar, const double *sx_bar,
                                     const double *sy_bar, const double *c0_bar,

@@ -180,6 +180,9 @@ size_t krylov_batch_stage_bytes(int precision, int dim);
 // (ppe: the pressure operator's linear part with phi = x and wbar = pbar)
 void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, bool ppe, const double *phi,
                   const double *wbar, double *xh_bar, cudaStream_t st);
+// derivative of the density estimate with respect to the projected positions
+void launch_rhopos(const DevParams &P, Part cur, Work W, int64_t n, const double *rho_bar,
+                   double *xh_bar, cudaStream_t st);
 // derivative of the corrected gradient with respect to the projected positions
 void launch_gradpos(const DevParams &P, Part cur, Work W, int64_t n, int ncomp, const double *phi,
                     const double *grad_bar, double *xh_bar, cudaStream_t st);

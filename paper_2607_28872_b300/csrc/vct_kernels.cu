@@ -5159,6 +5159,58 @@ void launch_d2pos(const DevParams &P, Part cur, Work W, int64_t n, bool ppe, con
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// a12 (part): derivative of the density estimate rho^_i = rho (sum_j V0 w_ij +
+// V0 w(0)) (Sec. 4.4.2's <rho^>, over every neighbour type) with respect to the
+// projected positions, neighbour sets fixed: d rho^_i / d r_j = rho V0 w'(rho_ij)
+// r_ij / rho_ij for j != i (r_ij = r_j - r_i) and minus their sum for r_i.  For
+// the loss sum_i rhobar_i rho^_i (fluid i) particle k gathers, over its
+// neighbours m, rho V0 w' r_mk / rho_mk (rhobar_m [m fluid] + rhobar_k [k
+// fluid]).  FP64.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(128) k_rhopos(DevParams P, const Part c, Work W, int n,
+                                                const double *rho_bar, double *xh_bar)
+{
+    if (step_failed(W.status)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t cap = W.cap;
+    const int ok = c.orig[k];
+    const double bk = c.type[k] == FLUID ? rho_bar[ok] : 0.0;
+    double xk[3], out[D];
+    load_hat<D>(c, k, xk);
+    for (int K = 0; K < D; ++K) out[K] = 0.0;
+    const int cnt = W.nbr_cnt[k];
+    for (int q = 0; q < cnt; ++q) {
+        const int m = W.nbr[(int64_t)q * cap + k];
+        const double bm = c.type[m] == FLUID ? rho_bar[c.orig[m]] : 0.0;
+        if (bk == 0.0 && bm == 0.0) continue;
+        double xm[3], r[D], rr2 = 0.0;
+        load_hat<D>(c, m, xm);
+        for (int K = 0; K < D; ++K) {
+            r[K] = xk[K] - xm[K];   // r_mk
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == 0.0) continue;
+        const double rr = sqrt(rr2);
+        double w, dw;
+        kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+        const double s = P.rho * P.V0 * dw / rr * (bm + bk);
+        for (int K = 0; K < D; ++K) out[K] += s * r[K];
+    }
+    for (int K = 0; K < D; ++K) xh_bar[(int64_t)K * n + ok] = out[K];
+}
+
+void launch_rhopos(const DevParams &P, Part cur, Work W, int64_t n, const double *rho_bar,
+                   double *xh_bar, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) k_rhopos<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, rho_bar, xh_bar);
+    else k_rhopos<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, rho_bar, xh_bar);
+}
+
 }  // namespace vct
 
 // ===========================================================================

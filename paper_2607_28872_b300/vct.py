@@ -22,7 +22,7 @@ VCT_MAX_GAUSS = 32
 EXPORTS = ("vct_init", "vct_set_stream", "vct_reset_history", "vct_build_neighbours",
            "vct_build_neighbours_noalloc",
            "sph2_derivatives", "sph2_derivatives_backward", "sph2_gradient_backward_positions",
-           "sph2_d2_backward_positions", "vct_ppe_backward_positions",
+           "sph2_d2_backward_positions", "vct_ppe_backward_positions", "vct_rho_backward_positions",
            "vct_map_backward", "vct_step",
            "vct_batch_step",
            "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling", "vct_stage_times",
@@ -110,6 +110,7 @@ def load_library(path=LIB_PATH):
     L.sph2_gradient_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp]
     L.sph2_d2_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp]
     L.vct_ppe_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp]
+    L.vct_rho_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp]
     L.vct_set_profiling.argtypes = [vp, C.c_int32]
     L.vct_stage_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.vct_last_error.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -120,7 +121,8 @@ def load_library(path=LIB_PATH):
     for name in ("vct_init", "vct_set_stream", "vct_reset_history", "vct_build_neighbours",
                  "sph2_derivatives",
                  "sph2_derivatives_backward", "sph2_gradient_backward_positions",
-                 "sph2_d2_backward_positions", "vct_ppe_backward_positions", "vct_map_backward",
+                 "sph2_d2_backward_positions", "vct_ppe_backward_positions",
+                 "vct_rho_backward_positions", "vct_map_backward",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
@@ -354,6 +356,18 @@ class Solver:
         self._check(self.lib.vct_ppe_backward_positions(
             self.ctx, C.byref(s), C.c_void_p(x.data_ptr()), C.c_void_p(p_bar.data_ptr()),
             C.c_void_p(out.data_ptr())), "vct_ppe_backward_positions")
+        return out
+
+    def vct_rho_backward_positions(self, state, rho_bar):
+        """Gradient of sum rho_bar . rho^ (the density estimate) with respect to
+        the projected positions, (dim, n) float64."""
+        import torch
+        rho_bar = torch.as_tensor(rho_bar, dtype=torch.float64, device="cuda").reshape(state.n).contiguous()
+        out = torch.zeros((self.dim, state.n), dtype=torch.float64, device="cuda")
+        s = state.struct()
+        self._check(self.lib.vct_rho_backward_positions(
+            self.ctx, C.byref(s), C.c_void_p(rho_bar.data_ptr()), C.c_void_p(out.data_ptr())),
+            "vct_rho_backward_positions")
         return out
 
     def vct_ppe_adjoint(self, p_bar):

@@ -170,3 +170,41 @@ def test_pressure_operator_position_gradient_matches_oracle_differences(vct, nam
                 vals.append(np.sum(pbar[unknown] * info["ppe_Ax"][unknown]))
             fd = (vals[0] - vals[1]) / (2 * eps)
             assert abs(fd - xb[K, p]) <= 1e-6 * scale, (p, nm, fd, xb[K, p])
+
+
+@pytest.mark.parametrize("name,make,aspect", CASES, ids=[c[0] for c in CASES])
+def test_density_position_gradient_matches_oracle_differences(vct, name, make, aspect):
+    """rhobar . rho^ with the oracle's density estimate (its probe), neighbour
+    sets checked unchanged by each step."""
+    import torch
+    sc = make()
+    d, n = sc.dim, sc.n
+    rng = np.random.default_rng(25)
+    rbar = rng.normal(size=n)
+    solver = vct.Solver(sc)
+    xb = solver.vct_rho_backward_positions(vct.DeviceState(sc), torch.tensor(rbar)).cpu().numpy()
+    fluid = sc.type == S.FLUID
+    l, re, re2 = O.radii(sc)
+    xh0, _ = O.projected(sc)
+    row0, col0 = O.neighbours(d, xh0, re, re2, mode=0)
+    eps = 1e-7 * sc.params["d0"]
+    names = ("x", "y", "z") if d == 3 else ("x", "z")
+    picks = list(np.flatnonzero(fluid)[::19][:4]) + list(np.flatnonzero(sc.type == S.WALL)[::13][:2]) + \
+        list(np.flatnonzero(sc.type == S.VIRTUAL)[::13][:2])
+    scale = np.abs(xb).max()
+    for p in picks:
+        for K, nm in enumerate(names):
+            step = eps / aspect if nm == "z" else eps
+            vals = []
+            for sgn in (1.0, -1.0):
+                s2 = sc.copy()
+                getattr(s2, nm)[p] += sgn * step
+                xh, _ = O.projected(s2)
+                row, col = O.neighbours(d, xh, re, re2, mode=0)
+                assert np.array_equal(row, row0) and np.array_equal(col, col0)
+                _, info = O.step(s2, probe=True, rtol=1e-13)
+                vals.append(np.sum(rbar[fluid] * info["rho_hat"][fluid]))
+            fd = (vals[0] - vals[1]) / (2 * eps)
+            assert abs(fd - xb[K, p]) <= 1e-6 * scale, (p, nm, fd, xb[K, p])
+    for K in range(d):
+        assert abs(xb[K].sum()) <= 1e-10 * np.abs(xb[K]).sum()
