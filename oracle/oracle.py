@@ -52,7 +52,9 @@ class OrcProbe(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # VCT_ORACLE_LIB names a separately built copy of the oracle (the planted-
+        # mistake tests compile mutated copies and run the pins against them)
+        path = os.environ.get("VCT_ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         L.orc_kernel.argtypes = [C.c_int, C.c_double, C.c_int, dp, dp, dp]

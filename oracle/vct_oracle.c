@@ -160,6 +160,9 @@ static void map_ab(const orc_params *P, const orc_bathy *b, double x, double y, 
     default:
         ab[0] = 1.0;
     }
+    if (P->dim == 2) {   /* a 2-D section (x, z) has no y direction: drop the y derivatives */
+        ab[2] = ab[4] = ab[7] = ab[9] = 0.0;
+    }
 }
 
 /* Per-particle metric: zh = alpha (z + beta), s = (s_x, s_y) the third column of

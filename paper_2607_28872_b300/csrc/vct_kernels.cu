@@ -112,6 +112,9 @@ __device__ void map_metric(const DevParams &P, double x, double y, double z, dou
             }
         }
     }
+    if (P.dim == 2) {  // a 2-D section has no y direction: h, alpha, beta depend on x only
+        ay = ayy = by = byy = 0.0;
+    }
     double zeta = z + b;
     zh = a * zeta;
     J = a;
@@ -4152,6 +4155,9 @@ __device__ void metric_dual(const DevParams &P, double x, double y, double z, in
                 }
             }
         }
+    }
+    if (P.dim == 2) {  // a 2-D section has no y direction
+        ay = Dual(0.0); ayy = Dual(0.0); by = Dual(0.0); byy = Dual(0.0);
     }
     Dual zeta = Dual(z) + b;
     Dual sx = ax * zeta + a * bx, sy = ay * zeta + a * by;
