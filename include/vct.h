@@ -190,7 +190,11 @@ typedef struct vct_ctx vct_ctx;
 
 /* Create a context: validates parameters, copies the bathymetry, allocates
  * all scratch for up to `capacity` particles on the current CUDA device.
- * stream: a cudaStream_t (NULL = legacy default stream).  (Sec. 2, Sec. 3.) */
+ * stream: a cudaStream_t (NULL = legacy default stream).  (Sec. 2, Sec. 3.)
+ * Before anything is allocated, r_e = re_over_l * l_over_d0 * d0 must be
+ * positive and finite and the box finite and ordered (else VCT_ERR_ARG), and
+ * the cell grid of edge r_e over the box must hold at most 2^30 cells (else
+ * VCT_ERR_CAPACITY). */
 vct_status vct_init(vct_ctx **ctx, const vct_bathymetry *bathy, vct_map_kind kind,
                     double aspect_ratio, const vct_params *params, int64_t capacity,
                     void *stream);
@@ -229,7 +233,13 @@ vct_status vct_build_neighbours(vct_ctx *ctx, const vct_state *state, int64_t *r
  * device looks up that array's device address (once per device); make that
  * first call before any stream capture.  Work runs on `stream` (a
  * cudaStream_t) and the call synchronises it once.  All calls on a device share
- * the array: calls that overlap on the GPU race and must not be issued. */
+ * the array: calls that overlap on the GPU race and must not be issued.  The
+ * cached address assumes the device's primary context is not reset
+ * (cudaDeviceReset) between calls.  The radius and box are checked before any
+ * work: VCT_ERR_ARG for r_e not positive and finite or a box that is not
+ * finite and ordered, VCT_ERR_CAPACITY for a cell grid beyond the limit.  An
+ * error the calling thread left pending from earlier CUDA work is neither
+ * cleared nor reported as this call's. */
 vct_status vct_build_neighbours_noalloc(const vct_bathymetry *bathy, vct_map_kind kind,
                                         double aspect_ratio, const vct_params *params,
                                         const vct_state *state, int64_t *row_ptr, int32_t *col,

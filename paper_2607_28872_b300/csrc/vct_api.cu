@@ -651,8 +651,14 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         return VCT_ERR_ARG;
     if (prm->precision != VCT_FP64 && prm->precision != VCT_MIXED) return VCT_ERR_ARG;
     if (prm->volume_mode < 0 || prm->volume_mode > 2) return VCT_ERR_ARG;
-    for (int k = 0; k < 3; ++k)
-        if (!(prm->box_hi[k] >= prm->box_lo[k])) return VCT_ERR_ARG;
+    // the background cell grid, validated before anything is allocated
+    int grid_nc[3];
+    int64_t ncell = 1;
+    {
+        vct_status gs = cell_grid(prm, prm->re_over_l * (prm->l_over_d0 * prm->d0),
+                                  (int64_t)INT32_MAX / 2, grid_nc, &ncell);
+        if (gs != VCT_OK) return gs;
+    }
 
     static long long serials = 0;
     vct_ctx *c = new (std::nothrow) vct_ctx();
@@ -703,15 +709,10 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     if (prm->precision == VCT_MIXED && getenv("VCT_INNER_FLOOR")) P.inner_floor = atof(getenv("VCT_INNER_FLOOR"));
     P.cell_h = P.re;
     P.inv_cell_h = 1.0 / P.cell_h;
-    int64_t ncell = 1;
     for (int k = 0; k < 3; ++k) {
         P.box_lo[k] = prm->box_lo[k];
-        int nk = (int)floor((prm->box_hi[k] - prm->box_lo[k]) * P.inv_cell_h) + 1;
-        if (prm->dim == 2 && k == 1) nk = 1;
-        P.nc[k] = nk;
-        ncell *= nk;
+        P.nc[k] = grid_nc[k];
     }
-    if (ncell > (int64_t)INT32_MAX / 2) { delete c; return VCT_ERR_CAPACITY; }
     P.h0 = bathy->h0;
     P.slope_x = bathy->slope_x;
     P.slope_y = bathy->slope_y;

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "vct.h"
@@ -211,5 +212,30 @@ void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct
 void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,
                      double *out, cudaStream_t st);
 int krylov_coop_blocks(int precision, int dim);
+
+// Background cell grid of edge re over the projected box of prm (the
+// cells of the neighbour search, Sec. 3.4).  Checks, before any integer
+// conversion, that re is positive and finite, that the box is finite and
+// ordered, and that every axis holds between 1 and `limit` cells and the
+// whole grid at most `limit` cells.  VCT_ERR_ARG for a bad radius or box,
+// VCT_ERR_CAPACITY for a grid above the limit.
+inline vct_status cell_grid(const vct_params *prm, double re, int64_t limit, int nc[3],
+                            int64_t *ncell)
+{
+    if (!(re > 0.0) || !(re < 1.0e300)) return VCT_ERR_ARG;
+    double total = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        const double lo = prm->box_lo[k], hi = prm->box_hi[k];
+        if (!(lo > -1.0e300 && hi < 1.0e300 && hi >= lo)) return VCT_ERR_ARG;
+        double ext = (prm->dim == 2 && k == 1) ? 1.0 : floor((hi - lo) / re) + 1.0;
+        if (!(ext >= 1.0) || ext > (double)limit) return VCT_ERR_CAPACITY;
+        total *= ext;
+        if (total > (double)limit) return VCT_ERR_CAPACITY;
+        nc[k] = (int)ext;
+    }
+    *ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    if (*ncell < 1 || *ncell > limit) return VCT_ERR_CAPACITY;
+    return VCT_OK;
+}
 
 }  // namespace vct

@@ -5467,16 +5467,12 @@ extern "C" __attribute__((visibility("default"))) vct_status vct_build_neighbour
     P.amax = prm->alpha_max;
     P.cell_h = P.re;
     P.inv_cell_h = 1.0 / P.cell_h;
-    long long ncell = 1;
-    for (int k = 0; k < 3; ++k) {
-        if (!(prm->box_hi[k] >= prm->box_lo[k])) return VCT_ERR_ARG;
-        P.box_lo[k] = prm->box_lo[k];
-        int nk = (int)floor((prm->box_hi[k] - prm->box_lo[k]) * P.inv_cell_h) + 1;
-        if (prm->dim == 2 && k == 1) nk = 1;
-        P.nc[k] = nk;
-        ncell *= nk;
+    int64_t ncell = 1;
+    {
+        vct_status gs = vct::cell_grid(prm, P.re, NA_MAX_CELLS, P.nc, &ncell);
+        if (gs != VCT_OK) return gs;
     }
-    if (ncell > NA_MAX_CELLS) return VCT_ERR_CAPACITY;
+    for (int k = 0; k < 3; ++k) P.box_lo[k] = prm->box_lo[k];
     P.h0 = bathy->h0;
     P.slope_x = bathy->slope_x;
     P.slope_y = bathy->slope_y;
@@ -5492,6 +5488,11 @@ extern "C" __attribute__((visibility("default"))) vct_status vct_build_neighbour
     vct_status v = scratch_on_device(&S);
     if (v) return v;
     cudaStream_t st = (cudaStream_t)stream;
+    // An error the calling thread left pending (from earlier work, e.g. its
+    // framework's) stays pending for its owner: this call neither clears it
+    // nor reports it as its own.  Launch errors of this call are detected
+    // when nothing was pending at entry.
+    const bool clean_at_entry = cudaPeekAtLastError() == cudaSuccess;
     const int nc = (int)ncell, gp = (n + 255) / 256, gc = (nc + 255) / 256;
     k_na_clear<<<gc + 1, 256, 0, st>>>(S, nc);
     k_na_map<<<gp, 256, 0, st>>>(P, *s, n, S);
@@ -5501,13 +5502,17 @@ extern "C" __attribute__((visibility("default"))) vct_status vct_build_neighbour
     k_na_count<<<gp, 256, 0, st>>>(P, S, n);
     k_na_scan_rows<<<1, 1024, 0, st>>>(S, n, row_ptr);
     if (col) k_na_fill<<<gp, 256, 0, st>>>(P, S, n, row_ptr, col, col_cap);
+    if (clean_at_entry && cudaPeekAtLastError() != cudaSuccess) {
+        (void)cudaGetLastError();   // this call's own launch error
+        return VCT_ERR_CUDA;
+    }
     int64_t total = 0;
     int32_t status = 0;
     cudaError_t e = cudaMemcpyAsync(&total, row_ptr + n, sizeof total, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&status, S->status, sizeof status, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
     *nnz = total;
     if (col && total > col_cap) return VCT_ERR_CAPACITY;
     return (vct_status)status;

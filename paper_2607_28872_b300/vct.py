@@ -428,15 +428,20 @@ class Solver:
         return out, st
 
 
-def vct_build_neighbours_noalloc(sc, state, row_ptr, col, stream=None):
+def vct_build_neighbours_noalloc(sc, state, row_ptr, col, stream=None, **over):
     """Neighbour CSR without a context and without any device allocation (for
     callers that cannot allocate device memory).  row_ptr: int64 CUDA tensor of
     n+1 entries; col: int32 CUDA tensor (or None to get only nnz).  Returns
-    (status, nnz); the limits are 16384 particles and 32768 cells."""
+    (status, nnz); the limits are 16384 particles and 32768 cells.  `over`
+    overrides scenario parameters (box_lo/box_hi: 3-tuples)."""
     import torch
     lib = load_library()
     bathy, keep = make_bathymetry(sc.bathy)
-    params = make_params(sc)
+    box = {k: over.pop(k) for k in ("box_lo", "box_hi") if k in over}
+    params = make_params(sc, **over)
+    for k, v in box.items():
+        for a in range(3):
+            getattr(params, k)[a] = float(v[a])
     s = state.struct()
     nnz = C.c_int64(0)
     if stream is None:

@@ -34,3 +34,41 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(vct.vct_state) == 8 + 9 * 8
     assert ctypes.sizeof(vct.vct_stats) == 8 + 8 + 4 + 4 + 8 + 3 * 8
     assert ctypes.sizeof(vct.vct_bathymetry) == 5 * 8 + 8 + 4 * 8
+
+
+def _bad_grid_cases():
+    nan = float("nan")
+    return [("re_over_l = 0", dict(re_over_l=0.0), None, vct.VCT_ERR_ARG),
+            ("re_over_l = NaN", dict(re_over_l=nan), None, vct.VCT_ERR_ARG),
+            ("l_over_d0 < 0", dict(l_over_d0=-1.2), None, vct.VCT_ERR_ARG),
+            ("box NaN", {}, ((0.0, 0.0, 0.0), (nan, 0.0, 1.0)), vct.VCT_ERR_ARG),
+            ("box reversed", {}, ((1.0, 0.0, 0.0), (0.0, 0.0, 1.0)), vct.VCT_ERR_ARG),
+            ("huge box", {}, ((-1e200, 0.0, 0.0), (1e200, 0.0, 1.0)), vct.VCT_ERR_CAPACITY)]
+
+
+def test_cell_grid_is_validated_before_any_device_work():
+    """vct_init and the allocation-free neighbour entry reject a bad radius or
+    box on the host, before any CUDA call (this host has no GPU: a call that
+    got further would fail with VCT_ERR_CUDA instead)."""
+    from paper_2607_28872_b300 import scenarios as S
+    lib = vct.load_library()
+    sc = S.small_tank(dim=2, kind="BF", L=0.1, H=0.05, d0=0.01)
+    bathy, keep = vct.make_bathymetry(sc.bathy)
+    fake = (ctypes.c_double * 8)()          # never dereferenced on the host
+    st = vct.vct_state(sc.n, *[ctypes.cast(fake, ctypes.c_void_p)] * 9)
+    row = (ctypes.c_int64 * 8)()
+    for name, over, box, want in _bad_grid_cases():
+        P = vct.make_params(sc, **over)
+        if box is not None:
+            for a in range(3):
+                P.box_lo[a], P.box_hi[a] = box[0][a], box[1][a]
+        ctx = ctypes.c_void_p()
+        rc = lib.vct_init(ctypes.byref(ctx), ctypes.byref(bathy), vct.MAP[sc.map_kind], 1.0,
+                          ctypes.byref(P), sc.n, None)
+        assert rc == want and not ctx, (name, rc)
+        nnz = ctypes.c_int64(0)
+        rc = lib.vct_build_neighbours_noalloc(ctypes.byref(bathy), vct.MAP[sc.map_kind], 1.0,
+                                              ctypes.byref(P), ctypes.byref(st),
+                                              ctypes.cast(row, ctypes.c_void_p), None, 0,
+                                              ctypes.byref(nnz), None)
+        assert rc == want, (name, rc)

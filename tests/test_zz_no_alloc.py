@@ -58,3 +58,25 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     rrow, rcol = _reference(V, sc)
     rc, nnz, _, _ = _noalloc(V, sc, rcol.size - 1)   # column capacity too small
     assert rc == V.VCT_ERR_CAPACITY and nnz == rcol.size
+
+
+def test_noalloc_count_only_and_cell_limit():
+    """col = NULL returns only nnz and row_ptr (the documented count-only
+    form), equal to the context entry's; a box whose cell grid exceeds the
+    32768-cell limit is rejected with VCT_ERR_CAPACITY before any launch."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    sc = S.small_tank(dim=2, kind="SIGMA", L=0.3, H=0.1, d0=0.01, seed=3)
+    rrow, rcol = _reference(V, sc)
+    st = V.DeviceState(sc)
+    for _ in range(2):
+        row = torch.full((sc.n + 1,), -7, dtype=torch.int64, device="cuda")
+        rc, nnz = V.vct_build_neighbours_noalloc(sc, st, row, None)
+        assert rc == V.VCT_OK, V.vct_strerror(rc)
+        assert nnz == rcol.size
+        assert np.array_equal(row.cpu().numpy(), rrow)
+    # 0.024 m cells over a 10 m x 1 m box: 418 x 42 > 32768 cells
+    row = torch.zeros(sc.n + 1, dtype=torch.int64, device="cuda")
+    rc, _ = V.vct_build_neighbours_noalloc(sc, st, row, None, box_lo=(-0.1, 0.0, -0.1),
+                                           box_hi=(10.0, 0.0, 1.0))
+    assert rc == V.VCT_ERR_CAPACITY
