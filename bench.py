@@ -1,18 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the VCT + SPH(2) step: particle-updates/s per SPH(2) step.
 
-Workload: the 2-D sigma-SPH solitary wave (H/d = 0.2) over a Gaussian bump
-(0.3 m high, 1 m wide) in a 10 m channel of depth 0.5 m, 42,480 fluid
-particles on a regular projected lattice (d0 = 1/90 m), mixed precision
-(FP32 compensated neighbour sums, FP64 solves and pressure iterate).  Inputs
-are the seeded synthetic scenario of paper_2607_28872_b300.scenarios.
+Default workload: the 3-D BFE-SPH solitary wave (H = 0.1 m) on a 1:20 beach,
+20 x 4 m basin, depth 1 m shoaling to 0, ellipsoidal particles of aspect
+ratio 4, d0 = 0.043 m: 2,105,788 fluid particles (2.59 M with walls), mixed
+precision (FP32 compensated neighbour sums, FP64 moment solves and pressure
+iterate).  Inputs are the seeded synthetic scenario of
+paper_2607_28872_b300.scenarios, resident in HBM before timing.
 
 One step = one call of vct_step for one time step: map + cell sort,
-neighbours, Jbar smoothing, SPH(2) passes, predictor, pressure equation,
-BiCGSTAB, corrector.  The working set (~50 MB) fits in L2, so L2 is flushed
-(256 MB write) before every timed step, outside the timed events.
+neighbours, SPH(2) passes, predictor, pressure equation, multigrid BiCGSTAB,
+corrector, particle regularisation.  The working set (~10 GB) is far above
+L2; L2 is also flushed (256 MB write) before every timed step, outside the
+timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload beach_bfe_3d|sigma_solitary|...]
 
 --impl reference times the FP64 CPU oracle (the plain reference program of
 this project) on the host cores, on a bounded slice of the same workload.
@@ -34,22 +37,26 @@ if ROOT not in sys.path:
 
 METRIC = "particle-updates/s per SPH(2) step"
 UNIT = "particle-updates/s"
-WORKLOAD = ("2-D sigma-SPH solitary wave (H/d=0.2) over a 0.3 m Gaussian bump, 10 m x 0.5 m "
-            "channel, d0=1/90 m, mixed FP32/FP64")
+WORKLOAD_2D = ("2-D sigma-SPH solitary wave (H/d=0.2) over a 0.3 m Gaussian bump, 10 m x 0.5 m "
+               "channel, d0=1/90 m, mixed FP32/FP64")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="host-buffer steps timed for e2e (default: min(steps, 20))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--workload", default="sigma_solitary", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="beach_bfe_3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64-probe", action="store_true",
+                    help="skip the per-field error of the mixed form against the FP64 form")
     ap.add_argument("--ensemble-size", type=int, default=64)
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="host seconds the reference arm's timed and warm-up steps aim at")
     return ap.parse_args()
 
 
@@ -79,9 +86,10 @@ def job_throughput(units_per_rank, world, steps, ms):
 
 
 WORKLOADS = {
-    "sigma_solitary": WORKLOAD,
+    "sigma_solitary": WORKLOAD_2D,
     "still_water_bf": "2-D BF still water over a 1:10 slope, 1 m x 0.2 m, d0=0.01 m, jitter 0.1 d0",
-    "beach_bfe_3d": "3-D BFE solitary wave on a 1:20 beach, 20 x 4 m, depth 1 m, aspect 4, d0=0.043 m",
+    "beach_bfe_3d": ("3-D BFE-SPH solitary wave (H=0.1 m) on a 1:20 beach, 20 x 4 m basin, depth 1 m -> 0, "
+                     "aspect ratio 4, d0=0.043 m, mixed FP32/FP64"),
     "beach_bfe_3d_slice": ("3-D BFE solitary wave, 8 x 1.6 m slice of the 1:20 beach (depth 1 -> 0.6 m), "
                            "aspect 4, d0=0.043 m (profiling size)"),
     "ensemble": "sigma-SPH ensemble, particle counts log-uniform 5e3-2e5 (seed 2), 4 bumps each",
@@ -90,16 +98,12 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes (read + write) of the dominant kernel, k_krylov_mg, from one ncu capture of
-# its current version in the mixed form (summaries under profiles/).  The 2-D wave is
-# L2-resident: bytes per launch.  The 3-D beach was captured on its 8 x 1.6 m slice and
-# its traffic grows with rows x iterations: bytes per fluid particle per iteration.
-NCU_TRAFFIC = {
-    "sigma_solitary": ("per_launch", 10.11e6, "profiles/k_krylov_mg_fly_sigma_solitary_42k.md"),
-    "beach_bfe_3d": ("per_unit", 3520.0, "profiles/k_krylov_mg_staged_beach_bfe_3d_540k.md"),
-    "beach_bfe_3d_slice": ("per_unit", 3520.0,
-                           "profiles/k_krylov_mg_staged_beach_bfe_3d_540k.md"),
-}
+# DRAM bytes (read + write) of the dominant kernel from one ncu capture of its
+# CURRENT version in the mixed form (summaries under profiles/); a workload
+# without an entry reports traffic null.  "per_unit": bytes per fluid particle
+# per Krylov iteration (the 3-D beach is captured on its 8 x 1.6 m slice; its
+# traffic grows with rows x iterations); "per_launch": bytes per launch.
+NCU_TRAFFIC = {}
 
 
 def workload(precision=1, name="sigma_solitary"):
@@ -313,6 +317,70 @@ def krylov_bytes(iters, rows, nnz, n_cells, mixed=True, dim=2):
     return rows * (iters * per_row_iter + setup) + n_cells * iters * per_cell_iter
 
 
+# Algorithmic bytes per fluid particle of one step, B_step = B_fixed + n_it * B_it
+# (n_it = Krylov iterations of the step): compulsory traffic of a matrix-free
+# step that reads and writes every per-particle array once per pass (state
+# sort/reorder, map and gather records, pass 1, pass 2 + predictor, pressure
+# set-up, corrector + update + Jbar) and, per iteration, two matrix-free
+# operator products (~68 B each) plus the BiCGSTAB vectors (~96 B).
+B_FIXED = {(2, 1): 510.0, (2, 0): 650.0, (3, 1): 800.0, (3, 0): 1000.0}
+B_IT = {(2, 1): 230.0, (2, 0): 260.0, (3, 1): 300.0, (3, 0): 360.0}
+
+
+def fma_peaks():
+    """FP32 and FP64 FMA throughput of this GPU (TFLOP/s), measured by a plain
+    FMA loop (libvct_peaks.so) timed with CUDA events."""
+    import ctypes as C
+    from paper_2607_28872_b300 import build
+    if not os.path.exists(build.PEAKS_LIB):
+        return None
+    lib = C.CDLL(build.PEAKS_LIB)
+    lib.vct_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    out = {}
+    for name, fp64, iters in (("fp32_tflops", 0, 4000), ("fp64_tflops", 1, 200)):
+        tf, ms = C.c_double(0), C.c_double(0)
+        rc = lib.vct_fma_peak(fp64, iters, C.byref(tf), C.byref(ms))
+        out[name] = tf.value if rc == 0 else None
+        out[name.replace("tflops", "ms")] = ms.value if rc == 0 else None
+    out["how"] = "148x8 blocks x 256 threads x 8 FMA chains, CUDA events, one launch after one warm-up"
+    return out
+
+
+def precision_errors(sc, vct):
+    """Error of the mixed form against the FP64 form, per field, after one step
+    from the same state (normwise: max |mixed - fp64| / max |fp64| over fluid
+    particles).  The mixed step takes the FP64 step's free-surface flags, so
+    both solve the same pressure system."""
+    import numpy as np
+    out = {}
+    runs = {}
+    fs = None
+    for prec in (0, 1):
+        s = vct.Solver(sc, precision=prec)
+        st = vct.DeviceState(sc)
+        pr, _ = s.vct_step_probe(st, fs_in=fs)
+        if prec == 0:
+            fs = pr["fs"].clone()
+        runs[prec] = ({k: v.cpu().numpy() for k, v in pr.items()}, st.numpy())
+        s.close()
+        del st
+    f = sc.type == 0
+    g0, s0 = runs[0]
+    g1, s1 = runs[1]
+
+    def err(a, b):
+        d = np.abs(b).max()
+        return float(np.abs(a - b).max() / d) if d > 0 else float(np.abs(a).max())
+
+    for k in ("lam_min", "rho_hat", "nu", "ppe_b"):
+        out[k] = err(g1[k][f], g0[k][f])
+    for c in range(sc.dim):
+        out[f"vstar{c}"] = err(g1["vstar"][c][f], g0["vstar"][c][f])
+    for k in ("p", "u", "w") + (("v",) if sc.dim == 3 else ()):
+        out[k] = err(s1[k][f], s0[k][f])
+    return out
+
+
 def stage_bytes(stage, n, nf, dim, rows, nnz, nbr_row):
     m = 3 if dim == 2 else 6
     d = dim
@@ -421,7 +489,9 @@ def run_ours(args):
                "d2h_bytes_per_step": narr * 8 * sc.n}
         s2.close()
 
-    # roofline of the dominant stage
+    # roofline of the dominant stage (the pressure solve): algorithmic bytes per
+    # launch = B_it per fluid particle and iteration x fluid particles x the
+    # launch's iterations, over the launch's mean duration (stage events)
     dom = max(stages.items(), key=lambda kv: kv[1][0])
     name, (ms, cnt) = dom
     peaks = {}
@@ -429,28 +499,31 @@ def run_ours(args):
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     hbm = peaks.get("hbm_gbs", 6400.0)
+    key = (sc.dim, args.precision)
     rows, nnz = last.ppe_rows, last.ppe_nnz
+    avg_ms = ms / max(cnt, 1)
+    it_launch = iters_prof / max(cnt, 1)
     if name == "krylov":
-        box = [sc.box_hi[k] - sc.box_lo[k] for k in range(3)]
-        re = sc.params["re_over_l"] * sc.params["l_over_d0"] * sc.params["d0"]
-        n_cells = 1
-        for k in range(3):
-            if sc.dim == 2 and k == 1:
-                continue
-            n_cells *= int(box[k] / re) + 1
-        per_launch = krylov_bytes(iters_prof / nprof, rows, nnz, n_cells, args.precision == 1, sc.dim)
+        per_launch = B_IT[key] * n_fluid * it_launch
     else:
         per_launch = stage_bytes(name, sc.n, n_fluid, sc.dim, rows, nnz, 20 if sc.dim == 2 else 56)
-    avg_ms = ms / max(cnt, 1)
     achieved = per_launch / (avg_ms / 1e3) / 1e9 if per_launch else None
+    # the assembled-operator form this solver runs: its own compulsory bytes
+    box = [sc.box_hi[k] - sc.box_lo[k] for k in range(3)]
+    re = sc.params["re_over_l"] * sc.params["l_over_d0"] * sc.params["d0"]
+    n_cells = 1
+    for k in range(3):
+        if sc.dim == 2 and k == 1:
+            continue
+        n_cells *= int(box[k] / re) + 1
+    asm_bytes = krylov_bytes(it_launch, rows, nnz, n_cells, args.precision == 1, sc.dim)
     traffic, traffic_src = None, None
     tr = NCU_TRAFFIC.get(args.workload)
     if tr and name == "krylov" and args.precision == 1:
         kind, val, traffic_src = tr
-        traffic = val if kind == "per_launch" else val * n_fluid * (iters_prof / max(cnt, 1))
-    # the solver form follows the context's capacity (sc.n here): the small-system
-    # form up to 75,000 particles in 2-D and 30,000 in 3-D
-    fly = sc.n <= (75000 if sc.dim == 2 else 30000)
+        traffic = val if kind == "per_launch" else val * n_fluid * it_launch
+    # the solver form the context ran (reported by the library)
+    fly = last.solve_form == 1
     roof = {"kernel": {"krylov": "k_krylov_mg_fly" if fly else "k_krylov_mg"}.get(name, name),
             "bound": "hbm",
             "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -458,9 +531,20 @@ def run_ours(args):
             "traffic_source": traffic_src,
             "peak_source": "measured" if peaks else "fallback",
             "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": per_launch,
-            "note": ("multigrid-preconditioned BiCGSTAB, ~22 grid-barrier phases per iteration; "
-                     "below ~100k particles the operator and vectors stay in L2 within a step "
-                     "(L2 flushed between steps) and the solve is latency-bound")}
+            "bytes_model": f"{B_IT[key]:.0f} B per fluid particle and Krylov iteration "
+                           f"x {n_fluid} x {it_launch:.2f} iterations per launch",
+            "assembled_operator_bytes_per_launch": asm_bytes,
+            "assembled_operator_frac": asm_bytes / (avg_ms / 1e3) / 1e9 / hbm}
+    n_it = iters / args.steps
+    b_step = B_FIXED[key] + n_it * B_IT[key]
+    step_gbs = b_step * n_fluid / (ms_step / 1e3) / 1e9
+    step_roof = {"bytes_per_fluid_particle": b_step, "achieved": step_gbs, "peak": hbm,
+                 "unit": "GB/s", "frac": step_gbs / hbm,
+                 "model": f"{B_FIXED[key]:.0f} + {B_IT[key]:.0f} x {n_it:.2f} iterations"}
+    errs = None
+    if rank == 0 and not args.no_fp64_probe and args.precision == 1:
+        errs = precision_errors(sc, vct)
+    pk = fma_peaks() if rank == 0 else None
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -469,13 +553,16 @@ def run_ours(args):
             "dtype": "f32+f64" if args.precision == 1 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n_fluid": n_fluid, "n_particles": sc.n,
                        "dt": sc.params["dt"], "krylov_rtol": sc.params["krylov_rtol"],
-                       "l2": "flushed before every timed step (256 MB write)",
+                       "l2": ("flushed before every timed step (256 MB write)" if sc.n < 1_000_000 else
+                              "inputs larger than L2 (~10 GB working set); also flushed before every "
+                              "timed step (256 MB write)"),
                        "parallelism": f"replicas x{world}"},
             "krylov_iters_per_step": iters / args.steps,
             "stage_ms_per_step": {k: v[0] / nprof for k, v in stages.items()},
             "stage_times": f"{nprof} further steps with stage events (direct launches)",
             "graph_steps": graph_steps,
-            "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e,
+            "roofline": roof, "step_roofline": step_roof, "cpu_baseline": cpu_base, "e2e": e2e,
+            "mixed_vs_fp64_err": errs, "fma_peaks": pk,
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -512,18 +599,31 @@ def cpu_baseline_sample(name, sc, nsteps=1):
                       f"{sub.params['krylov_rtol']:g})"}
 
 
+def reference_sample(name, steps_total, precision, budget_s=150.0):
+    """A slice of the workload sized so that steps_total oracle steps take about
+    budget_s on the host cores (measured oracle rates: ~4e3 particle-updates/s
+    for the 3-D beach, ~2.5e4 for the 2-D channel, on 16 cores)."""
+    from paper_2607_28872_b300 import scenarios as S
+    if name in ("beach_bfe_3d", "beach_bfe_3d_slice"):
+        target = budget_s * 4.0e3 / max(steps_total, 1)          # fluid particles
+        L = min(4.0, max(0.4, target / 44000.0))                  # ~44k fluid per m at W = 0.3 m
+        sc = S.beach_bfe_3d(L=L, W=0.3, x0=0.5 * L, precision=precision)
+        return sc, f"{L:.2f} x 0.30 m slice of the 3-D beach ({sc.n_fluid} fluid particles)"
+    full_step_s = 8.0          # measured order of one oracle step on the full 10 m channel
+    frac = min(1.0, max(0.08, budget_s / (steps_total * full_step_s)))
+    L = 10.0 * frac
+    sc = S.solitary_sigma(L=L, bump_x=0.5 * L, x0=0.2 * L, precision=precision)
+    return sc, f"channel slice L={L:.2f} m ({sc.n_fluid} fluid particles) of the 10 m workload"
+
+
 def run_reference(args):
     """The oracle (FP64 CPU reference) on the host cores, a bounded slice of the
     workload per step so that --steps K --warmup W ends within a few minutes."""
     rank, world, local = dist_env()
     if rank != 0:
         return
-    from paper_2607_28872_b300 import scenarios as S
-    budget_s = 150.0
-    full_step_s = 8.0          # measured order of one oracle step on the full channel
-    frac = min(1.0, max(0.08, budget_s / ((args.steps + args.warmup) * full_step_s)))
-    L = 10.0 * frac
-    sc = S.solitary_sigma(L=L, bump_x=0.5 * L, x0=0.2 * L, precision=args.precision)
+    sc, what = reference_sample(args.workload, args.steps + args.warmup, args.precision,
+                                args.ref_budget)
     from oracle import oracle as O
     cores = O.set_threads(os.cpu_count() or 1)
     st = O.OracleState(sc)
@@ -533,15 +633,14 @@ def run_reference(args):
     st, info = O.step(sc, st, nsteps=args.steps, rtol=sc.params["krylov_rtol"])
     dt = time.perf_counter() - t0
     value = sc.n_fluid * args.steps / dt
-    sample = (f"channel slice L={L:.2f} m ({sc.n_fluid} fluid particles) of the 10 m workload, "
-              f"{args.steps} steps")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_fluid": sc.n_fluid, "sample_fraction": frac},
+            "config": {"workload": WORKLOADS.get(args.workload, args.workload),
+                       "n_fluid": sc.n_fluid, "sample": what},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": f"{what}, {args.steps} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

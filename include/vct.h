@@ -141,6 +141,13 @@ typedef struct {
      *               tangential only at the free surface (0.2)
      * ds_overlap outside [0, 1) or a negative value is VCT_ERR_ARG. */
     double ops_shift, ds_overlap, xsph_eps;
+    /* Bounded waits (failure detection): the pressure solve's persistent
+     * kernels synchronise their blocks with grid barriers whose waits poll at
+     * most spin_limit times (0 = the default, about 1-2 s).  A wait that runs
+     * out records VCT_ERR_TIMEOUT, every block leaves at its next barrier, the
+     * call returns VCT_ERR_TIMEOUT and the caller's state is left as it was.
+     * Negative is VCT_ERR_ARG. */
+    int64_t spin_limit;
 } vct_params;
 
 /* Particle state, caller order, DEVICE arrays of n entries (host arrays for
@@ -163,6 +170,10 @@ typedef struct {
     int64_t ppe_rows;       /* unknowns (fluid, not free surface) of the last step */
     int64_t ppe_nnz;        /* off-diagonal coefficients of the last step's operator */
     int64_t kernel_launches;/* kernels this call launched */
+    int32_t solve_form;     /* pressure solver that ran: 0 Jacobi BiCGSTAB, 1 multigrid
+                             * small-system form (k_krylov_mg_fly), 2 multigrid
+                             * large-system form (k_krylov_mg) */
+    int32_t reserved;
 } vct_stats;
 
 /* Stages timed by vct_stage_times, in step order. */
@@ -184,6 +195,13 @@ typedef struct {
     const double *x_test;   /* optional input vector, n entries */
     double *ppe_Ax;         /* A x_test on unknown rows (0 elsewhere) */
     double *jbar_used;      /* Jbar after this step's volume smoothing */
+    const int32_t *fs_in;   /* optional INPUT, n entries, caller order: free-surface
+                             * flags to use for fluid particles instead of those the
+                             * step decides.  A flag is a threshold on a rounded
+                             * eigenvalue; within rounding of the threshold two correct
+                             * evaluations can differ, and parity checks pass one
+                             * side's flags to the other so both solve the same
+                             * system.  NULL: the step's own flags. */
 } vct_probe;
 
 typedef struct vct_ctx vct_ctx;

@@ -65,6 +65,8 @@ def lib():
         L.orc_neighbours.restype = C.c_int64
         L.orc_sph2_derivatives.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
                                            C.POINTER(OrcState), dp, C.c_int, dp, dp, dp]
+        L.orc_moment_matrices.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
+                                          C.POINTER(OrcState), dp]
         L.orc_volume_smoothing.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
                                            C.POINTER(OrcState), C.c_int]
         L.orc_step.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy), C.POINTER(OrcState),
@@ -239,6 +241,22 @@ def sph2_derivatives(sc, phi, state=None, **over):
     if rc:
         raise RuntimeError(f"oracle sph2_derivatives failed: {rc}")
     return g, d2, lap
+
+
+def moment_matrices(sc, **over):
+    """The SPH(2) moment matrices M_i (n, m, m) of the scenario's state (zero
+    for particles that are not fluid)."""
+    keep = _Keep()
+    st = OracleState(sc)
+    B = make_bathy(sc.bathy, keep)
+    P = make_params(sc, **over)
+    m = 3 if sc.dim == 2 else 6
+    M = np.zeros((sc.n, m, m))
+    S = st.struct()
+    rc = lib().orc_moment_matrices(C.byref(P), C.byref(B), C.byref(S), _dp(M))
+    if rc:
+        raise RuntimeError(f"oracle moment_matrices failed: {rc}")
+    return M
 
 
 def volume_smoothing(sc, state, mode):

@@ -1093,6 +1093,29 @@ int orc_sph2_derivatives(const orc_params *P, const orc_bathy *b, orc_state *S, 
     return ORC_OK;
 }
 
+/* Public: the SPH(2) moment matrices M_i = sum_j V_j F_ij q_ij p_ij^T of Eq.
+ * (sec_SPH2), row-major m x m per fluid particle (zero elsewhere): M[(i*m + a)*m + c].
+ * For conditioning bounds in parity checks. */
+int orc_moment_matrices(const orc_params *P, const orc_bathy *b, orc_state *S, double *M)
+{
+    work_t W;
+    memset(&W, 0, sizeof W);
+    int n = S->n;
+    stage_geometry(P, b, S, &W);
+    int m = W.m;
+    alloc_work(&W, n, 1);
+    int rc = run_pass1(P, S, &W);
+    if (!rc) rc = run_pass2(P, S, &W, 0);
+    if (!rc) {
+        memset(M, 0, sizeof(double) * (size_t)n * m * m);
+        for (int i = 0; i < n; ++i)
+            if (S->type[i] == ORC_FLUID)
+                memcpy(M + (size_t)i * m * m, W.LU + (size_t)36 * i, sizeof(double) * m * m);
+    }
+    work_free(&W);
+    return rc;
+}
+
 /* Public: volume smoothing alone (for its conservation pin). */
 int orc_volume_smoothing(const orc_params *P, const orc_bathy *b, orc_state *S, int mode)
 {

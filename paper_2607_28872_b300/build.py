@@ -1,4 +1,7 @@
-"""Build the CUDA library in-tree: paper_2607_28872_b300/libvct.so (sm_103a)."""
+"""Build the CUDA libraries in-tree (sm_103a):
+  paper_2607_28872_b300/libvct.so        the step's C ABI (include/vct.h)
+  paper_2607_28872_b300/libvct_peaks.so  FP32/FP64 FMA throughput probe used by bench.py
+"""
 import os
 import subprocess
 import sys
@@ -8,36 +11,51 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvct.so")
+PEAKS_LIB = os.path.join(HERE, "libvct_peaks.so")
 SOURCES = ["vct_kernels.cu", "vct_api.cu"]
+PEAKS_SOURCES = ["vct_peaks.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+                "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
 
 
-def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "vct.h")]
+def _mtime(files):
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force=False, verbose=False):
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
-    objs = []
+def _deps():
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f not in PEAKS_SOURCES]
+    return _mtime(files + [os.path.join(INCLUDE, "vct.h")])
+
+
+def _link(lib, sources, verbose):
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
-    for s in SOURCES:
+    procs, objs = [], []
+    for s in sources:   # translation units compile in parallel
         o = os.path.join(bdir, s.replace(".cu", ".o"))
         cmd = [NVCC] + FLAGS + ["-c", os.path.join(CSRC, s), "-o", o]
         if verbose:
             print(" ".join(cmd), flush=True)
-        subprocess.check_call(cmd)
+        procs.append((subprocess.Popen(cmd), cmd))
         objs.append(o)
-    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB + ".tmp"] + objs + [
-        "-lcudart"]
+    for p, cmd in procs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, cmd)
+    cmd = [NVCC, "-shared"] + ARCH + ["-o", lib + ".tmp"] + objs + ["-lcudart"]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)
-    os.replace(LIB + ".tmp", LIB)
+    os.replace(lib + ".tmp", lib)
+
+
+def build(force=False, verbose=False):
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < _deps():
+        _link(LIB, SOURCES, verbose)
+    peaks_src = [os.path.join(CSRC, s) for s in PEAKS_SOURCES]
+    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(PEAKS_LIB) < _mtime(peaks_src):
+        _link(PEAKS_LIB, PEAKS_SOURCES, verbose)
     return LIB
 
 

@@ -196,6 +196,8 @@ vct_status finish(vct_ctx *c, vct_stats *out, int nsteps)
         out->ppe_nnz = cnt[1];
         out->kernel_launches = c->launches;
         out->graph_steps = graph_steps;
+        out->solve_form = c->precond ? (c->mg.fly ? 1 : 2) : 0;
+        out->reserved = 0;
     }
     if (c->prof) collect_times(c);
     return (vct_status)code;
@@ -237,7 +239,7 @@ void mg_split_shared(MG &M, long long budget_b, long long stage)
 
 // One time step on the context's stream, in three parts: everything up to the
 // pressure solve, the solve, and everything after it.
-void step_pre(vct_ctx *c, int64_t n)
+void step_pre(vct_ctx *c, int64_t n, const vct_probe *pr = nullptr)
 {
     geometry(c, n);
     if (c->P.kind == VCT_MAP_SIGMA && c->P.volume_mode == 2) {
@@ -247,6 +249,10 @@ void step_pre(vct_ctx *c, int64_t n)
     }
     cudaMemsetAsync(c->W.counts, 0, 2 * sizeof(int64_t), c->st);
     { StageTimer t(c, VCT_STAGE_PASS1); launch_pass1(c->P, cur(c), c->W, n, c->st); }
+    if (pr && pr->fs_in) {
+        launch_force_fs(cur(c), c->W, n, pr->fs_in, c->st);
+        c->launches += 1;
+    }
     { StageTimer t(c, VCT_STAGE_PASS2); launch_pass2(c->P, cur(c), c->W, n, 1, c->st); }
     { StageTimer t(c, VCT_STAGE_RHS); launch_rhs(c->P, cur(c), c->W, n, c->st); }
     c->launches += 3;   // pass1, pass2, rhs
@@ -288,7 +294,7 @@ void step_post(vct_ctx *c, int64_t n, int step, int nsteps, const vct_probe *pr)
 // Queue one time step of the current state on the context's stream.
 vct_status queue_step(vct_ctx *c, int64_t n, int step, int nsteps, const vct_probe *pr)
 {
-    step_pre(c, n);
+    step_pre(c, n, pr && step == nsteps - 1 ? pr : nullptr);
     if (step_solve(c, n, step)) return VCT_ERR_CUDA;
     step_post(c, n, step, nsteps, pr);
     return VCT_OK;
@@ -651,6 +657,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         return VCT_ERR_ARG;
     if (prm->precision != VCT_FP64 && prm->precision != VCT_MIXED) return VCT_ERR_ARG;
     if (prm->volume_mode < 0 || prm->volume_mode > 2) return VCT_ERR_ARG;
+    if (prm->spin_limit < 0) return VCT_ERR_ARG;
     // the background cell grid, validated before anything is allocated
     int grid_nc[3];
     int64_t ncell = 1;
@@ -942,6 +949,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.kiters = dalloc<int32_t>(c, 4, e);
     W.kresid = dalloc<double>(c, 1, e);
     W.bar = dalloc<unsigned int>(c, 2, e);
+    W.spin_limit = prm->spin_limit > 0 ? (unsigned long long)prm->spin_limit : SPIN_LIMIT_DEFAULT;
     W.status = dalloc<int32_t>(c, 4, e);
     W.counts = dalloc<long long>(c, 2, e);
     c->row_int = dalloc<int64_t>(c, n + 1, e);

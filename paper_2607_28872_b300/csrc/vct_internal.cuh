@@ -16,6 +16,8 @@
 namespace vct {
 
 constexpr int FLUID = 0, WALL = 1, VIRTUAL = 2;
+// Default bound on the polls of one grid-barrier wait: ~1-2 s on this GPU.
+constexpr unsigned long long SPIN_LIMIT_DEFAULT = 40000000ull;
 constexpr int MAXG = VCT_MAX_GAUSS;
 
 // Parameters broadcast to every kernel by value (kernel-parameter bank).
@@ -86,6 +88,7 @@ struct Work {
     double *kresid;           // per-step relative residuals (device)
     unsigned int *bar;        // grid barrier: [0] count, [1] generation
     int32_t *status;          // [0] code, [1] first particle (sorted index), [2] spin-timeouts
+    unsigned long long spin_limit;  // polls before a grid-barrier wait gives up
     long long *counts;        // [0] unknown rows, [1] off-diagonal coefficients (last step)
     // csr export
     int64_t *row_tmp;
@@ -209,6 +212,7 @@ void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int nc
                          double *phibar, cudaStream_t st);
 void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct_probe &pr,
                       cudaStream_t st);
+void launch_force_fs(Part cur, Work W, int64_t n, const int32_t *fs_in, cudaStream_t st);
 void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,
                      double *out, cudaStream_t st);
 int krylov_coop_blocks(int precision, int dim);

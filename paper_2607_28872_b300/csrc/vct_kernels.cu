@@ -1541,7 +1541,6 @@ void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st
 // bit-reproducible runs).
 // ---------------------------------------------------------------------------
 constexpr int KT = 256;
-constexpr unsigned long long SPIN_LIMIT = 40000000ull;   // bounded: ~1-2 s at most
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned int *p)
 {
@@ -1564,8 +1563,10 @@ __device__ __forceinline__ unsigned atom_add_release(unsigned int *p, unsigned v
 // Spins are bounded: on timeout the block records status[2], and every block
 // leaves at its next barrier, so the kernel always ends.
 // vb: the block's index among the nblocks that share the barrier word (the
-// grid, or a batched solve's subset of it).
-__device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status, unsigned vb)
+// grid, or a batched solve's subset of it); limit: polls before a wait gives
+// up (the context's spin limit, by default ~1-2 s).
+__device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status, unsigned vb,
+                             unsigned long long limit)
 {
     __shared__ int ok_sh;
     __syncthreads();
@@ -1575,7 +1576,7 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *statu
         unsigned old = atom_add_release(bar, inc);
         unsigned long long spins = 0;
         while (((ld_acquire(bar) ^ old) & 0x80000000u) == 0u) {
-            if (++spins > SPIN_LIMIT) {
+            if (++spins > limit) {
                 ok = 0;
                 atomicExch(status + 2, 1);
                 break;
@@ -1588,10 +1589,6 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *statu
     return ok_sh != 0;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *status)
-{
-    return grid_barrier(bar, nblocks, status, blockIdx.x);
-}
 
 // Per-block partial sums, stored k-major: partial[k * PSTRIDE + block].
 constexpr int PSTRIDE = 4096;
@@ -1804,7 +1801,7 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
             }
         }
         block_partials<2>(part, W.partial);
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
         double tot[2];
         grid_totals<2>(W.partial, nb, tot);
         rn = sqrt(tot[0]);
@@ -1868,7 +1865,7 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
                 double pd[1] = {(double)pa};
                 block_partials<1>(pd, W.partial);
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
             double tv[1];
             grid_totals<1>(W.partial, nb, tv);
             first = false;
@@ -1904,7 +1901,7 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
                 double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
                 block_partials<5>(pd, W.partial);
             }
-            if (!grid_barrier(W.bar, nb, W.status)) return;
+            if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
             double tq[5];
             grid_totals<5>(W.partial, nb, tq);
             T *tp = pold; pold = pnew; pnew = tp;
@@ -1935,7 +1932,7 @@ __global__ void __launch_bounds__(KT) k_krylov(Work W, int n, int maxit, double 
             if (have_pend) d += fa * pold[i] + fw * s[i];
             x[i] += (double)d;
         }
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
         if (fail) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -2535,7 +2532,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
         [&](int i, T acc, const Own4<T> &o) {
             if (lead) r0[i] = o.v[0] - acc - o.v[2] * o.v[1];
         });
-    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     // D1: restriction to the cells, one Jacobi step from zero on level 1
     {
         const LV c = lv_global(W, M, 1);
@@ -2548,11 +2545,11 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
             c.z[I] = M.omega_c * bs * c.dinv[I];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     const int fl = M.first_local;
     for (int l = 1; l < fl; ++l) {
         lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     }
     if (vb == 0) {
         {
@@ -2577,10 +2574,10 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
             for (int q = threadIdx.x; q < g.n; q += blockDim.x) g.zu[q] = s.zu[q];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     for (int l = fl - 1; l >= 1; --l) {
         lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, M.kappa_c, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     }
     // P0: prolongation from the cells, zb = z0 + kappa zu_1(cell)
     {
@@ -2590,7 +2587,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
             zb[i] = __ldcg(z0 + i) + (T)kap * (T)__ldcg(zu1 + W.cellid[i]);
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     // U0: one damped Jacobi step on the fine level
     rows_pipelined<T, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(zb, j, l1); },
         [&](int i) { return Own4<T>{{__ldcg(zb + i), __ldcg(v + i), (T)W.diag[i], (T)W.mg_dsc[i]}}; },
@@ -2600,7 +2597,7 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
                 zout[i] = o.v[0] + (T)om * res * o.v[3];
             }
         });
-    return grid_barrier(W.bar, nb, W.status, vb);
+    return grid_barrier(W.bar, nb, W.status, vb, W.spin_limit);
 }
 
 // Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
@@ -2646,7 +2643,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 }
             });
         block_partials<2>(part, W.partial, vb);
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
         double tot[2];
         grid_totals<2>(W.partial, nb, tot);
         rn = sqrt(tot[0]);
@@ -2689,7 +2686,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 pnew[i] = pn;
                 z0[i] = (T)om * pn * (T)W.mg_dsc[i];
             }
-            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, pnew, z0, zb, ph, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb))
                 return;
             first = false;
@@ -2709,7 +2706,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 double pd[1] = {(double)pa};
                 block_partials<1>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             double tv[1];
             grid_totals<1>(W.partial, nb, tv);
             if (tv[0] == 0.0) {
@@ -2725,7 +2722,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 s[i] = si;
                 z0[i] = (T)om * si * (T)W.mg_dsc[i];
             }
-            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, s, z0, zb, sh, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb))
                 return;
             // t = A s^; partials (t,s) (t,t) (s,s) (rh,s) (rh,t)
@@ -2748,7 +2745,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
                 block_partials<5>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             double tq[5];
             grid_totals<5>(W.partial, nb, tq);
             T *tp = pold; pold = pnew; pnew = tp;
@@ -2778,7 +2775,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
             if (have_pend) d += fa * __ldcg(ph + i) + fw * __ldcg(sh + i);
             x[i] += (double)d;
         }
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
         if (fail) break;
     }
     if (vb == 0 && threadIdx.x == 0) {
@@ -2827,7 +2824,7 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             r0[i] = vi - acc - (T)om * vi;
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     }
     // D1: restriction to the cells (of r0, or of v itself without pre-smoothing,
     // where own(i) runs here instead), one Jacobi step from zero on level 1
@@ -2849,11 +2846,11 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             c.z[I] = M.omega_c * bs * c.dinv[I];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     const int fl = M.first_local;
     for (int l = 1; l < fl; ++l) {
         lv_down<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     }
     if (vb == 0) {
         // levels fl..L in shared memory: b and z of level fl come from global
@@ -2879,10 +2876,10 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             for (int q = threadIdx.x; q < g.n; q += blockDim.x) g.zu[q] = s.zu[q];
         }
     }
-    if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     for (int l = fl - 1; l >= 1; --l) {
         lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, M.kappa_c, gtid, gthreads);
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return false;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
     }
     // U0: prolongation from the cells + one damped Jacobi step on the fine level
     const float *zu1 = W.mg_pool + M.offv[1] + 3 * M.n[1];
@@ -2901,7 +2898,7 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
             zout[i] = zi + (T)om * res * (T)W.mg_dsc[i];
         }
     }
-    return grid_barrier(W.bar, nb, W.status, vb);
+    return grid_barrier(W.bar, nb, W.status, vb, W.spin_limit);
 }
 
 // Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
@@ -2943,7 +2940,7 @@ __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, d
             }
         }
         block_partials<2>(part, W.partial, vb);
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
         double tot[2];
         grid_totals<2>(W.partial, nb, tot);
         rn = sqrt(tot[0]);
@@ -3009,7 +3006,7 @@ __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, d
                 double pd[1] = {(double)pa};
                 block_partials<1>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             double tv[1];
             grid_totals<1>(W.partial, nb, tv);
             if (tv[0] == 0.0) {
@@ -3046,7 +3043,7 @@ __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, d
                 double pd[5] = {(double)pb0, (double)pb1, (double)pb2, (double)pb3, (double)pb4};
                 block_partials<5>(pd, W.partial, vb);
             }
-            if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+            if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             double tq[5];
             grid_totals<5>(W.partial, nb, tq);
             T *tp = pold; pold = pnew; pnew = tp;
@@ -3076,7 +3073,7 @@ __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, d
             if (have_pend) d += fa * ph[i] + fw * sh[i];
             x[i] += (double)d;
         }
-        if (!grid_barrier(W.bar, nb, W.status, vb)) return;
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
         if (fail) break;
     }
     if (vb == 0 && threadIdx.x == 0) {
@@ -4255,6 +4252,21 @@ __global__ void k_probe_out(DevParams P, const Part c, Work W, int n, vct_probe 
     if (pr.jbar_used) pr.jbar_used[o] = c.jbar[i];
 }
 
+// Parity probes only: replace the free-surface flags pass 1 decided by the
+// caller's (caller order), for fluid particles, before anything reads them.
+__global__ void k_force_fs(const Part c, Work W, int n, const int32_t *fs_in)
+{
+    if (step_failed(W.status)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || c.type[i] != FLUID) return;
+    W.fs[i] = fs_in[c.orig[i]] ? 1 : 0;
+}
+
+void launch_force_fs(Part cur, Work W, int64_t n, const int32_t *fs_in, cudaStream_t st)
+{
+    k_force_fs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cur, W, (int)n, fs_in);
+}
+
 void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct_probe &pr,
                       cudaStream_t st)
 {
@@ -4387,7 +4399,7 @@ __global__ void __launch_bounds__(KT) k_adj_bicgstab(Work W, int n, int maxit, d
         part[0] += gi * gi;
     }
     block_partials<1>(part, W.partial);
-    if (!grid_barrier(W.bar, nb, W.status)) return;
+    if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
     double tot[1];
     grid_totals<1>(W.partial, nb, tot);
     const double bn = sqrt(tot[0]);
@@ -4409,7 +4421,7 @@ __global__ void __launch_bounds__(KT) k_adj_bicgstab(Work W, int n, int maxit, d
             pv[0] += rh[i] * vi;
         }
         block_partials<1>(pv, W.partial);
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
         grid_totals<1>(W.partial, nb, tot);
         if (tot[0] == 0.0) {
             fail = true;
@@ -4423,7 +4435,7 @@ __global__ void __launch_bounds__(KT) k_adj_bicgstab(Work W, int n, int maxit, d
             s[i] = si;
             sh[i] = si * adj_dinv(W, i);
         }
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
         // t = A^T sh; (t, s), (t, t), (s, s), (rh, s), (rh, t)
         double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int i = gtid; i < n; i += gth) {
@@ -4437,7 +4449,7 @@ __global__ void __launch_bounds__(KT) k_adj_bicgstab(Work W, int n, int maxit, d
             q[4] += hi * ti;
         }
         block_partials<5>(q, W.partial);
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
         double tq[5];
         grid_totals<5>(W.partial, nb, tq);
         const double omega = tq[1] > 0.0 ? tq[0] / tq[1] : 0.0;
@@ -4458,7 +4470,7 @@ __global__ void __launch_bounds__(KT) k_adj_bicgstab(Work W, int n, int maxit, d
             ph[i] = pi * adj_dinv(W, i);
         }
         rho = rho_new;
-        if (!grid_barrier(W.bar, nb, W.status)) return;
+        if (!grid_barrier(W.bar, nb, W.status, blockIdx.x, W.spin_limit)) return;
         if (omega == 0.0 || rho_new == 0.0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -47,7 +47,8 @@ class vct_params(C.Structure):
         ("krylov_max_iter", C.c_int32), ("smagorinsky", C.c_int32), ("precision", C.c_int32),
         ("volume_mode", C.c_int32), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("max_neighbours", C.c_int32), ("preconditioner", C.c_int32),
-        ("ops_shift", C.c_double), ("ds_overlap", C.c_double), ("xsph_eps", C.c_double)]
+        ("ops_shift", C.c_double), ("ds_overlap", C.c_double), ("xsph_eps", C.c_double),
+        ("spin_limit", C.c_int64)]
 
 
 class vct_state(C.Structure):
@@ -59,7 +60,7 @@ class vct_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("krylov_iters_total", C.c_int64),
                 ("krylov_iters_max", C.c_int32), ("graph_steps", C.c_int32),
                 ("last_residual", C.c_double), ("ppe_rows", C.c_int64), ("ppe_nnz", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("solve_form", C.c_int32), ("reserved", C.c_int32)]
 
 
 STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "rhs", "precond",
@@ -69,7 +70,7 @@ STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "r
 
 class vct_probe(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("fs", "rho_hat", "nu", "lam_min", "vstar", "ppe_b",
-                                          "x_test", "ppe_Ax", "jbar_used")]
+                                          "x_test", "ppe_Ax", "jbar_used", "fs_in")]
 
 
 _lib = None
@@ -177,6 +178,7 @@ def make_params(sc, **over):
     P.preconditioner = int(p.get("preconditioner", 1))
     for k in ("ops_shift", "ds_overlap", "xsph_eps"):
         setattr(P, k, float(p.get(k, 0.0)))
+    P.spin_limit = int(p.get("spin_limit", 0))
     return P
 
 
@@ -405,7 +407,10 @@ class Solver:
         self._check(self.lib.vct_stage_times(self.ctx, ms, cnt), "vct_stage_times")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(STAGES)}
 
-    def vct_step_probe(self, state, x_test=None):
+    def vct_step_probe(self, state, x_test=None, fs_in=None):
+        """One step that also exports intermediate fields.  fs_in: optional int32
+        CUDA tensor of free-surface flags (caller order) to use instead of the
+        step's own (parity checks pass the oracle's flags)."""
         import torch
         n, d = state.n, self.dim
         out = dict(fs=torch.zeros(n, dtype=torch.int32, device="cuda"),
@@ -418,9 +423,12 @@ class Solver:
         if x_test is not None:
             out["ppe_Ax"] = torch.zeros(n, dtype=torch.float64, device="cuda")
             x_test = x_test.contiguous()
+        if fs_in is not None:
+            fs_in = fs_in.to(dtype=torch.int32).contiguous()   # kept alive until the call returns
         pr = vct_probe(_ptr(out["fs"]), _ptr(out["rho_hat"]), _ptr(out["nu"]),
                        _ptr(out["lam_min"]), _ptr(out["vstar"]), _ptr(out["ppe_b"]),
-                       _ptr(x_test), _ptr(out.get("ppe_Ax")), _ptr(out["jbar_used"]))
+                       _ptr(x_test), _ptr(out.get("ppe_Ax")), _ptr(out["jbar_used"]),
+                       _ptr(fs_in))
         s = state.struct()
         st = vct_stats()
         self._check(self.lib.vct_step_probe(self.ctx, C.byref(s), C.byref(pr), C.byref(st)),

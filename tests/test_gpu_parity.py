@@ -136,14 +136,22 @@ def _fields(sc):
 
 # Second derivatives (and the Laplacian built from them) at FREE-SURFACE particles:
 # their support is one-sided, so after the linear part is projected out of q_ij
-# (p_ij = q_ij - C~^T r_ij) the z^2 column of M_i is nearly degenerate and
-# cond(M_i) reaches ~1e5.  Two evaluations that round differently then differ by
-# ~cond * eps: measured up to 1.9e-10 (FP64) and 4e-3 (mixed, M_i summed in FP32).
-# These particles carry the Dirichlet condition p = 0, so their D v enters only the
-# nu Lap v term of the predictor.  Bounds there: 1e-9 (FP64), 2e-2 (mixed).  Every
-# other fluid particle is held to the strict bounds (measured: <= 1e-14 FP64,
-# <= 7e-7 mixed).
-FS_TOL = {0: 1e-9, 1: 2e-2}
+# (p_ij = q_ij - C~^T r_ij) the moment matrix M_i is much worse conditioned than
+# in the interior.  D = 2 M^-1 b then carries the rounding of M and b amplified by
+# cond(M_i): |dD_i| <= cond_1(M_i) (|dM|/|M| + |db|/|b|) |D_i|.  Each entry of M
+# and b is a sum of n_i pair terms of m-vector products, so its rounding is at most
+# ~(n_i + m^2) eps relative to the sum of magnitudes (eps = 2^-53 in the FP64 form;
+# in the mixed form the pair inputs are FP32 roundings, eps = 2^-24).  The bound at
+# each free-surface particle is therefore 4 (n_i + m^2) cond_1(M_i) eps times the
+# field's scale, with cond_1(M_i) from the oracle's own M_i.  Every other fluid
+# particle is held to the strict bounds.
+EPS = {0: 2.0 ** -53, 1: 2.0 ** -24}
+
+
+def report(tag, value, bound):
+    """Print a measured error next to its bound (collected in the GPU logs)."""
+    print(f"PARITY {tag} err={value:.3e} bound={bound:.1e}")
+    return value < bound
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)], ids=["fp64", "mixed"])
@@ -158,21 +166,45 @@ def test_sph2_derivatives_parity(vct, name, make, precision, tol):
     og, od2, olap = O.sph2_derivatives(sc, phi)
     _, info = O.step(sc, probe=True)
     fs = info["fs"] == 1
+    f = sc.type == S.FLUID
+    M = O.moment_matrices(sc)
+    m = M.shape[1]
+    xh, _ = O.projected(sc)
+    _, re, re2 = O.radii(sc)
+    row, col = O.neighbours(sc.dim, xh, re, re2)
+    nb = np.diff(row)
+    cond = np.zeros(sc.n)
+    for i in np.flatnonzero(f & fs):
+        cond[i] = np.linalg.cond(M[i], 1)
+    fs_bound = 4.0 * (nb + m * m) * cond * EPS[precision]
     g, d2, lap = g.cpu().numpy(), d2.cpu().numpy(), lap.cpu().numpy()
     # normwise per field: a gradient or a second-derivative set is one field
     for c in range(phi.shape[0]):
-        assert rel(g[c], og[c]) < tol, ("grad", c, rel(g[c], og[c]))
+        assert report(f"{name} p{precision} grad{c}", rel(g[c], og[c]), tol)
         sd = np.abs(od2[c]).max()
         sl = np.abs(olap[c]).max()
         e2 = np.abs(d2[c] - od2[c]).max(axis=0) / sd
         el = np.abs(lap[c] - olap[c]) / sl
-        assert e2[~fs].max() < tol, ("d2 interior", c, e2[~fs].max())
-        assert el[~fs].max() < tol, ("lap interior", c, el[~fs].max())
-        assert e2[fs].max() < FS_TOL[precision], ("d2 free surface", c, e2[fs].max())
-        assert el[fs].max() < FS_TOL[precision], ("lap free surface", c, el[fs].max())
+        assert report(f"{name} p{precision} d2 interior{c}", e2[f & ~fs].max(), tol)
+        assert report(f"{name} p{precision} lap interior{c}", el[f & ~fs].max(), tol)
+        if (f & fs).any():
+            k = np.flatnonzero(f & fs)
+            r2 = (e2[k] / np.maximum(fs_bound[k], tol)).max()
+            rl = (el[k] / np.maximum(fs_bound[k], tol)).max()
+            print(f"PARITY {name} p{precision} free-surface cond max {cond[k].max():.2e} "
+                  f"d2 err {e2[k].max():.2e} lap err {el[k].max():.2e}")
+            assert report(f"{name} p{precision} d2 fs/bound{c}", r2, 1.0)
+            assert report(f"{name} p{precision} lap fs/bound{c}", rl, 1.0)
 
 
-def _probe_compare(vct, sc, precision, tol, band):
+def _probe_compare(vct, sc, precision, tol, band, name="case"):
+    """One step through vct_step_probe against the oracle's probe.
+
+    Free-surface flags must agree outside the tie band.  Inside it both
+    decisions are correct roundings of the same threshold test; when they
+    differ, the GPU step is repeated with the oracle's flags (the probe's
+    fs_in), so the pressure system, the solve and the corrector are compared
+    on every case.  Returns (stats, number of tied particles, forced)."""
     import torch
     sc = sc.copy()
     sc.params["precision"] = precision
@@ -181,9 +213,10 @@ def _probe_compare(vct, sc, precision, tol, band):
     n = sc.n
     rng = np.random.default_rng(5)
     xt = rng.normal(size=n)
+    xt_d = torch.tensor(xt, device="cuda")
     solver = vct.Solver(sc)
     st = vct.DeviceState(sc)
-    out, stats = solver.vct_step_probe(st, torch.tensor(xt, device="cuda"))
+    out, stats = solver.vct_step_probe(st, xt_d)
     g = {k: v.cpu().numpy() for k, v in out.items()}
     gs = st.numpy()
     ost, info = O.step(sc, probe=True, x_test=xt, rtol=1e-13)
@@ -196,41 +229,65 @@ def _probe_compare(vct, sc, precision, tol, band):
     tied = f & ~clear
     if precision == 0:
         assert np.array_equal(g["fs"], info["fs"]), "flags differ"
-    assert rel(g["lam_min"][f], lam[f]) < tol
-    assert rel(g["rho_hat"][f], info["rho_hat"][f]) < tol
-    assert rel(g["nu"][f], info["nu"][f]) < tol
-    assert rel(g["jbar_used"], info["jbar_used"]) < tol
+    tag = f"{name} p{precision}"
+    assert report(f"{tag} lam_min", rel(g["lam_min"][f], lam[f]), tol)
+    assert report(f"{tag} rho_hat", rel(g["rho_hat"][f], info["rho_hat"][f]), tol)
+    assert report(f"{tag} nu", rel(g["nu"][f], info["nu"][f]), tol)
+    assert report(f"{tag} jbar", rel(g["jbar_used"], info["jbar_used"]), tol)
     for c in range(sc.dim):
-        assert rel(g["vstar"][c][f], info["vstar"][c][f]) < tol
-    if np.array_equal(g["fs"], info["fs"]):
-        # identical unknown set: compare the linear system itself
-        assert rel(g["ppe_b"], info["ppe_b"]) < tol * 10
-        assert rel(g["ppe_Ax"], info["ppe_Ax"]) < tol * 10
-        ptol = 1e-7 if precision == 0 else 1e-4
-        assert rel(gs["p"][f], ost.p[f]) < ptol
-        for k in ("u", "w") + (("v",) if sc.dim == 3 else ()):
-            assert rel(gs[k][f], getattr(ost, k)[f]) < ptol
-        for k in ("x", "z") + (("y",) if sc.dim == 3 else ()):
-            assert np.abs(gs[k][f] - getattr(ost, k)[f]).max() < ptol * sc.params["dt"] * (
-                np.abs(getattr(ost, "u")[f]).max() + np.abs(getattr(ost, "w")[f]).max() + 1.0)
-    return stats, tied.sum()
+        assert report(f"{tag} vstar{c}", rel(g["vstar"][c][f], info["vstar"][c][f]), tol)
+    forced = not np.array_equal(g["fs"], info["fs"])
+    if forced:
+        solver2 = vct.Solver(sc)
+        st2 = vct.DeviceState(sc)
+        fs_in = torch.tensor(info["fs"], dtype=torch.int32, device="cuda")
+        out, stats = solver2.vct_step_probe(st2, xt_d, fs_in=fs_in)
+        g = {k: v.cpu().numpy() for k, v in out.items()}
+        gs = st2.numpy()
+        assert np.array_equal(g["fs"], info["fs"])
+    print(f"PARITY {tag} tied={int(tied.sum())} differing={int((g['fs'] != info['fs']).sum())} "
+          f"forced={forced}")
+    # identical unknown set: the linear system itself, then the solve and the corrector
+    assert report(f"{tag} ppe_b", rel(g["ppe_b"], info["ppe_b"]), tol)
+    assert report(f"{tag} ppe_Ax", rel(g["ppe_Ax"], info["ppe_Ax"]), tol)
+    # The solve: the GPU pressure must solve the ORACLE's FP64 system with normwise
+    # backward error eta = |A p - b| / (|A| |p| + |b|) within the form's tolerance
+    # (independent of the system's conditioning; |A| estimated from below by
+    # |A x| / |x| for the random x above, which only makes eta larger).
+    unk = f & (info["fs"] == 0)
+    if unk.any():
+        _, ip = O.step(sc, probe=True, x_test=np.where(unk, gs["p"], 0.0), max_iter=1)
+        res = np.abs(ip["ppe_Ax"][unk] - info["ppe_b"][unk]).max()
+        a_norm = np.abs(info["ppe_Ax"][unk]).max() / np.abs(xt[unk]).max()
+        eta = res / (a_norm * np.abs(gs["p"][unk]).max() + np.abs(info["ppe_b"][unk]).max())
+        assert report(f"{tag} solve backward error", eta, tol)
+    # forward errors of the solved fields (both sides stop at a residual; the
+    # error is at most cond(A) times the backward error): regression bounds
+    ptol = 1e-7 if precision == 0 else 1e-4
+    assert report(f"{tag} p", rel(gs["p"][f], ost.p[f]), ptol)
+    for k in ("u", "w") + (("v",) if sc.dim == 3 else ()):
+        assert report(f"{tag} {k}", rel(gs[k][f], getattr(ost, k)[f]), ptol)
+    vs = sc.params["dt"] * (np.abs(ost.u[f]).max() + np.abs(ost.w[f]).max() + 1.0)
+    for k in ("x", "z") + (("y",) if sc.dim == 3 else ()):
+        assert report(f"{tag} {k}/dt|v|", np.abs(gs[k][f] - getattr(ost, k)[f]).max() / vs, ptol)
+    return stats, int(tied.sum()), forced
 
 
 @pytest.mark.parametrize("name,make", SMALL + [("still_water_bf", S.still_water_bf)],
                          ids=[s[0] for s in SMALL] + ["still_water_bf"])
 def test_step_parity_fp64(vct, name, make):
-    _probe_compare(vct, make(), 0, 1e-12, 1e-9)
+    _probe_compare(vct, make(), 0, 1e-12, 1e-9, name)
 
 
 @pytest.mark.parametrize("name,make", SMALL + [("still_water_bf", S.still_water_bf)],
                          ids=[s[0] for s in SMALL] + ["still_water_bf"])
 def test_step_parity_mixed(vct, name, make):
-    _probe_compare(vct, make(), 1, 1e-5, 1e-5)
+    _probe_compare(vct, make(), 1, 1e-5, 1e-5, name)
 
 
 def test_step_parity_sigma_solitary_mixed(vct):
     """Full-size sigma solitary wave over a Gaussian bump (~42.5k fluid), mixed form."""
-    _probe_compare(vct, S.solitary_sigma(), 1, 1e-5, 1e-5)
+    _probe_compare(vct, S.solitary_sigma(), 1, 1e-5, 1e-5, "solitary")
 
 
 # Particle regularisation on (dynamic stabilization, XSPH, shifting; Sec. 4.1):
@@ -253,7 +310,7 @@ def test_step_parity_regularised(vct, name, make, precision, tol, band):
     pts = np.asarray(xh).T if np.asarray(xh).shape[0] == sc.dim else np.asarray(xh)
     dmin, _ = cKDTree(pts).query(pts, k=2)
     assert dmin[:, 1].min() < 0.6 * sc.params["d0"]       # stabilization is exercised
-    _probe_compare(vct, sc, precision, tol, band)
+    _probe_compare(vct, sc, precision, tol, band, name)
 
 
 # The multigrid solver has two forms: V-cycle inputs formed on the fly (systems up
@@ -265,12 +322,12 @@ def test_step_parity_regularised(vct, name, make, precision, tol, band):
                          ids=[SMALL[1][0], SMALL[3][0], "still_water_bf"])
 def test_step_parity_explicit_form(vct, monkeypatch, name, make, precision, tol, band):
     monkeypatch.setenv("VCT_MG_FORM", "explicit")
-    _probe_compare(vct, make(), precision, tol, band)
+    _probe_compare(vct, make(), precision, tol, band, name + "-explicit")
 
 
 def test_step_parity_sigma_solitary_explicit_form(vct, monkeypatch):
     monkeypatch.setenv("VCT_MG_FORM", "explicit")
-    _probe_compare(vct, S.solitary_sigma(), 1, 1e-5, 1e-5)
+    _probe_compare(vct, S.solitary_sigma(), 1, 1e-5, 1e-5, "solitary-explicit")
 
 
 def test_forms_agree_over_steps(vct, monkeypatch):

@@ -61,7 +61,8 @@ def test_reference_arm_prints_the_contract_line():
     import json
     import subprocess
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                        "--steps", "1", "--warmup", "1", "--ref-budget", "5"],
+                       capture_output=True, text=True,
                        timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
