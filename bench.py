@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-fp64-probe", action="store_true",
                     help="skip the per-field error of the mixed form against the FP64 form")
     ap.add_argument("--ensemble-size", type=int, default=64)
+    ap.add_argument("--horizon", type=int, default=None,
+                    help="restart from the initial state every this many steps (default 150 "
+                         "in 2-D, 30 in 3-D; 0 = never)")
     ap.add_argument("--ref-budget", type=float, default=150.0,
                     help="host seconds the reference arm's timed and warm-up steps aim at")
     return ap.parse_args()
@@ -93,6 +96,8 @@ WORKLOADS = {
     "beach_bfe_3d_slice": ("3-D BFE solitary wave, 8 x 1.6 m slice of the 1:20 beach (depth 1 -> 0.6 m), "
                            "aspect 4, d0=0.043 m (profiling size)"),
     "ensemble": "sigma-SPH ensemble, particle counts log-uniform 5e3-2e5 (seed 2), 4 bumps each",
+    "efficiency": ("hydrostatic 1 m tank, H = 0.2 m, bottom 0.12 x + 0.01 (1 - cos(2 pi x / 0.5)): "
+                   "BF d0 = 0.2 cm, BFE d0 = 0.5 cm alpha 2.5, sigma d0 = 0.5 cm alpha 1-2.5"),
     "adjoint": ("2-D sigma channel 10 m, flat 0.5 m + 16 random Gaussian bumps (seed 1), d0=0.01 m, "
                 "adjoint of the SPH(2) derivative operator"),
 }
@@ -177,6 +182,60 @@ def run_adjoint(args):
                                     "adjoint_iters": int(ast.krylov_iters_total)},
                       "scope": "operator adjoint and pressure-solve adjoint; the checkpointed "
                                "full-step adjoint is not built"}), flush=True)
+
+
+def run_efficiency(args):
+    """The BF / BFE / sigma efficiency comparison (Sec. 4.4.1, Table fig:s4_s_time)
+    on the hydrostatic sine + slope tank: per model the particles, the device
+    memory of its context, the time per step, particle-updates/s and the
+    relative L2 error of the pressure against hydrostatic after the run.  Not
+    the headline line."""
+    import numpy as np
+    import torch
+    from paper_2607_28872_b300 import scenarios as S
+    from paper_2607_28872_b300 import vct
+    if dist_env()[0] != 0:
+        return
+    steps = min(args.steps, 400) if args.steps else 400
+    rows = {}
+    for kind in ("BF", "BFE", "SIGMA"):
+        sc = S.efficiency_tank(kind, precision=args.precision)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        solver = vct.Solver(sc)
+        state = vct.DeviceState(sc)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        solver.vct_step(state, max(args.warmup, 3))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = solver.vct_step(state, steps)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        g = state.numpy()
+        f = sc.type == S.FLUID
+        surf = np.sort(g["z"][f])[-1]
+        hyd = sc.params["rho"] * sc.params["g"] * (sc.params["H"] - g["z"])
+        deep = f & (g["p"] > 0)
+        e_l2 = float(np.linalg.norm((g["p"] - hyd)[deep]) / np.linalg.norm(hyd[deep]))
+        vmax = float(np.sqrt(g["u"] ** 2 + g["w"] ** 2)[f].max())
+        rows[kind] = {"n_fluid": sc.n_fluid, "n_particles": sc.n, "d0": sc.params["d0"],
+                      "context_mb": (free0 - free1) / 2 ** 20, "ms_per_step": ms,
+                      "particle_updates_per_s": sc.n_fluid / (ms / 1e3),
+                      "krylov_iters_per_step": st.krylov_iters_total / steps,
+                      "p_rel_l2_err": e_l2, "v_max": vmax, "top_z": float(surf)}
+        solver.close()
+        del state
+    bf = rows["BF"]
+    for kind in rows:
+        rows[kind]["particles_vs_bf"] = rows[kind]["n_fluid"] / bf["n_fluid"]
+        rows[kind]["time_vs_bf"] = rows[kind]["ms_per_step"] / bf["ms_per_step"]
+    print(json.dumps({"metric": "BF / BFE / sigma efficiency on the hydrostatic sine + slope tank",
+                      "steps": steps, "dt": 5e-4, "n_gpus": 1, "data": "synthetic",
+                      "dtype": "f32+f64" if args.precision == 1 else "f64",
+                      "config": {"workload": WORKLOADS["efficiency"]}, "models": rows}), flush=True)
 
 
 def run_ensemble(args):
@@ -414,15 +473,16 @@ def run_ours(args):
     # (the 2-D wave to ~280, the 3-D beach slice to ~40, both sides of the parity
     # tests alike): longer runs start again from the initial state every
     # `horizon` steps, outside the timed brackets
-    horizon = 150 if sc.dim == 2 else 30
-    run = {"state": vct.DeviceState(sc), "since": 0}
+    horizon = (150 if sc.dim == 2 else 30) if args.horizon is None else args.horizon
+    run = {"state": vct.DeviceState(sc), "since": 0, "total": 0}
 
     def fresh():
-        if run["since"] >= horizon:
+        if horizon and run["since"] >= horizon:
             run["state"] = vct.DeviceState(sc)
             run["since"] = 0
             torch.cuda.synchronize()
         run["since"] += 1
+        run["total"] += 1
         return run["state"]
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -445,7 +505,11 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st = solver.vct_step(state, 1)
+        try:
+            st = solver.vct_step(state, 1)
+        except vct.VCTError as err:
+            print(f"step {run['total']} of the run failed: {err}", file=sys.stderr, flush=True)
+            raise
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
@@ -652,6 +716,8 @@ def main():
         run_reference(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "efficiency":
+        run_efficiency(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
     else:

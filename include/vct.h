@@ -148,6 +148,15 @@ typedef struct {
      * call returns VCT_ERR_TIMEOUT and the caller's state is left as it was.
      * Negative is VCT_ERR_ARG. */
     int64_t spin_limit;
+    /* Operator set (Table tab:case_names): 0 = ISPH(2): SPH(2) second derivatives
+     * (Eq. sec_SPH2) in the viscous term and the pressure equation, first-order
+     * corrected pressure gradient (Eq. gra_1st); 1 = ISPH: 0th-order second
+     * derivatives of Espanol & Revenga (Eq. sec_0th), summation pressure
+     * gradient (Eq. gra_sum).  Velocity divergence first-order in both.
+     * sph2_derivatives returns the set's second derivatives.  The backward
+     * entries differentiate the ISPH(2) set only.  Other values: VCT_ERR_ARG. */
+    int32_t operators;
+    int32_t reserved2;
 } vct_params;
 
 /* Particle state, caller order, DEVICE arrays of n entries (host arrays for

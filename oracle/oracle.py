@@ -31,7 +31,8 @@ class OrcParams(C.Structure):
                                   "ppe_rtol")] + [
         (k, C.c_int) for k in ("ppe_max_iter", "smagorinsky", "volume_mode", "neighbour_mode",
                                "smoothing_mode", "pad_")] + [
-        (k, C.c_double) for k in ("ops_shift", "ds_overlap", "xsph_eps")]
+        (k, C.c_double) for k in ("ops_shift", "ds_overlap", "xsph_eps")] + [
+        ("operators", C.c_int), ("pad2_", C.c_int)]
 
 
 class OrcState(C.Structure):
@@ -65,6 +66,8 @@ def lib():
         L.orc_neighbours.restype = C.c_int64
         L.orc_sph2_derivatives.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
                                            C.POINTER(OrcState), dp, C.c_int, dp, dp, dp]
+        L.orc_summation_gradient.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
+                                             C.POINTER(OrcState), dp, C.c_int, dp]
         L.orc_moment_matrices.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
                                           C.POINTER(OrcState), dp]
         L.orc_volume_smoothing.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcBathy),
@@ -130,6 +133,7 @@ def make_params(sc, neighbour_mode=1, smoothing_mode=1, rtol=1e-13, max_iter=200
     P.smoothing_mode = int(smoothing_mode)
     for k in ("ops_shift", "ds_overlap", "xsph_eps"):
         setattr(P, k, float(p.get(k, 0.0)))
+    P.operators = int(p.get("operators", 0))
     return P
 
 
@@ -241,6 +245,23 @@ def sph2_derivatives(sc, phi, state=None, **over):
     if rc:
         raise RuntimeError(f"oracle sph2_derivatives failed: {rc}")
     return g, d2, lap
+
+
+def summation_gradient(sc, phi, **over):
+    """The summation gradient of Eq. (gra_sum), projected coordinates:
+    (ncomp, d, n) for phi (ncomp, n)."""
+    keep = _Keep()
+    st = OracleState(sc)
+    B = make_bathy(sc.bathy, keep)
+    P = make_params(sc, **over)
+    phi = keep.f64(np.atleast_2d(phi))
+    nc = phi.shape[0]
+    out = np.zeros((nc, sc.dim, sc.n))
+    S = st.struct()
+    rc = lib().orc_summation_gradient(C.byref(P), C.byref(B), C.byref(S), _dp(phi), nc, _dp(out))
+    if rc:
+        raise RuntimeError(f"oracle summation_gradient failed: {rc}")
+    return out
 
 
 def moment_matrices(sc, **over):

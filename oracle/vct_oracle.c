@@ -72,6 +72,11 @@ typedef struct {
     double H, H_hat, alpha_min, alpha_max, lam_fs_lo, lam_fs_hi, ppe_rtol;
     int ppe_max_iter, smagorinsky, volume_mode, neighbour_mode, smoothing_mode, pad_;
     double ops_shift, ds_overlap, xsph_eps;   /* particle regularisation, 0 = off */
+    int operators;   /* 0: ISPH(2) -- SPH(2) second derivatives (Eq. sec_SPH2), 1st-order
+                      *    pressure gradient (Eq. gra_1st); 1: ISPH -- 0th-order second
+                      *    derivatives (Eq. sec_0th), summation pressure gradient (Eq. gra_sum);
+                      *    velocity divergence 1st-order in both (Table tab:case_names) */
+    int pad2_;
 } orc_params;
 
 typedef struct {
@@ -489,6 +494,27 @@ static void ctilde(int d, const double *met, double *ct)
     }
 }
 
+/* Weights k_a(r) of the 0th-order second derivatives of Espanol & Revenga
+ * (Eq. sec_0th) in the order of the SPH(2) output D (cross entries doubled):
+ *   d2 phi / dx^I dx^J ~ sum_j V_j (c r^I r^J / |r|^2 - delta^IJ) (r . grad w)/|r|^2 phi_ij,
+ * c = 4 (2-D), 5 (3-D); with grad w = -(w'/|r|) r, (r . grad w)/|r|^2 = -w'/|r|. */
+static void er_weights(int d, const double *r, double rr2, double dw, double *k)
+{
+    double rr = sqrt(rr2), f = -dw / rr, c = d == 2 ? 4.0 : 5.0;
+    if (d == 2) {
+        k[0] = f * (c * r[0] * r[0] / rr2 - 1.0);
+        k[1] = f * (c * r[1] * r[1] / rr2 - 1.0);
+        k[2] = 2.0 * f * c * r[0] * r[1] / rr2;
+    } else {
+        k[0] = f * (c * r[0] * r[0] / rr2 - 1.0);
+        k[1] = f * (c * r[1] * r[1] / rr2 - 1.0);
+        k[2] = f * (c * r[2] * r[2] / rr2 - 1.0);
+        k[3] = 2.0 * f * c * r[0] * r[1] / rr2;
+        k[4] = 2.0 * f * c * r[1] * r[2] / rr2;
+        k[5] = 2.0 * f * c * r[2] * r[0] / rr2;
+    }
+}
+
 /* Jacobian of Eq. (jacobi) restricted to the d used coordinates, row-major:
  * 2-D rows x, z: [1 s_x; 0 alpha]; 3-D: [1 0 s_x; 0 1 s_y; 0 0 alpha]. */
 static void jac(int d, const double *met, double *Jm)
@@ -514,6 +540,8 @@ typedef struct {
     double gt[3];       /* L_i grad w_ij */
     double F;           /* F_ij */
     double q[6];
+    double k0[6];       /* 0th-order second-derivative weights (Eq. sec_0th) */
+    double dw;          /* w'(|r^_ij|) */
 } pair_t;
 
 typedef struct {
@@ -797,6 +825,8 @@ static int pass2_one(const orc_params *P, const orc_state *S, work_t *W, int i, 
         pr->tj = tj;
         pr->V = vol_j(P, W, S, j);
         double dw = kern_dw(rr, W->l, d), rg = 0.0;
+        pr->dw = dw;
+        er_weights(d, pr->r, rr2, dw, pr->k0);
         for (int K = 0; K < d; ++K) pr->gw[K] = -dw / rr * pr->r[K];
         for (int K = 0; K < d; ++K) {
             double s = 0.0;
@@ -831,8 +861,20 @@ static int pass2_one(const orc_params *P, const orc_state *S, work_t *W, int i, 
     if (!do_pred) return ORC_OK;
     double Mc[36];
     memcpy(Mc, M, sizeof Mc);
-    if (gauss_solve(m, Mc, d, bv)) return ORC_ERR_SINGULAR;
-    /* D_c = 2 M^-1 b_c */
+    if (P->operators == 1) {
+        /* ISPH: D_c = the 0th-order second derivatives of v_c, stored as b = D/2 */
+        for (int k = 0; k < m * d; ++k) bv[k] = 0.0;
+        for (int k = 0; k < np; ++k) {
+            const pair_t *pr = pp + k;
+            for (int c = 0; c < d; ++c) {
+                double vij = (pr->tj == ORC_FLUID ? vel(S, d, pr->j, c) : 0.0) - vel(S, d, i, c);
+                for (int a = 0; a < m; ++a) bv[a * d + c] += 0.5 * pr->V * pr->k0[a] * vij;
+            }
+        }
+    } else if (gauss_solve(m, Mc, d, bv)) {
+        return ORC_ERR_SINGULAR;
+    }
+    /* D_c = 2 M^-1 b_c (SPH(2)) or the 0th-order second derivatives (ISPH) */
     double ct[6], Jm[9], gnh[3], gn[3];
     ctilde(d, W->met + 7 * i, ct);
     jac(d, W->met + 7 * i, Jm);
@@ -891,9 +933,25 @@ static double ppe_op_one(const orc_params *P, const work_t *W, int i, const doub
         for (int K = 0; K < d; ++K) rg += pr->r[K] * gp[K];
         for (int a = 0; a < m; ++a) b[a] += pr->V * pr->F * pr->q[a] * (pij - rg);
     }
-    double Mc[36];
-    memcpy(Mc, W->LU + (size_t)36 * i, sizeof(double) * m * m);
-    gauss_solve(m, Mc, 1, b);
+    if (P->operators == 1) {
+        /* ISPH: D = the 0th-order second derivatives of the pressure */
+        for (int a = 0; a < m; ++a) b[a] = 0.0;
+        for (int k = 0; k < np && pp[k].j >= 0; ++k) {
+            const pair_t *pr = pp + k;
+            double pij;
+            if (pr->tj == ORC_FLUID) pij = x[pr->j] - x[i];
+            else {
+                double s = 0.0;
+                for (int K = 0; K < d; ++K) s += pr->rp[K] * W->acc[d * i + K];
+                pij = P->rho * s;
+            }
+            for (int a = 0; a < m; ++a) b[a] += 0.5 * pr->V * pr->k0[a] * pij;
+        }
+    } else {
+        double Mc[36];
+        memcpy(Mc, W->LU + (size_t)36 * i, sizeof(double) * m * m);
+        gauss_solve(m, Mc, 1, b);
+    }
     double ct[6];
     ctilde(d, W->met + 7 * i, ct);
     double out = W->met[7 * i + 3] * gp[d - 1];
@@ -1073,10 +1131,16 @@ int orc_sph2_derivatives(const orc_params *P, const orc_bathy *b, orc_state *S, 
                 for (int a = 0; a < m; ++a)
                     bb[a] += pp[k].V * pp[k].F * pp[k].q[a] * ((f[pp[k].j] - f[i]) - rg);
             }
-            double Mc[36];
-            memcpy(Mc, W.LU + (size_t)36 * i, sizeof(double) * m * m);
-            if (gauss_solve(m, Mc, 1, bb)) continue;
-            for (int a = 0; a < m; ++a) bb[a] *= 2.0;   /* D = 2 M^-1 b */
+            if (P->operators == 1) {   /* ISPH: 0th-order second derivatives */
+                for (int a = 0; a < m; ++a) bb[a] = 0.0;
+                for (int k = 0; k < np && pp[k].j >= 0; ++k)
+                    for (int a = 0; a < m; ++a) bb[a] += pp[k].V * pp[k].k0[a] * (f[pp[k].j] - f[i]);
+            } else {
+                double Mc[36];
+                memcpy(Mc, W.LU + (size_t)36 * i, sizeof(double) * m * m);
+                if (gauss_solve(m, Mc, 1, bb)) continue;
+                for (int a = 0; a < m; ++a) bb[a] *= 2.0;   /* D = 2 M^-1 b */
+            }
             if (grad_hat)
                 for (int K = 0; K < d; ++K) grad_hat[((size_t)c * d + K) * n + i] = g[K];
             if (d2_hat)
@@ -1087,6 +1151,39 @@ int orc_sph2_derivatives(const orc_params *P, const orc_bathy *b, orc_state *S, 
                 for (int a = 0; a < m; ++a) lap += ct[a] * bb[a];
                 lap_phys[(size_t)c * n + i] = lap;
             }
+        }
+    }
+    work_free(&W);
+    return ORC_OK;
+}
+
+/* Public: the summation gradient of Eq. (gra_sum) with constant density,
+ * <grad^ phi>+_i = sum_j V_j (phi_j + phi_i) grad w_ij over fluid and wall
+ * neighbours (wall values from phi), in projected coordinates, for fluid
+ * particles (0 elsewhere): out[(c*d + K)*n + i]. */
+int orc_summation_gradient(const orc_params *P, const orc_bathy *b, orc_state *S, const double *phi,
+                           int ncomp, double *out)
+{
+    work_t W;
+    memset(&W, 0, sizeof W);
+    int n = S->n, d = P->dim;
+    stage_geometry(P, b, S, &W);
+    alloc_work(&W, n, 1);
+    int rc = run_pass1(P, S, &W);
+    if (!rc) rc = run_pass2(P, S, &W, 0);
+    if (rc) { work_free(&W); return rc; }
+    memset(out, 0, sizeof(double) * (size_t)ncomp * d * n);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        if (S->type[i] != ORC_FLUID) continue;
+        const pair_t *pp = W.pairs + W.pstart[i];
+        int np = (int)(W.pstart[i + 1] - W.pstart[i]);
+        for (int c = 0; c < ncomp; ++c) {
+            const double *f = phi + (size_t)c * n;
+            double g[3] = {0};
+            for (int k = 0; k < np && pp[k].j >= 0; ++k)
+                for (int K = 0; K < d; ++K) g[K] += pp[k].V * (f[pp[k].j] + f[i]) * pp[k].gw[K];
+            for (int K = 0; K < d; ++K) out[((size_t)c * d + K) * n + i] = g[K];
         }
     }
     work_free(&W);
@@ -1407,7 +1504,10 @@ int orc_step(const orc_params *P, const orc_bathy *b, orc_state *S, int nsteps, 
                         for (int K = 0; K < d; ++K) s += pp[k].rp[K] * W.acc[d * i + K];
                         pij = P->rho * s;
                     }
-                    for (int K = 0; K < d; ++K) gp[K] += pp[k].V * pij * pp[k].gt[K];
+                    if (P->operators == 1)   /* summation gradient (Eq. gra_sum), p_j + p_i */
+                        for (int K = 0; K < d; ++K) gp[K] += pp[k].V * (pij + 2.0 * pn[i]) * pp[k].gw[K];
+                    else
+                        for (int K = 0; K < d; ++K) gp[K] += pp[k].V * pij * pp[k].gt[K];
                 }
                 double Jm[9];
                 jac(d, W.met + 7 * i, Jm);

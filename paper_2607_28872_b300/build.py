@@ -29,7 +29,10 @@ def _deps():
     return _mtime(files + [os.path.join(INCLUDE, "vct.h")])
 
 
-def _link(lib, sources, verbose):
+def _link(lib, sources, verbose, stamp):
+    """Compile and link; the library's mtime is set to `stamp`, the newest source
+    time seen when the build started, so a source edited during the build
+    makes the library stale for the next build."""
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
     procs, objs = [], []
@@ -48,14 +51,17 @@ def _link(lib, sources, verbose):
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)
     os.replace(lib + ".tmp", lib)
+    os.utime(lib, (stamp, stamp))
 
 
 def build(force=False, verbose=False):
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < _deps():
-        _link(LIB, SOURCES, verbose)
+    t = _deps()
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < t:
+        _link(LIB, SOURCES, verbose, t)
     peaks_src = [os.path.join(CSRC, s) for s in PEAKS_SOURCES]
-    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(PEAKS_LIB) < _mtime(peaks_src):
-        _link(PEAKS_LIB, PEAKS_SOURCES, verbose)
+    t = _mtime(peaks_src)
+    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(PEAKS_LIB) < t:
+        _link(PEAKS_LIB, PEAKS_SOURCES, verbose, t)
     return LIB
 
 

@@ -658,6 +658,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     if (prm->precision != VCT_FP64 && prm->precision != VCT_MIXED) return VCT_ERR_ARG;
     if (prm->volume_mode < 0 || prm->volume_mode > 2) return VCT_ERR_ARG;
     if (prm->spin_limit < 0) return VCT_ERR_ARG;
+    if (prm->operators != 0 && prm->operators != 1) return VCT_ERR_ARG;
     // the background cell grid, validated before anything is allocated
     int grid_nc[3];
     int64_t ncell = 1;
@@ -711,6 +712,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     P.ops_shift = prm->ops_shift;
     P.ds_overlap = prm->ds_overlap;
     P.xsph_eps = prm->xsph_eps;
+    P.operators = prm->operators;
     P.pguess = getenv("VCT_PGUESS") ? atoi(getenv("VCT_PGUESS")) : 2;   // 0: none, 1: linear
     P.inner_floor = prm->precision == VCT_MIXED ? 1e-4 : 0.0;
     if (prm->precision == VCT_MIXED && getenv("VCT_INNER_FLOOR")) P.inner_floor = atof(getenv("VCT_INNER_FLOOR"));

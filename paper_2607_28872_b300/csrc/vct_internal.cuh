@@ -29,7 +29,9 @@ struct DevParams {
     double aspect, rho, nu_k, g, dt, d0, l, inv_l, re, re2, V0, ad;
     double ops_shift, ds_overlap, xsph_eps;   // particle regularisation (0: off)
     int pguess;               // order of the pressure extrapolation of the initial guess
-    int pad2;
+    int operators;            // 0: ISPH(2) (SPH(2) second derivatives, 1st-order pressure
+                              // gradient); 1: ISPH (0th-order second derivatives, summation
+                              // pressure gradient)
     double gamma, cv, cs, ds, H, H_hat, amin, amax, lam_lo, lam_hi, rtol;
     double inner_floor;       // mixed form: each FP32 BiCGSTAB pass stops at this relative residual
     double box_lo[3], cell_h, inv_cell_h;

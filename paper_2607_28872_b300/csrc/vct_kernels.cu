@@ -220,6 +220,28 @@ __device__ __forceinline__ void qvec(const R *r, R *q)
     }
 }
 
+// Weights k_a(r) of the 0th-order second derivatives of Espanol & Revenga
+// (Eq. sec_0th), in the order of the SPH(2) output D (cross entries doubled):
+//   d2 phi/dx^I dx^J ~ sum_j V_j (c r^I r^J/|r|^2 - delta^IJ) (r . grad w)/|r|^2 phi_ij,
+// c = d + 2; with grad w = fac r, fac = -w'/|r|, (r . grad w)/|r|^2 = fac.
+template <int D, typename R>
+__device__ __forceinline__ void er_weights(const R *r, R rr2, R fac, R *k)
+{
+    const R c = R(D + 2), inv = R(1) / rr2;
+    if constexpr (D == 2) {
+        k[0] = fac * (c * r[0] * r[0] * inv - R(1));
+        k[1] = fac * (c * r[1] * r[1] * inv - R(1));
+        k[2] = R(2) * fac * c * r[0] * r[1] * inv;
+    } else {
+        k[0] = fac * (c * r[0] * r[0] * inv - R(1));
+        k[1] = fac * (c * r[1] * r[1] * inv - R(1));
+        k[2] = fac * (c * r[2] * r[2] * inv - R(1));
+        k[3] = R(2) * fac * c * r[0] * r[1] * inv;
+        k[4] = R(2) * fac * c * r[1] * r[2] * inv;
+        k[5] = R(2) * fac * c * r[2] * r[0] * inv;
+    }
+}
+
 // Inverse of a D x D matrix (row-major) by the adjugate.  Returns false if singular.
 template <int D>
 __device__ bool inv_small(const double *B, double *L)
@@ -1408,10 +1430,191 @@ __global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams 
     atomicAdd((unsigned long long *)&W.counts[1], (unsigned long long)pc);
 }
 
+// Pass 2 of the ISPH operator set (Table tab:case_names): the predictor with the
+// 0th-order second derivatives of Eq. (sec_0th), D_a v = sum_j V_j k_a(r_ij) v_ij,
+// and the pressure row c_trans . <D^ p>^(0): a_ij = V_j (c0 (L grad w)_z^ +
+// sum_a c~_a k_a(r_ij)).  No moment matrix and no per-particle solve.
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_pass2_isph(DevParams P, const Part c, Work W, int n)
+{
+    if (step_failed(W.status)) return;
+    constexpr int M = D == 2 ? 3 : 6;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (c.type[i] != FLUID) {
+        W.pcnt[i] = -1;
+        return;
+    }
+    const int64_t cap = W.cap;
+    double xi[3], vi[3];
+    load_hat<D>(c, i, xi);
+    const float4 hfi = W.hatf[i], lfi = W.hatlo[i];
+    load_vel<D>(c, i, vi);
+    R L[D * D];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) L[k] = (R)W.L[(int64_t)k * cap + i];
+    const double nui = W.nu[i];
+    constexpr bool MIXED = sizeof(R) == sizeof(float);
+    const float4 vhi = W.velhi[i], vlo = W.vello[i];
+    Acc<R> Dv[M * D], Gnu[D];
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        int tj = c.type[j];
+        if (tj == VIRTUAL) continue;
+        R r[D], rr2 = R(0);
+        pair_r<D, R>(c, W, j, xi, hfi, lfi, r);
+#pragma unroll
+        for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        const R fac = -dw / rr, Vj = vol_at<R>(W, j);
+        R kw[M];
+        er_weights<D, R>(r, rr2, fac, kw);
+        R vij[D];
+        if constexpr (MIXED) {
+            float vf[D];
+            if (tj == FLUID) {
+                hilo_diff<D>(W.velhi[j], W.vello[j], vhi, vlo, vf);
+            } else {
+                vf[0] = -(vhi.x + vlo.x);
+                if (D == 3) vf[1] = -(vhi.y + vlo.y);
+                vf[D - 1] = -(vhi.z + vlo.z);
+            }
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) vij[cc] = vf[cc];
+        } else {
+            double vj[3] = {0.0, 0.0, 0.0};
+            if (tj == FLUID) load_vel<D>(c, j, vj);
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) vij[cc] = (R)(vj[cc] - vi[cc]);
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) Dv[a * D + cc].add(Vj * kw[a] * vij[cc]);
+        if (P.smag) {
+            double nuj = tj == FLUID ? W.nu[j] : P.nu_k;
+            R dn = (R)(nuj - nui);
+#pragma unroll
+            for (int K = 0; K < D; ++K) Gnu[K].add(Vj * dn * fac * r[K]);
+        }
+    }
+    double ct[M];
+    ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
+    double acc[D];
+    {
+        double gnh[D], gn[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            double s = 0.0;
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + i] * (double)Gnu[L2].val();
+            gnh[K] = s;
+        }
+        jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gnh, gn);
+        double G[D * D];  // G[I*D + cc] = d v_cc / d x_I
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double gh[D], g[D];
+#pragma unroll
+            for (int K = 0; K < D; ++K) gh[K] = W.gv[(int64_t)(cc * D + K) * cap + i];
+            jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gh, g);
+#pragma unroll
+            for (int I = 0; I < D; ++I) G[I * D + cc] = g[I];
+        }
+        const double c0i = c.c0[i];
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double lap = c0i * W.gv[(int64_t)(cc * D + (D - 1)) * cap + i];
+#pragma unroll
+            for (int a = 0; a < M; ++a) lap += ct[a] * (double)Dv[a * D + cc].val();
+            double term = 0.0;
+#pragma unroll
+            for (int J2 = 0; J2 < D; ++J2) term += (G[cc * D + J2] + G[J2 * D + cc]) * gn[J2];
+            double g = cc == D - 1 ? -P.g : 0.0;
+            acc[cc] = nui * lap + term + g;
+            W.acc[(int64_t)cc * cap + i] = acc[cc];
+            W.vstar[(int64_t)cc * cap + i] = vi[cc] + P.dt * acc[cc];
+        }
+        double vs[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) vs[cc] = W.vstar[(int64_t)cc * cap + i];
+        float4 lo;
+        W.vshi[i] = f4_hilo_split(vs[0], D == 3 ? vs[1] : 0.0, vs[D - 1], lo);
+        W.vslo[i] = lo;
+    }
+    if (W.fs[i]) {
+        W.pcnt[i] = -1;
+        return;
+    }
+    R ctr[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) ctr[a] = (R)ct[a];
+    const R c0r = (R)c.c0[i];
+    double diag = 0.0, wallrhs = 0.0;
+    double pi_[3];
+    load_phys<D>(c, i, pi_);
+    int pc = 0;
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        int tj = c.type[j];
+        if (tj == VIRTUAL) continue;
+        R r[D], rr2 = R(0);
+        pair_r<D, R>(c, W, j, xi, hfi, lfi, r);
+#pragma unroll
+        for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        const R fac = -dw / rr;
+        R kw[M], gz = R(0), sk = R(0);
+        er_weights<D, R>(r, rr2, fac, kw);
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) gz += L[(D - 1) * D + L2] * fac * r[L2];
+#pragma unroll
+        for (int a = 0; a < M; ++a) sk += ctr[a] * kw[a];
+        double aij = (double)(vol_at<R>(W, j) * (c0r * gz + sk));
+        if (tj == FLUID) {
+            diag -= aij;
+            if (!W.fs[j]) {
+                const int64_t q = ell_at<ell_group<D>()>(pc, i, cap);
+                W.pcol[q] = j;
+                if (P.precision == VCT_MIXED) W.pvalf[q] = (float)aij;
+                else W.pval[q] = aij;
+                ++pc;
+            }
+        } else {  // wall: p_ij = rho r_ij . f_i (Eq. PNC)
+            double pj[3], s2 = 0.0;
+            load_phys<D>(c, j, pj);
+#pragma unroll
+            for (int K = 0; K < D; ++K) s2 += (pj[K] - pi_[K]) * acc[K];
+            wallrhs += aij * P.rho * s2;
+        }
+    }
+    W.pcnt[i] = pc;
+    W.diag[i] = diag;
+    W.wallrhs[i] = wallrhs;
+    atomicAdd((unsigned long long *)&W.counts[0], 1ull);
+    atomicAdd((unsigned long long *)&W.counts[1], (unsigned long long)pc);
+}
+
 void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor,
                   cudaStream_t st)
 {
     unsigned g = (unsigned)((n + 127) / 128);
+    if (P.operators == 1 && predictor) {
+        if (P.dim == 2) {
+            if (P.precision == VCT_MIXED) k_pass2_isph<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            else k_pass2_isph<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        } else {
+            if (P.precision == VCT_MIXED) k_pass2_isph<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            else k_pass2_isph<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        }
+        return;
+    }
     if (P.dim == 2) {
         if (P.precision == VCT_MIXED) k_pass2<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n, predictor);
         else k_pass2<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n, predictor);
@@ -1579,6 +1782,9 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned nblocks, int32_t *statu
             if (++spins > limit) {
                 ok = 0;
                 atomicExch(status + 2, 1);
+                // also the call's error code: the steps queued after this one become
+                // no-ops and the caller's state is not written back
+                set_error(status, VCT_ERR_TIMEOUT, -1);
                 break;
             }
         }
@@ -3255,7 +3461,11 @@ int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njob
 // ---------------------------------------------------------------------------
 // a9: corrector and position update (Eqs. VCT_predictor, VCT_update)
 // ---------------------------------------------------------------------------
-template <int D, typename R>
+// SUM: the summation pressure gradient of Eq. (gra_sum) (ISPH), rho constant:
+// <grad^ p>+_i = sum_j V_j (p_j + p_i) grad w_ij = 2 p_i sum_j V_j grad w_ij +
+// sum_j V_j p_ij grad w_ij (both sums kept apart; combined in FP64); else the
+// corrected gradient of Eq. (gra_1st).
+template <int D, typename R, bool SUM = false>
 __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, int n)
 {
     if (step_failed(W.status)) return;
@@ -3270,7 +3480,7 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
 #pragma unroll
     for (int cc = 0; cc < D; ++cc) acci[cc] = W.acc[(int64_t)cc * cap + i];
     const double p_i = W.pcnt[i] >= 0 ? W.kx[i] : 0.0;
-    Acc<R> G[D];
+    Acc<R> G[D], Gs[SUM ? D : 1];
     const R inv_l = (R)P.inv_l, ad = (R)P.ad;
     const int cnt = W.nbr_cnt[i];
     for (int k = 0; k < cnt; ++k) {
@@ -3294,16 +3504,25 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
             for (int K = 0; K < D; ++K) s += (pj[K] - pi_[K]) * acci[K];
             pij = P.rho * s;
         }
-        R e = vol_at<R>(W, j) * (R)pij * (-dw / rr);
+        const R vf = vol_at<R>(W, j) * (-dw / rr);
+        R e = vf * (R)pij;
 #pragma unroll
         for (int K = 0; K < D; ++K) G[K].add(e * r[K]);
+        if constexpr (SUM) {
+#pragma unroll
+            for (int K = 0; K < D; ++K) Gs[K].add(vf * r[K]);
+        }
     }
     double gh[D], g[D];
 #pragma unroll
     for (int K = 0; K < D; ++K) {
         double s = 0.0;
+        if constexpr (SUM) {
+            s = (double)G[K].val() + 2.0 * p_i * (double)Gs[K].val();
+        } else {
 #pragma unroll
-        for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + i] * (double)G[L2].val();
+            for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + i] * (double)G[L2].val();
+        }
         gh[K] = s;
     }
     jac_apply<D>(c.J[i], c.sx[i], c.sy[i], gh, g);
@@ -3333,6 +3552,16 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
 {
     unsigned g = (unsigned)((n + 127) / 128);
+    if (P.operators == 1) {
+        if (P.dim == 2) {
+            if (P.precision == VCT_MIXED) k_corrector<2, float, true><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            else k_corrector<2, double, true><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        } else {
+            if (P.precision == VCT_MIXED) k_corrector<3, float, true><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            else k_corrector<3, double, true><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        }
+        return;
+    }
     if (P.dim == 2) {
         if (P.precision == VCT_MIXED) k_corrector<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
         else k_corrector<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
@@ -3784,6 +4013,14 @@ __global__ void __launch_bounds__(128) k_sph2_field(DevParams P, const Part c, W
                 for (int L2 = 0; L2 < D; ++L2) s += L[K * D + L2] * gw[L2];
                 rg += r[K] * s;
             }
+            if (P.operators == 1) {   // ISPH: D_a = sum_j V_j k_a(r_ij) phi_ij (Eq. sec_0th)
+                R kw[M];
+                er_weights<D, R>(r, rr2, fac, kw);
+                R e0 = (R)vol_of(P, c, j) * (R)(f[c.orig[j]] - fi);
+#pragma unroll
+                for (int a = 0; a < M; ++a) b[a].add(e0 * kw[a]);
+                continue;
+            }
             R VF = (R)vol_of(P, c, j) * rg / (rr2 * rr2), q[M];
             qvec<D, R>(r, q);
             // phi_ij - r_ij . <grad phi>_i formed in FP64 (cancellation), summed in R
@@ -3796,9 +4033,11 @@ __global__ void __launch_bounds__(128) k_sph2_field(DevParams P, const Part c, W
         for (int k = 0; k < M * M; ++k) A[k] = (double)Mm[k].val();
 #pragma unroll
         for (int a = 0; a < M; ++a) bb[a] = (double)b[a].val();
-        if (!lu_solve<M, 1>(A, bb)) set_error(W.status, VCT_ERR_SINGULAR, i);
+        if (P.operators != 1) {
+            if (!lu_solve<M, 1>(A, bb)) set_error(W.status, VCT_ERR_SINGULAR, i);
 #pragma unroll
-        for (int a = 0; a < M; ++a) bb[a] *= 2.0;   // D = 2 M^-1 b
+            for (int a = 0; a < M; ++a) bb[a] *= 2.0;   // D = 2 M^-1 b
+        }
         if (grad)
             for (int K = 0; K < D; ++K) grad[((int64_t)cc * D + K) * n + o] = g[K];
         if (d2)

@@ -287,9 +287,13 @@ def solitary_wave(amplitude, depth, x0, g):
 
 def still_water_bf(d0=0.01, L=1.0, H=0.2, seed=0, jitter=0.1, precision=0, **kw):
     """2-D BF-SPH still water over a 1:10 slope, mean depth 0.2 m:
-    h(x) = 0.1 (x - 0.5), so the depth runs 0.25 m -> 0.15 m."""
+    h(x) = 0.1 (x - 0.5), so the depth runs 0.25 m -> 0.15 m.  Particle
+    regularisation on, as in every simulation of Sec. 4 (without it the
+    jittered tank's motion grows until the run fails near step 85, in the
+    oracle and the CUDA path alike)."""
     bathy = Bathymetry(h0=-0.05 * (L / 1.0), slope_x=0.1)
     prm = dict(d0=d0, H=H, H_hat=H, dt=1.0e-3, precision=precision)
+    prm.update(REGULARISATION)
     prm.update(kw)
     return build_tank("still_water_bf", 2, "BF", 1.0, bathy, prm, L, seed=seed, jitter=jitter)
 
@@ -378,6 +382,27 @@ def ensemble(n_scen=64, seed=2, precision=1, jitter=0.0, **kw):
                               surface=lambda x, y: 0.5 + eta(x), velocity=vel, seed=seed + s,
                               jitter=jitter))
     return out
+
+
+def efficiency_tank(kind, precision=1, **kw):
+    """The hydrostatic tank of the BF / BFE / sigma efficiency comparison
+    (Sec. 4.4.1, Table fig:s4_s_time), with a stated stand-in for the bottom of
+    the missing figure: 1 m long, still-water level H = 0.2 m, bottom
+    h(x) = 0.12 x + 0.01 (1 - cos(2 pi x / 0.5)) -- a slope plus a sine, depth
+    0.2 m at x = 0 and 0.08 m at the shallowest point x = 1 m.  The models share
+    the vertical spacing at the shallowest point (0.2 cm): BF with d0 = 0.2 cm,
+    BFE with d0 = 0.5 cm and alpha = 2.5, sigma with d0 = 0.5 cm and
+    H = H^ = 0.2 m (alpha = 1 at the deepest point, 2.5 at the shallowest).
+    Regular lattice, hydrostatic start, dt = 5e-4 s, particle regularisation on
+    (Sec. 4)."""
+    bathy = Bathymetry(slope_x=0.12, h0=0.01, cos_amp=-0.01, cos_len=0.5)
+    d0 = 0.002 if kind == "BF" else 0.005
+    aspect = 2.5 if kind == "BFE" else 1.0
+    prm = dict(d0=d0, H=0.2, H_hat=0.2 * aspect if kind != "SIGMA" else 0.2, dt=5.0e-4,
+               precision=precision, alpha_min=1.0, alpha_max=2.5)
+    prm.update(REGULARISATION)
+    prm.update(kw)
+    return build_tank(f"efficiency_{kind.lower()}", 2, kind, aspect, bathy, prm, 1.0, jitter=0.0)
 
 
 def small_tank(dim=2, kind="BF", L=0.3, W=0.1, H=0.1, d0=0.01, seed=0, aspect=1.0,

@@ -48,7 +48,7 @@ class vct_params(C.Structure):
         ("volume_mode", C.c_int32), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("max_neighbours", C.c_int32), ("preconditioner", C.c_int32),
         ("ops_shift", C.c_double), ("ds_overlap", C.c_double), ("xsph_eps", C.c_double),
-        ("spin_limit", C.c_int64)]
+        ("spin_limit", C.c_int64), ("operators", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class vct_state(C.Structure):
@@ -179,6 +179,7 @@ def make_params(sc, **over):
     for k in ("ops_shift", "ds_overlap", "xsph_eps"):
         setattr(P, k, float(p.get(k, 0.0)))
     P.spin_limit = int(p.get("spin_limit", 0))
+    P.operators = int(p.get("operators", 0))
     return P
 
 

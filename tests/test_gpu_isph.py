@@ -1,0 +1,78 @@
+"""The ISPH operator set on the GPU (Table tab:case_names, row ISPH): 0th-order
+second derivatives of Espanol & Revenga (Eq. sec_0th) in the viscous term and
+the pressure equation, summation pressure gradient (Eq. gra_sum) in the
+corrector, first-order velocity divergence.
+
+  * the second derivatives (sph2_derivatives of a context with operators = 1)
+    against the oracle's, FP64 and mixed;
+  * one step through vct_step_probe against the oracle's ISPH step (same
+    checks as the ISPH(2) step parity);
+  * the paper's hydrostatic comparison (Sec. 4.1, Fig. s4_e_l2): E-map tanks
+    of aspect 0.5 to 2.5, regular lattice, hydrostatic start, 200 steps; the
+    relative L2 pressure error of ISPH(2) is below ISPH's at every aspect.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2607_28872_b300 import scenarios as S
+
+from test_gpu_parity import SMALL, _fields, _probe_compare, rel, report
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vct():
+    from paper_2607_28872_b300 import vct as V
+    V.load_library()
+    return V
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_isph_second_derivatives(vct, name, make, precision, tol):
+    import torch
+    sc = make()
+    sc.params.update(precision=precision, operators=1)
+    phi = _fields(sc)
+    solver = vct.Solver(sc)
+    g, d2, lap = solver.sph2_derivatives(vct.DeviceState(sc), torch.tensor(phi, device="cuda"))
+    og, od2, olap = O.sph2_derivatives(sc, phi)
+    f = sc.type == S.FLUID
+    g, d2, lap = g.cpu().numpy(), d2.cpu().numpy(), lap.cpu().numpy()
+    for c in range(phi.shape[0]):
+        assert report(f"isph {name} p{precision} grad{c}", rel(g[c][:, f], og[c][:, f]), tol)
+        assert report(f"isph {name} p{precision} d2{c}", rel(d2[c][:, f], od2[c][:, f]), tol)
+        assert report(f"isph {name} p{precision} lap{c}", rel(lap[c][f], olap[c][f]), tol)
+
+
+@pytest.mark.parametrize("precision,tol,band", [(0, 1e-12, 1e-9), (1, 1e-5, 1e-5)],
+                         ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name,make", [SMALL[0], SMALL[1], SMALL[3]],
+                         ids=[SMALL[0][0], SMALL[1][0], SMALL[3][0]])
+def test_isph_step_parity(vct, name, make, precision, tol, band):
+    sc = make()
+    sc.params["operators"] = 1
+    _probe_compare(vct, sc, precision, tol, band, "isph-" + name)
+
+
+def test_hydrostatic_error_isph_vs_isph2(vct):
+    errs = {}
+    for aspect in (0.5, 1.5, 2.5):
+        for ops in (0, 1):
+            sc = S.small_tank(dim=2, kind="E", L=0.5, H=0.25, d0=0.01, jitter=0.0, aspect=aspect,
+                              bathy=S.Bathymetry(), precision=1, operators=ops,
+                              **S.REGULARISATION)
+            s = vct.Solver(sc)
+            st = vct.DeviceState(sc)
+            s.vct_step(st, 200)
+            g = st.numpy()
+            _, info = O.step(sc, probe=True, max_iter=1)     # free-surface flags of the start
+            f = (sc.type == S.FLUID) & (info["fs"] == 0)
+            hyd = sc.params["rho"] * sc.params["g"] * (sc.params["H"] - g["z"])
+            errs[(aspect, ops)] = np.linalg.norm((g["p"] - hyd)[f]) / np.linalg.norm(hyd[f])
+        print(f"PARITY hydrostatic aspect {aspect}: e_L2 ISPH(2) {errs[(aspect, 0)]:.3e} "
+              f"ISPH {errs[(aspect, 1)]:.3e}")
+    for aspect in (0.5, 1.5, 2.5):
+        assert errs[(aspect, 0)] < errs[(aspect, 1)], errs

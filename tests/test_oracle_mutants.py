@@ -22,6 +22,7 @@ SRC = os.path.join(ROOT, "oracle", "vct_oracle.c")
 PINS = "tests/test_oracle_pins.py"
 PRED = "tests/test_oracle_predictor_pins.py"
 REG = "tests/test_oracle_regularise.py"
+ISPH = "tests/test_oracle_isph_pins.py"
 
 # (name, original snippet, planted snippet, pin files or test ids that must fail)
 MUTANTS = [
@@ -58,6 +59,14 @@ MUTANTS = [
      [PRED]),
     ("Jbar/J inverted", "S->jbar[i] / W.met[7 * i];", "W.met[7 * i] / S->jbar[i];", [PRED]),
     ("PNC sign", "pij = P->rho * s;", "pij = -P->rho * s;", [PINS]),
+    # ISPH operator set (Eqs. sec_0th, gra_sum)
+    ("E-R constant", "c = d == 2 ? 4.0 : 5.0", "c = d == 2 ? 5.0 : 5.0", [ISPH]),
+    ("E-R drops delta", "k[0] = f * (c * r[0] * r[0] / rr2 - 1.0);",
+     "k[0] = f * (c * r[0] * r[0] / rr2);", [ISPH]),
+    ("E-R cross undoubled", "k[2] = 2.0 * f * c * r[0] * r[1] / rr2;", "k[2] = f * c * r[0] * r[1] / rr2;",
+     [ISPH]),
+    ("summation as a difference", "g[K] += pp[k].V * (f[pp[k].j] + f[i]) * pp[k].gw[K];",
+     "g[K] += pp[k].V * (f[pp[k].j] - f[i]) * pp[k].gw[K];", [ISPH]),
     # regularisation (Sec. 4.1, restated methods)
     ("DS fluid share", "double mu = S->type[j] == ORC_FLUID ? 0.5 : 1.0;",
      "double mu = S->type[j] == ORC_FLUID ? 1.0 : 1.0;", [REG]),

@@ -75,8 +75,8 @@ def test_noalloc_count_only_and_cell_limit():
         assert rc == V.VCT_OK, V.vct_strerror(rc)
         assert nnz == rcol.size
         assert np.array_equal(row.cpu().numpy(), rrow)
-    # 0.024 m cells over a 10 m x 1 m box: 418 x 42 > 32768 cells
+    # 0.024 m cells over a 20.1 m x 1.1 m box: 838 x 46 = 38,548 > 32,768 cells
     row = torch.zeros(sc.n + 1, dtype=torch.int64, device="cuda")
     rc, _ = V.vct_build_neighbours_noalloc(sc, st, row, None, box_lo=(-0.1, 0.0, -0.1),
-                                           box_hi=(10.0, 0.0, 1.0))
+                                           box_hi=(20.0, 0.0, 1.0))
     assert rc == V.VCT_ERR_CAPACITY
