@@ -254,7 +254,12 @@ def build_tank(name, dim, kind, aspect, bathy, params, L, W=0.0, surface=None,
         u[:nf], v[:nf], w[:nf] = fu, fv, fw
     p = np.zeros(n)
     p[:nf] = np.maximum(prm["rho"] * prm["g"] * (top_f - fz), 0.0)
-    jbar = np.zeros(n)  # <= 0: each solver initialises Jbar = J at its first step
+    # Jbar carries each particle's initial volume (V_i = V0 J_i / Jbar_i, Sec. 3.6):
+    # a fluid particle's lattice cell is d0^(d-1) x its column's layer spacing, so
+    # Jbar0 = J0 * d0 / spacing (= J0 on an exact d0 lattice); walls and virtual
+    # particles sit on the exact lattice (<= 0: the solver sets Jbar = J there).
+    jbar = np.zeros(n)
+    jbar[:nf] = a_f * d0 / sp
 
     zmax = float(wzh.max() if wzh.size else 0.0)
     if box_top_margin is None:

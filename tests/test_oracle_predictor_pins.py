@@ -235,9 +235,10 @@ def test_ppe_rhs_divergence_of_linear_vstar():
 
 def test_ppe_rhs_stabilisation_source():
     """The same linear field with gamma = 100 dt: the right side gains
-    gamma (rho - rho^_i)/dt^2 (BF: Jbar = J), with rho^_i = rho sum_j V0 w_ij
-    (self term included, all particle types) summed here by brute force from
-    the kernel values.  A sign flip or a dropped self term fails."""
+    gamma (rho Jbar_i/J_i - rho^_i)/dt^2 (BF: J = 1, Jbar from the state), with
+    rho^_i = rho sum_j V0 w_ij (self term included, all particle types) summed
+    here by brute force from the kernel values.  A sign flip or a dropped self
+    term fails."""
     sc, A = _linear_velocity_tank(100.0)
     xh, met, row, col = _csr(sc)
     _, info = O.step(sc, probe=True)
@@ -255,8 +256,9 @@ def test_ppe_rhs_stabilisation_source():
         rho_hat[i] = rho * V0 * w.sum()            # includes j = i (r = 0)
     dt = sc.params["dt"]
     gamma = 100.0 * dt
-    ref = rho / dt * np.trace(A) + gamma * (rho - rho_hat[sel]) / dt ** 2
-    assert np.abs(rho - rho_hat[sel]).max() > 1.0    # the jitter makes the source non-trivial
+    target = rho * np.where(sc.jbar > 0, sc.jbar, 1.0)[sel] / met[sel, 0]
+    ref = rho / dt * np.trace(A) + gamma * (target - rho_hat[sel]) / dt ** 2
+    assert np.abs(target - rho_hat[sel]).max() > 1.0    # the jitter makes the source non-trivial
     assert np.allclose(info["ppe_b"][sel], ref, rtol=1e-10, atol=1e-9 * np.abs(ref).max())
 
 
