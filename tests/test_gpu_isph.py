@@ -8,8 +8,11 @@ corrector, first-order velocity divergence.
   * one step through vct_step_probe against the oracle's ISPH step (same
     checks as the ISPH(2) step parity);
   * the paper's hydrostatic comparison (Sec. 4.1, Fig. s4_e_l2): E-map tanks
-    of aspect 0.5 to 2.5, regular lattice, hydrostatic start, 200 steps; the
-    relative L2 pressure error of ISPH(2) is below ISPH's at every aspect.
+    of aspect 0.5 to 2.5, regular lattice, hydrostatic start, 100 steps; the
+    relative L2 pressure error of ISPH(2) is below ISPH's at every aspect (an
+    ISPH run that breaks down -- a singular correction matrix after its
+    particles disorder -- counts as an unbounded error; the paper reports
+    ISPH's spurious velocities reaching 30 cm/s).
 """
 import numpy as np
 import pytest
@@ -66,7 +69,12 @@ def test_hydrostatic_error_isph_vs_isph2(vct):
                               **S.REGULARISATION)
             s = vct.Solver(sc)
             st = vct.DeviceState(sc)
-            s.vct_step(st, 200)
+            try:
+                s.vct_step(st, 100)
+            except vct.VCTError as e:
+                assert ops == 1, e                     # ISPH(2) must not break down
+                errs[(aspect, ops)] = np.inf
+                continue
             g = st.numpy()
             _, info = O.step(sc, probe=True, max_iter=1)     # free-surface flags of the start
             f = (sc.type == S.FLUID) & (info["fs"] == 0)
