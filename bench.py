@@ -96,6 +96,8 @@ WORKLOADS = {
     "beach_bfe_3d_slice": ("3-D BFE solitary wave, 8 x 1.6 m slice of the 1:20 beach (depth 1 -> 0.6 m), "
                            "aspect 4, d0=0.043 m (profiling size)"),
     "ensemble": "sigma-SPH ensemble, particle counts log-uniform 5e3-2e5 (seed 2), 4 bumps each",
+    "dam_break_3d": ("3-D sigma-SPH dam break, bottom 0.1 x + 0.02 cos(2 pi x / 0.2) m, projected basin "
+                     "25 x 20 x 10 cm, H = 15 cm, H^ = 10 cm, d0 = 0.25 cm, dt = 1e-4 s, column x < 8 cm"),
     "efficiency": ("hydrostatic 1 m tank, H = 0.2 m, bottom 0.12 x + 0.01 (1 - cos(2 pi x / 0.5)): "
                    "BF d0 = 0.2 cm, BFE d0 = 0.5 cm alpha 2.5, sigma d0 = 0.5 cm alpha 1-2.5"),
     "adjoint": ("2-D sigma channel 10 m, flat 0.5 m + 16 random Gaussian bumps (seed 1), d0=0.01 m, "
@@ -122,6 +124,8 @@ def workload(precision=1, name="sigma_solitary"):
         return S.beach_bfe_3d(precision=precision)
     if name == "beach_bfe_3d_slice":
         return S.beach_bfe_3d(L=8.0, W=1.6, precision=precision)
+    if name == "dam_break_3d":
+        return S.dam_break_sigma_3d(precision=precision)
     return S.solitary_sigma(precision=precision)
 
 

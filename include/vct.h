@@ -156,7 +156,12 @@ typedef struct {
      * sph2_derivatives returns the set's second derivatives.  The backward
      * entries differentiate the ISPH(2) set only.  Other values: VCT_ERR_ARG. */
     int32_t operators;
-    int32_t reserved2;
+    /* Wall condition for the velocity (Sec. 3.5): 0 = no-slip, wall particles at
+     * rest; 1 = free-slip, a wall particle carries (I - 2 n n) v_wall with
+     * v_wall the SPH interpolation of its fluid neighbours' velocity and n the
+     * outer unit normal in physical space (J^T of the projected normal, which
+     * points to the virtual particles outside).  Other values: VCT_ERR_ARG. */
+    int32_t wall_slip;
 } vct_params;
 
 /* Particle state, caller order, DEVICE arrays of n entries (host arrays for
@@ -211,6 +216,9 @@ typedef struct {
                              * evaluations can differ, and parity checks pass one
                              * side's flags to the other so both solve the same
                              * system.  NULL: the step's own flags. */
+    double *vwall;          /* velocity each wall particle carries in the step's sums,
+                             * dim x n component-major (free-slip walls; 0 under
+                             * no-slip and for other particles) */
 } vct_probe;
 
 typedef struct vct_ctx vct_ctx;

@@ -32,7 +32,7 @@ class OrcParams(C.Structure):
         (k, C.c_int) for k in ("ppe_max_iter", "smagorinsky", "volume_mode", "neighbour_mode",
                                "smoothing_mode", "pad_")] + [
         (k, C.c_double) for k in ("ops_shift", "ds_overlap", "xsph_eps")] + [
-        ("operators", C.c_int), ("pad2_", C.c_int)]
+        ("operators", C.c_int), ("wall_slip", C.c_int)]
 
 
 class OrcState(C.Structure):
@@ -47,7 +47,7 @@ class OrcProbe(C.Structure):
                 ("vstar", C.POINTER(C.c_double)), ("ppe_b", C.POINTER(C.c_double)),
                 ("x_test", C.POINTER(C.c_double)), ("ppe_Ax", C.POINTER(C.c_double)),
                 ("jbar_used", C.POINTER(C.c_double)), ("n_iter", C.c_int), ("pad_", C.c_int),
-                ("resid", C.c_double)]
+                ("resid", C.c_double), ("vwall", C.POINTER(C.c_double))]
 
 
 def lib():
@@ -134,6 +134,7 @@ def make_params(sc, neighbour_mode=1, smoothing_mode=1, rtol=1e-13, max_iter=200
     for k in ("ops_shift", "ds_overlap", "xsph_eps"):
         setattr(P, k, float(p.get(k, 0.0)))
     P.operators = int(p.get("operators", 0))
+    P.wall_slip = int(p.get("wall_slip", 0))
     return P
 
 
@@ -313,14 +314,14 @@ def step(sc, state=None, nsteps=1, probe=False, x_test=None, **over):
     if probe:
         info = dict(fs=np.zeros(n, dtype=np.int32), rho_hat=np.zeros(n), nu=np.zeros(n),
                     lam_min=np.zeros(n), vstar=np.zeros((d, n)), ppe_b=np.zeros(n),
-                    jbar_used=np.zeros(n))
+                    jbar_used=np.zeros(n), vwall=np.zeros((d, n)))
         xt = keep.f64(x_test) if x_test is not None else None
         if xt is not None:
             info["ppe_Ax"] = np.zeros(n)
         pr = OrcProbe(info["fs"].ctypes.data_as(C.POINTER(C.c_int32)), _dp(info["rho_hat"]),
                       _dp(info["nu"]), _dp(info["lam_min"]), _dp(info["vstar"]),
                       _dp(info["ppe_b"]), _dp(xt), _dp(info.get("ppe_Ax")),
-                      _dp(info["jbar_used"]), 0, 0, 0.0)
+                      _dp(info["jbar_used"]), 0, 0, 0.0, _dp(info["vwall"]))
     S = st.struct()
     iters = C.c_int(0)
     rc = lib().orc_step(C.byref(P), C.byref(B), C.byref(S), nsteps,

@@ -76,7 +76,7 @@ typedef struct {
                       *    pressure gradient (Eq. gra_1st); 1: ISPH -- 0th-order second
                       *    derivatives (Eq. sec_0th), summation pressure gradient (Eq. gra_sum);
                       *    velocity divergence 1st-order in both (Table tab:case_names) */
-    int pad2_;
+    int wall_slip;   /* 0: no-slip walls, v = 0; 1: free-slip, v = (I - 2 n n) v_wall (Sec. 3.5) */
 } orc_params;
 
 typedef struct {
@@ -95,6 +95,7 @@ typedef struct {
     double *jbar_used;      /* Jbar after the smoothing of the last step */
     int n_iter, pad_;
     double resid;
+    double *vwall;          /* d x n: velocity each wall particle carries (0 elsewhere) */
 } orc_probe;
 
 /* ------------------------------------------------------------------------ */
@@ -561,6 +562,7 @@ typedef struct {
     /* pass 2 */
     double *LU;         /* n x m*m (M_i), factorised copy kept for the operator */
     double *vstar, *acc;/* n x d */
+    double *vw;         /* n x 3: free-slip wall velocities (NULL: no-slip, walls at rest) */
     int64_t *pstart;    /* pair cache offsets (n+1) */
     pair_t *pairs;
     int64_t npairs;
@@ -571,7 +573,7 @@ static void work_free(work_t *W)
     free(W->xh); free(W->xp); free(W->met); free(W->row_ptr); free(W->col);
     free(W->L); free(W->Ct); free(W->gv); free(W->G); free(W->rho_hat); free(W->lam);
     free(W->nu); free(W->fs); free(W->LU); free(W->vstar); free(W->acc);
-    free(W->pstart); free(W->pairs);
+    free(W->pstart); free(W->pairs); free(W->vw);
     memset(W, 0, sizeof *W);
 }
 
@@ -586,6 +588,13 @@ static double vel(const orc_state *S, int dim, int i, int c)
 {
     if (dim == 2) return c == 0 ? S->u[i] : S->w[i];
     return c == 0 ? S->u[i] : (c == 1 ? S->v[i] : S->w[i]);
+}
+
+/* Velocity a wall particle carries in the sums of its fluid neighbours:
+ * 0 under no-slip (Sec. 3.5, v = v_wall = 0), the free-slip value otherwise. */
+static double wall_vel(const work_t *W, int j, int c)
+{
+    return W->vw ? W->vw[3 * (size_t)j + c] : 0.0;
 }
 
 /* Map + metric + neighbours for the current positions. */
@@ -663,6 +672,55 @@ static void stage_smoothing(const orc_params *P, const orc_state *S, const work_
     free(ratio);
 }
 
+/* Free-slip wall velocities (Sec. 3.5): v_j = (I - 2 n n) v_wall,j.  v_wall,j is
+ * the SPH (Shepard) interpolation of the fluid velocity at wall particle j,
+ * sum_k V_k v_k w_jk / sum_k V_k w_jk over its fluid neighbours (0 without
+ * any).  n is the outer unit normal in physical space: the projected normal
+ * n^ points from j towards the virtual particles outside the wall,
+ * n^ ~ sum_{k virtual} V0 grad w_jk, and transforms as a gradient,
+ * n ~ J^T n^ (the transpose of the Jacobian of Eq. jacobi): on the bottom
+ * z^ = 0 this is the surface normal (h_x, h_y, -1)/|.|, which the paper
+ * builds from rotations by arctan(dh/dx), arctan(dh/dy). */
+static void stage_wall_velocity(const orc_params *P, const orc_state *S, work_t *W)
+{
+    int n = S->n, d = W->dim;
+    W->vw = (double *)calloc((size_t)n * 3 + 1, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int j = 0; j < n; ++j) {
+        if (S->type[j] != ORC_WALL) continue;
+        double num[3] = {0}, den = 0.0, nh[3] = {0};
+        for (int64_t q = W->row_ptr[j]; q < W->row_ptr[j + 1]; ++q) {
+            int k = W->col[q], tk = S->type[k];
+            double r[3], rr2 = 0.0;
+            for (int K = 0; K < d; ++K) {
+                r[K] = W->xh[d * k + K] - W->xh[d * j + K];
+                rr2 += r[K] * r[K];
+            }
+            double rr = sqrt(rr2);
+            if (tk == ORC_FLUID) {
+                double wv = vol_j(P, W, S, k) * kern_w(rr, W->l, d);
+                for (int c = 0; c < d; ++c) num[c] += wv * vel(S, d, k, c);
+                den += wv;
+            } else if (tk == ORC_VIRTUAL && rr > 0.0) {
+                double dw = kern_dw(rr, W->l, d);
+                for (int K = 0; K < d; ++K) nh[K] += W->V0 * (-dw / rr) * r[K];
+            }
+        }
+        if (!(den > 0.0)) continue;
+        double v[3] = {0}, Jm[9], nn[3] = {0}, nl = 0.0, vn = 0.0;
+        for (int c = 0; c < d; ++c) v[c] = num[c] / den;
+        jac(d, W->met + 7 * (size_t)j, Jm);
+        for (int I = 0; I < d; ++I) {
+            for (int K = 0; K < d; ++K) nn[I] += Jm[I * d + K] * nh[K];
+            nl += nn[I] * nn[I];
+        }
+        nl = sqrt(nl);
+        if (nl > 0.0)
+            for (int I = 0; I < d; ++I) { nn[I] /= nl; vn += nn[I] * v[I]; }
+        for (int c = 0; c < d; ++c) W->vw[3 * (size_t)j + c] = v[c] - 2.0 * vn * nn[c];
+    }
+}
+
 /* Pass 1 for one fluid particle: B_i, L_i, <grad^ v>, C~_i, rho^_i, free-surface
  * flag, eddy viscosity. */
 static int pass1_one(const orc_params *P, const orc_state *S, work_t *W, int i)
@@ -695,7 +753,7 @@ static int pass1_one(const orc_params *P, const orc_state *S, work_t *W, int i)
         for (int K = 0; K < d; ++K)
             for (int L2 = 0; L2 < d; ++L2) B[K * d + L2] += Vj * gw[K] * r[L2];
         for (int c = 0; c < d; ++c) {
-            double vij = (tj == ORC_FLUID ? vel(S, d, j, c) : 0.0) - vel(S, d, i, c);
+            double vij = (tj == ORC_FLUID ? vel(S, d, j, c) : wall_vel(W, j, c)) - vel(S, d, i, c);
             for (int K = 0; K < d; ++K) Gv[c * d + K] += Vj * vij * gw[K];
         }
         for (int K = 0; K < d; ++K)
@@ -846,7 +904,8 @@ static int pass2_one(const orc_params *P, const orc_state *S, work_t *W, int i, 
             for (int c = 0; c < m; ++c) M[a * m + c] += pr->V * pr->F * pr->q[a] * pv[c];
         if (do_pred) {
             for (int c = 0; c < d; ++c) {
-                double vij = (tj == ORC_FLUID ? vel(S, d, j, c) : 0.0) - vel(S, d, i, c), rgv = 0.0;
+                double vij = (tj == ORC_FLUID ? vel(S, d, j, c) : wall_vel(W, j, c)) - vel(S, d, i, c),
+                       rgv = 0.0;
                 for (int K = 0; K < d; ++K) rgv += pr->r[K] * gv[c * d + K];
                 for (int a = 0; a < m; ++a) bv[a * d + c] += pr->V * pr->F * pr->q[a] * (vij - rgv);
             }
@@ -867,7 +926,8 @@ static int pass2_one(const orc_params *P, const orc_state *S, work_t *W, int i, 
         for (int k = 0; k < np; ++k) {
             const pair_t *pr = pp + k;
             for (int c = 0; c < d; ++c) {
-                double vij = (pr->tj == ORC_FLUID ? vel(S, d, pr->j, c) : 0.0) - vel(S, d, i, c);
+                double vij = (pr->tj == ORC_FLUID ? vel(S, d, pr->j, c) : wall_vel(W, pr->j, c)) -
+                             vel(S, d, i, c);
                 for (int a = 0; a < m; ++a) bv[a * d + c] += 0.5 * pr->V * pr->k0[a] * vij;
             }
         }
@@ -1419,6 +1479,7 @@ int orc_step(const orc_params *P, const orc_bathy *b, orc_state *S, int nsteps, 
         if (P->map_kind == ORC_MAP_SIGMA && P->volume_mode == 2)
             stage_smoothing(P, S, &W, P->smoothing_mode);
         alloc_work(&W, n, 1);
+        if (P->wall_slip) stage_wall_velocity(P, S, &W);
         rc = run_pass1(P, S, &W);
         if (!rc) rc = run_pass2(P, S, &W, 1);
         if (rc) { work_free(&W); break; }
@@ -1441,7 +1502,7 @@ int orc_step(const orc_params *P, const orc_bathy *b, orc_state *S, int nsteps, 
                     /* a wall neighbour carries v_wall + dt f_i: the intermediate velocity
                      * it would have under the acceleration that Eq. (PNC) assumes */
                     double vj = pp[k].tj == ORC_FLUID ? W.vstar[d * pp[k].j + c]
-                                                      : P->dt * W.acc[d * i + c];
+                                                      : wall_vel(&W, pp[k].j, c) + P->dt * W.acc[d * i + c];
                     double vij = vj - W.vstar[d * i + c];
                     for (int K = 0; K < d; ++K) X[c * d + K] += pp[k].V * vij * pp[k].gt[K];
                 }
@@ -1476,6 +1537,10 @@ int orc_step(const orc_params *P, const orc_bathy *b, orc_state *S, int nsteps, 
                         pr->vstar[(size_t)c * n + i] = S->type[i] == ORC_FLUID ? W.vstar[d * i + c] : 0.0;
             if (pr->ppe_b) for (int i = 0; i < n; ++i) pr->ppe_b[i] = bl[i];
             if (pr->jbar_used) for (int i = 0; i < n; ++i) pr->jbar_used[i] = S->jbar[i];
+            if (pr->vwall)
+                for (int c = 0; c < d; ++c)
+                    for (int i = 0; i < n; ++i)
+                        pr->vwall[(size_t)c * n + i] = S->type[i] == ORC_WALL ? wall_vel(&W, i, c) : 0.0;
             if (pr->x_test && pr->ppe_Ax) {
                 double *xt = calloc((size_t)n + 1, 8);
                 for (int i = 0; i < n; ++i) xt[i] = unk[i] ? pr->x_test[i] : 0.0;

@@ -248,6 +248,10 @@ void step_pre(vct_ctx *c, int64_t n, const vct_probe *pr = nullptr)
         c->launches += 1;
     }
     cudaMemsetAsync(c->W.counts, 0, 2 * sizeof(int64_t), c->st);
+    if (c->P.slip) {
+        launch_wall_velocity(c->P, cur(c), c->W, n, c->st);
+        c->launches += 1;
+    }
     { StageTimer t(c, VCT_STAGE_PASS1); launch_pass1(c->P, cur(c), c->W, n, c->st); }
     if (pr && pr->fs_in) {
         launch_force_fs(cur(c), c->W, n, pr->fs_in, c->st);
@@ -659,6 +663,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     if (prm->volume_mode < 0 || prm->volume_mode > 2) return VCT_ERR_ARG;
     if (prm->spin_limit < 0) return VCT_ERR_ARG;
     if (prm->operators != 0 && prm->operators != 1) return VCT_ERR_ARG;
+    if (prm->wall_slip != 0 && prm->wall_slip != 1) return VCT_ERR_ARG;
     // the background cell grid, validated before anything is allocated
     int grid_nc[3];
     int64_t ncell = 1;
@@ -713,6 +718,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     P.ds_overlap = prm->ds_overlap;
     P.xsph_eps = prm->xsph_eps;
     P.operators = prm->operators;
+    P.slip = prm->wall_slip;
     P.pguess = getenv("VCT_PGUESS") ? atoi(getenv("VCT_PGUESS")) : 2;   // 0: none, 1: linear
     P.inner_floor = prm->precision == VCT_MIXED ? 1e-4 : 0.0;
     if (prm->precision == VCT_MIXED && getenv("VCT_INNER_FLOOR")) P.inner_floor = atof(getenv("VCT_INNER_FLOOR"));

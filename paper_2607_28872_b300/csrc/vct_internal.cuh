@@ -25,7 +25,7 @@ struct DevParams {
     int dim, kind, smag, volume_mode;
     int n_gauss, max_nbr, precision, max_iter;
     int nc[3];                // cells per axis (x, y, z); 2-D: y = 1
-    int pad1;
+    int slip;                 // 1: free-slip walls (wall particles carry a mirrored velocity)
     double aspect, rho, nu_k, g, dt, d0, l, inv_l, re, re2, V0, ad;
     double ops_shift, ds_overlap, xsph_eps;   // particle regularisation (0: off)
     int pguess;               // order of the pressure extrapolation of the initial guess
@@ -215,6 +215,8 @@ void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int nc
 void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct_probe &pr,
                       cudaStream_t st);
 void launch_force_fs(Part cur, Work W, int64_t n, const int32_t *fs_in, cudaStream_t st);
+// free-slip wall velocities (Sec. 3.5) into the sorted state's wall particles
+void launch_wall_velocity(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 void launch_probe_ax(const DevParams &P, Part cur, Work W, int64_t n, const double *x_test,
                      double *out, cudaStream_t st);
 int krylov_coop_blocks(int precision, int dim);

@@ -996,7 +996,7 @@ __global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams 
         }
         R vij[D];
         if constexpr (sizeof(R) == sizeof(float)) {   // mixed: hi/lo differences
-            if (tj == FLUID) {
+            if (tj == FLUID || P.slip) {   // a free-slip wall carries its own velocity
                 hilo_diff<D>(W.velhi[j], W.vello[j], vhi, vlo, vij);
             } else {
                 vij[0] = -(vhi.x + vlo.x);
@@ -1005,7 +1005,7 @@ __global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams 
             }
         } else {
             double vj[3] = {0.0, 0.0, 0.0};
-            if (tj == FLUID) load_vel<D>(c, j, vj);
+            if (tj == FLUID || P.slip) load_vel<D>(c, j, vj);
 #pragma unroll
             for (int cc = 0; cc < D; ++cc) vij[cc] = (R)(vj[cc] - vi[cc]);
         }
@@ -1254,7 +1254,7 @@ __global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams 
             // ~5u |v_ij| / |e| in e, which only enters the viscous term.
             if constexpr (MIXED) {
                 float vij[D];
-                if (tj == FLUID) {
+                if (tj == FLUID || P.slip) {
                     hilo_diff<D>(W.velhi[j], W.vello[j], vhi, vlo, vij);
                 } else {
                     vij[0] = -(vhi.x + vlo.x);
@@ -1272,7 +1272,7 @@ __global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams 
                 }
             } else {
                 double vj[3] = {0.0, 0.0, 0.0};
-                if (tj == FLUID) load_vel<D>(c, j, vj);
+                if (tj == FLUID || P.slip) load_vel<D>(c, j, vj);
 #pragma unroll
                 for (int cc = 0; cc < D; ++cc) {
                     double rgv = 0.0;
@@ -1476,7 +1476,7 @@ __global__ void __launch_bounds__(128) k_pass2_isph(DevParams P, const Part c, W
         R vij[D];
         if constexpr (MIXED) {
             float vf[D];
-            if (tj == FLUID) {
+            if (tj == FLUID || P.slip) {
                 hilo_diff<D>(W.velhi[j], W.vello[j], vhi, vlo, vf);
             } else {
                 vf[0] = -(vhi.x + vlo.x);
@@ -1487,7 +1487,7 @@ __global__ void __launch_bounds__(128) k_pass2_isph(DevParams P, const Part c, W
             for (int cc = 0; cc < D; ++cc) vij[cc] = vf[cc];
         } else {
             double vj[3] = {0.0, 0.0, 0.0};
-            if (tj == FLUID) load_vel<D>(c, j, vj);
+            if (tj == FLUID || P.slip) load_vel<D>(c, j, vj);
 #pragma unroll
             for (int cc = 0; cc < D; ++cc) vij[cc] = (R)(vj[cc] - vi[cc]);
         }
@@ -1673,6 +1673,12 @@ __global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, 
         if (tj != FLUID) {
 #pragma unroll
             for (int cc = 0; cc < D; ++cc) dv[cc] = wall_dv[cc];
+            if (P.slip) {   // a free-slip wall carries its velocity + dt f_i
+                double vj[3] = {0.0, 0.0, 0.0};
+                load_vel<D>(c, j, vj);
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) dv[cc] += (R)vj[cc];
+            }
         } else if constexpr (sizeof(R) == sizeof(float)) {   // mixed: hi/lo differences
             hilo_diff<D>(W.vshi[j], W.vslo[j], vshi_i, vslo_i, dv);
         } else {
@@ -4489,6 +4495,91 @@ __global__ void k_probe_out(DevParams P, const Part c, Work W, int n, vct_probe 
             pr.vstar[(int64_t)cc * n + o] = fl ? W.vstar[(int64_t)cc * W.cap + i] : 0.0;
     if (pr.ppe_b) pr.ppe_b[o] = W.bvec[i];
     if (pr.jbar_used) pr.jbar_used[o] = c.jbar[i];
+    if (pr.vwall) {
+        const bool wl = c.type[i] == WALL && P.slip;
+        const double vv[3] = {c.u[i], P.dim == 3 ? c.v[i] : 0.0, c.w[i]};
+        for (int cc = 0; cc < P.dim; ++cc)
+            pr.vwall[(int64_t)cc * n + o] = wl ? vv[cc == P.dim - 1 ? 2 : cc] : 0.0;
+    }
+}
+
+// Free-slip walls (Sec. 3.5): wall particle j carries v_j = (I - 2 n n) v_wall,j,
+// v_wall,j = sum_k V_k v_k w_jk / sum_k V_k w_jk over its fluid neighbours (SPH
+// interpolation; 0 without any), n the outer unit normal in physical space: the
+// projected normal n^ ~ sum_{k virtual} V0 grad w_jk (towards the virtual
+// particles outside the wall) transformed as a gradient, n ~ J^T n^ (on the
+// bottom: the surface normal the paper builds from rotations by arctan h_x,
+// arctan h_y).  Written into the sorted state (FP64 and the hi/lo FP32 copy) of
+// wall particles, where pass 1, pass 2 and the right side read it.
+template <int D>
+__global__ void __launch_bounds__(128) k_wall_velocity(DevParams P, Part c, Work W, int n)
+{
+    if (step_failed(W.status)) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || c.type[j] != WALL) return;
+    const int64_t cap = W.cap;
+    double xj[3];
+    load_hat<D>(c, j, xj);
+    double num[3] = {0.0, 0.0, 0.0}, den = 0.0, nh[3] = {0.0, 0.0, 0.0};
+    const int cnt = W.nbr_cnt[j];
+    for (int q = 0; q < cnt; ++q) {
+        const int k = W.nbr[(int64_t)q * cap + j];
+        const int tk = c.type[k];
+        if (tk == WALL) continue;
+        double xk[3], r[3], rr2 = 0.0;
+        load_hat<D>(c, k, xk);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xk[K] - xj[K];
+            rr2 += r[K] * r[K];
+        }
+        const double rr = sqrt(rr2);
+        double w, dw;
+        kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+        if (tk == FLUID) {
+            double vk[3];
+            load_vel<D>(c, k, vk);
+            const double wv = vol_of(P, c, k) * w;
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) num[cc] += wv * vk[cc];
+            den += wv;
+        } else if (rr > 0.0) {
+#pragma unroll
+            for (int K = 0; K < D; ++K) nh[K] += P.V0 * (-dw / rr) * r[K];
+        }
+    }
+    double v[3] = {0.0, 0.0, 0.0};
+    if (den > 0.0) {
+        double nn[D], nl = 0.0, vn = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) v[cc] = num[cc] / den;
+        jac_apply<D>(c.J[j], c.sx[j], c.sy[j], nh, nn);
+#pragma unroll
+        for (int I = 0; I < D; ++I) nl += nn[I] * nn[I];
+        nl = sqrt(nl);
+        if (nl > 0.0) {
+#pragma unroll
+            for (int I = 0; I < D; ++I) {
+                nn[I] /= nl;
+                vn += nn[I] * v[I];
+            }
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) v[cc] -= 2.0 * vn * nn[cc];
+        }
+    }
+    c.u[j] = v[0];
+    if (D == 3) c.v[j] = v[1];
+    c.w[j] = v[D - 1];
+    float4 lo;
+    W.velhi[j] = f4_hilo_split(v[0], D == 3 ? v[1] : 0.0, v[D - 1], lo);
+    W.vello[j] = lo;
+}
+
+void launch_wall_velocity(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) k_wall_velocity<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    else k_wall_velocity<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
 }
 
 // Parity probes only: replace the free-surface flags pass 1 decided by the

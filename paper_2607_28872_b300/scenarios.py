@@ -410,6 +410,24 @@ def efficiency_tank(kind, precision=1, **kw):
     return build_tank(f"efficiency_{kind.lower()}", 2, kind, aspect, bathy, prm, 1.0, jitter=0.0)
 
 
+def dam_break_sigma_3d(d0=0.0025, x_dam=0.08, precision=1, **kw):
+    """3-D sigma-SPH dam break (Sec. 4.4.3): bottom h(x, y) = 0.1 x + 2 cos(2 pi x / 20)
+    in cm (here h = 0.1 x + 0.02 cos(2 pi x / 0.2) m), projected domain 25 x 20 x 10 cm,
+    H = 15 cm, H^ = 10 cm (alpha = H^/(H - h), 0.63-0.91), d0 = 0.25 cm, dt = 1e-4 s,
+    Condition C with C_V = 100 dt.  The figure with the dam's position is missing:
+    the water column stands at the still-water level H over 0 <= x < x_dam (8 cm),
+    the rest of the basin is dry.  Particle regularisation on (Sec. 4)."""
+    bathy = Bathymetry(slope_x=0.1, cos_amp=0.02, cos_len=0.2)
+    prm = dict(d0=d0, H=0.15, H_hat=0.10, dt=1.0e-4, precision=precision,
+               alpha_min=0.5, alpha_max=1.5, volume_mode=2)
+    prm.update(REGULARISATION)
+    prm.update(kw)
+    H = prm["H"]
+    surf = lambda x, y: np.where(np.asarray(x) < x_dam, H, bathy.height(x, y))  # noqa: E731
+    return build_tank("dam_break_sigma_3d", 3, "SIGMA", 1.0, bathy, prm, 0.25, 0.20,
+                      surface=surf, jitter=0.0)
+
+
 def small_tank(dim=2, kind="BF", L=0.3, W=0.1, H=0.1, d0=0.01, seed=0, aspect=1.0,
                bathy=None, jitter=0.1, with_wave=False, precision=0, **kw):
     """A few-thousand-particle tank for parity and edge-case tests."""

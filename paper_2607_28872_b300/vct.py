@@ -48,7 +48,7 @@ class vct_params(C.Structure):
         ("volume_mode", C.c_int32), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("max_neighbours", C.c_int32), ("preconditioner", C.c_int32),
         ("ops_shift", C.c_double), ("ds_overlap", C.c_double), ("xsph_eps", C.c_double),
-        ("spin_limit", C.c_int64), ("operators", C.c_int32), ("reserved2", C.c_int32)]
+        ("spin_limit", C.c_int64), ("operators", C.c_int32), ("wall_slip", C.c_int32)]
 
 
 class vct_state(C.Structure):
@@ -70,7 +70,7 @@ STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "r
 
 class vct_probe(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("fs", "rho_hat", "nu", "lam_min", "vstar", "ppe_b",
-                                          "x_test", "ppe_Ax", "jbar_used", "fs_in")]
+                                          "x_test", "ppe_Ax", "jbar_used", "fs_in", "vwall")]
 
 
 _lib = None
@@ -180,6 +180,7 @@ def make_params(sc, **over):
         setattr(P, k, float(p.get(k, 0.0)))
     P.spin_limit = int(p.get("spin_limit", 0))
     P.operators = int(p.get("operators", 0))
+    P.wall_slip = int(p.get("wall_slip", 0))
     return P
 
 
@@ -420,7 +421,8 @@ class Solver:
                    lam_min=torch.zeros(n, dtype=torch.float64, device="cuda"),
                    vstar=torch.zeros((d, n), dtype=torch.float64, device="cuda"),
                    ppe_b=torch.zeros(n, dtype=torch.float64, device="cuda"),
-                   jbar_used=torch.zeros(n, dtype=torch.float64, device="cuda"))
+                   jbar_used=torch.zeros(n, dtype=torch.float64, device="cuda"),
+                   vwall=torch.zeros((d, n), dtype=torch.float64, device="cuda"))
         if x_test is not None:
             out["ppe_Ax"] = torch.zeros(n, dtype=torch.float64, device="cuda")
             x_test = x_test.contiguous()
@@ -429,7 +431,7 @@ class Solver:
         pr = vct_probe(_ptr(out["fs"]), _ptr(out["rho_hat"]), _ptr(out["nu"]),
                        _ptr(out["lam_min"]), _ptr(out["vstar"]), _ptr(out["ppe_b"]),
                        _ptr(x_test), _ptr(out.get("ppe_Ax")), _ptr(out["jbar_used"]),
-                       _ptr(fs_in))
+                       _ptr(fs_in), _ptr(out["vwall"]))
         s = state.struct()
         st = vct_stats()
         self._check(self.lib.vct_step_probe(self.ctx, C.byref(s), C.byref(pr), C.byref(st)),

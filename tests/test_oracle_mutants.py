@@ -23,6 +23,7 @@ PINS = "tests/test_oracle_pins.py"
 PRED = "tests/test_oracle_predictor_pins.py"
 REG = "tests/test_oracle_regularise.py"
 ISPH = "tests/test_oracle_isph_pins.py"
+SLIP = "tests/test_oracle_free_slip.py"
 
 # (name, original snippet, planted snippet, pin files or test ids that must fail)
 MUTANTS = [
@@ -67,6 +68,11 @@ MUTANTS = [
      [ISPH]),
     ("summation as a difference", "g[K] += pp[k].V * (f[pp[k].j] + f[i]) * pp[k].gw[K];",
      "g[K] += pp[k].V * (f[pp[k].j] - f[i]) * pp[k].gw[K];", [ISPH]),
+    # free-slip walls (Sec. 3.5)
+    ("slip normal not transformed", "for (int K = 0; K < d; ++K) nn[I] += Jm[I * d + K] * nh[K];",
+     "for (int K = 0; K < d; ++K) nn[I] += (I == K ? 1.0 : 0.0) * nh[K];", [SLIP]),
+    ("slip projects instead of reflecting", "W->vw[3 * (size_t)j + c] = v[c] - 2.0 * vn * nn[c];",
+     "W->vw[3 * (size_t)j + c] = v[c] - vn * nn[c];", [SLIP]),
     # regularisation (Sec. 4.1, restated methods)
     ("DS fluid share", "double mu = S->type[j] == ORC_FLUID ? 0.5 : 1.0;",
      "double mu = S->type[j] == ORC_FLUID ? 1.0 : 1.0;", [REG]),
