@@ -54,6 +54,10 @@
 #define ORC_FLUID 0
 #define ORC_WALL 1
 #define ORC_VIRTUAL 2
+/* smallest eigenvalue of B_i (all types, symmetrised) below which a fluid
+ * particle is isolated: 1 with a full kernel support, ~0.5 at a flat free
+ * surface, ~0.1 at a corner of the fluid */
+#define ORC_LAM_ISOLATED 0.05
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_CAPACITY = 2, ORC_ERR_SINGULAR = 3,
        ORC_ERR_NOCONV = 4, ORC_ERR_NONFINITE = 5 };
@@ -768,7 +772,11 @@ static int pass1_one(const orc_params *P, const orc_state *S, work_t *W, int i)
     rho += W->V0 * kern_w(0.0, W->l, d);          /* self term, j = i in S_i */
     W->rho_hat[i] = P->rho * rho;
     double *L = W->L + (size_t)9 * i;
-    if (invert_dxd(d, B, L)) return ORC_ERR_SINGULAR;
+    int iso = 0;
+    if (invert_dxd(d, B, L)) {
+        iso = 1;
+        for (int k = 0; k < 9; ++k) L[k] = 0.0;
+    }
     double *gv = W->gv + (size_t)9 * i, *Ct = W->Ct + (size_t)18 * i;
     for (int c = 0; c < d; ++c)
         for (int K = 0; K < d; ++K) {
@@ -828,7 +836,17 @@ static int pass1_one(const orc_params *P, const orc_state *S, work_t *W, int i)
             }
         }
     }
-    W->fs[i] = fs;
+    /* Isolated particle (a splash or droplet): B_i not invertible, or the
+     * smallest eigenvalue of B over all particle types below ORC_LAM_ISOLATED.
+     * It is a free-surface particle without corrected derivatives: L_i = 0, so
+     * its gradients, SPH(2) second derivatives and pressure gradient vanish and
+     * it moves under gravity alone.  Flag value 2. */
+    if (!iso && lam < ORC_LAM_ISOLATED) iso = 1;
+    if (iso) {
+        for (int k = 0; k < 9; ++k) { L[k] = 0.0; gv[k] = 0.0; }
+        for (int k = 0; k < 18; ++k) Ct[k] = 0.0;
+    }
+    W->fs[i] = iso ? 2 : fs;
     /* physical velocity gradient G[I][c] = sum_K J[I][K] d v_c / d x^_K (Eq. grad_VCT) */
     double Jm[9], *G = W->G + (size_t)9 * i;
     jac(d, W->met + 7 * i, Jm);
@@ -920,7 +938,10 @@ static int pass2_one(const orc_params *P, const orc_state *S, work_t *W, int i, 
     if (!do_pred) return ORC_OK;
     double Mc[36];
     memcpy(Mc, M, sizeof Mc);
-    if (P->operators == 1) {
+    if (W->fs[i] == 2) {
+        /* isolated: no second derivatives */
+        for (int k = 0; k < m * d; ++k) bv[k] = 0.0;
+    } else if (P->operators == 1) {
         /* ISPH: D_c = the 0th-order second derivatives of v_c, stored as b = D/2 */
         for (int k = 0; k < m * d; ++k) bv[k] = 0.0;
         for (int k = 0; k < np; ++k) {
@@ -932,7 +953,10 @@ static int pass2_one(const orc_params *P, const orc_state *S, work_t *W, int i, 
             }
         }
     } else if (gauss_solve(m, Mc, d, bv)) {
-        return ORC_ERR_SINGULAR;
+        /* a free-surface particle with too few neighbours for M_i loses its
+         * viscous term; anywhere else a singular M_i is an error */
+        if (!W->fs[i]) return ORC_ERR_SINGULAR;
+        for (int k = 0; k < m * d; ++k) bv[k] = 0.0;
     }
     /* D_c = 2 M^-1 b_c (SPH(2)) or the 0th-order second derivatives (ISPH) */
     double ct[6], Jm[9], gnh[3], gn[3];

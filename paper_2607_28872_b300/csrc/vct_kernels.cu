@@ -273,8 +273,53 @@ __device__ bool inv_small(const double *B, double *L)
     }
 }
 
-// Smallest eigenvalue of a symmetric D x D matrix (closed forms; trigonometric
-// form of the cubic's roots in 3-D).
+// Smallest eigenvalue of B_i (over all particle types, symmetrised) below which
+// a fluid particle counts as isolated; 1 for a full kernel support, ~0.5 at a
+// flat free surface, ~0.1 at a corner of the fluid.
+constexpr double LAM_ISOLATED = 0.05;
+
+// Smallest eigenvalue of a symmetric 3 x 3 matrix by cyclic Jacobi rotations
+// (each rotation zeroes one off-diagonal entry; the diagonal converges to the
+// eigenvalues with an absolute error of a few eps |S|).
+__device__ double sym_lam_min_jacobi3(const double *S)
+{
+    double A[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A[k] = S[k];
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        const double dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+        if (off <= 1e-36 * dia || off < 1e-300) break;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = p + 1; q < 3; ++q) {
+                const double apq = A[p * 3 + q];
+                if (apq == 0.0) continue;
+                const double theta = 0.5 * (A[q * 3 + q] - A[p * 3 + p]) / apq;
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double akp = A[k * 3 + p], akq = A[k * 3 + q];
+                    A[k * 3 + p] = cs * akp - sn * akq;
+                    A[k * 3 + q] = sn * akp + cs * akq;
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double apk = A[p * 3 + k], aqk = A[q * 3 + k];
+                    A[p * 3 + k] = cs * apk - sn * aqk;
+                    A[q * 3 + k] = sn * apk + cs * aqk;
+                }
+            }
+    }
+    return fmin(A[0], fmin(A[4], A[8]));
+}
+
+// Smallest eigenvalue of a symmetric D x D matrix: closed form in 2-D; in 3-D
+// the trigonometric form of the cubic's roots, except where the two smallest
+// eigenvalues cluster (the cosine argument near 1, where acos loses half the
+// digits): there cyclic Jacobi rotations.
 template <int D>
 __device__ double sym_lam_min(const double *S)
 {
@@ -292,6 +337,7 @@ __device__ double sym_lam_min(const double *S)
         double B0 = a * ip, B4 = b * ip, B8 = c * ip, B1 = S[1] * ip, B2 = S[2] * ip, B5 = S[5] * ip;
         double det = B0 * (B4 * B8 - B5 * B5) - B1 * (B1 * B8 - B5 * B2) + B2 * (B1 * B5 - B4 * B2);
         double r = fmin(1.0, fmax(-1.0, 0.5 * det));
+        if (r > 0.5) return sym_lam_min_jacobi3(S);
         double phi = acos(r) / 3.0;
         return q + 2.0 * p * cos(phi + 2.0 * 3.14159265358979323846 / 3.0);
     }
@@ -1027,8 +1073,9 @@ __global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams 
     double Bd[D * D], L[D * D];
 #pragma unroll
     for (int k = 0; k < D * D; ++k) Bd[k] = (double)B[k].val();
+    bool iso = false;   // isolated: no correction, no derivatives (see below)
     if (!inv_small<D>(Bd, L)) {
-        set_error(W.status, VCT_ERR_SINGULAR, i);
+        iso = true;
         for (int k = 0; k < D * D; ++k) L[k] = 0.0;
     }
 #pragma unroll
@@ -1111,7 +1158,23 @@ __global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams 
             }
         }
     }
-    W.fs[i] = fs;
+    // An isolated particle (a splash or droplet: B_i not invertible, or the
+    // smallest eigenvalue of B over all particle types below LAM_ISOLATED) is a
+    // free-surface particle without corrected derivatives: L_i = 0, so its
+    // gradients, SPH(2) second derivatives and pressure gradient vanish and it
+    // moves under gravity alone until it has neighbours again.  Flag value 2.
+    if (!iso && lam < LAM_ISOLATED) iso = true;
+    if (iso) {
+#pragma unroll
+        for (int k = 0; k < D * D; ++k) {
+            W.L[(int64_t)k * cap + i] = 0.0;
+            W.gv[(int64_t)k * cap + i] = 0.0;
+            gv[k] = 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < D * M; ++k) W.Ct[(int64_t)k * cap + i] = 0.0;
+    }
+    W.fs[i] = iso ? 2 : fs;
     // Smagorinsky: nu_E = (C_s f_s r_e)^2 sqrt(2 S:S), S from G = J grad^ v
     double nue = 0.0;
     if (P.smag) {
@@ -1304,9 +1367,18 @@ __global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams 
         double Bv[M * D];
 #pragma unroll
         for (int k = 0; k < M * D; ++k) Bv[k] = (double)bv[k].val();
-        // M is factored once: D^v = 2 M^-1 b here, M^-T c~ for the pressure row below
-        if (!lu_factor<M>(Md, piv)) set_error(W.status, VCT_ERR_SINGULAR, i);
-        lu_apply<M, D>(Md, piv, Bv);
+        // M is factored once: D^v = 2 M^-1 b here, M^-T c~ for the pressure row below.
+        // An isolated particle has no second derivatives; a free-surface particle
+        // whose M_i cannot be factored (too few neighbours) loses its viscous
+        // term; anywhere else a singular M_i is an error.
+        const int fsi = W.fs[i];
+        bool ok = fsi != 2 && lu_factor<M>(Md, piv);
+        if (ok) lu_apply<M, D>(Md, piv, Bv);
+        else {
+            if (!fsi) set_error(W.status, VCT_ERR_SINGULAR, i);
+#pragma unroll
+            for (int k = 0; k < M * D; ++k) Bv[k] = 0.0;
+        }
         // physical grad nu = J L sum V (nu_j - nu_i) grad w
         double gnh[D], gn[D];
 #pragma unroll
@@ -1526,11 +1598,12 @@ __global__ void __launch_bounds__(128) k_pass2_isph(DevParams P, const Part c, W
             for (int I = 0; I < D; ++I) G[I * D + cc] = g[I];
         }
         const double c0i = c.c0[i];
+        const double dscale = W.fs[i] == 2 ? 0.0 : 1.0;   // isolated: no second derivatives
 #pragma unroll
         for (int cc = 0; cc < D; ++cc) {
             double lap = c0i * W.gv[(int64_t)(cc * D + (D - 1)) * cap + i];
 #pragma unroll
-            for (int a = 0; a < M; ++a) lap += ct[a] * (double)Dv[a * D + cc].val();
+            for (int a = 0; a < M; ++a) lap += dscale * ct[a] * (double)Dv[a * D + cc].val();
             double term = 0.0;
 #pragma unroll
             for (int J2 = 0; J2 < D; ++J2) term += (G[cc * D + J2] + G[J2 * D + cc]) * gn[J2];
@@ -4039,8 +4112,15 @@ __global__ void __launch_bounds__(128) k_sph2_field(DevParams P, const Part c, W
         for (int k = 0; k < M * M; ++k) A[k] = (double)Mm[k].val();
 #pragma unroll
         for (int a = 0; a < M; ++a) bb[a] = (double)b[a].val();
-        if (P.operators != 1) {
-            if (!lu_solve<M, 1>(A, bb)) set_error(W.status, VCT_ERR_SINGULAR, i);
+        if (W.fs[i] == 2) {   // isolated particle: no derivatives
+#pragma unroll
+            for (int a = 0; a < M; ++a) bb[a] = 0.0;
+        } else if (P.operators != 1) {
+            if (!lu_solve<M, 1>(A, bb)) {
+                if (!W.fs[i]) set_error(W.status, VCT_ERR_SINGULAR, i);
+#pragma unroll
+                for (int a = 0; a < M; ++a) bb[a] = 0.0;
+            }
 #pragma unroll
             for (int a = 0; a < M; ++a) bb[a] *= 2.0;   // D = 2 M^-1 b
         }
@@ -4589,7 +4669,8 @@ __global__ void k_force_fs(const Part c, Work W, int n, const int32_t *fs_in)
     if (step_failed(W.status)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || c.type[i] != FLUID) return;
-    W.fs[i] = fs_in[c.orig[i]] ? 1 : 0;
+    const int32_t v = fs_in[c.orig[i]];
+    W.fs[i] = v == 2 ? 2 : (v ? 1 : 0);
 }
 
 void launch_force_fs(Part cur, Work W, int64_t n, const int32_t *fs_in, cudaStream_t st)

@@ -231,7 +231,8 @@ def _probe_compare(vct, sc, precision, tol, band, name="case"):
     f = sc.type == S.FLUID
     lam = info["lam_min"]
     lo, hi = sc.params["lam_fs_lo"], sc.params["lam_fs_hi"]
-    clear = f & (np.abs(lam - lo) > band) & (np.abs(lam - hi) > band)
+    # thresholds: free surface lo / hi, isolated 0.05
+    clear = f & (np.abs(lam - lo) > band) & (np.abs(lam - hi) > band) & (np.abs(lam - 0.05) > band)
     assert np.array_equal(g["fs"][clear], info["fs"][clear])
     tied = f & ~clear
     if precision == 0:
