@@ -255,8 +255,16 @@ def _probe_compare(vct, sc, precision, tol, band, name="case"):
         assert np.array_equal(g["fs"], info["fs"])
     print(f"PARITY {tag} tied={int(tied.sum())} differing={int((g['fs'] != info['fs']).sum())} "
           f"forced={forced}")
-    # identical unknown set: the linear system itself, then the solve and the corrector
-    assert report(f"{tag} ppe_b", rel(g["ppe_b"], info["ppe_b"]), tol)
+    # identical unknown set: the linear system itself, then the solve and the corrector.
+    # The right side's stabilisation term gamma (rho Jbar/J - rho^)/dt^2 takes the
+    # difference of the target and the density estimate; in the mixed form rho^ is a
+    # compensated FP32 sum, exact to a few 2^-24 rho^, so a row's right side is held
+    # to tol |b|_max + (gamma/dt^2) 8 2^-24 rho^_i (the FP64 form: tol |b|_max).
+    bscale = np.abs(info["ppe_b"]).max()
+    gam = sc.params["gamma_over_dt"] * sc.params["dt"]
+    extra = (gam / sc.params["dt"] ** 2) * 8.0 * 2.0 ** -24 * info["rho_hat"] if precision else 0.0
+    bratio = (np.abs(g["ppe_b"] - info["ppe_b"]) / (tol * bscale + extra)).max()
+    assert report(f"{tag} ppe_b/bound", bratio, 1.0)
     assert report(f"{tag} ppe_Ax", rel(g["ppe_Ax"], info["ppe_Ax"]), tol)
     # The solve: the GPU pressure must solve the ORACLE's FP64 system with normwise
     # backward error eta = |A p - b| / (|A| |p| + |b|) within the form's tolerance
