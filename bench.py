@@ -546,6 +546,8 @@ def run_ours(args):
     # e2e: the host-buffer entry point, copies in and out inside the timed region
     e2e = None
     e2e_steps = min(args.steps, 20) if args.e2e_steps is None else args.e2e_steps
+    if horizon:   # one fresh run of the workload, within its horizon
+        e2e_steps = min(e2e_steps, horizon - 1)
     if rank == 0 and e2e_steps > 0:
         s2 = vct.Solver(sc)
         host = vct.HostState(sc, pin=True)
