@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-fp64-probe", action="store_true",
                     help="skip the per-field error of the mixed form against the FP64 form")
     ap.add_argument("--ensemble-size", type=int, default=64)
+    ap.add_argument("--tune", default=None, metavar="PATH",
+                    help="ensemble: run the schedule autotuner first and write its table to PATH")
+    ap.add_argument("--no-tuning", action="store_true",
+                    help="ensemble: run with the built-in schedule, not the tuned table")
     ap.add_argument("--horizon", type=int, default=None,
                     help="restart from the initial state every this many steps (default 150 "
                          "in 2-D, 15 in 3-D; 0 = never)")
@@ -245,6 +249,10 @@ def run_efficiency(args):
                       "config": {"workload": WORKLOADS["efficiency"]}, "models": rows}), flush=True)
 
 
+# schedule table of the ensemble (paper_2607_28872_b300/autotune.py), measured on a B300
+TUNING_TABLE = os.path.join(ROOT, "paper_2607_28872_b300", "tuning", "ensemble_b300.json")
+
+
 def run_ensemble(args):
     """Ensemble throughput through vct_batch_step (not the headline line)."""
     import torch
@@ -254,7 +262,18 @@ def run_ensemble(args):
         return
     scs = S.ensemble(n_scen=args.ensemble_size, precision=args.precision)
     nf = sum(sc.n_fluid for sc in scs)
-    solvers = [vct.Solver(sc) for sc in scs]
+    from paper_2607_28872_b300 import autotune
+    table, schedule = None, "built-in defaults"
+    if args.tune:
+        # the batch runs the large-system form above 75k particles in total
+        table = autotune.tune(scs, form=2)
+        autotune.save(table, args.tune)
+        schedule = f"autotuned now ({len(table)} size classes, written to {args.tune})"
+    elif not args.no_tuning and os.path.exists(TUNING_TABLE):
+        table = autotune.load(TUNING_TABLE)
+        schedule = f"autotuned table {os.path.relpath(TUNING_TABLE, ROOT)} ({len(table)} size classes)"
+    knobs = [autotune.tuned(sc, table) if table else {} for sc in scs]
+    solvers = [vct.Solver(sc, **kn) for sc, kn in zip(scs, knobs)]
     states = [vct.DeviceState(sc) for sc in scs]
     # every scenario is a wave with the 2-D wave's stable horizon: time at most 100 steps
     steps, warmup = min(args.steps, 100), max(args.warmup, 3)
@@ -308,6 +327,7 @@ def run_ensemble(args):
                       "krylov_iters_per_step": sum(s.krylov_iters_total for s in stats) / steps,
                       "gpu_launches": int(sum(s.kernel_launches for s in stats)),
                       "graph_steps": int(stats[0].graph_steps), "roofline": roof,
+                      "schedule": schedule,
                       "dtype": "f32+f64" if args.precision == 1 else "f64", "clocks": clk}),
           flush=True)
 

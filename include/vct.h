@@ -162,6 +162,22 @@ typedef struct {
      * outer unit normal in physical space (J^T of the projected normal, which
      * points to the virtual particles outside).  Other values: VCT_ERR_ARG. */
     int32_t wall_slip;
+    /* Schedule knobs (chosen per scenario size by the autotuner of the Python
+     * package; 0 = the built-in defaults).  They change how the step runs, not
+     * what it computes (the same neighbour sets, the same system, the same
+     * solution to the solver tolerance):
+     *   cell_over_re  edge of the background cells over r_e (>= 1; neighbour
+     *                 search visits the 3^dim adjacent cells; the multigrid's
+     *                 first coarse level is the cells)
+     *   mg_omega      Jacobi damping of the multigrid smoother on the particles
+     *   mg_kappa      scale of the coarse-grid correction
+     *   solve_form    1: small-system form (V-cycle inputs formed inside the
+     *                 products), 2: large-system form (staged rows), 0: by size
+     * cell_over_re in (0, 1), a negative value or a solve_form other than 0-2
+     * is VCT_ERR_ARG. */
+    double cell_over_re, mg_omega, mg_kappa;
+    int32_t solve_form;
+    int32_t reserved3;
 } vct_params;
 
 /* Particle state, caller order, DEVICE arrays of n entries (host arrays for

@@ -664,11 +664,15 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     if (prm->spin_limit < 0) return VCT_ERR_ARG;
     if (prm->operators != 0 && prm->operators != 1) return VCT_ERR_ARG;
     if (prm->wall_slip != 0 && prm->wall_slip != 1) return VCT_ERR_ARG;
+    if (!(prm->cell_over_re == 0.0 || prm->cell_over_re >= 1.0) || !(prm->mg_omega >= 0.0) ||
+        !(prm->mg_kappa >= 0.0) || prm->solve_form < 0 || prm->solve_form > 2)
+        return VCT_ERR_ARG;
     // the background cell grid, validated before anything is allocated
     int grid_nc[3];
     int64_t ncell = 1;
     {
-        vct_status gs = cell_grid(prm, prm->re_over_l * (prm->l_over_d0 * prm->d0),
+        vct_status gs = cell_grid(prm, (prm->cell_over_re > 0.0 ? prm->cell_over_re : 1.0) *
+                                           prm->re_over_l * (prm->l_over_d0 * prm->d0),
                                   (int64_t)INT32_MAX / 2, grid_nc, &ncell);
         if (gs != VCT_OK) return gs;
     }
@@ -722,7 +726,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     P.pguess = getenv("VCT_PGUESS") ? atoi(getenv("VCT_PGUESS")) : 2;   // 0: none, 1: linear
     P.inner_floor = prm->precision == VCT_MIXED ? 1e-4 : 0.0;
     if (prm->precision == VCT_MIXED && getenv("VCT_INNER_FLOOR")) P.inner_floor = atof(getenv("VCT_INNER_FLOOR"));
-    P.cell_h = P.re;
+    P.cell_h = (prm->cell_over_re > 0.0 ? prm->cell_over_re : 1.0) * P.re;
     P.inv_cell_h = 1.0 / P.cell_h;
     for (int k = 0; k < 3; ++k) {
         P.box_lo[k] = prm->box_lo[k];
@@ -895,6 +899,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         // blocks still fit on an SM (<= 110 KB each).
         // VCT_MG_FORM=fly|explicit overrides the size rule (tests cover both forms)
         M.fly = krylov_mg_fly_default(n, prm->dim) ? 1 : 0;
+        if (prm->solve_form) M.fly = prm->solve_form == 1 ? 1 : 0;
         if (const char *fm = getenv("VCT_MG_FORM")) {
             if (!strcmp(fm, "fly")) M.fly = 1;
             if (!strcmp(fm, "explicit")) M.fly = 0;
@@ -915,6 +920,8 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         // pay (2-D wave, per step: 8 sweeps 15.72 iterations / 2372 us, 2 sweeps
         // 15.68 / 2310, none 15.63 / 2285)
         M.coarse_sweeps = 0;
+        if (prm->mg_omega > 0.0) M.omega = (float)prm->mg_omega;
+        if (prm->mg_kappa > 0.0) M.kappa = (float)prm->mg_kappa;
         if (getenv("VCT_MG_OMEGA")) M.omega = (float)atof(getenv("VCT_MG_OMEGA"));
         if (getenv("VCT_MG_KAPPA")) M.kappa = (float)atof(getenv("VCT_MG_KAPPA"));
         M.kappa_c = M.kappa;

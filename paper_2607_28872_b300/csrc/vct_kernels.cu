@@ -4684,11 +4684,13 @@ void launch_probe_out(const DevParams &P, Part cur, Work W, int64_t n, const vct
     k_probe_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, cur, W, (int)n, pr);
 }
 
+// (After a failed step the pressure rows may never have been written: the
+// probe's A x then reads nothing from them and writes zeros.)
 __global__ void k_gather_masked(const Part c, Work W, int n, const double *xin, double *xs)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    xs[i] = W.pcnt[i] >= 0 ? xin[c.orig[i]] : 0.0;
+    xs[i] = !step_failed(W.status) && W.pcnt[i] >= 0 ? xin[c.orig[i]] : 0.0;
 }
 
 __global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double *out,
@@ -4696,7 +4698,7 @@ __global__ void k_spmv_out(const Part c, Work W, int n, const double *xs, double
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int pc = W.pcnt[i];
+    int pc = step_failed(W.status) ? -1 : W.pcnt[i];
     double y = 0.0;
     if (pc >= 0) {
         y = W.diag[i] * xs[i];

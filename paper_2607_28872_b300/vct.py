@@ -48,7 +48,9 @@ class vct_params(C.Structure):
         ("volume_mode", C.c_int32), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("max_neighbours", C.c_int32), ("preconditioner", C.c_int32),
         ("ops_shift", C.c_double), ("ds_overlap", C.c_double), ("xsph_eps", C.c_double),
-        ("spin_limit", C.c_int64), ("operators", C.c_int32), ("wall_slip", C.c_int32)]
+        ("spin_limit", C.c_int64), ("operators", C.c_int32), ("wall_slip", C.c_int32),
+        ("cell_over_re", C.c_double), ("mg_omega", C.c_double), ("mg_kappa", C.c_double),
+        ("solve_form", C.c_int32), ("reserved3", C.c_int32)]
 
 
 class vct_state(C.Structure):
@@ -181,6 +183,9 @@ def make_params(sc, **over):
     P.spin_limit = int(p.get("spin_limit", 0))
     P.operators = int(p.get("operators", 0))
     P.wall_slip = int(p.get("wall_slip", 0))
+    for k in ("cell_over_re", "mg_omega", "mg_kappa"):
+        setattr(P, k, float(p.get(k, 0.0)))
+    P.solve_form = int(p.get("solve_form", 0))
     return P
 
 

@@ -30,7 +30,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_structs_match_header_sizes():
     # vct_params: 2 ints + 18 doubles + 4 ints + 6 doubles + 2 ints + 3 doubles + 1 int64 + 2 ints
-    assert ctypes.sizeof(vct.vct_params) == 8 + 18 * 8 + 16 + 48 + 8 + 24 + 8 + 8
+    # + 3 doubles + 2 ints
+    assert ctypes.sizeof(vct.vct_params) == 8 + 18 * 8 + 16 + 48 + 8 + 24 + 8 + 8 + 24 + 8
     assert ctypes.sizeof(vct.vct_state) == 8 + 9 * 8
     assert ctypes.sizeof(vct.vct_stats) == 8 + 8 + 4 + 4 + 8 + 3 * 8 + 4 + 4
     assert ctypes.sizeof(vct.vct_bathymetry) == 5 * 8 + 8 + 4 * 8
