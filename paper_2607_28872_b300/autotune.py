@@ -33,8 +33,8 @@ KNOBS = ("cell_over_re", "mg_omega", "mg_kappa", "solve_form")
 def candidates(dim, form=0):
     """The schedule grid searched per size class."""
     cells = (1.0, 1.25)
-    omegas = (0.8, 0.85, 0.9) if dim == 2 else (0.65, 0.7, 0.75)
-    kappas = (1.2, 1.3, 1.4) if dim == 2 else (1.1, 1.2, 1.3)
+    omegas = (0.85, 0.9, 0.95) if dim == 2 else (0.65, 0.7, 0.75)
+    kappas = (1.3, 1.4, 1.5, 1.6) if dim == 2 else (1.1, 1.2, 1.3)
     return [dict(cell_over_re=c, mg_omega=w, mg_kappa=k, solve_form=form)
             for c, w, k in itertools.product(cells, omegas, kappas)]
 

@@ -25,7 +25,7 @@ def test_tuner_keeps_the_fastest_successful_candidate(tmp_path):
         seen.append((sc.n, knobs["cell_over_re"], knobs["mg_omega"], knobs["mg_kappa"]))
         if sc.n == 160000:
             return None                                   # every candidate fails there
-        if knobs["mg_kappa"] == 1.4:
+        if knobs["mg_kappa"] == 1.5:
             return None                                   # this knob fails everywhere
         # fastest: the larger cells for small systems, omega 0.85 everywhere
         t = 1.0 + abs(knobs["mg_omega"] - 0.85) * 10 + (0.0 if knobs["cell_over_re"] > 1 else 0.5)
@@ -37,9 +37,9 @@ def test_tuner_keeps_the_fastest_successful_candidate(tmp_path):
     assert reps == {5100, 41000, 160000}
     assert set(table) == {"d2_p1_n2^12", "d2_p1_n2^15"}       # the 2^17 class failed
     small = table["d2_p1_n2^12"]["knobs"]
-    assert small["mg_omega"] == 0.85 and small["mg_kappa"] != 1.4 and small["solve_form"] == 2
+    assert small["mg_omega"] == 0.85 and small["mg_kappa"] != 1.5 and small["solve_form"] == 2
     assert all(t["ms_per_step"] is None for t in table["d2_p1_n2^12"]["tried"]
-               if t["knobs"]["mg_kappa"] == 1.4)
+               if t["knobs"]["mg_kappa"] == 1.5)
     path = tmp_path / "t.json"
     A.save(table, path)
     again = A.load(path)
