@@ -297,7 +297,8 @@ def run_ensemble(args):
     nprof = 10
     solvers[0].vct_set_profiling(True)
     pst = vct.vct_batch_step(solvers, states, nprof)
-    k_ms, k_cnt = solvers[0].vct_stage_times()["krylov"]
+    stage_t = solvers[0].vct_stage_times()   # the batched launches of all scenarios
+    k_ms, k_cnt = stage_t["krylov"]
     solvers[0].vct_set_profiling(False)
     per_launch = 0.0
     for sc, s in zip(scs, pst):
@@ -327,6 +328,7 @@ def run_ensemble(args):
                       "krylov_iters_per_step": sum(s.krylov_iters_total for s in stats) / steps,
                       "gpu_launches": int(sum(s.kernel_launches for s in stats)),
                       "graph_steps": int(stats[0].graph_steps), "roofline": roof,
+                      "stage_ms_per_step": {k: v[0] / nprof for k, v in stage_t.items() if v[1]},
                       "schedule": schedule,
                       "dtype": "f32+f64" if args.precision == 1 else "f64", "clocks": clk}),
           flush=True)

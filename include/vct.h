@@ -433,21 +433,27 @@ vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct
  * dimension and precision, the scenarios run side by side (to the solver the
  * batch counts as one system: above 75k particles in total in 2-D, 30k in 3-D,
  * or with any large scenario, every solve uses the large-system form): each
- * queues its kernels on a stream of its own (created on first use, kept by
- * its context), and one cooperative launch on a stream the FIRST context
- * keeps for it solves all pressure systems at once, each on a share of the
- * grid in proportion to its particles; results then agree with vct_step to
- * the solver tolerance (the solves' partial sums are grouped differently),
- * and repeat bit for bit.  In this form, steps run in pairs from a CUDA graph:
- * the first call for a batch captures two steps (every scenario's kernels, the
- * batched solve and the events between the streams) and instantiates them
- * once; that call's and later calls' pairs (same contexts, particle counts
- * and buffer parity) are one graph launch each, an odd last step runs from
- * direct launches.  A changed batch is captured anew (the first context keeps
- * one graph).  Not with stage profiling on, nor with the environment variable
- * VCT_BATCH_NOGRAPH set; if a capture fails, the first context uses direct
- * launches from then on.  Graph and direct launches give identical results;
- * stats.graph_steps counts the replayed steps.
+ * stage of the step is ONE launch over all scenarios (every scenario on the
+ * blocks its own launch of the stage would take, with its own parameters and
+ * buffers), and one cooperative launch solves all pressure systems at once,
+ * each on a share of the grid in proportion to its particles, all on a
+ * stream the FIRST context keeps for it (each scenario's load and store run
+ * on a stream of its own, created on first use and kept by its context).
+ * Every stage but the solve computes exactly what the scenario's own
+ * launches compute; results agree with vct_step to the solver tolerance (the
+ * solves' partial sums are grouped differently), and repeat bit for bit.
+ * The batch's launches are counted in the first scenario's
+ * stats.kernel_launches (the others count their load and store).  In this
+ * form, steps run in pairs from a CUDA graph: the first call for a batch
+ * captures two steps and instantiates them once; that call's and later
+ * calls' pairs (same contexts, particle counts and buffer parity) are one
+ * graph launch each, an odd last step runs from direct launches.  A changed
+ * batch is captured anew (the first context keeps one graph).  Not with
+ * stage profiling on (the first context's stage times are then the batch's),
+ * nor with the environment variable VCT_BATCH_NOGRAPH set; if a capture
+ * fails, the first context uses direct launches from then on.  Graph and
+ * direct launches give identical results; stats.graph_steps counts the
+ * replayed steps.
  * Otherwise, or with the environment variable VCT_BATCH_SERIAL set, all
  * kernels are queued back to back on the first context's stream and each
  * result is bit-identical to vct_step on its own.  The call returns when all
@@ -470,8 +476,8 @@ vct_status vct_step_probe(vct_ctx *ctx, vct_state *state, const vct_probe *probe
  * elapsed device milliseconds per stage and the number of bracketed launches
  * (host arrays of VCT_NSTAGES).  Turning profiling on resets the totals.  Off
  * by default; when off no event is recorded.  In vct_batch_step side by side,
- * the first context's VCT_STAGE_KRYLOV times the one batched solve of all
- * scenarios (on its own stream), and no step is replayed from the graph. */
+ * the first context's stage times are those of the batched launches of all
+ * scenarios (on its batch stream), and no step is replayed from the graph. */
 vct_status vct_set_profiling(vct_ctx *ctx, int32_t on);
 vct_status vct_stage_times(vct_ctx *ctx, double *ms, int64_t *launches);
 

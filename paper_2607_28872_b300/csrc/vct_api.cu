@@ -41,6 +41,8 @@ struct vct_ctx {
     bool rows_list;            // a batch runs this scenario's solve in the large-system form
     FlyJob *jobs_dev;
     int jobs_cap;
+    unsigned char *plan_dev;   // (first context) the batched stages' job and block tables
+    size_t plan_cap;
     // (first context of a batch) two side-by-side batch steps captured as a CUDA
     // graph, the batch it was captured for, and each scenario's launches in it
     cudaGraphExec_t bgraph;
@@ -393,20 +395,48 @@ vct_status run_steps(vct_ctx *c, vct_state *s, int nsteps, const vct_probe *pr, 
     return finish(c, out, nsteps);
 }
 
-// Ensemble step with the scenarios side by side: every scenario queues its
-// kernels up to the pressure solve on its own stream; one cooperative launch
-// then solves all pressure systems at once, each on its own share of the grid
-// (blocks in proportion to its particles); the rest of each step runs again on
-// the scenarios' streams.  Eligible when every scenario uses the multigrid
-// solver with the same dimension and precision, and the grid holds a block per
-// scenario; otherwise returns VCT_ERR_ARG (the caller then queues the
-// scenarios one after another).  To the solver the batch is one system: when
-// it exceeds the small-system size in total, or any scenario is a large system,
-// every scenario's solve runs in the large-system form (vectors, staged rows,
-// L1 gathers, 16 KB of shared levels; VCT_BATCH_FORM=fly|explicit overrides
-// where it can).  The solves' partial
-// sums are grouped by the scenario's share of blocks, so results agree with
-// vct_step to the solver tolerance, not bit for bit.
+// One launch of a batched ensemble stage: the stage, its coarsening level
+// (BS_MG_COARSEN), its blocks in total, the offset of its block-start table,
+// whether it reads the buffers this step's reorder wrote, and the profiling
+// stage it counts toward.
+struct BatchLaunch {
+    int stage, level, total, post_sort, group;
+    size_t bs_off;
+};
+
+int batch_group(int s)
+{
+    switch (s) {
+    case BS_ZERO: case BS_MAP_KEY: return VCT_STAGE_MAP;
+    case BS_CSCAN_BLOCKS: case BS_CSCAN_TOPS: case BS_CSCAN_ADD: case BS_SCATTER: case BS_CELL_SORT:
+    case BS_REORDER: return VCT_STAGE_SORT;
+    case BS_NEIGHBOURS: return VCT_STAGE_NEIGHBOURS;
+    case BS_SMOOTHING: case BS_JBAR_COPY: return VCT_STAGE_SMOOTHING;
+    case BS_WALL_VELOCITY: case BS_PASS1: return VCT_STAGE_PASS1;
+    case BS_PASS2: case BS_PASS2_ISPH: return VCT_STAGE_PASS2;
+    case BS_RHS: return VCT_STAGE_RHS;
+    case BS_CORRECTOR: case BS_CORRECTOR_SUM: return VCT_STAGE_CORRECTOR;
+    case BS_REG_GEOM: case BS_REG_DS: case BS_REG_APPLY: return VCT_STAGE_REGULARISE;
+    default: return VCT_STAGE_PRECOND;
+    }
+}
+
+// Ensemble step with the scenarios side by side: every stage of the step runs
+// as one launch over all scenarios (each on the blocks of its own launch of
+// the stage, reading its own parameters and buffers), and one cooperative
+// launch solves all pressure systems at once, each on its own share of the
+// grid (blocks in proportion to its particles): about 30 launches a step
+// whatever the number of scenarios.  Eligible when every scenario uses the
+// multigrid solver with the same dimension and precision, and the grid holds a
+// block per scenario; otherwise returns VCT_ERR_ARG (the caller then queues
+// the scenarios one after another).  To the solver the batch is one system:
+// when it exceeds the small-system size in total, or any scenario is a large
+// system, every scenario's solve runs in the large-system form (vectors,
+// staged rows, L1 gathers, 16 KB of shared levels; VCT_BATCH_FORM=fly|explicit
+// overrides where it can).  Every stage but the solve computes exactly what the
+// scenario's own launches compute; the solves' partial sums are grouped by the
+// scenario's share of blocks, so results agree with vct_step to the solver
+// tolerance, not bit for bit.
 vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int n_scen, int nsteps,
                             vct_stats *out)
 {
@@ -482,6 +512,63 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         j.nb = (unsigned)nb[k];
         b0 += (unsigned)nb[k];
     }
+    // The batched stages of one step, in step order: every stage some scenario
+    // runs, with its block-start table (each scenario's blocks are those of its
+    // own launch of the stage).  Stages up to the reorder read the state buffers
+    // current at the step's start, the rest the other set.
+    std::vector<BatchLaunch> plan;
+    std::vector<int> tables;
+    bool too_big = false;
+    auto add = [&](int s, int level) {
+        BatchLaunch L;
+        L.stage = s;
+        L.level = level;
+        L.post_sort = s >= BS_NEIGHBOURS;
+        L.group = batch_group(s);
+        L.bs_off = tables.size();
+        int64_t total = 0;
+        tables.push_back(0);
+        for (int k = 0; k < n_scen; ++k) {
+            const vct_ctx *c = ctxs[k];
+            const bool rows = !c->mg.fly || expl;
+            total += batch_stage_blocks(s, c->P, c->W, c->mg, states[k]->n, rows, level);
+            if (total > (int64_t)INT32_MAX / 2) too_big = true;
+            tables.push_back((int)(too_big ? 0 : total));
+        }
+        L.total = (int)(too_big ? 0 : total);
+        if (L.total > 0) plan.push_back(L);
+        else tables.resize(L.bs_off);
+    };
+    for (int s = BS_ZERO; s <= BS_MG_LEVEL1; ++s) add(s, 0);
+    int maxl = 0;
+    for (int k = 0; k < n_scen; ++k) {
+        const int l = batch_coarsen_levels(ctxs[k]->mg);
+        if (l > maxl) maxl = l;
+    }
+    for (int l = 1; l < maxl; ++l) add(BS_MG_COARSEN, l);
+    add(BS_MG_COARSEN_SMALL, 0);
+    const size_t n_pre = plan.size();   // the pressure solve runs after these
+    for (int s = BS_CORRECTOR; s <= BS_REG_APPLY; ++s) add(s, 0);
+    if (too_big) return VCT_ERR_ARG;
+    // device copy: the job table of each buffer parity, then the block tables
+    const size_t sj_bytes = sizeof(StageJob) * (size_t)n_scen;
+    const size_t plan_bytes = 2 * sj_bytes + sizeof(int) * tables.size();
+    std::vector<unsigned char> hplan(plan_bytes);
+    for (int k = 0; k < n_scen; ++k) {
+        vct_ctx *c = ctxs[k];
+        for (int t = 0; t < 2; ++t) {
+            StageJob j;
+            memset(&j, 0, sizeof j);
+            j.n = states[k]->n;
+            j.cur = t == 0 ? cur(c) : alt(c);
+            j.alt = t == 0 ? alt(c) : cur(c);
+            j.W = c->W;
+            j.P = c->P;
+            j.M = c->mg;
+            memcpy(hplan.data() + (size_t)t * sj_bytes + sizeof(StageJob) * (size_t)k, &j, sizeof j);
+        }
+    }
+    memcpy(hplan.data() + 2 * sj_bytes, tables.data(), sizeof(int) * tables.size());
     vct_ctx *c0 = ctxs[0];
     cudaStream_t main = c0->st;   // the caller's: job table upload
     cudaError_t e = cudaSuccess;
@@ -493,19 +580,32 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         if (e != cudaSuccess) return VCT_ERR_CUDA;
         c0->jobs_cap = n_scen;
     }
+    if (c0->plan_cap < plan_bytes) {
+        if (c0->plan_dev) cudaFree(c0->plan_dev);
+        c0->plan_dev = nullptr;
+        c0->plan_cap = 0;
+        e = cudaMalloc((void **)&c0->plan_dev, plan_bytes);
+        if (e != cudaSuccess) return VCT_ERR_CUDA;
+        c0->plan_cap = plan_bytes;
+    }
     e = cudaMemcpyAsync(c0->jobs_dev, jobs.data(), sizeof(FlyJob) * (size_t)n_scen,
                         cudaMemcpyHostToDevice, main);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(main);   // jobs is a host temporary
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c0->plan_dev, hplan.data(), plan_bytes, cudaMemcpyHostToDevice, main);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(main);   // jobs and hplan are host temporaries
     for (int k = 0; k < n_scen && e == cudaSuccess; ++k) {
         vct_ctx *c = ctxs[k];
         if (!c->bst) e = cudaStreamCreateWithFlags(&c->bst, cudaStreamNonBlocking);
         if (e == cudaSuccess && !c->bev) e = cudaEventCreateWithFlags(&c->bev, cudaEventDisableTiming);
     }
-    // the batched solve runs on a stream of the first context's own (a graph
+    // the batched steps run on a stream of the first context's own (a graph
     // cannot be captured on the legacy default stream a caller may pass)
     if (e == cudaSuccess && !c0->gst) e = cudaStreamCreateWithFlags(&c0->gst, cudaStreamNonBlocking);
     if (e != cudaSuccess) return VCT_ERR_CUDA;
     main = c0->gst;
+    const StageJob *T[2] = {reinterpret_cast<const StageJob *>(c0->plan_dev),
+                            reinterpret_cast<const StageJob *>(c0->plan_dev + sj_bytes)};
+    const int *tb = reinterpret_cast<const int *>(c0->plan_dev + 2 * sj_bytes);
     std::vector<cudaStream_t> saved(n_scen);
     bool prof = false;
     for (int k = 0; k < n_scen; ++k) {
@@ -517,43 +617,56 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         reset_status(c);
         launch_load(c->P, cur(c), *states[k], states[k]->n, c->st);
         c->launches += 1;
+        cudaEventRecord(c->bev, c->st);   // the steps start after every scenario's load
+        cudaStreamWaitEvent(main, c->bev, 0);
     }
-    // one step: each scenario's kernels up to the solve on its stream, the
-    // batched solve on the first context's stream, the rest on the scenarios'
+    // One step on the batch stream: the batched stages up to the solve, the
+    // batched solve, the batched stages after it.  Step `step` of the call
+    // starts from job table step % 2 (each scenario's buffers alternate every
+    // step).  The launches are counted on the first context; with profiling on,
+    // its stage times are the batch's.
     auto one_step = [&](int step) -> cudaError_t {
-        for (int k = 0; k < n_scen; ++k) {
-            vct_ctx *c = ctxs[k];
-            step_pre(c, states[k]->n);
-            cudaMemsetAsync(c->W.bar, 0, 2 * sizeof(unsigned int), c->st);
-            cudaEventRecord(c->bev, c->st);
-            cudaStreamWaitEvent(main, c->bev, 0);
-        }
+        const StageJob *X = T[step & 1], *Y = T[(step + 1) & 1];
+        StageTimer *t = nullptr;
+        int grp = -1;
+        auto run = [&](const BatchLaunch &L) {
+            if (prof && L.group != grp) {
+                delete t;
+                t = new StageTimer(c0, L.group, main);
+                grp = L.group;
+            }
+            launch_batched(L.stage, dim, prec, L.post_sort ? Y : X, tb + L.bs_off, n_scen, L.total,
+                           L.level, main);
+            c0->launches += 1;
+        };
+        for (size_t q = 0; q < n_pre; ++q) run(plan[q]);
+        delete t;
+        t = nullptr;
+        grp = -1;
         int le;
-        {   // with profiling on, the first context's krylov stage times the batched solve
-            StageTimer t(c0, VCT_STAGE_KRYLOV, main);
+        {
+            StageTimer tk(c0, VCT_STAGE_KRYLOV, main);
             le = launch_krylov_fly_batch(prec, dim, c0->jobs_dev, n_scen, b0, smem, expl, main);
         }
-        cudaEventRecord(c0->bev, main);
+        c0->launches += 1;
+        for (size_t q = n_pre; q < plan.size(); ++q) run(plan[q]);
+        delete t;
         for (int k = 0; k < n_scen; ++k) {
-            vct_ctx *c = ctxs[k];
-            cudaStreamWaitEvent(c->st, c0->bev, 0);
-            c->launches += 1;   // its share of the batched solve
-            c->ppe_n = states[k]->n;
-            step_post(c, states[k]->n, step, nsteps, nullptr);
+            ctxs[k]->cur_is_A = !ctxs[k]->cur_is_A;
+            ctxs[k]->ppe_n = states[k]->n;
         }
         return le ? (cudaError_t)le : cudaSuccess;
     };
     // Steps in pairs from a CUDA graph: the state buffers alternate every step,
     // so after two steps every pointer is back where it started and one captured
-    // pair serves all pairs of this and later calls with the same batch.  The
-    // capture forks from the first context's stream to each scenario's stream
-    // and joins back; a replay is one graph launch on the first context's
-    // stream.  Not with stage profiling (its events are per step), nor with
-    // VCT_BATCH_NOGRAPH set; if a capture fails, direct launches from then on.
+    // pair serves all pairs of this and later calls with the same batch.  Not
+    // with stage profiling (its events are per step), nor with VCT_BATCH_NOGRAPH
+    // set; if a capture fails, direct launches from then on.
     int step0 = 0;
     if (nsteps >= 2 && !prof && !c0->bgraph_off && !getenv("VCT_BATCH_NOGRAPH")) {
         std::vector<long long> key = {n_scen, expl ? 1 : 0, (long long)smem, (long long)b0,
-                                      (long long)(intptr_t)c0->jobs_dev};
+                                      (long long)(intptr_t)c0->jobs_dev,
+                                      (long long)(intptr_t)c0->plan_dev, (long long)plan_bytes};
         for (int k = 0; k < n_scen; ++k) {
             key.push_back(ctxs[k]->serial);
             key.push_back(states[k]->n);
@@ -563,23 +676,18 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             if (c0->bgraph) cudaGraphExecDestroy(c0->bgraph);
             c0->bgraph = nullptr;
             c0->bgraph_key.clear();
-            std::vector<int64_t> l0(n_scen);
+            const int64_t l0 = c0->launches;
             std::vector<char> cur0(n_scen);
+            std::vector<int64_t> pn0(n_scen);
             for (int k = 0; k < n_scen; ++k) {
-                l0[k] = ctxs[k]->launches;
                 cur0[k] = ctxs[k]->cur_is_A;
+                pn0[k] = ctxs[k]->ppe_n;
             }
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed);
             cudaError_t se = cudaSuccess;
             if (ce == cudaSuccess) {
-                cudaEventRecord(c0->bev, main);
-                for (int k = 0; k < n_scen; ++k) cudaStreamWaitEvent(ctxs[k]->st, c0->bev, 0);
                 for (int q = 0; q < 2 && se == cudaSuccess; ++q) se = one_step(q);
-                for (int k = 0; k < n_scen; ++k) {
-                    cudaEventRecord(ctxs[k]->bev, ctxs[k]->st);
-                    cudaStreamWaitEvent(main, ctxs[k]->bev, 0);
-                }
                 ce = cudaStreamEndCapture(main, &g);
             }
             if (ce == cudaSuccess && se == cudaSuccess && g)
@@ -587,11 +695,11 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             else if (ce == cudaSuccess)
                 ce = se;
             if (g) cudaGraphDestroy(g);
-            c0->bgraph_launches.assign(n_scen, 0);
+            c0->bgraph_launches.assign(1, c0->launches - l0);
+            c0->launches = l0;   // nothing ran yet
             for (int k = 0; k < n_scen; ++k) {
-                c0->bgraph_launches[k] = ctxs[k]->launches - l0[k];
-                ctxs[k]->launches = l0[k];   // nothing ran yet
                 ctxs[k]->cur_is_A = cur0[k] != 0;
+                ctxs[k]->ppe_n = pn0[k];
             }
             if (ce != cudaSuccess) {
                 cudaGetLastError();   // the failed capture launched nothing
@@ -602,24 +710,21 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             }
         }
         if (c0->bgraph) {
-            for (int k = 0; k < n_scen; ++k) {   // the loads before the first replay
-                cudaEventRecord(ctxs[k]->bev, ctxs[k]->st);
-                cudaStreamWaitEvent(main, ctxs[k]->bev, 0);
-            }
             const int pairs = nsteps / 2;
             for (int q = 0; q < pairs && e == cudaSuccess; ++q) e = cudaGraphLaunch(c0->bgraph, main);
-            cudaEventRecord(c0->bev, main);   // and the scenarios' work after the last
+            c0->launches += (int64_t)pairs * c0->bgraph_launches[0];
             for (int k = 0; k < n_scen; ++k) {
-                cudaStreamWaitEvent(ctxs[k]->st, c0->bev, 0);
-                ctxs[k]->launches += (int64_t)pairs * c0->bgraph_launches[k];
                 ctxs[k]->graph_steps = 2 * pairs;
+                ctxs[k]->ppe_n = states[k]->n;
             }
             step0 = 2 * pairs;
         }
     }
     for (int step = step0; step < nsteps && e == cudaSuccess; ++step) e = one_step(step);
+    cudaEventRecord(c0->bev, main);   // the stores after the last step
     for (int k = 0; k < n_scen; ++k) {
         vct_ctx *c = ctxs[k];
+        cudaStreamWaitEvent(c->st, c0->bev, 0);
         launch_store(c->P, cur(c), *states[k], states[k]->n, c->W.status, c->st);
         c->launches += 1;
     }
@@ -1332,6 +1437,7 @@ VCT_API void vct_destroy(vct_ctx *c)
     }
     if (c->bev) cudaEventDestroy(c->bev);
     if (c->jobs_dev) cudaFree(c->jobs_dev);
+    if (c->plan_dev) cudaFree(c->plan_dev);
     if (c->bgraph) cudaGraphExecDestroy(c->bgraph);
     for (int par = 0; par < 2; ++par)
         if (c->sgraph[par]) cudaGraphExecDestroy(c->sgraph[par]);

@@ -158,9 +158,47 @@ struct FlyJob {
     unsigned b0, nb;
 };
 
+// One scenario in a batched stage launch (vct_batch_step): each stage of the
+// step except the pressure solve runs as one launch over all scenarios, every
+// scenario on a contiguous range of the launch's blocks.  The members most
+// stages read come first, so that a block copies into shared memory only the
+// prefix its stage reads; every member's size is a multiple of 16 bytes.
+struct StageJob {
+    int64_t n;
+    int64_t reserved;
+    Part cur;                 // the sorted state the stage reads
+    Work W;
+    DevParams P;
+    Part alt;                 // the other buffer set (reorder target)
+    MG M;
+};
+
+// Stages of a batched step, in step order (BS_MG_COARSEN once per level).
+enum BatchStage {
+    BS_ZERO, BS_MAP_KEY, BS_CSCAN_BLOCKS, BS_CSCAN_TOPS, BS_CSCAN_ADD, BS_SCATTER,
+    BS_CELL_SORT, BS_REORDER,
+    BS_NEIGHBOURS, BS_SMOOTHING, BS_JBAR_COPY, BS_WALL_VELOCITY, BS_PASS1, BS_PASS2,
+    BS_PASS2_ISPH, BS_RHS, BS_UROW_FLAGS, BS_RSCAN_BLOCKS, BS_RSCAN_TOPS, BS_RSCAN_ADD,
+    BS_UROW_SCATTER, BS_MG_DSC, BS_MG_LEVEL1, BS_MG_COARSEN, BS_MG_COARSEN_SMALL,
+    BS_CORRECTOR, BS_CORRECTOR_SUM, BS_REG_GEOM, BS_REG_DS, BS_REG_APPLY,
+    BS_COUNT
+};
+
 struct Ctx;
 
 // ---- launchers (vct_kernels.cu) ----
+// Blocks one scenario takes in batched stage s (0: the scenario skips it);
+// rows_list: its solve iterates over the unknown-row list; level: the
+// coarsening level of BS_MG_COARSEN.  Exactly the grid of the stage's own
+// launcher for that scenario.
+int batch_stage_blocks(int s, const DevParams &P, const Work &W, const MG &M, int64_t n,
+                       bool rows_list, int level);
+// Deepest level BS_MG_COARSEN runs at for any scenario of the batch, plus one.
+int batch_coarsen_levels(const MG &M);
+// One batched launch of stage s over njobs scenarios: jobs (device), bs
+// (device, njobs + 1 ascending block starts, bs[njobs] = total blocks).
+void launch_batched(int s, int dim, int precision, const StageJob *jobs, const int *bs, int njobs,
+                    int total, int level, cudaStream_t st);
 void launch_load(const DevParams &P, Part cur, vct_state s, int64_t n, cudaStream_t st);
 void launch_store(const DevParams &P, Part cur, vct_state s, int64_t n, const int32_t *status,
                   cudaStream_t st);

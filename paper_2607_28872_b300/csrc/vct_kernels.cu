@@ -7,6 +7,7 @@
 // iterate and residual.  No tensor cores: every sum is a gather over about 20
 // (2-D) or 56 (3-D) neighbours.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <mutex>
@@ -586,10 +587,10 @@ __device__ __forceinline__ int cell_coord(const DevParams &P, double xh, int axi
     return c;
 }
 
-__global__ void k_map_key(DevParams P, Part c, Work W, int n)
+__device__ __forceinline__ void map_key_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double zh, J, sx, sy, c0, c3;
     map_metric(P, c.x[i], P.dim == 3 ? c.y[i] : 0.0, c.z[i], zh, J, sx, sy, c0, c3);
@@ -608,6 +609,11 @@ __global__ void k_map_key(DevParams P, Part c, Work W, int n)
     int key = (cz * P.nc[1] + cy) * P.nc[0] + cx;
     W.key[i] = key;
     atomicAdd(&W.cell_count[key], 1);
+}
+
+__global__ void k_map_key(DevParams P, Part c, Work W, int n)
+{
+    map_key_body(P, c, W, n, blockIdx.x);
 }
 
 void launch_map_key(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -642,10 +648,10 @@ __device__ T block_exclusive_scan(T v, T *sh, T &total)
 }
 
 template <typename T>
-__global__ void k_scan_blocks(const int32_t *in, T *out, T *blk, int64_t m)
+__device__ __forceinline__ void scan_blocks_body(const int32_t *in, T *out, T *blk, int64_t m, int bid_)
 {
     __shared__ T sh[SCAN_T];
-    int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_V;
+    int64_t base = (int64_t)bid_ * SCAN_B + (int64_t)threadIdx.x * SCAN_V;
     T loc[SCAN_V], s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_V; ++k) {
@@ -659,11 +665,17 @@ __global__ void k_scan_blocks(const int32_t *in, T *out, T *blk, int64_t m)
         if (base + k < m) out[base + k] = ex;
         ex += loc[k];
     }
-    if (threadIdx.x == 0) blk[blockIdx.x] = total;
+    if (threadIdx.x == 0) blk[bid_] = total;
 }
 
 template <typename T>
-__global__ void k_scan_tops(T *blk, int64_t nb, T *out_end, int64_t m)
+__global__ void k_scan_blocks(const int32_t *in, T *out, T *blk, int64_t m)
+{
+    scan_blocks_body<T>(in, out, blk, m, blockIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void scan_tops_body(T *blk, int64_t nb, T *out_end, int64_t m, int bid_)
 {
     // one block: exclusive scan of nb block totals (nb <= SCAN_T * 64)
     __shared__ T sh[SCAN_T];
@@ -684,10 +696,22 @@ __global__ void k_scan_tops(T *blk, int64_t nb, T *out_end, int64_t m)
 }
 
 template <typename T>
+__global__ void k_scan_tops(T *blk, int64_t nb, T *out_end, int64_t m)
+{
+    scan_tops_body<T>(blk, nb, out_end, m, blockIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void scan_add_body(T *out, const T *blk, int64_t m, int bid_)
+{
+    int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x;
+    if (i < m) out[i] += blk[i / SCAN_B];
+}
+
+template <typename T>
 __global__ void k_scan_add(T *out, const T *blk, int64_t m)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[i] += blk[i / SCAN_B];
+    scan_add_body<T>(out, blk, m, blockIdx.x);
 }
 
 // out[0..m] = exclusive scan of in[0..m-1], out[m] = total.
@@ -701,21 +725,26 @@ static void exclusive_scan(const int32_t *in, T *out, T *tmp, int64_t m, cudaStr
     k_scan_add<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(out, tmp, m);
 }
 
-__global__ void k_scatter(Work W, const Part c, int n)
+__device__ __forceinline__ void scatter_body(const Work &W, const Part &c, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int key = W.key[i];
     int slot = W.cell_start[key] + atomicAdd(&W.cursor[key], 1);
     W.perm[slot] = i;
 }
 
+__global__ void k_scatter(Work W, const Part c, int n)
+{
+    scatter_body(W, c, n, blockIdx.x);
+}
+
 // Within each cell, order particles by caller index (deterministic layout).
-__global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
+__device__ __forceinline__ void cell_sort_body(const Work &W, const Part &c, int64_t ncell, int bid_)
 {
     if (step_failed(W.status)) return;
-    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t cell = (int64_t)bid_ * blockDim.x + threadIdx.x;
     if (cell >= ncell) return;
     int a = W.cell_start[cell], b = W.cell_start[cell + 1];
     for (int k = a + 1; k < b; ++k) {
@@ -730,10 +759,15 @@ __global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
     }
 }
 
-__global__ void k_reorder(const Part c, Part a, Work W, int n, DevParams P)
+__global__ void k_cell_sort(Work W, const Part c, int64_t ncell)
+{
+    cell_sort_body(W, c, ncell, blockIdx.x);
+}
+
+__device__ __forceinline__ void reorder_body(const Part &c, const Part &a, const Work &W, int n, const DevParams &P, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int s = W.perm[i];
     a.x[i] = c.x[s]; a.y[i] = c.y[s]; a.z[i] = c.z[s];
@@ -753,6 +787,11 @@ __global__ void k_reorder(const Part c, Part a, Work W, int n, DevParams P)
     const double V = P.volume_mode == 0 ? P.V0 : P.V0 * c.J[s] / c.jbar[s];   // vol_of
     W.vol[i] = V;
     W.volf[i] = (float)V;
+}
+
+__global__ void k_reorder(const Part c, Part a, Work W, int n, DevParams P)
+{
+    reorder_body(c, a, W, n, P, blockIdx.x);
 }
 
 void launch_sort(const DevParams &P, Part cur, Part alt, Work W, int64_t n, cudaStream_t st)
@@ -797,10 +836,10 @@ __device__ __forceinline__ float nbr_bound(float ad, float xa)
 }
 
 template <int D>
-__global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
+__device__ __forceinline__ void neighbours_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double xi[3];
     load_hat<D>(c, i, xi);
@@ -880,6 +919,12 @@ __global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
     }
 }
 
+template <int D>
+__global__ void k_neighbours(DevParams P, const Part c, Work W, int n)
+{
+    neighbours_body<D>(P, c, W, n, blockIdx.x);
+}
+
 void launch_neighbours(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
 {
     unsigned g = (unsigned)((n + 127) / 128);
@@ -919,10 +964,10 @@ __global__ void k_csr_fill(const Part c, Work W, int n, const int64_t *row_ptr, 
 // pair is applied once from each end, from the values before the sweep.
 // ---------------------------------------------------------------------------
 template <int D, typename R>
-__global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
+__device__ __forceinline__ void smoothing_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double jb = c.jbar[i];
     if (c.type[i] != FLUID) {
@@ -962,6 +1007,12 @@ __global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
     W.volf[i] = (float)V;
 }
 
+template <int D, typename R>
+__global__ void k_smoothing(DevParams P, const Part c, Work W, int n)
+{
+    smoothing_body<D, R>(P, c, W, n, blockIdx.x);
+}
+
 void launch_smoothing(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
 {
     unsigned g = (unsigned)((n + 127) / 128);
@@ -989,11 +1040,11 @@ constexpr int pass2_min_blocks() { return D == 2 ? 3 : 1; }
 // free-surface flag, Smagorinsky eddy viscosity (Sec. 3.4).
 // ---------------------------------------------------------------------------
 template <int D, typename R>
-__global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams P, const Part c, Work W, int n)
+__device__ __forceinline__ void pass1_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
     constexpr int M = D == 2 ? 3 : 6;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (c.type[i] != FLUID) return;
     const int64_t cap = W.cap;
@@ -1204,6 +1255,12 @@ __global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams 
     W.nu[i] = P.nu_k + nue;
 }
 
+template <int D, typename R>
+__global__ void __launch_bounds__(128, pass1_min_blocks<D>()) k_pass1(DevParams P, const Part c, Work W, int n)
+{
+    pass1_body<D, R>(P, c, W, n, blockIdx.x);
+}
+
 void launch_pass1(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
 {
     unsigned g = (unsigned)((n + 127) / 128);
@@ -1224,12 +1281,11 @@ void launch_pass1(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t 
 //   w = M_i^-T c~,  u = sum_j V_j F_ij (w . q_ij) r_ij.
 // ---------------------------------------------------------------------------
 template <int D, typename R>
-__global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams P, const Part c, Work W, int n,
-                                               int predictor)
+__device__ __forceinline__ void pass2_body(const DevParams &P, const Part &c, const Work &W, int n, int predictor, int bid_)
 {
     if (step_failed(W.status)) return;
     constexpr int M = D == 2 ? 3 : 6;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (c.type[i] != FLUID) {
         if (predictor) W.pcnt[i] = -1;
@@ -1502,16 +1558,23 @@ __global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams 
     atomicAdd((unsigned long long *)&W.counts[1], (unsigned long long)pc);
 }
 
+template <int D, typename R>
+__global__ void __launch_bounds__(128, pass2_min_blocks<D>()) k_pass2(DevParams P, const Part c, Work W, int n,
+                                               int predictor)
+{
+    pass2_body<D, R>(P, c, W, n, predictor, blockIdx.x);
+}
+
 // Pass 2 of the ISPH operator set (Table tab:case_names): the predictor with the
 // 0th-order second derivatives of Eq. (sec_0th), D_a v = sum_j V_j k_a(r_ij) v_ij,
 // and the pressure row c_trans . <D^ p>^(0): a_ij = V_j (c0 (L grad w)_z^ +
 // sum_a c~_a k_a(r_ij)).  No moment matrix and no per-particle solve.
 template <int D, typename R>
-__global__ void __launch_bounds__(128) k_pass2_isph(DevParams P, const Part c, Work W, int n)
+__device__ __forceinline__ void pass2_isph_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
     constexpr int M = D == 2 ? 3 : 6;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (c.type[i] != FLUID) {
         W.pcnt[i] = -1;
@@ -1674,6 +1737,12 @@ __global__ void __launch_bounds__(128) k_pass2_isph(DevParams P, const Part c, W
     atomicAdd((unsigned long long *)&W.counts[1], (unsigned long long)pc);
 }
 
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_pass2_isph(DevParams P, const Part c, Work W, int n)
+{
+    pass2_isph_body<D, R>(P, c, W, n, blockIdx.x);
+}
+
 void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor,
                   cudaStream_t st)
 {
@@ -1704,10 +1773,10 @@ void launch_pass2(const DevParams &P, Part cur, Work W, int64_t n, int predictor
 // the acceleration Eq. (PNC) assumes.
 // ---------------------------------------------------------------------------
 template <int D, typename R>
-__global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, int n)
+__device__ __forceinline__ void rhs_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t cap = W.cap;
     if (c.type[i] != FLUID || W.fs[i]) {
@@ -1794,6 +1863,12 @@ __global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, 
     }
     if (P.pguess == 0) x0 = pn;
     W.kx[i] = x0;
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_rhs(DevParams P, const Part c, Work W, int n)
+{
+    rhs_body<D, R>(P, c, W, n, blockIdx.x);
 }
 
 void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -2310,13 +2385,13 @@ __device__ __forceinline__ void stencil_add(float (&acc)[S], int o, float v)
 // One warp per cell: the lanes take the slots of the cell's rows in turn and
 // the 3^d sums are reduced across the warp in a fixed order.
 template <int D>
-__global__ void k_mg_level1(Work W, MG M, int mixed)
+__device__ __forceinline__ void mg_level1_body(const Work &W, const MG &M, int mixed, int bid_)
 {
     if (step_failed(W.status)) return;
     constexpr int S = D == 2 ? 9 : 27;
     const int N = M.n[1];
     const int lane = threadIdx.x & 31;
-    const int I = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int I = (int)((bid_ * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (I >= N) return;
     float acc[S];
 #pragma unroll
@@ -2353,6 +2428,12 @@ __global__ void k_mg_level1(Work W, MG M, int mixed)
 #pragma unroll
     for (int o = 0; o < S; ++o) A[(int64_t)o * N + I] = acc[o];
     v[I] = (rows > 0 && acc[cidx] != 0.f) ? 1.f / acc[cidx] : 0.f;   // dinv
+}
+
+template <int D>
+__global__ void k_mg_level1(Work W, MG M, int mixed)
+{
+    mg_level1_body<D>(W, M, mixed, blockIdx.x);
 }
 
 // Node Ic of level l+1 from level l: sums of the children's stencils.
@@ -2401,16 +2482,22 @@ __device__ void coarsen_node(const Work &W, const MG &M, int l, int Ic)
 }
 
 template <int D>
-__global__ void k_mg_coarsen(Work W, MG M, int l)   // builds level l+1 from level l
+__device__ __forceinline__ void mg_coarsen_body(const Work &W, const MG &M, int l, int bid_)
 {
     if (step_failed(W.status)) return;
-    const int Ic = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Ic = bid_ * blockDim.x + threadIdx.x;
     if (Ic < M.n[l + 1]) coarsen_node<D>(W, M, l, Ic);
+}
+
+template <int D>
+__global__ void k_mg_coarsen(Work W, MG M, int l)
+{
+    mg_coarsen_body<D>(W, M, l, blockIdx.x);
 }
 
 // Levels l0+1 .. L (small) built by one block, level after level.
 template <int D>
-__global__ void k_mg_coarsen_small(Work W, MG M, int l0)
+__device__ __forceinline__ void mg_coarsen_small_body(const Work &W, const MG &M, int l0, int bid_)
 {
     if (step_failed(W.status)) return;
     for (int l = l0; l < M.L; ++l) {
@@ -2420,28 +2507,49 @@ __global__ void k_mg_coarsen_small(Work W, MG M, int l0)
     }
 }
 
-__global__ void k_mg_dsc(Work W, int n)
+template <int D>
+__global__ void k_mg_coarsen_small(Work W, MG M, int l0)
+{
+    mg_coarsen_small_body<D>(W, M, l0, blockIdx.x);
+}
+
+__device__ __forceinline__ void mg_dsc_body(const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     W.mg_dsc[i] = (W.pcnt[i] >= 0 && W.diag[i] != 0.0) ? (float)(1.0 / W.diag[i]) : 0.f;
 }
 
+__global__ void k_mg_dsc(Work W, int n)
+{
+    mg_dsc_body(W, n, blockIdx.x);
+}
+
 // The large-system solve iterates over the unknown rows only (walls, virtual
 // and free-surface particles have no row): their ascending list, by a scan.
-__global__ void k_urow_flags(Work W, int n)
+__device__ __forceinline__ void urow_flags_body(const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid_ * blockDim.x + threadIdx.x;
     if (i < n) W.urow_flag[i] = W.pcnt[i] >= 0 ? 1 : 0;
+}
+
+__global__ void k_urow_flags(Work W, int n)
+{
+    urow_flags_body(W, n, blockIdx.x);
+}
+
+__device__ __forceinline__ void urow_scatter_body(const Work &W, int n, int bid_)
+{
+    if (step_failed(W.status)) return;
+    const int i = bid_ * blockDim.x + threadIdx.x;
+    if (i < n && W.urow_flag[i]) W.urow[W.urow_pos[i]] = i;
 }
 
 __global__ void k_urow_scatter(Work W, int n)
 {
-    if (step_failed(W.status)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && W.urow_flag[i]) W.urow[W.urow_pos[i]] = i;
+    urow_scatter_body(W, n, blockIdx.x);
 }
 
 // coarse levels up to this size are built by one block (2-D wave, set-up per step
@@ -3544,11 +3652,11 @@ int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njob
 // <grad^ p>+_i = sum_j V_j (p_j + p_i) grad w_ij = 2 p_i sum_j V_j grad w_ij +
 // sum_j V_j p_ij grad w_ij (both sums kept apart; combined in FP64); else the
 // corrected gradient of Eq. (gra_1st).
-template <int D, typename R, bool SUM = false>
-__global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, int n)
+template <int D, typename R, bool SUM>
+__device__ __forceinline__ void corrector_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (c.type[i] != FLUID) return;
     const int64_t cap = W.cap;
@@ -3626,6 +3734,12 @@ __global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, 
     bool finite = isfinite(c.x[i]) && isfinite(c.z[i]) && isfinite(p_i) && isfinite(vn[0]) &&
                   isfinite(vn[D - 1]);
     if (!finite) set_error(W.status, VCT_ERR_NONFINITE, i);
+}
+
+template <int D, typename R, bool SUM = false>
+__global__ void __launch_bounds__(128) k_corrector(DevParams P, Part c, Work W, int n)
+{
+    corrector_body<D, R, SUM>(P, c, W, n, blockIdx.x);
 }
 
 void launch_corrector(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -3726,10 +3840,10 @@ __device__ bool reg_invert(double (&A)[D * D], double (&X)[D * D])
 
 // Projected positions and metric at the updated positions; velocity copies.
 template <int D>
-__global__ void __launch_bounds__(128) k_reg_geom(DevParams P, Part c, Work W, int n)
+__device__ __forceinline__ void reg_geom_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t cap = W.cap;
     double zh, J, sx, sy, c0, c3;
@@ -3755,6 +3869,12 @@ __global__ void __launch_bounds__(128) k_reg_geom(DevParams P, Part c, Work W, i
 }
 
 template <int D>
+__global__ void __launch_bounds__(128) k_reg_geom(DevParams P, Part c, Work W, int n)
+{
+    reg_geom_body<D>(P, c, W, n, blockIdx.x);
+}
+
+template <int D>
 __device__ __forceinline__ void reg_load(const Work &W, int i, double *x)
 {
 #pragma unroll
@@ -3765,10 +3885,10 @@ __device__ __forceinline__ void reg_load(const Work &W, int i, double *x)
 // R: precision of the pair terms (FP64 form: double; mixed form: float, the
 // differences formed in FP64 first).
 template <int D, typename R>
-__global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int n)
+__device__ __forceinline__ void reg_ds_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n || c.type[i] != FLUID) return;
     const int64_t cap = W.cap;
     const double dds = (1.0 - P.ds_overlap) * P.d0;
@@ -3810,12 +3930,18 @@ __global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int
     }
 }
 
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_reg_ds(DevParams P, Part c, Work W, int n)
+{
+    reg_ds_body<D, R>(P, c, W, n, blockIdx.x);
+}
+
 // XSPH on free-surface particles, shifting, and the final write of the state.
 template <int D, typename R>
-__global__ void __launch_bounds__(128) k_reg_apply(DevParams P, Part c, Work W, int n)
+__device__ __forceinline__ void reg_apply_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n || c.type[i] != FLUID) return;
     const int64_t cap = W.cap;
     const R inv_l = (R)P.inv_l, ad = (R)P.ad, V0 = (R)P.V0;
@@ -3931,6 +4057,12 @@ __global__ void __launch_bounds__(128) k_reg_apply(DevParams P, Part c, Work W, 
     c.w[i] = un[D - 1];
     if (!(isfinite(c.x[i]) && isfinite(c.z[i]) && isfinite(un[0]) && isfinite(un[D - 1])))
         set_error(W.status, VCT_ERR_NONFINITE, i);
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_reg_apply(DevParams P, Part c, Work W, int n)
+{
+    reg_apply_body<D, R>(P, c, W, n, blockIdx.x);
 }
 
 bool regularise_on(const DevParams &P)
@@ -4592,10 +4724,10 @@ __global__ void k_probe_out(DevParams P, const Part c, Work W, int n, vct_probe 
 // arctan h_y).  Written into the sorted state (FP64 and the hi/lo FP32 copy) of
 // wall particles, where pass 1, pass 2 and the right side read it.
 template <int D>
-__global__ void __launch_bounds__(128) k_wall_velocity(DevParams P, Part c, Work W, int n)
+__device__ __forceinline__ void wall_velocity_body(const DevParams &P, const Part &c, const Work &W, int n, int bid_)
 {
     if (step_failed(W.status)) return;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = bid_ * blockDim.x + threadIdx.x;
     if (j >= n || c.type[j] != WALL) return;
     const int64_t cap = W.cap;
     double xj[3];
@@ -4653,6 +4785,12 @@ __global__ void __launch_bounds__(128) k_wall_velocity(DevParams P, Part c, Work
     float4 lo;
     W.velhi[j] = f4_hilo_split(v[0], D == 3 ? v[1] : 0.0, v[D - 1], lo);
     W.vello[j] = lo;
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_wall_velocity(DevParams P, Part c, Work W, int n)
+{
+    wall_velocity_body<D>(P, c, W, n, blockIdx.x);
 }
 
 void launch_wall_velocity(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -5640,6 +5778,326 @@ void launch_rhopos(const DevParams &P, Part cur, Work W, int64_t n, const double
     const unsigned g = (unsigned)((n + 127) / 128);
     if (P.dim == 2) k_rhopos<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, rho_bar, xh_bar);
     else k_rhopos<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, rho_bar, xh_bar);
+}
+
+// ---------------------------------------------------------------------------
+// a11: the stages of an ensemble step, each as one launch over all scenarios.
+// Block b of a launch belongs to the scenario k with bs[k] <= b < bs[k + 1];
+// it copies the part of that scenario's StageJob its stage reads into shared
+// memory and runs the stage's body as block b - bs[k] of the scenario's own
+// launch, so every scenario computes exactly what its own launches compute.
+// ---------------------------------------------------------------------------
+static_assert(sizeof(Part) % 16 == 0 && sizeof(Work) % 16 == 0 && sizeof(DevParams) % 16 == 0 &&
+                  sizeof(MG) % 16 == 0 && sizeof(StageJob) % 16 == 0,
+              "StageJob members are copied in 16-byte words");
+constexpr int SJ_CW = (int)offsetof(StageJob, P);      // n, cur, W
+constexpr int SJ_CWP = (int)offsetof(StageJob, alt);   // + P
+constexpr int SJ_CWPA = (int)offsetof(StageJob, M);    // + alt
+constexpr int SJ_ALL = (int)sizeof(StageJob);          // + M
+
+template <class F>
+__global__ void __launch_bounds__(F::NT, F::MINB) k_batched(const StageJob *__restrict__ jobs,
+                                                            const int *__restrict__ bs, int njobs, F f)
+{
+    __shared__ int4 sj[F::BYTES / 16];
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = njobs;   // bs[lo] <= b < bs[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(bs + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    const int4 *src = reinterpret_cast<const int4 *>(jobs + lo);
+    for (int k = threadIdx.x; k < F::BYTES / 16; k += blockDim.x) sj[k] = __ldg(src + k);
+    __syncthreads();
+    f(*reinterpret_cast<const StageJob *>(sj), b - __ldg(bs + lo));
+}
+
+struct BZero {   // the counters a step starts from: cell counts and cursors, row counts, barrier
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        const int64_t i = (int64_t)b * NT + threadIdx.x;
+        if (i <= j.W.ncell) j.W.cell_count[i] = 0;
+        if (i < j.W.ncell) j.W.cursor[i] = 0;
+        if (i < 2) {
+            j.W.counts[i] = 0;
+            j.W.bar[i] = 0u;
+        }
+    }
+};
+struct BMapKey {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { map_key_body(j.P, j.cur, j.W, (int)j.n, b); }
+};
+// exclusive scans: of the cell counts (CELLS) or of the unknown-row flags
+template <bool CELLS>
+__device__ __forceinline__ void scan_args(const StageJob &j, const int32_t *&in, int32_t *&out, int64_t &m)
+{
+    in = CELLS ? j.W.cell_count : j.W.urow_flag;
+    out = CELLS ? j.W.cell_start : j.W.urow_pos;
+    m = CELLS ? j.W.ncell : j.n;
+}
+template <bool CELLS>
+struct BScanBlocks {
+    static constexpr int NT = SCAN_T, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        const int32_t *in;
+        int32_t *out;
+        int64_t m;
+        scan_args<CELLS>(j, in, out, m);
+        scan_blocks_body<int32_t>(in, out, j.W.scan_tmp, m, b);
+    }
+};
+template <bool CELLS>
+struct BScanTops {
+    static constexpr int NT = SCAN_T, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        const int32_t *in;
+        int32_t *out;
+        int64_t m;
+        scan_args<CELLS>(j, in, out, m);
+        int64_t nb = (m + SCAN_B - 1) / SCAN_B;
+        if (nb == 0) nb = 1;
+        scan_tops_body<int32_t>(j.W.scan_tmp, nb, out, m, b);
+    }
+};
+template <bool CELLS>
+struct BScanAdd {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        const int32_t *in;
+        int32_t *out;
+        int64_t m;
+        scan_args<CELLS>(j, in, out, m);
+        scan_add_body<int32_t>(out, j.W.scan_tmp, m, b);
+    }
+};
+struct BScatter {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const { scatter_body(j.W, j.cur, (int)j.n, b); }
+};
+struct BCellSort {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const { cell_sort_body(j.W, j.cur, j.W.ncell, b); }
+};
+struct BReorder {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CWPA;
+    __device__ void operator()(const StageJob &j, int b) const { reorder_body(j.cur, j.alt, j.W, (int)j.n, j.P, b); }
+};
+template <int D, typename R>
+struct BNeighbours {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { neighbours_body<D>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BSmoothing {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { smoothing_body<D, R>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+struct BJbarCopy {   // the smoothed Jbar into the state
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        const int64_t i = (int64_t)b * NT + threadIdx.x;
+        if (i < j.n) j.cur.jbar[i] = j.W.jbar_tmp[i];
+    }
+};
+template <int D, typename R>
+struct BWallVelocity {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { wall_velocity_body<D>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BPass1 {
+    static constexpr int NT = 128, MINB = pass1_min_blocks<D>(), BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { pass1_body<D, R>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BPass2 {
+    static constexpr int NT = 128, MINB = pass2_min_blocks<D>(), BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { pass2_body<D, R>(j.P, j.cur, j.W, (int)j.n, 1, b); }
+};
+template <int D, typename R>
+struct BPass2Isph {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { pass2_isph_body<D, R>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BRhs {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { rhs_body<D, R>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+struct BUrowFlags {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const { urow_flags_body(j.W, (int)j.n, b); }
+};
+struct BUrowScatter {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const { urow_scatter_body(j.W, (int)j.n, b); }
+};
+struct BMgDsc {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_CW;
+    __device__ void operator()(const StageJob &j, int b) const { mg_dsc_body(j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BMgLevel1 {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_ALL;
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        mg_level1_body<D>(j.W, j.M, j.P.precision == VCT_MIXED, b);
+    }
+};
+template <int D, typename R>
+struct BMgCoarsen {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_ALL;
+    int l;
+    __device__ void operator()(const StageJob &j, int b) const { mg_coarsen_body<D>(j.W, j.M, l, b); }
+};
+template <int D, typename R>
+struct BMgCoarsenSmall {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_ALL;
+    int small;   // the host's small-level size
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        int l = 1;   // the first level the per-level launches did not build
+        while (l < j.M.L && j.M.n[l + 1] > small) ++l;
+        mg_coarsen_small_body<D>(j.W, j.M, l, b);
+    }
+};
+template <int D, typename R, bool SUM>
+struct BCorrector {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { corrector_body<D, R, SUM>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BCorrectorPlain : BCorrector<D, R, false> {};
+template <int D, typename R>
+struct BCorrectorSum : BCorrector<D, R, true> {};
+template <int D, typename R>
+struct BRegGeom {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { reg_geom_body<D>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BRegDs {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { reg_ds_body<D, R>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+template <int D, typename R>
+struct BRegApply {
+    static constexpr int NT = 128, MINB = 1, BYTES = SJ_CWP;
+    __device__ void operator()(const StageJob &j, int b) const { reg_apply_body<D, R>(j.P, j.cur, j.W, (int)j.n, b); }
+};
+
+int batch_coarsen_levels(const MG &M)
+{
+    int l = 1;
+    while (l < M.L && M.n[l + 1] > small_level()) ++l;
+    return l;   // BS_MG_COARSEN runs at levels 1 .. l - 1
+}
+
+int batch_stage_blocks(int s, const DevParams &P, const Work &W, const MG &M, int64_t n,
+                       bool rows_list, int level)
+{
+    const int64_t nc = W.ncell;
+    const int b256 = (int)((n + 255) / 256), b128 = (int)((n + 127) / 128);
+    const bool smooth = P.kind == VCT_MAP_SIGMA && P.volume_mode == 2;
+    const bool reg = regularise_on(P);
+    const int lend = batch_coarsen_levels(M);
+    int64_t snb;
+    switch (s) {
+    case BS_ZERO: return (int)((nc + 1 + 255) / 256);
+    case BS_MAP_KEY: case BS_SCATTER: case BS_REORDER: case BS_MG_DSC: return b256;
+    case BS_CSCAN_BLOCKS:
+        snb = (nc + SCAN_B - 1) / SCAN_B;
+        return snb == 0 ? 1 : (int)snb;
+    case BS_CSCAN_TOPS: return 1;
+    case BS_CSCAN_ADD: return (int)((nc + 255) / 256);
+    case BS_CELL_SORT: return (int)((nc + 127) / 128);
+    case BS_NEIGHBOURS: case BS_PASS1: case BS_RHS: return b128;
+    case BS_SMOOTHING: return smooth ? b128 : 0;
+    case BS_JBAR_COPY: return smooth ? b256 : 0;
+    case BS_WALL_VELOCITY: return P.slip ? b128 : 0;
+    case BS_PASS2: return P.operators == 1 ? 0 : b128;
+    case BS_PASS2_ISPH: return P.operators == 1 ? b128 : 0;
+    case BS_UROW_FLAGS: case BS_RSCAN_ADD: case BS_UROW_SCATTER: return rows_list ? b256 : 0;
+    case BS_RSCAN_BLOCKS:
+        snb = (n + SCAN_B - 1) / SCAN_B;
+        return rows_list ? (snb == 0 ? 1 : (int)snb) : 0;
+    case BS_RSCAN_TOPS: return rows_list ? 1 : 0;
+    case BS_MG_LEVEL1: return (int)(((int64_t)M.n[1] * 32 + 255) / 256);
+    case BS_MG_COARSEN: return level >= 1 && level < lend ? (M.n[level + 1] + 127) / 128 : 0;
+    case BS_MG_COARSEN_SMALL: return lend < M.L ? 1 : 0;
+    case BS_CORRECTOR: return P.operators == 1 ? 0 : b128;
+    case BS_CORRECTOR_SUM: return P.operators == 1 ? b128 : 0;
+    case BS_REG_GEOM: case BS_REG_APPLY: return reg ? b128 : 0;
+    case BS_REG_DS: return reg && P.ds_overlap > 0.0 ? b128 : 0;
+    default: return 0;
+    }
+}
+
+template <class F>
+static void run_batched(const StageJob *jobs, const int *bs, int njobs, int total, F f, cudaStream_t st)
+{
+    k_batched<F><<<(unsigned)total, F::NT, 0, st>>>(jobs, bs, njobs, f);
+}
+
+// the functor template FT<D, R> of the batch's dimension and precision
+template <template <int, typename> class FT, class... A>
+static void run_dr(int dim, bool mixed, const StageJob *jobs, const int *bs, int njobs, int total,
+                   cudaStream_t st, A... a)
+{
+    if (dim == 2) {
+        if (mixed) run_batched(jobs, bs, njobs, total, FT<2, float>{a...}, st);
+        else run_batched(jobs, bs, njobs, total, FT<2, double>{a...}, st);
+    } else {
+        if (mixed) run_batched(jobs, bs, njobs, total, FT<3, float>{a...}, st);
+        else run_batched(jobs, bs, njobs, total, FT<3, double>{a...}, st);
+    }
+}
+
+void launch_batched(int s, int dim, int precision, const StageJob *jobs, const int *bs, int njobs,
+                    int total, int level, cudaStream_t st)
+{
+    if (total <= 0) return;
+    const bool mx = precision == VCT_MIXED;
+    switch (s) {
+    case BS_ZERO: run_batched(jobs, bs, njobs, total, BZero{}, st); break;
+    case BS_MAP_KEY: run_batched(jobs, bs, njobs, total, BMapKey{}, st); break;
+    case BS_CSCAN_BLOCKS: run_batched(jobs, bs, njobs, total, BScanBlocks<true>{}, st); break;
+    case BS_CSCAN_TOPS: run_batched(jobs, bs, njobs, total, BScanTops<true>{}, st); break;
+    case BS_CSCAN_ADD: run_batched(jobs, bs, njobs, total, BScanAdd<true>{}, st); break;
+    case BS_SCATTER: run_batched(jobs, bs, njobs, total, BScatter{}, st); break;
+    case BS_CELL_SORT: run_batched(jobs, bs, njobs, total, BCellSort{}, st); break;
+    case BS_REORDER: run_batched(jobs, bs, njobs, total, BReorder{}, st); break;
+    case BS_NEIGHBOURS: run_dr<BNeighbours>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_SMOOTHING: run_dr<BSmoothing>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_JBAR_COPY: run_batched(jobs, bs, njobs, total, BJbarCopy{}, st); break;
+    case BS_WALL_VELOCITY: run_dr<BWallVelocity>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_PASS1: run_dr<BPass1>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_PASS2: run_dr<BPass2>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_PASS2_ISPH: run_dr<BPass2Isph>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_RHS: run_dr<BRhs>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_UROW_FLAGS: run_batched(jobs, bs, njobs, total, BUrowFlags{}, st); break;
+    case BS_RSCAN_BLOCKS: run_batched(jobs, bs, njobs, total, BScanBlocks<false>{}, st); break;
+    case BS_RSCAN_TOPS: run_batched(jobs, bs, njobs, total, BScanTops<false>{}, st); break;
+    case BS_RSCAN_ADD: run_batched(jobs, bs, njobs, total, BScanAdd<false>{}, st); break;
+    case BS_UROW_SCATTER: run_batched(jobs, bs, njobs, total, BUrowScatter{}, st); break;
+    case BS_MG_DSC: run_batched(jobs, bs, njobs, total, BMgDsc{}, st); break;
+    case BS_MG_LEVEL1: run_dr<BMgLevel1>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_MG_COARSEN: run_dr<BMgCoarsen>(dim, mx, jobs, bs, njobs, total, st, level); break;
+    case BS_MG_COARSEN_SMALL: run_dr<BMgCoarsenSmall>(dim, mx, jobs, bs, njobs, total, st, small_level()); break;
+    case BS_CORRECTOR: run_dr<BCorrectorPlain>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_CORRECTOR_SUM: run_dr<BCorrectorSum>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_REG_GEOM: run_dr<BRegGeom>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_REG_DS: run_dr<BRegDs>(dim, mx, jobs, bs, njobs, total, st); break;
+    case BS_REG_APPLY: run_dr<BRegApply>(dim, mx, jobs, bs, njobs, total, st); break;
+    default: break;
+    }
 }
 
 }  // namespace vct

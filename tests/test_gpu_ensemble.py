@@ -164,3 +164,57 @@ def test_batch_graph_replay_equals_direct_launches(monkeypatch, form):
         for a, b in zip(call_g, call_d):
             for k in ("x", "z", "u", "w", "p", "jbar"):
                 assert np.array_equal(a[k], b[k]), k
+
+
+def test_batched_stages_exact_before_the_solve():
+    """Every stage of a side-by-side step before the pressure solve is one
+    launch over all scenarios that computes exactly what the scenario's own
+    launches compute: after one step the smoothed volumes Jbar (set before the
+    solve, Eq. VCT_bar_a) are bit-identical to the individual steps'."""
+    from paper_2607_28872_b300 import vct as V
+    scs = _scenarios()
+    ref = _individual(V, scs, 1)
+    solvers = [V.Solver(sc) for sc in scs]
+    states = [V.DeviceState(sc) for sc in scs]
+    V.vct_batch_step(solvers, states, 1)
+    for st, r in zip(states, ref):
+        assert np.array_equal(st.numpy()["jbar"], r["jbar"])
+
+
+def test_batch_launches_do_not_grow_with_scenarios(monkeypatch):
+    """Side by side, a step is a fixed number of launches (one per stage plus
+    the batched solve), counted on the first scenario, whatever the number of
+    scenarios; the other scenarios count their own load and store only."""
+    from paper_2607_28872_b300 import vct as V
+    monkeypatch.setenv("VCT_BATCH_NOGRAPH", "1")
+    scs = _scenarios()
+    per_step = []
+    for m in (2, 3):
+        solvers = [V.Solver(sc) for sc in scs[:m]]
+        states = [V.DeviceState(sc) for sc in scs[:m]]
+        a = V.vct_batch_step(solvers, states, 1)
+        b = V.vct_batch_step(solvers, states, 3)
+        per_step.append((b[0].kernel_launches - a[0].kernel_launches) / 2)
+        assert all(s.kernel_launches == 2 for s in b[1:])
+    assert per_step[0] == per_step[1] and per_step[0] <= 40, per_step
+
+
+def test_batch_with_different_options_per_scenario():
+    """Scenarios that run different stages (free-slip walls and regularisation,
+    the ISPH operator set and regularisation, neither) in one batch: each batched stage runs only for the
+    scenarios that need it, and every scenario agrees with its own steps to the
+    solver tolerance."""
+    from paper_2607_28872_b300 import vct as V
+    scs = _scenarios()
+    scs[0].params.update(wall_slip=1, **S.REGULARISATION)
+    scs[1].params.update(operators=1, **S.REGULARISATION)
+    ref = _individual(V, scs, 2)
+    solvers = [V.Solver(sc) for sc in scs]
+    states = [V.DeviceState(sc) for sc in scs]
+    stats = V.vct_batch_step(solvers, states, 2)
+    assert all(s.steps_done == 2 for s in stats)
+    for sc, st, r in zip(scs, states, ref):
+        g = st.numpy()
+        f = sc.type == S.FLUID
+        for k in ("p", "u", "w"):
+            assert rel(g[k][f], r[k][f]) < 1e-4, k
