@@ -114,10 +114,7 @@ WORKLOADS = {
 # without an entry reports traffic null.  "per_unit": bytes per fluid particle
 # per Krylov iteration (the 3-D beach is captured on its 8 x 1.6 m slice; its
 # traffic grows with rows x iterations); "per_launch": bytes per launch.
-NCU_TRAFFIC = {
-    "beach_bfe_3d": ("per_unit", 3610.0, "profiles/k_krylov_mg_beach_bfe_3d_slice_540k.md"),
-    "beach_bfe_3d_slice": ("per_unit", 3610.0, "profiles/k_krylov_mg_beach_bfe_3d_slice_540k.md"),
-}
+NCU_TRAFFIC = {}
 
 
 def workload(precision=1, name="sigma_solitary"):
@@ -266,7 +263,11 @@ def run_ensemble(args):
     table, schedule = None, "built-in defaults"
     if args.tune:
         # the batch runs the large-system form above 75k particles in total
-        table = autotune.tune(scs, form=2)
+        # every class in the large-system form with the batch's V(0,1) cycle: timed
+        # alone, V(1,1) wins some classes by a few per cent, side by side it
+        # loses (the batch is bandwidth-bound where a single solve is not)
+        table = autotune.tune(scs, form=2,
+                              grid=lambda dim, form: autotune.candidates(dim, form, cycles=(2,)))
         autotune.save(table, args.tune)
         schedule = f"autotuned now ({len(table)} size classes, written to {args.tune})"
     elif not args.no_tuning and os.path.exists(TUNING_TABLE):
@@ -300,13 +301,16 @@ def run_ensemble(args):
     stage_t = solvers[0].vct_stage_times()   # the batched launches of all scenarios
     k_ms, k_cnt = stage_t["krylov"]
     solvers[0].vct_set_profiling(False)
-    per_launch = 0.0
+    per_launch, asm = 0.0, 0.0
+    key = (2, args.precision)
     for sc, s in zip(scs, pst):
         box = [sc.box_hi[k] - sc.box_lo[k] for k in range(3)]
         re = sc.params["re_over_l"] * sc.params["l_over_d0"] * sc.params["d0"]
         n_cells = (int(box[0] / re) + 1) * (int(box[2] / re) + 1)
-        per_launch += krylov_bytes(s.krylov_iters_total / nprof, s.ppe_rows, s.ppe_nnz, n_cells,
-                                   args.precision == 1, sc.dim)
+        it = s.krylov_iters_total / nprof
+        per_launch += B_IT[key] * sc.n_fluid * it
+        asm += krylov_bytes(it, s.ppe_rows, s.ppe_nnz, n_cells, args.precision == 1, sc.dim,
+                            s.mg_cycle)
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(pk_path)) if os.path.exists(pk_path) else {}
     hbm = peaks.get("hbm_gbs", 6400.0)
@@ -316,9 +320,11 @@ def run_ensemble(args):
             "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "traffic_source": None,
             "peak_source": "measured" if peaks else "fallback", "avg_launch_ms": avg_ms,
             "algorithmic_bytes_per_launch": per_launch, "launches_timed": k_cnt,
-            "note": "all scenarios' pressure solves in one cooperative launch per step; "
-                    "algorithmic bytes summed over the scenarios (last step's rows and "
-                    "coefficients, mean iterations over the profiled call)"}
+            "bytes_model": f"{B_IT[key]:.0f} B per fluid particle and Krylov iteration, summed "
+                           "over the scenarios (mean iterations over the profiled call)",
+            "assembled_operator_bytes_per_launch": asm,
+            "assembled_operator_frac": asm / (avg_ms / 1e3) / 1e9 / hbm,
+            "note": "all scenarios' pressure solves in one cooperative launch per step"}
     print(json.dumps({"metric": METRIC, "value": nf * steps / (ms / 1e3), "unit": UNIT,
                       "n_gpus": 1, "steps": steps, "warmup": warmup,
                       "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
@@ -386,22 +392,29 @@ class Clocks:
 # algorithmic bytes per unit of each stage (compulsory traffic: every array
 # read or written once per pass; neighbour re-reads are not counted)
 # ---------------------------------------------------------------------------
-def krylov_bytes(iters, rows, nnz, n_cells, mixed=True, dim=2):
-    """Algorithmic bytes of one multigrid-preconditioned BiCGSTAB launch.
-    Per unknown row and iteration the operator is streamed six times (two
-    products and, in each of the two V-cycles, the fine residual and the fine
-    post-smoothing): 6 x (pcnt 4 + diag 8 + (4 col + 4 or 8 value) per
-    coefficient); fine vectors 2 V-cycles x (read 4 inputs + dsc + cell + r0
-    write/read + output write) + products (read p^ or s^, write v or t, read
-    r, rh, s) ~ 30 words of the inner precision.  Coarse levels: per V-cycle
-    each level-1 cell is read (stencil + 4 vectors) in the down and up phases
-    (deeper levels add < 1/3).  Set-up: x, b, the operator once."""
+def krylov_bytes(iters, rows, nnz, n_cells, mixed=True, dim=2, cycle=2):
+    """Bytes one multigrid-preconditioned BiCGSTAB launch of the assembled
+    (large-system) form moves at least, per unknown row and iteration:
+    two operator products, each streaming the row (pcnt 4 + diag 8 + (4 col +
+    4 or 8 value) per coefficient); the two V-cycles' fine phases -- cycle 2,
+    V(0,1) through the row-cell operator: restriction of the input, then the
+    3^d row-cell entries plus row index, cell, D^-1, input and output; cycle
+    1, V(1,1): the fine residual and the post-smoothing each stream the row
+    again -- and the BiCGSTAB vectors (~24 words of the inner precision).
+    Coarse levels: per V-cycle each level-1 cell is read (stencil + 4 vectors)
+    in the down and up phases (deeper levels add < 1/3).  Set-up: x, b, the
+    operator once (twice with the row-cell operator, which it writes)."""
     w = 4 if mixed else 8
-    nnz_row = nnz / max(rows, 1)
-    per_row_iter = 6 * (12 + (4 + w) * nnz_row) + 30 * w
     S = 9 if dim == 2 else 27
+    nnz_row = nnz / max(rows, 1)
+    row = 12 + (4 + w) * nnz_row
+    if cycle == 2:
+        per_row_iter = 2 * row + 2 * (4 * S + 16 + 3 * w) + 24 * w
+        setup = 16 + 12 + 2 * (4 + w) * nnz_row + 4 * S
+    else:
+        per_row_iter = 6 * row + 30 * w
+        setup = 16 + 12 + (4 + w) * nnz_row
     per_cell_iter = 2 * 2 * (S + 4) * 4 * 4 / 3
-    setup = 16 + 12 + (4 + w) * nnz_row
     return rows * (iters * per_row_iter + setup) + n_cells * iters * per_cell_iter
 
 
@@ -612,7 +625,8 @@ def run_ours(args):
         if sc.dim == 2 and k == 1:
             continue
         n_cells *= int(box[k] / re) + 1
-    asm_bytes = krylov_bytes(it_launch, rows, nnz, n_cells, args.precision == 1, sc.dim)
+    asm_bytes = krylov_bytes(it_launch, rows, nnz, n_cells, args.precision == 1, sc.dim,
+                             last.mg_cycle)
     traffic, traffic_src = None, None
     tr = NCU_TRAFFIC.get(args.workload)
     if tr and name == "krylov" and args.precision == 1:

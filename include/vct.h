@@ -173,11 +173,17 @@ typedef struct {
      *   mg_kappa      scale of the coarse-grid correction
      *   solve_form    1: small-system form (V-cycle inputs formed inside the
      *                 products), 2: large-system form (staged rows), 0: by size
-     * cell_over_re in (0, 1), a negative value or a solve_form other than 0-2
-     * is VCT_ERR_ARG. */
+     *   mg_cycle      large-system form's multigrid cycle: 1: V(1,1) (a fine
+     *                 Jacobi step before and after the coarse correction, each
+     *                 through the assembled rows), 2: V(0,1) whose fine step
+     *                 reads the row-cell operator (per row, the sums of its
+     *                 coefficients over the 3^dim cells around its own: 9 or
+     *                 27 values instead of the row), 0: the default, 2
+     * cell_over_re in (0, 1), a negative value, a solve_form other than 0-2 or
+     * an mg_cycle other than 0-2 is VCT_ERR_ARG. */
     double cell_over_re, mg_omega, mg_kappa;
     int32_t solve_form;
-    int32_t reserved3;
+    int32_t mg_cycle;
 } vct_params;
 
 /* Particle state, caller order, DEVICE arrays of n entries (host arrays for
@@ -202,8 +208,11 @@ typedef struct {
     int64_t kernel_launches;/* kernels this call launched */
     int32_t solve_form;     /* pressure solver that ran: 0 Jacobi BiCGSTAB, 1 multigrid
                              * small-system form (k_krylov_mg_fly), 2 multigrid
-                             * large-system form (k_krylov_mg) */
-    int32_t reserved;
+                             * large-system form (k_krylov_mg, or the batched solve
+                             * of vct_batch_step in that form) */
+    int32_t mg_cycle;       /* its cycle in the large-system form (vct_params.mg_cycle:
+                             * 1 V(1,1), 2 V(0,1) through the row-cell operator); 0
+                             * in the other forms */
 } vct_stats;
 
 /* Stages timed by vct_stage_times, in step order. */

@@ -11,7 +11,9 @@ computes:
                 aggregates);
   mg_omega      Jacobi damping of the multigrid smoother;
   mg_kappa      scale of the coarse-grid correction;
-  solve_form    1: small-system form, 2: large-system form of the solver.
+  solve_form    1: small-system form, 2: large-system form of the solver;
+  mg_cycle      the large-system form's cycle, 1: V(1,1) through the
+                assembled rows, 2: V(0,1) through the row-cell operator.
 
 `tune` times every candidate on one representative scenario per size class
 (CUDA events around a few steps after a warm-up, the iterations per step
@@ -27,16 +29,16 @@ import itertools
 import json
 import math
 
-KNOBS = ("cell_over_re", "mg_omega", "mg_kappa", "solve_form")
+KNOBS = ("cell_over_re", "mg_omega", "mg_kappa", "solve_form", "mg_cycle")
 
 
-def candidates(dim, form=0):
-    """The schedule grid searched per size class."""
+def candidates(dim, form=0, cycles=(0,)):
+    """The schedule grid searched per size class (cycles: the mg_cycle values)."""
     cells = (1.0, 1.25)
     omegas = (0.85, 0.9, 0.95) if dim == 2 else (0.65, 0.7, 0.75)
-    kappas = (1.3, 1.4, 1.5, 1.6) if dim == 2 else (1.1, 1.2, 1.3)
-    return [dict(cell_over_re=c, mg_omega=w, mg_kappa=k, solve_form=form)
-            for c, w, k in itertools.product(cells, omegas, kappas)]
+    kappas = (1.2, 1.3, 1.4, 1.5) if dim == 2 else (1.1, 1.2, 1.3)
+    return [dict(cell_over_re=c, mg_omega=w, mg_kappa=k, solve_form=form, mg_cycle=y)
+            for c, w, k, y in itertools.product(cells, omegas, kappas, cycles)]
 
 
 def size_class(sc):

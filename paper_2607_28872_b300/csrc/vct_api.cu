@@ -198,8 +198,8 @@ vct_status finish(vct_ctx *c, vct_stats *out, int nsteps)
         out->ppe_nnz = cnt[1];
         out->kernel_launches = c->launches;
         out->graph_steps = graph_steps;
-        out->solve_form = c->precond ? (c->mg.fly ? 1 : 2) : 0;
-        out->reserved = 0;
+        out->solve_form = c->precond ? (c->mg.fly && !c->rows_list ? 1 : 2) : 0;
+        out->mg_cycle = out->solve_form == 2 ? (c->mg.rowcell ? 2 : 1) : 0;
     }
     if (c->prof) collect_times(c);
     return (vct_status)code;
@@ -531,7 +531,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         for (int k = 0; k < n_scen; ++k) {
             const vct_ctx *c = ctxs[k];
             const bool rows = !c->mg.fly || expl;
-            total += batch_stage_blocks(s, c->P, c->W, c->mg, states[k]->n, rows, level);
+            total += batch_stage_blocks(s, c->P, c->W, mgs[k], states[k]->n, rows, level);
             if (total > (int64_t)INT32_MAX / 2) too_big = true;
             tables.push_back((int)(too_big ? 0 : total));
         }
@@ -542,7 +542,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
     for (int s = BS_ZERO; s <= BS_MG_LEVEL1; ++s) add(s, 0);
     int maxl = 0;
     for (int k = 0; k < n_scen; ++k) {
-        const int l = batch_coarsen_levels(ctxs[k]->mg);
+        const int l = batch_coarsen_levels(mgs[k]);
         if (l > maxl) maxl = l;
     }
     for (int l = 1; l < maxl; ++l) add(BS_MG_COARSEN, l);
@@ -564,7 +564,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             j.alt = t == 0 ? alt(c) : cur(c);
             j.W = c->W;
             j.P = c->P;
-            j.M = c->mg;
+            j.M = mgs[k];
             memcpy(hplan.data() + (size_t)t * sj_bytes + sizeof(StageJob) * (size_t)k, &j, sizeof j);
         }
     }
@@ -770,7 +770,8 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     if (prm->operators != 0 && prm->operators != 1) return VCT_ERR_ARG;
     if (prm->wall_slip != 0 && prm->wall_slip != 1) return VCT_ERR_ARG;
     if (!(prm->cell_over_re == 0.0 || prm->cell_over_re >= 1.0) || !(prm->mg_omega >= 0.0) ||
-        !(prm->mg_kappa >= 0.0) || prm->solve_form < 0 || prm->solve_form > 2)
+        !(prm->mg_kappa >= 0.0) || prm->solve_form < 0 || prm->solve_form > 2 ||
+        prm->mg_cycle < 0 || prm->mg_cycle > 2)
         return VCT_ERR_ARG;
     // the background cell grid, validated before anything is allocated
     int grid_nc[3];
@@ -1042,6 +1043,13 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         if (getenv("VCT_MG_SWEEPS")) M.coarse_sweeps = atoi(getenv("VCT_MG_SWEEPS"));
         M.presmooth = 1;
         if (getenv("VCT_MG_PRESMOOTH")) M.presmooth = atoi(getenv("VCT_MG_PRESMOOTH"));
+        // large-system form (also when a batch runs a small scenario in it):
+        // V(0,1) cycles through the row-cell operator by default.  Measured on
+        // the 2.1M-particle 3-D beach (krylov ms per step, iterations): V(1,1)
+        // 128.0 / 31.8, V(0,1) 114.1 / 47.3 (each iteration 1.9x cheaper); 64 2-D
+        // scenarios side by side: 29.4 vs 46.6 ms per step.
+        M.rowcell = prm->mg_cycle == 1 ? 0 : 1;
+        if (getenv("VCT_MG_ROWCELL")) M.rowcell = atoi(getenv("VCT_MG_ROWCELL")) != 0;
         long long pos = 0;
         for (int q = 1; q <= M.L; ++q) {
             M.offA[q] = pos;
@@ -1051,6 +1059,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         }
         W.mg_pool = dalloc<float>(c, pos, e);
         W.mg_dsc = dalloc<float>(c, n, e);
+        W.mg_B = M.rowcell ? dalloc<float>(c, (int64_t)M.S * n, e) : nullptr;
         W.cellid = dalloc<int32_t>(c, n, e);
         W.kr0 = dalloc<double>(c, n, e);
         W.kq0 = dalloc<double>(c, n, e);

@@ -98,6 +98,7 @@ struct Work {
     int32_t *cellid;          // level-1 node (cell) of each sorted particle
     float *mg_dsc;            // 1 / diag of each unknown row (0 elsewhere)
     float *mg_pool;           // coarse operators and vectors of all levels
+    float *mg_B;              // row-cell operator (3^d entries per row, entry-major), or null
     double *kr0;              // fine residual of the V-cycle (FP32 or FP64 slots)
     double *kq0, *kq1;        // preconditioned directions p^, s^
     double *kz0, *kzb;        // V-cycle: first Jacobi step and prolonged correction
@@ -144,6 +145,8 @@ struct MG {
     int fly;                       // 1: V-cycle inputs formed on the fly (small systems)
     int staged;                    // large-system form: rows staged by cp.async
     int gather_l1;                 // large-system form: fine gathers through L1
+    int rowcell;                   // large-system form: V(0,1) cycles whose fine post-smoothing
+                                   // reads the row-cell operator W.mg_B (0: V(1,1) cycles)
     long long stage_off;           // byte offset of the row-staging area (large systems)
     long long smem_bytes;          // dynamic shared memory of the solver launch
 };
@@ -162,15 +165,15 @@ struct FlyJob {
 // step except the pressure solve runs as one launch over all scenarios, every
 // scenario on a contiguous range of the launch's blocks.  The members most
 // stages read come first, so that a block copies into shared memory only the
-// prefix its stage reads; every member's size is a multiple of 16 bytes.
+// prefix its stage reads; every member starts on a 16-byte boundary.
 struct StageJob {
     int64_t n;
     int64_t reserved;
-    Part cur;                 // the sorted state the stage reads
-    Work W;
-    DevParams P;
-    Part alt;                 // the other buffer set (reorder target)
-    MG M;
+    alignas(16) Part cur;     // the sorted state the stage reads
+    alignas(16) Work W;
+    alignas(16) DevParams P;
+    alignas(16) Part alt;     // the other buffer set (reorder target)
+    alignas(16) MG M;
 };
 
 // Stages of a batched step, in step order (BS_MG_COARSEN once per level).
@@ -179,7 +182,7 @@ enum BatchStage {
     BS_CELL_SORT, BS_REORDER,
     BS_NEIGHBOURS, BS_SMOOTHING, BS_JBAR_COPY, BS_WALL_VELOCITY, BS_PASS1, BS_PASS2,
     BS_PASS2_ISPH, BS_RHS, BS_UROW_FLAGS, BS_RSCAN_BLOCKS, BS_RSCAN_TOPS, BS_RSCAN_ADD,
-    BS_UROW_SCATTER, BS_MG_DSC, BS_MG_LEVEL1, BS_MG_COARSEN, BS_MG_COARSEN_SMALL,
+    BS_UROW_SCATTER, BS_MG_DSC, BS_MG_ROWCELL, BS_MG_LEVEL1, BS_MG_COARSEN, BS_MG_COARSEN_SMALL,
     BS_CORRECTOR, BS_CORRECTOR_SUM, BS_REG_GEOM, BS_REG_DS, BS_REG_APPLY,
     BS_COUNT
 };
@@ -215,6 +218,8 @@ int launch_krylov(const DevParams &P, Part cur, Work W, int64_t n, int step_slot
 void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStream_t st,
                      bool rows_list);
 int mg_setup_launches(const MG &M);
+// the large-system form's V(0,1) cycles with the row-cell operator
+bool mg_rowcell_on(const MG &M);
 int launch_krylov_mg(const DevParams &P, Work W, const MG &M, int64_t n, int nblocks_coop,
                      cudaStream_t st);
 bool krylov_mg_fly_default(long long rows, int dim);

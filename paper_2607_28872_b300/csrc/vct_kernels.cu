@@ -1898,6 +1898,16 @@ void launch_rhs(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st
 // bit-reproducible runs).
 // ---------------------------------------------------------------------------
 constexpr int KT = 256;
+// Solver blocks per SM the large-system and the batched solvers are compiled
+// for (register budget 65536 / (KT x this)).  Measured, krylov ms per step:
+// 2.1M-particle 3-D beach, V(0,1) cycles, 2 blocks 121.6, 3 blocks 114.1, 4
+// blocks 116.2; 64 2-D scenarios side by side, 2 blocks 29.4, 3 blocks 18.8.
+#ifndef VCT_KMG_MINB
+#define VCT_KMG_MINB 3
+#endif
+#ifndef VCT_KBATCH_MINB
+#define VCT_KBATCH_MINB 3
+#endif
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned int *p)
 {
@@ -2436,6 +2446,53 @@ __global__ void k_mg_level1(Work W, MG M, int mixed)
     mg_level1_body<D>(W, M, mixed, blockIdx.x);
 }
 
+// Row-cell operator of the large-system form's V(0,1) cycle: for every unknown
+// row i and each of the 3^d cells around its own, the sum of the row's
+// coefficients on the particles of that cell (the diagonal in its own cell's
+// entry), B[o][i] = sum over k in cell(i) + o of a_ik.  For a correction
+// prolonged from the cells, zb_k = zu(cell(k)), (A zb)_i = sum_o B[o][i]
+// zu(cell(i) + o): the fine post-smoothing then reads 3^d values per row
+// instead of the row's coefficients and one gather per neighbour.  The lanes
+// of a row's group take its slots in turn; the 3^d sums are reduced across the
+// group in a fixed order.
+template <int D>
+__device__ __forceinline__ void mg_rowcell_body(const Work &W, const MG &M, int n, int mixed, int bid_)
+{
+    if (step_failed(W.status)) return;
+    constexpr int S = D == 2 ? 9 : 27, G = ell_group<D>();
+    const int lg = threadIdx.x & (G - 1);
+    const int i = (int)((bid_ * (unsigned)blockDim.x + threadIdx.x) / G);
+    if (i >= n) return;
+    const int pc = W.pcnt[i];   // the same for the row's whole group
+    if (pc < 0) return;
+    float acc[S];
+#pragma unroll
+    for (int o = 0; o < S; ++o) acc[o] = 0.f;
+    int cx, cy, cz;
+    mg_coords(M, 1, W.cellid[i], cx, cy, cz);
+    const int64_t cap = W.cap;
+    for (int kk = lg; kk < pc; kk += G) {
+        const int64_t q = ell_at<G>(kk, i, cap);
+        const int j = W.pcol[q];
+        const float av = mixed ? W.pvalf[q] : (float)W.pval[q];
+        int jx, jy, jz;
+        mg_coords(M, 1, W.cellid[j], jx, jy, jz);
+        stencil_add<S>(acc, stencil_index<D>(jx - cx, jy - cy, jz - cz), av);
+    }
+#pragma unroll
+    for (int o = 0; o < S; ++o) acc[o] = group_sum<G>(acc[o]);
+    if (lg != 0) return;
+    acc[stencil_index<D>(0, 0, 0)] += (float)W.diag[i];
+#pragma unroll
+    for (int o = 0; o < S; ++o) W.mg_B[(int64_t)o * cap + i] = acc[o];
+}
+
+template <int D>
+__global__ void k_mg_rowcell(Work W, MG M, int n, int mixed)
+{
+    mg_rowcell_body<D>(W, M, n, mixed, blockIdx.x);
+}
+
 // Node Ic of level l+1 from level l: sums of the children's stencils.
 template <int D>
 __device__ void coarsen_node(const Work &W, const MG &M, int l, int Ic)
@@ -2573,6 +2630,11 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
     k_mg_dsc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
     const unsigned g1 = (unsigned)(((int64_t)M.n[1] * 32 + 255) / 256);   // a warp per cell
     const int mixed = P.precision == VCT_MIXED;
+    if (mg_rowcell_on(M)) {   // a row group per row
+        const unsigned gr = (unsigned)((n * (P.dim == 2 ? 4 : 8) + 255) / 256);
+        if (P.dim == 2) k_mg_rowcell<2><<<gr, 256, 0, st>>>(W, M, (int)n, mixed);
+        else k_mg_rowcell<3><<<gr, 256, 0, st>>>(W, M, (int)n, mixed);
+    }
     if (P.dim == 2) k_mg_level1<2><<<g1, 256, 0, st>>>(W, M, mixed);
     else k_mg_level1<3><<<g1, 256, 0, st>>>(W, M, mixed);
     int l = 1;
@@ -2587,9 +2649,14 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
     }
 }
 
+bool mg_rowcell_on(const MG &M)
+{
+    return M.rowcell != 0 && M.fly == 0;
+}
+
 int mg_setup_launches(const MG &M)
 {
-    int l = 1, n = 2;   // dsc, level 1
+    int l = 1, n = mg_rowcell_on(M) ? 3 : 2;   // dsc, (row-cell operator,) level 1
     for (; l < M.L && M.n[l + 1] > small_level(); ++l) ++n;
     return n + (l < M.L ? 1 : 0);
 }
@@ -2653,34 +2720,49 @@ __device__ __forceinline__ float ldv(const float *p)
 }
 
 // Down phase: nodes of the coarse level c sum the residuals of their children
-// in f and take one damped Jacobi step from zero.
+// in f and take one damped Jacobi step from zero.  The G = 2^(shifts) children
+// of a coarse node (2, 4 or 8) are the lanes of one group of G consecutive
+// lanes, each lane one child's residual, summed across the group by shuffles
+// in a fixed order: G x (coarse nodes) threads share the work instead of one
+// thread per coarse node walking its children (measured on the 3-D slice: a
+// level's down phase 65.6 -> 17.1 us on average).  start and stride are
+// multiples of 32, so a group
+// never straddles a warp and its lanes always run the same trips.
 template <int D, bool GL>
 __device__ void lv_down(const LV &f, const LV &c, float om, int start, int stride)
 {
-    for (int Ic = start; Ic < c.n; Ic += stride) {
+    const int sy = D == 3 ? f.shy : 0;
+    const int lg2 = f.shx + sy + f.shz;
+    const int G = 1 << lg2;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+    const long long total = (long long)c.n << lg2;
+    for (long long q = start; q < total; q += stride) {
+        const int Ic = (int)(q >> lg2), ch = (int)(q & (G - 1));
         const int px = Ic % c.nx, pr = Ic / c.nx, py = pr % c.ny, pz = pr / c.ny;
-        float bsum = 0.f;
-        const int sy = D == 3 ? f.shy : 0;
-        for (int ch = 0; ch < (1 << (f.shx + sy + f.shz)); ++ch) {
-            const int ax = (px << f.shx) + (ch & ((1 << f.shx) - 1));
-            const int ay = D == 3 ? (py << f.shy) + ((ch >> f.shx) & ((1 << f.shy) - 1)) : 0;
-            const int az = (pz << f.shz) + (ch >> (f.shx + sy));
-            if (ax >= f.nx || ay >= f.ny || az >= f.nz) continue;
+        const int ax = (px << f.shx) + (ch & ((1 << f.shx) - 1));
+        const int ay = D == 3 ? (py << f.shy) + ((ch >> f.shx) & ((1 << f.shy) - 1)) : 0;
+        const int az = (pz << f.shz) + (ch >> (f.shx + sy));
+        float res = 0.f;
+        if (ax < f.nx && ay < f.ny && az < f.nz) {
             const int If = (az * f.ny + ay) * f.nx + ax;
-            if (f.dinv[If] == 0.f) continue;
-            float res = ldv<GL>(f.b + If);
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int jx = ax + dx, jy = ay + dy, jz = az + dz;
-                        if (jx < 0 || jy < 0 || jz < 0 || jx >= f.nx || jy >= f.ny || jz >= f.nz) continue;
-                        res -= f.A[(int64_t)stencil_index<D>(dx, dy, dz) * f.n + If] *
-                               ldv<GL>(f.z + (jz * f.ny + jy) * f.nx + jx);
-                    }
-            bsum += res;
+            if (f.dinv[If] != 0.f) {
+                res = ldv<GL>(f.b + If);
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int jx = ax + dx, jy = ay + dy, jz = az + dz;
+                            if (jx < 0 || jy < 0 || jz < 0 || jx >= f.nx || jy >= f.ny || jz >= f.nz) continue;
+                            res -= f.A[(int64_t)stencil_index<D>(dx, dy, dz) * f.n + If] *
+                                   ldv<GL>(f.z + (jz * f.ny + jy) * f.nx + jx);
+                        }
+            }
         }
-        c.b[Ic] = bsum;
-        c.z[Ic] = om * bsum * c.dinv[Ic];
+        for (int o = G >> 1; o > 0; o >>= 1) res += __shfl_xor_sync(gmask, res, o, G);
+        if (ch == 0) {
+            c.b[Ic] = res;
+            c.z[Ic] = om * res * c.dinv[Ic];
+        }
     }
 }
 
@@ -2904,10 +2986,13 @@ __device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT,
     cp_async_wait<0>();
 }
 
-// z_out = M^-1 v.  On entry v and z0 = omega D^-1 v (the first Jacobi step from
-// zero) are in memory for every unknown row and visible grid-wide; each fine
-// product then gathers one value per neighbour.  Returns false if a grid
-// barrier timed out.
+// z_out = M^-1 v.  V(1,1) (M.rowcell = 0): on entry v and z0 = omega D^-1 v
+// (the first Jacobi step from zero) are in memory for every unknown row and
+// visible grid-wide; each fine product gathers one value per neighbour.
+// V(0,1) (M.rowcell = 1): v alone; the cells take the restriction of v, and the
+// fine post-smoothing reads the row-cell operator W.mg_B and the cells'
+// correction instead of the rows' coefficients (z0, zb unused).  Returns false
+// if a grid barrier timed out.
 template <typename T, typename CT, int G, int NS, int D>
 __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT, NS> &S, int n,
                        const T *v, const T *z0, T *zb, T *zout, int lg, bool lead, int g0, int ngroups,
@@ -2916,24 +3001,29 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
     const unsigned nb = vnb;
     const float om = M.omega, kap = M.kappa;
     const bool l1 = M.gather_l1 != 0;
+    const bool rc = M.rowcell != 0;
     const int32_t *urow = W.urow;
     const int nu = W.urow_pos[n];
     T *r0 = (T *)W.kr0;
-    // D0: fine residual r0 = v - A z0
-    rows_pipelined<T, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(z0, j, l1); },
-        [&](int i) { return Own4<T>{{__ldcg(v + i), __ldcg(z0 + i), (T)W.diag[i], T(0)}}; },
-        [&](int i, T acc, const Own4<T> &o) {
-            if (lead) r0[i] = o.v[0] - acc - o.v[2] * o.v[1];
-        });
-    if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
-    // D1: restriction to the cells, one Jacobi step from zero on level 1
+    if (!rc) {
+        // D0: fine residual r0 = v - A z0
+        rows_pipelined<T, CT, G, NS>(W, S, urow, nu, g0, ngroups, lg, [&](int j) { return ldx(z0, j, l1); },
+            [&](int i) { return Own4<T>{{__ldcg(v + i), __ldcg(z0 + i), (T)W.diag[i], T(0)}}; },
+            [&](int i, T acc, const Own4<T> &o) {
+                if (lead) r0[i] = o.v[0] - acc - o.v[2] * o.v[1];
+            });
+        if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
+    }
+    // D1: restriction to the cells (of r0, or of v in V(0,1)), one Jacobi step
+    // from zero on level 1
     {
         const LV c = lv_global(W, M, 1);
+        const T *rs = rc ? v : r0;
         for (int I = gtid; I < c.n; I += gthreads) {
             float bs = 0.f;
             const int a = W.cell_start[I], b = W.cell_start[I + 1];
             for (int i = a; i < b; ++i)
-                if (W.pcnt[i] >= 0) bs += (float)__ldcg(r0 + i);
+                if (W.pcnt[i] >= 0) bs += (float)__ldcg(rs + i);
             c.b[I] = bs;
             c.z[I] = M.omega_c * bs * c.dinv[I];
         }
@@ -2971,6 +3061,36 @@ __device__ bool vcycle(const Work &W, const MG &M, float *sh, const RowStage<CT,
     for (int l = fl - 1; l >= 1; --l) {
         lv_up<D, true>(lv_global(W, M, l), lv_global(W, M, l + 1), M.omega_c, M.kappa_c, gtid, gthreads);
         if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return false;
+    }
+    if (rc) {
+        // U0 of V(0,1): zb = kappa zu_1(cell) and one damped Jacobi step,
+        // z = zb + omega D^-1 (v - A zb) with (A zb)_i = kappa sum_o B[o][i] zu_1(cell(i) + o)
+        const float *zu1 = W.mg_pool + M.offv[1] + 3 * M.n[1];
+        const int nx = M.dims[1][0], ny = M.dims[1][1], nz = M.dims[1][2];
+        const int64_t cap = W.cap;
+        const float *B = W.mg_B;
+        for (int q = gtid; q < nu; q += gthreads) {
+            const int i = __ldg(urow + q);
+            const int I = W.cellid[i];
+            int cx, cy, cz;
+            mg_coords(M, 1, I, cx, cy, cz);
+            float acc = 0.f;
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                for (int dy = (D == 3 ? -1 : 0); dy <= (D == 3 ? 1 : 0); ++dy)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int jx = cx + dx, jy = cy + dy, jz = cz + dz;
+                        if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
+                        acc += __ldg(B + (int64_t)stencil_index<D>(dx, dy, dz) * cap + i) *
+                               __ldcg(zu1 + (jz * ny + jy) * nx + jx);
+                    }
+            const T zi = (T)kap * (T)__ldcg(zu1 + I);
+            const T res = __ldcg(v + i) - (T)kap * (T)acc;
+            zout[i] = zi + (T)om * res * (T)W.mg_dsc[i];
+        }
+        return grid_barrier(W.bar, nb, W.status, vb, W.spin_limit);
     }
     // P0: prolongation from the cells, zb = z0 + kappa zu_1(cell)
     {
@@ -3014,6 +3134,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
     const int32_t *urow = W.urow;
     const int nu = W.urow_pos[n];
     const bool l1 = M.gather_l1 != 0;
+    const bool rc = M.rowcell != 0;
     const float om = M.omega;
     double *x = W.kx, *f = W.kf;
     T *r = (T *)W.kr, *rh = (T *)W.krh, *s = (T *)W.ks, *t = (T *)W.kt, *dl = (T *)W.kd;
@@ -3077,7 +3198,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 }
                 r[i] = ri;
                 pnew[i] = pn;
-                z0[i] = (T)om * pn * (T)W.mg_dsc[i];
+                if (!rc) z0[i] = (T)om * pn * (T)W.mg_dsc[i];
             }
             if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, pnew, z0, zb, ph, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb))
@@ -3113,7 +3234,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
                 const int i = __ldg(urow + q);
                 const T si = r[i] - ta2 * __ldcg(vnew + i);
                 s[i] = si;
-                z0[i] = (T)om * si * (T)W.mg_dsc[i];
+                if (!rc) z0[i] = (T)om * si * (T)W.mg_dsc[i];
             }
             if (!grid_barrier(W.bar, nb, W.status, vb, W.spin_limit)) return;
             if (!vcycle<T, CT, G, NS, D>(W, M, mg_sh, S, n, s, z0, zb, sh, lg, lead, g0, ngroups, gtid, gthreads, vb, vnb))
@@ -3181,7 +3302,7 @@ __device__ void krylov_explicit_solve(const Work &W, const MG &M, int n, int max
 }
 
 template <typename T, typename CT, int G, int NS, int D>
-__global__ void __launch_bounds__(KT, 2) k_krylov_mg(Work W, MG M, int n, int maxit, double rtol,
+__global__ void __launch_bounds__(KT, VCT_KMG_MINB) k_krylov_mg(Work W, MG M, int n, int maxit, double rtol,
                                                   double inner_floor, int32_t *iters_out,
                                                   double *resid_out)
 {
@@ -3506,7 +3627,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly_tr(Work W, MG M, int n, in
 static_assert(sizeof(FlyJob) % sizeof(int) == 0, "FlyJob copies as ints");
 
 template <typename T, typename CT, int G, int NS, int D, bool EXPL>
-__global__ void __launch_bounds__(KT, 2) k_krylov_fly_batch(const FlyJob *jobs, int njobs)
+__global__ void __launch_bounds__(KT, VCT_KBATCH_MINB) k_krylov_fly_batch(const FlyJob *jobs, int njobs)
 {
     __shared__ __align__(16) FlyJob job;
     __shared__ int jid;
@@ -5787,9 +5908,9 @@ void launch_rhopos(const DevParams &P, Part cur, Work W, int64_t n, const double
 // memory and runs the stage's body as block b - bs[k] of the scenario's own
 // launch, so every scenario computes exactly what its own launches compute.
 // ---------------------------------------------------------------------------
-static_assert(sizeof(Part) % 16 == 0 && sizeof(Work) % 16 == 0 && sizeof(DevParams) % 16 == 0 &&
-                  sizeof(MG) % 16 == 0 && sizeof(StageJob) % 16 == 0,
-              "StageJob members are copied in 16-byte words");
+static_assert(offsetof(StageJob, P) % 16 == 0 && offsetof(StageJob, alt) % 16 == 0 &&
+                  offsetof(StageJob, M) % 16 == 0 && sizeof(StageJob) % 16 == 0,
+              "StageJob prefixes are copied in 16-byte words");
 constexpr int SJ_CW = (int)offsetof(StageJob, P);      // n, cur, W
 constexpr int SJ_CWP = (int)offsetof(StageJob, alt);   // + P
 constexpr int SJ_CWPA = (int)offsetof(StageJob, M);    // + alt
@@ -5944,6 +6065,14 @@ struct BMgDsc {
     __device__ void operator()(const StageJob &j, int b) const { mg_dsc_body(j.W, (int)j.n, b); }
 };
 template <int D, typename R>
+struct BMgRowcell {
+    static constexpr int NT = 256, MINB = 1, BYTES = SJ_ALL;
+    __device__ void operator()(const StageJob &j, int b) const
+    {
+        mg_rowcell_body<D>(j.W, j.M, (int)j.n, j.P.precision == VCT_MIXED, b);
+    }
+};
+template <int D, typename R>
 struct BMgLevel1 {
     static constexpr int NT = 256, MINB = 1, BYTES = SJ_ALL;
     __device__ void operator()(const StageJob &j, int b) const
@@ -6029,6 +6158,7 @@ int batch_stage_blocks(int s, const DevParams &P, const Work &W, const MG &M, in
         snb = (n + SCAN_B - 1) / SCAN_B;
         return rows_list ? (snb == 0 ? 1 : (int)snb) : 0;
     case BS_RSCAN_TOPS: return rows_list ? 1 : 0;
+    case BS_MG_ROWCELL: return mg_rowcell_on(M) ? (int)((n * (P.dim == 2 ? 4 : 8) + 255) / 256) : 0;
     case BS_MG_LEVEL1: return (int)(((int64_t)M.n[1] * 32 + 255) / 256);
     case BS_MG_COARSEN: return level >= 1 && level < lend ? (M.n[level + 1] + 127) / 128 : 0;
     case BS_MG_COARSEN_SMALL: return lend < M.L ? 1 : 0;
@@ -6088,6 +6218,7 @@ void launch_batched(int s, int dim, int precision, const StageJob *jobs, const i
     case BS_RSCAN_ADD: run_batched(jobs, bs, njobs, total, BScanAdd<false>{}, st); break;
     case BS_UROW_SCATTER: run_batched(jobs, bs, njobs, total, BUrowScatter{}, st); break;
     case BS_MG_DSC: run_batched(jobs, bs, njobs, total, BMgDsc{}, st); break;
+    case BS_MG_ROWCELL: run_dr<BMgRowcell>(dim, mx, jobs, bs, njobs, total, st); break;
     case BS_MG_LEVEL1: run_dr<BMgLevel1>(dim, mx, jobs, bs, njobs, total, st); break;
     case BS_MG_COARSEN: run_dr<BMgCoarsen>(dim, mx, jobs, bs, njobs, total, st, level); break;
     case BS_MG_COARSEN_SMALL: run_dr<BMgCoarsenSmall>(dim, mx, jobs, bs, njobs, total, st, small_level()); break;

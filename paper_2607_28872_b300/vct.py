@@ -50,7 +50,7 @@ class vct_params(C.Structure):
         ("ops_shift", C.c_double), ("ds_overlap", C.c_double), ("xsph_eps", C.c_double),
         ("spin_limit", C.c_int64), ("operators", C.c_int32), ("wall_slip", C.c_int32),
         ("cell_over_re", C.c_double), ("mg_omega", C.c_double), ("mg_kappa", C.c_double),
-        ("solve_form", C.c_int32), ("reserved3", C.c_int32)]
+        ("solve_form", C.c_int32), ("mg_cycle", C.c_int32)]
 
 
 class vct_state(C.Structure):
@@ -62,7 +62,7 @@ class vct_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("krylov_iters_total", C.c_int64),
                 ("krylov_iters_max", C.c_int32), ("graph_steps", C.c_int32),
                 ("last_residual", C.c_double), ("ppe_rows", C.c_int64), ("ppe_nnz", C.c_int64),
-                ("kernel_launches", C.c_int64), ("solve_form", C.c_int32), ("reserved", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("solve_form", C.c_int32), ("mg_cycle", C.c_int32)]
 
 
 STAGES = ("load", "map", "sort", "neighbours", "smoothing", "pass1", "pass2", "rhs", "precond",
@@ -186,6 +186,7 @@ def make_params(sc, **over):
     for k in ("cell_over_re", "mg_omega", "mg_kappa"):
         setattr(P, k, float(p.get(k, 0.0)))
     P.solve_form = int(p.get("solve_form", 0))
+    P.mg_cycle = int(p.get("mg_cycle", 0))
     return P
 
 

@@ -73,3 +73,20 @@ def test_cell_grid_is_validated_before_any_device_work():
                                               ctypes.cast(row, ctypes.c_void_p), None, 0,
                                               ctypes.byref(nnz), None)
         assert rc == want, (name, rc)
+
+
+def test_schedule_knobs_are_validated_on_the_host():
+    """vct_init rejects schedule knobs outside their ranges (cell edge below
+    r_e, negative damping or scale, unknown solver form or multigrid cycle)
+    before any CUDA call."""
+    from paper_2607_28872_b300 import scenarios as S
+    lib = vct.load_library()
+    sc = S.small_tank(dim=2, kind="BF", L=0.1, H=0.05, d0=0.01)
+    bathy, keep = vct.make_bathymetry(sc.bathy)
+    for over in (dict(cell_over_re=0.5), dict(mg_omega=-0.1), dict(mg_kappa=-1.0),
+                 dict(solve_form=3), dict(mg_cycle=3), dict(mg_cycle=-1)):
+        P = vct.make_params(sc, **over)
+        ctx = ctypes.c_void_p()
+        rc = lib.vct_init(ctypes.byref(ctx), ctypes.byref(bathy), vct.MAP[sc.map_kind], 1.0,
+                          ctypes.byref(P), sc.n, None)
+        assert rc == vct.VCT_ERR_ARG and not ctx, (over, rc)
