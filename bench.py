@@ -114,7 +114,10 @@ WORKLOADS = {
 # without an entry reports traffic null.  "per_unit": bytes per fluid particle
 # per Krylov iteration (the 3-D beach is captured on its 8 x 1.6 m slice; its
 # traffic grows with rows x iterations); "per_launch": bytes per launch.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "beach_bfe_3d": ("per_unit", 1690.0, "profiles/k_krylov_mg_beach_bfe_3d_slice_540k.md"),
+    "beach_bfe_3d_slice": ("per_unit", 1690.0, "profiles/k_krylov_mg_beach_bfe_3d_slice_540k.md"),
+}
 
 
 def workload(precision=1, name="sigma_solitary"):

@@ -2868,6 +2868,14 @@ __device__ __forceinline__ const float *coef_ptr<float>(const Work &W) { return 
 #define VCT_ROW_STAGES 2
 #endif
 constexpr int ROW_STAGES = VCT_ROW_STAGES;
+// Slots of a row each lane of a 3-D row group (8 lanes) loads before the row's
+// count is known, and stages in the large-system form: 8 x NS3 slots cover a
+// row without a second round trip (3-D rows hold ~57-66 coefficients; measured
+// on the 2.1M-particle beach, solve per step: 7 slots 90.8 ms, 8 86.8, 9 85.2)
+#ifndef VCT_NS3
+#define VCT_NS3 9
+#endif
+constexpr int NS3 = VCT_NS3;
 
 template <typename CT, int NS>
 struct RowStage {
@@ -2953,18 +2961,31 @@ __device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT,
         }
         return;
     }
-    static_assert(ROW_STAGES == 2, "the row-index prefetch below assumes two stages");
-    int b = 0;   // stage of the current row
-    int icur = g0 < nr ? __ldg(rows + g0) : 0;
-    if (g0 < nr) stage_row<CT, G, NS>(W, S, 0, icur, lg);
-    cp_async_commit();
-    int inext = g0 + ngroups < nr ? __ldg(rows + g0 + ngroups) : 0;
-    for (int q = g0; q < nr; q += ngroups) {
-        const int i = icur;
-        if (q + ngroups < nr) stage_row<CT, G, NS>(W, S, b ^ 1, inext, lg);
+    constexpr int R = ROW_STAGES;
+    static_assert(R >= 2 && R <= 4, "2 to 4 row stages");
+    // iq[k]: index of row q + k ngroups.  At the top of an iteration rows q ..
+    // q + (R - 2) ngroups are staged (stages b, b + 1, ... mod R); row
+    // q + (R - 1) ngroups is staged now and the index R rows ahead loaded, so
+    // the list adds no round trip.
+    int iq[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int qk = g0 + k * ngroups;
+        iq[k] = qk < nr ? __ldg(rows + qk) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < R - 1; ++k) {
+        if (g0 + k * ngroups < nr) stage_row<CT, G, NS>(W, S, k, iq[k], lg);
         cp_async_commit();
-        const int iafter = q + 2 * ngroups < nr ? __ldg(rows + q + 2 * ngroups) : 0;
-        cp_async_wait<ROW_STAGES - 1>();
+    }
+    int b = 0;   // stage of the current row
+    for (int q = g0; q < nr; q += ngroups) {
+        const int i = iq[0];
+        const int bs = b + R - 1 >= R ? b - 1 : b + R - 1;
+        if (q + (R - 1) * ngroups < nr) stage_row<CT, G, NS>(W, S, bs, iq[R - 1], lg);
+        cp_async_commit();
+        const int iafter = q + R * ngroups < nr ? __ldg(rows + q + R * ngroups) : 0;
+        cp_async_wait<R - 1>();
         const int pc = S.pc[b * KT + t];
         const auto o = own(i);
         T acc = T(0);
@@ -2976,9 +2997,10 @@ __device__ __forceinline__ void rows_pipelined(const Work &W, const RowStage<CT,
             const int64_t q = ell_at<G>(kk, i, cap);
             acc += (T)coef<CT>(W, q) * getx(W.pcol[q]);
         }
-        b ^= 1;
-        icur = inext;
-        inext = iafter;
+        b = b + 1 == R ? 0 : b + 1;
+#pragma unroll
+        for (int k = 0; k < R - 1; ++k) iq[k] = iq[k + 1];
+        iq[R - 1] = iafter;
         if (pc < 0) continue;
         acc = group_sum<G>(acc);
         body(i, acc, o);
@@ -3664,15 +3686,15 @@ static const void *krylov_mg_fn(int precision, int dim, bool fly)
     if (fly) {
         if (precision == VCT_MIXED)
             return dim == 2 ? (const void *)k_krylov_mg_fly<float, float, 4, 5, 2>
-                            : (const void *)k_krylov_mg_fly<float, float, 8, 7, 3>;
+                            : (const void *)k_krylov_mg_fly<float, float, 8, NS3, 3>;
         return dim == 2 ? (const void *)k_krylov_mg_fly<double, double, 4, 5, 2>
-                        : (const void *)k_krylov_mg_fly<double, double, 8, 7, 3>;
+                        : (const void *)k_krylov_mg_fly<double, double, 8, NS3, 3>;
     }
     if (precision == VCT_MIXED)
         return dim == 2 ? (const void *)k_krylov_mg<float, float, 4, 5, 2>
-                        : (const void *)k_krylov_mg<float, float, 8, 7, 3>;
+                        : (const void *)k_krylov_mg<float, float, 8, NS3, 3>;
     return dim == 2 ? (const void *)k_krylov_mg<double, double, 4, 5, 2>
-                    : (const void *)k_krylov_mg<double, double, 8, 7, 3>;
+                    : (const void *)k_krylov_mg<double, double, 8, NS3, 3>;
 }
 
 bool krylov_mg_fly_default(long long rows, int dim)
@@ -3683,8 +3705,8 @@ bool krylov_mg_fly_default(long long rows, int dim)
 size_t krylov_mg_stage_bytes(int precision, int dim, bool staged)
 {
     if (!staged) return 0;
-    if (precision == VCT_MIXED) return dim == 2 ? row_stage_bytes<float, 5>() : row_stage_bytes<float, 7>();
-    return dim == 2 ? row_stage_bytes<double, 5>() : row_stage_bytes<double, 7>();
+    if (precision == VCT_MIXED) return dim == 2 ? row_stage_bytes<float, 5>() : row_stage_bytes<float, NS3>();
+    return dim == 2 ? row_stage_bytes<double, 5>() : row_stage_bytes<double, NS3>();
 }
 
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly)
@@ -3728,9 +3750,9 @@ static const void *krylov_batch_fn_form(int precision, int dim)
 {
     if (precision == VCT_MIXED)
         return dim == 2 ? (const void *)k_krylov_fly_batch<float, float, 4, 5, 2, EXPL>
-                        : (const void *)k_krylov_fly_batch<float, float, 8, 7, 3, EXPL>;
+                        : (const void *)k_krylov_fly_batch<float, float, 8, NS3, 3, EXPL>;
     return dim == 2 ? (const void *)k_krylov_fly_batch<double, double, 4, 5, 2, EXPL>
-                    : (const void *)k_krylov_fly_batch<double, double, 8, 7, 3, EXPL>;
+                    : (const void *)k_krylov_fly_batch<double, double, 8, NS3, 3, EXPL>;
 }
 
 static const void *krylov_fly_batch_fn(int precision, int dim, bool expl)
@@ -5172,9 +5194,9 @@ static const void *adj_mg_fn(int precision, int dim)
 {
     if (precision == VCT_MIXED)
         return dim == 2 ? (const void *)k_krylov_mg_fly_tr<float, float, 4, 5, 2>
-                        : (const void *)k_krylov_mg_fly_tr<float, float, 8, 7, 3>;
+                        : (const void *)k_krylov_mg_fly_tr<float, float, 8, NS3, 3>;
     return dim == 2 ? (const void *)k_krylov_mg_fly_tr<double, double, 4, 5, 2>
-                    : (const void *)k_krylov_mg_fly_tr<double, double, 8, 7, 3>;
+                    : (const void *)k_krylov_mg_fly_tr<double, double, 8, NS3, 3>;
 }
 
 int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_t n,
