@@ -580,10 +580,12 @@ __global__ void k_store_w(DevParams P, Part c, vct_state s, int n, const int32_t
 // ---------------------------------------------------------------------------
 // a1: map + metric + cell key (current order)
 // ---------------------------------------------------------------------------
+// Cell index along one axis, clamped to the grid before the integer
+// conversion; a non-finite coordinate (NaN) goes to cell 0.
 __device__ __forceinline__ int cell_coord(const DevParams &P, double xh, int axis)
 {
     double f = floor((xh - P.box_lo[axis]) * P.inv_cell_h);
-    int c = f < 0.0 ? 0 : (f > (double)(P.nc[axis] - 1) ? P.nc[axis] - 1 : (int)f);
+    int c = !(f >= 0.0) ? 0 : (f > (double)(P.nc[axis] - 1) ? P.nc[axis] - 1 : (int)f);
     return c;
 }
 
@@ -1901,12 +1903,14 @@ constexpr int KT = 256;
 // Solver blocks per SM the large-system and the batched solvers are compiled
 // for (register budget 65536 / (KT x this)).  Measured, krylov ms per step:
 // 2.1M-particle 3-D beach, V(0,1) cycles, 2 blocks 121.6, 3 blocks 114.1, 4
-// blocks 116.2; 64 2-D scenarios side by side, 2 blocks 29.4, 3 blocks 18.8.
+// blocks 116.2 (after the later changes: 3 blocks 85.1, 4 blocks 95.8); 64 2-D
+// scenarios side by side, 2 blocks 29.4, 3 blocks 18.8 (later: 3 blocks 100.7,
+// 4 blocks 105.4 M particle-updates/s for the whole step).
 #ifndef VCT_KMG_MINB
 #define VCT_KMG_MINB 3
 #endif
 #ifndef VCT_KBATCH_MINB
-#define VCT_KBATCH_MINB 3
+#define VCT_KBATCH_MINB 4   // the batch in the large-system form (the small-system form: 2)
 #endif
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned int *p)
@@ -3649,7 +3653,7 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly_tr(Work W, MG M, int n, in
 static_assert(sizeof(FlyJob) % sizeof(int) == 0, "FlyJob copies as ints");
 
 template <typename T, typename CT, int G, int NS, int D, bool EXPL>
-__global__ void __launch_bounds__(KT, VCT_KBATCH_MINB) k_krylov_fly_batch(const FlyJob *jobs, int njobs)
+__global__ void __launch_bounds__(KT, EXPL ? VCT_KBATCH_MINB : 2) k_krylov_fly_batch(const FlyJob *jobs, int njobs)
 {
     __shared__ __align__(16) FlyJob job;
     __shared__ int jid;

@@ -513,7 +513,10 @@ class Checkpointer:
     `every` steps, and the states of one segment recomputed from its checkpoint
     on demand.  The context's pressure history is reset at every checkpoint,
     on the forward run and on the replays alike, so a replay reproduces the
-    forward run's states bit for bit."""
+    forward run's states bit for bit.  The resets change the pressure solve's
+    initial guess, so a checkpointed run agrees with the same steps queued by
+    vct_step without resets to the solver tolerance only: a finite-difference
+    or oracle gradient must use the same reset schedule as the run it checks."""
 
     def __init__(self, solver, every=20):
         self.solver = solver
