@@ -1026,6 +1026,20 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         // pay (2-D wave, per step: 8 sweeps 15.72 iterations / 2372 us, 2 sweeps
         // 15.68 / 2310, none 15.63 / 2285)
         M.coarse_sweeps = 0;
+        // large-system form (also when a batch runs a small scenario in it):
+        // V(0,1) cycles through the row-cell operator by default.  Measured on
+        // the 2.1M-particle 3-D beach (krylov ms per step, iterations): V(1,1)
+        // 128.0 / 31.8, V(0,1) 114.1 / 47.3 (each iteration 1.9x cheaper); 64 2-D
+        // scenarios side by side: 29.4 vs 46.6 ms per step.
+        M.rowcell = prm->mg_cycle == 1 ? 0 : 1;
+        if (getenv("VCT_MG_ROWCELL")) M.rowcell = atoi(getenv("VCT_MG_ROWCELL")) != 0;
+        // the 3-D V(0,1) cycle's damping and scale (beach, krylov ms per step at
+        // omega / kappa: 0.7 / 1.2 82.9, 0.8 / 1.1 80.5, 0.9 / 1.1 81.7, 0.8 / 1.0
+        // 86.8, 0.8 / 0.9 106.5; the V(1,1) cycle diverges at omega 0.8)
+        if (prm->dim == 3 && M.rowcell && !M.fly) {
+            M.omega = 0.8f;
+            M.kappa = 1.1f;
+        }
         if (prm->mg_omega > 0.0) M.omega = (float)prm->mg_omega;
         if (prm->mg_kappa > 0.0) M.kappa = (float)prm->mg_kappa;
         if (getenv("VCT_MG_OMEGA")) M.omega = (float)atof(getenv("VCT_MG_OMEGA"));
@@ -1043,13 +1057,6 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         if (getenv("VCT_MG_SWEEPS")) M.coarse_sweeps = atoi(getenv("VCT_MG_SWEEPS"));
         M.presmooth = 1;
         if (getenv("VCT_MG_PRESMOOTH")) M.presmooth = atoi(getenv("VCT_MG_PRESMOOTH"));
-        // large-system form (also when a batch runs a small scenario in it):
-        // V(0,1) cycles through the row-cell operator by default.  Measured on
-        // the 2.1M-particle 3-D beach (krylov ms per step, iterations): V(1,1)
-        // 128.0 / 31.8, V(0,1) 114.1 / 47.3 (each iteration 1.9x cheaper); 64 2-D
-        // scenarios side by side: 29.4 vs 46.6 ms per step.
-        M.rowcell = prm->mg_cycle == 1 ? 0 : 1;
-        if (getenv("VCT_MG_ROWCELL")) M.rowcell = atoi(getenv("VCT_MG_ROWCELL")) != 0;
         long long pos = 0;
         for (int q = 1; q <= M.L; ++q) {
             M.offA[q] = pos;
