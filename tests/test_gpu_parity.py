@@ -331,14 +331,18 @@ def test_step_parity_regularised(vct, name, make, precision, tol, band):
 
 # The multigrid solver has two forms: V-cycle inputs formed on the fly (systems up
 # to 75k particles in 2-D, 30k in 3-D) and kept as vectors with cp.async-staged rows (larger ones).
-# VCT_MG_FORM forces the large-system form on the small cases.
+# VCT_MG_FORM forces the large-system form on the small cases; its cycle is V(0,1) through
+# the row-cell operator (mg_cycle 2, the default) or V(1,1) (mg_cycle 1).
+@pytest.mark.parametrize("cycle", [1, 2], ids=["V11", "V01-rowcell"])
 @pytest.mark.parametrize("precision,tol,band", [(0, 1e-12, 1e-9), (1, 1e-5, 1e-5)],
                          ids=["fp64", "mixed"])
 @pytest.mark.parametrize("name,make", [SMALL[1], SMALL[3], ("still_water_bf", S.still_water_bf)],
                          ids=[SMALL[1][0], SMALL[3][0], "still_water_bf"])
-def test_step_parity_explicit_form(vct, monkeypatch, name, make, precision, tol, band):
+def test_step_parity_explicit_form(vct, monkeypatch, name, make, precision, tol, band, cycle):
     monkeypatch.setenv("VCT_MG_FORM", "explicit")
-    _probe_compare(vct, make(), precision, tol, band, name + "-explicit")
+    sc = make()
+    sc.params["mg_cycle"] = cycle
+    _probe_compare(vct, sc, precision, tol, band, f"{name}-explicit-cycle{cycle}")
 
 
 def test_step_parity_sigma_solitary_explicit_form(vct, monkeypatch):
@@ -347,19 +351,24 @@ def test_step_parity_sigma_solitary_explicit_form(vct, monkeypatch):
 
 
 def test_forms_agree_over_steps(vct, monkeypatch):
-    """Both solver forms run the same iteration; after 20 mixed steps of the still-water tank
-    their states agree to the solver tolerance."""
+    """Both solver forms and both cycles of the large-system form solve the same system;
+    after 20 mixed steps of the still-water tank their states agree to the solver
+    tolerance, and the stats name the form and cycle that ran."""
     out = {}
-    for form in ("fly", "explicit"):
+    for form, cycle, want in (("fly", 0, (1, 0)), ("explicit", 1, (2, 1)), ("explicit", 2, (2, 2))):
         monkeypatch.setenv("VCT_MG_FORM", form)
         sc = S.still_water_bf(precision=1)
+        sc.params["mg_cycle"] = cycle
         s = vct.Solver(sc)
         st = vct.DeviceState(sc)
-        s.vct_step(st, 20)
-        out[form] = st.numpy()
+        stats = s.vct_step(st, 20)
+        assert (stats.solve_form, stats.mg_cycle) == want
+        out[(form, cycle)] = st.numpy()
     f = S.still_water_bf().type == S.FLUID
-    assert rel(out["fly"]["p"][f], out["explicit"]["p"][f]) < 1e-5
-    assert rel(out["fly"]["w"][f], out["explicit"]["w"][f]) < 1e-4
+    ref = out[("fly", 0)]
+    for key in (("explicit", 1), ("explicit", 2)):
+        assert rel(ref["p"][f], out[key]["p"][f]) < 1e-5, key
+        assert rel(ref["w"][f], out[key]["w"][f]) < 1e-4, key
 
 
 def test_multi_step_fp64_matches_oracle(vct):
