@@ -2497,6 +2497,43 @@ __global__ void k_mg_rowcell(Work W, MG M, int n, int mixed)
     mg_rowcell_body<D>(W, M, n, mixed, blockIdx.x);
 }
 
+// Level 1 from the row-cell operator: the cell's stencil entry o is the sum of
+// B[o][i] over its unknown rows, the Galerkin sum the warp-per-cell form
+// gathers from the coefficients (B's own-cell entry holds the diagonal).  One
+// thread per cell, the cell's rows in order.
+template <int D>
+__device__ __forceinline__ void mg_level1_rc_body(const Work &W, const MG &M, int bid_)
+{
+    if (step_failed(W.status)) return;
+    constexpr int S = D == 2 ? 9 : 27;
+    const int N = M.n[1];
+    const int I = bid_ * blockDim.x + threadIdx.x;
+    if (I >= N) return;
+    const int a = W.cell_start[I], b = W.cell_start[I + 1];
+    const int64_t cap = W.cap;
+    float acc[S];
+#pragma unroll
+    for (int o = 0; o < S; ++o) acc[o] = 0.f;
+    int rows = 0;
+    for (int i = a; i < b; ++i) {
+        if (W.pcnt[i] < 0) continue;
+        ++rows;
+#pragma unroll
+        for (int o = 0; o < S; ++o) acc[o] += W.mg_B[(int64_t)o * cap + i];
+    }
+    float *A = W.mg_pool + M.offA[1];
+#pragma unroll
+    for (int o = 0; o < S; ++o) A[(int64_t)o * N + I] = acc[o];
+    const float cc = acc[stencil_index<D>(0, 0, 0)];
+    W.mg_pool[M.offv[1] + I] = (rows > 0 && cc != 0.f) ? 1.f / cc : 0.f;   // dinv
+}
+
+template <int D>
+__global__ void k_mg_level1_rc(Work W, MG M)
+{
+    mg_level1_rc_body<D>(W, M, blockIdx.x);
+}
+
 // Node Ic of level l+1 from level l: sums of the children's stencils.
 template <int D>
 __device__ void coarsen_node(const Work &W, const MG &M, int l, int Ic)
@@ -2634,13 +2671,20 @@ void launch_mg_setup(const DevParams &P, Work W, const MG &M, int64_t n, cudaStr
     k_mg_dsc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, (int)n);
     const unsigned g1 = (unsigned)(((int64_t)M.n[1] * 32 + 255) / 256);   // a warp per cell
     const int mixed = P.precision == VCT_MIXED;
-    if (mg_rowcell_on(M)) {   // a row group per row
+    if (mg_rowcell_on(M)) {   // a row group per row, then level 1 from its cell sums
         const unsigned gr = (unsigned)((n * (P.dim == 2 ? 4 : 8) + 255) / 256);
-        if (P.dim == 2) k_mg_rowcell<2><<<gr, 256, 0, st>>>(W, M, (int)n, mixed);
-        else k_mg_rowcell<3><<<gr, 256, 0, st>>>(W, M, (int)n, mixed);
+        const unsigned gl = (unsigned)(((int64_t)M.n[1] + 255) / 256);
+        if (P.dim == 2) {
+            k_mg_rowcell<2><<<gr, 256, 0, st>>>(W, M, (int)n, mixed);
+            k_mg_level1_rc<2><<<gl, 256, 0, st>>>(W, M);
+        } else {
+            k_mg_rowcell<3><<<gr, 256, 0, st>>>(W, M, (int)n, mixed);
+            k_mg_level1_rc<3><<<gl, 256, 0, st>>>(W, M);
+        }
+    } else {
+        if (P.dim == 2) k_mg_level1<2><<<g1, 256, 0, st>>>(W, M, mixed);
+        else k_mg_level1<3><<<g1, 256, 0, st>>>(W, M, mixed);
     }
-    if (P.dim == 2) k_mg_level1<2><<<g1, 256, 0, st>>>(W, M, mixed);
-    else k_mg_level1<3><<<g1, 256, 0, st>>>(W, M, mixed);
     int l = 1;
     for (; l < M.L && M.n[l + 1] > small_level(); ++l) {
         const unsigned g = (unsigned)((M.n[l + 1] + 127) / 128);
@@ -6103,7 +6147,8 @@ struct BMgLevel1 {
     static constexpr int NT = 256, MINB = 1, BYTES = SJ_ALL;
     __device__ void operator()(const StageJob &j, int b) const
     {
-        mg_level1_body<D>(j.W, j.M, j.P.precision == VCT_MIXED, b);
+        if (j.M.rowcell && !j.M.fly) mg_level1_rc_body<D>(j.W, j.M, b);
+        else mg_level1_body<D>(j.W, j.M, j.P.precision == VCT_MIXED, b);
     }
 };
 template <int D, typename R>
@@ -6185,7 +6230,9 @@ int batch_stage_blocks(int s, const DevParams &P, const Work &W, const MG &M, in
         return rows_list ? (snb == 0 ? 1 : (int)snb) : 0;
     case BS_RSCAN_TOPS: return rows_list ? 1 : 0;
     case BS_MG_ROWCELL: return mg_rowcell_on(M) ? (int)((n * (P.dim == 2 ? 4 : 8) + 255) / 256) : 0;
-    case BS_MG_LEVEL1: return (int)(((int64_t)M.n[1] * 32 + 255) / 256);
+    case BS_MG_LEVEL1:
+        return mg_rowcell_on(M) ? (int)(((int64_t)M.n[1] + 255) / 256)
+                                : (int)(((int64_t)M.n[1] * 32 + 255) / 256);
     case BS_MG_COARSEN: return level >= 1 && level < lend ? (M.n[level + 1] + 127) / 128 : 0;
     case BS_MG_COARSEN_SMALL: return lend < M.L ? 1 : 0;
     case BS_CORRECTOR: return P.operators == 1 ? 0 : b128;
