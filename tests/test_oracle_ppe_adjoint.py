@@ -1,5 +1,5 @@
 """Pins of the oracle's pressure-equation assembly and transpose solve (the
-adjoint of the pressure solve, survey row a12).
+adjoint of the pressure solve).
 
   * the dense matrix assembled column by column from the oracle's operator
     reproduces the oracle's own solve: A p = b on the unknown rows (a matrix
