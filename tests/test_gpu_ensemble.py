@@ -218,3 +218,32 @@ def test_batch_with_different_options_per_scenario():
         f = sc.type == S.FLUID
         for k in ("p", "u", "w"):
             assert rel(g[k][f], r[k][f]) < 1e-4, k
+
+
+def test_batch_isolates_a_failing_scenario():
+    """A scenario whose step fails inside a batch (a singular SPH(2) moment matrix
+    off the free surface) stops at its own status word: the call reports
+    VCT_ERR_SINGULAR, that scenario's state is left as it was, and the other
+    scenarios, whose stages shared every launch with it, are stepped and agree
+    with their own steps to the solver tolerance."""
+    from paper_2607_28872_b300 import vct as V
+    from test_gpu_failures import _cross
+    bad = _cross()
+    bad.params["precision"] = 1
+    good = _scenarios()[:2]
+    ref = _individual(V, good, 2)
+    scs = [good[0], bad, good[1]]
+    solvers = [V.Solver(sc) for sc in scs]
+    states = [V.DeviceState(sc) for sc in scs]
+    before = states[1].numpy()
+    with pytest.raises(V.VCTError) as e:
+        V.vct_batch_step(solvers, states, 2)
+    assert e.value.status == V.VCT_ERR_SINGULAR
+    after = states[1].numpy()
+    for k in ("x", "z", "u", "w", "p"):
+        assert np.array_equal(before[k], after[k]), k
+    for sc, st, r in zip(good, (states[0], states[2]), ref):
+        g = st.numpy()
+        f = sc.type == S.FLUID
+        for k in ("p", "u", "w"):
+            assert rel(g[k][f], r[k][f]) < 1e-4, k
