@@ -448,9 +448,10 @@ vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct
  * each on a share of the grid in proportion to its particles, all on a
  * stream the FIRST context keeps for it (each scenario's load and store run
  * on a stream of its own, created on first use and kept by its context).
- * Every stage but the solve computes exactly what the scenario's own
- * launches compute; results agree with vct_step to the solver tolerance (the
- * solves' partial sums are grouped differently), and repeat bit for bit.
+ * Every stage runs the same device code as the scenario's own launch of it
+ * (compiled into another kernel, so multiply-add fusion may differ in the last
+ * bit); results agree with vct_step to the solver tolerance (the solves'
+ * partial sums are grouped differently), and repeat bit for bit.
  * The batch's launches are counted in the first scenario's
  * stats.kernel_launches (the others count their load and store).  In this
  * form, steps run in pairs from a CUDA graph: the first call for a batch

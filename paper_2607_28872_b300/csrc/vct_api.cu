@@ -433,10 +433,11 @@ int batch_group(int s)
 // when it exceeds the small-system size in total, or any scenario is a large
 // system, every scenario's solve runs in the large-system form (vectors,
 // staged rows, L1 gathers, 16 KB of shared levels; VCT_BATCH_FORM=fly|explicit
-// overrides where it can).  Every stage but the solve computes exactly what the
-// scenario's own launches compute; the solves' partial sums are grouped by the
-// scenario's share of blocks, so results agree with vct_step to the solver
-// tolerance, not bit for bit.
+// overrides where it can).  Every stage runs the same device code as the
+// scenario's own launch of it (compiled into a different kernel, so multiply-add
+// fusion may differ: agreement to rounding); the solves' partial sums are
+// grouped by the scenario's share of blocks, so results agree with vct_step to
+// the solver tolerance, not bit for bit.
 vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int n_scen, int nsteps,
                             vct_stats *out)
 {

@@ -5976,7 +5976,9 @@ void launch_rhopos(const DevParams &P, Part cur, Work W, int64_t n, const double
 // Block b of a launch belongs to the scenario k with bs[k] <= b < bs[k + 1];
 // it copies the part of that scenario's StageJob its stage reads into shared
 // memory and runs the stage's body as block b - bs[k] of the scenario's own
-// launch, so every scenario computes exactly what its own launches compute.
+// launch: every scenario runs the same device code as its own launch of the
+// stage (the two kernels are compiled separately, so the compiler may fuse a
+// multiply and an add differently: results agree to rounding).
 // ---------------------------------------------------------------------------
 // Blocks of 128 per SM the light batched stages (smoothing, wall velocities,
 // right side, corrector, regularisation) are compiled for: their parameters come
@@ -5987,6 +5989,15 @@ void launch_rhopos(const DevParams &P, Part cur, Work W, int64_t n, const double
 #define VCT_BATCH_LIGHT_MINB 8
 #endif
 constexpr int BATCH_LIGHT_MINB = VCT_BATCH_LIGHT_MINB;
+// ... and the 2-D passes (pass 2 at 4 blocks: 3.67 -> 3.30 ms per ensemble step;
+// pass 1 at 2 blocks: no change)
+#ifndef VCT_BATCH_PASS1_MINB2
+#define VCT_BATCH_PASS1_MINB2 1
+#endif
+#ifndef VCT_BATCH_PASS2_MINB2
+#define VCT_BATCH_PASS2_MINB2 4
+#endif
+constexpr int BATCH_PASS1_MINB2 = VCT_BATCH_PASS1_MINB2, BATCH_PASS2_MINB2 = VCT_BATCH_PASS2_MINB2;
 static_assert(offsetof(StageJob, P) % 16 == 0 && offsetof(StageJob, alt) % 16 == 0 &&
                   offsetof(StageJob, M) % 16 == 0 && sizeof(StageJob) % 16 == 0,
               "StageJob prefixes are copied in 16-byte words");
@@ -6113,12 +6124,12 @@ struct BWallVelocity {
 };
 template <int D, typename R>
 struct BPass1 {
-    static constexpr int NT = 128, MINB = pass1_min_blocks<D>(), BYTES = SJ_CWP;
+    static constexpr int NT = 128, MINB = D == 2 ? BATCH_PASS1_MINB2 : pass1_min_blocks<D>(), BYTES = SJ_CWP;
     __device__ void operator()(const StageJob &j, int b) const { pass1_body<D, R>(j.P, j.cur, j.W, (int)j.n, b); }
 };
 template <int D, typename R>
 struct BPass2 {
-    static constexpr int NT = 128, MINB = pass2_min_blocks<D>(), BYTES = SJ_CWP;
+    static constexpr int NT = 128, MINB = D == 2 ? BATCH_PASS2_MINB2 : pass2_min_blocks<D>(), BYTES = SJ_CWP;
     __device__ void operator()(const StageJob &j, int b) const { pass2_body<D, R>(j.P, j.cur, j.W, (int)j.n, 1, b); }
 };
 template <int D, typename R>

@@ -167,10 +167,10 @@ def test_batch_graph_replay_equals_direct_launches(monkeypatch, form):
 
 
 def test_batched_stages_exact_before_the_solve():
-    """Every stage of a side-by-side step before the pressure solve is one
-    launch over all scenarios that computes exactly what the scenario's own
-    launches compute: after one step the smoothed volumes Jbar (set before the
-    solve, Eq. VCT_bar_a) are bit-identical to the individual steps'."""
+    """Every stage of a side-by-side step is one launch over all scenarios that
+    runs the scenario's own stage code: after one step the smoothed volumes Jbar
+    (set before the solve from the map, the sort and the neighbour lists, Eq.
+    VCT_bar_a) are bit-identical to the individual steps'."""
     from paper_2607_28872_b300 import vct as V
     scs = _scenarios()
     ref = _individual(V, scs, 1)
