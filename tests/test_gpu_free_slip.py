@@ -8,7 +8,7 @@
     particles, dt = 1e-4 s) for 150 steps: the water column starts to
     collapse into the dry part of the basin, the state stays bounded and the
     total volume (sum of V0 / Jbar, Condition C) stays within 1 %.  (Near
-    step 185 a free-surface particle at the upper corner of the column and the
+    step 190 a free-surface particle at the upper corner of the column and the
     left wall is ejected and the run breaks down; the horizon is stated.)
 """
 import numpy as np
