@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <optional>
 #include <vector>
 
 #include "vct_internal.cuh"
@@ -628,12 +629,12 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
     // its stage times are the batch's.
     auto one_step = [&](int step) -> cudaError_t {
         const StageJob *X = T[step & 1], *Y = T[(step + 1) & 1];
-        StageTimer *t = nullptr;
+        std::optional<StageTimer> t;   // brackets a run of launches of one profiling stage
         int grp = -1;
         auto run = [&](const BatchLaunch &L) {
             if (prof && L.group != grp) {
-                delete t;
-                t = new StageTimer(c0, L.group, main);
+                t.reset();
+                t.emplace(c0, L.group, main);
                 grp = L.group;
             }
             launch_batched(L.stage, dim, prec, L.post_sort ? Y : X, tb + L.bs_off, n_scen, L.total,
@@ -641,8 +642,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
             c0->launches += 1;
         };
         for (size_t q = 0; q < n_pre; ++q) run(plan[q]);
-        delete t;
-        t = nullptr;
+        t.reset();
         grp = -1;
         int le;
         {
@@ -651,7 +651,7 @@ vct_status batch_concurrent(vct_ctx *const *ctxs, vct_state *const *states, int 
         }
         c0->launches += 1;
         for (size_t q = n_pre; q < plan.size(); ++q) run(plan[q]);
-        delete t;
+        t.reset();
         for (int k = 0; k < n_scen; ++k) {
             ctxs[k]->cur_is_A = !ctxs[k]->cur_is_A;
             ctxs[k]->ppe_n = states[k]->n;
