@@ -395,6 +395,23 @@ vct_status vct_map_backward(vct_ctx *ctx, const vct_state *state, const double *
                             const double *J_bar, const double *sx_bar, const double *sy_bar,
                             const double *c0_bar, const double *c3_bar, double *theta_bar);
 
+/* Derivative through the map with respect to the particles' physical positions
+ * (the metric under moving particles): given the same per-particle adjoints as
+ * vct_map_backward (DEVICE arrays of n, caller order, any may be NULL for
+ * zero) of z^, J, s_x, s_y, c0 and c3, writes pos_bar (DEVICE, dim x n,
+ * component-major: x, z in 2-D; x, y, z in 3-D) with
+ * pos_bar[k*n + i] = sum_q mbar_q,i dm_q,i / dx_k,i -- each particle's metric
+ * depends on its own position only (Sec. 2: alpha, beta and their derivatives
+ * at (x, y); z^ = alpha (z + beta)).  The identity parts x^ = x, y^ = y of the
+ * projected position are not included.  Exact derivatives (forward-mode dual
+ * arithmetic, one coordinate per pass; third derivatives of the bathymetry
+ * enter through c0); where the sigma clamp holds alpha its derivatives are 0.
+ * FP64, deterministic. */
+vct_status vct_map_backward_positions(vct_ctx *ctx, const vct_state *state, const double *zh_bar,
+                                      const double *J_bar, const double *sx_bar,
+                                      const double *sy_bar, const double *c0_bar,
+                                      const double *c3_bar, double *pos_bar);
+
 /* Advance the state by nsteps steps of Sec. 3.3 with the VCT equations:
  * map + cell sort, neighbours, Jbar smoothing (sigma, volume_mode 2),
  * corrected gradients, free surface, eddy viscosity, SPH(2) predictor,

@@ -1287,6 +1287,23 @@ VCT_API vct_status vct_map_backward(vct_ctx *c, const vct_state *s, const double
     return VCT_OK;
 }
 
+VCT_API vct_status vct_map_backward_positions(vct_ctx *c, const vct_state *s, const double *zh_bar,
+                                              const double *J_bar, const double *sx_bar,
+                                              const double *sy_bar, const double *c0_bar,
+                                              const double *c3_bar, double *pos_bar)
+{
+    if (!c || !s || !pos_bar) return VCT_ERR_ARG;
+    if (s->n <= 0 || s->n > c->cap) return s->n > c->cap ? VCT_ERR_CAPACITY : VCT_ERR_ARG;
+    if (!s->x || !s->z || (c->P.dim == 3 && !s->y)) return VCT_ERR_ARG;
+    const double *tab[6] = {zh_bar, J_bar, sx_bar, sy_bar, c0_bar, c3_bar};
+    cudaError_t e = cudaMemcpyAsync(c->W.scal, tab, sizeof tab, cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
+    launch_map_pos_adjoint(c->P, *s, s->n, (const double *const *)c->W.scal, pos_bar, c->st);
+    e = cudaStreamSynchronize(c->st);   // tab is a host temporary
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    return VCT_OK;
+}
+
 VCT_API vct_status vct_step(vct_ctx *c, vct_state *s, int32_t nsteps, vct_stats *out)
 {
     return run_steps(c, s, nsteps, nullptr, out);

@@ -252,6 +252,9 @@ void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t 
                        int32_t *col, int64_t col_cap, cudaStream_t st);
 int launch_map_adjoint(const DevParams &P, vct_state s, int64_t n, const double *const *mbar_dev,
                        double *partial, int64_t partial_cap, double *out, cudaStream_t st);
+// derivative of the per-particle metric with respect to the physical positions
+void launch_map_pos_adjoint(const DevParams &P, vct_state s, int64_t n, const double *const *mbar_dev,
+                            double *pos_bar, cudaStream_t st);
 void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
                          const double *gbar, const double *d2bar, const double *lapbar,
                          double *phibar, cudaStream_t st);

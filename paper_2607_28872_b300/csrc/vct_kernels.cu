@@ -4740,9 +4740,8 @@ __device__ __forceinline__ Dual theta(const DevParams &P, int k, int seed)
     return Dual(v, k == seed ? 1.0 : 0.0);
 }
 
-__device__ void bathy_dual(const DevParams &P, double x, double y, int seed, Dual h[5])
+__device__ void bathy_dual(const DevParams &P, Dual X, Dual Y, int seed, Dual h[5])
 {
-    Dual X(x), Y(y);
     Dual sx = theta(P, 1, seed), sy = theta(P, 2, seed);
     h[0] = theta(P, 0, seed) + sx * X + sy * Y;
     h[1] = sx;
@@ -4771,14 +4770,15 @@ __device__ void bathy_dual(const DevParams &P, double x, double y, int seed, Dua
 }
 
 // Same metric as map_metric, in dual arithmetic: out = {z^, J, s_x, s_y, c0, c3}.
-__device__ void metric_dual(const DevParams &P, double x, double y, double z, int seed, Dual out[6])
+// The position (X, Y, Z) and the parameter `seed` of theta may carry derivatives.
+__device__ void metric_dual(const DevParams &P, Dual X, Dual Y, Dual Z, int seed, Dual out[6])
 {
     Dual a(1.0), ax, ay, axx, ayy, b, bx, by, bxx, byy;
     if (P.kind == VCT_MAP_E) {
         a = Dual(P.aspect);
     } else {
         Dual h[5];
-        bathy_dual(P, x, y, seed, h);
+        bathy_dual(P, X, Y, seed, h);
         b = -h[0]; bx = -h[1]; by = -h[2]; bxx = -h[3]; byy = -h[4];
         if (P.kind == VCT_MAP_BFE) {
             a = Dual(P.aspect);
@@ -4804,7 +4804,7 @@ __device__ void metric_dual(const DevParams &P, double x, double y, double z, in
     if (P.dim == 2) {  // a 2-D section has no y direction
         ay = Dual(0.0); ayy = Dual(0.0); by = Dual(0.0); byy = Dual(0.0);
     }
-    Dual zeta = Dual(z) + b;
+    Dual zeta = Z + b;
     Dual sx = ax * zeta + a * bx, sy = ay * zeta + a * by;
     out[0] = a * zeta;
     out[1] = a;
@@ -4835,7 +4835,7 @@ __global__ void __launch_bounds__(MAPT) k_map_adjoint(DevParams P, vct_state s, 
         double c = 0.0;
         if (act) {
             Dual out[6];
-            metric_dual(P, x, y, z, k, out);
+            metric_dual(P, Dual(x), Dual(y), Dual(z), k, out);
             for (int q = 0; q < 6; ++q) c += bar[q] * out[q].d;
         }
 #pragma unroll
@@ -4869,6 +4869,37 @@ int launch_map_adjoint(const DevParams &P, vct_state s, int64_t n, const double 
     k_map_adjoint<<<nblk, MAPT, 0, st>>>(P, s, (int)n, nparam, mbar_dev, partial);
     k_map_adjoint_sum<<<(nparam + 127) / 128, 128, 0, st>>>(partial, nblk, nparam, out);
     return 0;
+}
+
+// Derivative of the per-particle metric with respect to the particle's own
+// physical position (the map's metric under moving particles): for each
+// coordinate seeded in turn, pos_bar[k * n + i] = sum_q mbar_q,i dm_q,i / dx_k
+// (k over x, z in 2-D; x, y, z in 3-D).  The projected position's x^ = x and
+// y^ = y parts are the identity and are not included.
+__global__ void __launch_bounds__(MAPT) k_map_pos_adjoint(DevParams P, vct_state s, int n,
+                                                          const double *const *mbar, double *pos_bar)
+{
+    const int i = blockIdx.x * MAPT + threadIdx.x;
+    if (i >= n) return;
+    const double x = s.x[i], y = P.dim == 3 && s.y ? s.y[i] : 0.0, z = s.z[i];
+    double bar[6];
+    for (int q = 0; q < 6; ++q) bar[q] = mbar[q] ? mbar[q][i] : 0.0;
+    const int naxes = P.dim == 3 ? 3 : 2;
+    for (int k = 0; k < naxes; ++k) {
+        const int axis = P.dim == 3 ? k : (k == 0 ? 0 : 2);   // 2-D: x and z
+        Dual out[6];
+        metric_dual(P, Dual(x, axis == 0 ? 1.0 : 0.0), Dual(y, axis == 1 ? 1.0 : 0.0),
+                    Dual(z, axis == 2 ? 1.0 : 0.0), -1, out);
+        double c = 0.0;
+        for (int q = 0; q < 6; ++q) c += bar[q] * out[q].d;
+        pos_bar[(int64_t)k * n + i] = c;
+    }
+}
+
+void launch_map_pos_adjoint(const DevParams &P, vct_state s, int64_t n, const double *const *mbar_dev,
+                            double *pos_bar, cudaStream_t st)
+{
+    k_map_pos_adjoint<<<(unsigned)((n + MAPT - 1) / MAPT), MAPT, 0, st>>>(P, s, (int)n, mbar_dev, pos_bar);
 }
 
 void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,

@@ -23,7 +23,7 @@ EXPORTS = ("vct_init", "vct_set_stream", "vct_reset_history", "vct_build_neighbo
            "vct_build_neighbours_noalloc",
            "sph2_derivatives", "sph2_derivatives_backward", "sph2_gradient_backward_positions",
            "sph2_d2_backward_positions", "vct_ppe_backward_positions", "vct_rho_backward_positions",
-           "vct_map_backward", "vct_step",
+           "vct_map_backward", "vct_map_backward_positions", "vct_step",
            "vct_batch_step",
            "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
@@ -102,6 +102,7 @@ def load_library(path=LIB_PATH):
     L.sph2_derivatives_backward.argtypes = [vp, C.POINTER(vct_state), C.c_int32, vp, vp, vp, vp]
     L.vct_map_backward.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp, vp, vp, vp,
                                    C.POINTER(C.c_double)]
+    L.vct_map_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp, vp, vp, vp, vp]
     L.vct_step.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_host.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_batch_step.argtypes = [C.POINTER(vp), C.POINTER(C.POINTER(vct_state)), C.c_int32,
@@ -125,7 +126,7 @@ def load_library(path=LIB_PATH):
                  "sph2_derivatives",
                  "sph2_derivatives_backward", "sph2_gradient_backward_positions",
                  "sph2_d2_backward_positions", "vct_ppe_backward_positions",
-                 "vct_rho_backward_positions", "vct_map_backward",
+                 "vct_rho_backward_positions", "vct_map_backward", "vct_map_backward_positions",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
@@ -324,6 +325,21 @@ class Solver:
                                               c(sy_bar), c(c0_bar), c(c3_bar), out),
                     "vct_map_backward")
         return np.array(out[:])
+
+    def vct_map_backward_positions(self, state, zh_bar=None, J_bar=None, sx_bar=None, sy_bar=None,
+                                   c0_bar=None, c3_bar=None):
+        """(dim, n) float64 CUDA tensor: adjoint of the per-particle metric
+        (z^, J, s_x, s_y, c0, c3) pulled back to the physical positions (x, z in
+        2-D; x, y, z in 3-D), the identity parts of x^, y^ excluded."""
+        import torch
+        out = torch.zeros((self.dim, state.n), dtype=torch.float64, device="cuda")
+        s = state.struct()
+        c = lambda t: None if t is None else _ptr(t.contiguous())
+        self._check(self.lib.vct_map_backward_positions(self.ctx, C.byref(s), c(zh_bar), c(J_bar),
+                                                        c(sx_bar), c(sy_bar), c(c0_bar), c(c3_bar),
+                                                        C.c_void_p(out.data_ptr())),
+                    "vct_map_backward_positions")
+        return out
 
     def sph2_gradient_backward_positions(self, state, phi, grad_bar):
         """Gradient of sum grad_bar . grad_hat (sph2_derivatives' corrected

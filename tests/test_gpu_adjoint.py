@@ -145,3 +145,43 @@ def test_map_backward_matches_oracle_differences(kind, dim):
         tm[k] -= h
         fd = (objective(tp) - objective(tm)) / (2 * h)
         assert abs(fd - got[k]) <= 1e-5 * (abs(fd) + abs(got[k]) + 1e-3), (k, fd, got[k])
+
+
+@pytest.mark.parametrize("kind,dim", [("SIGMA", 2), ("BF", 2), ("BFE", 3), ("SIGMA", 3)])
+def test_map_backward_positions_matches_oracle_differences(kind, dim):
+    """The metric under moving particles: pos_bar from the GPU against central
+    differences of the oracle's per-particle metric (z^, J, s_x, s_y, c0, c3) in
+    each physical coordinate of every particle, with the sigma clamp active on
+    part of the tank (alpha_max 4 over the deepest bump)."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    bathy = S.Bathymetry(h0=0.01, slope_x=0.03, slope_y=-0.02, cos_amp=0.004, cos_len=0.17,
+                         amp=[0.02, -0.015], cx=[0.05, 0.09], cy=[0.02, 0.03], width=[0.03, 0.04])
+    sc = S.small_tank(dim=dim, kind=kind, L=0.12, W=0.05, H=0.06, d0=0.01, seed=6, bathy=bathy,
+                      aspect=2.0, alpha_min=0.5, alpha_max=4.0)
+    rng = np.random.default_rng(8)
+    n = sc.n
+    bars = [rng.normal(size=n) for _ in range(6)]
+    s = V.Solver(sc)
+    got = s.vct_map_backward_positions(V.DeviceState(sc),
+                                       *[torch.tensor(b, device="cuda") for b in bars]).cpu().numpy()
+    y0 = sc.y if sc.y is not None else np.zeros(n)
+
+    def objective(x, y, z):
+        zh, met = O.map_metric(sc, x, y, z)
+        q = [zh, met[:, 0], met[:, 1], met[:, 2], met[:, 3], met[:, 4]]
+        return np.array([sum(bars[k][i] * q[k][i] for k in range(6)) for i in range(n)])
+
+    coords = [sc.x, y0, sc.z]
+    axes = (0, 2) if dim == 2 else (0, 1, 2)
+    for k, a in enumerate(axes):
+        h = 1e-6
+        cp = [c.copy() for c in coords]
+        cm = [c.copy() for c in coords]
+        cp[a] = cp[a] + h
+        cm[a] = cm[a] - h
+        fd = (objective(*cp) - objective(*cm)) / (2 * h)
+        scale = np.abs(fd).max() + 1e-3
+        err = np.abs(fd - got[k]).max() / scale
+        print(f"PARITY map positions {kind} {dim}-D axis {a}: err {err:.2e}")
+        assert err < 1e-6, (a, err)
