@@ -412,6 +412,21 @@ vct_status vct_map_backward_positions(vct_ctx *ctx, const vct_state *state, cons
                                       const double *sy_bar, const double *c0_bar,
                                       const double *c3_bar, double *pos_bar);
 
+/* Water level at wave gauges and the squared-level loss of the adjoint workload
+ * (the paper's experiments record water levels at fixed gauges, Sec. 4.4.2).
+ * At gauge g, eta_g = sum_i w_ig z_i / sum_i w_ig - H over the free-surface
+ * fluid particles (fs[i] == 1; fs DEVICE int32, caller order, e.g. the flags
+ * vct_step_probe exports; they are held fixed), w_ig = the cubic spline shape
+ * of the horizontal distance to the gauge over l (support 2 l); eta_g = 0 if no
+ * surface particle lies within 2 l.  gauges (HOST): n_gauges x positions in
+ * 2-D, n_gauges (x, y) pairs in 3-D; 1 <= n_gauges <= 16.  Writes loss (HOST)
+ * = sum_g eta_g^2, eta (HOST, n_gauges, may be NULL) and pos_bar (DEVICE,
+ * dim x n component-major: x, z in 2-D; x, y, z in 3-D; may be NULL) = the
+ * loss's gradient with respect to the physical positions.  FP64; sums in a
+ * fixed order.  VCT_ERR_ARG for a bad count or non-finite gauge position. */
+vct_status vct_gauge_loss(vct_ctx *ctx, const vct_state *state, const int32_t *fs, int32_t n_gauges,
+                          const double *gauges, double *loss, double *eta, double *pos_bar);
+
 /* Advance the state by nsteps steps of Sec. 3.3 with the VCT equations:
  * map + cell sort, neighbours, Jbar smoothing (sigma, volume_mode 2),
  * corrected gradients, free surface, eddy viscosity, SPH(2) predictor,

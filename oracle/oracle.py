@@ -358,3 +358,43 @@ def ppe_adjoint(A, p_bar):
     """b_bar = A^-T p_bar: the adjoint of p = A^-1 b with respect to b (the
     transpose solve; numpy's dense LU)."""
     return np.linalg.solve(A.T, p_bar)
+
+
+def _spline(q):
+    """The cubic spline's shape (unnormalised): 1 - 1.5 q^2 + 0.75 q^3 below 1,
+    0.25 (2 - q)^3 below 2, 0 beyond."""
+    q = np.asarray(q, dtype=np.float64)
+    return np.where(q < 1.0, 1.0 - 1.5 * q * q + 0.75 * q ** 3,
+                    np.where(q < 2.0, 0.25 * (2.0 - q) ** 3, 0.0))
+
+
+def gauge_levels(sc, fs, gauges, x=None, y=None, z=None):
+    """Water level at wave gauges (the paper's experiments record water levels
+    at fixed gauges, Sec. 4.4.2): at gauge g, the free-surface particles'
+    heights (fs == 1, fluid) averaged with weights w = spline(|r_h| / l) of their
+    horizontal distance r_h to the gauge (support 2 l), minus the still-water
+    level H.  A gauge with no surface particle within 2 l reads 0.  gauges:
+    (G,) x positions in 2-D, (G, 2) x, y positions in 3-D."""
+    x = sc.x if x is None else np.asarray(x, dtype=np.float64)
+    z = sc.z if z is None else np.asarray(z, dtype=np.float64)
+    l, _, _ = radii(sc)
+    surf = (np.asarray(fs) == 1) & (sc.type == 0)
+    g = np.asarray(gauges, dtype=np.float64).reshape(len(gauges), -1)
+    eta = np.zeros(len(g))
+    for k in range(len(g)):
+        dx = x - g[k, 0]
+        r2 = dx * dx
+        if sc.dim == 3:
+            yy = sc.y if y is None else np.asarray(y, dtype=np.float64)
+            dy = yy - g[k, 1]
+            r2 = r2 + dy * dy
+        w = np.where(surf, _spline(np.sqrt(r2) / l), 0.0)
+        den = w.sum()
+        eta[k] = (w * z).sum() / den - sc.params["H"] if den > 0 else 0.0
+    return eta
+
+
+def gauge_loss(sc, fs, gauges, x=None, y=None, z=None):
+    """Squared water levels summed over the gauges, sum_g eta_g^2."""
+    eta = gauge_levels(sc, fs, gauges, x, y, z)
+    return float((eta * eta).sum())

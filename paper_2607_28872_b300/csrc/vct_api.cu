@@ -1304,6 +1304,38 @@ VCT_API vct_status vct_map_backward_positions(vct_ctx *c, const vct_state *s, co
     return VCT_OK;
 }
 
+VCT_API vct_status vct_gauge_loss(vct_ctx *c, const vct_state *s, const int32_t *fs, int32_t n_gauges,
+                                  const double *gauges, double *loss, double *eta, double *pos_bar)
+{
+    if (!c || !s || !fs || !gauges || !loss) return VCT_ERR_ARG;
+    if (s->n <= 0 || s->n > c->cap) return s->n > c->cap ? VCT_ERR_CAPACITY : VCT_ERR_ARG;
+    if (!s->x || !s->z || !s->type || (c->P.dim == 3 && !s->y)) return VCT_ERR_ARG;
+    if (n_gauges < 1 || n_gauges > 16) return VCT_ERR_ARG;
+    // gauge positions (x, y; y = 0 in 2-D) and the results in the context's small scratch
+    double gxy[32];
+    for (int g = 0; g < n_gauges; ++g) {
+        gxy[2 * g] = gauges[(c->P.dim == 3 ? 2 : 1) * g];
+        gxy[2 * g + 1] = c->P.dim == 3 ? gauges[2 * g + 1] : 0.0;
+        if (!(gxy[2 * g] > -1.0e300 && gxy[2 * g] < 1.0e300) ||
+            !(gxy[2 * g + 1] > -1.0e300 && gxy[2 * g + 1] < 1.0e300))
+            return VCT_ERR_ARG;
+    }
+    double *gdev = c->theta_out, *res = c->theta_out + 32;
+    cudaError_t e = cudaMemcpyAsync(gdev, gxy, sizeof(double) * 2 * n_gauges, cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return VCT_ERR_CUDA;
+    const int rc = launch_gauge_loss(c->P, *s, s->n, fs, n_gauges, gdev, c->W.adj,
+                                     c->cap * (c->P.dim == 2 ? 5 : 9), res, pos_bar, c->st);
+    if (rc) return VCT_ERR_CAPACITY;
+    double out[3 * 16 + 1];
+    e = cudaMemcpyAsync(out, res, sizeof(double) * (3 * n_gauges + 1), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    *loss = out[3 * n_gauges];
+    if (eta)
+        for (int g = 0; g < n_gauges; ++g) eta[g] = out[2 * n_gauges + g];
+    return VCT_OK;
+}
+
 VCT_API vct_status vct_step(vct_ctx *c, vct_state *s, int32_t nsteps, vct_stats *out)
 {
     return run_steps(c, s, nsteps, nullptr, out);

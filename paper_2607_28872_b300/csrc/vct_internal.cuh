@@ -252,6 +252,11 @@ void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t 
                        int32_t *col, int64_t col_cap, cudaStream_t st);
 int launch_map_adjoint(const DevParams &P, vct_state s, int64_t n, const double *const *mbar_dev,
                        double *partial, int64_t partial_cap, double *out, cudaStream_t st);
+// water level at gauges, its squared sum and gradient (returns 1: bad gauge
+// count, 2: scratch too small); res: 3 ng + 1 doubles on the device
+int launch_gauge_loss(const DevParams &P, vct_state s, int64_t n, const int32_t *fs, int ng,
+                      const double *gxy, double *partial, int64_t partial_cap, double *res,
+                      double *pos_bar, cudaStream_t st);
 // derivative of the per-particle metric with respect to the physical positions
 void launch_map_pos_adjoint(const DevParams &P, vct_state s, int64_t n, const double *const *mbar_dev,
                             double *pos_bar, cudaStream_t st);

@@ -4902,6 +4902,130 @@ void launch_map_pos_adjoint(const DevParams &P, vct_state s, int64_t n, const do
     k_map_pos_adjoint<<<(unsigned)((n + MAPT - 1) / MAPT), MAPT, 0, st>>>(P, s, (int)n, mbar_dev, pos_bar);
 }
 
+// ---------------------------------------------------------------------------
+// a12 (loss): water level at wave gauges (the paper's experiments record water
+// levels at fixed gauges, Sec. 4.4.2).  At gauge g the free-surface fluid
+// particles' heights are averaged with the weights w = spline(|r_h| / l) of
+// their horizontal distance to the gauge (support 2 l); eta_g = that average
+// minus the still-water level H (0 without a surface particle within 2 l), and
+// the loss is sum_g eta_g^2.  Its gradient with respect to each surface
+// particle's position: z_bar = sum_g 2 eta_g w / S_g, and along the horizontal
+// axes 2 eta_g (z - level_g) (dw/dx) / S_g, S_g = sum w.  Caller order; the
+// free-surface flags are the caller's (frozen).
+// ---------------------------------------------------------------------------
+constexpr int GAUGE_MAX = 16;
+
+__device__ __forceinline__ void gauge_w(double r, double inv_l, double &w, double &dwdr)
+{
+    const double q = r * inv_l;
+    if (q < 1.0) {
+        w = 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+        dwdr = (-3.0 * q + 2.25 * q * q) * inv_l;
+    } else if (q < 2.0) {
+        const double t = 2.0 - q;
+        w = 0.25 * t * t * t;
+        dwdr = -0.75 * t * t * inv_l;
+    } else {
+        w = 0.0;
+        dwdr = 0.0;
+    }
+}
+
+// partial[(2 g + 0/1) * nblk + block] = the block's sum of w z / w for gauge g
+__global__ void __launch_bounds__(MAPT) k_gauge_partials(DevParams P, vct_state s, int n,
+                                                          const int32_t *fs, int ng,
+                                                          const double *gxy, double *partial)
+{
+    __shared__ double red[MAPT / 32];
+    const int i = blockIdx.x * MAPT + threadIdx.x;
+    const bool act = i < n && fs[i] == 1 && s.type[i] == FLUID;
+    const double x = act ? s.x[i] : 0.0, z = act ? s.z[i] : 0.0;
+    const double y = act && P.dim == 3 ? s.y[i] : 0.0;
+    for (int q = 0; q < 2 * ng; ++q) {
+        const int g = q >> 1;
+        double c = 0.0;
+        if (act) {
+            const double dx = x - gxy[2 * g], dy = P.dim == 3 ? y - gxy[2 * g + 1] : 0.0;
+            double w, dwdr;
+            gauge_w(sqrt(dx * dx + dy * dy), P.inv_l, w, dwdr);
+            c = (q & 1) ? w : w * z;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < MAPT / 32; ++w) t += red[w];
+            partial[(int64_t)q * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// res[0..ng) level, res[ng..2ng) S_g, res[2ng..3ng) eta, res[3ng] the loss
+__global__ void k_gauge_final(DevParams P, const double *partial, int nblk, int ng, double *res)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double loss = 0.0;
+    for (int g = 0; g < ng; ++g) {
+        double num = 0.0, den = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            num += partial[(int64_t)(2 * g) * nblk + b];
+            den += partial[(int64_t)(2 * g + 1) * nblk + b];
+        }
+        const double level = den > 0.0 ? num / den : 0.0;
+        const double eta = den > 0.0 ? level - P.H : 0.0;
+        res[g] = level;
+        res[ng + g] = den;
+        res[2 * ng + g] = eta;
+        loss += eta * eta;
+    }
+    res[3 * ng] = loss;
+}
+
+__global__ void __launch_bounds__(MAPT) k_gauge_grad(DevParams P, vct_state s, int n, const int32_t *fs,
+                                                     int ng, const double *gxy, const double *res,
+                                                     double *pos_bar)
+{
+    const int i = blockIdx.x * MAPT + threadIdx.x;
+    if (i >= n) return;
+    const int nd = P.dim == 3 ? 3 : 2;
+    double bar[3] = {0.0, 0.0, 0.0};   // x, (y,) z
+    if (fs[i] == 1 && s.type[i] == FLUID) {
+        const double x = s.x[i], z = s.z[i], y = P.dim == 3 ? s.y[i] : 0.0;
+        for (int g = 0; g < ng; ++g) {
+            const double den = res[ng + g];
+            if (!(den > 0.0)) continue;
+            const double dx = x - gxy[2 * g], dy = P.dim == 3 ? y - gxy[2 * g + 1] : 0.0;
+            const double r = sqrt(dx * dx + dy * dy);
+            double w, dwdr;
+            gauge_w(r, P.inv_l, w, dwdr);
+            const double f = 2.0 * res[2 * ng + g] / den;
+            bar[nd - 1] += f * w;
+            if (r > 0.0) {
+                const double h = f * (z - res[g]) * dwdr / r;
+                bar[0] += h * dx;
+                if (P.dim == 3) bar[1] += h * dy;
+            }
+        }
+    }
+    for (int k = 0; k < nd; ++k) pos_bar[(int64_t)k * n + i] = bar[k];
+}
+
+int launch_gauge_loss(const DevParams &P, vct_state s, int64_t n, const int32_t *fs, int ng,
+                      const double *gxy, double *partial, int64_t partial_cap, double *res,
+                      double *pos_bar, cudaStream_t st)
+{
+    if (ng < 1 || ng > GAUGE_MAX) return 1;
+    const int nblk = (int)((n + MAPT - 1) / MAPT);
+    if ((int64_t)nblk * 2 * ng > partial_cap) return 2;
+    k_gauge_partials<<<nblk, MAPT, 0, st>>>(P, s, (int)n, fs, ng, gxy, partial);
+    k_gauge_final<<<1, 32, 0, st>>>(P, partial, nblk, ng, res);
+    if (pos_bar) k_gauge_grad<<<nblk, MAPT, 0, st>>>(P, s, (int)n, fs, ng, gxy, res, pos_bar);
+    return 0;
+}
+
 void launch_csr_export(const DevParams &P, Part cur, Work W, int64_t n, int64_t *row_ptr,
                        int32_t *col, int64_t col_cap, cudaStream_t st)
 {

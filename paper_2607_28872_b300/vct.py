@@ -23,7 +23,7 @@ EXPORTS = ("vct_init", "vct_set_stream", "vct_reset_history", "vct_build_neighbo
            "vct_build_neighbours_noalloc",
            "sph2_derivatives", "sph2_derivatives_backward", "sph2_gradient_backward_positions",
            "sph2_d2_backward_positions", "vct_ppe_backward_positions", "vct_rho_backward_positions",
-           "vct_map_backward", "vct_map_backward_positions", "vct_step",
+           "vct_map_backward", "vct_map_backward_positions", "vct_gauge_loss", "vct_step",
            "vct_batch_step",
            "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling", "vct_stage_times",
            "vct_last_error", "vct_strerror", "vct_destroy")
@@ -103,6 +103,8 @@ def load_library(path=LIB_PATH):
     L.vct_map_backward.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp, vp, vp, vp,
                                    C.POINTER(C.c_double)]
     L.vct_map_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp, vp, vp, vp, vp]
+    L.vct_gauge_loss.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     L.vct_step.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_step_host.argtypes = [vp, C.POINTER(vct_state), C.c_int32, C.POINTER(vct_stats)]
     L.vct_batch_step.argtypes = [C.POINTER(vp), C.POINTER(C.POINTER(vct_state)), C.c_int32,
@@ -127,6 +129,7 @@ def load_library(path=LIB_PATH):
                  "sph2_derivatives_backward", "sph2_gradient_backward_positions",
                  "sph2_d2_backward_positions", "vct_ppe_backward_positions",
                  "vct_rho_backward_positions", "vct_map_backward", "vct_map_backward_positions",
+                 "vct_gauge_loss",
                  "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
@@ -340,6 +343,25 @@ class Solver:
                                                         C.c_void_p(out.data_ptr())),
                     "vct_map_backward_positions")
         return out
+
+    def vct_gauge_loss(self, state, fs, gauges, grad=True):
+        """(loss, eta numpy (G,), pos_bar (dim, n) CUDA tensor or None): the
+        squared water levels at the gauges and their gradient with respect to
+        the physical positions, for the free-surface flags fs (int32 CUDA
+        tensor, caller order)."""
+        import torch
+        g = np.ascontiguousarray(np.asarray(gauges, dtype=np.float64).reshape(-1))
+        ng = g.size if self.dim == 2 else g.size // 2
+        loss = C.c_double(0.0)
+        eta = (C.c_double * max(ng, 1))()
+        out = torch.zeros((self.dim, state.n), dtype=torch.float64, device="cuda") if grad else None
+        s = state.struct()
+        fs = fs.to(torch.int32).contiguous()
+        self._check(self.lib.vct_gauge_loss(self.ctx, C.byref(s), C.c_void_p(fs.data_ptr()), ng,
+                                            g.ctypes.data_as(C.POINTER(C.c_double)), C.byref(loss),
+                                            eta, None if out is None else C.c_void_p(out.data_ptr())),
+                    "vct_gauge_loss")
+        return loss.value, np.array(eta[:ng]), out
 
     def sph2_gradient_backward_positions(self, state, phi, grad_bar):
         """Gradient of sum grad_bar . grad_hat (sph2_derivatives' corrected
