@@ -467,6 +467,38 @@ vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *o
  * out (host, may be NULL) receives the iteration count and residual. */
 vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct_stats *out);
 
+/* Reverse of one time step with respect to the fluid velocities (Sec. 3.3:
+ * predictor Eq. VCT_predictor with the viscous term of Eq. lap_VCT, the
+ * pressure equation Eqs. VCT_ppe and PNC, corrector and update Eq. VCT_update),
+ * with the positions held at the start of the step.  At fixed positions the
+ * step is affine in the velocities v^N (neighbour sets, free-surface flags,
+ * volumes, metric, moment matrices and the pressure operator all follow from
+ * the positions), so the result is the exact gradient, to the transposed
+ * solve's tolerance, of the loss
+ *   l = v_bar . v^(N+1) + x_bar . x^(N+1) + p_bar . p^(N+1)
+ * with respect to v^N; the positions' own gradient (x^(N+1) = x^N + dt v^(N+1)
+ * passes x_bar on, the geometry's dependence on x^N) is not part of it.
+ * state: device SoA in caller order at the start of the step (read only; the
+ * step is not advanced).  v_bar, x_bar: device, dim x n doubles, component-major
+ * (u, [v], w / x, [y], z), caller order; p_bar: device, n doubles; each may be
+ * NULL (zero); entries of non-fluid particles are ignored, and p_bar's off the
+ * unknown rows (the fluid particles off the free surface).  v_bar_in: device,
+ * dim x n doubles, written with dl/dv^N (0 for non-fluid particles).  Runs the
+ * step's assembly at the state's positions (map, sort, neighbours, smoothing,
+ * pass 1, pass 2, right side, multigrid setup), then the corrector's adjoint,
+ * the transposed pressure solve (as vct_ppe_adjoint: out receives its
+ * iteration count and residual), the right side's and the wall terms'
+ * adjoints, and the SPH(2) derivative operator's adjoint for the viscous term.
+ * FP64 arithmetic in the reverse; the operators in the context's precision.
+ * VCT_ERR_ARG with the Smagorinsky model, free-slip walls, regularisation or
+ * the ISPH operator set (terms whose reverse is not built), or v_bar_in NULL.
+ * Allocates (3 dim + dim^2 + dim + 2) doubles per particle of capacity on the
+ * first call; afterwards the context holds this step's pressure system (as
+ * after vct_step, for vct_ppe_adjoint). */
+vct_status vct_step_backward_velocity(vct_ctx *ctx, const vct_state *state, const double *v_bar,
+                                      const double *x_bar, const double *p_bar, double *v_bar_in,
+                                      vct_stats *out);
+
 /* Ensemble: advance n_scen independent scenarios (one context and one device
  * state each, uneven particle counts allowed) by nsteps steps in one call,
  * with no host synchronisation until the end, where each scenario's status is

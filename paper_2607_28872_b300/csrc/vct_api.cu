@@ -886,6 +886,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.diag = dalloc<double>(c, n, e);
     W.bvec = dalloc<double>(c, n, e);
     W.wallrhs = dalloc<double>(c, n, e);
+    W.pwall = dalloc<double>(c, n * d, e);
     W.jbar_tmp = dalloc<double>(c, n, e);
     W.jratio = dalloc<double>(c, n, e);
     W.hatf = dalloc<float4>(c, n, e);
@@ -1382,11 +1383,11 @@ VCT_API vct_status vct_batch_step(vct_ctx *const *ctxs, vct_state *const *states
     return first;
 }
 
-VCT_API vct_status vct_ppe_adjoint(vct_ctx *c, const double *p_bar, double *b_bar, vct_stats *out)
+// Transposed pressure solve on the held system, with the Jacobi-preconditioned
+// BiCGSTAB as the fallback when the forward hierarchy does not carry it.
+static vct_status ppe_adjoint_solve(vct_ctx *c, int64_t n, const double *p_bar, double *b_bar,
+                                    vct_stats *out)
 {
-    if (!c || !p_bar || !b_bar) return VCT_ERR_ARG;
-    if (c->ppe_n <= 0) return VCT_ERR_ARG;   // no pressure system held
-    const int64_t n = c->ppe_n;
     reset_status(c);
     int e = launch_ppe_adjoint(c->P, cur(c), c->W, c->precond ? &c->mg : nullptr, n, p_bar,
                                b_bar, c->st);
@@ -1394,14 +1395,70 @@ VCT_API vct_status vct_ppe_adjoint(vct_ctx *c, const double *p_bar, double *b_ba
     if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
     vct_status v = finish(c, out, 1);
     if (v == VCT_ERR_NOCONV && c->precond) {
-        // the forward hierarchy did not carry the transposed system: solve it
-        // again with the Jacobi-preconditioned BiCGSTAB
         reset_status(c);
         e = launch_ppe_adjoint(c->P, cur(c), c->W, nullptr, n, p_bar, b_bar, c->st);
         c->launches += 4;
         if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
         v = finish(c, out, 1);
     }
+    return v;
+}
+
+VCT_API vct_status vct_ppe_adjoint(vct_ctx *c, const double *p_bar, double *b_bar, vct_stats *out)
+{
+    if (!c || !p_bar || !b_bar) return VCT_ERR_ARG;
+    if (c->ppe_n <= 0) return VCT_ERR_ARG;   // no pressure system held
+    return ppe_adjoint_solve(c, c->ppe_n, p_bar, b_bar, out);
+}
+
+VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, const double *v_bar,
+                                              const double *x_bar, const double *p_bar,
+                                              double *v_bar_in, vct_stats *out)
+{
+    vct_status v = check_state(c, s);
+    if (v) return v;
+    if (!v_bar_in) return VCT_ERR_ARG;
+    // terms of the step that are not in the reverse: the eddy viscosity (nu
+    // depends on the velocity gradient), free-slip walls (wall velocities from
+    // the fluid's), the regularisation (shifts that scale with the speed) and
+    // the ISPH operator set
+    if (c->P.smag || c->P.slip || c->P.operators != 0 || regularise_on(c->P)) return VCT_ERR_ARG;
+    const int64_t n = s->n;
+    const int d = c->P.dim;
+    if (!c->W.sadj) {
+        cudaError_t e = cudaSuccess;
+        c->W.sadj = dalloc<double>(c, c->cap * (3 * d + d * d), e);
+        c->W.sadj_co = dalloc<double>(c, c->cap * (d + 2), e);
+        if (e != cudaSuccess) {
+            c->W.sadj = c->W.sadj_co = nullptr;
+            return VCT_ERR_CUDA;
+        }
+    }
+    reset_status(c);
+    launch_load(c->P, cur(c), *s, n, c->st);
+    c->launches += 1;
+    step_pre(c, n);   // the step's operators at the given positions (no solve, no update)
+    launch_stepadj_a(c->P, cur(c), c->W, n, v_bar, x_bar, p_bar, c->st);
+    c->launches += 2;
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    v = finish(c, nullptr, 0);   // errors of the operators' assembly
+    if (v) return v;
+    c->ppe_n = n;
+    double *pb = c->W.sadj_co, *bb = c->W.sadj_co + n, *lb = c->W.sadj_co + 2 * n;
+    v = ppe_adjoint_solve(c, n, pb, bb, out);
+    if (v) return v;
+    reset_status(c);
+    // the transposed solve kept its slot table in the neighbour lists: list the
+    // neighbours again (the same lists: same sorted positions)
+    launch_neighbours(c->P, cur(c), c->W, n, c->st);
+    c->launches += 1;
+    launch_stepadj_b(c->P, cur(c), c->W, n, c->st);
+    launch_sph2_adjoint(c->P, cur(c), c->W, n, d, nullptr, nullptr, lb, v_bar_in, c->st);
+    launch_stepadj_c(c->P, cur(c), c->W, n, v_bar_in, c->st);
+    c->launches += 2 + 2 * d + 1;
+    if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+    v = finish(c, nullptr, 0);
+    if (out) out->kernel_launches = c->launches;
     return v;
 }
 

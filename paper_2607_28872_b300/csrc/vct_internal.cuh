@@ -80,6 +80,8 @@ struct Work {
     double *vstar, *acc;      // [d] per particle
     int32_t *pcnt, *pcol;     // pressure-equation coefficients (ELL, slot-blocked: ell_at)
     double *pval, *diag, *bvec, *wallrhs;
+    double *pwall;            // [d] per unknown row: rho sum over wall neighbours of a_ij (r_j - r_i),
+                              // so that wallrhs = pwall . f_i (Eq. PNC; read by the step's reverse)
     float *pvalf;             // FP32 coefficients of the mixed form
     double *jbar_tmp;
     // Krylov
@@ -103,6 +105,8 @@ struct Work {
     double *kq0, *kq1;        // preconditioned directions p^, s^
     double *kz0, *kzb;        // V-cycle: first Jacobi step and prolonged correction
     double *adj;              // adjoint scratch: [m + dim] per particle
+    double *sadj;             // step reverse, cell order: [3 dim + dim^2] per particle (allocated on first use)
+    double *sadj_co;          // step reverse, caller order: [dim + 2] per particle
     double *rxh, *rmet;       // regularisation: projected position [d] and J, s_x, s_y
     double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
                               //   projected displacement [d]
@@ -239,6 +243,17 @@ void launch_gradpos(const DevParams &P, Part cur, Work W, int64_t n, int ncomp, 
 // (M: the context's multigrid hierarchy, or null for Jacobi preconditioning)
 int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_t n,
                        const double *p_bar, double *b_bar, cudaStream_t st);
+// reverse of one step with respect to the velocities, in three parts around the
+// two adjoint solves (scratch W.sadj, W.sadj_co):
+//   a: the corrector's adjoint, the pressure adjoint p_bar into W.sadj_co (caller order);
+//   b: after b_bar = A^-T p_bar (W.sadj_co + n), the right side's adjoint and the
+//      viscous term's lap_bar into W.sadj_co + 2n;
+//   c: after the SPH(2) adjoint wrote phi_bar into v_bar_in, v_bar_in += v*_bar.
+void launch_stepadj_a(const DevParams &P, Part cur, Work W, int64_t n, const double *v_bar,
+                      const double *x_bar, const double *p_bar, cudaStream_t st);
+void launch_stepadj_b(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+void launch_stepadj_c(const DevParams &P, Part cur, Work W, int64_t n, double *v_bar_in,
+                      cudaStream_t st);
 int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,
                             size_t smem, bool expl, cudaStream_t st);
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly);

@@ -1503,7 +1503,9 @@ __device__ __forceinline__ void pass2_body(const DevParams &P, const Part &c, co
 #pragma unroll
     for (int K = 0; K < D; ++K) ur[K] = (R)u[K];
     const R c0r = (R)c.c0[i];
-    double diag = 0.0, wallrhs = 0.0;
+    double diag = 0.0, wallrhs = 0.0, pw[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) pw[K] = 0.0;
     double pi_[3];
     load_phys<D>(c, i, pi_);
     int pc = 0;
@@ -1549,13 +1551,18 @@ __device__ __forceinline__ void pass2_body(const DevParams &P, const Part &c, co
             double pj[3], s = 0.0;
             load_phys<D>(c, j, pj);
 #pragma unroll
-            for (int K = 0; K < D; ++K) s += (pj[K] - pi_[K]) * acc[K];
+            for (int K = 0; K < D; ++K) {
+                s += (pj[K] - pi_[K]) * acc[K];
+                pw[K] += aij * P.rho * (pj[K] - pi_[K]);
+            }
             wallrhs += aij * P.rho * s;
         }
     }
     W.pcnt[i] = pc;
     W.diag[i] = diag;
     W.wallrhs[i] = wallrhs;
+#pragma unroll
+    for (int K = 0; K < D; ++K) W.pwall[(int64_t)K * cap + i] = pw[K];
     atomicAdd((unsigned long long *)&W.counts[0], 1ull);
     atomicAdd((unsigned long long *)&W.counts[1], (unsigned long long)pc);
 }
@@ -1692,7 +1699,9 @@ __device__ __forceinline__ void pass2_isph_body(const DevParams &P, const Part &
 #pragma unroll
     for (int a = 0; a < M; ++a) ctr[a] = (R)ct[a];
     const R c0r = (R)c.c0[i];
-    double diag = 0.0, wallrhs = 0.0;
+    double diag = 0.0, wallrhs = 0.0, pw[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) pw[K] = 0.0;
     double pi_[3];
     load_phys<D>(c, i, pi_);
     int pc = 0;
@@ -1728,13 +1737,18 @@ __device__ __forceinline__ void pass2_isph_body(const DevParams &P, const Part &
             double pj[3], s2 = 0.0;
             load_phys<D>(c, j, pj);
 #pragma unroll
-            for (int K = 0; K < D; ++K) s2 += (pj[K] - pi_[K]) * acc[K];
+            for (int K = 0; K < D; ++K) {
+                s2 += (pj[K] - pi_[K]) * acc[K];
+                pw[K] += aij * P.rho * (pj[K] - pi_[K]);
+            }
             wallrhs += aij * P.rho * s2;
         }
     }
     W.pcnt[i] = pc;
     W.diag[i] = diag;
     W.wallrhs[i] = wallrhs;
+#pragma unroll
+    for (int K = 0; K < D; ++K) W.pwall[(int64_t)K * cap + i] = pw[K];
     atomicAdd((unsigned long long *)&W.counts[0], 1ull);
     atomicAdd((unsigned long long *)&W.counts[1], (unsigned long long)pc);
 }
@@ -4568,7 +4582,14 @@ __global__ void __launch_bounds__(128) k_sph2_adj1(DevParams P, const Part c, Wo
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int b = 0; b < M; ++b) A[a * M + b] = (double)Mm[b * M + a].val();
-    if (!lu_solve<M, 1>(A, Dbar)) set_error(W.status, VCT_ERR_SINGULAR, i);
+    // as in the forward operator: an isolated particle has no second derivatives,
+    // and a free-surface particle whose M_i cannot be factored loses them
+    const int fsi = W.fs[i];
+    if (fsi == 2 || !lu_solve<M, 1>(A, Dbar)) {
+        if (!fsi) set_error(W.status, VCT_ERR_SINGULAR, i);
+#pragma unroll
+        for (int a = 0; a < M; ++a) Dbar[a] = 0.0;
+    }
     R bb[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) bb[a] = (R)(2.0 * Dbar[a]);
@@ -5463,6 +5484,315 @@ int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_
     if (e != cudaSuccess) return (int)e;
     k_adj_scatter<<<g, 256, 0, st>>>(cur, W, (int)n, b_bar);
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// a12 (part): reverse of one time step with respect to the fluid velocities
+// (Eqs. VCT_predictor, VCT_ppe, PNC, VCT_update), positions held at the start
+// of the step.  With the positions fixed the step is affine in v^N:
+//   f_i   = nu lap(v)_i + g                        (predictor, Eq. lap_VCT)
+//   v*_i  = v_i + dt f_i
+//   b_i   = rho/dt tr(J L_i X_i) - w_i . f_i + c   (X_i[c][K] = sum_j V_j (v_j - v*_i)_c fac r_K,
+//                                                   a wall j carrying v_wall + dt f_i; w_i: the
+//                                                   wall coefficients of Eq. PNC, W.pwall)
+//   p     = A^-1 b                                 (unknown rows: fluid off the free surface)
+//   v'_i  = v*_i - dt/rho J L_i sum_j V_j fac r p_ij,  p_ij = p_j - p_i or rho (r_j - r_i)_phys . f_i
+//   x'_i  = x_i + dt v'_i
+// so its adjoint is the transposed chain, run backwards: u = v'_bar + dt x'_bar,
+// a_i = L_i^T J^T (-dt/rho u_i), then p_bar (gathers over the symmetric neighbour
+// relation), b_bar = A^-T p_bar, the right side's adjoint (Y_i = rho/dt b_bar_i J L_i
+// per unknown row), f_bar, and the viscous term's adjoint (the SPH(2) derivative
+// operator's, with lap_bar = nu f_bar).  W.sadj rows: a [0, d), v*_bar [d, 2d),
+// f_bar [2d, 3d), Y [3d, 3d + d^2); W.sadj_co: p_bar, b_bar, lap_bar (d rows), all
+// caller order with stride n.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void jac_apply_t(double J, double sx, double sy, const double *g,
+                                            double *gh)
+{
+    // gh = J_m^T g for the Jacobian applied by jac_apply
+    if (D == 2) {
+        gh[0] = g[0];
+        gh[1] = sx * g[0] + J * g[1];
+    } else {
+        gh[0] = g[0];
+        gh[1] = g[1];
+        gh[2] = sx * g[0] + sy * g[1] + J * g[2];
+    }
+}
+
+__device__ __forceinline__ bool pp_unknown(const Part &c, const Work &W, int i)
+{
+    return c.type[i] == FLUID && !W.fs[i];
+}
+
+// -dw/r of the pair at separation r (projected), or 0 for coincident particles
+template <int D>
+__device__ __forceinline__ double pair_fac(const DevParams &P, const double *r)
+{
+    double rr2 = 0.0;
+#pragma unroll
+    for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
+    if (rr2 == 0.0) return 0.0;
+    double rr = sqrt(rr2), w, dw;
+    kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+    return -dw / rr;
+}
+
+// Corrector: u, a_i = L_i^T J^T (-dt/rho u_i), v*_bar = u, f_bar from the wall pairs
+// p_ij = rho (r_j - r_i)_phys . f_i.
+template <int D>
+__global__ void __launch_bounds__(128) k_stepadj_corr(DevParams P, const Part c, Work W, int n,
+                                                      const double *v_bar, const double *x_bar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    double *S = W.sadj;
+    if (c.type[i] != FLUID) {
+#pragma unroll
+        for (int k = 0; k < 3 * D; ++k) S[(int64_t)k * cap + i] = 0.0;
+        return;
+    }
+    const int o = c.orig[i];
+    double u[D], g[D], gh[D], a[D];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        u[cc] = (v_bar ? v_bar[(int64_t)cc * n + o] : 0.0) +
+                (x_bar ? P.dt * x_bar[(int64_t)cc * n + o] : 0.0);
+        g[cc] = -P.dt / P.rho * u[cc];
+    }
+    jac_apply_t<D>(c.J[i], c.sx[i], c.sy[i], g, gh);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double s = 0.0;
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(L2 * D + K) * cap + i] * gh[L2];
+        a[K] = s;
+    }
+    double xi[3], pi_[3], fb[D];
+    load_hat<D>(c, i, xi);
+    load_phys<D>(c, i, pi_);
+#pragma unroll
+    for (int K = 0; K < D; ++K) fb[K] = 0.0;
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        const int j = W.nbr[(int64_t)k * cap + i];
+        const int tj = c.type[j];
+        if (tj == VIRTUAL || tj == FLUID) continue;
+        double xj[3], pj[3], r[D], ra = 0.0;
+        load_hat<D>(c, j, xj);
+        load_phys<D>(c, j, pj);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xj[K] - xi[K];
+            ra += r[K] * a[K];
+        }
+        const double e = P.rho * W.vol[j] * pair_fac<D>(P, r) * ra;
+#pragma unroll
+        for (int K = 0; K < D; ++K) fb[K] += e * (pj[K] - pi_[K]);
+    }
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        S[(int64_t)K * cap + i] = a[K];
+        S[(int64_t)(D + K) * cap + i] = u[K];
+        S[(int64_t)(2 * D + K) * cap + i] = fb[K];
+    }
+}
+
+// p_bar_k = p_bar_in + sum_{i fluid in S_k} [V_k fac (r_ik . a_i) + V_i fac (r_ik . a_k)]
+// on unknown rows (r_ik = x^_k - x^_i), 0 elsewhere; caller order.
+template <int D>
+__global__ void __launch_bounds__(128) k_stepadj_pbar(DevParams P, const Part c, Work W, int n,
+                                                      const double *p_bar)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t cap = W.cap;
+    const int o = c.orig[k];
+    double *pb = W.sadj_co;
+    if (!pp_unknown(c, W, k)) {
+        pb[o] = 0.0;
+        return;
+    }
+    double xk[3], ak[D];
+    load_hat<D>(c, k, xk);
+#pragma unroll
+    for (int K = 0; K < D; ++K) ak[K] = W.sadj[(int64_t)K * cap + k];
+    const double Vk = W.vol[k];
+    double s = p_bar ? p_bar[o] : 0.0;
+    const int cnt = W.nbr_cnt[k];
+    for (int q = 0; q < cnt; ++q) {
+        const int i = W.nbr[(int64_t)q * cap + k];
+        if (c.type[i] != FLUID) continue;
+        double xi[3], r[D], rai = 0.0, rak = 0.0;
+        load_hat<D>(c, i, xi);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xk[K] - xi[K];
+            rai += r[K] * W.sadj[(int64_t)K * cap + i];
+            rak += r[K] * ak[K];
+        }
+        s += pair_fac<D>(P, r) * (Vk * rai + W.vol[i] * rak);
+    }
+    pb[o] = s;
+}
+
+// Right side, own terms of each unknown row i (b_bar_i from the transposed solve):
+// Y = rho/dt b_bar J L_i; v*_bar_i -= sum_j V_j fac (Y r); f_bar_i += dt sum_walls
+// V_j fac (Y r) - b_bar w_i.
+template <int D>
+__global__ void __launch_bounds__(128) k_stepadj_rhs(DevParams P, const Part c, Work W, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    double *S = W.sadj;
+    if (!pp_unknown(c, W, i)) {
+#pragma unroll
+        for (int k = 0; k < D * D; ++k) S[(int64_t)(3 * D + k) * cap + i] = 0.0;
+        return;
+    }
+    const double bb = W.sadj_co[(int64_t)n + c.orig[i]];
+    double Y[D * D];
+#pragma unroll
+    for (int Lc = 0; Lc < D; ++Lc) {   // column Lc of J L_i
+        double col[D], jc[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) col[K] = W.L[(int64_t)(K * D + Lc) * cap + i];
+        jac_apply<D>(c.J[i], c.sx[i], c.sy[i], col, jc);
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) Y[cc * D + Lc] = P.rho / P.dt * bb * jc[cc];
+    }
+    double xi[3], vb[D], fb[D];
+    load_hat<D>(c, i, xi);
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        vb[cc] = S[(int64_t)(D + cc) * cap + i];
+        fb[cc] = S[(int64_t)(2 * D + cc) * cap + i] - bb * W.pwall[(int64_t)cc * cap + i];
+    }
+    const int cnt = W.nbr_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        const int j = W.nbr[(int64_t)k * cap + i];
+        const int tj = c.type[j];
+        if (tj == VIRTUAL) continue;
+        double xj[3], r[D];
+        load_hat<D>(c, j, xj);
+#pragma unroll
+        for (int K = 0; K < D; ++K) r[K] = xj[K] - xi[K];
+        const double w = W.vol[j] * pair_fac<D>(P, r);
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double t = 0.0;
+#pragma unroll
+            for (int K = 0; K < D; ++K) t += Y[cc * D + K] * r[K];
+            vb[cc] -= w * t;
+            if (tj != FLUID) fb[cc] += P.dt * w * t;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) S[(int64_t)(3 * D + k) * cap + i] = Y[k];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        S[(int64_t)(D + cc) * cap + i] = vb[cc];
+        S[(int64_t)(2 * D + cc) * cap + i] = fb[cc];
+    }
+}
+
+// Right side, neighbour terms (the transpose as a gather): v*_bar_j += sum over
+// unknown k in S_j of V_j fac (Y_k r_kj); then f_bar_j += dt v*_bar_j and
+// lap_bar_j = nu_j f_bar_j (caller order) for the viscous term's adjoint.
+template <int D>
+__global__ void __launch_bounds__(128) k_stepadj_gather(DevParams P, const Part c, Work W, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t cap = W.cap;
+    double *S = W.sadj;
+    const int o = c.orig[j];
+    double *lb = W.sadj_co + 2 * (int64_t)n;
+    if (c.type[j] != FLUID) {
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) lb[(int64_t)cc * n + o] = 0.0;
+        return;
+    }
+    double xj[3], vb[D];
+    load_hat<D>(c, j, xj);
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) vb[cc] = S[(int64_t)(D + cc) * cap + j];
+    const double Vj = W.vol[j];
+    const int cnt = W.nbr_cnt[j];
+    for (int q = 0; q < cnt; ++q) {
+        const int k = W.nbr[(int64_t)q * cap + j];
+        if (!pp_unknown(c, W, k)) continue;
+        double xk[3], r[D];
+        load_hat<D>(c, k, xk);
+#pragma unroll
+        for (int K = 0; K < D; ++K) r[K] = xj[K] - xk[K];
+        const double w = Vj * pair_fac<D>(P, r);
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            double t = 0.0;
+#pragma unroll
+            for (int K = 0; K < D; ++K) t += S[(int64_t)(3 * D + cc * D + K) * cap + k] * r[K];
+            vb[cc] += w * t;
+        }
+    }
+    const double nu = W.nu[j];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        S[(int64_t)(D + cc) * cap + j] = vb[cc];
+        lb[(int64_t)cc * n + o] = nu * (S[(int64_t)(2 * D + cc) * cap + j] + P.dt * vb[cc]);
+    }
+}
+
+// v_bar_in (holding the viscous term's phi_bar) += v*_bar on fluid particles, 0 elsewhere.
+template <int D>
+__global__ void k_stepadj_out(const Part c, Work W, int n, double *v_bar_in)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    const int o = c.orig[i];
+    const bool fl = c.type[i] == FLUID;
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        double *y = v_bar_in + (int64_t)cc * n + o;
+        *y = fl ? *y + W.sadj[(int64_t)(D + cc) * cap + i] : 0.0;
+    }
+}
+
+void launch_stepadj_a(const DevParams &P, Part cur, Work W, int64_t n, const double *v_bar,
+                      const double *x_bar, const double *p_bar, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        k_stepadj_corr<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+        k_stepadj_pbar<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+    } else {
+        k_stepadj_corr<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+        k_stepadj_pbar<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+    }
+}
+
+void launch_stepadj_b(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        k_stepadj_rhs<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_stepadj_gather<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    } else {
+        k_stepadj_rhs<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_stepadj_gather<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+    }
+}
+
+void launch_stepadj_c(const DevParams &P, Part cur, Work W, int64_t n, double *v_bar_in,
+                      cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) k_stepadj_out<2><<<g, 128, 0, st>>>(cur, W, (int)n, v_bar_in);
+    else k_stepadj_out<3><<<g, 128, 0, st>>>(cur, W, (int)n, v_bar_in);
 }
 
 

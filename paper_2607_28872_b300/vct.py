@@ -25,8 +25,8 @@ EXPORTS = ("vct_init", "vct_set_stream", "vct_reset_history", "vct_build_neighbo
            "sph2_d2_backward_positions", "vct_ppe_backward_positions", "vct_rho_backward_positions",
            "vct_map_backward", "vct_map_backward_positions", "vct_gauge_loss", "vct_step",
            "vct_batch_step",
-           "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling", "vct_stage_times",
-           "vct_last_error", "vct_strerror", "vct_destroy")
+           "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_step_backward_velocity",
+           "vct_set_profiling", "vct_stage_times", "vct_last_error", "vct_strerror", "vct_destroy")
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -113,6 +113,8 @@ def load_library(path=LIB_PATH):
     L.vct_step_probe.argtypes = [vp, C.POINTER(vct_state), C.POINTER(vct_probe),
                                  C.POINTER(vct_stats)]
     L.vct_ppe_adjoint.argtypes = [vp, vp, vp, C.POINTER(vct_stats)]
+    L.vct_step_backward_velocity.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp, vp,
+                                             C.POINTER(vct_stats)]
     L.sph2_gradient_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, C.c_int32, vp, vp]
     L.sph2_d2_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp]
     L.vct_ppe_backward_positions.argtypes = [vp, C.POINTER(vct_state), vp, vp, vp]
@@ -130,7 +132,8 @@ def load_library(path=LIB_PATH):
                  "sph2_d2_backward_positions", "vct_ppe_backward_positions",
                  "vct_rho_backward_positions", "vct_map_backward", "vct_map_backward_positions",
                  "vct_gauge_loss",
-                 "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint", "vct_set_profiling",
+                 "vct_step", "vct_step_host", "vct_step_probe", "vct_ppe_adjoint",
+                 "vct_step_backward_velocity", "vct_set_profiling",
                  "vct_stage_times", "vct_last_error"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -429,6 +432,29 @@ class Solver:
                                              C.c_void_p(b_bar.data_ptr()), C.byref(st)),
                     "vct_ppe_adjoint")
         return b_bar, st
+
+    def vct_step_backward_velocity(self, state, v_bar=None, x_bar=None, p_bar=None):
+        """Gradient with respect to the state's fluid velocities of
+        v_bar . v' + x_bar . x' + p_bar . p' after one step from `state`
+        (positions held; the state is not advanced).  v_bar, x_bar: (dim, n),
+        p_bar: (n,), caller order, each optional; returns ((dim, n) float64 CUDA
+        tensor, stats of the transposed pressure solve)."""
+        import torch
+        d, n = state.dim, state.n
+
+        def dev(a, shape):
+            if a is None:
+                return None
+            return torch.as_tensor(a).to(device="cuda", dtype=torch.float64).reshape(shape).contiguous()
+        vb, xb, pb = dev(v_bar, (d, n)), dev(x_bar, (d, n)), dev(p_bar, (n,))
+        out = torch.zeros((d, n), dtype=torch.float64, device="cuda")
+        ptr = (lambda t: None if t is None else C.c_void_p(t.data_ptr()))
+        s = state.struct()
+        st = vct_stats()
+        self._check(self.lib.vct_step_backward_velocity(self.ctx, C.byref(s), ptr(vb), ptr(xb),
+                                                        ptr(pb), ptr(out), C.byref(st)),
+                    "vct_step_backward_velocity")
+        return out, st
 
     def vct_step(self, state, nsteps=1):
         s = state.struct()

@@ -1,0 +1,137 @@
+"""Reverse of one time step with respect to the velocities
+(vct_step_backward_velocity).
+
+With the positions fixed the step is affine in the fluid velocities v^N, so
+the gradient of l = v_bar . v' + x_bar . x' + p_bar . p' is exactly the change
+of l for a unit change of one velocity component.  The oracle's step
+(Sec. 3.3, Eqs. VCT_predictor, VCT_ppe, PNC, VCT_update) gives every component
+that way, one oracle step per component, and the GPU gradient is compared with
+it element by element; a second check takes directional differences of the
+GPU's own forward step.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2607_28872_b300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+COMP = {2: ("u", "w"), 3: ("u", "v", "w")}
+POS = {2: ("x", "z"), 3: ("x", "y", "z")}
+
+
+def _tank(kind, dim, precision=0):
+    over = dict(smagorinsky=0, krylov_rtol=1e-12, krylov_max_iter=20000, precision=precision)
+    if kind in ("E", "BFE"):
+        over["aspect"] = 2.0
+    if dim == 2:
+        return S.small_tank(dim=2, kind=kind, L=0.12, H=0.06, d0=0.01, seed=3, with_wave=True,
+                            **over)
+    return S.small_tank(dim=3, kind=kind, L=0.08, W=0.06, H=0.06, d0=0.01, seed=4, **over)
+
+
+def _weights(sc, seed):
+    rng = np.random.default_rng(seed)
+    d, n = sc.dim, sc.n
+    fl = (sc.type == S.FLUID).astype(float)
+    return rng.normal(size=(d, n)) * fl, rng.normal(size=(d, n)) * fl, rng.normal(size=n) * fl
+
+
+def _oracle_loss(sc, vel, vb, xb, pb):
+    st = O.OracleState(sc)
+    for c, name in enumerate(COMP[sc.dim]):
+        getattr(st, name)[:] = vel[c]
+    st, info = O.step(sc, state=st)
+    assert info["rc"] == 0
+    v1 = np.stack([getattr(st, k) for k in COMP[sc.dim]])
+    x1 = np.stack([getattr(st, k) for k in POS[sc.dim]])
+    return float((vb * v1).sum() + (xb * x1).sum() + (pb * st.p).sum())
+
+
+def _base_velocity(sc):
+    return np.stack([np.asarray(getattr(sc, k), dtype=np.float64) for k in COMP[sc.dim]])
+
+
+@pytest.mark.parametrize("kind,dim,precision,tol", [("SIGMA", 2, 0, 1e-9), ("BF", 2, 0, 1e-9),
+                                                    ("E", 2, 0, 1e-9), ("BF", 3, 0, 1e-9),
+                                                    ("BFE", 3, 0, 1e-9), ("SIGMA", 2, 1, 1e-5)],
+                         ids=["sigma-2d", "bf-2d", "e-2d", "bf-3d", "bfe-3d", "sigma-2d-mixed"])
+def test_step_backward_velocity_matches_oracle(kind, dim, precision, tol):
+    """Every fluid velocity component's gradient against the oracle's exact
+    one-sided difference (the loss is affine in the velocities).  FP64: to
+    the solves' tolerance; mixed: the operators' FP32 sums bound it."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    sc = _tank(kind, dim, precision)
+    vb, xb, pb = _weights(sc, 11)
+    s = V.Solver(sc)
+    got, st = s.vct_step_backward_velocity(V.DeviceState(sc), torch.tensor(vb), torch.tensor(xb),
+                                           torch.tensor(pb))
+    got = got.cpu().numpy()
+    assert got.shape == (dim, sc.n)
+    fl = np.flatnonzero(sc.type == S.FLUID)
+    assert np.all(got[:, sc.type != S.FLUID] == 0.0)
+    if fl.size > 100:   # a sample of the particles (one oracle step per component)
+        fl = np.sort(np.random.default_rng(5).choice(fl, 100, replace=False))
+    v0 = _base_velocity(sc)
+    l0 = _oracle_loss(sc, v0, vb, xb, pb)
+    h = 0.05
+    ref = np.zeros((dim, fl.size))
+    for c in range(dim):
+        for k, i in enumerate(fl):
+            vp = v0.copy()
+            vp[c, i] += h
+            ref[c, k] = (_oracle_loss(sc, vp, vb, xb, pb) - l0) / h
+    scale = np.abs(ref).max()
+    err = np.abs(got[:, fl] - ref).max() / scale
+    print(f"PARITY step backward velocity {kind} {dim}-D precision {precision}: max err "
+          f"{err:.2e} of max |grad| {scale:.3e}, transposed solve {st.krylov_iters_total} iterations")
+    assert scale > 0.0
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("kind,dim", [("SIGMA", 2), ("BF", 3)])
+def test_step_backward_velocity_matches_gpu_forward(kind, dim):
+    """<grad, dv> against (l(v + dv) - l(v - dv)) / 2 of the GPU step itself, for
+    random directions dv on the fluid particles."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    sc = _tank(kind, dim)
+    vb, xb, pb = _weights(sc, 12)
+    s = V.Solver(sc)
+    got, _ = s.vct_step_backward_velocity(V.DeviceState(sc), torch.tensor(vb), torch.tensor(xb),
+                                          torch.tensor(pb))
+    got = got.cpu().numpy()
+    v0 = _base_velocity(sc)
+    fl = (sc.type == S.FLUID).astype(float)
+
+    def loss(vel):
+        st = V.DeviceState(sc)
+        for c, k in enumerate(COMP[dim]):
+            getattr(st, k)[:] = torch.tensor(vel[c], device="cuda")
+        V.Solver(sc).vct_step(st, 1)
+        v1 = np.stack([getattr(st, k).cpu().numpy() for k in COMP[dim]])
+        x1 = np.stack([getattr(st, k).cpu().numpy() for k in POS[dim]])
+        return float((vb * v1).sum() + (xb * x1).sum() + (pb * st.p.cpu().numpy()).sum())
+
+    rng = np.random.default_rng(13)
+    for _ in range(3):
+        dv = rng.normal(size=v0.shape) * fl * 0.01
+        fd = (loss(v0 + dv) - loss(v0 - dv)) / 2.0
+        an = float((got * dv).sum())
+        scale = float(np.abs(got * dv).sum())
+        print(f"PARITY step backward velocity vs GPU forward {kind} {dim}-D: "
+              f"{an:.9e} against {fd:.9e}")
+        assert abs(an - fd) <= 1e-7 * scale, (an, fd, scale)
+
+
+def test_step_backward_velocity_rejects_terms_without_a_reverse():
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    for over in (dict(smagorinsky=1), dict(wall_slip=1), dict(operators=1),
+                 dict(S.REGULARISATION)):
+        sc = S.small_tank(dim=2, kind="BF", L=0.12, H=0.06, d0=0.01, seed=3, **over)
+        s = V.Solver(sc)
+        with pytest.raises(V.VCTError):
+            s.vct_step_backward_velocity(V.DeviceState(sc), torch.zeros((2, sc.n)))
