@@ -182,13 +182,11 @@ def run_adjoint(args):
     e1.synchronize()
     ppe_adj_ms = e0.elapsed_time(e1)
     # the reverse of one step with respect to the velocities against one forward
-    # step, on the same channel without the eddy viscosity (a term whose reverse
-    # is not built); the reverse re-assembles the step's operators itself
-    sc0 = S.adjoint_sigma(precision=args.precision, smagorinsky=0)
-    s_f, s_b = vct.Solver(sc0), vct.Solver(sc0)
-    st_f, st_b = vct.DeviceState(sc0), vct.DeviceState(sc0)
-    vb = torch.randn((2, sc0.n), dtype=torch.float64, device="cuda", generator=g)
-    xb = torch.randn((2, sc0.n), dtype=torch.float64, device="cuda", generator=g)
+    # step of the same workload (the reverse re-assembles the step's operators)
+    s_f, s_b = vct.Solver(sc), vct.Solver(sc)
+    st_f, st_b = vct.DeviceState(sc), vct.DeviceState(sc)
+    vb = torch.randn((2, sc.n), dtype=torch.float64, device="cuda", generator=g)
+    xb = torch.randn((2, sc.n), dtype=torch.float64, device="cuda", generator=g)
     ks = min(args.steps, 10)
     step_ms = timed(lambda: s_f.vct_step(st_f, 1), ks)
     sbw_ms = timed(lambda: s_b.vct_step_backward_velocity(st_b, vb, xb), ks)
@@ -205,8 +203,7 @@ def run_adjoint(args):
                                     "adjoint_iters": int(ast.krylov_iters_total)},
                       "step_velocity": {"forward_step_ms": step_ms, "backward_ms": sbw_ms,
                                         "ratio": sbw_ms / step_ms, "calls": ks,
-                                        "adjoint_iters": int(sst.krylov_iters_total),
-                                        "smagorinsky": 0},
+                                        "adjoint_iters": int(sst.krylov_iters_total)},
                       "scope": "operator adjoint, pressure-solve adjoint and the one-step "
                                "reverse with respect to the velocities (positions held); the "
                                "reverse through the positions, chained over steps, is not "

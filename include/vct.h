@@ -470,16 +470,21 @@ vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct
 /* Reverse of one time step with respect to the fluid velocities (Sec. 3.3:
  * predictor Eq. VCT_predictor with the viscous term of Eq. lap_VCT, the
  * pressure equation Eqs. VCT_ppe and PNC, corrector and update Eq. VCT_update),
- * with the positions held at the start of the step.  At fixed positions the
- * step is affine in the velocities v^N (neighbour sets, free-surface flags,
- * volumes, metric, moment matrices and the pressure operator all follow from
- * the positions), so the result is the exact gradient, to the transposed
- * solve's tolerance, of the loss
+ * with the positions held at the start of the step.  At fixed positions and
+ * without the eddy viscosity the step is affine in the velocities v^N
+ * (neighbour sets, free-surface flags, volumes, metric, moment matrices and
+ * the pressure operator all follow from the positions), so the result is the
+ * exact gradient, to the transposed solve's tolerance, of the loss
  *   l = v_bar . v^(N+1) + x_bar . x^(N+1) + p_bar . p^(N+1)
  * with respect to v^N; the positions' own gradient (x^(N+1) = x^N + dt v^(N+1)
  * passes x_bar on, the geometry's dependence on x^N) is not part of it.
  * state: device SoA in caller order at the start of the step (read only; the
- * step is not advanced).  v_bar, x_bar: device, dim x n doubles, component-major
+ * step is not advanced).  With the Smagorinsky model (Sec. 3.4) the step is not
+ * affine in v (nu_E grows with the strain rate): the result is then the
+ * gradient at v^N (the chain through nu_E, its gradient term and the eddy
+ * viscosity's Laplacian factor; nu_E is not differentiable where the strain
+ * rate vanishes, and its share is taken as 0 there).
+ * v_bar, x_bar: device, dim x n doubles, component-major
  * (u, [v], w / x, [y], z), caller order; p_bar: device, n doubles; each may be
  * NULL (zero); entries of non-fluid particles are ignored, and p_bar's off the
  * unknown rows (the fluid particles off the free surface).  v_bar_in: device,
@@ -488,11 +493,12 @@ vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct
  * pass 1, pass 2, right side, multigrid setup), then the corrector's adjoint,
  * the transposed pressure solve (as vct_ppe_adjoint: out receives its
  * iteration count and residual), the right side's and the wall terms'
- * adjoints, and the SPH(2) derivative operator's adjoint for the viscous term.
- * FP64 arithmetic in the reverse; the operators in the context's precision.
- * VCT_ERR_ARG with the Smagorinsky model, free-slip walls, regularisation or
- * the ISPH operator set (terms whose reverse is not built), or v_bar_in NULL.
- * Allocates (3 dim + dim^2 + dim + 2) doubles per particle of capacity on the
+ * adjoints, the SPH(2) derivative operator's adjoint for the viscous term, and
+ * with free-slip walls (Sec. 3.5) the adjoint of the wall particles' reflected
+ * Shepard velocities.  FP64 arithmetic in the reverse; the operators in the
+ * context's precision.  VCT_ERR_ARG with regularisation or the ISPH operator
+ * set (terms whose reverse is not built), or v_bar_in NULL.
+ * Allocates (7 dim + 3 dim^2 + 3) doubles per particle of capacity on the
  * first call; afterwards the context holds this step's pressure system (as
  * after vct_step, for vct_ppe_adjoint). */
 vct_status vct_step_backward_velocity(vct_ctx *ctx, const vct_state *state, const double *v_bar,

@@ -1418,17 +1418,15 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
     vct_status v = check_state(c, s);
     if (v) return v;
     if (!v_bar_in) return VCT_ERR_ARG;
-    // terms of the step that are not in the reverse: the eddy viscosity (nu
-    // depends on the velocity gradient), free-slip walls (wall velocities from
-    // the fluid's), the regularisation (shifts that scale with the speed) and
-    // the ISPH operator set
-    if (c->P.smag || c->P.slip || c->P.operators != 0 || regularise_on(c->P)) return VCT_ERR_ARG;
+    // terms of the step that are not in the reverse: the regularisation (shifts
+    // that scale with the speed) and the ISPH operator set
+    if (c->P.operators != 0 || regularise_on(c->P)) return VCT_ERR_ARG;
     const int64_t n = s->n;
     const int d = c->P.dim;
     if (!c->W.sadj) {
         cudaError_t e = cudaSuccess;
-        c->W.sadj = dalloc<double>(c, c->cap * (3 * d + d * d), e);
-        c->W.sadj_co = dalloc<double>(c, c->cap * (d + 2), e);
+        c->W.sadj = dalloc<double>(c, c->cap * (4 * d + 2 * d * d + 1), e);
+        c->W.sadj_co = dalloc<double>(c, c->cap * (3 * d + d * d + 2), e);
         if (e != cudaSuccess) {
             c->W.sadj = c->W.sadj_co = nullptr;
             return VCT_ERR_CUDA;
@@ -1439,7 +1437,7 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
     c->launches += 1;
     step_pre(c, n);   // the step's operators at the given positions (no solve, no update)
     launch_stepadj_a(c->P, cur(c), c->W, n, v_bar, x_bar, p_bar, c->st);
-    c->launches += 2;
+    c->launches += 2 + (c->P.smag ? 2 : 0);
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
     v = finish(c, nullptr, 0);   // errors of the operators' assembly
     if (v) return v;
@@ -1453,9 +1451,12 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
     launch_neighbours(c->P, cur(c), c->W, n, c->st);
     c->launches += 1;
     launch_stepadj_b(c->P, cur(c), c->W, n, c->st);
-    launch_sph2_adjoint(c->P, cur(c), c->W, n, d, nullptr, nullptr, lb, v_bar_in, c->st);
+    // the eddy viscosity's share reaches the velocities through the corrected
+    // gradient: the SPH(2) adjoint takes it as the gradient's adjoint
+    const double *gb = c->P.smag ? c->W.sadj_co + (2 + 3 * d) * n : nullptr;
+    launch_sph2_adjoint(c->P, cur(c), c->W, n, d, gb, nullptr, lb, v_bar_in, c->st);
     launch_stepadj_c(c->P, cur(c), c->W, n, v_bar_in, c->st);
-    c->launches += 2 + 2 * d + 1;
+    c->launches += 2 + (c->P.smag ? 2 : 0) + 2 * d + 1 + (c->P.slip ? 1 : 0);
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
     v = finish(c, nullptr, 0);
     if (out) out->kernel_launches = c->launches;

@@ -5711,11 +5711,12 @@ __global__ void __launch_bounds__(128) k_stepadj_gather(DevParams P, const Part 
     double *S = W.sadj;
     const int o = c.orig[j];
     double *lb = W.sadj_co + 2 * (int64_t)n;
-    if (c.type[j] != FLUID) {
+    const int tj = c.type[j];
 #pragma unroll
-        for (int cc = 0; cc < D; ++cc) lb[(int64_t)cc * n + o] = 0.0;
-        return;
-    }
+    for (int cc = 0; cc < D; ++cc) lb[(int64_t)cc * n + o] = 0.0;
+    // a free-slip wall particle's velocity enters the right side like a fluid
+    // particle's (its v_j - v*_i); it gathers the same terms
+    if (tj == VIRTUAL || (tj == WALL && !P.slip)) return;
     double xj[3], vb[D];
     load_hat<D>(c, j, xj);
 #pragma unroll
@@ -5738,41 +5739,327 @@ __global__ void __launch_bounds__(128) k_stepadj_gather(DevParams P, const Part 
             vb[cc] += w * t;
         }
     }
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) S[(int64_t)(D + cc) * cap + j] = vb[cc];
+    if (tj != FLUID) return;
     const double nu = W.nu[j];
 #pragma unroll
     for (int cc = 0; cc < D; ++cc) {
-        S[(int64_t)(D + cc) * cap + j] = vb[cc];
-        lb[(int64_t)cc * n + o] = nu * (S[(int64_t)(2 * D + cc) * cap + j] + P.dt * vb[cc]);
+        const double fb = S[(int64_t)(2 * D + cc) * cap + j] + P.dt * vb[cc];   // f_bar, final
+        S[(int64_t)(2 * D + cc) * cap + j] = fb;
+        lb[(int64_t)cc * n + o] = nu * fb;
     }
 }
 
-// v_bar_in (holding the viscous term's phi_bar) += v*_bar on fluid particles, 0 elsewhere.
+// The velocity field the step's viscous term differentiates (fluid velocities,
+// and the free-slip wall velocities where on), in caller order for the SPH(2)
+// operator: phi_co[c n + orig].
 template <int D>
-__global__ void k_stepadj_out(const Part c, Work W, int n, double *v_bar_in)
+__global__ void k_stepadj_vcopy(const Part c, Work W, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v[3];
+    load_vel<D>(c, i, v);
+    double *phi = W.sadj_co + (2 + D) * (int64_t)n;
+    const int o = c.orig[i];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) phi[(int64_t)cc * n + o] = c.type[i] == VIRTUAL ? 0.0 : v[cc];
+}
+
+// Eddy viscosity (Sec. 3.4), first part, per fluid particle j with its final
+// f_bar: the step has f = nu lap + T + g, T_c = sum_J (G_cJ + G_Jc) gn_J with
+// G_IJ = dv_J/dx_I, gn = J L sum_k V_k (nu_k - nu_j) grad w_jk, nu = nu_K + nu_E.
+// Writes nu_bar_j = f_bar . lap - (its own share of gn's sum), G_bar from T, and
+// b_j = L^T J^T gn_bar for the neighbours' share (k_stepadj_smag2).
+// W.sadj rows: b [3d + d^2, 4d + d^2), nu_bar 4d + d^2, G_bar [4d + d^2 + 1, 4d + 2 d^2 + 1).
+template <int D>
+__global__ void __launch_bounds__(128) k_stepadj_smag1(DevParams P, const Part c, Work W, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || c.type[j] != FLUID) return;
+    const int64_t cap = W.cap;
+    double *S = W.sadj;
+    const int RB = 3 * D + D * D, RN = RB + D, RG = RN + 1;
+    const int o = c.orig[j];
+    const double *lap = W.sadj_co + (2 + 2 * D) * (int64_t)n;
+    double G[D * D], fb[D];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        double gh[D], g[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) gh[K] = W.gv[(int64_t)(cc * D + K) * cap + j];
+        jac_apply<D>(c.J[j], c.sx[j], c.sy[j], gh, g);
+#pragma unroll
+        for (int I = 0; I < D; ++I) G[I * D + cc] = g[I];
+        fb[cc] = S[(int64_t)(2 * D + cc) * cap + j];
+    }
+    // gn (forward) from the neighbours' viscosities
+    double xj[3], gs[D];
+    load_hat<D>(c, j, xj);
+#pragma unroll
+    for (int K = 0; K < D; ++K) gs[K] = 0.0;
+    const double nuj = W.nu[j];
+    const int cnt = W.nbr_cnt[j];
+    for (int q = 0; q < cnt; ++q) {
+        const int k = W.nbr[(int64_t)q * cap + j];
+        const int tk = c.type[k];
+        if (tk == VIRTUAL) continue;
+        double xk[3], r[D];
+        load_hat<D>(c, k, xk);
+#pragma unroll
+        for (int K = 0; K < D; ++K) r[K] = xk[K] - xj[K];
+        const double e = W.vol[k] * ((tk == FLUID ? W.nu[k] : P.nu_k) - nuj) * pair_fac<D>(P, r);
+#pragma unroll
+        for (int K = 0; K < D; ++K) gs[K] += e * r[K];
+    }
+    double gnh[D], gn[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double s = 0.0;
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(K * D + L2) * cap + j] * gs[L2];
+        gnh[K] = s;
+    }
+    jac_apply<D>(c.J[j], c.sx[j], c.sy[j], gnh, gn);
+    // T's adjoint
+    double Gb[D * D], gnb[D], nub = 0.0;
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) Gb[k] = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) nub += fb[cc] * lap[(int64_t)cc * n + o];
+#pragma unroll
+    for (int J2 = 0; J2 < D; ++J2) {
+        double s = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+            Gb[cc * D + J2] += fb[cc] * gn[J2];
+            Gb[J2 * D + cc] += fb[cc] * gn[J2];
+            s += fb[cc] * (G[cc * D + J2] + G[J2 * D + cc]);
+        }
+        gnb[J2] = s;
+    }
+    double gnbh[D], b[D];
+    jac_apply_t<D>(c.J[j], c.sx[j], c.sy[j], gnb, gnbh);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double s = 0.0;
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(L2 * D + K) * cap + j] * gnbh[L2];
+        b[K] = s;
+    }
+    // own share of the sum: -nu_j sum_k V_k grad w_jk . b
+    double own = 0.0;
+    for (int q = 0; q < cnt; ++q) {
+        const int k = W.nbr[(int64_t)q * cap + j];
+        if (c.type[k] == VIRTUAL) continue;
+        double xk[3], r[D], rb = 0.0;
+        load_hat<D>(c, k, xk);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xk[K] - xj[K];
+            rb += r[K] * b[K];
+        }
+        own += W.vol[k] * pair_fac<D>(P, r) * rb;
+    }
+    nub -= own;
+#pragma unroll
+    for (int K = 0; K < D; ++K) S[(int64_t)(RB + K) * cap + j] = b[K];
+    S[(int64_t)RN * cap + j] = nub;
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) S[(int64_t)(RG + k) * cap + j] = Gb[k];
+}
+
+// Eddy viscosity, second part, per particle k: nu_bar_k += sum over fluid j in S_k of
+// V_k grad w_jk . b_j (its share of its neighbours' gn), then through
+// nu_E = (C_s f_s r_e)^2 sqrt(2 S:S): G_bar += nu_bar nu_E S / (S:S), and
+// grad^_bar = J^T G_bar per velocity component into the SPH(2) adjoint's gradient
+// input (caller order, [(c d + K) n + orig]; 0 off the fluid).
+template <int D>
+__global__ void __launch_bounds__(128) k_stepadj_smag2(DevParams P, const Part c, Work W, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t cap = W.cap;
+    const double *S = W.sadj;
+    const int RB = 3 * D + D * D, RN = RB + D, RG = RN + 1;
+    const int o = c.orig[k];
+    double *gbar = W.sadj_co + (2 + 3 * D) * (int64_t)n;
+    if (c.type[k] != FLUID) {
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) gbar[(int64_t)q * n + o] = 0.0;
+        return;
+    }
+    double xk[3], nub = S[(int64_t)RN * cap + k];
+    load_hat<D>(c, k, xk);
+    const double Vk = W.vol[k];
+    const int cnt = W.nbr_cnt[k];
+    for (int q = 0; q < cnt; ++q) {
+        const int j = W.nbr[(int64_t)q * cap + k];
+        if (c.type[j] != FLUID) continue;
+        double xj[3], r[D], rb = 0.0;
+        load_hat<D>(c, j, xj);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xk[K] - xj[K];   // r_jk, seen from j
+            rb += r[K] * S[(int64_t)(RB + K) * cap + j];
+        }
+        nub += Vk * pair_fac<D>(P, r) * rb;
+    }
+    double G[D * D], Gb[D * D], SS = 0.0, Sm[D * D];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        double gh[D], g[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) gh[K] = W.gv[(int64_t)(cc * D + K) * cap + k];
+        jac_apply<D>(c.J[k], c.sx[k], c.sy[k], gh, g);
+#pragma unroll
+        for (int I = 0; I < D; ++I) G[I * D + cc] = g[I];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            Sm[a * D + b] = 0.5 * (G[a * D + b] + G[b * D + a]);
+            SS += Sm[a * D + b] * Sm[a * D + b];
+        }
+    const double nue = W.nu[k] - P.nu_k;
+    const double s = SS > 0.0 ? nub * nue / SS : 0.0;
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) Gb[q] = S[(int64_t)(RG + q) * cap + k] + s * Sm[q];
+    // G[I d + c] = sum_K J[I][K] grad^[c d + K]: grad^_bar[c d + K] = (J^T G_bar[., c])_K
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) {
+        double col[D], gh[D];
+#pragma unroll
+        for (int I = 0; I < D; ++I) col[I] = Gb[I * D + cc];
+        jac_apply_t<D>(c.J[k], c.sx[k], c.sy[k], col, gh);
+#pragma unroll
+        for (int K = 0; K < D; ++K) gbar[(int64_t)(cc * D + K) * n + o] = gh[K];
+    }
+}
+
+// Free-slip walls: wall j carries v_j = R_j sum_k V_k w_jk v_k / den_j (R_j = I - 2 n n^T,
+// the Shepard average of its fluid neighbours reflected at the wall).  Its adjoint
+// t_j (the viscous operator's phi_bar, in v_bar_in, plus the right side's, in W.sadj)
+// becomes y_j = R_j t_j / den_j (rows [3d, 4d) of W.sadj, free on wall particles);
+// k_stepadj_out hands V_k w_jk y_j to each fluid neighbour k.
+template <int D>
+__global__ void __launch_bounds__(128) k_stepadj_wall(DevParams P, const Part c, Work W, int n,
+                                                      const double *v_bar_in)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || c.type[j] != WALL) return;
+    const int64_t cap = W.cap;
+    const int o = c.orig[j];
+    double xj[3], den = 0.0, nh[3] = {0.0, 0.0, 0.0};
+    load_hat<D>(c, j, xj);
+    const int cnt = W.nbr_cnt[j];
+    for (int q = 0; q < cnt; ++q) {
+        const int k = W.nbr[(int64_t)q * cap + j];
+        const int tk = c.type[k];
+        if (tk == WALL) continue;
+        double xk[3], r[3], rr2 = 0.0;
+        load_hat<D>(c, k, xk);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = xk[K] - xj[K];
+            rr2 += r[K] * r[K];
+        }
+        const double rr = sqrt(rr2);
+        double w, dw;
+        kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+        if (tk == FLUID) den += W.vol[k] * w;
+        else if (rr > 0.0) {
+#pragma unroll
+            for (int K = 0; K < D; ++K) nh[K] += P.V0 * (-dw / rr) * r[K];
+        }
+    }
+    double y[D];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) y[cc] = 0.0;
+    if (den > 0.0) {
+        double nn[D], nl = 0.0, tn = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc)
+            y[cc] = v_bar_in[(int64_t)cc * n + o] + W.sadj[(int64_t)(D + cc) * cap + j];
+        jac_apply<D>(c.J[j], c.sx[j], c.sy[j], nh, nn);
+#pragma unroll
+        for (int I = 0; I < D; ++I) nl += nn[I] * nn[I];
+        nl = sqrt(nl);
+        if (nl > 0.0) {
+#pragma unroll
+            for (int I = 0; I < D; ++I) {
+                nn[I] /= nl;
+                tn += nn[I] * y[I];
+            }
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) y[cc] -= 2.0 * tn * nn[cc];
+        }
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) y[cc] /= den;
+    }
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) W.sadj[(int64_t)(3 * D + cc) * cap + j] = y[cc];
+}
+
+// v_bar_in (holding the viscous term's phi_bar) += v*_bar on fluid particles, and
+// with free-slip walls the wall neighbours' V_k w_jk y_j; 0 elsewhere.
+template <int D>
+__global__ void k_stepadj_out(DevParams P, const Part c, Work W, int n, double *v_bar_in)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t cap = W.cap;
     const int o = c.orig[i];
-    const bool fl = c.type[i] == FLUID;
+    if (c.type[i] != FLUID) {
 #pragma unroll
-    for (int cc = 0; cc < D; ++cc) {
-        double *y = v_bar_in + (int64_t)cc * n + o;
-        *y = fl ? *y + W.sadj[(int64_t)(D + cc) * cap + i] : 0.0;
+        for (int cc = 0; cc < D; ++cc) v_bar_in[(int64_t)cc * n + o] = 0.0;
+        return;
     }
+    double t[D];
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc)
+        t[cc] = v_bar_in[(int64_t)cc * n + o] + W.sadj[(int64_t)(D + cc) * cap + i];
+    if (P.slip) {
+        double xi[3];
+        load_hat<D>(c, i, xi);
+        const double Vi = W.vol[i];
+        const int cnt = W.nbr_cnt[i];
+        for (int q = 0; q < cnt; ++q) {
+            const int j = W.nbr[(int64_t)q * cap + i];
+            if (c.type[j] != WALL) continue;
+            double xj[3], rr2 = 0.0;
+            load_hat<D>(c, j, xj);
+#pragma unroll
+            for (int K = 0; K < D; ++K) rr2 += (xi[K] - xj[K]) * (xi[K] - xj[K]);
+            double w, dw;
+            kern_wdw<double>(sqrt(rr2), P.inv_l, P.ad, w, dw);
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) t[cc] += Vi * w * W.sadj[(int64_t)(3 * D + cc) * cap + j];
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < D; ++cc) v_bar_in[(int64_t)cc * n + o] = t[cc];
 }
 
 void launch_stepadj_a(const DevParams &P, Part cur, Work W, int64_t n, const double *v_bar,
                       const double *x_bar, const double *p_bar, cudaStream_t st)
 {
     const unsigned g = (unsigned)((n + 127) / 128);
-    if (P.dim == 2) {
+    const int D = P.dim;
+    if (D == 2) {
         k_stepadj_corr<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
         k_stepadj_pbar<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        if (P.smag) k_stepadj_vcopy<2><<<g, 128, 0, st>>>(cur, W, (int)n);
     } else {
         k_stepadj_corr<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
         k_stepadj_pbar<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        if (P.smag) k_stepadj_vcopy<3><<<g, 128, 0, st>>>(cur, W, (int)n);
     }
+    if (P.smag)   // the forward viscous term's Laplacian, for nu_bar
+        launch_sph2_field(P, cur, W, n, W.sadj_co + (2 + D) * n, D, nullptr, nullptr,
+                          W.sadj_co + (2 + 2 * D) * n, st);
 }
 
 void launch_stepadj_b(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
@@ -5781,9 +6068,17 @@ void launch_stepadj_b(const DevParams &P, Part cur, Work W, int64_t n, cudaStrea
     if (P.dim == 2) {
         k_stepadj_rhs<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
         k_stepadj_gather<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.smag) {
+            k_stepadj_smag1<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            k_stepadj_smag2<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        }
     } else {
         k_stepadj_rhs<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
         k_stepadj_gather<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.smag) {
+            k_stepadj_smag1<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+            k_stepadj_smag2<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        }
     }
 }
 
@@ -5791,8 +6086,13 @@ void launch_stepadj_c(const DevParams &P, Part cur, Work W, int64_t n, double *v
                       cudaStream_t st)
 {
     const unsigned g = (unsigned)((n + 127) / 128);
-    if (P.dim == 2) k_stepadj_out<2><<<g, 128, 0, st>>>(cur, W, (int)n, v_bar_in);
-    else k_stepadj_out<3><<<g, 128, 0, st>>>(cur, W, (int)n, v_bar_in);
+    if (P.dim == 2) {
+        if (P.slip) k_stepadj_wall<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar_in);
+        k_stepadj_out<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar_in);
+    } else {
+        if (P.slip) k_stepadj_wall<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar_in);
+        k_stepadj_out<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar_in);
+    }
 }
 
 

@@ -21,8 +21,9 @@ COMP = {2: ("u", "w"), 3: ("u", "v", "w")}
 POS = {2: ("x", "z"), 3: ("x", "y", "z")}
 
 
-def _tank(kind, dim, precision=0):
+def _tank(kind, dim, precision=0, **extra):
     over = dict(smagorinsky=0, krylov_rtol=1e-12, krylov_max_iter=20000, precision=precision)
+    over.update(extra)
     if kind in ("E", "BFE"):
         over["aspect"] = 2.0
     if dim == 2:
@@ -53,17 +54,20 @@ def _base_velocity(sc):
     return np.stack([np.asarray(getattr(sc, k), dtype=np.float64) for k in COMP[sc.dim]])
 
 
-@pytest.mark.parametrize("kind,dim,precision,tol", [("SIGMA", 2, 0, 1e-9), ("BF", 2, 0, 1e-9),
-                                                    ("E", 2, 0, 1e-9), ("BF", 3, 0, 1e-9),
-                                                    ("BFE", 3, 0, 1e-9), ("SIGMA", 2, 1, 1e-5)],
-                         ids=["sigma-2d", "bf-2d", "e-2d", "bf-3d", "bfe-3d", "sigma-2d-mixed"])
-def test_step_backward_velocity_matches_oracle(kind, dim, precision, tol):
+@pytest.mark.parametrize("kind,dim,precision,slip,tol",
+                         [("SIGMA", 2, 0, 0, 1e-9), ("BF", 2, 0, 0, 1e-9), ("E", 2, 0, 0, 1e-9),
+                          ("BF", 3, 0, 0, 1e-9), ("BFE", 3, 0, 0, 1e-9), ("SIGMA", 2, 1, 0, 1e-5),
+                          ("SIGMA", 2, 0, 1, 1e-9), ("BF", 3, 0, 1, 1e-9)],
+                         ids=["sigma-2d", "bf-2d", "e-2d", "bf-3d", "bfe-3d", "sigma-2d-mixed",
+                              "sigma-2d-slip", "bf-3d-slip"])
+def test_step_backward_velocity_matches_oracle(kind, dim, precision, slip, tol):
     """Every fluid velocity component's gradient against the oracle's exact
-    one-sided difference (the loss is affine in the velocities).  FP64: to
-    the solves' tolerance; mixed: the operators' FP32 sums bound it."""
+    one-sided difference (the loss is affine in the velocities, free-slip wall
+    velocities included).  FP64: to the solves' tolerance; mixed: the
+    operators' FP32 sums bound it."""
     import torch
     from paper_2607_28872_b300 import vct as V
-    sc = _tank(kind, dim, precision)
+    sc = _tank(kind, dim, precision, wall_slip=slip)
     vb, xb, pb = _weights(sc, 11)
     s = V.Solver(sc)
     got, st = s.vct_step_backward_velocity(V.DeviceState(sc), torch.tensor(vb), torch.tensor(xb),
@@ -85,10 +89,69 @@ def test_step_backward_velocity_matches_oracle(kind, dim, precision, tol):
             ref[c, k] = (_oracle_loss(sc, vp, vb, xb, pb) - l0) / h
     scale = np.abs(ref).max()
     err = np.abs(got[:, fl] - ref).max() / scale
-    print(f"PARITY step backward velocity {kind} {dim}-D precision {precision}: max err "
+    print(f"PARITY step backward velocity {kind} {dim}-D precision {precision} slip {slip}: max err "
           f"{err:.2e} of max |grad| {scale:.3e}, transposed solve {st.krylov_iters_total} iterations")
     assert scale > 0.0
     assert err < tol, err
+
+
+def _sheared(sc):
+    """The scenario's velocities plus a smooth flow whose strain rate is nowhere
+    near zero on the fluid (the eddy viscosity's |S| has its kink there)."""
+    v = _base_velocity(sc)
+    x, z = np.asarray(sc.x), np.asarray(sc.z)
+    fl = sc.type == S.FLUID
+    v[0] += 0.3 * fl * (1.0 + z / 0.06 + 0.5 * np.sin(2 * np.pi * x / 0.12))
+    v[-1] += 0.2 * fl * np.cos(2 * np.pi * x / 0.12)
+    return v
+
+
+def _device_state(sc, vel):
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    st = V.DeviceState(sc)
+    for c, k in enumerate(COMP[sc.dim]):
+        getattr(st, k)[:] = torch.tensor(vel[c], device="cuda")
+    return st
+
+
+@pytest.mark.parametrize("kind,dim,slip", [("SIGMA", 2, 0), ("BF", 2, 1), ("BF", 3, 0)],
+                         ids=["sigma-2d", "bf-2d-slip", "bf-3d"])
+def test_step_backward_velocity_eddy_viscosity_matches_oracle(kind, dim, slip):
+    """With the Smagorinsky model the step is not affine in the velocities: the
+    GPU gradient at a sheared flow against the oracle's central differences,
+    component by component (a sample of 40 particles in 3-D)."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    sc = _tank(kind, dim, wall_slip=slip, smagorinsky=1)
+    vb, xb, pb = _weights(sc, 21)
+    v0 = _sheared(sc)
+    s = V.Solver(sc)
+    got, _ = s.vct_step_backward_velocity(_device_state(sc, v0), torch.tensor(vb), torch.tensor(xb),
+                                          torch.tensor(pb))
+    got = got.cpu().numpy()
+    fl = np.flatnonzero(sc.type == S.FLUID)
+    if dim == 3:
+        fl = np.sort(np.random.default_rng(6).choice(fl, 40, replace=False))
+    h = 1e-5
+    ref = np.zeros((dim, fl.size))
+    for c in range(dim):
+        for k, i in enumerate(fl):
+            vp, vm = v0.copy(), v0.copy()
+            vp[c, i] += h
+            vm[c, i] -= h
+            ref[c, k] = (_oracle_loss(sc, vp, vb, xb, pb) - _oracle_loss(sc, vm, vb, xb, pb)) / (2 * h)
+    scale = np.abs(ref).max()
+    err = np.abs(got[:, fl] - ref).max() / scale
+    # the eddy viscosity's share, for scale: the same gradient with the model off
+    s0 = V.Solver(_tank(kind, dim, wall_slip=slip))
+    g0, _ = s0.vct_step_backward_velocity(_device_state(sc, v0), torch.tensor(vb), torch.tensor(xb),
+                                          torch.tensor(pb))
+    share = np.abs(got - g0.cpu().numpy()).max() / scale
+    print(f"PARITY step backward velocity, eddy viscosity, {kind} {dim}-D slip {slip}: max err "
+          f"{err:.2e} of max |grad| {scale:.3e}; the model's share of the gradient {share:.2e}")
+    assert err < 1e-6, err
+    assert share > 100 * err
 
 
 @pytest.mark.parametrize("kind,dim", [("SIGMA", 2), ("BF", 3)])
@@ -129,7 +192,7 @@ def test_step_backward_velocity_matches_gpu_forward(kind, dim):
 def test_step_backward_velocity_rejects_terms_without_a_reverse():
     import torch
     from paper_2607_28872_b300 import vct as V
-    for over in (dict(smagorinsky=1), dict(wall_slip=1), dict(operators=1),
+    for over in (dict(operators=1),
                  dict(S.REGULARISATION)):
         sc = S.small_tank(dim=2, kind="BF", L=0.12, H=0.06, d0=0.01, seed=3, **over)
         s = V.Solver(sc)
