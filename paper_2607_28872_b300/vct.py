@@ -219,6 +219,32 @@ class DeviceState:
         out["type"] = self.type.cpu().numpy()
         return out
 
+    def clone(self):
+        out = DeviceState.__new__(DeviceState)
+        out.n, out.dim = self.n, self.dim
+        for k in self.FIELDS + ("type",):
+            setattr(out, k, getattr(self, k).clone())
+        return out
+
+    def _names(self, vel):
+        if vel:
+            return ("u", "w") if self.dim == 2 else ("u", "v", "w")
+        return ("x", "z") if self.dim == 2 else ("x", "y", "z")
+
+    def velocity(self):
+        """(dim, n) copy of the velocities (u, [v], w)."""
+        import torch
+        return torch.stack([getattr(self, k) for k in self._names(True)])
+
+    def position(self):
+        """(dim, n) copy of the positions (x, [y], z)."""
+        import torch
+        return torch.stack([getattr(self, k) for k in self._names(False)])
+
+    def set_velocity(self, vel):
+        for c, k in enumerate(self._names(True)):
+            getattr(self, k).copy_(vel[c])
+
 
 class HostState:
     """Host (pinned) copy of a particle state for vct_step_host."""
@@ -553,6 +579,37 @@ def sph2_function():
             return phib, None, None
 
     return SPH2Derivatives
+
+
+def step_function():
+    """torch.autograd.Function over one time step as a function of the velocities,
+    the positions held: apply(vel, solver, state) runs vct_step on a copy of
+    `state` with velocities `vel` ((dim, n), caller order) and returns
+    (v', x', p'); backward is vct_step_backward_velocity at `vel`.  `state` is
+    not modified."""
+    import torch
+
+    class StepVelocity(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, vel, solver, state):
+            vel = vel.detach()
+            st = state.clone()
+            st.set_velocity(vel)
+            solver.vct_step(st, 1)
+            ctx.solver = solver
+            ctx.state = state
+            ctx.save_for_backward(vel)
+            return st.velocity(), st.position(), st.p.clone()
+
+        @staticmethod
+        def backward(ctx, vbar, xbar, pbar):
+            (vel,) = ctx.saved_tensors
+            st = ctx.state.clone()
+            st.set_velocity(vel)
+            g, _ = ctx.solver.vct_step_backward_velocity(st, vbar, xbar, pbar)
+            return g, None, None
+
+    return StepVelocity
 
 
 def vct_batch_step(solvers, states, nsteps=1):

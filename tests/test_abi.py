@@ -90,3 +90,12 @@ def test_schedule_knobs_are_validated_on_the_host():
         rc = lib.vct_init(ctypes.byref(ctx), ctypes.byref(bathy), vct.MAP[sc.map_kind], 1.0,
                           ctypes.byref(P), sc.n, None)
         assert rc == vct.VCT_ERR_ARG and not ctx, (over, rc)
+
+
+def test_step_backward_velocity_rejects_missing_arguments_on_the_host():
+    """vct_step_backward_velocity returns VCT_ERR_ARG for a missing context or
+    state before any CUDA call."""
+    lib = vct.load_library()
+    out = (ctypes.c_double * 8)()
+    assert lib.vct_step_backward_velocity(None, None, None, None, None,
+                                          ctypes.cast(out, ctypes.c_void_p), None) == vct.VCT_ERR_ARG

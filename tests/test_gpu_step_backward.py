@@ -189,6 +189,40 @@ def test_step_backward_velocity_matches_gpu_forward(kind, dim):
         assert abs(an - fd) <= 1e-7 * scale, (an, fd, scale)
 
 
+def test_step_function_autograd():
+    """The torch.autograd.Function over a step: vel.grad of a loss on (v', x', p')
+    equals the entry's gradient and the GPU step's own directional differences;
+    the state passed in is left as it was."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    sc = _tank("SIGMA", 2, smagorinsky=1)
+    v0 = _sheared(sc)
+    s = V.Solver(sc)
+    state = _device_state(sc, v0)
+    before = {k: getattr(state, k).clone() for k in V.DeviceState.FIELDS}
+    vb, xb, pb = [torch.tensor(a, device="cuda") for a in _weights(sc, 31)]
+    F = V.step_function()
+
+    def loss(vel):
+        v1, x1, p1 = F.apply(vel, s, state)
+        return (vb * v1).sum() + (xb * x1).sum() + (pb * p1).sum()
+
+    vel = torch.tensor(v0, device="cuda", requires_grad=True)
+    loss(vel).backward()
+    for k, t in before.items():
+        assert torch.equal(getattr(state, k), t), k
+    direct, _ = s.vct_step_backward_velocity(_device_state(sc, v0), vb, xb, pb)
+    assert torch.allclose(vel.grad, direct, rtol=0, atol=1e-9 * float(direct.abs().max()))
+    fl = torch.tensor((sc.type == S.FLUID).astype(float), device="cuda")
+    dv = torch.randn(v0.shape, dtype=torch.float64, device="cuda",
+                     generator=torch.Generator(device="cuda").manual_seed(3)) * fl * 1e-5
+    with torch.no_grad():
+        fd = float(loss(vel + dv) - loss(vel - dv)) / 2.0
+    an = float((vel.grad * dv).sum())
+    print(f"PARITY step function autograd: {an:.9e} against {fd:.9e}")
+    assert abs(an - fd) <= 1e-6 * float((vel.grad * dv).abs().sum())
+
+
 def test_step_backward_velocity_rejects_terms_without_a_reverse():
     import torch
     from paper_2607_28872_b300 import vct as V
