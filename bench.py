@@ -139,6 +139,7 @@ def run_adjoint(args):
     forward call (neighbours, corrected gradient, moment solves, derivatives of
     three fields) against its adjoint (sph2_derivatives_backward, all three
     outputs carrying adjoints).  Not the headline line."""
+    import numpy as np
     import torch
     from paper_2607_28872_b300 import scenarios as S
     from paper_2607_28872_b300 import vct
@@ -191,6 +192,27 @@ def run_adjoint(args):
     step_ms = timed(lambda: s_f.vct_step(st_f, 1), ks)
     sbw_ms = timed(lambda: s_b.vct_step_backward_velocity(st_b, vb, xb), ks)
     _, sst = s_b.vct_step_backward_velocity(st_b, vb, xb)
+    # the workload's loss (squared levels at 8 gauges, the step's free-surface
+    # flags) after one step, and its gradient with respect to the starting
+    # velocities: forward step + loss against forward step + loss + position
+    # gradient + step reverse
+    gauges = np.linspace(2.0, 8.0, 8)
+    fs = s_b.vct_step_probe(st_b.clone())[0]["fs"]
+    st1 = st_b.clone()
+
+    def loss_only():
+        for k in vct.DeviceState.FIELDS:   # one step on from st_b's state
+            getattr(st1, k).copy_(getattr(st_b, k))
+        s_f.vct_step(st1, 1)
+        return s_f.vct_gauge_loss(st1, fs, gauges, grad=False)
+
+    def loss_and_grad():
+        loss_only()
+        _, _, pos_bar = s_f.vct_gauge_loss(st1, fs, gauges)
+        return s_b.vct_step_backward_velocity(st_b, None, pos_bar, None)
+
+    fwd_loss_ms = timed(loss_only, ks)
+    grad_ms = timed(loss_and_grad, ks)
     print(json.dumps({"metric": "adjoint/forward time, SPH(2) derivative operator",
                       "value": bwd / fwd, "unit": "x", "higher_is_better": False,
                       "forward_ms": fwd, "backward_ms": bwd, "calls": k, "n_gpus": 1,
@@ -204,6 +226,10 @@ def run_adjoint(args):
                       "step_velocity": {"forward_step_ms": step_ms, "backward_ms": sbw_ms,
                                         "ratio": sbw_ms / step_ms, "calls": ks,
                                         "adjoint_iters": int(sst.krylov_iters_total)},
+                      "gauge_loss_gradient": {"what": "d(gauge loss after one step)/d(starting "
+                                                      "velocities), 8 gauges",
+                                              "forward_ms": fwd_loss_ms, "gradient_ms": grad_ms,
+                                              "ratio": grad_ms / fwd_loss_ms},
                       "scope": "operator adjoint, pressure-solve adjoint and the one-step "
                                "reverse with respect to the velocities (positions held); the "
                                "reverse through the positions, chained over steps, is not "

@@ -223,6 +223,55 @@ def test_step_function_autograd():
     assert abs(an - fd) <= 1e-6 * float((vel.grad * dv).abs().sum())
 
 
+def test_gauge_loss_gradient_through_a_step():
+    """The adjoint workload's loss after one step, differentiated with respect to
+    the step's starting velocities: vct_gauge_loss's position gradient at the
+    updated state, fed to the step reverse as x_bar, against central
+    differences of oracle.gauge_loss of the oracle's step (free-surface flags
+    of the step held; a sample of 40 fluid particles)."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    sc = _tank("SIGMA", 2)
+    gauges = np.array([0.02, 0.045, 0.07, 0.1])
+    _, info = O.step(sc, probe=True)
+    fs = info["fs"].astype(np.int32)
+    fs_dev = torch.tensor(fs, device="cuda")
+    s = V.Solver(sc)
+    st0 = V.DeviceState(sc)
+    st1 = st0.clone()
+    s.vct_step(st1, 1)
+    loss, eta, pos_bar = s.vct_gauge_loss(st1, fs_dev, gauges)
+    got, _ = s.vct_step_backward_velocity(st0, None, pos_bar, None)
+    got = got.cpu().numpy()
+    assert np.abs(eta).max() > 1e-3
+
+    def oracle_loss(vel):
+        st = O.OracleState(sc)
+        st.u[:], st.w[:] = vel[0], vel[1]
+        st, inf = O.step(sc, state=st)
+        assert inf["rc"] == 0
+        return O.gauge_loss(sc, fs, gauges, st.x, None, st.z)
+
+    v0 = _base_velocity(sc)
+    assert abs(loss - oracle_loss(v0)) <= 1e-8 * loss
+    fl = np.flatnonzero(sc.type == S.FLUID)
+    fl = np.sort(np.random.default_rng(7).choice(fl, 40, replace=False))
+    h = 1e-5
+    ref = np.zeros((2, fl.size))
+    for c in range(2):
+        for k, i in enumerate(fl):
+            vp, vm = v0.copy(), v0.copy()
+            vp[c, i] += h
+            vm[c, i] -= h
+            ref[c, k] = (oracle_loss(vp) - oracle_loss(vm)) / (2 * h)
+    scale = np.abs(ref).max()
+    err = np.abs(got[:, fl] - ref).max() / scale
+    print(f"PARITY gauge loss through a step, d loss / d v: max err {err:.2e} of max |grad| "
+          f"{scale:.3e}")
+    assert scale > 0.0
+    assert err < 1e-5, err
+
+
 def test_step_backward_velocity_rejects_terms_without_a_reverse():
     import torch
     from paper_2607_28872_b300 import vct as V
