@@ -532,7 +532,8 @@ def stage_bytes(stage, n, nf, dim, rows, nnz, nbr_row):
     if stage == "pass1":   # reads pos^, pos, vel, type, J, jbar, nbr list; writes L, gv, Ct, rho, lam, fs, nu
         return nf * (8 * (3 * d + 3) + 4 + 4 * nbr_row + 8 * (2 * d * d + d * m + 3) + 4)
     if stage == "pass2":   # reads L, Ct, gv, nu, pos^, vel, metric; writes acc, v*, coefficients
-        return nf * (8 * (2 * d * d + d * m + 1 + 2 * d + 4) + 4 * nbr_row + 8 * 2 * d
+        # (diagonal, wall right side and its d coefficients, counts)
+        return nf * (8 * (2 * d * d + d * m + 1 + 2 * d + 4) + 4 * nbr_row + 8 * 3 * d
                      + 12 * (nnz / max(rows, 1)) + 8 * 3 + 4)
     return 0
 
