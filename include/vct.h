@@ -495,9 +495,11 @@ vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct
  * iteration count and residual), the right side's and the wall terms'
  * adjoints, the SPH(2) derivative operator's adjoint for the viscous term, and
  * with free-slip walls (Sec. 3.5) the adjoint of the wall particles' reflected
- * Shepard velocities.  FP64 arithmetic in the reverse; the operators in the
- * context's precision.  VCT_ERR_ARG with regularisation or the ISPH operator
- * set (terms whose reverse is not built), or v_bar_in NULL.
+ * Shepard velocities; under the ISPH operator set (vct_params.operators = 1)
+ * the adjoints of its summation pressure gradient and 0th-order second
+ * derivatives.  FP64 arithmetic in the reverse; the operators in the context's
+ * precision.  VCT_ERR_ARG with regularisation (it acts on the updated
+ * positions; its reverse is not built), or v_bar_in NULL.
  * Allocates (7 dim + 3 dim^2 + 3) doubles per particle of capacity on the
  * first call; afterwards the context holds this step's pressure system (as
  * after vct_step, for vct_ppe_adjoint). */

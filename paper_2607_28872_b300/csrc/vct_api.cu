@@ -1418,9 +1418,9 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
     vct_status v = check_state(c, s);
     if (v) return v;
     if (!v_bar_in) return VCT_ERR_ARG;
-    // terms of the step that are not in the reverse: the regularisation (shifts
-    // that scale with the speed) and the ISPH operator set
-    if (c->P.operators != 0 || regularise_on(c->P)) return VCT_ERR_ARG;
+    // the one term of the step that is not in the reverse: the regularisation
+    // (it moves the updated positions; shifts that scale with the speed)
+    if (regularise_on(c->P)) return VCT_ERR_ARG;
     const int64_t n = s->n;
     const int d = c->P.dim;
     if (!c->W.sadj) {
@@ -1454,7 +1454,8 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
     // the eddy viscosity's share reaches the velocities through the corrected
     // gradient: the SPH(2) adjoint takes it as the gradient's adjoint
     const double *gb = c->P.smag ? c->W.sadj_co + (2 + 3 * d) * n : nullptr;
-    launch_sph2_adjoint(c->P, cur(c), c->W, n, d, gb, nullptr, lb, v_bar_in, c->st);
+    if (c->P.operators == 1) launch_isph_adjoint(c->P, cur(c), c->W, n, d, gb, lb, v_bar_in, c->st);
+    else launch_sph2_adjoint(c->P, cur(c), c->W, n, d, gb, nullptr, lb, v_bar_in, c->st);
     launch_stepadj_c(c->P, cur(c), c->W, n, v_bar_in, c->st);
     c->launches += 2 + (c->P.smag ? 2 : 0) + 2 * d + 1 + (c->P.slip ? 1 : 0);
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;

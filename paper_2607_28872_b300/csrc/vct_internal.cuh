@@ -254,6 +254,10 @@ void launch_stepadj_a(const DevParams &P, Part cur, Work W, int64_t n, const dou
 void launch_stepadj_b(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 void launch_stepadj_c(const DevParams &P, Part cur, Work W, int64_t n, double *v_bar_in,
                       cudaStream_t st);
+// adjoint of the ISPH operator set's gradient and Laplacian (the step reverse's
+// viscous term under that set); arrays as launch_sph2_adjoint's
+void launch_isph_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
+                         const double *gbar, const double *lapbar, double *phibar, cudaStream_t st);
 int launch_krylov_fly_batch(int precision, int dim, const FlyJob *jobs, int njobs, unsigned nblocks,
                             size_t smem, bool expl, cudaStream_t st);
 int krylov_mg_coop_blocks(int precision, int dim, size_t smem, bool fly);

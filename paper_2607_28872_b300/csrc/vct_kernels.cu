@@ -4719,6 +4719,114 @@ void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int nc
     }
 }
 
+// Adjoint of the ISPH operator set's derivatives (Table tab:case_names, Eq. sec_0th)
+// for the step's reverse: g_i = L_i sum_j V_j phi_ij grad w_ij and the 0th-order
+// second derivatives D_a = sum_j V_j k_a(r_ij) phi_ij (none on an isolated
+// particle), lap_i = c0 g_i,z + c~ . D_i.  Pass 1 forms per fluid particle
+// bbar_a = lapbar c~_a (0 when isolated) and gbar' = gbar + c0 lapbar e_z (rows [0, m)
+// and [m, m + d) of W.adj); each pair (i, j) carries w_ij = V_j [bbar_i . k(r_ij) +
+// (L_i grad w_ij) . gbar'_i], gathered as for the SPH(2) operator.  FP64.
+template <int D>
+__global__ void __launch_bounds__(128) k_isph_adj1(DevParams P, const Part c, Work W, int n,
+                                                   const double *gbar, const double *lapbar,
+                                                   int comp)
+{
+    constexpr int M = D == 2 ? 3 : 6;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    if (c.type[i] != FLUID) {
+        for (int a = 0; a < M + D; ++a) W.adj[(int64_t)a * cap + i] = 0.0;
+        return;
+    }
+    const int o = c.orig[i];
+    const double lb = lapbar ? lapbar[(int64_t)comp * n + o] : 0.0;
+    double ct[M];
+    ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
+    const double ds = W.fs[i] == 2 ? 0.0 : 1.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) W.adj[(int64_t)a * cap + i] = ds * ct[a] * lb;
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double gb = gbar ? gbar[((int64_t)comp * D + K) * n + o] : 0.0;
+        if (K == D - 1) gb += c.c0[i] * lb;
+        W.adj[(int64_t)(M + K) * cap + i] = gb;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ double adj_pair_isph(const DevParams &P, const Part &c, const Work &W,
+                                                int i, int j, const double *xi, const double *xj)
+{
+    constexpr int M = D == 2 ? 3 : 6;
+    const int64_t cap = W.cap;
+    double r[D], rr2 = 0.0;
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        r[K] = xj[K] - xi[K];
+        rr2 += r[K] * r[K];
+    }
+    if (rr2 == 0.0) return 0.0;
+    double rr = sqrt(rr2), w, dw;
+    kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+    const double fac = -dw / rr;
+    double kw[M], s = 0.0;
+    er_weights<D, double>(r, rr2, fac, kw);
+#pragma unroll
+    for (int a = 0; a < M; ++a) s += W.adj[(int64_t)a * cap + i] * kw[a];
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        double gt = 0.0;
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) gt += W.L[(int64_t)(K * D + L2) * cap + i] * fac * r[L2];
+        s += gt * W.adj[(int64_t)(M + K) * cap + i];
+    }
+    return W.vol[j] * s;
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_isph_adj2(DevParams P, const Part c, Work W, int n,
+                                                   double *phibar, int comp)
+{
+    const int jdx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jdx >= n) return;
+    const int o = c.orig[jdx];
+    const int tj = c.type[jdx];
+    if (tj == VIRTUAL) {
+        phibar[(int64_t)comp * n + o] = 0.0;
+        return;
+    }
+    const int64_t cap = W.cap;
+    double xj[3], s = 0.0;
+    load_hat<D>(c, jdx, xj);
+    const int cnt = W.nbr_cnt[jdx];
+    for (int k = 0; k < cnt; ++k) {
+        const int i = W.nbr[(int64_t)k * cap + jdx];
+        const int ti = c.type[i];
+        if (ti == VIRTUAL) continue;
+        double xi[3];
+        load_hat<D>(c, i, xi);
+        if (ti == FLUID) s += adj_pair_isph<D>(P, c, W, i, jdx, xi, xj);    // incoming w_ij
+        if (tj == FLUID) s -= adj_pair_isph<D>(P, c, W, jdx, i, xj, xi);    // outgoing w_ji
+    }
+    phibar[(int64_t)comp * n + o] = s;
+}
+
+void launch_isph_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
+                         const double *gbar, const double *lapbar, double *phibar, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    for (int comp = 0; comp < ncomp; ++comp) {
+        if (P.dim == 2) {
+            k_isph_adj1<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, gbar, lapbar, comp);
+            k_isph_adj2<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, phibar, comp);
+        } else {
+            k_isph_adj1<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, gbar, lapbar, comp);
+            k_isph_adj2<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, phibar, comp);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a12 (map part): derivative of the per-particle metric with respect to the
 // bathymetry parameters theta = [h0, slope_x, slope_y, cos_amp, cos_len,
@@ -5539,9 +5647,10 @@ __device__ __forceinline__ double pair_fac(const DevParams &P, const double *r)
     return -dw / rr;
 }
 
-// Corrector: u, a_i = L_i^T J^T (-dt/rho u_i), v*_bar = u, f_bar from the wall pairs
-// p_ij = rho (r_j - r_i)_phys . f_i.
-template <int D>
+// Corrector: u, a_i = L_i^T J^T (-dt/rho u_i) (SUM, the ISPH summation gradient
+// sum_j V_j (p_ij + 2 p_i) grad w_ij: J^T (-dt/rho u_i), no L), v*_bar = u, f_bar from
+// the wall pairs p_ij = rho (r_j - r_i)_phys . f_i.
+template <int D, bool SUM>
 __global__ void __launch_bounds__(128) k_stepadj_corr(DevParams P, const Part c, Work W, int n,
                                                       const double *v_bar, const double *x_bar)
 {
@@ -5568,7 +5677,7 @@ __global__ void __launch_bounds__(128) k_stepadj_corr(DevParams P, const Part c,
         double s = 0.0;
 #pragma unroll
         for (int L2 = 0; L2 < D; ++L2) s += W.L[(int64_t)(L2 * D + K) * cap + i] * gh[L2];
-        a[K] = s;
+        a[K] = SUM ? gh[K] : s;
     }
     double xi[3], pi_[3], fb[D];
     load_hat<D>(c, i, xi);
@@ -5601,8 +5710,10 @@ __global__ void __launch_bounds__(128) k_stepadj_corr(DevParams P, const Part c,
 }
 
 // p_bar_k = p_bar_in + sum_{i fluid in S_k} [V_k fac (r_ik . a_i) + V_i fac (r_ik . a_k)]
-// on unknown rows (r_ik = x^_k - x^_i), 0 elsewhere; caller order.
-template <int D>
+// on unknown rows (r_ik = x^_k - x^_i), 0 elsewhere; caller order.  SUM: the summation
+// gradient's 2 p_k sum_j V_j grad w_kj adds -2 V_j fac (r_jk . a_k) over every fluid and
+// wall neighbour j.
+template <int D, bool SUM>
 __global__ void __launch_bounds__(128) k_stepadj_pbar(DevParams P, const Part c, Work W, int n,
                                                       const double *p_bar)
 {
@@ -5624,7 +5735,8 @@ __global__ void __launch_bounds__(128) k_stepadj_pbar(DevParams P, const Part c,
     const int cnt = W.nbr_cnt[k];
     for (int q = 0; q < cnt; ++q) {
         const int i = W.nbr[(int64_t)q * cap + k];
-        if (c.type[i] != FLUID) continue;
+        const int ti = c.type[i];
+        if (ti == VIRTUAL || (!SUM && ti != FLUID)) continue;
         double xi[3], r[D], rai = 0.0, rak = 0.0;
         load_hat<D>(c, i, xi);
 #pragma unroll
@@ -5633,7 +5745,9 @@ __global__ void __launch_bounds__(128) k_stepadj_pbar(DevParams P, const Part c,
             rai += r[K] * W.sadj[(int64_t)K * cap + i];
             rak += r[K] * ak[K];
         }
-        s += pair_fac<D>(P, r) * (Vk * rai + W.vol[i] * rak);
+        const double fac = pair_fac<D>(P, r), Vi = W.vol[i];
+        if (ti == FLUID) s += fac * (Vk * rai + Vi * rak);
+        if (SUM) s -= 2.0 * fac * Vi * rak;
     }
     pb[o] = s;
 }
@@ -6048,13 +6162,24 @@ void launch_stepadj_a(const DevParams &P, Part cur, Work W, int64_t n, const dou
 {
     const unsigned g = (unsigned)((n + 127) / 128);
     const int D = P.dim;
+    const bool sum = P.operators == 1;
     if (D == 2) {
-        k_stepadj_corr<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
-        k_stepadj_pbar<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        if (sum) {
+            k_stepadj_corr<2, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+            k_stepadj_pbar<2, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        } else {
+            k_stepadj_corr<2, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+            k_stepadj_pbar<2, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        }
         if (P.smag) k_stepadj_vcopy<2><<<g, 128, 0, st>>>(cur, W, (int)n);
     } else {
-        k_stepadj_corr<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
-        k_stepadj_pbar<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        if (sum) {
+            k_stepadj_corr<3, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+            k_stepadj_pbar<3, true><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        } else {
+            k_stepadj_corr<3, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+            k_stepadj_pbar<3, false><<<g, 128, 0, st>>>(P, cur, W, (int)n, p_bar);
+        }
         if (P.smag) k_stepadj_vcopy<3><<<g, 128, 0, st>>>(cur, W, (int)n);
     }
     if (P.smag)   // the forward viscous term's Laplacian, for nu_bar

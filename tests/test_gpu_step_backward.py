@@ -57,17 +57,20 @@ def _base_velocity(sc):
 @pytest.mark.parametrize("kind,dim,precision,slip,tol",
                          [("SIGMA", 2, 0, 0, 1e-9), ("BF", 2, 0, 0, 1e-9), ("E", 2, 0, 0, 1e-9),
                           ("BF", 3, 0, 0, 1e-9), ("BFE", 3, 0, 0, 1e-9), ("SIGMA", 2, 1, 0, 1e-5),
-                          ("SIGMA", 2, 0, 1, 1e-9), ("BF", 3, 0, 1, 1e-9)],
+                          ("SIGMA", 2, 0, 1, 1e-9), ("BF", 3, 0, 1, 1e-9),
+                          ("SIGMA", 2, 0, 2, 1e-9), ("BF", 3, 0, 2, 1e-9)],
                          ids=["sigma-2d", "bf-2d", "e-2d", "bf-3d", "bfe-3d", "sigma-2d-mixed",
-                              "sigma-2d-slip", "bf-3d-slip"])
+                              "sigma-2d-slip", "bf-3d-slip", "sigma-2d-isph", "bf-3d-isph"])
 def test_step_backward_velocity_matches_oracle(kind, dim, precision, slip, tol):
     """Every fluid velocity component's gradient against the oracle's exact
     one-sided difference (the loss is affine in the velocities, free-slip wall
     velocities included).  FP64: to the solves' tolerance; mixed: the
-    operators' FP32 sums bound it."""
+    operators' FP32 sums bound it.  slip 2: no-slip walls under the ISPH
+    operator set instead."""
     import torch
     from paper_2607_28872_b300 import vct as V
-    sc = _tank(kind, dim, precision, wall_slip=slip)
+    extra = dict(operators=1) if slip == 2 else dict(wall_slip=slip)
+    sc = _tank(kind, dim, precision, **extra)
     vb, xb, pb = _weights(sc, 11)
     s = V.Solver(sc)
     got, st = s.vct_step_backward_velocity(V.DeviceState(sc), torch.tensor(vb), torch.tensor(xb),
@@ -115,15 +118,16 @@ def _device_state(sc, vel):
     return st
 
 
-@pytest.mark.parametrize("kind,dim,slip", [("SIGMA", 2, 0), ("BF", 2, 1), ("BF", 3, 0)],
-                         ids=["sigma-2d", "bf-2d-slip", "bf-3d"])
-def test_step_backward_velocity_eddy_viscosity_matches_oracle(kind, dim, slip):
+@pytest.mark.parametrize("kind,dim,slip,ops", [("SIGMA", 2, 0, 0), ("BF", 2, 1, 0), ("BF", 3, 0, 0),
+                                              ("SIGMA", 2, 0, 1)],
+                         ids=["sigma-2d", "bf-2d-slip", "bf-3d", "sigma-2d-isph"])
+def test_step_backward_velocity_eddy_viscosity_matches_oracle(kind, dim, slip, ops):
     """With the Smagorinsky model the step is not affine in the velocities: the
     GPU gradient at a sheared flow against the oracle's central differences,
     component by component (a sample of 40 particles in 3-D)."""
     import torch
     from paper_2607_28872_b300 import vct as V
-    sc = _tank(kind, dim, wall_slip=slip, smagorinsky=1)
+    sc = _tank(kind, dim, wall_slip=slip, smagorinsky=1, operators=ops)
     vb, xb, pb = _weights(sc, 21)
     v0 = _sheared(sc)
     s = V.Solver(sc)
@@ -144,11 +148,11 @@ def test_step_backward_velocity_eddy_viscosity_matches_oracle(kind, dim, slip):
     scale = np.abs(ref).max()
     err = np.abs(got[:, fl] - ref).max() / scale
     # the eddy viscosity's share, for scale: the same gradient with the model off
-    s0 = V.Solver(_tank(kind, dim, wall_slip=slip))
+    s0 = V.Solver(_tank(kind, dim, wall_slip=slip, operators=ops))
     g0, _ = s0.vct_step_backward_velocity(_device_state(sc, v0), torch.tensor(vb), torch.tensor(xb),
                                           torch.tensor(pb))
     share = np.abs(got - g0.cpu().numpy()).max() / scale
-    print(f"PARITY step backward velocity, eddy viscosity, {kind} {dim}-D slip {slip}: max err "
+    print(f"PARITY step backward velocity, eddy viscosity, {kind} {dim}-D slip {slip} ops {ops}: max err "
           f"{err:.2e} of max |grad| {scale:.3e}; the model's share of the gradient {share:.2e}")
     assert err < 1e-6, err
     assert share > 100 * err
@@ -275,8 +279,7 @@ def test_gauge_loss_gradient_through_a_step():
 def test_step_backward_velocity_rejects_terms_without_a_reverse():
     import torch
     from paper_2607_28872_b300 import vct as V
-    for over in (dict(operators=1),
-                 dict(S.REGULARISATION)):
+    for over in (dict(S.REGULARISATION),):
         sc = S.small_tank(dim=2, kind="BF", L=0.12, H=0.06, d0=0.01, seed=3, **over)
         s = V.Solver(sc)
         with pytest.raises(V.VCTError):
