@@ -497,11 +497,19 @@ vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct
  * with free-slip walls (Sec. 3.5) the adjoint of the wall particles' reflected
  * Shepard velocities; under the ISPH operator set (vct_params.operators = 1)
  * the adjoints of its summation pressure gradient and 0th-order second
- * derivatives.  FP64 arithmetic in the reverse; the operators in the context's
- * precision.  VCT_ERR_ARG with regularisation (it acts on the updated
- * positions; its reverse is not built), or v_bar_in NULL.
+ * derivatives; with the particle regularisation on (Sec. 4.1: dynamic
+ * stabilization, XSPH, optimized shifting, all acting on the corrector's
+ * positions x' and velocities u'), its reverse first: the call then runs the
+ * step forward up to and through the regularisation (solve, corrector), takes
+ * the regularisation's reverse at x', u' (its pair terms' position derivatives
+ * through w' and w'', the metric at x' through duals), and clears the context's
+ * pressure history (as vct_reset_history), which that forward run wrote.  The
+ * dynamic stabilization switches on below a pair distance and the shift
+ * scales with |v|: the gradient is that of the branch the step took.  FP64
+ * arithmetic in the reverse; the operators in the context's precision.
+ * VCT_ERR_ARG if v_bar_in is NULL.
  * Allocates (7 dim + 3 dim^2 + 3) doubles per particle of capacity on the
- * first call; afterwards the context holds this step's pressure system (as
+ * first call (with the regularisation on, (10 dim + dim^2 + 3) more); afterwards the context holds this step's pressure system (as
  * after vct_step, for vct_ppe_adjoint). */
 vct_status vct_step_backward_velocity(vct_ctx *ctx, const vct_state *state, const double *v_bar,
                                       const double *x_bar, const double *p_bar, double *v_bar_in,

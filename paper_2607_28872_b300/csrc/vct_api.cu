@@ -1418,11 +1418,9 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
     vct_status v = check_state(c, s);
     if (v) return v;
     if (!v_bar_in) return VCT_ERR_ARG;
-    // the one term of the step that is not in the reverse: the regularisation
-    // (it moves the updated positions; shifts that scale with the speed)
-    if (regularise_on(c->P)) return VCT_ERR_ARG;
     const int64_t n = s->n;
     const int d = c->P.dim;
+    const bool reg = regularise_on(c->P);
     if (!c->W.sadj) {
         cudaError_t e = cudaSuccess;
         c->W.sadj = dalloc<double>(c, c->cap * (4 * d + 2 * d * d + 1), e);
@@ -1431,6 +1429,36 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
             c->W.sadj = c->W.sadj_co = nullptr;
             return VCT_ERR_CUDA;
         }
+    }
+    if (reg && !c->W.radj) {
+        cudaError_t e = cudaSuccess;
+        c->W.radj = dalloc<double>(c, c->cap * (regadj_rows(d) + 2 * d), e);
+        if (e != cudaSuccess) {
+            c->W.radj = nullptr;
+            return VCT_ERR_CUDA;
+        }
+    }
+    if (reg) {
+        // The regularisation acts last, on the corrector's x' and u': run the
+        // step forward up to it, take its reverse first (into u'_bar, x'_bar),
+        // then the rest of the step's reverse from there.
+        double *vb_co = c->W.radj + (int64_t)regadj_rows(d) * c->cap, *xb_co = vb_co + d * n;
+        reset_status(c);
+        launch_load(c->P, cur(c), *s, n, c->st);
+        step_pre(c, n);
+        if (step_solve(c, n, 0)) return VCT_ERR_CUDA;
+        launch_corrector(c->P, cur(c), c->W, n, c->st);
+        launch_regadj_save(c->P, cur(c), c->W, n, c->st);
+        c->launches += 3 + launch_regularise(c->P, cur(c), c->W, n, c->st);
+        launch_regadj(c->P, cur(c), c->W, n, v_bar, x_bar, vb_co, xb_co, c->st);
+        c->launches += 4;
+        if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+        v = finish(c, nullptr, 0);
+        if (v) return v;
+        // the corrector wrote the pressure history of the context: clear it
+        if (vct_reset_history(c) != VCT_OK) return VCT_ERR_CUDA;
+        v_bar = vb_co;
+        x_bar = xb_co;
     }
     reset_status(c);
     launch_load(c->P, cur(c), *s, n, c->st);

@@ -107,6 +107,8 @@ struct Work {
     double *adj;              // adjoint scratch: [m + dim] per particle
     double *sadj;             // step reverse, cell order: [3 dim + dim^2] per particle (allocated on first use)
     double *sadj_co;          // step reverse, caller order: [dim + 2] per particle
+    double *radj;             // regularisation reverse, cell order (rows: regadj_rows) + caller-order
+                              // u'_bar, x'_bar [2 dim] (allocated on first use)
     double *rxh, *rmet;       // regularisation: projected position [d] and J, s_x, s_y
     double *rud, *rdh;        //   at the updated positions; corrected velocity [d],
                               //   projected displacement [d]
@@ -254,6 +256,14 @@ void launch_stepadj_a(const DevParams &P, Part cur, Work W, int64_t n, const dou
 void launch_stepadj_b(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
 void launch_stepadj_c(const DevParams &P, Part cur, Work W, int64_t n, double *v_bar_in,
                       cudaStream_t st);
+// reverse of the particle regularisation for the step's reverse: the rows of
+// W.radj per particle, x' saved before the forward regularisation runs, and the
+// reverse itself from the step outputs' adjoints (v_bar, x_bar, caller order) to
+// u'_bar and x'_bar (caller order) at the corrector's output
+int regadj_rows(int dim);
+void launch_regadj_save(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st);
+void launch_regadj(const DevParams &P, Part cur, Work W, int64_t n, const double *v_bar,
+                   const double *x_bar, double *vb_co, double *xb_co, cudaStream_t st);
 // adjoint of the ISPH operator set's gradient and Laplacian (the step reverse's
 // viscous term under that set); arrays as launch_sph2_adjoint's
 void launch_isph_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,

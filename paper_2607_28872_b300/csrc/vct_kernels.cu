@@ -143,6 +143,15 @@ __device__ __forceinline__ void kern_wdw(R r, R inv_l, R ad, R &w, R &dw)
     }
 }
 
+// Second derivative w'' of the cubic spline (FP64).
+__device__ __forceinline__ double kern_w2(double r, double inv_l, double ad)
+{
+    const double q = r * inv_l;
+    if (q < 1.0) return ad * (-3.0 + 4.5 * q) * inv_l * inv_l;
+    if (q < 2.0) return ad * 1.5 * (2.0 - q) * inv_l * inv_l;
+    return 0.0;
+}
+
 template <int D>
 __device__ __forceinline__ void load_hat(const Part &c, int i, double *x)
 {
@@ -6220,6 +6229,485 @@ void launch_stepadj_c(const DevParams &P, Part cur, Work W, int64_t n, double *v
     }
 }
 
+// ---------------------------------------------------------------------------
+// a12 (part): reverse of the particle regularisation (Sec. 4.1: dynamic
+// stabilization, XSPH on free-surface particles, optimized shifting) at the
+// positions x' and velocities u' the corrector left, for the step's reverse.
+// Forward, per fluid particle i, with e_ij = r^'_j - r^'_i over the step's
+// neighbour lists and free-surface flags:
+//   du_i = -sum_j f_j (d_s - r)/(dt r) e_ij  (r < d_s = (1 - overlap) d0; f_j = 1/2 on fluid j)
+//   ud_i = u'_i + T_i du_i,   dh_i = dt du_i        (T_i: projected to physical at x')
+//   un_i = ud_i + eps sum_fluid j V0 (ud_j - ud_i) w_ij          (free-surface i only)
+//   gc_i = sum_j V0 (w'/r)(-e_ij),  B_i = -sum_j V0 (w'/r) e_ij e_ij^T
+//   s_i  = -K |v^_i| gc_i (K = shift l dt; v^ = the projected un), minus its part along
+//          n_i = normalize(-B_i^-1 gc_i) on free-surface i
+//   x''_i = x'_i + T_i (dh_i + s_i),   u''_i = un_i
+// Its adjoint runs backwards through these lines: k_regadj_seed forms each
+// particle's seeds (s's, v^'s and T's adjoints), k_regadj_vel the velocity
+// adjoints (XSPH's transpose as a gather, du's), k_regadj_pos the pair terms'
+// position adjoint (gathered from both ends of every pair, w' and w'' of the
+// kernel) and k_regadj_out maps it to physical positions through the metric at
+// x' (duals) and writes u'_bar and x'_bar (caller order) for the step's reverse.
+// W.radj rows (cell order): gc_bar [0, d), B_bar [d, d + d^2), un_bar, h_bar
+// (the projected displacement's adjoint), the metric's (J, s_x, s_y), x''_bar,
+// du_bar, u'_bar, r^'_bar, x' (d rows each but the metric's 3).
+// ---------------------------------------------------------------------------
+template <int D>
+struct RegRows {
+    static constexpr int GC = 0, B = D, UN = D + D * D, H = 2 * D + D * D, M = 3 * D + D * D,
+                         XD = M + 3, DU = XD + D, UP = DU + D, XH = UP + D, XP = XH + D,
+                         N = XP + D;
+};
+
+// y = T^T x for T the projected-to-physical map of reg_to_phys; tb += the adjoint of
+// T's entries (J, s_x, s_y) for the forward input dh and output dp.
+template <int D>
+__device__ __forceinline__ void reg_to_phys_t(double J, double sx, double sy, const double *dh,
+                                              const double *xb, double *y, double *mb)
+{
+    if (D == 2) {
+        const double dp1 = (dh[1] - sx * dh[0]) / J;
+        y[0] = xb[0] - sx * xb[1] / J;
+        y[1] = xb[1] / J;
+        mb[0] += -xb[1] * dp1 / J;
+        mb[1] += -xb[1] * dh[0] / J;
+    } else {
+        const double dp2 = (dh[2] - sx * dh[0] - sy * dh[1]) / J;
+        y[0] = xb[0] - sx * xb[2] / J;
+        y[1] = xb[1] - sy * xb[2] / J;
+        y[2] = xb[2] / J;
+        mb[0] += -xb[2] * dp2 / J;
+        mb[1] += -xb[2] * dh[0] / J;
+        mb[2] += -xb[2] * dh[1] / J;
+    }
+}
+
+// x' (physical) before the regularisation moves it.
+template <int D>
+__global__ void k_regadj_save(const Part c, Work W, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    using RR = RegRows<D>;
+    double x[3];
+    load_phys<D>(c, i, x);
+#pragma unroll
+    for (int K = 0; K < D; ++K) W.radj[(int64_t)(RR::XP + K) * W.cap + i] = x[K];
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_regadj_seed(DevParams P, const Part c, Work W, int n,
+                                                     const double *v_bar, const double *x_bar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    using RR = RegRows<D>;
+    const int64_t cap = W.cap;
+    double *R = W.radj;
+    if (c.type[i] != FLUID) {
+        for (int q = 0; q < RR::XP; ++q) R[(int64_t)q * cap + i] = 0.0;
+        return;
+    }
+    const int o = c.orig[i];
+    const double J = W.rmet[i], sx = W.rmet[cap + i], sy = W.rmet[2 * cap + i];
+    double xb[D], ub[D], un[D], rdh[D];
+    load_vel<D>(c, i, un);   // the regularised velocity (the step's output)
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        xb[K] = x_bar ? x_bar[(int64_t)K * n + o] : 0.0;
+        ub[K] = v_bar ? v_bar[(int64_t)K * n + o] : 0.0;
+        rdh[K] = W.rdh[K * cap + i];
+    }
+    // forward shift (gc, B, s) at x'
+    const bool fsi = W.fs[i] != 0, do_s = P.ops_shift > 0.0;
+    double gc[D], B[D * D], s[D], sraw[D], nv[D], nn = 0.0, Df = 0.0, sp = 0.0, vh[D];
+    bool proj = false;
+#pragma unroll
+    for (int K = 0; K < D; ++K) gc[K] = s[K] = sraw[K] = nv[K] = 0.0;
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) B[q] = 0.0;
+    if (do_s) {
+        double xi[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) xi[K] = W.rxh[K * cap + i];
+        const int cnt = W.nbr_cnt[i];
+        for (int k = 0; k < cnt; ++k) {
+            const int j = W.nbr[(int64_t)k * cap + i];
+            double r[D], r2 = 0.0;
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                r[K] = xi[K] - W.rxh[K * cap + j];
+                r2 += r[K] * r[K];
+            }
+            const double rr = sqrt(r2);
+            if (rr == 0.0) continue;
+            double w, dw;
+            kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+            const double dwr = dw / rr;
+#pragma unroll
+            for (int K = 0; K < D; ++K) gc[K] += P.V0 * dwr * r[K];
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) B[a * D + b] -= P.V0 * dwr * r[a] * r[b];
+        }
+        vh[0] = un[0];
+        if (D == 2) {
+            vh[1] = sx * un[0] + J * un[1];
+        } else {
+            vh[1] = un[1];
+            vh[2] = sx * un[0] + sy * un[1] + J * un[2];
+        }
+#pragma unroll
+        for (int K = 0; K < D; ++K) sp += vh[K] * vh[K];
+        Df = P.ops_shift * P.l * sqrt(sp) * P.dt;
+#pragma unroll
+        for (int K = 0; K < D; ++K) s[K] = sraw[K] = -Df * gc[K];
+        if (fsi) {
+            double Bc[D * D], Li[D * D];
+#pragma unroll
+            for (int q = 0; q < D * D; ++q) Bc[q] = B[q];
+            const bool ok = reg_invert<D>(Bc, Li);
+            if (ok) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+#pragma unroll
+                    for (int b = 0; b < D; ++b) nv[a] -= Li[a * D + b] * gc[b];
+                    nn += nv[a] * nv[a];
+                }
+            }
+            if (!ok || !(nn > 0.0)) {
+#pragma unroll
+                for (int K = 0; K < D; ++K) s[K] = 0.0;
+            } else {
+                proj = true;
+                nn = sqrt(nn);
+                double sn = 0.0;
+#pragma unroll
+                for (int K = 0; K < D; ++K) sn += s[K] * nv[K] / nn;
+#pragma unroll
+                for (int K = 0; K < D; ++K) s[K] -= sn * nv[K] / nn;
+            }
+        }
+    }
+    // x'' = x' + T (dh + s)
+    double dht[D], hb[D], mb[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int K = 0; K < D; ++K) dht[K] = rdh[K] + s[K];
+    reg_to_phys_t<D>(J, sx, sy, dht, xb, hb, mb);
+    double gcb[D], Bb[D * D], unb[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        gcb[K] = 0.0;
+        unb[K] = ub[K];
+    }
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) Bb[q] = 0.0;
+    if (do_s && !(fsi && !proj)) {
+        double srb[D];
+        if (proj) {
+            double n1[D], hn = 0.0, sn = 0.0, nb[D], nbn = 0.0;
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                n1[K] = nv[K] / nn;
+                hn += hb[K] * n1[K];
+                sn += sraw[K] * n1[K];
+            }
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                srb[K] = hb[K] - hn * n1[K];
+                nb[K] = -sn * hb[K] - hn * sraw[K];
+                nbn += nb[K] * n1[K];
+            }
+            // n = nv / |nv|, nv = -B^-1 gc: nv_bar = (nb - (nb . n) n) / |nv|, y = B^-T nv_bar
+            double nvb[D], Bt[D * D], Lt[D * D];
+#pragma unroll
+            for (int K = 0; K < D; ++K) nvb[K] = (nb[K] - nbn * n1[K]) / nn;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) Bt[a * D + b] = B[b * D + a];
+            if (reg_invert<D>(Bt, Lt)) {
+                double y[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    y[a] = 0.0;
+#pragma unroll
+                    for (int b = 0; b < D; ++b) y[a] += Lt[a * D + b] * nvb[b];
+                }
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    gcb[a] -= y[a];
+#pragma unroll
+                    for (int b = 0; b < D; ++b) Bb[a * D + b] -= y[a] * nv[b];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int K = 0; K < D; ++K) srb[K] = hb[K];
+        }
+        // s_raw = -Df gc, Df = K |v^|
+        double Dfb = 0.0;
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            Dfb -= srb[K] * gc[K];
+            gcb[K] -= Df * srb[K];
+        }
+        if (sp > 0.0) {
+            const double kf = Dfb * P.ops_shift * P.l * P.dt / sqrt(sp);
+            double vb[D];
+#pragma unroll
+            for (int K = 0; K < D; ++K) vb[K] = kf * vh[K];
+            if (D == 2) {
+                unb[0] += vb[0] + sx * vb[1];
+                unb[1] += J * vb[1];
+                mb[0] += un[1] * vb[1];
+                mb[1] += un[0] * vb[1];
+            } else {
+                unb[0] += vb[0] + sx * vb[2];
+                unb[1] += vb[1] + sy * vb[2];
+                unb[2] += J * vb[2];
+                mb[0] += un[2] * vb[2];
+                mb[1] += un[0] * vb[2];
+                mb[2] += un[1] * vb[2];
+            }
+        }
+    }
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        R[(int64_t)(RR::GC + K) * cap + i] = gcb[K];
+        R[(int64_t)(RR::UN + K) * cap + i] = unb[K];
+        R[(int64_t)(RR::H + K) * cap + i] = hb[K];
+        R[(int64_t)(RR::XD + K) * cap + i] = xb[K];
+    }
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) R[(int64_t)(RR::B + q) * cap + i] = Bb[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) R[(int64_t)(RR::M + q) * cap + i] = mb[q];
+}
+
+// Velocity adjoints: ud_bar (XSPH's transpose gathered from free-surface fluid
+// neighbours), then u'_bar = ud_bar and du_bar = T^T ud_bar + dt h_bar.
+template <int D>
+__global__ void __launch_bounds__(128) k_regadj_vel(DevParams P, const Part c, Work W, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || c.type[k] != FLUID) return;
+    using RR = RegRows<D>;
+    const int64_t cap = W.cap;
+    double *R = W.radj;
+    const bool do_x = P.xsph_eps > 0.0;
+    double udb[D], xk[D], wsum = 0.0;
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        udb[K] = 0.0;
+        xk[K] = W.rxh[K * cap + k];
+    }
+    if (do_x) {
+        const int cnt = W.nbr_cnt[k];
+        for (int q = 0; q < cnt; ++q) {
+            const int j = W.nbr[(int64_t)q * cap + k];
+            if (c.type[j] != FLUID) continue;
+            double r2 = 0.0;
+#pragma unroll
+            for (int K = 0; K < D; ++K) {
+                const double dr = xk[K] - W.rxh[K * cap + j];
+                r2 += dr * dr;
+            }
+            const double rr = sqrt(r2);
+            if (rr == 0.0) continue;
+            double w, dw;
+            kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+            wsum += P.V0 * w;
+            if (W.fs[j] != 0) {   // j's XSPH reads ud_k
+#pragma unroll
+                for (int K = 0; K < D; ++K) udb[K] += P.xsph_eps * P.V0 * w * R[(int64_t)(RR::UN + K) * cap + j];
+            }
+        }
+    }
+    const double own = (do_x && W.fs[k] != 0) ? 1.0 - P.xsph_eps * wsum : 1.0;
+#pragma unroll
+    for (int K = 0; K < D; ++K) udb[K] += own * R[(int64_t)(RR::UN + K) * cap + k];
+    // ud = u' + T du (dynamic stabilization), dh = dt du
+    const double J = W.rmet[k], sx = W.rmet[cap + k], sy = W.rmet[2 * cap + k];
+    double du[D], dub[D], mb[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int K = 0; K < D; ++K) du[K] = W.rdh[K * cap + k] / P.dt;
+    reg_to_phys_t<D>(J, sx, sy, du, udb, dub, mb);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        R[(int64_t)(RR::UP + K) * cap + k] = udb[K];
+        R[(int64_t)(RR::DU + K) * cap + k] = P.ds_overlap > 0.0 ? dub[K] + P.dt * R[(int64_t)(RR::H + K) * cap + k] : 0.0;
+    }
+    if (P.ds_overlap > 0.0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) R[(int64_t)(RR::M + q) * cap + k] += mb[q];
+}
+
+// Adjoint of pair (i, j)'s terms owned by fluid particle i with respect to its
+// separation e = r^'_j - r^'_i.
+template <int D>
+__device__ __forceinline__ void reg_pair_ebar(const DevParams &P, const Part &c, const Work &W, int i,
+                                              int j, double *eb)
+{
+    using RR = RegRows<D>;
+    const int64_t cap = W.cap;
+    const double *R = W.radj;
+    double e[D], r2 = 0.0;
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        e[K] = W.rxh[K * cap + j] - W.rxh[K * cap + i];
+        r2 += e[K] * e[K];
+        eb[K] = 0.0;
+    }
+    const double rr = sqrt(r2);
+    if (rr == 0.0) return;
+    const int tj = c.type[j];
+    const double dds = (1.0 - P.ds_overlap) * P.d0;
+    if (P.ds_overlap > 0.0 && rr < dds) {
+        const double f = tj == FLUID ? 0.5 : 1.0, g = (dds - rr) / (P.dt * rr),
+                     gp = -dds / (P.dt * rr * rr);
+        double de = 0.0;
+#pragma unroll
+        for (int K = 0; K < D; ++K) de += R[(int64_t)(RR::DU + K) * cap + i] * e[K];
+#pragma unroll
+        for (int K = 0; K < D; ++K) eb[K] -= f * (g * R[(int64_t)(RR::DU + K) * cap + i] + de * gp * e[K] / rr);
+    }
+    double w, dw;
+    kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
+    if (P.xsph_eps > 0.0 && W.fs[i] != 0 && tj == FLUID) {
+        double sdot = 0.0;
+#pragma unroll
+        for (int K = 0; K < D; ++K)
+            sdot += R[(int64_t)(RR::UN + K) * cap + i] * (W.rud[K * cap + j] - W.rud[K * cap + i]);
+#pragma unroll
+        for (int K = 0; K < D; ++K) eb[K] += P.xsph_eps * P.V0 * sdot * dw * e[K] / rr;
+    }
+    if (P.ops_shift > 0.0) {   // forward separation r_s = -e
+        const double phi = dw / rr, dphi = (kern_w2(rr, P.inv_l, P.ad) - dw / rr) / rr;
+        double gb[D], Bb[D * D], rs[D], gr = 0.0, rBr = 0.0, Brs[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            gb[K] = R[(int64_t)(RR::GC + K) * cap + i];
+            rs[K] = -e[K];
+            gr += gb[K] * rs[K];
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Bb[q] = R[(int64_t)(RR::B + q) * cap + i];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            Brs[a] = 0.0;
+#pragma unroll
+            for (int b = 0; b < D; ++b) Brs[a] += (Bb[a * D + b] + Bb[b * D + a]) * rs[b];
+#pragma unroll
+            for (int b = 0; b < D; ++b) rBr += rs[a] * Bb[a * D + b] * rs[b];
+        }
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            const double grs = P.V0 * (phi * gb[K] + gr * dphi * rs[K] / rr - phi * Brs[K] -
+                                       rBr * dphi * rs[K] / rr);
+            eb[K] -= grs;   // d/de = -d/dr_s
+        }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_regadj_pos(DevParams P, const Part c, Work W, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || c.type[k] != FLUID) return;
+    using RR = RegRows<D>;
+    const int64_t cap = W.cap;
+    double rb[D], eb[D];
+#pragma unroll
+    for (int K = 0; K < D; ++K) rb[K] = 0.0;
+    const int cnt = W.nbr_cnt[k];
+    for (int q = 0; q < cnt; ++q) {
+        const int j = W.nbr[(int64_t)q * cap + k];
+        reg_pair_ebar<D>(P, c, W, k, j, eb);   // k's own pair: e = r^_j - r^_k
+#pragma unroll
+        for (int K = 0; K < D; ++K) rb[K] -= eb[K];
+        if (c.type[j] == FLUID) {
+            reg_pair_ebar<D>(P, c, W, j, k, eb);   // j's pair: e = r^_k - r^_j
+#pragma unroll
+            for (int K = 0; K < D; ++K) rb[K] += eb[K];
+        }
+    }
+#pragma unroll
+    for (int K = 0; K < D; ++K) W.radj[(int64_t)(RR::XH + K) * cap + k] = rb[K];
+}
+
+// Physical x'_bar = (d r^'/d x')^T r^'_bar + the metric's adjoint through duals at x'
+// + x''_bar; writes u'_bar and x'_bar in caller order (0 off the fluid).
+template <int D>
+__global__ void __launch_bounds__(128) k_regadj_out(DevParams P, const Part c, Work W, int n,
+                                                    double *vb_co, double *xb_co)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    using RR = RegRows<D>;
+    const int64_t cap = W.cap;
+    const double *R = W.radj;
+    const int o = c.orig[k];
+    if (c.type[k] != FLUID) {
+#pragma unroll
+        for (int K = 0; K < D; ++K) vb_co[(int64_t)K * n + o] = xb_co[(int64_t)K * n + o] = 0.0;
+        return;
+    }
+    const double J = W.rmet[k], sx = W.rmet[cap + k], sy = W.rmet[2 * cap + k];
+    double a[D], xb[D], xp[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        a[K] = R[(int64_t)(RR::XH + K) * cap + k];
+        xp[K] = R[(int64_t)(RR::XP + K) * cap + k];
+    }
+    // r^ = (x, [y], z^(x, y, z)): d z^/d(x, y, z) = (s_x, s_y, J)
+    xb[0] = a[0] + sx * a[D - 1];
+    if (D == 3) xb[1] = a[1] + sy * a[2];
+    xb[D - 1] = J * a[D - 1];
+    const double mJ = R[(int64_t)RR::M * cap + k], msx = R[(int64_t)(RR::M + 1) * cap + k],
+                 msy = R[(int64_t)(RR::M + 2) * cap + k];
+    const double x = xp[0], y = D == 3 ? xp[1] : 0.0, z = xp[D - 1];
+    for (int K = 0; K < D; ++K) {
+        const int axis = D == 3 ? K : (K == 0 ? 0 : 2);
+        Dual out[6];
+        metric_dual(P, Dual(x, axis == 0 ? 1.0 : 0.0), Dual(y, axis == 1 ? 1.0 : 0.0),
+                    Dual(z, axis == 2 ? 1.0 : 0.0), -1, out);
+        xb[K] += mJ * out[1].d + msx * out[2].d + msy * out[3].d;
+    }
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        vb_co[(int64_t)K * n + o] = R[(int64_t)(RR::UP + K) * cap + k];
+        xb_co[(int64_t)K * n + o] = xb[K] + R[(int64_t)(RR::XD + K) * cap + k];
+    }
+}
+
+int regadj_rows(int dim) { return dim == 2 ? RegRows<2>::N : RegRows<3>::N; }
+
+void launch_regadj_save(const DevParams &P, Part cur, Work W, int64_t n, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) k_regadj_save<2><<<g, 128, 0, st>>>(cur, W, (int)n);
+    else k_regadj_save<3><<<g, 128, 0, st>>>(cur, W, (int)n);
+}
+
+void launch_regadj(const DevParams &P, Part cur, Work W, int64_t n, const double *v_bar,
+                   const double *x_bar, double *vb_co, double *xb_co, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (P.dim == 2) {
+        k_regadj_seed<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+        k_regadj_vel<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_regadj_pos<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_regadj_out<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, vb_co, xb_co);
+    } else {
+        k_regadj_seed<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
+        k_regadj_vel<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_regadj_pos<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        k_regadj_out<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, vb_co, xb_co);
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // a12 (part): derivative of the corrected gradient <grad^ phi>_i = L_i g_i,
@@ -6236,13 +6724,6 @@ void launch_stepadj_c(const DevParams &P, Part cur, Work W, int64_t n, double *v
 // k_gradpos_b gathers every particle's sum over its pairs from both ends (the
 // neighbour relation is symmetric), deterministic.  FP64.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double kern_w2(double r, double inv_l, double ad)
-{
-    const double q = r * inv_l;
-    if (q < 1.0) return ad * (-3.0 + 4.5 * q) * inv_l * inv_l;
-    if (q < 2.0) return ad * 1.5 * (2.0 - q) * inv_l * inv_l;
-    return 0.0;
-}
 
 template <int D>
 __global__ void __launch_bounds__(128) k_gradpos_a(DevParams P, const Part c, Work W, int n,
