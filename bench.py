@@ -105,7 +105,7 @@ WORKLOADS = {
     "efficiency": ("hydrostatic 1 m tank, H = 0.2 m, bottom 0.12 x + 0.01 (1 - cos(2 pi x / 0.5)): "
                    "BF d0 = 0.2 cm, BFE d0 = 0.5 cm alpha 2.5, sigma d0 = 0.5 cm alpha 1-2.5"),
     "adjoint": ("2-D sigma channel 10 m, flat 0.5 m + 16 random Gaussian bumps (seed 1), d0=0.01 m, "
-                "adjoint of the SPH(2) derivative operator"),
+                "the step's reverse and the operator adjoints"),
 }
 
 
@@ -134,11 +134,14 @@ def workload(precision=1, name="sigma_solitary"):
 
 
 def run_adjoint(args):
-    """Adjoint/forward time of the SPH(2) derivative operator on the 2-D adjoint
-    workload (sigma channel, flat 0.5 m + 16 random bumps, ~53k fluid): the
-    forward call (neighbours, corrected gradient, moment solves, derivatives of
-    three fields) against its adjoint (sph2_derivatives_backward, all three
-    outputs carrying adjoints).  Not the headline line."""
+    """Adjoint/forward times on the 2-D adjoint workload (sigma channel, flat
+    0.5 m + 16 random bumps, ~53k fluid).  The line's value is the reverse of one
+    whole step with respect to the velocities (vct_step_backward_velocity, which
+    re-assembles the step's operators) against one forward step.  Beside it:
+    the SPH(2) derivative operator (sph2_derivatives against
+    sph2_derivatives_backward, three fields), the pressure solve against its
+    transposed solve, and the gauge loss after one step with and without its
+    gradient with respect to the starting velocities.  Not the headline line."""
     import numpy as np
     import torch
     from paper_2607_28872_b300 import scenarios as S
@@ -213,13 +216,15 @@ def run_adjoint(args):
 
     fwd_loss_ms = timed(loss_only, ks)
     grad_ms = timed(loss_and_grad, ks)
-    print(json.dumps({"metric": "adjoint/forward time, SPH(2) derivative operator",
-                      "value": bwd / fwd, "unit": "x", "higher_is_better": False,
-                      "forward_ms": fwd, "backward_ms": bwd, "calls": k, "n_gpus": 1,
+    print(json.dumps({"metric": "adjoint/forward time, one step (its reverse with respect to "
+                                "the velocities)",
+                      "value": sbw_ms / step_ms, "unit": "x", "higher_is_better": False,
+                      "forward_ms": step_ms, "backward_ms": sbw_ms, "calls": ks, "n_gpus": 1,
                       "data": "synthetic",
                       "dtype": "f32+f64" if args.precision == 1 else "f64",
-                      "config": {"workload": WORKLOADS["adjoint"], "n_fluid": sc.n_fluid,
-                                 "fields": 3},
+                      "config": {"workload": WORKLOADS["adjoint"], "n_fluid": sc.n_fluid},
+                      "sph2_operator": {"forward_ms": fwd, "adjoint_ms": bwd, "ratio": bwd / fwd,
+                                        "fields": 3, "calls": k},
                       "ppe_solve": {"forward_ms": fwd_solve_ms, "adjoint_ms": ppe_adj_ms,
                                     "ratio": ppe_adj_ms / fwd_solve_ms,
                                     "adjoint_iters": int(ast.krylov_iters_total)},
