@@ -849,6 +849,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
         P.gcx[g] = bathy->cx[g];
         P.gcy[g] = bathy->cy[g];
         P.gwid[g] = bathy->width[g];
+        P.ginv2[g] = 1.0 / (bathy->width[g] * bathy->width[g]);
     }
 
     cudaError_t e = cudaSuccess;

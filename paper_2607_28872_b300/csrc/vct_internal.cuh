@@ -37,6 +37,7 @@ struct DevParams {
     double box_lo[3], cell_h, inv_cell_h;
     double h0, slope_x, slope_y, cos_amp, cos_len;
     double gamp[MAXG], gcx[MAXG], gcy[MAXG], gwid[MAXG];
+    double ginv2[MAXG];       // 1 / width^2 of each bump (the map's per-particle divisions, once)
 };
 
 // One buffer set of the cell-sorted particle state.

@@ -69,7 +69,7 @@ __device__ void bathy(const DevParams &P, double x, double y, double h[5])
         hxx -= P.cos_amp * k * k * cs;
     }
     for (int g = 0; g < P.n_gauss; ++g) {
-        double dx = x - P.gcx[g], dy = y - P.gcy[g], inv_s2 = 1.0 / (P.gwid[g] * P.gwid[g]);
+        double dx = x - P.gcx[g], dy = y - P.gcy[g], inv_s2 = P.ginv2[g];
         double e = P.gamp[g] * exp(-0.5 * (dx * dx + dy * dy) * inv_s2);
         v += e;
         hx -= e * dx * inv_s2;
@@ -7981,6 +7981,7 @@ extern "C" __attribute__((visibility("default"))) vct_status vct_build_neighbour
         P.gcx[g] = bathy->cx[g];
         P.gcy[g] = bathy->cy[g];
         P.gwid[g] = bathy->width[g];
+        P.ginv2[g] = 1.0 / (bathy->width[g] * bathy->width[g]);
     }
     Scratch *S = nullptr;
     vct_status v = scratch_on_device(&S);
