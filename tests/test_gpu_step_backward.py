@@ -326,3 +326,39 @@ def test_step_backward_velocity_needs_an_output():
     st = V.DeviceState(sc).struct()
     rc = s.lib.vct_step_backward_velocity(s.ctx, V.C.byref(st), None, None, None, None, None)
     assert rc == V.VCT_ERR_ARG
+
+
+@pytest.mark.parametrize("name", ["adjoint_sigma", "solitary_sigma"])
+def test_step_backward_velocity_full_size(name):
+    """At the workloads' full sizes (the adjoint workload's 53k-particle channel
+    with the eddy viscosity; the 2-D wave's 42k particles with the particle
+    regularisation too), FP64: the step reverse against central differences of
+    the GPU's own step along two random directions."""
+    import torch
+    from paper_2607_28872_b300 import vct as V
+    sc = getattr(S, name)(precision=0, krylov_rtol=1e-12, krylov_max_iter=20000)
+    d, n = sc.dim, sc.n
+    rng = np.random.default_rng(17)
+    fl = (sc.type == S.FLUID).astype(float)
+    vb = torch.tensor(rng.normal(size=(d, n)) * fl, device="cuda")
+    xb = torch.tensor(rng.normal(size=(d, n)) * fl, device="cuda")
+    s = V.Solver(sc)
+    st0 = V.DeviceState(sc)
+    got, _ = s.vct_step_backward_velocity(st0, vb, xb)
+    v0 = st0.velocity()
+    flt = torch.tensor(fl, device="cuda")
+
+    def loss(vel):
+        st = st0.clone()
+        st.set_velocity(vel)
+        s.vct_step(st, 1)
+        return float((vb * st.velocity()).sum() + (xb * st.position()).sum())
+
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    for _ in range(2):
+        dv = torch.randn(v0.shape, dtype=torch.float64, device="cuda", generator=gen) * flt * 1e-6
+        fd = (loss(v0 + dv) - loss(v0 - dv)) / 2.0
+        an = float((got * dv).sum())
+        scale = float((got * dv).abs().sum())
+        print(f"PARITY step backward velocity full size {name} (n={n}): {an:.9e} against {fd:.9e}")
+        assert abs(an - fd) <= 1e-5 * scale, (an, fd, scale)
