@@ -341,6 +341,30 @@ def run_ensemble(args):
     e1.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # end to end: the states in pinned host memory, every step's inputs copied to the
+    # device, one vct_batch_step of one step, the states read back
+    hosts = [{k: getattr(st, k).cpu().pin_memory() for k in vct.DeviceState.FIELDS}
+             for st in states]
+    nbytes = sum(t.numel() * t.element_size() for h in hosts for t in h.values())
+    ke = min(steps, 10)
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(ke):
+        for st, h in zip(states, hosts):
+            for k, t in h.items():
+                getattr(st, k).copy_(t, non_blocking=True)
+        vct.vct_batch_step(solvers, states, 1)
+        for st, h in zip(states, hosts):
+            for k, t in h.items():
+                t.copy_(getattr(st, k), non_blocking=True)
+    e3.record()
+    e3.synchronize()
+    e2e_ms = e2.elapsed_time(e3) / ke
+    e2e = {"value": nf / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": ke, "ms_per_step": e2e_ms,
+           "note": "one vct_batch_step of one step per step (no graph replay)"}
     # roofline of the batched solve (one launch per step for all scenarios),
     # timed by the first context's profiling events in a further short call
     # (profiling runs the steps from direct launches)
@@ -384,7 +408,7 @@ def run_ensemble(args):
                       "gpu_launches": int(sum(s.kernel_launches for s in stats)),
                       "graph_steps": int(stats[0].graph_steps), "roofline": roof,
                       "stage_ms_per_step": {k: v[0] / nprof for k, v in stage_t.items() if v[1]},
-                      "schedule": schedule,
+                      "schedule": schedule, "e2e": e2e,
                       "dtype": "f32+f64" if args.precision == 1 else "f64", "clocks": clk}),
           flush=True)
 
