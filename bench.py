@@ -216,6 +216,14 @@ def run_adjoint(args):
 
     fwd_loss_ms = timed(loss_only, ks)
     grad_ms = timed(loss_and_grad, ks)
+    # the same reverse on the 2-D wave (45k particles), whose steps run the particle
+    # regularisation: the reverse then replays the step forward up to it first
+    sw = S.solitary_sigma(precision=args.precision)
+    w_f, w_b = vct.Solver(sw), vct.Solver(sw)
+    wst_f, wst_b = vct.DeviceState(sw), vct.DeviceState(sw)
+    wvb = torch.randn((2, sw.n), dtype=torch.float64, device="cuda", generator=g)
+    wave_step_ms = timed(lambda: w_f.vct_step(wst_f, 1), ks)
+    wave_bwd_ms = timed(lambda: w_b.vct_step_backward_velocity(wst_b, wvb), ks)
     print(json.dumps({"metric": "adjoint/forward time, one step (its reverse with respect to "
                                 "the velocities)",
                       "value": sbw_ms / step_ms, "unit": "x", "higher_is_better": False,
@@ -231,6 +239,11 @@ def run_adjoint(args):
                       "step_velocity": {"forward_step_ms": step_ms, "backward_ms": sbw_ms,
                                         "ratio": sbw_ms / step_ms, "calls": ks,
                                         "adjoint_iters": int(sst.krylov_iters_total)},
+                      "step_velocity_regularised": {"workload": "2-D sigma solitary wave, "
+                                                                "45k particles, regularisation on",
+                                                    "forward_step_ms": wave_step_ms,
+                                                    "backward_ms": wave_bwd_ms,
+                                                    "ratio": wave_bwd_ms / wave_step_ms},
                       "gauge_loss_gradient": {"what": "d(gauge loss after one step)/d(starting "
                                                       "velocities), 8 gauges",
                                               "forward_ms": fwd_loss_ms, "gradient_ms": grad_ms,
