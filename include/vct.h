@@ -450,12 +450,11 @@ vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *o
  * loss with respect to p, writes b_bar = A^-T p_bar, the gradient with respect
  * to b; the gradient with respect to A's coefficients is then -b_bar p^T on A's
  * pattern.  The operator is the one the forward solve used (FP32 coefficients
- * in the mixed form).  The transposed system is solved like the forward one:
- * BiCGSTAB in the form's precision inside FP64 refinement, right-preconditioned
- * by the forward solve's multigrid V-cycle without coarse over-correction (A is
- * close to symmetric, so its hierarchy serves A^T; small-system solver form at
- * any size), or by Jacobi in FP64 when the context has no multigrid or the
- * multigrid solve does not converge (then the call solves again that way); to
+ * in the mixed form).  A's pattern is symmetric, so A^T is formed in place of A
+ * (each pair of coefficients swapped) and solved by the context's own solver
+ * (its form for A, with a multigrid hierarchy built for A^T), then A is
+ * restored; without multigrid, or if that solve does not converge, the call
+ * solves again by Jacobi-preconditioned BiCGSTAB in FP64 on A^T's products; to
  * the context's krylov_rtol relative to |p_bar|, at most krylov_max_iter
  * iterations per attempt (VCT_ERR_NOCONV otherwise).
  * p_bar, b_bar: device arrays of n doubles in caller order, n the particle
@@ -463,8 +462,9 @@ vct_status vct_step(vct_ctx *ctx, vct_state *state, int32_t nsteps, vct_stats *o
  * p_bar and written as 0 in b_bar.  Returns VCT_ERR_ARG if the context holds
  * no pressure system (no step yet, or a call since then that sorted the
  * particles again: vct_build_neighbours, sph2_derivatives).  Overwrites the
- * context's neighbour lists and solver vectors, which the next step rebuilds.
- * out (host, may be NULL) receives the iteration count and residual. */
+ * context's neighbour lists, solver vectors and multigrid hierarchy, which the
+ * next step rebuilds.  out (host, may be NULL) receives the iteration count and
+ * residual. */
 vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct_stats *out);
 
 /* Reverse of one time step with respect to the fluid velocities (Sec. 3.3:

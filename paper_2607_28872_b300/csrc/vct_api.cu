@@ -1389,16 +1389,27 @@ VCT_API vct_status vct_batch_step(vct_ctx *const *ctxs, vct_state *const *states
 static vct_status ppe_adjoint_solve(vct_ctx *c, int64_t n, const double *p_bar, double *b_bar,
                                     vct_stats *out)
 {
-    reset_status(c);
-    int e = launch_ppe_adjoint(c->P, cur(c), c->W, c->precond ? &c->mg : nullptr, n, p_bar,
-                               b_bar, c->st);
-    c->launches += 4;   // gather, transposed slots, solve, scatter
-    if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
-    vct_status v = finish(c, out, 1);
-    if (v == VCT_ERR_NOCONV && c->precond) {
+    vct_status v = VCT_ERR_NOCONV;
+    if (c->precond) {
+        // A^T in place of A, its own multigrid hierarchy and the forward solver
+        // (the form the context uses for A) on it, then A restored
         reset_status(c);
-        e = launch_ppe_adjoint(c->P, cur(c), c->W, nullptr, n, p_bar, b_bar, c->st);
-        c->launches += 4;
+        launch_ppe_transpose(c->P, c->W, n, true, c->st);
+        const bool rows = !c->mg.fly || c->rows_list;
+        launch_mg_setup(c->P, c->W, c->mg, n, c->st, rows);
+        launch_adj_gather(cur(c), c->W, n, p_bar, c->st);
+        const int e = launch_krylov_mg(c->P, c->W, c->mg, n, c->coop_blocks_mg, c->st);
+        launch_adj_scatter(cur(c), c->W, n, b_bar, c->st);
+        launch_ppe_transpose(c->P, c->W, n, false, c->st);
+        c->launches += 2 + mg_setup_launches(c->mg) + (rows ? 5 : 0) + 1 + 1 + 1 + 1;
+        if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+        v = finish(c, out, 1);
+    }
+    if (v == VCT_ERR_NOCONV) {
+        // no hierarchy, or it did not carry A^T: the Jacobi-preconditioned BiCGSTAB
+        reset_status(c);
+        const int e = launch_ppe_adjoint(c->P, cur(c), c->W, n, p_bar, b_bar, c->st);
+        c->launches += 4;   // gather, transposed slots, solve, scatter
         if (e || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
         v = finish(c, out, 1);
     }

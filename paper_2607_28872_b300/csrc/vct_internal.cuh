@@ -242,10 +242,16 @@ void launch_rhopos(const DevParams &P, Part cur, Work W, int64_t n, const double
 // derivative of the corrected gradient with respect to the projected positions
 void launch_gradpos(const DevParams &P, Part cur, Work W, int64_t n, int ncomp, const double *phi,
                     const double *grad_bar, double *xh_bar, cudaStream_t st);
-// adjoint of the last step's pressure solve: b_bar = A^-T p_bar (caller order)
-// (M: the context's multigrid hierarchy, or null for Jacobi preconditioning)
-int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_t n,
-                       const double *p_bar, double *b_bar, cudaStream_t st);
+// adjoint of the last step's pressure solve by the Jacobi-preconditioned BiCGSTAB
+// on A^T (products through the transposed-slot table): b_bar = A^-T p_bar (caller order)
+int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, int64_t n, const double *p_bar,
+                       double *b_bar, cudaStream_t st);
+// A <-> A^T in place (build_slots: write the transposed-slot table first, into
+// the neighbour-list scratch); the right side p_bar gathered into the solver's
+// vectors, and the solution scattered to b_bar (caller order)
+void launch_ppe_transpose(const DevParams &P, Work W, int64_t n, bool build_slots, cudaStream_t st);
+void launch_adj_gather(Part cur, Work W, int64_t n, const double *p_bar, cudaStream_t st);
+void launch_adj_scatter(Part cur, Work W, int64_t n, double *b_bar, cudaStream_t st);
 // reverse of one step with respect to the velocities, in three parts around the
 // two adjoint solves (scratch W.sadj, W.sadj_co):
 //   a: the corrector's adjoint, the pressure adjoint p_bar into W.sadj_co (caller order);

@@ -2136,32 +2136,6 @@ __device__ __forceinline__ T row_dot_pc(const Work &W, int i, int lg, int &pc_ou
     return acc;
 }
 
-// Row j of A^T x: row j's columns i, each with row i's coefficient in column j,
-// whose slot in row i is W.nbr[k * cap + j] (written by k_adj_tslot).  The
-// pattern is symmetric (see the adjoint of the pressure solve).
-template <typename T, typename CT, int G, typename GetX>
-__device__ __forceinline__ T row_dot_tr(const Work &W, int j, int lg, int &pc_out, GetX getx)
-{
-    const int64_t cap = W.cap;
-    const int pc = W.pcnt[j];
-    T acc = T(0);
-    for (int kk = lg; kk < pc; kk += G) {
-        const int i = W.pcol[ell_at<G>(kk, j, cap)];
-        const int t = W.nbr[(int64_t)kk * cap + j];
-        if (t >= 0) acc += (T)coef<CT>(W, ell_at<G>(t, i, cap)) * getx(i);
-    }
-    pc_out = pc;
-    return acc;
-}
-
-// A x (TR = false) or A^T x (TR = true) over row i's stored coefficients
-template <bool TR, typename T, typename CT, int G, int NS, typename GetX>
-__device__ __forceinline__ T prod_row(const Work &W, int i, int lg, int &pc_out, GetX getx)
-{
-    if constexpr (TR) return row_dot_tr<T, CT, G>(W, i, lg, pc_out, getx);
-    else return row_dot_pc<T, CT, G, NS>(W, i, lg, pc_out, getx);
-}
-
 // G lanes per row; the row's scalar work is repeated by every lane of the group
 // (same addresses, broadcast loads) and only lane 0 writes.  Dot-product
 // partials are accumulated per thread in T and summed per block in FP64.
@@ -3511,7 +3485,7 @@ __device__ bool vcycle_fly(const Work &W, const MG &M, float *sh, int n, In in, 
 // Right-preconditioned BiCGSTAB inside FP64 iterative refinement (as k_krylov).
 // The solve on vnb blocks (block vb of them) sharing W.bar and W.partial: the
 // whole grid, or one scenario's subset of a batched launch.
-template <typename T, typename CT, int G, int NS, int D, bool TR = false>
+template <typename T, typename CT, int G, int NS, int D>
 __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, double rtol,
                                  double inner_floor, int32_t *iters_out, double *resid_out,
                                  unsigned vb, unsigned vnb)
@@ -3536,7 +3510,7 @@ __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, d
         double part[2] = {0.0, 0.0};
         for (int i = g0; i < n; i += ngroups) {
             int pc;
-            double ax = prod_row<TR, double, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(x + j); });
+            double ax = row_dot_pc<double, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(x + j); });
             if (pc < 0) continue;
             ax = group_sum<G>(ax);
             if (lead) {
@@ -3600,7 +3574,7 @@ __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, d
             T pa = T(0);
             for (int i = g0; i < n; i += ngroups) {
                 int pc;
-                T acc = prod_row<TR, T, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(ph + j); });
+                T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(ph + j); });
                 if (pc < 0) continue;
                 acc = group_sum<G>(acc);
                 if (lead) {
@@ -3632,7 +3606,7 @@ __device__ void krylov_fly_solve(const Work &W, const MG &M, int n, int maxit, d
             T pb0 = T(0), pb1 = T(0), pb2 = T(0), pb3 = T(0), pb4 = T(0);
             for (int i = g0; i < n; i += ngroups) {
                 int pc;
-                T acc = prod_row<TR, T, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(sh + j); });
+                T acc = row_dot_pc<T, CT, G, NS>(W, i, lg, pc, [&](int j) { return __ldcg(sh + j); });
                 if (pc < 0) continue;
                 acc = group_sum<G>(acc);
                 if (lead) {
@@ -3699,18 +3673,6 @@ __global__ void __launch_bounds__(KT) k_krylov_mg_fly(Work W, MG M, int n, int m
 {
     krylov_fly_solve<T, CT, G, NS, D>(W, M, n, maxit, rtol, inner_floor, iters_out, resid_out,
                                       blockIdx.x, gridDim.x);
-}
-
-// The same solve for A^T y = g: the products and the FP64 residual with the
-// transposed operator, the V-cycle of A as the preconditioner (A is close to
-// symmetric: the same hierarchy serves A^T).  The adjoint of the pressure solve.
-template <typename T, typename CT, int G, int NS, int D>
-__global__ void __launch_bounds__(KT) k_krylov_mg_fly_tr(Work W, MG M, int n, int maxit, double rtol,
-                                                     double inner_floor, int32_t *iters_out,
-                                                     double *resid_out)
-{
-    krylov_fly_solve<T, CT, G, NS, D, true>(W, M, n, maxit, rtol, inner_floor, iters_out, resid_out,
-                                            blockIdx.x, gridDim.x);
 }
 
 // Batched solves (ensembles): job j owns blocks [b0, b0 + nb) of one cooperative
@@ -5531,17 +5493,60 @@ static const void *adj_fn(int precision, int dim)
     return dim == 2 ? (const void *)k_adj_bicgstab<2, double> : (const void *)k_adj_bicgstab<3, double>;
 }
 
-static const void *adj_mg_fn(int precision, int dim)
+// A^T in place of A.  The pattern is symmetric (row i holds the unknown
+// neighbours of i, the neighbour relation is symmetric), so A^T has A's pattern,
+// and its coefficient in row j, column i is A's in row i, column j: with the
+// transposed-slot table of k_adj_tslot (in the neighbour-list scratch) each pair
+// of coefficients is swapped once, by the row with the smaller index.  A second
+// pass restores A.
+template <int D, typename T>
+__global__ void k_ell_transpose(Work W, int n, T *vals)
 {
-    if (precision == VCT_MIXED)
-        return dim == 2 ? (const void *)k_krylov_mg_fly_tr<float, float, 4, 5, 2>
-                        : (const void *)k_krylov_mg_fly_tr<float, float, 8, NS3, 3>;
-    return dim == 2 ? (const void *)k_krylov_mg_fly_tr<double, double, 4, 5, 2>
-                    : (const void *)k_krylov_mg_fly_tr<double, double, 8, NS3, 3>;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int pc = W.pcnt[j];
+    const int64_t cap = W.cap;
+    for (int k = 0; k < pc; ++k) {
+        const int64_t q = ell_at<ell_group<D>()>(k, j, cap);
+        const int i = W.pcol[q];
+        if (i <= j) continue;
+        const int t = W.nbr[(int64_t)k * cap + j];
+        if (t < 0) continue;
+        const int64_t qt = ell_at<ell_group<D>()>(t, i, cap);
+        const T a = vals[q];
+        vals[q] = vals[qt];
+        vals[qt] = a;
+    }
 }
 
-int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_t n,
-                       const double *p_bar, double *b_bar, cudaStream_t st)
+void launch_ppe_transpose(const DevParams &P, Work W, int64_t n, bool build_slots, cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (build_slots) {
+        if (P.dim == 2) k_adj_tslot<2><<<g, 256, 0, st>>>(W, (int)n);
+        else k_adj_tslot<3><<<g, 256, 0, st>>>(W, (int)n);
+    }
+    if (P.precision == VCT_MIXED) {
+        if (P.dim == 2) k_ell_transpose<2, float><<<g, 256, 0, st>>>(W, (int)n, W.pvalf);
+        else k_ell_transpose<3, float><<<g, 256, 0, st>>>(W, (int)n, W.pvalf);
+    } else {
+        if (P.dim == 2) k_ell_transpose<2, double><<<g, 256, 0, st>>>(W, (int)n, W.pval);
+        else k_ell_transpose<3, double><<<g, 256, 0, st>>>(W, (int)n, W.pval);
+    }
+}
+
+void launch_adj_gather(Part cur, Work W, int64_t n, const double *p_bar, cudaStream_t st)
+{
+    k_adj_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cur, W, (int)n, p_bar);
+}
+
+void launch_adj_scatter(Part cur, Work W, int64_t n, double *b_bar, cudaStream_t st)
+{
+    k_adj_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cur, W, (int)n, b_bar);
+}
+
+int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, int64_t n, const double *p_bar,
+                       double *b_bar, cudaStream_t st)
 {
     const unsigned g = (unsigned)((n + 255) / 256);
     k_adj_gather<<<g, 256, 0, st>>>(cur, W, (int)n, p_bar);
@@ -5550,38 +5555,6 @@ int launch_ppe_adjoint(const DevParams &P, Part cur, Work W, const MG *M, int64_
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (M) {   // multigrid: the forward V-cycle preconditions the transposed system
-        const void *fn = adj_mg_fn(P.precision, P.dim);
-        const size_t smem = (size_t)M->smem_bytes;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, KT, smem);
-        if (per > 2) per = 2;
-        const int G = P.dim == 2 ? 4 : 8;
-        const int64_t want = (n * G + KT - 1) / KT;
-        int nblk = sms * per;
-        if (nblk > PSTRIDE) nblk = PSTRIDE;
-        if (want < nblk) nblk = (int)want;
-        if (nblk < 1) nblk = 1;
-        int nn = (int)n, maxit = P.max_iter;
-        double rtol = P.rtol, floor_ = P.inner_floor;
-        int32_t *it_out = W.kiters;
-        double *res_out = W.kresid;
-        // No over-correction of the coarse levels here: on the 2-D channel with
-        // 16 bumps (53k particles) the transposed solve with the forward scale
-        // kappa = 1.3 did not converge in 20,000 iterations and took 35 with 1.0
-        // (the forward solve 24); the hierarchy itself does not depend on kappa.
-        MG Mc = *M;
-        Mc.kappa = 1.0f;
-        Mc.kappa_c = 1.0f;
-        void *args[] = {(void *)&W, (void *)&Mc, (void *)&nn, (void *)&maxit, (void *)&rtol,
-                        (void *)&floor_, (void *)&it_out, (void *)&res_out};
-        cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), st);
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblk), dim3(KT), args, smem, st);
-        if (e != cudaSuccess) return (int)e;
-        k_adj_scatter<<<g, 256, 0, st>>>(cur, W, (int)n, b_bar);
-        return 0;
-    }
     const void *fn = adj_fn(P.precision, P.dim);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, KT, 0);
     if (per > 2) per = 2;
