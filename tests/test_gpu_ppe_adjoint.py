@@ -137,3 +137,22 @@ def test_ppe_adjoint_identity_bumpy_channel(vct):
     rhs = b_bar[unknown] @ info["ppe_b"][unknown]
     scale = np.abs(p_bar[unknown]) @ np.abs(ost.p[unknown])
     assert abs(lhs - rhs) < 1e-7 * scale
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_ppe_adjoint_leaves_the_operator_as_it_was(vct, precision):
+    """The transposed solve swaps A's coefficient pairs to stand A^T in A's place
+    and swaps them back: two calls in a row give the same b_bar bit for bit (had
+    the first left A^T in place, the second would solve with A itself)."""
+    import torch
+    sc = TANKS[0][1]().copy()
+    sc.params["precision"] = precision
+    sc.params["krylov_rtol"] = 1e-12
+    sc.params["krylov_max_iter"] = 20000
+    rng = np.random.default_rng(21)
+    p_bar = torch.tensor(rng.normal(size=sc.n), device="cuda")
+    solver = vct.Solver(sc)
+    solver.vct_step_probe(vct.DeviceState(sc))
+    b1, _ = solver.vct_ppe_adjoint(p_bar)
+    b2, _ = solver.vct_ppe_adjoint(p_bar)
+    assert torch.equal(b1, b2)
