@@ -227,16 +227,23 @@ def test_step_function_autograd():
     assert abs(an - fd) <= 1e-6 * float((vel.grad * dv).abs().sum())
 
 
-def test_gauge_loss_gradient_through_a_step():
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gauge_loss_gradient_through_a_step(dim):
     """The adjoint workload's loss after one step, differentiated with respect to
     the step's starting velocities: vct_gauge_loss's position gradient at the
     updated state, fed to the step reverse as x_bar, against central
     differences of oracle.gauge_loss of the oracle's step (free-surface flags
-    of the step held; a sample of 40 fluid particles)."""
+    of the step held; a sample of 40 fluid particles).  2-D sigma tank with a
+    wave; 3-D BFE tank with a wave at aspect 2."""
     import torch
     from paper_2607_28872_b300 import vct as V
-    sc = _tank("SIGMA", 2)
-    gauges = np.array([0.02, 0.045, 0.07, 0.1])
+    if dim == 2:
+        sc = _tank("SIGMA", 2)
+        gauges = np.array([0.02, 0.045, 0.07, 0.1])
+    else:
+        sc = S.small_tank(dim=3, kind="BFE", L=0.2, W=0.08, H=0.05, d0=0.01, seed=4, aspect=2.0,
+                          with_wave=True, smagorinsky=0, krylov_rtol=1e-12, krylov_max_iter=20000)
+        gauges = np.array([[0.04, 0.03], [0.09, 0.05], [0.15, 0.04]])
     _, info = O.step(sc, probe=True)
     fs = info["fs"].astype(np.int32)
     fs_dev = torch.tensor(fs, device="cuda")
@@ -251,18 +258,19 @@ def test_gauge_loss_gradient_through_a_step():
 
     def oracle_loss(vel):
         st = O.OracleState(sc)
-        st.u[:], st.w[:] = vel[0], vel[1]
+        for c, name in enumerate(COMP[dim]):
+            getattr(st, name)[:] = vel[c]
         st, inf = O.step(sc, state=st)
         assert inf["rc"] == 0
-        return O.gauge_loss(sc, fs, gauges, st.x, None, st.z)
+        return O.gauge_loss(sc, fs, gauges, st.x, st.y if dim == 3 else None, st.z)
 
     v0 = _base_velocity(sc)
     assert abs(loss - oracle_loss(v0)) <= 1e-8 * loss
     fl = np.flatnonzero(sc.type == S.FLUID)
     fl = np.sort(np.random.default_rng(7).choice(fl, 40, replace=False))
     h = 1e-5
-    ref = np.zeros((2, fl.size))
-    for c in range(2):
+    ref = np.zeros((dim, fl.size))
+    for c in range(dim):
         for k, i in enumerate(fl):
             vp, vm = v0.copy(), v0.copy()
             vp[c, i] += h
@@ -270,7 +278,7 @@ def test_gauge_loss_gradient_through_a_step():
             ref[c, k] = (oracle_loss(vp) - oracle_loss(vm)) / (2 * h)
     scale = np.abs(ref).max()
     err = np.abs(got[:, fl] - ref).max() / scale
-    print(f"PARITY gauge loss through a step, d loss / d v: max err {err:.2e} of max |grad| "
+    print(f"PARITY gauge loss through a step, {dim}-D, d loss / d v: max err {err:.2e} of max |grad| "
           f"{scale:.3e}")
     assert scale > 0.0
     assert err < 1e-5, err
