@@ -224,6 +224,14 @@ def run_adjoint(args):
     wvb = torch.randn((2, sw.n), dtype=torch.float64, device="cuda", generator=g)
     wave_step_ms = timed(lambda: w_f.vct_step(wst_f, 1), ks)
     wave_bwd_ms = timed(lambda: w_b.vct_step_backward_velocity(wst_b, wvb), ks)
+    # and on the 3-D beach slice (702,810 particles, aspect 4, regularisation on)
+    s3 = S.beach_bfe_3d(L=8.0, W=1.6, precision=args.precision)
+    b_f, b_b = vct.Solver(s3), vct.Solver(s3)
+    bst_f, bst_b = vct.DeviceState(s3), vct.DeviceState(s3)
+    bvb = torch.randn((3, s3.n), dtype=torch.float64, device="cuda", generator=g)
+    k3 = min(ks, 3)
+    slice_step_ms = timed(lambda: b_f.vct_step(bst_f, 1), k3)
+    slice_bwd_ms = timed(lambda: b_b.vct_step_backward_velocity(bst_b, bvb), k3)
     print(json.dumps({"metric": "adjoint/forward time, one step (its reverse with respect to "
                                 "the velocities)",
                       "value": sbw_ms / step_ms, "unit": "x", "higher_is_better": False,
@@ -244,6 +252,11 @@ def run_adjoint(args):
                                                     "forward_step_ms": wave_step_ms,
                                                     "backward_ms": wave_bwd_ms,
                                                     "ratio": wave_bwd_ms / wave_step_ms},
+                      "step_velocity_3d": {"workload": "3-D BFE beach slice 8 x 1.6 m, 702,810 "
+                                                       "particles, aspect 4, regularisation on",
+                                           "forward_step_ms": slice_step_ms,
+                                           "backward_ms": slice_bwd_ms,
+                                           "ratio": slice_bwd_ms / slice_step_ms},
                       "gauge_loss_gradient": {"what": "d(gauge loss after one step)/d(starting "
                                                       "velocities), 8 gauges",
                                               "forward_ms": fwd_loss_ms, "gradient_ms": grad_ms,
