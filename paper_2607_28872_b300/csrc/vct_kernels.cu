@@ -143,13 +143,19 @@ __device__ __forceinline__ void kern_wdw(R r, R inv_l, R ad, R &w, R &dw)
     }
 }
 
-// Second derivative w'' of the cubic spline (FP64).
+// Second derivative w'' of the cubic spline (FP64; kern_w2t in type T).
+template <typename T>
+__device__ __forceinline__ T kern_w2t(T r, T inv_l, T ad)
+{
+    const T q = r * inv_l;
+    if (q < T(1)) return ad * (T(-3) + T(4.5) * q) * inv_l * inv_l;
+    if (q < T(2)) return ad * T(1.5) * (T(2) - q) * inv_l * inv_l;
+    return T(0);
+}
+
 __device__ __forceinline__ double kern_w2(double r, double inv_l, double ad)
 {
-    const double q = r * inv_l;
-    if (q < 1.0) return ad * (-3.0 + 4.5 * q) * inv_l * inv_l;
-    if (q < 2.0) return ad * 1.5 * (2.0 - q) * inv_l * inv_l;
-    return 0.0;
+    return kern_w2t<double>(r, inv_l, ad);
 }
 
 template <int D>
@@ -6518,92 +6524,97 @@ __global__ void __launch_bounds__(128) k_regadj_vel(DevParams P, const Part c, W
 }
 
 // Adjoint of pair (i, j)'s terms owned by fluid particle i with respect to its
-// separation e = r^'_j - r^'_i.
-template <int D>
+// separation e = r^'_j - r^'_i.  T: the pair arithmetic's type (the mixed form's
+// FP32, as its forward regularisation's pair sums; the separation itself is
+// formed in FP64 first), one reciprocal of |e| per pair.
+template <int D, typename T>
 __device__ __forceinline__ void reg_pair_ebar(const DevParams &P, const Part &c, const Work &W, int i,
-                                              int j, double *eb)
+                                              int j, T *eb)
 {
     using RR = RegRows<D>;
     const int64_t cap = W.cap;
     const double *R = W.radj;
-    double e[D], r2 = 0.0;
+    T e[D], r2 = T(0);
 #pragma unroll
     for (int K = 0; K < D; ++K) {
-        e[K] = W.rxh[K * cap + j] - W.rxh[K * cap + i];
+        e[K] = (T)(W.rxh[K * cap + j] - W.rxh[K * cap + i]);
         r2 += e[K] * e[K];
-        eb[K] = 0.0;
+        eb[K] = T(0);
     }
-    const double rr = sqrt(r2);
-    if (rr == 0.0) return;
+    if (r2 == T(0)) return;
+    const T rr = sqrt(r2), ir = T(1) / rr;
     const int tj = c.type[j];
-    const double dds = (1.0 - P.ds_overlap) * P.d0;
+    const T dds = (T)((1.0 - P.ds_overlap) * P.d0);
     if (P.ds_overlap > 0.0 && rr < dds) {
-        const double f = tj == FLUID ? 0.5 : 1.0, g = (dds - rr) / (P.dt * rr),
-                     gp = -dds / (P.dt * rr * rr);
-        double de = 0.0;
-#pragma unroll
-        for (int K = 0; K < D; ++K) de += R[(int64_t)(RR::DU + K) * cap + i] * e[K];
-#pragma unroll
-        for (int K = 0; K < D; ++K) eb[K] -= f * (g * R[(int64_t)(RR::DU + K) * cap + i] + de * gp * e[K] / rr);
-    }
-    double w, dw;
-    kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
-    if (P.xsph_eps > 0.0 && W.fs[i] != 0 && tj == FLUID) {
-        double sdot = 0.0;
-#pragma unroll
-        for (int K = 0; K < D; ++K)
-            sdot += R[(int64_t)(RR::UN + K) * cap + i] * (W.rud[K * cap + j] - W.rud[K * cap + i]);
-#pragma unroll
-        for (int K = 0; K < D; ++K) eb[K] += P.xsph_eps * P.V0 * sdot * dw * e[K] / rr;
-    }
-    if (P.ops_shift > 0.0) {   // forward separation r_s = -e
-        const double phi = dw / rr, dphi = (kern_w2(rr, P.inv_l, P.ad) - dw / rr) / rr;
-        double gb[D], Bb[D * D], rs[D], gr = 0.0, rBr = 0.0, Brs[D];
+        const T idt = (T)(1.0 / P.dt), f = tj == FLUID ? T(0.5) : T(1);
+        const T g = (dds - rr) * idt * ir, gp = -dds * idt * ir * ir;
+        T du[D], de = T(0);
 #pragma unroll
         for (int K = 0; K < D; ++K) {
-            gb[K] = R[(int64_t)(RR::GC + K) * cap + i];
+            du[K] = (T)R[(int64_t)(RR::DU + K) * cap + i];
+            de += du[K] * e[K];
+        }
+#pragma unroll
+        for (int K = 0; K < D; ++K) eb[K] -= f * (g * du[K] + de * gp * e[K] * ir);
+    }
+    T w, dw;
+    kern_wdw<T>(rr, (T)P.inv_l, (T)P.ad, w, dw);
+    if (P.xsph_eps > 0.0 && W.fs[i] != 0 && tj == FLUID) {
+        T sdot = T(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K)
+            sdot += (T)R[(int64_t)(RR::UN + K) * cap + i] * (T)(W.rud[K * cap + j] - W.rud[K * cap + i]);
+        const T fx = (T)(P.xsph_eps * P.V0) * sdot * dw * ir;
+#pragma unroll
+        for (int K = 0; K < D; ++K) eb[K] += fx * e[K];
+    }
+    if (P.ops_shift > 0.0) {   // forward separation r_s = -e
+        const T phi = dw * ir, dphi = (kern_w2t<T>(rr, (T)P.inv_l, (T)P.ad) - phi) * ir;
+        T gb[D], Bb[D * D], rs[D], gr = T(0), rBr = T(0), Brs[D];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            gb[K] = (T)R[(int64_t)(RR::GC + K) * cap + i];
             rs[K] = -e[K];
             gr += gb[K] * rs[K];
         }
 #pragma unroll
-        for (int q = 0; q < D * D; ++q) Bb[q] = R[(int64_t)(RR::B + q) * cap + i];
+        for (int q = 0; q < D * D; ++q) Bb[q] = (T)R[(int64_t)(RR::B + q) * cap + i];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            Brs[a] = 0.0;
+        for (int a2 = 0; a2 < D; ++a2) {
+            Brs[a2] = T(0);
 #pragma unroll
-            for (int b = 0; b < D; ++b) Brs[a] += (Bb[a * D + b] + Bb[b * D + a]) * rs[b];
+            for (int b2 = 0; b2 < D; ++b2) Brs[a2] += (Bb[a2 * D + b2] + Bb[b2 * D + a2]) * rs[b2];
 #pragma unroll
-            for (int b = 0; b < D; ++b) rBr += rs[a] * Bb[a * D + b] * rs[b];
+            for (int b2 = 0; b2 < D; ++b2) rBr += rs[a2] * Bb[a2 * D + b2] * rs[b2];
         }
+        const T V0 = (T)P.V0, sc = (gr - rBr) * dphi * ir;
 #pragma unroll
-        for (int K = 0; K < D; ++K) {
-            const double grs = P.V0 * (phi * gb[K] + gr * dphi * rs[K] / rr - phi * Brs[K] -
-                                       rBr * dphi * rs[K] / rr);
-            eb[K] -= grs;   // d/de = -d/dr_s
-        }
+        for (int K = 0; K < D; ++K)
+            eb[K] -= V0 * (phi * (gb[K] - Brs[K]) + sc * rs[K]);   // d/de = -d/dr_s
     }
 }
 
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(128) k_regadj_pos(DevParams P, const Part c, Work W, int n)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || c.type[k] != FLUID) return;
     using RR = RegRows<D>;
     const int64_t cap = W.cap;
-    double rb[D], eb[D];
+    double rb[D];
+    T eb[D];
 #pragma unroll
     for (int K = 0; K < D; ++K) rb[K] = 0.0;
     const int cnt = W.nbr_cnt[k];
     for (int q = 0; q < cnt; ++q) {
         const int j = W.nbr[(int64_t)q * cap + k];
-        reg_pair_ebar<D>(P, c, W, k, j, eb);   // k's own pair: e = r^_j - r^_k
+        reg_pair_ebar<D, T>(P, c, W, k, j, eb);   // k's own pair: e = r^_j - r^_k
 #pragma unroll
-        for (int K = 0; K < D; ++K) rb[K] -= eb[K];
+        for (int K = 0; K < D; ++K) rb[K] -= (double)eb[K];
         if (c.type[j] == FLUID) {
-            reg_pair_ebar<D>(P, c, W, j, k, eb);   // j's pair: e = r^_k - r^_j
+            reg_pair_ebar<D, T>(P, c, W, j, k, eb);   // j's pair: e = r^_k - r^_j
 #pragma unroll
-            for (int K = 0; K < D; ++K) rb[K] += eb[K];
+            for (int K = 0; K < D; ++K) rb[K] += (double)eb[K];
         }
     }
 #pragma unroll
@@ -6671,12 +6682,14 @@ void launch_regadj(const DevParams &P, Part cur, Work W, int64_t n, const double
     if (P.dim == 2) {
         k_regadj_seed<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
         k_regadj_vel<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
-        k_regadj_pos<2><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.precision == VCT_MIXED) k_regadj_pos<2, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_regadj_pos<2, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
         k_regadj_out<2><<<g, 128, 0, st>>>(P, cur, W, (int)n, vb_co, xb_co);
     } else {
         k_regadj_seed<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, v_bar, x_bar);
         k_regadj_vel<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
-        k_regadj_pos<3><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        if (P.precision == VCT_MIXED) k_regadj_pos<3, float><<<g, 128, 0, st>>>(P, cur, W, (int)n);
+        else k_regadj_pos<3, double><<<g, 128, 0, st>>>(P, cur, W, (int)n);
         k_regadj_out<3><<<g, 128, 0, st>>>(P, cur, W, (int)n, vb_co, xb_co);
     }
 }
