@@ -898,7 +898,7 @@ VCT_API vct_status vct_init(vct_ctx **out, const vct_bathymetry *bathy, vct_map_
     W.vslo = dalloc<float4>(c, n, e);
     W.vol = dalloc<double>(c, n, e);
     W.volf = dalloc<float>(c, n, e);
-    W.adj = dalloc<double>(c, n * (m + d), e);
+    W.adj = dalloc<double>(c, n * 3 * (m + d), e);   // the operator adjoint's rows, up to 3 fields at once
     if (prm->ops_shift > 0.0 || prm->ds_overlap > 0.0 || prm->xsph_eps > 0.0) {
         W.rxh = dalloc<double>(c, n * d, e);
         W.rmet = dalloc<double>(c, n * 3, e);

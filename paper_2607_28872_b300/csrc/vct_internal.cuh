@@ -105,7 +105,7 @@ struct Work {
     double *kr0;              // fine residual of the V-cycle (FP32 or FP64 slots)
     double *kq0, *kq1;        // preconditioned directions p^, s^
     double *kz0, *kzb;        // V-cycle: first Jacobi step and prolonged correction
-    double *adj;              // adjoint scratch: [m + dim] per particle
+    double *adj;              // adjoint scratch: [3 (m + dim)] per particle
     double *sadj;             // step reverse, cell order: [3 dim + dim^2] per particle (allocated on first use)
     double *sadj_co;          // step reverse, caller order: [dim + 2] per particle
     double *radj;             // regularisation reverse, cell order (rows: regadj_rows) + caller-order

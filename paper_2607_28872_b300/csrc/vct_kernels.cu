@@ -4670,10 +4670,262 @@ __global__ void __launch_bounds__(128) k_sph2_adj2(DevParams P, const Part c, Wo
     phibar[(int64_t)comp * n + o] = (double)acc.val();
 }
 
+// The same adjoint for NC <= 3 fields at once: M_i is summed and factored once
+// and solved for the NC right sides, each pair's geometry is formed once for all
+// fields (the forward operator shares them the same way).  W.adj holds the NC
+// fields' (bbar, gbar') rows one after the other.
+template <int D, typename R, int NC>
+__global__ void __launch_bounds__(128) k_sph2_adjm1(DevParams P, const Part c, Work W, int n,
+                                                    const double *gbar, const double *d2bar,
+                                                    const double *lapbar)
+{
+    constexpr int M = D == 2 ? 3 : 6, S = M + D;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cap = W.cap;
+    if (c.type[i] != FLUID) {
+        for (int a = 0; a < NC * S; ++a) W.adj[(int64_t)a * cap + i] = 0.0;
+        return;
+    }
+    const int o = c.orig[i];
+    double xi[3];
+    load_hat<D>(c, i, xi);
+    R L[D * D], Ct[D * M];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) L[k] = (R)W.L[(int64_t)k * cap + i];
+#pragma unroll
+    for (int k = 0; k < D * M; ++k) Ct[k] = (R)W.Ct[(int64_t)k * cap + i];
+    const R inv_l = (R)P.inv_l, ad = (R)P.ad;
+    const int cnt = W.nbr_cnt[i];
+    Acc<R> Mm[M * M];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R gw[D], fac = -dw / rr, rg = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) gw[K] = fac * r[K];
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R s2 = R(0);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s2 += L[K * D + L2] * gw[L2];
+            rg += r[K] * s2;
+        }
+        R VF = (R)vol_of(P, c, j) * rg / (rr2 * rr2), q[M], pv[M];
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            R s2 = R(0);
+#pragma unroll
+            for (int K = 0; K < D; ++K) s2 += Ct[K * M + a] * r[K];
+            pv[a] = q[a] - s2;
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) Mm[a * M + b].add(VF * q[a] * pv[b]);
+    }
+    double ct[M];
+    ctilde<D>(c.c3[i], c.sx[i], c.sy[i], ct);
+    double Dbar[M * NC], gb[NC][D];   // Dbar row-major M x NC
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        const double lb = lapbar ? lapbar[(int64_t)cc * n + o] : 0.0;
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            const double d2b = d2bar ? d2bar[((int64_t)cc * M + a) * n + o] : 0.0;
+            Dbar[a * NC + cc] = (a < D ? d2b : 0.5 * d2b) + ct[a] * lb;
+        }
+#pragma unroll
+        for (int K = 0; K < D; ++K) gb[cc][K] = gbar ? gbar[((int64_t)cc * D + K) * n + o] : 0.0;
+        gb[cc][D - 1] += c.c0[i] * lb;
+    }
+    double A[M * M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) A[a * M + b] = (double)Mm[b * M + a].val();
+    const int fsi = W.fs[i];
+    if (fsi == 2 || !lu_solve<M, NC>(A, Dbar)) {
+        if (!fsi) set_error(W.status, VCT_ERR_SINGULAR, i);
+#pragma unroll
+        for (int a = 0; a < M * NC; ++a) Dbar[a] = 0.0;
+    }
+    R bb[NC][M];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+        for (int a = 0; a < M; ++a) bb[cc][a] = (R)(2.0 * Dbar[a * NC + cc]);
+    Acc<R> u[NC][D];
+    for (int k = 0; k < cnt; ++k) {
+        int j = W.nbr[(int64_t)k * cap + i];
+        if (c.type[j] == VIRTUAL) continue;
+        double xj[3];
+        load_hat<D>(c, j, xj);
+        R r[D], rr2 = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            r[K] = (R)(xj[K] - xi[K]);
+            rr2 += r[K] * r[K];
+        }
+        if (rr2 == R(0)) continue;
+        R rr = sqrt(rr2), w, dw;
+        kern_wdw<R>(rr, inv_l, ad, w, dw);
+        R fac = -dw / rr, rg = R(0);
+#pragma unroll
+        for (int K = 0; K < D; ++K) {
+            R s2 = R(0);
+#pragma unroll
+            for (int L2 = 0; L2 < D; ++L2) s2 += L[K * D + L2] * fac * r[L2];
+            rg += r[K] * s2;
+        }
+        R VF = (R)vol_of(P, c, j) * rg / (rr2 * rr2), q[M];
+        qvec<D, R>(r, q);
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+            R bq = R(0);
+#pragma unroll
+            for (int a = 0; a < M; ++a) bq += bb[cc][a] * q[a];
+#pragma unroll
+            for (int K = 0; K < D; ++K) u[cc][K].add(VF * bq * r[K]);
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+#pragma unroll
+        for (int a = 0; a < M; ++a) W.adj[(int64_t)(cc * S + a) * cap + i] = (double)bb[cc][a];
+#pragma unroll
+        for (int K = 0; K < D; ++K)
+            W.adj[(int64_t)(cc * S + M + K) * cap + i] = gb[cc][K] - (double)u[cc][K].val();
+    }
+}
+
+// Pair weights w_ij of the NC fields seen from particle i (the owner) for neighbour j.
+template <int D, typename R, int NC>
+__device__ __forceinline__ void adj_pair_m(const DevParams &P, const Part &c, const Work &W, int i,
+                                           int j, const double *xi, const double *xj, R *wout)
+{
+    constexpr int M = D == 2 ? 3 : 6, S = M + D;
+    const int64_t cap = W.cap;
+    R r[D], rr2 = R(0);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        r[K] = (R)(xj[K] - xi[K]);
+        rr2 += r[K] * r[K];
+    }
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) wout[cc] = R(0);
+    if (rr2 == R(0)) return;
+    R rr = sqrt(rr2), w, dw;
+    kern_wdw<R>(rr, (R)P.inv_l, (R)P.ad, w, dw);
+    R fac = -dw / rr, gt[D], rg = R(0);
+#pragma unroll
+    for (int K = 0; K < D; ++K) {
+        R s2 = R(0);
+#pragma unroll
+        for (int L2 = 0; L2 < D; ++L2) s2 += (R)W.L[(int64_t)(K * D + L2) * cap + i] * fac * r[L2];
+        gt[K] = s2;
+        rg += r[K] * s2;
+    }
+    R F = rg / (rr2 * rr2), q[M];
+    qvec<D, R>(r, q);
+    const R V = (R)vol_of(P, c, j);
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        R bq = R(0), gg = R(0);
+#pragma unroll
+        for (int a = 0; a < M; ++a) bq += (R)W.adj[(int64_t)(cc * S + a) * cap + i] * q[a];
+#pragma unroll
+        for (int K = 0; K < D; ++K) gg += gt[K] * (R)W.adj[(int64_t)(cc * S + M + K) * cap + i];
+        wout[cc] = V * (F * bq + gg);
+    }
+}
+
+template <int D, typename R, int NC>
+__global__ void __launch_bounds__(128) k_sph2_adjm2(DevParams P, const Part c, Work W, int n,
+                                                    double *phibar)
+{
+    int jdx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jdx >= n) return;
+    const int o = c.orig[jdx];
+    const int tj = c.type[jdx];
+    if (tj == VIRTUAL) {
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) phibar[(int64_t)cc * n + o] = 0.0;
+        return;
+    }
+    const int64_t cap = W.cap;
+    double xj[3];
+    load_hat<D>(c, jdx, xj);
+    Acc<R> acc[NC];
+    R wv[NC];
+    const int cnt = W.nbr_cnt[jdx];
+    for (int k = 0; k < cnt; ++k) {
+        const int i = W.nbr[(int64_t)k * cap + jdx];
+        const int ti = c.type[i];
+        if (ti == VIRTUAL) continue;
+        double xi[3];
+        load_hat<D>(c, i, xi);
+        if (ti == FLUID) {   // incoming w_ij
+            adj_pair_m<D, R, NC>(P, c, W, i, jdx, xi, xj, wv);
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) acc[cc].add(wv[cc]);
+        }
+        if (tj == FLUID) {   // outgoing w_ji
+            adj_pair_m<D, R, NC>(P, c, W, jdx, i, xj, xi, wv);
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) acc[cc].add(-wv[cc]);
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) phibar[(int64_t)cc * n + o] = (double)acc[cc].val();
+}
+
+template <int D, typename R, int NC>
+static void launch_sph2_adjm(const DevParams &P, Part cur, Work W, int64_t n, const double *gbar,
+                             const double *d2bar, const double *lapbar, double *phibar,
+                             cudaStream_t st)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    k_sph2_adjm1<D, R, NC><<<g, 128, 0, st>>>(P, cur, W, (int)n, gbar, d2bar, lapbar);
+    k_sph2_adjm2<D, R, NC><<<g, 128, 0, st>>>(P, cur, W, (int)n, phibar);
+}
+
+template <int D, typename R>
+static void launch_sph2_adjm_nc(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
+                                const double *gbar, const double *d2bar, const double *lapbar,
+                                double *phibar, cudaStream_t st)
+{
+    if (ncomp == 1) launch_sph2_adjm<D, R, 1>(P, cur, W, n, gbar, d2bar, lapbar, phibar, st);
+    else if (ncomp == 2) launch_sph2_adjm<D, R, 2>(P, cur, W, n, gbar, d2bar, lapbar, phibar, st);
+    else launch_sph2_adjm<D, R, 3>(P, cur, W, n, gbar, d2bar, lapbar, phibar, st);
+}
+
 void launch_sph2_adjoint(const DevParams &P, Part cur, Work W, int64_t n, int ncomp,
                          const double *gbar, const double *d2bar, const double *lapbar,
                          double *phibar, cudaStream_t st)
 {
+    if (ncomp <= 3) {   // all fields in one pair of launches
+        if (P.dim == 2) {
+            if (P.precision == VCT_MIXED) launch_sph2_adjm_nc<2, float>(P, cur, W, n, ncomp, gbar, d2bar, lapbar, phibar, st);
+            else launch_sph2_adjm_nc<2, double>(P, cur, W, n, ncomp, gbar, d2bar, lapbar, phibar, st);
+        } else {
+            if (P.precision == VCT_MIXED) launch_sph2_adjm_nc<3, float>(P, cur, W, n, ncomp, gbar, d2bar, lapbar, phibar, st);
+            else launch_sph2_adjm_nc<3, double>(P, cur, W, n, ncomp, gbar, d2bar, lapbar, phibar, st);
+        }
+        return;
+    }
     unsigned g = (unsigned)((n + 127) / 128);
     for (int comp = 0; comp < ncomp; ++comp) {
         if (P.dim == 2) {
