@@ -509,7 +509,7 @@ vct_status vct_ppe_adjoint(vct_ctx *ctx, const double *p_bar, double *b_bar, vct
  * arithmetic in the reverse; the operators in the context's precision.
  * VCT_ERR_ARG if v_bar_in is NULL.
  * Allocates (7 dim + 3 dim^2 + 3) doubles per particle of capacity on the
- * first call (with the regularisation on, (10 dim + dim^2 + 3) more);
+ * first call (with the regularisation on, (10 dim + dim^2 + 13) more);
  * afterwards the context holds this step's pressure system (as after
  * vct_step, for vct_ppe_adjoint). */
 vct_status vct_step_backward_velocity(vct_ctx *ctx, const vct_state *state, const double *v_bar,

@@ -1444,38 +1444,67 @@ VCT_API vct_status vct_step_backward_velocity(vct_ctx *c, const vct_state *s, co
     }
     if (reg && !c->W.radj) {
         cudaError_t e = cudaSuccess;
-        c->W.radj = dalloc<double>(c, c->cap * (regadj_rows(d) + 2 * d), e);
+        // + the step-start positions, velocities and FP32 position copies kept
+        //   across the forward run (6 doubles and 2 float4 per particle)
+        c->W.radj = dalloc<double>(c, c->cap * (regadj_rows(d) + 2 * d + 10), e);
         if (e != cudaSuccess) {
             c->W.radj = nullptr;
             return VCT_ERR_CUDA;
         }
     }
+    bool assembled = false;
     if (reg) {
         // The regularisation acts last, on the corrector's x' and u': run the
         // step forward up to it, take its reverse first (into u'_bar, x'_bar),
-        // then the rest of the step's reverse from there.
+        // then the rest of the step's reverse from there, on the operators this
+        // forward run assembled (the positions, velocities and FP32 position
+        // copies that the corrector and the regularisation overwrite are kept
+        // and put back).
         double *vb_co = c->W.radj + (int64_t)regadj_rows(d) * c->cap, *xb_co = vb_co + d * n;
         reset_status(c);
         launch_load(c->P, cur(c), *s, n, c->st);
+        c->launches += 1;
         step_pre(c, n);
+        const Part pc = cur(c);
+        double *keep = c->W.radj + (int64_t)(regadj_rows(d) + 2 * d) * c->cap;
+        double *fields[6] = {pc.x, pc.y, pc.z, pc.u, pc.v, pc.w};
+        const size_t nb8 = sizeof(double) * (size_t)n, nb16 = sizeof(float4) * (size_t)n;
+        cudaError_t ce = cudaSuccess;
+        for (int q = 0; q < 6 && ce == cudaSuccess; ++q)
+            ce = cudaMemcpyAsync(keep + q * c->cap, fields[q], nb8, cudaMemcpyDeviceToDevice, c->st);
+        float4 *keepf = reinterpret_cast<float4 *>(keep + 6 * c->cap);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(keepf, c->W.hatf, nb16, cudaMemcpyDeviceToDevice, c->st);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(keepf + c->cap, c->W.hatlo, nb16, cudaMemcpyDeviceToDevice, c->st);
+        if (ce != cudaSuccess) return VCT_ERR_CUDA;
         if (step_solve(c, n, 0)) return VCT_ERR_CUDA;
         launch_corrector(c->P, cur(c), c->W, n, c->st);
         launch_regadj_save(c->P, cur(c), c->W, n, c->st);
-        c->launches += 3 + launch_regularise(c->P, cur(c), c->W, n, c->st);
+        c->launches += 2 + launch_regularise(c->P, cur(c), c->W, n, c->st);
         launch_regadj(c->P, cur(c), c->W, n, v_bar, x_bar, vb_co, xb_co, c->st);
         c->launches += 4;
-        if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
+        for (int q = 0; q < 6 && ce == cudaSuccess; ++q)
+            ce = cudaMemcpyAsync(fields[q], keep + q * c->cap, nb8, cudaMemcpyDeviceToDevice, c->st);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(c->W.hatf, keepf, nb16, cudaMemcpyDeviceToDevice, c->st);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(c->W.hatlo, keepf + c->cap, nb16, cudaMemcpyDeviceToDevice, c->st);
+        if (ce != cudaSuccess || cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
         v = finish(c, nullptr, 0);
         if (v) return v;
         // the corrector wrote the pressure history of the context: clear it
         if (vct_reset_history(c) != VCT_OK) return VCT_ERR_CUDA;
         v_bar = vb_co;
         x_bar = xb_co;
+        assembled = true;
     }
     reset_status(c);
-    launch_load(c->P, cur(c), *s, n, c->st);
-    c->launches += 1;
-    step_pre(c, n);   // the step's operators at the given positions (no solve, no update)
+    if (!assembled) {
+        launch_load(c->P, cur(c), *s, n, c->st);
+        c->launches += 1;
+        step_pre(c, n);   // the step's operators at the given positions (no solve, no update)
+    }
     launch_stepadj_a(c->P, cur(c), c->W, n, v_bar, x_bar, p_bar, c->st);
     c->launches += 2 + (c->P.smag ? 2 : 0);
     if (cudaGetLastError() != cudaSuccess) return VCT_ERR_CUDA;
