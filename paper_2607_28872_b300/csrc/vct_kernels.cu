@@ -5874,7 +5874,8 @@ __device__ __forceinline__ bool pp_unknown(const Part &c, const Work &W, int i)
     return c.type[i] == FLUID && !W.fs[i];
 }
 
-// -dw/r of the pair at separation r (projected), or 0 for coincident particles
+// -dw/r of the pair at separation r (projected), or 0 for coincident particles;
+// in the mixed form's arithmetic (FP32 there, the separation formed in FP64 first)
 template <int D>
 __device__ __forceinline__ double pair_fac(const DevParams &P, const double *r)
 {
@@ -5882,6 +5883,12 @@ __device__ __forceinline__ double pair_fac(const DevParams &P, const double *r)
 #pragma unroll
     for (int K = 0; K < D; ++K) rr2 += r[K] * r[K];
     if (rr2 == 0.0) return 0.0;
+    if (P.precision == VCT_MIXED) {
+        const float rr = sqrtf((float)rr2);
+        float w, dw;
+        kern_wdw<float>(rr, (float)P.inv_l, (float)P.ad, w, dw);
+        return (double)(-dw / rr);
+    }
     double rr = sqrt(rr2), w, dw;
     kern_wdw<double>(rr, P.inv_l, P.ad, w, dw);
     return -dw / rr;
